@@ -1,0 +1,92 @@
+"""Pins of the oracle's coupled problem and algorithms (Section 5): the
+monolithic mortar system against the interface reduction, Methods S1, S2 and
+S3 against each other, their solve counts against Eqs. 5.11-5.13 (with the
+two extra solves per realization the paper counts), and the moments against
+brute force over monolithic solves."""
+
+import numpy as np
+import pytest
+
+import sfb_workloads as W
+from oracle import coupled
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.mark.parametrize("wl", [
+    W.tiny(),
+    W.small_test(bottom_pressure=1.0, source=[0.5, -0.3, 0.2, 1.1]),
+    W.small_test(nx=7, ny=9, px=3, py=1, n_sd=2, n_dd=3, degree=2, stokes=(9, 4)),
+], ids=["tiny", "sources", "quadratic"])
+def test_monolithic_equals_interface_reduction(wl):
+    prob = coupled.Problem(wl)
+    ys, _ = prob.grid()
+    for y in ys[:3]:
+        lam_d, S, g, bs = prob.interface_dense(y)
+        lam_m, f_m = prob.monolithic(y)
+        assert _rel(lam_d, lam_m) < 1e-10
+        assert np.allclose(S, S.T, atol=1e-13 * np.abs(S).max())
+        assert np.linalg.eigvalsh(S).min() > 0
+        f_d = prob.recover(lam_d, bs)
+        for k in f_d:
+            assert _rel(f_d[k], f_m[k]) < 1e-10, k
+
+
+def test_methods_agree_and_count_solves():
+    wl = W.small_test(nx=6, ny=5, px=2, py=1, n_term=2, stokes=(6, 4),
+                      collocation={"kind": "smolyak", "lmax": 1, "rule": "paper"})
+    prob = coupled.Problem(wl)
+    ys, ws = prob.grid()
+    assert len(ys) == 2 * 4 + 1
+    l1, it1, c1 = coupled.method_s1(prob, ys, rtol=1e-13)
+    l2, it2, c2 = coupled.method_s2(prob, ys, rtol=1e-13)
+    l3, it3, c3 = coupled.method_s3(prob, ys, rtol=1e-13)
+    dense = np.array([prob.interface_dense(y)[0] for y in ys])
+    for lam in (l1, l2, l3):
+        assert _rel(lam, dense) < 1e-10
+    assert np.all(it1 > 0) and np.all(it3 > 0)
+    n_real = len(ys)
+    for s, sub in enumerate(prob.subs):
+        R = len(sub.dofs)
+        loc, _ = prob.local_realizations(s, ys)
+        assert c2[s] == (R + 2) * n_real                       # Eq. 5.12 + 2 extras
+        assert c3[s] == R * len(loc) + 2 * n_real              # Eq. 5.13 + 2 extras
+        assert c1[s] == it1.sum() + 2 * n_real                 # Eq. 5.11 + 2 extras
+        assert c3[s] < c2[s]
+
+
+def test_moments_brute_force_tiny():
+    """Mean and variance over the 16 tensor points from one monolithic solve
+    per point agree with the basis-driven pipeline."""
+    prob = coupled.Problem(W.tiny())
+    ys, ws = prob.grid()
+    lams, mom = coupled.solve_all(prob, ys, ws)
+    brute = {k: [] for k in mom}
+    lam_m = []
+    for y in ys:
+        lam, f = prob.monolithic(y)
+        lam_m.append(lam)
+        for k in brute:
+            brute[k].append(f[k])
+    assert _rel(lams, lam_m) < 1e-10
+    for k in mom:
+        v = np.array(brute[k])
+        mean = (ws[:, None] * v).sum(0)
+        var = (ws[:, None] * (v - mean) ** 2).sum(0)
+        assert _rel(mom[k][0], mean) < 1e-10, k
+        assert _rel(mom[k][1], var) < 1e-8, k
+    # the Stokes field is stochastic through the coupling (Section 6.2)
+    assert mom["stokes_u"][1].max() > 0
+    assert mom["darcy_p"][1].max() > 0
+
+
+def test_moments_definition():
+    rng = np.random.default_rng(5)
+    v = rng.normal(size=(7, 4))
+    w = rng.random(7)
+    w /= w.sum()
+    mean, var = coupled.moments(v, w)
+    assert np.allclose(mean, sum(w[i] * v[i] for i in range(7)))
+    assert np.allclose(var, sum(w[i] * v[i] ** 2 for i in range(7)) - mean ** 2)
