@@ -1,0 +1,194 @@
+/*
+ * sfb.h - C ABI of the GB300 stochastic multiscale flux basis library.
+ *
+ * The library computes, on one GPU, the hot path of Method S3 of
+ * Ambartsumyan, Khattatov, Wang, Yotov, "Stochastic multiscale flux basis for
+ * Stokes-Darcy flows" (arXiv 1802.06263, Section 5.4): for every Darcy
+ * subdomain and every local realization of its KL region the log-normal
+ * permeability (Section 2.1, Eq. 2.13), the lowest-order RT / cell-centred
+ * operator, its block-tridiagonal factorization and the multiscale flux basis
+ * (Section 5.3); then the interface problem Eq. 5.10 for a batch of global
+ * collocation points (Section 5.4, Steps 3-5) and the moments (Step 6,
+ * Eq. 2.1).
+ *
+ * Conventions shared by every entry point:
+ *  - The status is the return value; no C++ exception crosses the ABI.
+ *    sfb_last_error() returns the message of the last failing call.
+ *  - Descriptors passed in are deep-copied; the caller keeps ownership of
+ *    every pointer it passes.
+ *  - Device memory comes only from the caller: sfb_workspace_size() says how
+ *    much, sfb_set_workspace() hands it over (the caller frees it after
+ *    sfb_destroy). All device work is ordered on the stream given to
+ *    sfb_create() / sfb_set_stream(); entry points that return host data
+ *    synchronise that stream.
+ *  - "host or device" arguments are detected with cudaPointerGetAttributes;
+ *    host buffers are copied inside the call.
+ *  - Geometry: the Darcy box is tiled by px x py subdomains (s = iy*px + ix,
+ *    bottom row first); one Stokes subdomain sits on top. Global mortar DOFs:
+ *    Stokes-Darcy edges left to right, then vertical Darcy-Darcy edges row by
+ *    row, then horizontal Darcy-Darcy edges row by row; inside an interface
+ *    element by element along increasing coordinate, then local node. A
+ *    subdomain's local mortar DOFs are its global DOFs in increasing order.
+ */
+#ifndef SFB_H
+#define SFB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SFB_OK = 0,
+  SFB_ERR_ARG = 1,            /* bad argument or descriptor                     */
+  SFB_ERR_STATE = 2,          /* call out of order (e.g. moments before solve)  */
+  SFB_ERR_CUDA = 3,           /* a CUDA runtime call failed                     */
+  SFB_ERR_WORKSPACE = 4,      /* no workspace set, or it is too small           */
+  SFB_ERR_NONFINITE = 5,      /* non-finite permeability or solution            */
+  SFB_ERR_NOT_CONVERGED = 6,  /* some point did not converge (outputs filled)   */
+  SFB_ERR_NOT_SPD = 7,        /* a non-positive pivot in a factorization        */
+  SFB_ERR_UNSUPPORTED = 8     /* size beyond a compiled limit                   */
+} sfb_status;
+
+typedef enum {
+  SFB_FP64 = 0,          /* factor and solve in FP64                                  */
+  SFB_MIXED = 1,         /* FP32 factor/solves with diagonal scaling, refined by FP64 */
+                         /* residuals of the 5-point operator                          */
+  SFB_FP32_NOREFINE = 2  /* FP32 factor/solve only: diagnostics of the unrefined error */
+} sfb_precision;
+
+typedef enum { SFB_CG = 0 } sfb_krylov;
+
+typedef enum {
+  SFB_FIELD_DARCY_P = 0,     /* cell pressures, subdomain by subdomain, c = iy*nx+ix    */
+  SFB_FIELD_DARCY_FLUX = 1,  /* per subdomain: x-face normal velocities (ny x (nx+1)), */
+                             /* then y-face ones ((ny+1) x nx), +x / +y orientation    */
+  SFB_FIELD_STOKES_U = 2,    /* P2 nodes: all u_x then all u_y, node j*(2Sx+1)+i       */
+  SFB_FIELD_STOKES_P = 3     /* P1 vertices J*(Sx+1)+I                                 */
+} sfb_field;
+
+/* Problem geometry and data (Section 3.1 decomposition, Section 6 set-up). */
+typedef struct {
+  double darcy_box[4];        /* x0, x1, y0, y1                                   */
+  double stokes_box[4];       /* x0, x1, y1, y2 (same x extent, directly above)   */
+  int32_t px, py;             /* Darcy subdomain array                            */
+  const int32_t* darcy_nx;    /* [px*py] cells in x                               */
+  const int32_t* darcy_ny;    /* [px*py] cells in y                               */
+  int32_t stokes_sx, stokes_sy;
+  int32_t mortar_degree;      /* 1 or 2, discontinuous                            */
+  const int32_t* mortar_sd;   /* [px] elements on each Stokes-Darcy edge          */
+  const int32_t* mortar_dd_v; /* [py*(px-1)] vertical Darcy-Darcy edges           */
+  const int32_t* mortar_dd_h; /* [(py-1)*px] horizontal Darcy-Darcy edges         */
+  double nu_s, nu_d, alpha;   /* viscosities, BJS friction (Eqs. 2.2, 2.5, 2.10)  */
+  double u_in;                /* peak of the parabolic Stokes inflow              */
+  double bottom_pressure;     /* Dirichlet pressure on the Darcy bottom           */
+  const double* source;       /* [px*py] constant q_d per subdomain, or NULL      */
+} sfb_problem;
+
+/* One KL region per Darcy subdomain, covariance Eq. 6.1 on its rectangle. */
+typedef struct {
+  double sigma2;              /* multiplies the kernel (the variance of Y)         */
+  double eta1, eta2;          /* correlation lengths                               */
+  double mean_y;              /* E[Y]                                              */
+  int32_t n_term;             /* kept modes: the n_term largest products           */
+} sfb_kl_region;
+
+/* Collocation (Section 4): tensor grid of m-point rules, or the Smolyak
+ * combination formula of level lmax with 1-D rule sizes rule[p]
+ * (n_rule == 0: the paper's 2^(p+1)-1). local_tensor = 1 builds every
+ * region's basis on the full local tensor grid of the largest 1-D rule;
+ * 0 on the distinct projections of the global grid. */
+typedef struct {
+  int32_t kind;               /* 0 tensor, 1 Smolyak */
+  int32_t m;
+  int32_t lmax;
+  int32_t n_rule;
+  const int32_t* rule;
+  int32_t local_tensor;
+} sfb_collocation;
+
+typedef struct {
+  int64_t n_items;            /* (subdomain, local realization) pairs            */
+  int64_t n_flux_responses;   /* sum over items of the subdomain's mortar DOFs    */
+  int32_t max_refine_steps;   /* mixed form: largest refinement count             */
+  int32_t n_not_converged;    /* mixed form: items that stopped above tolerance   */
+  double max_rel_residual;    /* final ||B - A X||_F / ||B||_F over items         */
+  double max_first_correction;/* mixed form: max ||dX_1||_F / ||X||_F: the        */
+                              /* relative error of the unrefined FP32 solve       */
+  double ms;                  /* device time of the build (CUDA events)           */
+} sfb_basis_stats;
+
+typedef struct sfb_ctx sfb_ctx;
+
+/* Creates a context for one problem on the current CUDA device; stream is a
+ * cudaStream_t (NULL = legacy default stream). Copies the descriptor and
+ * assembles the host-side geometry (interfaces, mortar DOF maps, face
+ * projections of Section 5.2 step 1). No device memory is touched. */
+sfb_status sfb_create(const sfb_problem* prob, void* stream, sfb_ctx** out);
+void sfb_destroy(sfb_ctx* ctx);
+const char* sfb_last_error(const sfb_ctx* ctx);
+sfb_status sfb_set_stream(sfb_ctx* ctx, void* stream);
+
+/* Sizes of the problem: total mortar DOFs, Darcy subdomains, the mortar DOF
+ * count of a subdomain (sub = -1: the Stokes subdomain), and field lengths. */
+sfb_status sfb_sizes(const sfb_ctx* ctx, int64_t* n_lambda, int32_t* n_darcy);
+sfb_status sfb_subdomain_dofs(const sfb_ctx* ctx, int32_t sub, int32_t* n_dof,
+                              int64_t* global_dofs /* nullable [n_dof] */);
+sfb_status sfb_field_size(const sfb_ctx* ctx, int32_t field, int64_t* n);
+
+/* KL eigenpairs of Eq. 2.11 for the covariance Eq. 6.1 of every region (one
+ * per Darcy subdomain, in subdomain order), from the 1-D transcendental
+ * equations of the exponential kernel. eigvals_out (nullable, host) receives
+ * sum(n_term) eigenvalues, region by region, in decreasing order. */
+sfb_status sfb_kl_setup(sfb_ctx* ctx, const sfb_kl_region* regions, int32_t n_regions,
+                        double* eigvals_out);
+
+/* Global grid (Section 4.1 / 4.2) and every region's local realizations
+ * (Section 5.4 Steps 1-2). n_pts_out receives the global point count. */
+sfb_status sfb_collocation_setup(sfb_ctx* ctx, const sfb_collocation* spec, int64_t* n_pts_out);
+/* Copies the global grid to host buffers y_out [n_pts x n_dim] and w_out [n_pts]. */
+sfb_status sfb_collocation_points(const sfb_ctx* ctx, double* y_out, double* w_out);
+/* Local realization count and coordinates [n_local x n_term] of a region. */
+sfb_status sfb_local_points(const sfb_ctx* ctx, int32_t region, int32_t* n_local, double* y_out);
+
+/* Device bytes needed for precision `prec` and batches of up to max_pts
+ * points, and the hand-over of that memory (256-byte aligned). */
+sfb_status sfb_workspace_size(const sfb_ctx* ctx, int32_t prec, int64_t max_pts, size_t* bytes);
+sfb_status sfb_set_workspace(sfb_ctx* ctx, void* dev_ptr, size_t bytes);
+
+/* Section 5.4 pre-computation loop for every (Darcy subdomain, local
+ * realization) item: permeability, assembly, block-tridiagonal
+ * factorization, R+1 right-hand sides (R mortar DOFs plus the particular
+ * problem Eqs. 5.7-5.8), and the flux basis Phi[l][j] = -<u*(xi_j).n, xi_l>
+ * with g[l] = <u_bar.n, xi_l>; also the deterministic Stokes basis (Section
+ * 5.4: N_real = 1 for Stokes subdomains). stats_out is nullable. */
+sfb_status sfb_build_stochastic_basis(sfb_ctx* ctx, int32_t prec, sfb_basis_stats* stats_out);
+
+/* Read-back of one stored basis item (host buffers): phi [R x R] row-major,
+ * g [R], x [n_cells x (R+1)] (pressure responses, nullable). sub = -1 and
+ * k = 0 return the Stokes basis (x must be NULL). */
+sfb_status sfb_get_basis(sfb_ctx* ctx, int32_t sub, int32_t k, double* phi, double* g, double* x);
+
+/* Section 5.4 Steps 3-6 for a batch of global points y [n_pts x n_dim] with
+ * weights w [n_pts] (host or device): local index conversion, CG on
+ * S^l = sum_i R_i^T Phi_i^{k_i(l)} R_i (Eq. 5.10) from zero until
+ * ||r|| <= rtol ||g||, recovery and accumulation of the moments. Outputs
+ * (nullable, host or device): lambda_out [n_pts x n_lambda], iters_out
+ * [n_pts] (negative: not converged). Returns SFB_ERR_NOT_CONVERGED with all
+ * outputs filled if a point did not converge within max_it. */
+sfb_status sfb_interface_solve_batch(sfb_ctx* ctx, const double* y, const double* w, int64_t n_pts,
+                                     int32_t krylov, double rtol, int32_t max_it,
+                                     double* lambda_out, int32_t* iters_out);
+
+/* Mean and variance (Eq. 2.1; variance sum_l w_l (x_l - mean)^2) of a field
+ * over every point solved since the last reset (host buffers of the field's
+ * length). SFB_ERR_STATE if nothing was solved. */
+sfb_status sfb_moments(sfb_ctx* ctx, int32_t field, double* mean_out, double* var_out);
+sfb_status sfb_moments_reset(sfb_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFB_H */

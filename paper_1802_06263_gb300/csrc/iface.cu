@@ -1,0 +1,650 @@
+// Main loop of Method S3 (Section 5.4, Steps 3-6) for a batch of global
+// collocation points, all on the device:
+//  Step 4  kmap_kernel: global -> local index of every point in every KL
+//          region (projection of y onto the region's dims, looked up in an
+//          open-addressing table of the local realizations);
+//          group_kernel: points of each subdomain grouped by local index
+//          (stable), cut into tiles that share one stored basis Phi_i^k;
+//  Step 5  CG on S^l = sum_i R_i^T Phi_i^{k_i(l)} R_i (Eq. 5.10), all points in
+//          lockstep: matvec_kernel applies each stored basis to the tile of
+//          points that use it, update_kernel assembles q = S p per point from
+//          the per-subdomain products and does the CG update with
+//          warp-shuffle dot products;
+//  Step 6  recovery u = u*(lambda) + u_bar and the collocation-weighted
+//          moments: darcy_moments_kernel / stokes_moments_kernel accumulate
+//          sum w (x - shift) and sum w (x - shift)^2 per field entry in a
+//          fixed order (deterministic, no atomics on floating point).
+#include <algorithm>
+#include <cmath>
+
+#include "sfb_ctx.h"
+
+namespace sfb {
+
+namespace {
+
+constexpr int kTP = 8;  // points per matvec / moments tile
+
+__host__ __device__ inline uint64_t mix_key(uint64_t h, int64_t v) {
+  h ^= (uint64_t)v;
+  h *= 1099511628211ull;
+  return h;
+}
+__host__ __device__ inline uint64_t fin_key(uint64_t h) { return h ^ (h >> 29); }
+__device__ inline int64_t qkey_dev(double v) {
+  const double r = v * 1e12;
+  return (int64_t)(r < 0 ? r - 0.5 : r + 0.5);
+}
+
+__global__ void kmap_kernel(const double* y, int64_t n_pts, int n_dim, const SubDev* subs, int ns,
+                            const int* dim_off, const double* yloc, const int* hash, const int64_t* hash_off,
+                            const int* hash_cap, int* kmap, int* pstat) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_pts * ns;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = e / ns;
+    const int s = (int)(e - l * ns);
+    const int nt = subs[s].n_term;
+    const double* yl = y + l * n_dim + dim_off[s];
+    uint64_t h = 1469598103934665603ull;
+    for (int j = 0; j < nt; ++j) h = mix_key(h, qkey_dev(yl[j]));
+    h = fin_key(h);
+    const int cap = hash_cap[s];
+    const int* tab = hash + hash_off[s];
+    int found = -1;
+    for (int probe = 0; probe < cap; ++probe) {
+      const int slot = (int)((h + probe) & (uint64_t)(cap - 1));
+      const int k = tab[slot];
+      if (k < 0) break;
+      const double* cand = yloc + subs[s].yloc_off + (int64_t)k * nt;
+      bool eq = true;
+      for (int j = 0; j < nt; ++j) eq = eq && (qkey_dev(cand[j]) == qkey_dev(yl[j]));
+      if (eq) { found = k; break; }
+    }
+    kmap[l * ns + s] = found;
+    if (found < 0) atomicOr(&pstat[l], 0x40000000);
+  }
+}
+
+// One CTA per Darcy subdomain: histogram, scan, stable scatter, tiles.
+__global__ void __launch_bounds__(256) group_kernel(const int* kmap, int64_t n_pts, int ns, const SubDev* subs,
+                                                    const int64_t* loc_off, int* grp_count, int* grp_start,
+                                                    int* grp_pts, int64_t pts_ld, int* tiles, int max_tiles,
+                                                    int* n_tiles) {
+  const int s = blockIdx.x;
+  const int nl = subs[s].n_local;
+  int* cnt = grp_count + loc_off[s];
+  int* start = grp_start + loc_off[s];
+  int* pts = grp_pts + (int64_t)s * pts_ld;
+  for (int k = threadIdx.x; k < nl; k += blockDim.x) cnt[k] = 0;
+  __syncthreads();
+  for (int64_t l = threadIdx.x; l < n_pts; l += blockDim.x) {
+    const int k = kmap[l * ns + s];
+    if (k >= 0) atomicAdd(&cnt[k], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int k = 0; k < nl; ++k) { start[k] = acc; acc += cnt[k]; cnt[k] = start[k]; }
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {  // stable scatter by one warp, 32 points at a time
+    const int lane = threadIdx.x;
+    for (int64_t base = 0; base < n_pts; base += 32) {
+      const int64_t l = base + lane;
+      const int k = l < n_pts ? kmap[l * ns + s] : -1;
+      const unsigned peers = __match_any_sync(0xffffffffu, k);
+      const int rank = __popc(peers & ((1u << lane) - 1u));
+      int pos = 0;
+      if (k >= 0) pos = cnt[k];
+      __syncwarp();
+      if (k >= 0) {
+        pts[pos + rank] = (int)l;
+        if (rank == 0) cnt[k] = pos + __popc(peers);
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int nt_ = 0;
+    for (int k = 0; k < nl; ++k) {
+      const int c0 = start[k], c1 = cnt[k];  // cnt now holds the end of group k
+      for (int q = c0; q < c1 && nt_ < max_tiles; q += kTP) {
+        tiles[3 * ((int64_t)s * max_tiles + nt_) + 0] = k;
+        tiles[3 * ((int64_t)s * max_tiles + nt_) + 1] = q;
+        tiles[3 * ((int64_t)s * max_tiles + nt_) + 2] = min(kTP, c1 - q);
+        ++nt_;
+      }
+    }
+    n_tiles[s] = nt_;
+  }
+}
+
+// Stokes unit: one group holding every point in order.
+__global__ void stokes_group_kernel(int64_t n_pts, int unit, int* grp_pts, int64_t pts_ld, int* tiles,
+                                    int max_tiles, int* n_tiles) {
+  int* pts = grp_pts + (int64_t)unit * pts_ld;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n_pts; l += (int64_t)gridDim.x * blockDim.x)
+    pts[l] = (int)l;
+  const int nt_ = (int)((n_pts + kTP - 1) / kTP);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt_ && t < max_tiles; t += gridDim.x * blockDim.x) {
+    tiles[3 * ((int64_t)unit * max_tiles + t) + 0] = 0;
+    tiles[3 * ((int64_t)unit * max_tiles + t) + 1] = t * kTP;
+    tiles[3 * ((int64_t)unit * max_tiles + t) + 2] = (int)(n_pts - (int64_t)t * kTP < kTP ? n_pts - (int64_t)t * kTP : kTP);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) n_tiles[unit] = min(nt_, max_tiles);
+}
+
+struct IfaceArgs {
+  const SubDev* subs;
+  int ns;               // Darcy subdomains; unit ns is the Stokes subdomain
+  const ItemOff* off;
+  const double* phi;    // Darcy basis store
+  const double* s_phi;  // Stokes basis
+  int Rs;
+  const int64_t* gdof;  // Darcy local -> global
+  const int64_t* sgdof; // Stokes local -> global
+  const int64_t* ybase; // per unit offset into a point's Y row
+  int64_t NY;
+  const int* ldof;      // per global DOF: unit_a, local_a, unit_b, local_b
+  int64_t n_lambda;
+  const int* kmap;
+  const int* grp_pts;
+  int64_t pts_ld;
+  const int* tiles;
+  int max_tiles;
+  const int* n_tiles;
+  double* lam;
+  double* r;
+  double* p;
+  double* Y;
+  double* rr;
+  double* gn;
+  int* pstat;
+  int64_t n_pts;
+};
+
+__device__ __forceinline__ const double* unit_phi(const IfaceArgs& a, int u, int k, int& R) {
+  if (u == a.ns) { R = a.Rs; return a.s_phi; }
+  const SubDev& S = a.subs[u];
+  R = S.R;
+  return a.phi + a.off[S.item0 + k].phi;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// r = g = sum_i R_i^T g_i^{k_i(l)}, p = r, lambda = 0; one warp per point.
+__global__ void init_kernel(IfaceArgs a) {
+  const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (l >= a.n_pts) return;
+  double s2 = 0.0;
+  for (int64_t d = lane; d < a.n_lambda; d += 32) {
+    double g = 0.0;
+    for (int side = 0; side < 2; ++side) {
+      const int u = a.ldof[4 * d + 2 * side], loc = a.ldof[4 * d + 2 * side + 1];
+      int R;
+      const int k = u < a.ns ? a.kmap[l * a.ns + u] : 0;
+      if (k < 0) continue;
+      const double* ph = unit_phi(a, u, k, R);
+      g += ph[R * R + loc];
+    }
+    a.r[l * a.n_lambda + d] = g;
+    a.p[l * a.n_lambda + d] = g;
+    a.lam[l * a.n_lambda + d] = 0.0;
+    s2 += g * g;
+  }
+  s2 = warp_sum(s2);
+  if (lane == 0) {
+    a.rr[l] = s2;
+    a.gn[l] = sqrt(s2);
+    int st = a.pstat[l] & 0x40000000;  // keep a bad-index mark
+    if (!st && s2 == 0.0) st = 1;       // zero data: converged with lambda = 0
+    a.pstat[l] = st;
+  }
+}
+
+// Y[l][ybase_u + :] = Phi_u^k (R_u p_l) for the points of one tile.
+__global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a) {
+  extern __shared__ __align__(16) double smv[];
+  const int u = blockIdx.y;
+  const int t = blockIdx.x;
+  if (t >= a.n_tiles[u]) return;
+  const int* tl = a.tiles + 3 * ((int64_t)u * a.max_tiles + t);
+  const int k = tl[0], q0 = tl[1], cntp = tl[2];
+  int R;
+  const double* ph = unit_phi(a, u, k, R);
+  const int64_t* gd = u == a.ns ? a.sgdof : a.gdof + a.subs[u].gdof_off;
+  double* Ph = smv;             // [R][R]
+  double* Pv = smv + R * R;     // [kTP][R]
+  const int* pts = a.grp_pts + (int64_t)u * a.pts_ld + q0;
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) Ph[e] = ph[e];
+  for (int e = threadIdx.x; e < cntp * R; e += blockDim.x) {
+    const int q = e / R, i = e - q * R;
+    const int64_t l = pts[q];
+    Pv[e] = a.pstat[l] == 0 ? a.p[l * a.n_lambda + gd[i]] : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < cntp * R; e += blockDim.x) {
+    const int q = e / R, i = e - q * R;
+    const int64_t l = pts[q];
+    if (a.pstat[l] != 0) continue;
+    const double* row = Ph + i * R;
+    const double* v = Pv + q * R;
+    double acc = 0.0;
+    for (int j = 0; j < R; ++j) acc = fma(row[j], v[j], acc);
+    a.Y[l * a.NY + a.ybase[u] + i] = acc;
+  }
+}
+
+// q = S p from the per-unit products, then the CG update; one warp per point.
+__global__ void update_kernel(IfaceArgs a, int it, double rtol) {
+  const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (l >= a.n_pts) return;
+  if (a.pstat[l] != 0) return;
+  const double* Yl = a.Y + l * a.NY;
+  double* pl = a.p + l * a.n_lambda;
+  double* rl = a.r + l * a.n_lambda;
+  double* ll = a.lam + l * a.n_lambda;
+  double pq = 0.0;
+  for (int64_t d = lane; d < a.n_lambda; d += 32) {
+    const int ua = a.ldof[4 * d], la = a.ldof[4 * d + 1], ub = a.ldof[4 * d + 2], lb = a.ldof[4 * d + 3];
+    const double q = Yl[a.ybase[ua] + la] + Yl[a.ybase[ub] + lb];
+    pq += pl[d] * q;
+  }
+  pq = warp_sum(pq);
+  const double rr = a.rr[l];
+  const double alpha = pq > 0.0 ? rr / pq : 0.0;
+  double rn = 0.0;
+  for (int64_t d = lane; d < a.n_lambda; d += 32) {
+    const int ua = a.ldof[4 * d], la = a.ldof[4 * d + 1], ub = a.ldof[4 * d + 2], lb = a.ldof[4 * d + 3];
+    const double q = Yl[a.ybase[ua] + la] + Yl[a.ybase[ub] + lb];
+    ll[d] += alpha * pl[d];
+    const double rv = rl[d] - alpha * q;
+    rl[d] = rv;
+    rn += rv * rv;
+  }
+  rn = warp_sum(rn);
+  const bool done = sqrt(rn) <= rtol * a.gn[l] || !(pq > 0.0);
+  if (!done) {
+    const double beta = rn / rr;
+    for (int64_t d = lane; d < a.n_lambda; d += 32) pl[d] = rl[d] + beta * pl[d];
+  }
+  __syncwarp();
+  if (lane == 0) {
+    a.rr[l] = rn;
+    if (done) a.pstat[l] = pq > 0.0 ? it + 1 : -(it + 1);
+  }
+}
+
+__global__ void count_active(const int* pstat, int64_t n, int* out) {
+  int c = 0;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x)
+    c += pstat[l] == 0;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+__global__ void finish_status(int* pstat, int64_t n, int max_it, int* iters_out) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
+    int s = pstat[l];
+    if (s == 0) s = -max_it;
+    else if (s & 0x40000000) s = -max_it;
+    pstat[l] = s;
+    if (iters_out) iters_out[l] = s;
+  }
+}
+
+// ---- moments ---------------------------------------------------------------------
+struct MomArgs {
+  IfaceArgs ia;
+  const double* X;
+  const double* T;
+  const double* proj;
+  const double* w;
+  double* mom;          // [3][len]: shift, S1, S2 (offsets by field)
+  int64_t off_p, off_f, len_p, len_f, sub_p0, sub_f0;
+  int64_t mom_len_total;
+  int mode;             // 0: write shifts from point 0; 1: accumulate
+  int rt;               // rows per CTA
+  const int64_t* cell_off;  // per subdomain first cell in the Darcy pressure field
+  const int64_t* face_off;  // per subdomain first face in the Darcy flux field
+};
+
+__device__ __forceinline__ void mom_add(double* mom, int64_t L, int64_t idx, double v, double w, int mode) {
+  if (mode == 0) { mom[idx] = v; return; }
+  const double d = v - mom[idx];
+  mom[L + idx] += w * d;
+  mom[2 * L + idx] += w * d * d;
+}
+
+// One CTA per (row tile, subdomain). For every local realization k and every
+// tile of the points that use it: pressures z = X^k [R lambda; 1] on the tile
+// rows plus one halo row below, then pressures and face velocities.
+__global__ void __launch_bounds__(256) darcy_moments_kernel(MomArgs m) {
+  extern __shared__ __align__(16) double sm[];
+  const IfaceArgs& a = m.ia;
+  const int s = blockIdx.y;
+  const SubDev S = a.subs[s];
+  const int nx = S.nx, ny = S.ny, R = S.R, C = R + 1;
+  const int r0 = blockIdx.x * m.rt;
+  if (r0 >= ny) return;
+  const int r1 = min(ny, r0 + m.rt);
+  const int h0 = max(0, r0 - 1);            // first row evaluated (halo)
+  const int nrows = r1 - h0;
+  const int ncell = nrows * nx;
+  double* Cf = sm;                          // [kTP][C] coefficients
+  double* Z = Cf + kTP * C;                 // [ncell][kTP]
+  double* Wt = Z + ncell * kTP;             // [kTP]
+  const int64_t L = m.mom_len_total;
+  const int64_t* gd = a.gdof + S.gdof_off;
+  const int mode = m.mode;
+  for (int t = 0; t < a.n_tiles[s]; ++t) {
+    {
+      const int* tl = a.tiles + 3 * ((int64_t)s * a.max_tiles + t);
+      const int k = tl[0];
+      const ItemOff off = a.off[S.item0 + k];
+      const double* X = m.X + off.x;
+      const double* Tx = m.T + off.t;
+      const double* Ty = Tx + (int64_t)ny * (nx + 1);
+      const int q0 = tl[1];
+      int cntp = tl[2];
+      const int* pts = a.grp_pts + (int64_t)s * a.pts_ld + q0;
+      if (mode == 0) {
+        // only point 0 defines the shifts
+        int has0 = -1;
+        for (int q = 0; q < cntp; ++q) if (pts[q] == 0) has0 = q;
+        if (has0 < 0) continue;
+        pts += has0;
+        cntp = 1;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < cntp * C; e += blockDim.x) {
+        const int q = e / C, i = e - q * C;
+        const int64_t l = pts[q];
+        Cf[e] = i < R ? a.lam[l * a.n_lambda + gd[i]] : 1.0;
+      }
+      for (int q = threadIdx.x; q < cntp; q += blockDim.x) Wt[q] = m.w[pts[q]];
+      __syncthreads();
+      for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+        const double* xr = X + ((int64_t)h0 * nx + c) * C;
+        double acc[kTP];
+#pragma unroll
+        for (int q = 0; q < kTP; ++q) acc[q] = 0.0;
+        for (int i = 0; i < C; ++i) {
+          const double xv = xr[i];
+#pragma unroll
+          for (int q = 0; q < kTP; ++q) acc[q] = fma(xv, Cf[q * C + i], acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < kTP; ++q) Z[c * kTP + q] = acc[q];
+      }
+      __syncthreads();
+      // pressures of the owned rows
+      for (int c = threadIdx.x; c < (r1 - r0) * nx; c += blockDim.x) {
+        const int zc = (r0 - h0) * nx + c;
+        const int64_t idx = m.off_p + m.cell_off[s] + (int64_t)r0 * nx + c;
+        for (int q = 0; q < cntp; ++q) mom_add(m.mom, L, idx, Z[zc * kTP + q], Wt[q], mode);
+      }
+      // x-face velocities of the owned rows
+      for (int f = threadIdx.x; f < (r1 - r0) * (nx + 1); f += blockDim.x) {
+        const int rr_ = r0 + f / (nx + 1), ix = f % (nx + 1);
+        const int zrow = (rr_ - h0) * nx;
+        const double t = Tx[(int64_t)rr_ * (nx + 1) + ix];
+        const int64_t idx = m.off_f + m.face_off[s] + (int64_t)rr_ * (nx + 1) + ix;
+        for (int q = 0; q < cntp; ++q) {
+          double v;
+          if (ix > 0 && ix < nx) {
+            v = t * (Z[(zrow + ix - 1) * kTP + q] - Z[(zrow + ix) * kTP + q]) / S.hy;
+          } else {
+            const int side = ix == 0 ? 3 : 1;
+            const int cell = ix == 0 ? 0 : nx - 1;
+            double gb = 0.0;
+            if (S.side_type[side] == SIDE_IFACE) {
+              const double* P = m.proj + S.proj_off[side] + (int64_t)rr_ * R;
+              for (int i = 0; i < R; ++i) gb += P[i] * Cf[q * C + i];
+            } else if (S.side_type[side] == SIDE_DIRICHLET) {
+              gb = S.side_val[side];
+            }
+            const double F = S.side_type[side] == SIDE_NOFLOW ? 0.0 : t * (Z[(zrow + cell) * kTP + q] - gb);
+            v = (ix == 0 ? -F : F) / S.hy;
+          }
+          mom_add(m.mom, L, idx, v, Wt[q], mode);
+        }
+      }
+      // y-face velocities: faces r0..r1-1 (face j lies below row j), plus the top one
+      const int ftop = (r1 == ny) ? ny + 1 : r1;
+      for (int f = threadIdx.x; f < (ftop - r0) * nx; f += blockDim.x) {
+        const int j = r0 + f / nx, ix = f % nx;
+        const double t = Ty[(int64_t)j * nx + ix];
+        const int64_t idx = m.off_f + m.face_off[s] + (int64_t)ny * (nx + 1) + (int64_t)j * nx + ix;
+        for (int q = 0; q < cntp; ++q) {
+          double v;
+          if (j > 0 && j < ny) {
+            v = t * (Z[((j - 1 - h0) * nx + ix) * kTP + q] - Z[((j - h0) * nx + ix) * kTP + q]) / S.hx;
+          } else {
+            const int side = j == 0 ? 0 : 2;
+            const int zr = j == 0 ? 0 - h0 : ny - 1 - h0;
+            double gb = 0.0;
+            if (S.side_type[side] == SIDE_IFACE) {
+              const double* P = m.proj + S.proj_off[side] + (int64_t)ix * R;
+              for (int i = 0; i < R; ++i) gb += P[i] * Cf[q * C + i];
+            } else if (S.side_type[side] == SIDE_DIRICHLET) {
+              gb = S.side_val[side];
+            }
+            const double F = S.side_type[side] == SIDE_NOFLOW ? 0.0 : t * (Z[(zr * nx + ix) * kTP + q] - gb);
+            v = (j == 0 ? -F : F) / S.hx;
+          }
+          mom_add(m.mom, L, idx, v, Wt[q], mode);
+        }
+      }
+      if (mode == 0) break;
+    }
+  }
+}
+
+// Stokes velocity and pressure moments: one thread per field entry, every
+// point in order: x = U_s [R_s lambda; 1].
+__global__ void __launch_bounds__(256) stokes_moments_kernel(MomArgs m, const double* U, int n_u, const double* Pm,
+                                                              int n_p, int64_t off_u, int64_t off_pp) {
+  extern __shared__ __align__(16) double sm[];
+  const IfaceArgs& a = m.ia;
+  const int Rs = a.Rs, Cs = Rs + 1;
+  const int64_t L = m.mom_len_total;
+  double* Cf = sm;            // [kTP][Cs]
+  double* Wt = Cf + kTP * Cs;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = e < n_u + n_p;
+  const double* row = valid ? (e < n_u ? U + (int64_t)e * Cs : Pm + (int64_t)(e - n_u) * Cs) : U;
+  const int64_t idx = e < n_u ? off_u + e : off_pp + (e - n_u);
+  const int64_t npts = m.mode == 0 ? 1 : a.n_pts;
+  for (int64_t q0 = 0; q0 < npts; q0 += kTP) {
+    const int cntp = (int)(npts - q0 < kTP ? npts - q0 : kTP);
+    __syncthreads();
+    for (int t = threadIdx.x; t < cntp * Cs; t += blockDim.x) {
+      const int q = t / Cs, i = t - q * Cs;
+      Cf[t] = i < Rs ? a.lam[(q0 + q) * a.n_lambda + a.sgdof[i]] : 1.0;
+    }
+    for (int q = threadIdx.x; q < cntp; q += blockDim.x) Wt[q] = m.w[q0 + q];
+    __syncthreads();
+    if (!valid) continue;
+    double acc[kTP];
+#pragma unroll
+    for (int q = 0; q < kTP; ++q) acc[q] = 0.0;
+    for (int i = 0; i < Cs; ++i) {
+      const double xv = row[i];
+#pragma unroll
+      for (int q = 0; q < kTP; ++q) acc[q] = fma(xv, Cf[q * Cs + i], acc[q]);
+    }
+    for (int q = 0; q < cntp; ++q) mom_add(m.mom, L, idx, acc[q], Wt[q], m.mode);
+  }
+}
+
+__global__ void weight_sum(const double* w, int64_t n, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int64_t l = 0; l < n; ++l) s += w[l];
+  out[0] += s;
+}
+
+// mean = shift W + S1, var = S2 - 2 (mean - shift) S1 + (mean - shift)^2 W
+__global__ void finalize_moments(const double* mom, int64_t L, int64_t off, int64_t n, const double* W,
+                                 double* mean, double* var) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double sh = mom[off + e], s1 = mom[L + off + e], s2 = mom[2 * L + off + e], w = W[0];
+    const double mu = sh * w + s1;
+    const double dm = mu - sh;
+    mean[e] = mu;
+    var[e] = s2 - 2.0 * dm * s1 + dm * dm * w;
+  }
+}
+
+}  // namespace
+
+// ---- host orchestration -----------------------------------------------------------------
+void build_hash_tables(sfb_ctx* c, std::vector<int>& table, std::vector<int64_t>& off, std::vector<int>& cap) {
+  const int ns = (int)c->subs.size();
+  table.clear(); off.assign(ns, 0); cap.assign(ns, 0);
+  for (int s = 0; s < ns; ++s) {
+    int cp = 1;
+    while (cp < 2 * c->n_local[s] + 1) cp <<= 1;
+    off[s] = (int64_t)table.size();
+    cap[s] = cp;
+    table.resize(table.size() + cp, -1);
+    const int nt = c->subs[s].n_term;
+    for (int k = 0; k < c->n_local[s]; ++k) {
+      uint64_t h = 1469598103934665603ull;
+      for (int j = 0; j < nt; ++j) h = mix_key(h, qkey(c->loc_y[s][(size_t)k * nt + j]));
+      h = fin_key(h);
+      for (int probe = 0; probe < cp; ++probe) {
+        const int slot = (int)((h + probe) & (uint64_t)(cp - 1));
+        if (table[off[s] + slot] < 0) { table[off[s] + slot] = k; break; }
+      }
+    }
+  }
+}
+
+static IfaceArgs make_args(sfb_ctx* c, int64_t n_pts) {
+  Dev& d = c->dev;
+  IfaceArgs a;
+  a.subs = d.subs; a.ns = (int)c->subs.size(); a.off = d.off; a.phi = d.phi; a.s_phi = d.s_phi;
+  a.Rs = (int)c->stokes.dofs.size(); a.gdof = d.gdof; a.sgdof = d.s_gdof; a.ybase = d.ybase; a.NY = c->NY;
+  a.ldof = d.ldof; a.n_lambda = c->n_lambda; a.kmap = d.kmap; a.grp_pts = d.grp_pts; a.pts_ld = c->ws_pts;
+  a.tiles = d.tiles; a.max_tiles = c->max_tiles; a.n_tiles = d.n_tiles; a.lam = d.lam; a.r = d.r; a.p = d.p;
+  a.Y = d.Y; a.rr = d.rr; a.gn = d.gn; a.pstat = d.pstat; a.n_pts = n_pts;
+  return a;
+}
+
+__global__ void count_failed(const int* pstat, int64_t n, int* out) {
+  int c = 0;
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x)
+    c += pstat[l] < 0;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it, int* n_failed) {
+  Dev& d = c->dev;
+  cudaStream_t st = c->stream;
+  const int ns = (int)c->subs.size();
+  const int nu = ns + 1;
+  cudaError_t e;
+#define CK(x) do { e = (x); if (e != cudaSuccess) { c->err = std::string("interface solve: ") + cudaGetErrorString(e); return SFB_ERR_CUDA; } } while (0)
+  CK(cudaMemsetAsync(d.pstat, 0, sizeof(int) * n_pts, st));
+  const int64_t tot = n_pts * ns;
+  kmap_kernel<<<(int)std::min<int64_t>((tot + 255) / 256, 8192), 256, 0, st>>>(
+      d.y, n_pts, c->grid.n_dim, d.subs, ns, d.dim_off, d.yloc, d.hash, d.hash_off, d.hash_cap, d.kmap, d.pstat);
+  CK(cudaGetLastError());
+  group_kernel<<<ns, 256, 0, st>>>(d.kmap, n_pts, ns, d.subs, d.loc_off, d.grp_count, d.grp_start, d.grp_pts,
+                                   c->ws_pts, d.tiles, c->max_tiles, d.n_tiles);
+  stokes_group_kernel<<<64, 256, 0, st>>>(n_pts, ns, d.grp_pts, c->ws_pts, d.tiles, c->max_tiles, d.n_tiles);
+  CK(cudaGetLastError());
+  IfaceArgs a = make_args(c, n_pts);
+  const int warps_per_block = 8;
+  const int ublocks = (int)((n_pts + warps_per_block - 1) / warps_per_block);
+  init_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a);
+  CK(cudaGetLastError());
+  int maxR = (int)c->stokes.dofs.size();
+  for (const HostSub& S : c->subs) maxR = std::max(maxR, (int)S.dofs.size());
+  const size_t smv = sizeof(double) * ((size_t)maxR * maxR + (size_t)kTP * maxR);
+  CK(cudaFuncSetAttribute(matvec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv));
+  dim3 mgrid(c->max_tiles, nu);
+  const int chunk = 8;
+  int it = 0;
+  for (; it < max_it;) {
+    for (int q = 0; q < chunk && it < max_it; ++q, ++it) {
+      matvec_kernel<<<mgrid, 256, smv, st>>>(a);
+      update_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, it, rtol);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(d.active, 0, sizeof(int), st));
+    count_active<<<std::min(1024, (int)((n_pts + 255) / 256)), 256, 0, st>>>(d.pstat, n_pts, d.active);
+    int h_active = 0;
+    CK(cudaMemcpyAsync(&h_active, d.active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h_active == 0) break;
+  }
+  finish_status<<<std::min(1024, (int)((n_pts + 255) / 256)), 256, 0, st>>>(d.pstat, n_pts, max_it, nullptr);
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(d.active + 1, 0, sizeof(int), st));
+  count_failed<<<std::min(1024, (int)((n_pts + 255) / 256)), 256, 0, st>>>(d.pstat, n_pts, d.active + 1);
+  int h_failed = 0;
+  CK(cudaMemcpyAsync(&h_failed, d.active + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *n_failed = h_failed;
+  return SFB_OK;
+#undef CK
+}
+
+sfb_status moments_accumulate_device(sfb_ctx* c, int64_t n_pts) {
+  Dev& d = c->dev;
+  cudaStream_t st = c->stream;
+  const int ns = (int)c->subs.size();
+  cudaError_t e;
+#define CK(x) do { e = (x); if (e != cudaSuccess) { c->err = std::string("moments: ") + cudaGetErrorString(e); return SFB_ERR_CUDA; } } while (0)
+  MomArgs m;
+  m.ia = make_args(c, n_pts);
+  m.X = d.X; m.T = d.T; m.proj = d.proj; m.w = d.w; m.mom = d.mom;
+  m.off_p = c->mom_off[0]; m.off_f = c->mom_off[1]; m.len_p = c->mom_len[0]; m.len_f = c->mom_len[1];
+  m.mom_len_total = c->mom_off[3] + c->mom_len[3];
+  m.rt = 4;
+  m.cell_off = d.cell_off; m.face_off = d.face_off;
+  int max_ny = 0, max_nx = 0, maxC = 0;
+  for (const HostSub& S : c->subs) {
+    max_ny = std::max(max_ny, S.ny); max_nx = std::max(max_nx, S.nx);
+    maxC = std::max(maxC, (int)S.dofs.size() + 1);
+  }
+  const size_t smd = sizeof(double) * ((size_t)kTP * maxC + (size_t)(m.rt + 1) * max_nx * kTP + kTP);
+  CK(cudaFuncSetAttribute(darcy_moments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd));
+  const int Cs = (int)c->stokes.dofs.size() + 1;
+  const size_t sms = sizeof(double) * ((size_t)kTP * Cs + kTP);
+  const int n_se = c->stokes.n_u + c->stokes.n_p;
+  dim3 dgrid((max_ny + m.rt - 1) / m.rt, ns);
+  for (int mode = c->mom_shift_set ? 1 : 0; mode <= 1; ++mode) {
+    m.mode = mode;
+    darcy_moments_kernel<<<dgrid, 256, smd, st>>>(m);
+    stokes_moments_kernel<<<(n_se + 255) / 256, 256, sms, st>>>(m, d.s_U, c->stokes.n_u, d.s_P, c->stokes.n_p,
+                                                               c->mom_off[2], c->mom_off[3]);
+    CK(cudaGetLastError());
+  }
+  c->mom_shift_set = true;
+  weight_sum<<<1, 32, 0, st>>>(d.w, n_pts, d.mom_w);
+  CK(cudaGetLastError());
+  return SFB_OK;
+#undef CK
+}
+
+sfb_status moments_finalize_device(sfb_ctx* c, int field, double* mean_d, double* var_d) {
+  const int64_t L = c->mom_off[3] + c->mom_len[3];
+  finalize_moments<<<256, 256, 0, c->stream>>>(c->dev.mom, L, c->mom_off[field], c->mom_len[field], c->dev.mom_w,
+                                               mean_d, var_d);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return SFB_ERR_CUDA; }
+  return SFB_OK;
+}
+
+}  // namespace sfb

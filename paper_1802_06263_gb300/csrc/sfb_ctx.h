@@ -1,0 +1,153 @@
+// The opaque context behind sfb_ctx* and the device workspace layout.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sfb.h"
+#include "host_setup.h"
+#include "sfb_internal.h"
+
+namespace sfb {
+
+// Bump allocator over the caller's workspace: a dry run (base == nullptr)
+// measures, a second run hands out 256-byte aligned slices.
+struct Carver {
+  char* base = nullptr;
+  size_t used = 0;
+  template <typename T>
+  T* take(size_t count) {
+    used = (used + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + used) : nullptr;
+    used += count * sizeof(T);
+    return p;
+  }
+};
+
+struct StokesHost {
+  int sx = 0, sy = 0;
+  double x0 = 0, x1 = 0, y0 = 0, y1 = 0, hx = 0, hy = 0;
+  int NX = 0, NY = 0, n_nodes = 0, n_u = 0, n_p = 0;
+  std::vector<int64_t> dofs;       // Stokes-Darcy mortar DOFs (global)
+  std::vector<int> free_index;     // full DOF (u then p) -> free index or -1
+  std::vector<int> free_to_full;   // free index -> full DOF
+  int n_free = 0;
+  // assembled system on free DOFs as unique (row, col, value) triplets
+  std::vector<int> tr_row, tr_col;
+  std::vector<double> tr_val;
+  std::vector<double> rhs;         // [n_free][R_s + 1]
+  std::vector<double> dir_val;     // full velocity vector of Dirichlet values
+  std::vector<double> nb;          // [n_bottom_nodes][R_s]: <xi_l, phi_node . n>
+  std::vector<int> nb_node;        // bottom node ids
+};
+
+struct Dev {
+  // set-up tables
+  SubDev* subs = nullptr;
+  double* proj = nullptr;
+  int* dofinfo = nullptr;
+  double* kl = nullptr;
+  double* yloc = nullptr;
+  int64_t* gdof = nullptr;
+  int* item_sub = nullptr;
+  int* item_k = nullptr;
+  ItemOff* off = nullptr;
+  // basis store
+  double* X = nullptr;
+  double* T = nullptr;
+  void* G = nullptr;
+  void* Z = nullptr;
+  double* phi = nullptr;
+  double* D = nullptr;
+  int* status = nullptr;
+  double* resid = nullptr;
+  double* corr1 = nullptr;
+  int* nref = nullptr;
+  // Stokes
+  double* s_mat = nullptr;
+  int* s_piv = nullptr;
+  double* s_rhs = nullptr;
+  double* s_U = nullptr;     // [n_u][Cs]
+  double* s_P = nullptr;     // [n_p][Cs]
+  double* s_phi = nullptr;   // [Rs][Rs] then g [Rs]
+  double* s_dir = nullptr;
+  double* s_nb = nullptr;
+  int* s_nb_node = nullptr;
+  int* s_free_to_full = nullptr;
+  int* s_tr_row = nullptr;
+  int* s_tr_col = nullptr;
+  double* s_tr_val = nullptr;
+  int* s_status = nullptr;
+  // interface solve (sized for max_pts)
+  double* y = nullptr;
+  double* w = nullptr;
+  int* kmap = nullptr;        // [n_pts][n_sub]
+  int* hash = nullptr;        // per region open-addressing tables
+  int64_t* hash_off = nullptr;
+  int* hash_cap = nullptr;
+  int* grp_count = nullptr;   // per subdomain [n_local]
+  int* grp_start = nullptr;
+  int* grp_pts = nullptr;     // per subdomain [n_pts] points sorted by group
+  int* tiles = nullptr;       // per subdomain [max_tiles][3]
+  int* n_tiles = nullptr;     // per subdomain (+ Stokes)
+  int* ldof = nullptr;        // per global DOF: 2 (unit, local) pairs
+  double* lam = nullptr;
+  double* r = nullptr;
+  double* p = nullptr;
+  double* Y = nullptr;        // [n_pts][NY]
+  double* rr = nullptr;
+  double* gn = nullptr;
+  int* pstat = nullptr;       // per point: iterations (>0 converged, <0 active/failed)
+  int* active = nullptr;
+  int64_t* s_gdof = nullptr;  // Stokes local -> global mortar DOF
+  int64_t* ybase = nullptr;   // per unit offset into a point's Y row
+  int* dim_off = nullptr;     // per region first stochastic dimension
+  int64_t* loc_off = nullptr; // per region offset into grp_count / grp_start
+  int64_t* cell_off = nullptr;// per subdomain first cell in the Darcy pressure field
+  int64_t* face_off = nullptr;// per subdomain first face in the Darcy flux field
+  double* fin = nullptr;      // [2][max field length] finalised mean / variance
+  // moments
+  double* mom = nullptr;      // per field entry: shift, S1, S2
+  double* mom_w = nullptr;
+};
+
+}  // namespace sfb
+
+struct sfb_ctx {
+  std::string err;
+  cudaStream_t stream = nullptr;
+  // problem
+  sfb_problem prob{};
+  std::vector<int32_t> nx, ny, msd, mdv, mdh;
+  std::vector<double> source;
+  std::vector<sfb::HostSub> subs;
+  std::vector<sfb::HostIface> ifaces;
+  int64_t n_lambda = 0;
+  sfb::StokesHost stokes;
+  // state
+  bool kl_done = false, coll_done = false, basis_done = false;
+  int basis_prec = -1;
+  int64_t n_solved = 0;
+  // collocation
+  sfb::Grid grid;
+  std::vector<std::vector<double>> loc_y;  // per region [n_local][nt]
+  std::vector<int> n_local;
+  std::vector<int> dim_off;                // kappa(i, 0) per region
+  // workspace
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  int ws_prec = -1;
+  int64_t ws_pts = 0;
+  sfb::Dev dev;
+  int64_t n_items = 0;
+  int max_nx = 0, max_cols = 0, max_R = 0;
+  std::vector<sfb::ItemOff> offs;
+  std::vector<int64_t> ybase;              // per unit (Darcy subs, then Stokes) offset into Y
+  int64_t NY = 0;
+  int max_tiles = 0;
+  int64_t mom_len[4] = {0, 0, 0, 0};
+  int64_t mom_off[4] = {0, 0, 0, 0};
+  bool mom_shift_set = false;
+};

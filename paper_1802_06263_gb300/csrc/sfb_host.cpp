@@ -1,0 +1,763 @@
+// C ABI of the library (include/sfb.h): context, set-up, workspace carving
+// and the orchestration of the CUDA kernels on the caller's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <numeric>
+
+#include "sfb_ctx.h"
+
+namespace sfb {
+void stokes_assemble_host(sfb_ctx* c);
+size_t basis_smem_bytes(int prec_fp64, int max_nx, int max_cols);
+cudaError_t stokes_solve_device(sfb_ctx* c);
+sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it, int* n_failed);
+sfb_status moments_finalize_device(sfb_ctx* c, int field, double* mean_d, double* var_d);
+void build_hash_tables(sfb_ctx* c, std::vector<int>& table, std::vector<int64_t>& off, std::vector<int>& cap);
+sfb_status moments_accumulate_device(sfb_ctx* c, int64_t n_pts);
+}  // namespace sfb
+
+using namespace sfb;
+
+namespace {
+
+sfb_status fail(sfb_ctx* c, sfb_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+sfb_status cuda_fail(sfb_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, SFB_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define SFB_CUDA(call, where)                     \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int n_units(const sfb_ctx* c) { return (int)c->subs.size() + 1; }
+
+// Geometry: interfaces, mortar DOF numbering, face projections (Section 3.1,
+// 3.3; the subdomain-side L2 projections of Section 5.2 step 1).
+sfb_status build_geometry(sfb_ctx* c) {
+  const sfb_problem& P = c->prob;
+  const int px = P.px, py = P.py;
+  const double x0 = P.darcy_box[0], x1 = P.darcy_box[1], y0 = P.darcy_box[2], y1 = P.darcy_box[3];
+  const double W = (x1 - x0) / px, H = (y1 - y0) / py;
+  const int deg = P.mortar_degree;
+  c->subs.assign(px * py, HostSub());
+  for (int iy = 0; iy < py; ++iy)
+    for (int ix = 0; ix < px; ++ix) {
+      const int s = iy * px + ix;
+      HostSub& S = c->subs[s];
+      S.nx = c->nx[s]; S.ny = c->ny[s];
+      S.x0 = x0 + ix * W; S.x1 = S.x0 + W; S.y0 = y0 + iy * H; S.y1 = S.y0 + H;
+      S.hx = W / S.nx; S.hy = H / S.ny;
+      for (int q = 0; q < 4; ++q) { S.side_type[q] = SIDE_NOFLOW; S.side_val[q] = 0.0; S.side_iface[q] = -1; }
+      S.source = c->source.empty() ? 0.0 : c->source[s];
+    }
+  c->ifaces.clear();
+  int64_t off = 0;
+  auto add_iface = [&](int kind, double s0, double s1, int n_el, int sa, int qa, int sb, int qb) {
+    HostIface f;
+    f.kind = kind; f.s0 = s0; f.s1 = s1; f.n_el = n_el; f.deg = deg;
+    f.sub_a = sa; f.side_a = qa; f.sub_b = sb; f.side_b = qb;
+    f.off = off; f.n_dof = n_el * (deg + 1);
+    off += f.n_dof;
+    const int id = (int)c->ifaces.size();
+    c->ifaces.push_back(f);
+    if (sa >= 0) { c->subs[sa].side_type[qa] = SIDE_IFACE; c->subs[sa].side_iface[qa] = id; }
+    if (sb >= 0) { c->subs[sb].side_type[qb] = SIDE_IFACE; c->subs[sb].side_iface[qb] = id; }
+  };
+  for (int ix = 0; ix < px; ++ix)
+    add_iface(0, x0 + ix * W, x0 + (ix + 1) * W, c->msd[ix], (py - 1) * px + ix, 2, -1, 0);
+  for (int iy = 0; iy < py; ++iy)
+    for (int ix = 0; ix + 1 < px; ++ix)
+      add_iface(1, y0 + iy * H, y0 + (iy + 1) * H, c->mdv[iy * (px - 1) + ix], iy * px + ix, 1,
+                iy * px + ix + 1, 3);
+  for (int iy = 0; iy + 1 < py; ++iy)
+    for (int ix = 0; ix < px; ++ix)
+      add_iface(2, x0 + ix * W, x0 + (ix + 1) * W, c->mdh[iy * px + ix], iy * px + ix, 2,
+                (iy + 1) * px + ix, 0);
+  for (int ix = 0; ix < px; ++ix) {
+    c->subs[ix].side_type[0] = SIDE_DIRICHLET;
+    c->subs[ix].side_val[0] = P.bottom_pressure;
+  }
+  c->n_lambda = off;
+  // local DOFs, projections, per-DOF face ranges
+  for (HostSub& S : c->subs) {
+    std::vector<int> its;
+    for (int q = 0; q < 4; ++q) if (S.side_iface[q] >= 0) its.push_back(S.side_iface[q]);
+    std::sort(its.begin(), its.end());
+    S.dofs.clear();
+    for (int id : its)
+      for (int a = 0; a < c->ifaces[id].n_dof; ++a) S.dofs.push_back(c->ifaces[id].off + a);
+    const int R = (int)S.dofs.size();
+    if (R + 1 > kMaxCols) return fail(c, SFB_ERR_UNSUPPORTED, "too many mortar DOFs on a subdomain");
+    S.dofinfo.assign(3 * R, 0);
+    for (int q = 0; q < 4; ++q) {
+      const int nf = (q == 0 || q == 2) ? S.nx : S.ny;
+      S.proj[q].assign((size_t)nf * R, 0.0);
+      if (S.side_iface[q] < 0) continue;
+      const HostIface& itf = c->ifaces[S.side_iface[q]];
+      const double start = (q == 0 || q == 2) ? S.x0 : S.y0;
+      const double h = (q == 0 || q == 2) ? S.hx : S.hy;
+      std::vector<int> cols(itf.n_dof);
+      for (int a = 0; a < itf.n_dof; ++a)
+        cols[a] = (int)(std::lower_bound(S.dofs.begin(), S.dofs.end(), itf.off + a) - S.dofs.begin());
+      face_projection(itf, start, h, nf, cols, R, S.proj[q].data());
+      const double He = (itf.s1 - itf.s0) / itf.n_el;
+      for (int a = 0; a < itf.n_dof; ++a) {
+        const int e = a / (itf.deg + 1);
+        const double e0 = itf.s0 + e * He, e1 = e0 + He;
+        int fb = (int)std::floor((e0 - start) / h - 1e-9);
+        int fe = (int)std::ceil((e1 - start) / h + 1e-9);
+        fb = std::max(0, fb); fe = std::min(nf, fe);
+        S.dofinfo[3 * cols[a]] = q; S.dofinfo[3 * cols[a] + 1] = fb; S.dofinfo[3 * cols[a] + 2] = fe;
+      }
+    }
+    if (S.nx > kMaxNx || S.nx < 2 || S.ny < 2)
+      return fail(c, SFB_ERR_UNSUPPORTED, "Darcy grid sizes must satisfy 2 <= nx <= 128, ny >= 2");
+  }
+  c->stokes.dofs.clear();
+  for (const HostIface& f : c->ifaces)
+    if (f.kind == 0)
+      for (int a = 0; a < f.n_dof; ++a) c->stokes.dofs.push_back(f.off + a);
+  return SFB_OK;
+}
+
+// Workspace layout; `c->dev` gets the slices when carver.base is set.
+size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
+  Dev& d = c->dev;
+  const int ns = (int)c->subs.size();
+  const size_t gsz = prec == SFB_FP64 ? sizeof(double) : sizeof(float);
+  int64_t n_items = 0, nX = 0, nT = 0, nG = 0, nPhi = 0, nD = 0, nproj = 0, ninfo = 0, nkl = 0, nyl = 0, ngd = 0;
+  int64_t n_loc_tot = 0;
+  c->offs.clear();
+  for (int s = 0; s < ns; ++s) {
+    const HostSub& S = c->subs[s];
+    const int R = (int)S.dofs.size(), C = R + 1, nc = S.nx * S.ny;
+    const int nl = c->n_local.empty() ? 0 : c->n_local[s];
+    for (int k = 0; k < nl; ++k) {
+      ItemOff o;
+      o.x = nX; o.z = nX; nX += (int64_t)nc * C;
+      o.t = nT; nT += (int64_t)S.ny * (S.nx + 1) + (int64_t)(S.ny + 1) * S.nx;
+      o.g = nG; nG += (int64_t)S.ny * S.nx * S.nx;
+      o.phi = nPhi; nPhi += (int64_t)R * R + R;
+      o.diag = nD; nD += nc;
+      c->offs.push_back(o);
+    }
+    n_items += nl;
+    n_loc_tot += nl;
+    for (int q = 0; q < 4; ++q) nproj += (int64_t)S.proj[q].size();
+    ninfo += 3 * R;
+    nkl += S.n_term * (1 + S.nx + S.ny);
+    nyl += (int64_t)nl * S.n_term;
+    ngd += R;
+  }
+  c->n_items = n_items;
+  d.subs = cv.take<SubDev>(ns);
+  d.proj = cv.take<double>(nproj);
+  d.dofinfo = cv.take<int>(ninfo);
+  d.kl = cv.take<double>(nkl);
+  d.yloc = cv.take<double>(nyl);
+  d.gdof = cv.take<int64_t>(ngd);
+  d.item_sub = cv.take<int>(n_items);
+  d.item_k = cv.take<int>(n_items);
+  d.off = cv.take<ItemOff>(n_items);
+  d.X = cv.take<double>(nX);
+  d.T = cv.take<double>(nT);
+  d.G = cv.take<char>(nG * gsz);
+  d.Z = cv.take<char>(nX * gsz);
+  d.phi = cv.take<double>(nPhi);
+  d.D = cv.take<double>(nD);
+  d.status = cv.take<int>(n_items);
+  d.resid = cv.take<double>(n_items);
+  d.corr1 = cv.take<double>(n_items);
+  d.nref = cv.take<int>(n_items);
+  // Stokes
+  const StokesHost& St = c->stokes;
+  const int Rs = (int)St.dofs.size(), Cs = Rs + 1;
+  d.s_mat = cv.take<double>((size_t)St.n_free * St.n_free);
+  d.s_piv = cv.take<int>(St.n_free);
+  d.s_rhs = cv.take<double>((size_t)St.n_free * Cs);
+  d.s_U = cv.take<double>((size_t)St.n_u * Cs);
+  d.s_P = cv.take<double>((size_t)St.n_p * Cs);
+  d.s_phi = cv.take<double>((size_t)Rs * Rs + Rs);
+  d.s_dir = cv.take<double>(St.n_u);
+  d.s_nb = cv.take<double>(St.nb.size());
+  d.s_nb_node = cv.take<int>(St.nb_node.size());
+  d.s_free_to_full = cv.take<int>(St.n_free);
+  d.s_tr_row = cv.take<int>(St.tr_row.size());
+  d.s_tr_col = cv.take<int>(St.tr_col.size());
+  d.s_tr_val = cv.take<double>(St.tr_val.size());
+  d.s_status = cv.take<int>(4);
+  // interface solve
+  const int nu = n_units(c);
+  c->ybase.assign(nu + 1, 0);
+  for (int s = 0; s < ns; ++s) c->ybase[s + 1] = c->ybase[s] + (int64_t)c->subs[s].dofs.size();
+  c->ybase[nu] = c->ybase[ns] + Rs;
+  c->NY = c->ybase[nu];
+  int max_local = 1;
+  for (int nl : c->n_local) max_local = std::max(max_local, nl);
+  c->max_tiles = (int)std::min<int64_t>(max_pts, (int64_t)max_local + (max_pts + 7) / 8);
+  c->max_tiles = std::max(c->max_tiles, 1);
+  const int ndim = c->grid.n_dim;
+  int64_t hash_tot = 0;
+  for (int s = 0; s < ns; ++s) {
+    int cap = 1;
+    const int nl = c->n_local.empty() ? 1 : c->n_local[s];
+    while (cap < 2 * nl + 1) cap <<= 1;
+    hash_tot += cap;
+  }
+  const int64_t P = std::max<int64_t>(max_pts, 1);
+  d.y = cv.take<double>((size_t)P * std::max(ndim, 1));
+  d.w = cv.take<double>(P);
+  d.kmap = cv.take<int>((size_t)P * ns);
+  d.hash = cv.take<int>(hash_tot);
+  d.hash_off = cv.take<int64_t>(ns);
+  d.hash_cap = cv.take<int>(ns);
+  d.grp_count = cv.take<int>(std::max<int64_t>(n_loc_tot, 1));
+  d.grp_start = cv.take<int>(std::max<int64_t>(n_loc_tot, 1));
+  d.grp_pts = cv.take<int>((size_t)P * nu);
+  d.tiles = cv.take<int>((size_t)nu * c->max_tiles * 3);
+  d.n_tiles = cv.take<int>(nu);
+  d.ldof = cv.take<int>((size_t)c->n_lambda * 4);
+  d.lam = cv.take<double>((size_t)P * c->n_lambda);
+  d.r = cv.take<double>((size_t)P * c->n_lambda);
+  d.p = cv.take<double>((size_t)P * c->n_lambda);
+  d.Y = cv.take<double>((size_t)P * c->NY);
+  d.rr = cv.take<double>(P);
+  d.gn = cv.take<double>(P);
+  d.pstat = cv.take<int>(P);
+  d.active = cv.take<int>(2);
+  d.s_gdof = cv.take<int64_t>(std::max(Rs, 1));
+  d.ybase = cv.take<int64_t>(nu + 1);
+  d.dim_off = cv.take<int>(ns);
+  d.loc_off = cv.take<int64_t>(ns);
+  d.cell_off = cv.take<int64_t>(ns);
+  d.face_off = cv.take<int64_t>(ns);
+  // moments: Darcy p, Darcy flux, Stokes u, Stokes p
+  int64_t np_ = 0, nf_ = 0;
+  for (const HostSub& S : c->subs) {
+    np_ += (int64_t)S.nx * S.ny;
+    nf_ += (int64_t)S.ny * (S.nx + 1) + (int64_t)(S.ny + 1) * S.nx;
+  }
+  c->mom_len[0] = np_; c->mom_len[1] = nf_; c->mom_len[2] = St.n_u; c->mom_len[3] = St.n_p;
+  int64_t mo = 0;
+  for (int f = 0; f < 4; ++f) { c->mom_off[f] = mo; mo += c->mom_len[f]; }
+  d.mom = cv.take<double>((size_t)3 * mo);
+  d.mom_w = cv.take<double>(2);
+  d.fin = cv.take<double>((size_t)2 * std::max(std::max(np_, nf_), (int64_t)std::max(St.n_u, St.n_p)));
+  return cv.used + 256;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+sfb_status sfb_create(const sfb_problem* prob, void* stream, sfb_ctx** out) {
+  if (!prob || !out) return SFB_ERR_ARG;
+  *out = nullptr;
+  sfb_ctx* c = new (std::nothrow) sfb_ctx();
+  if (!c) return SFB_ERR_ARG;
+  const int px = prob->px, py = prob->py;
+  if (px < 1 || py < 1 || !prob->darcy_nx || !prob->darcy_ny || !prob->mortar_sd ||
+      (px > 1 && !prob->mortar_dd_v) || (py > 1 && !prob->mortar_dd_h) ||
+      (prob->mortar_degree != 1 && prob->mortar_degree != 2) || prob->stokes_sx < 1 ||
+      prob->stokes_sy < 1 || !(prob->nu_s > 0) || !(prob->nu_d > 0)) {
+    delete c;
+    return SFB_ERR_ARG;
+  }
+  c->prob = *prob;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  c->nx.assign(prob->darcy_nx, prob->darcy_nx + px * py);
+  c->ny.assign(prob->darcy_ny, prob->darcy_ny + px * py);
+  c->msd.assign(prob->mortar_sd, prob->mortar_sd + px);
+  if (px > 1) c->mdv.assign(prob->mortar_dd_v, prob->mortar_dd_v + py * (px - 1));
+  if (py > 1) c->mdh.assign(prob->mortar_dd_h, prob->mortar_dd_h + (py - 1) * px);
+  if (prob->source) c->source.assign(prob->source, prob->source + px * py);
+  for (int v : c->msd) if (v < 1) { delete c; return SFB_ERR_ARG; }
+  for (int v : c->mdv) if (v < 1) { delete c; return SFB_ERR_ARG; }
+  for (int v : c->mdh) if (v < 1) { delete c; return SFB_ERR_ARG; }
+  c->prob.darcy_nx = c->nx.data();
+  c->prob.darcy_ny = c->ny.data();
+  c->prob.mortar_sd = c->msd.data();
+  c->prob.mortar_dd_v = c->mdv.empty() ? nullptr : c->mdv.data();
+  c->prob.mortar_dd_h = c->mdh.empty() ? nullptr : c->mdh.data();
+  c->prob.source = c->source.empty() ? nullptr : c->source.data();
+  sfb_status s = build_geometry(c);
+  if (s != SFB_OK) {
+    delete c;
+    return s;
+  }
+  stokes_assemble_host(c);
+  *out = c;
+  return SFB_OK;
+}
+
+void sfb_destroy(sfb_ctx* c) { delete c; }
+
+const char* sfb_last_error(const sfb_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+sfb_status sfb_set_stream(sfb_ctx* c, void* stream) {
+  if (!c) return SFB_ERR_ARG;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  return SFB_OK;
+}
+
+sfb_status sfb_sizes(const sfb_ctx* c, int64_t* n_lambda, int32_t* n_darcy) {
+  if (!c) return SFB_ERR_ARG;
+  if (n_lambda) *n_lambda = c->n_lambda;
+  if (n_darcy) *n_darcy = (int32_t)c->subs.size();
+  return SFB_OK;
+}
+
+sfb_status sfb_subdomain_dofs(const sfb_ctx* c, int32_t sub, int32_t* n_dof, int64_t* gd) {
+  if (!c || !n_dof || sub < -1 || sub >= (int)c->subs.size()) return SFB_ERR_ARG;
+  const std::vector<int64_t>& v = sub < 0 ? c->stokes.dofs : c->subs[sub].dofs;
+  *n_dof = (int32_t)v.size();
+  if (gd) std::copy(v.begin(), v.end(), gd);
+  return SFB_OK;
+}
+
+sfb_status sfb_field_size(const sfb_ctx* c, int32_t field, int64_t* n) {
+  if (!c || !n || field < 0 || field > 3) return SFB_ERR_ARG;
+  int64_t np_ = 0, nf_ = 0;
+  for (const HostSub& S : c->subs) {
+    np_ += (int64_t)S.nx * S.ny;
+    nf_ += (int64_t)S.ny * (S.nx + 1) + (int64_t)(S.ny + 1) * S.nx;
+  }
+  const int64_t v[4] = {np_, nf_, (int64_t)c->stokes.n_u, (int64_t)c->stokes.n_p};
+  *n = v[field];
+  return SFB_OK;
+}
+
+sfb_status sfb_kl_setup(sfb_ctx* c, const sfb_kl_region* regions, int32_t n_regions, double* eig) {
+  if (!c) return SFB_ERR_ARG;
+  if (!regions || n_regions != (int)c->subs.size()) return fail(c, SFB_ERR_ARG, "one KL region per Darcy subdomain");
+  int64_t w = 0;
+  for (int s = 0; s < n_regions; ++s) {
+    const sfb_kl_region& r = regions[s];
+    if (r.n_term < 1 || r.n_term > 64 || !(r.sigma2 >= 0) || !(r.eta1 > 0) || !(r.eta2 > 0))
+      return fail(c, SFB_ERR_ARG, "bad KL region");
+    HostSub& S = c->subs[s];
+    S.n_term = r.n_term; S.sigma2 = r.sigma2; S.eta1 = r.eta1; S.eta2 = r.eta2; S.mean_y = r.mean_y;
+    const double Lx = S.x1 - S.x0, Ly = S.y1 - S.y0;
+    std::vector<double> omx, lx, omy, ly;
+    std::vector<int> parx, pary;
+    kl_1d_host(Lx, r.eta1, r.n_term, omx, lx, parx);
+    kl_1d_host(Ly, r.eta2, r.n_term, omy, ly, pary);
+    // the n_term largest products, ties broken by (a + b, a)
+    std::vector<std::tuple<double, int, int>> cand;
+    for (int a = 0; a < r.n_term; ++a)
+      for (int b = 0; b < r.n_term; ++b) cand.emplace_back(r.sigma2 * lx[a] * ly[b], a, b);
+    std::stable_sort(cand.begin(), cand.end(), [](const auto& p, const auto& q) {
+      if (std::get<0>(p) != std::get<0>(q)) return std::get<0>(p) > std::get<0>(q);
+      const int sp = std::get<1>(p) + std::get<2>(p), sq = std::get<1>(q) + std::get<2>(q);
+      if (sp != sq) return sp < sq;
+      return std::get<1>(p) < std::get<1>(q);
+    });
+    S.lam.assign(r.n_term, 0.0); S.slam.assign(r.n_term, 0.0);
+    S.fx.assign((size_t)r.n_term * S.nx, 0.0); S.fy.assign((size_t)r.n_term * S.ny, 0.0);
+    const double cx = 0.5 * (S.x0 + S.x1), cy = 0.5 * (S.y0 + S.y1);
+    for (int j = 0; j < r.n_term; ++j) {
+      const int a = std::get<1>(cand[j]), b = std::get<2>(cand[j]);
+      S.lam[j] = std::get<0>(cand[j]);
+      S.slam[j] = std::sqrt(S.lam[j]);
+      for (int i = 0; i < S.nx; ++i)
+        S.fx[(size_t)j * S.nx + i] = kl_1d_eval_host(S.x0 + (i + 0.5) * S.hx - cx, Lx, omx[a], parx[a]);
+      for (int i = 0; i < S.ny; ++i)
+        S.fy[(size_t)j * S.ny + i] = kl_1d_eval_host(S.y0 + (i + 0.5) * S.hy - cy, Ly, omy[b], pary[b]);
+      if (eig) eig[w++] = S.lam[j];
+    }
+  }
+  c->kl_done = true;
+  c->coll_done = false;
+  c->basis_done = false;
+  return SFB_OK;
+}
+
+sfb_status sfb_collocation_setup(sfb_ctx* c, const sfb_collocation* spec, int64_t* n_pts_out) {
+  if (!c || !spec) return SFB_ERR_ARG;
+  if (!c->kl_done) return fail(c, SFB_ERR_STATE, "sfb_kl_setup must come first");
+  const int ns = (int)c->subs.size();
+  int n_dim = 0;
+  c->dim_off.assign(ns, 0);
+  for (int s = 0; s < ns; ++s) { c->dim_off[s] = n_dim; n_dim += c->subs[s].n_term; }
+  std::vector<int> rule;
+  if (spec->kind == 1 && spec->n_rule > 0) {
+    if (!spec->rule) return fail(c, SFB_ERR_ARG, "rule missing");
+    rule.assign(spec->rule, spec->rule + spec->n_rule);
+  }
+  if (spec->kind == 0) {
+    if (spec->m < 1 || spec->m > 32) return fail(c, SFB_ERR_ARG, "bad tensor rule size");
+    double npts = std::pow((double)spec->m, n_dim);
+    if (npts > 5e7) return fail(c, SFB_ERR_UNSUPPORTED, "tensor grid too large");
+    tensor_grid_host(std::vector<int>(n_dim, spec->m), c->grid);
+  } else if (spec->kind == 1) {
+    if (spec->lmax < 0 || spec->lmax > 6) return fail(c, SFB_ERR_ARG, "bad Smolyak level");
+    smolyak_grid_host(n_dim, spec->lmax, rule, c->grid);
+  } else {
+    return fail(c, SFB_ERR_ARG, "unknown grid kind");
+  }
+  // local realizations (Section 5.4 Steps 1-2)
+  c->loc_y.assign(ns, {});
+  c->n_local.assign(ns, 0);
+  const int64_t np_ = c->grid.n_pts();
+  for (int s = 0; s < ns; ++s) {
+    const int nt = c->subs[s].n_term;
+    if (spec->local_tensor) {
+      int m = spec->kind == 0 ? spec->m : 1;
+      if (spec->kind == 1)
+        for (int p = 0; p <= spec->lmax; ++p) m = std::max(m, rule_size_host(p, rule));
+      Grid lg;
+      tensor_grid_host(std::vector<int>(nt, m), lg);
+      if (lg.n_pts() > 1000000) return fail(c, SFB_ERR_UNSUPPORTED, "local tensor grid too large");
+      c->loc_y[s] = lg.y;
+      c->n_local[s] = (int)lg.n_pts();
+    } else {
+      std::map<std::vector<int64_t>, std::vector<double>> uniq;
+      for (int64_t l = 0; l < np_; ++l) {
+        std::vector<int64_t> key(nt);
+        std::vector<double> val(nt);
+        for (int j = 0; j < nt; ++j) {
+          val[j] = c->grid.y[l * n_dim + c->dim_off[s] + j];
+          key[j] = qkey(val[j]);
+        }
+        uniq.emplace(key, val);
+      }
+      c->loc_y[s].clear();
+      for (auto& kv : uniq) c->loc_y[s].insert(c->loc_y[s].end(), kv.second.begin(), kv.second.end());
+      c->n_local[s] = (int)uniq.size();
+    }
+  }
+  c->coll_done = true;
+  c->basis_done = false;
+  if (n_pts_out) *n_pts_out = np_;
+  return SFB_OK;
+}
+
+sfb_status sfb_collocation_points(const sfb_ctx* c, double* y_out, double* w_out) {
+  if (!c) return SFB_ERR_ARG;
+  if (!c->coll_done) return SFB_ERR_STATE;
+  if (y_out) std::copy(c->grid.y.begin(), c->grid.y.end(), y_out);
+  if (w_out) std::copy(c->grid.w.begin(), c->grid.w.end(), w_out);
+  return SFB_OK;
+}
+
+sfb_status sfb_local_points(const sfb_ctx* c, int32_t region, int32_t* n_local, double* y_out) {
+  if (!c || region < 0 || region >= (int)c->subs.size()) return SFB_ERR_ARG;
+  if (!c->coll_done) return SFB_ERR_STATE;
+  if (n_local) *n_local = c->n_local[region];
+  if (y_out) std::copy(c->loc_y[region].begin(), c->loc_y[region].end(), y_out);
+  return SFB_OK;
+}
+
+sfb_status sfb_workspace_size(const sfb_ctx* cc, int32_t prec, int64_t max_pts, size_t* bytes) {
+  sfb_ctx* c = const_cast<sfb_ctx*>(cc);
+  if (!c || !bytes || prec < 0 || prec > 2 || max_pts < 0) return SFB_ERR_ARG;
+  if (!c->coll_done) return fail(c, SFB_ERR_STATE, "collocation set-up must come first");
+  Carver cv;
+  Dev saved = c->dev;
+  *bytes = layout(c, cv, prec == SFB_FP64 ? SFB_FP64 : SFB_MIXED, max_pts);
+  c->dev = saved;
+  c->ws_prec = prec == SFB_FP64 ? SFB_FP64 : SFB_MIXED;
+  c->ws_pts = max_pts;
+  return SFB_OK;
+}
+
+sfb_status sfb_set_workspace(sfb_ctx* c, void* ptr, size_t bytes) {
+  if (!c) return SFB_ERR_ARG;
+  if (!ptr || ((uintptr_t)ptr & 255)) return fail(c, SFB_ERR_ARG, "workspace must be 256-byte aligned");
+  if (!c->coll_done || c->ws_prec < 0)
+    return fail(c, SFB_ERR_STATE, "sfb_workspace_size must come first");
+  Carver cv0;
+  Dev saved = c->dev;
+  const size_t need = layout(c, cv0, c->ws_prec, c->ws_pts);
+  c->dev = saved;
+  if (bytes < need) return fail(c, SFB_ERR_WORKSPACE, "workspace smaller than sfb_workspace_size()");
+  c->ws = reinterpret_cast<char*>(ptr);
+  c->ws_bytes = bytes;
+  c->basis_done = false;
+  c->basis_prec = -1;
+  c->n_solved = 0;
+  c->mom_shift_set = false;
+  Carver cv;
+  cv.base = c->ws;
+  layout(c, cv, c->ws_prec, c->ws_pts);
+  const int64_t L = c->mom_off[3] + c->mom_len[3];
+  SFB_CUDA(cudaMemsetAsync(c->dev.mom, 0, sizeof(double) * 3 * L, c->stream), "memset");
+  SFB_CUDA(cudaMemsetAsync(c->dev.mom_w, 0, sizeof(double) * 2, c->stream), "memset");
+  return SFB_OK;
+}
+
+
+}  // extern "C"
+
+namespace {
+
+// Uploads the set-up tables once per workspace (synchronous; they are small).
+sfb_status upload_tables(sfb_ctx* c) {
+  Dev& d = c->dev;
+  cudaStream_t st = c->stream;
+  const int ns = (int)c->subs.size();
+  std::vector<SubDev> sd(ns);
+  std::vector<double> proj, kl, yloc;
+  std::vector<int> info;
+  std::vector<int64_t> gdof;
+  int64_t item0 = 0;
+  c->max_nx = 0; c->max_cols = 0; c->max_R = 0;
+  for (int s = 0; s < ns; ++s) {
+    const HostSub& S = c->subs[s];
+    SubDev& D = sd[s];
+    D.nx = S.nx; D.ny = S.ny; D.R = (int)S.dofs.size(); D.n_term = S.n_term; D.n_local = c->n_local[s];
+    D.x0 = S.x0; D.y0 = S.y0; D.hx = S.hx; D.hy = S.hy; D.nu = c->prob.nu_d; D.source = S.source;
+    D.mean_y = S.mean_y;
+    for (int q = 0; q < 4; ++q) {
+      D.side_type[q] = S.side_type[q];
+      D.side_val[q] = S.side_val[q];
+      D.proj_off[q] = (int64_t)proj.size();
+      proj.insert(proj.end(), S.proj[q].begin(), S.proj[q].end());
+    }
+    D.dofinfo_off = (int64_t)info.size();
+    info.insert(info.end(), S.dofinfo.begin(), S.dofinfo.end());
+    D.kl_off = (int64_t)kl.size();
+    kl.insert(kl.end(), S.slam.begin(), S.slam.end());
+    kl.insert(kl.end(), S.fx.begin(), S.fx.end());
+    kl.insert(kl.end(), S.fy.begin(), S.fy.end());
+    D.yloc_off = (int64_t)yloc.size();
+    yloc.insert(yloc.end(), c->loc_y[s].begin(), c->loc_y[s].end());
+    D.gdof_off = (int64_t)gdof.size();
+    gdof.insert(gdof.end(), S.dofs.begin(), S.dofs.end());
+    D.item0 = item0;
+    item0 += c->n_local[s];
+    c->max_nx = std::max(c->max_nx, S.nx);
+    c->max_cols = std::max(c->max_cols, D.R + 1);
+    c->max_R = std::max(c->max_R, D.R);
+  }
+  // items in decreasing cost: nx^3 ny (factor) + nx^2 ny (R+1) (solves)
+  std::vector<int> order(c->n_items), isub(c->n_items), ik(c->n_items);
+  std::vector<double> cost(c->n_items);
+  for (int s = 0, id = 0; s < ns; ++s)
+    for (int k = 0; k < c->n_local[s]; ++k, ++id) {
+      const double nx = sd[s].nx, ny = sd[s].ny;
+      cost[id] = nx * nx * nx * ny + nx * nx * ny * (sd[s].R + 1);
+      isub[id] = s; ik[id] = k;
+    }
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<int> item_sub(c->n_items), item_k(c->n_items);
+  for (int64_t i = 0; i < c->n_items; ++i) { item_sub[i] = isub[order[i]]; item_k[i] = ik[order[i]]; }
+  // interface-solve maps
+  const int nu = ns + 1;
+  std::vector<int> ldof(4 * c->n_lambda, 0);
+  std::vector<int> fill(c->n_lambda, 0);
+  auto put = [&](int64_t g, int unit, int loc) {
+    const int f = fill[g]++;
+    if (f < 2) { ldof[4 * g + 2 * f] = unit; ldof[4 * g + 2 * f + 1] = loc; }
+  };
+  for (int s = 0; s < ns; ++s)
+    for (size_t a = 0; a < c->subs[s].dofs.size(); ++a) put(c->subs[s].dofs[a], s, (int)a);
+  for (size_t a = 0; a < c->stokes.dofs.size(); ++a) put(c->stokes.dofs[a], ns, (int)a);
+  for (int64_t g = 0; g < c->n_lambda; ++g)
+    if (fill[g] != 2) return fail(c, SFB_ERR_ARG, "a mortar DOF is not shared by exactly two subdomains");
+  std::vector<int> dim_off(c->dim_off.begin(), c->dim_off.end());
+  std::vector<int64_t> loc_off(ns, 0), cell_off(ns, 0), face_off(ns, 0);
+  for (int s = 1; s < ns; ++s) {
+    loc_off[s] = loc_off[s - 1] + c->n_local[s - 1];
+    cell_off[s] = cell_off[s - 1] + (int64_t)sd[s - 1].nx * sd[s - 1].ny;
+    face_off[s] = face_off[s - 1] + (int64_t)sd[s - 1].ny * (sd[s - 1].nx + 1) + (int64_t)(sd[s - 1].ny + 1) * sd[s - 1].nx;
+  }
+  std::vector<int> htab, hcap;
+  std::vector<int64_t> hoff;
+  build_hash_tables(c, htab, hoff, hcap);
+#define UP(dst, vec) SFB_CUDA(cudaMemcpyAsync(dst, (vec).data(), sizeof((vec)[0]) * (vec).size(), cudaMemcpyHostToDevice, st), "upload")
+  UP(d.subs, sd); UP(d.proj, proj); UP(d.dofinfo, info); UP(d.kl, kl); UP(d.yloc, yloc); UP(d.gdof, gdof);
+  UP(d.item_sub, item_sub); UP(d.item_k, item_k); UP(d.off, c->offs);
+  UP(d.s_gdof, c->stokes.dofs); UP(d.ybase, c->ybase); UP(d.dim_off, dim_off); UP(d.loc_off, loc_off);
+  UP(d.cell_off, cell_off); UP(d.face_off, face_off); UP(d.ldof, ldof); UP(d.hash, htab); UP(d.hash_off, hoff);
+  UP(d.hash_cap, hcap);
+#undef UP
+  SFB_CUDA(cudaStreamSynchronize(st), "upload");
+  return SFB_OK;
+}
+
+bool host_or_device_copy(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st) == cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats* stats) {
+  if (!c) return SFB_ERR_ARG;
+  if (prec < 0 || prec > 2) return fail(c, SFB_ERR_ARG, "bad precision");
+  if (!c->ws) return fail(c, SFB_ERR_WORKSPACE, "no workspace set");
+  if (prec == SFB_FP64 && c->ws_prec != SFB_FP64)
+    return fail(c, SFB_ERR_WORKSPACE, "workspace was sized for the FP32 factor; FP64 needs more");
+  Dev& d = c->dev;
+  cudaStream_t st = c->stream;
+  if (c->basis_prec < 0) {
+    sfb_status s = upload_tables(c);
+    if (s != SFB_OK) return s;
+    cudaError_t e = stokes_solve_device(c);
+    if (e != cudaSuccess) return cuda_fail(c, e, "Stokes basis");
+    int sst = 0;
+    SFB_CUDA(cudaMemcpyAsync(&sst, d.s_status, sizeof(int), cudaMemcpyDeviceToHost, st), "Stokes status");
+    SFB_CUDA(cudaStreamSynchronize(st), "Stokes basis");
+    if (sst) return fail(c, SFB_ERR_NOT_SPD, "zero pivot in the Stokes factorization");
+    c->basis_prec = 99;  // tables and Stokes basis present
+  }
+  const int n = (int)c->n_items;
+  SFB_CUDA(cudaMemsetAsync(d.status, 0, sizeof(int) * n, st), "memset");
+  SFB_CUDA(cudaMemsetAsync(d.resid, 0, sizeof(double) * n, st), "memset");
+  SFB_CUDA(cudaMemsetAsync(d.corr1, 0, sizeof(double) * n, st), "memset");
+  SFB_CUDA(cudaMemsetAsync(d.nref, 0, sizeof(int) * n, st), "memset");
+  BasisArgs a;
+  a.subs = d.subs; a.proj = d.proj; a.dofinfo = d.dofinfo; a.kl = d.kl; a.yloc = d.yloc;
+  a.item_sub = d.item_sub; a.item_k = d.item_k; a.off = d.off; a.n_items = n;
+  a.X = d.X; a.T = d.T; a.G = d.G; a.Z = d.Z; a.phi = d.phi; a.D = d.D;
+  a.status = d.status; a.resid = d.resid; a.corr1 = d.corr1; a.nref = d.nref;
+  a.max_refine = 10;
+  a.refine_tol = 1e-13;
+  cudaEvent_t e0, e1;
+  SFB_CUDA(cudaEventCreate(&e0), "event");
+  SFB_CUDA(cudaEventCreate(&e1), "event");
+  SFB_CUDA(cudaEventRecord(e0, st), "event");
+  cudaError_t e;
+  if (prec == SFB_FP64) e = launch_basis_fp64(a, c->max_nx, c->max_cols, st);
+  else e = launch_basis_mixed(a, c->max_nx, c->max_cols, prec == SFB_MIXED ? a.max_refine : 0, st);
+  if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_fail(c, e, "basis kernel"); }
+  e = launch_flux_epilogue(a, c->max_R, st);
+  if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_fail(c, e, "flux epilogue"); }
+  SFB_CUDA(cudaEventRecord(e1, st), "event");
+  std::vector<int> status(n), nref(n);
+  std::vector<double> resid(n), corr(n);
+  SFB_CUDA(cudaMemcpyAsync(status.data(), d.status, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "stats");
+  SFB_CUDA(cudaMemcpyAsync(nref.data(), d.nref, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "stats");
+  SFB_CUDA(cudaMemcpyAsync(resid.data(), d.resid, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "stats");
+  SFB_CUDA(cudaMemcpyAsync(corr.data(), d.corr1, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "stats");
+  SFB_CUDA(cudaStreamSynchronize(st), "basis build");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int any = 0, n_nc = 0;
+  for (int i = 0; i < n; ++i) { any |= status[i]; n_nc += (status[i] & ST_NOT_CONVERGED) != 0; }
+  if (stats) {
+    stats->n_items = n;
+    int64_t fr = 0;
+    for (int s = 0; s < (int)c->subs.size(); ++s) fr += (int64_t)c->subs[s].dofs.size() * c->n_local[s];
+    stats->n_flux_responses = fr;
+    stats->max_refine_steps = n ? *std::max_element(nref.begin(), nref.end()) : 0;
+    stats->n_not_converged = n_nc;
+    stats->max_rel_residual = n ? *std::max_element(resid.begin(), resid.end()) : 0.0;
+    stats->max_first_correction = n ? *std::max_element(corr.begin(), corr.end()) : 0.0;
+    stats->ms = ms;
+  }
+  c->basis_done = true;
+  c->basis_prec = prec;
+  if (any & ST_NONFINITE) return fail(c, SFB_ERR_NONFINITE, "non-finite permeability or solution");
+  if (any & ST_NOT_SPD) return fail(c, SFB_ERR_NOT_SPD, "non-positive pivot in a block factorization");
+  if (any & ST_NOT_CONVERGED) return fail(c, SFB_ERR_NOT_CONVERGED, "iterative refinement stopped above tolerance");
+  return SFB_OK;
+}
+
+sfb_status sfb_get_basis(sfb_ctx* c, int32_t sub, int32_t k, double* phi, double* g, double* x) {
+  if (!c) return SFB_ERR_ARG;
+  if (!c->basis_done) return fail(c, SFB_ERR_STATE, "no basis built");
+  cudaStream_t st = c->stream;
+  if (sub == -1) {
+    const int Rs = (int)c->stokes.dofs.size();
+    if (k != 0 || x) return fail(c, SFB_ERR_ARG, "Stokes basis: k = 0, x = NULL");
+    if (phi) SFB_CUDA(cudaMemcpyAsync(phi, c->dev.s_phi, sizeof(double) * Rs * Rs, cudaMemcpyDefault, st), "copy");
+    if (g) SFB_CUDA(cudaMemcpyAsync(g, c->dev.s_phi + Rs * Rs, sizeof(double) * Rs, cudaMemcpyDefault, st), "copy");
+    SFB_CUDA(cudaStreamSynchronize(st), "copy");
+    return SFB_OK;
+  }
+  if (sub < 0 || sub >= (int)c->subs.size() || k < 0 || k >= c->n_local[sub])
+    return fail(c, SFB_ERR_ARG, "no such basis item");
+  int64_t id = 0;
+  for (int s = 0; s < sub; ++s) id += c->n_local[s];
+  id += k;
+  const ItemOff& o = c->offs[id];
+  const HostSub& S = c->subs[sub];
+  const int R = (int)S.dofs.size();
+  if (phi) SFB_CUDA(cudaMemcpyAsync(phi, c->dev.phi + o.phi, sizeof(double) * R * R, cudaMemcpyDefault, st), "copy");
+  if (g) SFB_CUDA(cudaMemcpyAsync(g, c->dev.phi + o.phi + (int64_t)R * R, sizeof(double) * R, cudaMemcpyDefault, st), "copy");
+  if (x) SFB_CUDA(cudaMemcpyAsync(x, c->dev.X + o.x, sizeof(double) * (size_t)S.nx * S.ny * (R + 1),
+                                  cudaMemcpyDefault, st), "copy");
+  SFB_CUDA(cudaStreamSynchronize(st), "copy");
+  return SFB_OK;
+}
+
+sfb_status sfb_interface_solve_batch(sfb_ctx* c, const double* y, const double* w, int64_t n_pts, int32_t krylov,
+                                     double rtol, int32_t max_it, double* lambda_out, int32_t* iters_out) {
+  if (!c) return SFB_ERR_ARG;
+  if (!c->basis_done) return fail(c, SFB_ERR_STATE, "sfb_build_stochastic_basis must come first");
+  if (!y || !w || n_pts < 1 || krylov != SFB_CG || !(rtol > 0) || max_it < 1)
+    return fail(c, SFB_ERR_ARG, "bad interface solve arguments");
+  if (n_pts > c->ws_pts) return fail(c, SFB_ERR_WORKSPACE, "batch larger than the workspace was sized for");
+  Dev& d = c->dev;
+  cudaStream_t st = c->stream;
+  const int nd = c->grid.n_dim;
+  if (!host_or_device_copy(d.y, y, sizeof(double) * n_pts * nd, st) ||
+      !host_or_device_copy(d.w, w, sizeof(double) * n_pts, st))
+    return fail(c, SFB_ERR_CUDA, "copy of the points");
+  int n_failed = 0;
+  sfb_status s = iface_solve_device(c, n_pts, rtol, max_it, &n_failed);
+  if (s != SFB_OK) return s;
+  s = moments_accumulate_device(c, n_pts);
+  if (s != SFB_OK) return s;
+  if (lambda_out)
+    SFB_CUDA(cudaMemcpyAsync(lambda_out, d.lam, sizeof(double) * n_pts * c->n_lambda, cudaMemcpyDefault, st),
+             "copy lambda");
+  if (iters_out)
+    SFB_CUDA(cudaMemcpyAsync(iters_out, d.pstat, sizeof(int) * n_pts, cudaMemcpyDefault, st), "copy iters");
+  SFB_CUDA(cudaStreamSynchronize(st), "interface solve");
+  c->n_solved += n_pts;
+  if (n_failed) return fail(c, SFB_ERR_NOT_CONVERGED, std::to_string(n_failed) + " points did not converge");
+  return SFB_OK;
+}
+
+sfb_status sfb_moments(sfb_ctx* c, int32_t field, double* mean_out, double* var_out) {
+  if (!c || field < 0 || field > 3) return SFB_ERR_ARG;
+  if (c->n_solved == 0) return fail(c, SFB_ERR_STATE, "no point solved since the last reset");
+  const int64_t n = c->mom_len[field];
+  sfb_status s = moments_finalize_device(c, field, c->dev.fin, c->dev.fin + n);
+  if (s != SFB_OK) return s;
+  if (mean_out) SFB_CUDA(cudaMemcpyAsync(mean_out, c->dev.fin, sizeof(double) * n, cudaMemcpyDefault, c->stream), "copy");
+  if (var_out) SFB_CUDA(cudaMemcpyAsync(var_out, c->dev.fin + n, sizeof(double) * n, cudaMemcpyDefault, c->stream), "copy");
+  SFB_CUDA(cudaStreamSynchronize(c->stream), "moments");
+  return SFB_OK;
+}
+
+sfb_status sfb_moments_reset(sfb_ctx* c) {
+  if (!c) return SFB_ERR_ARG;
+  if (!c->ws) return fail(c, SFB_ERR_WORKSPACE, "no workspace set");
+  const int64_t L = c->mom_off[3] + c->mom_len[3];
+  SFB_CUDA(cudaMemsetAsync(c->dev.mom, 0, sizeof(double) * 3 * L, c->stream), "memset");
+  SFB_CUDA(cudaMemsetAsync(c->dev.mom_w, 0, sizeof(double) * 2, c->stream), "memset");
+  c->mom_shift_set = false;
+  c->n_solved = 0;
+  return SFB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// Internal data layout shared by the host orchestration (sfb_host.cpp) and
+// the CUDA kernels. Everything here is plain data: device arrays are carved
+// out of the caller's workspace and addressed by 64-bit element offsets.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sfb {
+
+constexpr int kMaxNx = 128;      // cells per block row of a Darcy subdomain
+constexpr int kMaxCols = 129;    // mortar DOFs per subdomain + 1 particular column
+constexpr int kSides = 4;        // bottom, right, top, left
+enum SideType { SIDE_NOFLOW = 0, SIDE_IFACE = 1, SIDE_DIRICHLET = 2 };
+
+// Error bits written by kernels into a per-item / per-point status word.
+enum : int {
+  ST_NONFINITE = 1,
+  ST_NOT_SPD = 2,
+  ST_NOT_CONVERGED = 4,
+  ST_BAD_INDEX = 8,
+};
+
+// One Darcy subdomain. Side order: 0 bottom, 1 right, 2 top, 3 left; the
+// faces of a side are ordered by increasing coordinate.
+struct SubDev {
+  int nx, ny, R, n_term, n_local;
+  double x0, y0, hx, hy, nu, source, mean_y;
+  int side_type[kSides];
+  double side_val[kSides];
+  int64_t proj_off[kSides];  // into proj: dense [faces][R] face averages of the mortar basis
+  int64_t dofinfo_off;       // into dofinfo: per local DOF (side, first face, end face)
+  int64_t kl_off;            // into kl: sqrt(lambda)[nt] | fx[nt][nx] | fy[nt][ny]
+  int64_t yloc_off;          // into yloc: local realizations [n_local][nt]
+  int64_t gdof_off;          // into gdof: local -> global mortar DOF
+  int64_t item0;             // first basis item of this subdomain (items k = 0..n_local-1)
+};
+
+// Per-item storage offsets (elements) into the basis store arrays.
+struct ItemOff {
+  int64_t x;    // X: [n_cells][R+1] FP64 pressure responses
+  int64_t t;    // T: x-faces [ny][nx+1] then y-faces [ny+1][nx] FP64 transmissibilities
+  int64_t g;    // G: [ny][nx][nx] inverse Schur blocks (FP64 or FP32)
+  int64_t z;    // Z: [n_cells][R+1] solve scratch (factor precision)
+  int64_t phi;  // Phi: [R][R] then g: [R]
+  int64_t diag; // D: [n_cells] FP64 diagonal of A (mixed form scaling)
+};
+
+struct BasisArgs {
+  const SubDev* subs;
+  const double* proj;
+  const int* dofinfo;
+  const double* kl;
+  const double* yloc;
+  const int* item_sub;     // item -> subdomain (items sorted by decreasing cost)
+  const int* item_k;       // item -> local realization
+  const ItemOff* off;      // indexed by item id = subs[s].item0 + k
+  int n_items;
+  double* X;
+  double* T;
+  void* G;
+  void* Z;                 // [n_cells][R+1] solve scratch in the factor precision
+  double* phi;
+  double* D;
+  int* status;             // per item
+  double* resid;           // per item: final relative residual
+  double* corr1;           // per item: relative size of the first correction
+  int* nref;               // per item: refinement steps taken
+  int max_refine;
+  double refine_tol;
+};
+
+// Launchers (basis.cu).
+cudaError_t launch_basis_fp64(const BasisArgs& a, int max_nx, int max_cols, cudaStream_t st);
+cudaError_t launch_basis_mixed(const BasisArgs& a, int max_nx, int max_cols, int refine,
+                               cudaStream_t st);
+cudaError_t launch_flux_epilogue(const BasisArgs& a, int max_R, cudaStream_t st);
+
+}  // namespace sfb

@@ -1,0 +1,42 @@
+"""Shared helpers of the GPU parity tests: oracle reference results (cached
+per workload) and the relative-error measure."""
+
+import functools
+
+import numpy as np
+
+import sfb_workloads as W
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_case(key):
+    """Oracle basis, per-point solutions and moments for a named workload."""
+    from oracle import coupled
+    w = make_workload(key)
+    p = coupled.Problem(w)
+    y, wt = p.grid()
+    lams, mom = coupled.solve_all(p, y, wt)
+    return p, y, wt, lams, mom
+
+
+def make_workload(key):
+    if key == "tiny":
+        return W.tiny()
+    if key == "medium":
+        return W.medium()
+    if key == "ragged":
+        return W.small_test(nx=13, ny=9, px=3, py=2, n_sd=3, n_dd=2, n_term=2, degree=2, stokes=(7, 5),
+                            bottom_pressure=0.5, source=[0.3, -0.2, 0.1, 0.7, -0.4, 0.2],
+                            collocation={"kind": "smolyak", "lmax": 1, "rule": "paper"})
+    if key == "ragged_tensor":
+        return W.small_test(nx=10, ny=7, px=2, py=2, n_sd=2, n_dd=3, n_term=2, degree=1, stokes=(6, 5),
+                            sigma2=2.0)
+    raise KeyError(key)
+
+
+TOL = {0: 1e-10, 1: 1e-8}   # FP64 form, mixed form (refined)

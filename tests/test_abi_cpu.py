@@ -1,0 +1,80 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, exports
+every entry point declared in include/sfb.h, and its set-up (KL eigenpairs,
+collocation grids, mortar DOF maps, local realizations), computed by its own
+host code, agrees with the oracle."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+import sfb_workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    import paper_1802_06263_gb300 as sfb
+    if not os.path.exists(sfb.library_path()):
+        sfb.build()
+    return sfb
+
+
+def test_library_exports_every_declared_symbol():
+    sfb = _lib()
+    lib = sfb.load()
+    names = set()
+    for hdr in os.listdir(os.path.join(ROOT, "include")):
+        if hdr.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", hdr)).read()
+            names |= set(re.findall(r"^\s*(?:sfb_status|void|const char\*)\s+(sfb_\w+)\s*\(", txt, re.M))
+    assert len(names) >= 15
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+
+
+@pytest.mark.parametrize("name", ["tiny", "medium", "batched"])
+def test_host_setup_matches_oracle(name):
+    sfb = _lib()
+    from oracle import coupled
+    w = W.ALL[name]()
+    s = sfb.Solver(w)
+    p = coupled.Problem(w)
+    lam_o = np.concatenate([p.kl[i][0] for i in range(len(p.subs))])
+    assert np.allclose(s.eigvals, lam_o, rtol=1e-13)
+    assert s.n_lambda == p.n_lambda
+    y, wt = s.points()
+    yo, wo = p.grid()
+    assert y.shape == yo.shape
+    ref = {tuple(np.round(r, 10)): v for r, v in zip(yo, wo)}
+    for r, v in zip(y, wt):
+        assert abs(ref[tuple(np.round(r, 10))] - v) < 1e-12
+    for i in range(len(p.subs)):
+        assert list(s.subdomain_dofs(i)) == p.subs[i].dofs
+        assert np.allclose(s.local_points(i), p.local_grids[i], atol=1e-15)
+    assert list(s.subdomain_dofs(-1)) == p.stokes.dofs
+    assert s.field_size("darcy_p") == sum(sub.n_cells for sub in p.subs)
+    assert s.field_size("stokes_u") == 2 * p.stokes.n_nodes
+    assert s.field_size("stokes_p") == p.stokes.n_p
+
+
+def test_bad_arguments_are_rejected():
+    sfb = _lib()
+    w = W.tiny()
+    w["mortar_degree"] = 3
+    with pytest.raises(sfb.SfbError):
+        sfb.Solver(w)
+    w = W.tiny()
+    w["darcy_grid"] = [(200, 8), (8, 8)]
+    with pytest.raises(sfb.SfbError):
+        sfb.Solver(w)
+
+
+def test_workspace_size_grows_with_batch():
+    sfb = _lib()
+    s = sfb.Solver(W.medium())
+    a = s.workspace_bytes(sfb.FP64, 10)
+    b = s.workspace_bytes(sfb.FP64, 289)
+    c = s.workspace_bytes(sfb.MIXED, 289)
+    assert a < b and c < b

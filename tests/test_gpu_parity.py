@@ -1,0 +1,104 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle, element by
+element, on the same inputs. FP64 form within 1e-10 relative, mixed form
+(FP32 factor + FP64 refinement) within 1e-8 relative."""
+
+import numpy as np
+import pytest
+
+from gpu_common import TOL, make_workload, oracle_case, rel
+
+pytestmark = pytest.mark.gpu
+
+CASES = ["tiny", "ragged", "ragged_tensor", "medium"]
+
+
+def _solver(key, prec):
+    import torch
+    import paper_1802_06263_gb300 as sfb
+    assert torch.cuda.is_available()
+    s = sfb.Solver(make_workload(key))
+    s.allocate(prec)
+    st = s.build_basis(prec)
+    return s, st
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("key", CASES)
+def test_basis_parity(key, prec):
+    p, y, wt, lams, mom = oracle_case(key)
+    s, st = _solver(key, prec)
+    tol = TOL[prec]
+    worst = 0.0
+    for i in range(len(p.subs)):
+        loc = p.local_realizations(i, y)[0]
+        for k in range(len(loc)):
+            phi_o, g_o, X_o, _ = p.darcy_basis(i, loc[k])
+            phi, g, X = s.get_basis(i, k, with_x=True)
+            e = max(rel(phi, phi_o), rel(X, X_o), rel(g, g_o) if np.linalg.norm(g_o) > 0 else np.abs(g).max())
+            worst = max(worst, e)
+            assert e < tol, (i, k, e)
+    phs, gs, _ = s.get_basis(-1, 0)
+    phs_o, gs_o, _, _ = p.stokes_basis()
+    assert rel(phs, phs_o) < 1e-10
+    assert rel(gs, gs_o) < 1e-10
+    if prec == 1:
+        assert st["max_first_correction"] > 0
+    print(key, prec, "worst basis rel err", worst, st)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("key", CASES)
+def test_interface_and_moments_parity(key, prec):
+    p, y, wt, lams, mom = oracle_case(key)
+    s, _ = _solver(key, prec)
+    lam, it, rc = s.solve_host(y, wt, rtol=1e-14, max_it=5000, check=False)
+    assert np.all(it != 0)
+    tol = TOL[prec]
+    assert rel(lam, lams) < tol * 10
+    for f in ("darcy_p", "darcy_flux", "stokes_u", "stokes_p"):
+        m, v = s.moments(f)
+        assert rel(m, mom[f][0]) < tol * 10, f
+        assert rel(v, mom[f][1]) < tol * 100, f
+
+
+def test_split_batches_accumulate_the_same_moments():
+    """Moments over two half batches equal the moments over the full batch."""
+    p, y, wt, lams, mom = oracle_case("medium")
+    s, _ = _solver("medium", 0)
+    h = len(y) // 2
+    s.solve_host(y[:h], wt[:h], rtol=1e-14, max_it=5000)
+    s.solve_host(y[h:], wt[h:], rtol=1e-14, max_it=5000)
+    for f in ("darcy_p", "stokes_u"):
+        m, v = s.moments(f)
+        assert rel(m, mom[f][0]) < 1e-9
+        assert rel(v, mom[f][1]) < 1e-8
+    s.moments_reset()
+    import paper_1802_06263_gb300 as sfb
+    with pytest.raises(sfb.SfbError):
+        s.moments("darcy_p")
+
+
+def test_device_buffers_and_iteration_counts():
+    import torch
+    p, y, wt, lams, mom = oracle_case("tiny")
+    s, _ = _solver("tiny", 0)
+    yd = torch.tensor(y, device="cuda")
+    wd = torch.tensor(wt, device="cuda")
+    lam = torch.zeros((len(y), s.n_lambda), dtype=torch.float64, device="cuda")
+    it = torch.zeros(len(y), dtype=torch.int32, device="cuda")
+    s.solve(yd, wd, 1e-14, 100, lam, it)
+    torch.cuda.synchronize()
+    assert rel(lam.cpu().numpy(), lams) < 1e-10
+    # CG on an N-dimensional SPD system converges in about N steps; rounding
+    # at rtol = 1e-14 costs a few more
+    assert it.cpu().numpy().max() <= 2 * s.n_lambda
+    assert it.cpu().numpy().min() > 0
+
+
+def test_not_converged_is_reported():
+    import paper_1802_06263_gb300 as sfb
+    p, y, wt, lams, mom = oracle_case("medium")
+    s, _ = _solver("medium", 0)
+    lam, it, rc = s.solve_host(y, wt, rtol=1e-14, max_it=2, check=False)
+    assert rc == sfb.SFB_ERR_NOT_CONVERGED
+    assert np.all(it == -2)
