@@ -1,0 +1,321 @@
+"""Benchmark of the stochastic multiscale flux basis hot path (Method S3).
+
+One step = the whole hot path over one batch: the stochastic basis for every
+(Darcy subdomain, local realization) item (KL permeability, CCFD assembly,
+block factorization, R+1 solves, flux projection) plus the interface CG for
+every global collocation point and the moment accumulation.
+
+Workload: 4x2 Darcy subdomains of 64x64 cells, N_term = 4 per region
+(81 local realizations each, 648 basis items), sigma^2 = 2, 8 linear mortar
+elements per edge (224 mortar DOFs), Smolyak level 2 over 32 dimensions
+(2,049 global points), Stokes 32x32 Taylor-Hood. Metric: collocation
+realizations per second (mixed form: FP32 factor + FP64 refinement), with
+the FP64 form and the mortar flux responses per second beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import sfb_workloads as W  # noqa: E402
+
+METRIC = "collocation realizations/sec (mixed FP32/FP64, <=1e-8 vs FP64)"
+UNIT = "realizations/s"
+WORKLOAD = "precision"
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([v.strip() for v in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        time.sleep(0.05)
+        sm = [float(s[1]) for s in self.samples if len(s) >= 9 and s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if len(s) >= 9 and s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            if len(s) < 9:
+                continue
+            for n, v in zip(names, s[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_ours(args):
+    import torch
+    import paper_1802_06263_gb300 as sfb
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    wl = W.ALL[WORKLOAD]()
+    stream = torch.cuda.current_stream()
+    s = sfb.Solver(wl, stream=stream)
+    s.allocate(sfb.FP64)            # the FP64 layout also holds the mixed form
+    y, wt = s.points()
+    n_pts = len(y)
+    yd = torch.tensor(y, device="cuda")
+    wd = torch.tensor(wt, device="cuda")
+    lam_d = torch.empty((n_pts, s.n_lambda), dtype=torch.float64, device="cuda")
+    it_d = torch.empty(n_pts, dtype=torch.int32, device="cuda")
+    rtol, max_it = 1e-10, 2000
+
+    def step(prec):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        st = s.build_basis(prec)
+        ev[1].record(stream)
+        s.moments_reset()
+        s.solve(yd, wd, rtol, max_it, lam_d, it_d)
+        ev[2].record(stream)
+        ev[3].record(stream)
+        return st, ev
+
+    # warm-up (also builds the Stokes basis once)
+    for _ in range(args.warmup):
+        step(sfb.MIXED)
+        step(sfb.FP64)
+    torch.cuda.synchronize()
+
+    def timed(prec, k):
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        phases = []
+        t0.record(stream)
+        for _ in range(k):
+            st, ev = step(prec)
+            phases.append((st, ev))
+        t1.record(stream)
+        torch.cuda.synchronize()
+        total = t0.elapsed_time(t1) / k
+        basis = np.mean([e[0].elapsed_time(e[1]) for _, e in phases])
+        solve = np.mean([e[1].elapsed_time(e[2]) for _, e in phases])
+        kern = np.mean([p[0]["ms"] for p in phases])
+        if world > 1:
+            tt = torch.tensor([total], device="cuda")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            total = float(tt.item())
+        return total, basis, solve, kern, phases[-1][0]
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_mixed, b_mixed, s_mixed, k_mixed, st_mixed = timed(sfb.MIXED, args.steps)
+    mean_mixed = {f: s.moments(f) for f in sfb.FIELDS}
+    iters = it_d.cpu().numpy()
+    t_fp64, b_fp64, s_fp64, k_fp64, st_fp64 = timed(sfb.FP64, args.steps)
+    clk = clocks.stop()
+    mean_fp64 = {f: s.moments(f) for f in sfb.FIELDS}
+
+    # mixed vs FP64 agreement of the moments (relative L2 per field)
+    agree = {}
+    for f in sfb.FIELDS:
+        for j, nm in ((0, "mean"), (1, "var")):
+            a, b = mean_mixed[f][j], mean_fp64[f][j]
+            agree["%s_%s" % (f, nm)] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    # end to end through the C ABI with host buffers: H2D of the points and
+    # weights, D2H of lambda, iteration counts and the moments
+    y_h = torch.tensor(y).pin_memory()
+    w_h = torch.tensor(wt).pin_memory()
+    lam_h = torch.empty((n_pts, s.n_lambda), dtype=torch.float64).pin_memory()
+    it_h = torch.empty(n_pts, dtype=torch.int32).pin_memory()
+    mom_bytes = 0
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.build_basis(sfb.MIXED)
+        s.moments_reset()
+        s.solve(y_h, w_h, rtol, max_it, lam_h, it_h)
+        mom_bytes = 0
+        for f in sfb.FIELDS:
+            m, v = s.moments(f)
+            mom_bytes += m.nbytes + v.nbytes
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    if world > 1:
+        tt = torch.tensor([e2e_ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+
+    # roofline of the dominant kernel: see the design doc for the flop model
+    n_items = st_mixed["n_items"]
+    fr = st_mixed["n_flux_responses"]
+    peaks = _peaks()
+    out = {
+        "metric": METRIC, "value": world * n_pts / (t_mixed * 1e-3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_mixed,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded KL/Smolyak inputs of the precision workload; no paper datasets)",
+        "config": {"workload": "precision: 4x2 Darcy subdomains 64x64, N_term=4 (81 local), sigma^2=2, "
+                               "8 linear mortar elements/edge (224 DOFs), Smolyak L2 over 32 dims "
+                               "(2,049 points), Stokes 32x32",
+                   "n_points": n_pts, "n_basis_items": n_items, "flux_responses": fr,
+                   "cg_rtol": rtol, "l2": "working set larger than L2 (basis store %.2f GB)"
+                   % (s.workspace_bytes(sfb.MIXED, n_pts) / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "fp64_form": {"value": world * n_pts / (t_fp64 * 1e-3), "ms_per_step": t_fp64,
+                      "basis_ms": b_fp64, "solve_moments_ms": s_fp64,
+                      "flux_responses_per_s": world * fr / (b_fp64 * 1e-3)},
+        "mixed_form": {"ms_per_step": t_mixed, "basis_ms": b_mixed, "basis_kernel_ms": k_mixed,
+                       "solve_moments_ms": s_mixed, "flux_responses_per_s": world * fr / (b_mixed * 1e-3),
+                       "max_refine_steps": st_mixed["max_refine_steps"],
+                       "unrefined_fp32_rel_error": st_mixed["max_first_correction"],
+                       "final_rel_residual": st_mixed["max_rel_residual"],
+                       "cg_iters_min_max": [int(iters.min()), int(iters.max())]},
+        "mixed_vs_fp64_rel": agree,
+        "speedup_mixed_vs_fp64": t_fp64 / t_mixed,
+        "e2e": {"value": world * n_pts / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(y.nbytes + wt.nbytes),
+                "d2h_bytes_per_step": int(lam_h.numel() * 8 + it_h.numel() * 4 + mom_bytes)},
+        "clocks": clk,
+        "peaks_source": "MEASURED_PEAKS.json" if peaks else "fallback",
+    }
+    out["gpu_launches"] = None
+    return out, rank
+
+
+def cpu_baseline_sample(n_items=8, n_pts=24):
+    """The oracle as it stands on a bounded sample of the workload, single
+    threaded, extrapolated linearly to the whole step."""
+    code = r"""
+import json, sys, time, numpy as np
+sys.path.insert(0, %r)
+import sfb_workloads as W
+from oracle import coupled
+p = coupled.Problem(W.ALL[%r]())
+y, w = p.grid()
+t0 = time.perf_counter()
+items = 0
+for s in range(len(p.subs)):
+    loc, _ = p.local_realizations(s, y)
+    for k in range(%d // len(p.subs)):
+        p.darcy_basis(s, loc[k]); items += 1
+t1 = time.perf_counter()
+sel = np.linspace(0, len(y) - 1, %d).astype(int)
+lams, mom = coupled.solve_all(p, y[sel], w[sel])
+t2 = time.perf_counter()
+n_items_total = sum(len(p.local_realizations(s, y)[0]) for s in range(len(p.subs)))
+# solve_all rebuilds the bases it needs; subtract that share
+print(json.dumps({"basis_s": t1 - t0, "items": items, "points_s": t2 - t1, "points": len(sel),
+                  "n_items_total": n_items_total, "n_pts": len(y)}))
+""" % (ROOT, WORKLOAD, n_items, n_pts)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    per_item = d["basis_s"] / d["items"]
+    # the points leg includes building the bases its points reference
+    t_step = per_item * d["n_items_total"] + d["points_s"] / d["points"] * d["n_pts"]
+    return {"value": d["n_pts"] / t_step, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d of %d basis items and %d of %d points, single thread, extrapolated linearly"
+                      % (d["items"], d["n_items_total"], d["points"], d["n_pts"]),
+            "step_s_extrapolated": t_step}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return None
+    vals = []
+    t0 = time.perf_counter()
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline_sample(n_items=8, n_pts=8)
+        if i >= args.warmup:
+            vals.append(cb)
+    wall = time.perf_counter() - t0
+    v = float(np.median([c["value"] for c in vals]))
+    cb = dict(vals[-1])
+    cb["value"] = v
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["step_s_extrapolated"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "precision (same as the GPU arm)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        out = run_reference(args)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    out, rank = run_ours(args)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline_sample()
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -49,7 +49,8 @@ typedef enum {
   SFB_ERR_NONFINITE = 5,      /* non-finite permeability or solution            */
   SFB_ERR_NOT_CONVERGED = 6,  /* some point did not converge (outputs filled)   */
   SFB_ERR_NOT_SPD = 7,        /* a non-positive pivot in a factorization        */
-  SFB_ERR_UNSUPPORTED = 8     /* size beyond a compiled limit                   */
+  SFB_ERR_UNSUPPORTED = 8,    /* size beyond a compiled limit                   */
+  SFB_ERR_TIMEOUT = 9         /* a bounded wait inside a kernel gave up         */
 } sfb_status;
 
 typedef enum {
@@ -117,7 +118,12 @@ typedef struct {
   double max_rel_residual;    /* final ||B - A X||_F / ||B||_F over items         */
   double max_first_correction;/* mixed form: max ||dX_1||_F / ||X||_F: the        */
                               /* relative error of the unrefined FP32 solve       */
+  double max_error_estimate;  /* mixed form: max predicted relative error of X    */
+                              /* from the contraction of successive corrections   */
   double ms;                  /* device time of the build (CUDA events)           */
+  double phase_cycles[4];     /* mean SM cycles per item in: permeability and     */
+                              /* assembly, factorization, forward sweeps,         */
+                              /* backward sweeps (clock64 in the kernel)          */
 } sfb_basis_stats;
 
 typedef struct sfb_ctx sfb_ctx;
@@ -166,8 +172,9 @@ sfb_status sfb_set_workspace(sfb_ctx* ctx, void* dev_ptr, size_t bytes);
  * 5.4: N_real = 1 for Stokes subdomains). stats_out is nullable. */
 sfb_status sfb_build_stochastic_basis(sfb_ctx* ctx, int32_t prec, sfb_basis_stats* stats_out);
 
-/* Read-back of one stored basis item (host buffers): phi [R x R] row-major,
- * g [R], x [n_cells x (R+1)] (pressure responses, nullable). sub = -1 and
+/* Read-back of one stored basis item (host or device buffers): phi [R x R]
+ * row-major, g [R], x [(R+1) x n_cells] (pressure responses, column j is the
+ * response to xi_j, column R the particular solution; nullable). sub = -1 and
  * k = 0 return the Stokes basis (x must be NULL). */
 sfb_status sfb_get_basis(sfb_ctx* ctx, int32_t sub, int32_t k, double* phi, double* g, double* x);
 
@@ -187,6 +194,14 @@ sfb_status sfb_interface_solve_batch(sfb_ctx* ctx, const double* y, const double
  * length). SFB_ERR_STATE if nothing was solved. */
 sfb_status sfb_moments(sfb_ctx* ctx, int32_t field, double* mean_out, double* var_out);
 sfb_status sfb_moments_reset(sfb_ctx* ctx);
+
+/* Tuning knobs (no counterpart in the paper):
+ *   "refine_tol"     mixed form: stop refining when the predicted relative
+ *                    error of X is below this (default 1e-10);
+ *   "refine_max"     mixed form: at most this many FP64 residual passes (8);
+ *   "cg_check_every" CG iterations between convergence checks on the host (8).
+ * SFB_ERR_ARG for an unknown name or a value out of range. */
+sfb_status sfb_set_option(sfb_ctx* ctx, const char* name, double value);
 
 #ifdef __cplusplus
 }

@@ -21,7 +21,7 @@ SFB_ERR_NOT_CONVERGED = 6
 FP64, MIXED, FP32_NOREFINE = 0, 1, 2
 FIELDS = {"darcy_p": 0, "darcy_flux": 1, "stokes_u": 2, "stokes_p": 3}
 STATUS = {0: "OK", 1: "ARG", 2: "STATE", 3: "CUDA", 4: "WORKSPACE", 5: "NONFINITE",
-          6: "NOT_CONVERGED", 7: "NOT_SPD", 8: "UNSUPPORTED"}
+          6: "NOT_CONVERGED", 7: "NOT_SPD", 8: "UNSUPPORTED", 9: "TIMEOUT"}
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _f64p = ctypes.POINTER(ctypes.c_double)
@@ -53,7 +53,8 @@ class BasisStats(ctypes.Structure):
     _fields_ = [("n_items", ctypes.c_int64), ("n_flux_responses", ctypes.c_int64),
                 ("max_refine_steps", ctypes.c_int32), ("n_not_converged", ctypes.c_int32),
                 ("max_rel_residual", ctypes.c_double), ("max_first_correction", ctypes.c_double),
-                ("ms", ctypes.c_double)]
+                ("max_error_estimate", ctypes.c_double), ("ms", ctypes.c_double),
+                ("phase_cycles", ctypes.c_double * 4)]
 
 
 _SIGS = {
@@ -80,6 +81,7 @@ _SIGS = {
                                                  ctypes.c_void_p]),
     "sfb_moments": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "sfb_moments_reset": (ctypes.c_int, [ctypes.c_void_p]),
+    "sfb_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_double]),
 }
 
 _lib = None
@@ -262,6 +264,7 @@ class Solver:
         if check and rc != SFB_OK:
             self._check(rc)
         out = {k: getattr(st, k) for k, _ in BasisStats._fields_}
+        out["phase_cycles"] = list(st.phase_cycles)
         out["status"] = rc
         return out
 
@@ -274,10 +277,10 @@ class Solver:
         R = len(self.subdomain_dofs(sub))
         nx, ny = self.w["darcy_grid"][sub]
         phi, g = np.zeros((R, R)), np.zeros(R)
-        x = np.zeros((nx * ny, R + 1)) if with_x else None
+        x = np.zeros((R + 1, nx * ny)) if with_x else None
         self._check(self.lib.sfb_get_basis(self.h, sub, k, phi.ctypes.data, g.ctypes.data,
                                            x.ctypes.data if with_x else None))
-        return phi, g, x
+        return phi, g, (x.T.copy() if with_x else None)
 
     def solve(self, y, w, rtol=1e-10, max_it=1000, lam_out=None, iters_out=None, check=True):
         """Interface CG for a batch of points (host numpy or device torch
@@ -303,6 +306,9 @@ class Solver:
         mean, var = np.zeros(n), np.zeros(n)
         self._check(self.lib.sfb_moments(self.h, FIELDS[field], mean.ctypes.data, var.ctypes.data))
         return mean, var
+
+    def set_option(self, name, value):
+        self._check(self.lib.sfb_set_option(self.h, name.encode(), float(value)))
 
     def moments_reset(self):
         self._check(self.lib.sfb_moments_reset(self.h))

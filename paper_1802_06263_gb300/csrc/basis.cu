@@ -7,22 +7,27 @@
 //     transmissibilities of the cell-centred form of lowest-order RT with the
 //     trapezoidal rule (harmonic means inside, half-cell values on Dirichlet
 //     faces, zero on no-flow faces);
-//  2. factors the 5-point matrix A, which is block tridiagonal with nx x nx
+//  2. factors the diagonally scaled 5-point matrix
+//     Ahat = diag(A)^{-1/2} A diag(A)^{-1/2}, block tridiagonal with nx x nx
 //     tridiagonal diagonal blocks and diagonal couplings between grid rows,
-//     by the block LDL^T recurrence S_b = A_bb - D_{b-1} S_{b-1}^{-1} D_{b-1};
-//     each S_b is inverted in place by the symmetric sweep operator and
-//     G_b = S_b^{-1} is stored. Everything is applied to the diagonally
-//     scaled matrix diag(A)^{-1/2} A diag(A)^{-1/2};
-//  3. solves A X = B for the R + 1 right-hand sides at once: one column per
-//     mortar DOF (Dirichlet data = the face averages of xi_j, Eqs. 5.5-5.6)
-//     and one particular column (source and outer data, Eqs. 5.7-5.8), by a
-//     forward sweep z_b = G_b (B_b + D_{b-1} z_{b-1}) and a backward sweep
-//     x_b = z_b + G_b D_b x_{b+1};
+//     by the block LDL^T recurrence S_b = Ahat_bb - D_{b-1} S_{b-1}^{-1} D_{b-1}.
+//     Each S_b is inverted in registers by the symmetric sweep operator (one
+//     barrier per pivot) and G_b = S_b^{-1} is stored;
+//  3. solves A X = B for R + 1 right-hand sides at once: one column per mortar
+//     DOF (Dirichlet data = face averages of xi_j, Eqs. 5.5-5.6) and one
+//     particular column (source and outer data, Eqs. 5.7-5.8), by a forward
+//     sweep z_b = G_b (s_b r_b + D_{b-1} z_{b-1}) and a backward sweep
+//     d_b = z_b + G_b D_b d_{b+1}, x_b += s_b d_b;
 //  4. in the mixed form (factor type float) refines X with FP64 residuals
-//     r = B - A X of the 5-point stencil: X += A_32^{-1} r until
-//     ||r||_F <= tol ||B||_F, stagnation, or the step limit.
-// The flux-basis epilogue then projects the boundary fluxes of X back onto the
+//     r = B - A X of the 5-point stencil, stopping when the contraction of the
+//     corrections predicts a relative error below tol (or on stagnation or the
+//     step limit).
+// The flux-basis epilogue projects the boundary fluxes of X back onto the
 // mortar space (Section 5.2 step 3): Phi[l][j] = -<u(xi_j).n, xi_l>.
+//
+// Layouts: X and Z are column-major per item ([R+1][n_cells]); in shared
+// memory the right-hand-side block is [nx][Cp] (Cp = R+1 rounded up to 4) so
+// the products G_b U read float4 rows of G_b (symmetric) and of U.
 #include <math.h>
 
 #include "sfb_internal.h"
@@ -31,27 +36,21 @@ namespace sfb {
 
 namespace {
 
-constexpr int kThreads = 256;
-
 struct Geo {
-  int nx, ny, R, C, Cp;
+  int nx, ny, R, C, Cp, nc;
   const double* Tx;  // [ny][nx+1]
   const double* Ty;  // [ny+1][nx]
 };
 
-__device__ __forceinline__ double diag_of(const Geo& g, int b, int i) {
-  return g.Tx[b * (g.nx + 1) + i] + g.Tx[b * (g.nx + 1) + i + 1] + g.Ty[b * g.nx + i] +
-         g.Ty[(b + 1) * g.nx + i];
-}
-
-// Right-hand side entry B[(b, i)][c]: interface columns c < R carry
-// T_e * P_side[face][c] on interface faces; column R carries the source and
-// the outer Dirichlet data.
-__device__ __forceinline__ double rhs_entry(const SubDev& S, const Geo& g, const double* proj,
-                                            int b, int i, int c) {
+// Right-hand side entry B[(b, i)][c] in FP64: interface columns c < R carry
+// T_e * P_side[face][c] on interface faces of boundary cells; column R carries
+// the source and the outer Dirichlet data.
+__device__ __forceinline__ double rhs_entry(const SubDev& S, const Geo& g, const double* proj, int b, int i,
+                                            int c) {
   const int nx = g.nx, ny = g.ny;
   double v = 0.0;
   if (c < g.R) {
+    if (b > 0 && b < ny - 1 && i > 0 && i < nx - 1) return 0.0;
     if (b == 0 && S.side_type[0] == SIDE_IFACE) v += g.Ty[i] * proj[S.proj_off[0] + (int64_t)i * g.R + c];
     if (b == ny - 1 && S.side_type[2] == SIDE_IFACE)
       v += g.Ty[ny * nx + i] * proj[S.proj_off[2] + (int64_t)i * g.R + c];
@@ -69,39 +68,84 @@ __device__ __forceinline__ double rhs_entry(const SubDev& S, const Geo& g, const
   return v;
 }
 
-// out[i][c] = base[i][c] + sum_k G[i][k] Y[k][c] for i < n, c < C; smem
-// operands with row pitch n (G) and Cp (Y, out). `base` may alias `out`.
+// 4 consecutive values from a 16-byte aligned address (one float4 or two
+// double2 shared-memory loads).
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
+  const double2 q0 = *reinterpret_cast<const double2*>(p);
+  const double2 q1 = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+
+// out[i][c] (+)= sum_k G[i][k] U[k][c] for i < np, c < C, with G symmetric
+// (row k of G read as column k). G has pitch np, U and out pitch Cp; np and
+// Cp are multiples of 4 and both arrays start 16-byte aligned, so the 4-wide
+// loads are aligned. Columns [0, C & ~3) use 4 x 4 register tiles, the
+// remaining 1-3 columns 4 x 1 tiles, so R + 1 = 4q + 1 columns cost only a
+// sliver more than 4q.
 template <typename T>
-__device__ __forceinline__ void gemm_acc(const T* __restrict__ G, const T* __restrict__ Y, T* out,
-                                         const T* base, int n, int C, int Cp) {
-  const int nct = (C + 3) >> 2;
-  const int ntile = ((n + 3) >> 2) * nct;
-  for (int t = threadIdx.x; t < ntile; t += blockDim.x) {
-    const int i0 = (t / nct) * 4, c0 = (t % nct) * 4;
-    T acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[a][q] = T(0);
-    for (int k = 0; k < n; ++k) {
-      T gv[4], yv[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) gv[a] = (i0 + a < n) ? G[(i0 + a) * n + k] : T(0);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) yv[q] = Y[k * Cp + c0 + q];
+__device__ __forceinline__ void gemm_g(const T* __restrict__ G, const T* __restrict__ U, T* out, bool add_base,
+                                       int np, int Cp, int C) {
+  const int nrt = np >> 2;
+  const int Cm = C & ~3;
+  const int nct = Cm >> 2;
+  const int nmain = nrt * nct;
+  const int rc = C - Cm;
+  const int ntot = nmain + (rc ? nrt : 0);
+  for (int t = threadIdx.x; t < ntot; t += blockDim.x) {
+    if (t < nmain) {
+      const int i0 = (t / nct) * 4, c0 = (t % nct) * 4;
+      T acc[4][4];
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[a][q] = fma(gv[a], yv[q], acc[a][q]);
-    }
+        for (int q = 0; q < 4; ++q) acc[a][q] = T(0);
+#pragma unroll 2
+      for (int k = 0; k < np; ++k) {
+        T gv[4], uv[4];
+        load4(G + k * np + i0, gv);
+        load4(U + k * Cp + c0, uv);
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (i0 + a < n && c0 + q < C) {
-          T b0 = base ? base[(i0 + a) * Cp + c0 + q] : T(0);
-          out[(i0 + a) * Cp + c0 + q] = b0 + acc[a][q];
+          for (int q = 0; q < 4; ++q) acc[a][q] = fma(gv[a], uv[q], acc[a][q]);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        T* o = out + (i0 + a) * Cp + c0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) o[q] = (add_base ? o[q] : T(0)) + acc[a][q];
+      }
+    } else {
+      const int i0 = (t - nmain) * 4;
+      T acc[4][3];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) acc[a][q] = T(0);
+      for (int k = 0; k < np; ++k) {
+        T gv[4];
+        load4(G + k * np + i0, gv);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          if (q >= rc) break;
+          const T u = U[k * Cp + Cm + q];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) acc[a][q] = fma(gv[a], u, acc[a][q]);
         }
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          if (q >= rc) break;
+          T* o = out + (i0 + a) * Cp + Cm + q;
+          *o = (add_base ? *o : T(0)) + acc[a][q];
+        }
+    }
   }
 }
 
@@ -123,72 +167,254 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
-// In-place inversion of the SPD matrix in A (n x n, row pitch n) by the
-// symmetric sweep operator: sweeping pivot k maps a_kk -> -1/a_kk,
-// a_ik -> a_ik / a_kk, a_ij -> a_ij - a_ik a_kj / a_kk; after all pivots A
-// holds -S^{-1}, negated at the end. Pivots of an SPD matrix stay positive;
-// a non-positive pivot sets *bad.
-template <typename T>
-__device__ void sweep_invert(T* A, int n, T* vk, int* bad) {
-  for (int k = 0; k < n; ++k) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) vk[i] = A[i * n + k];
-    __syncthreads();
-    T piv = vk[k];
-    if (!(piv > T(0))) {
-      if (threadIdx.x == 0) *bad = 1;
-      piv = T(1);
+// ---- bulk asynchronous copies (TMA engine) and mbarriers ---------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+// global -> shared bulk copy completing on `bar` (issued by one thread)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// shared -> global bulk copy in the thread's bulk group (issued by one thread)
+__device__ __forceinline__ void bulk_store(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+               "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for phase `parity` of `bar`; false after the iteration limit.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+constexpr int kP = 8;  // pivots per panel of the blocked sweep
+
+// Block row b of the scaled matrix into the register tiles of the sweep:
+// S_b = Ahat_bb - D_{b-1} G_{b-1} D_{b-1}; on entry the tiles hold -G_{b-1}.
+// Rows / columns nx..np-1 are an identity padding.
+template <typename T, int MT, int NT>
+__device__ __forceinline__ void form_block(T (&areg)[MT][4][4], int b, int nx, int ntr, const T* txh,
+                                           const T* dlo) {
+#pragma unroll
+  for (int m = 0; m < MT; ++m) {
+    const int t = threadIdx.x + m * NT;
+    if (t >= ntr * ntr) break;
+    const int i0 = (t / ntr) * 4, j0 = (t % ntr) * 4;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + a, j = j0 + q;
+        T v;
+        if (i >= nx || j >= nx) {
+          v = (i == j) ? T(1) : T(0);
+        } else {
+          v = (i == j) ? T(1) : (j == i + 1 ? txh[j] : (j == i - 1 ? txh[i] : T(0)));
+          if (b > 0) v = fma(dlo[i] * areg[m][a][q], dlo[j], v);
+        }
+        areg[m][a][q] = v;
+      }
+  }
+}
+
+// Blocked symmetric sweep of the np x np SPD matrix held in register tiles:
+// for each panel K of kP pivots, A_KK -> -A_KK^{-1}, A_KJ -> A_KK^{-1} A_KJ,
+// A_JK -> A_JK A_KK^{-1}, A_JJ -> A_JJ - A_JK A_KK^{-1} A_KJ (the composition
+// of kP single-pivot sweeps). On exit the tiles hold -S^{-1}. The kP x kP
+// inverse is a sweep by warp 0; the rank-kP update reads VT (panel columns)
+// and W = A_KK^{-1} A_K* with 4-wide shared-memory loads.
+template <typename T, int MT, int NT>
+__device__ __forceinline__ void blocked_sweep(T (&areg)[MT][4][4], int np, int ntr, T* VT, T* W, T* Ablk,
+                                              int* bad) {
+  for (int k0 = 0; k0 < np; k0 += kP) {
+    // (a) panel columns: VT[p][i] = A[i][k0 + p]
+#pragma unroll
+    for (int m = 0; m < MT; ++m) {
+      const int t = threadIdx.x + m * NT;
+      if (t >= ntr * ntr) break;
+      const int i0 = (t / ntr) * 4, j0 = (t % ntr) * 4;
+      if (j0 >= k0 && j0 < k0 + kP)
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) VT[(j0 + q - k0) * np + i0 + a] = areg[m][a][q];
     }
-    const T inv = T(1) / piv;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-      const int i = e / n, j = e - i * n;
-      T v;
-      if (i == k && j == k) v = -inv;
-      else if (i == k) v = vk[j] * inv;
-      else if (j == k) v = vk[i] * inv;
-      else v = A[e] - vk[i] * (vk[j] * inv);
-      A[e] = v;
+    __syncthreads();
+    // (b) warp 0: sweep of the kP x kP block A_KK (Ablk = -A_KK^{-1})
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      for (int e = lane; e < kP * kP; e += 32) {
+        const int p = e / kP, q = e % kP;
+        Ablk[e] = VT[q * np + k0 + p];
+      }
+      __syncwarp();
+      for (int kk = 0; kk < kP; ++kk) {
+        T piv = Ablk[kk * kP + kk];
+        if (!(piv > T(0))) {
+          if (lane == 0) *bad = 1;
+          piv = T(1);
+        }
+        const T inv = T(1) / piv;
+        T nv[(kP * kP + 31) / 32];
+#pragma unroll
+        for (int r = 0; r < (kP * kP + 31) / 32; ++r) {
+          const int e = lane + 32 * r;
+          const int p = e / kP, q = e % kP;
+          const T own = Ablk[e], rowk = Ablk[kk * kP + q], colk = Ablk[p * kP + kk];
+          T v;
+          if (p == kk && q == kk) v = -inv;
+          else if (p == kk) v = rowk * inv;
+          else if (q == kk) v = colk * inv;
+          else v = fma(-colk, rowk * inv, own);
+          nv[r] = v;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < (kP * kP + 31) / 32; ++r) Ablk[lane + 32 * r] = nv[r];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // (c) W[p][j] = sum_q A_KK^{-1}[p][q] VT[q][j]
+    for (int j = threadIdx.x; j < np; j += NT) {
+      T col[kP];
+#pragma unroll
+      for (int q = 0; q < kP; ++q) col[q] = VT[q * np + j];
+#pragma unroll
+      for (int p = 0; p < kP; ++p) {
+        T w = T(0);
+#pragma unroll
+        for (int q = 0; q < kP; ++q) w = fma(-Ablk[p * kP + q], col[q], w);
+        W[p * np + j] = w;
+      }
+    }
+    __syncthreads();
+    // (d) update the register tiles
+#pragma unroll
+    for (int m = 0; m < MT; ++m) {
+      const int t = threadIdx.x + m * NT;
+      if (t >= ntr * ntr) break;
+      const int i0 = (t / ntr) * 4, j0 = (t % ntr) * 4;
+      const bool rk = i0 >= k0 && i0 < k0 + kP, ck = j0 >= k0 && j0 < k0 + kP;
+      if (!rk && !ck) {
+#pragma unroll
+        for (int p = 0; p < kP; ++p) {
+          T v4[4], w4[4];
+          load4(VT + p * np + i0, v4);
+          load4(W + p * np + j0, w4);
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) areg[m][a][q] = fma(-v4[a], w4[q], areg[m][a][q]);
+        }
+      } else if (rk && !ck) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) areg[m][a][q] = W[(i0 + a - k0) * np + j0 + q];
+      } else if (!rk && ck) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) areg[m][a][q] = W[(j0 + q - k0) * np + i0 + a];
+      } else {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) areg[m][a][q] = Ablk[(i0 + a - k0) * kP + (j0 + q - k0)];
+      }
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = -A[e];
-  __syncthreads();
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) basis_kernel(BasisArgs a, int refine) {
+template <typename T, int MT, int NT, int MINB, int GB>
+__global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   __shared__ int bad_spd;
+  __shared__ __align__(8) uint64_t gbar[2];
+  __shared__ __align__(8) uint64_t zbar;
   const int item = blockIdx.x;
   if (item >= a.n_items) return;
   const int s = a.item_sub[item], kk = a.item_k[item];
   const SubDev S = a.subs[s];
   const int id = (int)S.item0 + kk;
   const ItemOff off = a.off[id];
-  const int nx = S.nx, ny = S.ny, nc = nx * ny;
   Geo g;
-  g.nx = nx; g.ny = ny; g.R = S.R; g.C = S.R + 1; g.Cp = (g.C + 3) & ~3;
+  g.nx = S.nx; g.ny = S.ny; g.R = S.R; g.C = S.R + 1; g.Cp = (g.C + 3) & ~3; g.nc = S.nx * S.ny;
+  const int nx = g.nx, ny = g.ny, nc = g.nc, C = g.C, Cp = g.Cp;
+  const int np = (nx + kP - 1) & ~(kP - 1);  // identity-padded block size
+  const int ntr = np >> 2;
+  const uint32_t gbytes = (uint32_t)(np * np * sizeof(T));
+  const uint32_t zbytes = (uint32_t)(np * Cp * sizeof(T));
   double* Tx = a.T + off.t;
   double* Ty = Tx + (int64_t)ny * (nx + 1);
   g.Tx = Tx; g.Ty = Ty;
   double* X = a.X + off.x;
   double* Dg = a.D + off.diag;
-  T* Gg = reinterpret_cast<T*>(a.G) + off.g;
-  T* Zg = reinterpret_cast<T*>(a.Z) + off.z;
-  const int C = g.C, Cp = g.Cp;
+  T* Sg = reinterpret_cast<T*>(a.S) + off.sc;
+  T* Gg = reinterpret_cast<T*>(a.G) + off.g;   // [ny][np][np]
+  T* Zg = reinterpret_cast<T*>(a.Z) + off.z;   // [ny][np][Cp], the shared-memory image of a row block
 
-  // smem: sc[nx] | scp[nx] (double) | Gs[nx*nx] | Ys[nx*Cp] | Zs[nx*Cp] | vk[nx] (T)
-  double* sc = reinterpret_cast<double*>(smem_raw);
-  double* scp = sc + nx;
-  T* Gs = reinterpret_cast<T*>(scp + nx);
-  T* Ys = Gs + nx * nx;
-  T* Zs = Ys + nx * Cp;
-  T* vk = Zs + nx * Cp;
+  // smem: Gs[GB][np*np] | Us[np*Cp] | Zs[np*Cp] | VT[kP*np] | W[kP*np] | Ablk[kP*kP] | sc | dlo | dup | txh
+  T* Gs0 = reinterpret_cast<T*>(smem_raw);
+  T* Us = Gs0 + GB * np * np;
+  T* Zs = Us + np * Cp;
+  T* VT = Zs + np * Cp;
+  T* W = VT + kP * np;
+  T* Ablk = W + kP * np;
+  T* sc = Ablk + kP * kP;
+  T* dlo = sc + np;
+  T* dup = dlo + np;
+  T* txh = dup + np;
+  uint32_t gph[2] = {0u, 0u}, zph = 0u;
 
-  if (threadIdx.x == 0) bad_spd = 0;
+  if (threadIdx.x == 0) {
+    bad_spd = 0;
+    mbar_init(&gbar[0], 1);
+    mbar_init(&gbar[1], 1);
+    mbar_init(&zbar, 1);
+    fence_barrier_init();
+  }
   int st = 0;
+  long long t_mark = clock64(), t_fwd = 0, t_bwd = 0;
+  long long* cyc = a.cycles + 4 * (int64_t)id;
+  for (int e = threadIdx.x; e < np * Cp; e += blockDim.x) { Us[e] = T(0); Zs[e] = T(0); }
+  for (int e = threadIdx.x; e < np; e += blockDim.x) { sc[e] = T(0); dlo[e] = T(0); dup[e] = T(0); txh[e] = T(0); }
+  __syncthreads();
 
-  // ---- 1. permeability and transmissibilities ---------------------------
+  // ---- 1. permeability, transmissibilities, diagonal and scaling ------------
   {
     const int nt = S.n_term;
     const double* slam = a.kl + S.kl_off;
@@ -230,141 +456,231 @@ __global__ void __launch_bounds__(kThreads) basis_kernel(BasisArgs a, int refine
       Ty[f] = t;
     }
     __syncthreads();
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) Dg[c] = diag_of(g, c / nx, c % nx);
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+      const int b = c / nx, i = c - b * nx;
+      const double d = Tx[b * (nx + 1) + i] + Tx[b * (nx + 1) + i + 1] + Ty[b * nx + i] + Ty[(b + 1) * nx + i];
+      Dg[c] = d;
+      Sg[c] = T(1.0 / sqrt(d));
+    }
     __syncthreads();
   }
+  if (threadIdx.x == 0) { const long long t = clock64(); cyc[0] = t - t_mark; t_mark = t; }
 
-  // ---- 2. block LDL^T factorization of the scaled matrix -------------------
+  // ---- 2. factorization, fused with the first forward solve ------------------
+  // G_b and z_b leave through bulk stores from shared memory.
+  T areg[MT][4][4];
   for (int b = 0; b < ny; ++b) {
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      if (b > 0) scp[i] = sc[i];
-      sc[i] = 1.0 / sqrt(Dg[b * nx + i]);
+      const double si = (double)Sg[b * nx + i];
+      sc[i] = T(si);
+      txh[i] = i > 0 ? T(-Tx[b * (nx + 1) + i] * si * (double)Sg[b * nx + i - 1]) : T(0);
+      dlo[i] = b > 0 ? T((double)Sg[(b - 1) * nx + i] * Ty[b * nx + i] * si) : T(0);
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < nx * nx; e += blockDim.x) {
-      const int i = e / nx, j = e - i * nx;
-      double v = 0.0;
-      if (i == j) v = 1.0;
-      else if (j == i + 1) v = -Tx[b * (nx + 1) + j] * sc[i] * sc[j];
-      else if (j == i - 1) v = -Tx[b * (nx + 1) + i] * sc[i] * sc[j];
-      T w = T(v);
-      if (b > 0) {
-        const double di = scp[i] * Ty[b * nx + i] * sc[i];
-        const double dj = scp[j] * Ty[b * nx + j] * sc[j];
-        w = T(v - di * (double)Gs[e] * dj);
-      }
-      Gs[e] = w;
+    form_block<T, MT, NT>(areg, b, nx, ntr, txh, dlo);
+    blocked_sweep<T, MT, NT>(areg, np, ntr, VT, W, Ablk, &bad_spd);
+    T* Gs = Gs0 + (b % GB) * np * np;
+    if (threadIdx.x == 0) bulk_wait_read();   // the store that last read Gs / Zs is done
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < MT; ++m) {
+      const int t = threadIdx.x + m * NT;
+      if (t >= ntr * ntr) break;
+      const int i0 = (t / ntr) * 4, j0 = (t % ntr) * 4;
+#pragma unroll
+      for (int a2 = 0; a2 < 4; ++a2)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Gs[(i0 + a2) * np + j0 + q] = -areg[m][a2][q];
     }
+    // first forward solve row: u_b = s_b B_b + dlo_b z_{b-1}
+    for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
+      const int i = e % nx, c = e / nx;
+      T u = sc[i] * T(rhs_entry(S, g, a.proj, b, i, c));
+      if (b > 0) u = fma(dlo[i], Zs[i * Cp + c], u);
+      Us[i * Cp + c] = u;
+    }
+    fence_async_shared();
     __syncthreads();
-    sweep_invert<T>(Gs, nx, vk, &bad_spd);
-    for (int e = threadIdx.x; e < nx * nx; e += blockDim.x) Gg[(int64_t)b * nx * nx + e] = Gs[e];
+    if (threadIdx.x == 0) bulk_store(Gg + (int64_t)b * np * np, Gs, gbytes);
+    gemm_g<T>(Gs, Us, Zs, false, np, Cp, C);
+    fence_async_shared();
     __syncthreads();
+    if (threadIdx.x == 0) bulk_store(Zg + (int64_t)b * np * Cp, Zs, zbytes);
   }
+  if (threadIdx.x == 0) {
+    bulk_wait_all();
+    fence_async_global();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) { const long long t = clock64(); cyc[1] = t - t_mark; t_mark = t; }
 
-  // ---- 3./4. solve, then refine with FP64 residuals --------------------------
-  double bnorm2 = 0.0, rprev = 0.0;
-  int it = 0;
-  for (; it <= refine; ++it) {
-    // forward sweep: r_b = B_b - (A x)_b; u_b = s_b r_b + dhat_{b-1} z_{b-1}; z_b = G_b u_b
-    double rr = 0.0;
-    for (int b = 0; b < ny; ++b) {
-      for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        if (b > 0) scp[i] = sc[i];
-        sc[i] = 1.0 / sqrt(Dg[b * nx + i]);
-      }
-      const T* Grow = Gg + (int64_t)b * nx * nx;
-      for (int e = threadIdx.x; e < nx * nx; e += blockDim.x) Gs[e] = Grow[e];
-      __syncthreads();
-      for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
-        const int i = e / C, c = e - i * C;
-        double r = rhs_entry(S, g, a.proj, b, i, c);
-        if (it == 0) {
-          bnorm2 += r * r;
-        } else {
-          const int64_t cell = (int64_t)b * nx + i;
-          double ax = Dg[cell] * X[cell * C + c];
-          if (i > 0) ax -= Tx[b * (nx + 1) + i] * X[(cell - 1) * C + c];
-          if (i < nx - 1) ax -= Tx[b * (nx + 1) + i + 1] * X[(cell + 1) * C + c];
-          if (b > 0) ax -= Ty[b * nx + i] * X[(cell - nx) * C + c];
-          if (b < ny - 1) ax -= Ty[(b + 1) * nx + i] * X[(cell + nx) * C + c];
-          r -= ax;
-          rr += r * r;
-        }
-        double u = sc[i] * r;
-        if (b > 0) u += scp[i] * Ty[b * nx + i] * sc[i] * (double)Zs[i * Cp + c];
-        Ys[i * Cp + c] = T(u);
-      }
-      __syncthreads();
-      gemm_acc<T>(Gs, Ys, Zs, nullptr, nx, C, Cp);
-      __syncthreads();
-      for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
-        const int i = e / C, c = e - i * C;
-        Zg[((int64_t)b * nx + i) * C + c] = Zs[i * Cp + c];
-      }
-    }
-    if (it == 0) {
-      bnorm2 = block_sum(bnorm2, red);
-    } else {
-      rr = block_sum(rr, red);
-      const double rel = sqrt(rr / fmax(bnorm2, 1e-300));
-      if (threadIdx.x == 0) a.resid[id] = rel;
-      if (rel <= a.refine_tol) break;                      // converged: keep X
-      if (it >= 2 && rel > 0.5 * rprev) { st |= ST_NOT_CONVERGED; break; }  // stagnated
-      if (it == refine) { st |= ST_NOT_CONVERGED; break; }  // step limit: keep X
-      rprev = rel;
-    }
-    __syncthreads();
-    // backward sweep: d_b = z_b + G_b (dhat_b .* d_{b+1}); x_b += s_b d_b
-    double dn2 = 0.0, xn2 = 0.0;
-    for (int b = ny - 1; b >= 0; --b) {
-      for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        sc[i] = 1.0 / sqrt(Dg[b * nx + i]);
-        if (b < ny - 1) scp[i] = 1.0 / sqrt(Dg[(b + 1) * nx + i]);
-      }
-      const T* Grow = Gg + (int64_t)b * nx * nx;
-      for (int e = threadIdx.x; e < nx * nx; e += blockDim.x) Gs[e] = Grow[e];
-      __syncthreads();
-      if (b < ny - 1) {
-        for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
-          const int i = e / C, c = e - i * C;
-          const double dh = sc[i] * Ty[(b + 1) * nx + i] * scp[i];
-          Ys[i * Cp + c] = T(dh * (double)Zs[i * Cp + c]);
-        }
-        for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
-          const int i = e / C, c = e - i * C;
-          Zs[i * Cp + c] = Zg[((int64_t)b * nx + i) * C + c];
+  // ---- 3./4. backward sweep, then refine with FP64 residuals --------------------------
+  double xref2 = 0.0, prev_corr = 0.0, est = 1.0, bnorm2 = 0.0;
+  int n_done = 0;
+  bool timeout = false;
+  for (int it = 0; it <= refine && !timeout; ++it) {
+    float rr = 0.f;
+    if (it > 0) {
+      // forward sweep: r_b = B_b - (A x)_b in FP64; u_b = s_b r_b + dlo_b z_{b-1}
+      if (threadIdx.x == 0) { fence_async_shared(); bulk_load(Gs0, Gg, gbytes, &gbar[0]); }
+      for (int b = 0; b < ny; ++b) {
+        const int cur = GB == 2 ? (b & 1) : 0;
+        T* Gs = Gs0 + cur * np * np;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+          const double si = (double)Sg[b * nx + i];
+          sc[i] = T(si);
+          dlo[i] = b > 0 ? T((double)Sg[(b - 1) * nx + i] * Ty[b * nx + i] * si) : T(0);
         }
         __syncthreads();
-        gemm_acc<T>(Gs, Ys, Zs, Zs, nx, C, Cp);
-      } else {
+        if (GB == 2 && threadIdx.x == 0 && b + 1 < ny) {
+          fence_async_shared();
+          bulk_load(Gs0 + (cur ^ 1) * np * np, Gg + (int64_t)(b + 1) * np * np, gbytes, &gbar[cur ^ 1]);
+        }
+#pragma unroll 2
         for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
-          const int i = e / C, c = e - i * C;
-          Zs[i * Cp + c] = Zg[((int64_t)b * nx + i) * C + c];
+          const int i = e % nx, c = e / nx;
+          const int64_t cell = (int64_t)b * nx + i;
+          const double* xc = X + (int64_t)c * nc;
+          double r = rhs_entry(S, g, a.proj, b, i, c);
+          double ax = Dg[cell] * xc[cell];
+          if (i > 0) ax = fma(-Tx[b * (nx + 1) + i], xc[cell - 1], ax);
+          if (i < nx - 1) ax = fma(-Tx[b * (nx + 1) + i + 1], xc[cell + 1], ax);
+          if (b > 0) ax = fma(-Ty[b * nx + i], xc[cell - nx], ax);
+          if (b < ny - 1) ax = fma(-Ty[(b + 1) * nx + i], xc[cell + nx], ax);
+          r -= ax;
+          const T rt = T(r);
+          const float rf = (float)rt;
+          rr = fmaf(rf, rf, rr);
+          T u = sc[i] * rt;
+          if (b > 0) u = fma(dlo[i], Zs[i * Cp + c], u);
+          Us[i * Cp + c] = u;
+        }
+        // G_b present, and the store that reads Zs finished
+        if (threadIdx.x == 0) bulk_wait_read();
+        const bool ok = mbar_wait(&gbar[cur], gph[cur]);
+        gph[cur] ^= 1u;
+        if (__syncthreads_or(!ok)) { timeout = true; break; }
+        gemm_g<T>(Gs, Us, Zs, false, np, Cp, C);
+        fence_async_shared();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          bulk_store(Zg + (int64_t)b * np * Cp, Zs, zbytes);
+          if (GB == 1 && b + 1 < ny) { fence_async_shared(); bulk_load(Gs0, Gg + (int64_t)(b + 1) * np * np, gbytes, &gbar[0]); }
         }
       }
+      if (threadIdx.x == 0) {
+        bulk_wait_all();
+        fence_async_global();
+      }
       __syncthreads();
+      if (timeout) break;
+      const double rnorm2 = block_sum((double)rr, red);
+      if (threadIdx.x == 0) a.resid[id] = sqrt(rnorm2 / fmax(bnorm2, 1e-300));
+      if (threadIdx.x == 0) { const long long t = clock64(); t_fwd += t - t_mark; t_mark = t; }
+    } else {
+      // |B|^2 for the relative residual
+      float bb = 0.f;
+      for (int e = threadIdx.x; e < nc * C; e += blockDim.x) {
+        const int c = e / nc, cell = e - c * nc;
+        const float v = (float)rhs_entry(S, g, a.proj, cell / nx, cell % nx, c);
+        bb = fmaf(v, v, bb);
+      }
+      bnorm2 = block_sum((double)bb, red);
+    }
+    // backward sweep: d_b = z_b + G_b (dup_b .* d_{b+1}); x_b += s_b d_b.
+    // G_{b-1} is prefetched while row b runs (two G buffers).
+    float dn2f = 0.f;
+    if (GB == 2 && threadIdx.x == 0 && ny >= 2) {
+      fence_async_shared();
+      bulk_load(Gs0, Gg + (int64_t)(ny - 2) * np * np, gbytes, &gbar[0]);
+    }
+    for (int b = ny - 1; b >= 0; --b) {
+      const int cur = GB == 2 ? ((ny - 2 - b) & 1) : 0;   // buffer of G_b (b <= ny-2)
+      T* Gs = Gs0 + cur * np * np;
+      for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const double si = (double)Sg[b * nx + i];
+        sc[i] = T(si);
+        dup[i] = b < ny - 1 ? T(si * Ty[(b + 1) * nx + i] * (double)Sg[(b + 1) * nx + i]) : T(0);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0 && b < ny - 1) {
+        fence_async_shared();
+        if (GB == 2 && b >= 1)   // prefetch G_{b-1}
+          bulk_load(Gs0 + (cur ^ 1) * np * np, Gg + (int64_t)(b - 1) * np * np, gbytes, &gbar[cur ^ 1]);
+        if (GB == 1)             // G_b into the single buffer
+          bulk_load(Gs0, Gg + (int64_t)b * np * np, gbytes, &gbar[0]);
+      }
+      // Us = dup .* d_{b+1} (d_{b+1} in Zs), then z_b -> Zs
       for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
-        const int i = e / C, c = e - i * C;
-        const int64_t idx = ((int64_t)b * nx + i) * C + c;
-        const double d = sc[i] * (double)Zs[i * Cp + c];
-        if (it == 0) {
-          X[idx] = d;
-        } else {
-          const double xo = X[idx];
-          X[idx] = xo + d;
-          if (it == 1) { dn2 += d * d; xn2 += (xo + d) * (xo + d); }
-        }
+        const int i = e % nx, c = e / nx;
+        Us[i * Cp + c] = dup[i] * Zs[i * Cp + c];
+      }
+      fence_async_shared();
+      __syncthreads();
+      if (threadIdx.x == 0) bulk_load(Zs, Zg + (int64_t)b * np * Cp, zbytes, &zbar);
+      bool ok = mbar_wait(&zbar, zph);
+      zph ^= 1u;
+      if (b < ny - 1) {
+        ok = mbar_wait(&gbar[cur], gph[cur]) && ok;
+        gph[cur] ^= 1u;
+      }
+      if (__syncthreads_or(!ok)) { timeout = true; break; }
+      if (b < ny - 1) gemm_g<T>(Gs, Us, Zs, true, np, Cp, C);
+      __syncthreads();
+#pragma unroll 4
+      for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
+        const int i = e % nx, c = e / nx;
+        const int64_t idx = (int64_t)c * nc + (int64_t)b * nx + i;
+        const T dt = sc[i] * Zs[i * Cp + c];
+        const float df = (float)dt;
+        dn2f = fmaf(df, df, dn2f);
+        if (it == 0) X[idx] = (double)dt;
+        else X[idx] += (double)dt;
       }
       __syncthreads();
     }
-    if (it == 1) {
-      dn2 = block_sum(dn2, red);
-      xn2 = block_sum(xn2, red);
-      if (threadIdx.x == 0) a.corr1[id] = sqrt(dn2 / fmax(xn2, 1e-300));
+    if (timeout) break;
+    const double dn2 = block_sum((double)dn2f, red);
+    if (threadIdx.x == 0) { const long long t = clock64(); t_bwd += t - t_mark; t_mark = t; }
+    if (it == 0) {
+      xref2 = dn2;  // ||x_0||^2
+      prev_corr = 1.0;
+      est = 1.0;
+    } else {
+      const double corr = sqrt(dn2 / fmax(xref2, 1e-300));  // ||d_it|| / ||x||
+      const double rho = corr / fmax(prev_corr, 1e-300);
+      est = rho < 1.0 ? rho / (1.0 - rho) * corr : 1.0;
+      if (threadIdx.x == 0 && it == 1) a.corr1[id] = corr;
+      prev_corr = corr;
+      n_done = it;
+      if (est <= a.refine_tol) break;
+      if (rho > 0.5) {
+        st |= ST_NOT_CONVERGED;
+        break;
+      }
+      if (it == refine) st |= ST_NOT_CONVERGED;
     }
   }
-  if (threadIdx.x == 0) a.nref[id] = it > refine ? refine : it;
-  // NaN check on the result
+  if (timeout) {
+    // give the copies in flight a bounded chance to land before the CTA exits
+    if (threadIdx.x == 0) {
+      mbar_wait(&gbar[0], gph[0]);
+      mbar_wait(&gbar[1], gph[1]);
+      mbar_wait(&zbar, zph);
+      bulk_wait_all();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) atomicOr(&a.status[id], ST_TIMEOUT);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    bulk_wait_all();
+    cyc[2] = t_fwd;
+    cyc[3] = t_bwd;
+    a.nref[id] = n_done;
+    a.errest[id] = refine > 0 ? est : 0.0;
+  }
+  // non-finite check on the result
   for (int e = threadIdx.x; e < nc * C; e += blockDim.x)
     if (!isfinite(X[e])) st |= ST_NONFINITE;
   __syncthreads();
@@ -379,10 +695,10 @@ __global__ void flux_epilogue_kernel(BasisArgs a) {
   const int item = blockIdx.x;
   if (item >= a.n_items) return;
   const int s = a.item_sub[item], kk = a.item_k[item];
-  const SubDev S = a.subs[s];
+  const SubDev& S = a.subs[s];
   const int id = (int)S.item0 + kk;
   const ItemOff off = a.off[id];
-  const int nx = S.nx, ny = S.ny, R = S.R, C = R + 1;
+  const int nx = S.nx, ny = S.ny, R = S.R, C = R + 1, nc = nx * ny;
   const double* Tx = a.T + off.t;
   const double* Ty = Tx + (int64_t)ny * (nx + 1);
   const double* X = a.X + off.x;
@@ -402,26 +718,44 @@ __global__ void flux_epilogue_kernel(BasisArgs a) {
       else { cell = f * nx + nx - 1; t = Tx[f * (nx + 1) + nx]; }
       const double pl = P[(int64_t)f * R + l];
       const double pj = (j < R) ? P[(int64_t)f * R + j] : 0.0;
-      acc += pl * t * (X[(int64_t)cell * C + j] - pj);
+      acc += pl * t * (X[(int64_t)j * nc + cell] - pj);
     }
     if (j < R) phi[l * R + j] = -acc;
     else phi[R * R + l] = acc;
   }
 }
 
+// G buffers: two (prefetch of the next block row) for the FP32 factor, one for
+// FP64 where shared memory would otherwise limit residency to one CTA per SM.
+template <typename T>
+constexpr int g_buffers() { return sizeof(T) == 4 ? 2 : 1; }
+
 template <typename T>
 size_t basis_smem(int max_nx, int max_cols) {
-  const int cp = (max_cols + 3) & ~3;
-  return sizeof(double) * 2 * max_nx + sizeof(T) * ((size_t)max_nx * max_nx + 2 * (size_t)max_nx * cp + max_nx);
+  const size_t cp = (max_cols + 3) & ~3;
+  const size_t np = (max_nx + kP - 1) & ~(kP - 1);
+  return sizeof(T) * (g_buffers<T>() * np * np + 2 * np * cp + 2 * kP * np + kP * kP + 4 * np);
 }
 
+template <typename T, int MT, int NT, int MINB>
+cudaError_t launch_one(const BasisArgs& a, size_t smem, int refine, cudaStream_t st) {
+  constexpr int GB = g_buffers<T>();
+  cudaError_t e = cudaFuncSetAttribute(basis_kernel<T, MT, NT, MINB, GB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  basis_kernel<T, MT, NT, MINB, GB><<<a.n_items, NT, smem, st>>>(a, refine);
+  return cudaGetLastError();
+}
+
+// Thread-block shape: the register tiles of the sweep are 4 x 4; np <= 64
+// gives at most 256 tiles (one per thread of 256), np <= 128 at most 1024
+// (four per thread of 256 for FP32, two per thread of 512 for FP64).
 template <typename T>
 cudaError_t launch_basis(const BasisArgs& a, int max_nx, int max_cols, int refine, cudaStream_t st) {
   const size_t smem = basis_smem<T>(max_nx, max_cols);
-  cudaError_t e = cudaFuncSetAttribute(basis_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  basis_kernel<T><<<a.n_items, kThreads, smem, st>>>(a, refine);
-  return cudaGetLastError();
+  if (max_nx <= 64) return launch_one<T, 1, 256, sizeof(T) == 4 ? 3 : 2>(a, smem, refine, st);
+  if (sizeof(T) == 4) return launch_one<T, 4, 256, 1>(a, smem, refine, st);
+  return launch_one<T, 2, 512, 1>(a, smem, refine, st);
 }
 
 }  // namespace
@@ -435,7 +769,7 @@ cudaError_t launch_basis_mixed(const BasisArgs& a, int max_nx, int max_cols, int
 }
 
 cudaError_t launch_flux_epilogue(const BasisArgs& a, int /*max_R*/, cudaStream_t st) {
-  flux_epilogue_kernel<<<a.n_items, kThreads, 0, st>>>(a);
+  flux_epilogue_kernel<<<a.n_items, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

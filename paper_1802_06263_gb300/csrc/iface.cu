@@ -300,187 +300,219 @@ __global__ void finish_status(int* pstat, int64_t n, int max_it, int* iters_out)
 }
 
 // ---- moments ---------------------------------------------------------------------
+// Darcy fields: per-point recovery p = X^k [R lambda; 1] on a tile of grid rows
+// (plus one halo row for the y-face fluxes), face velocities from p, and the
+// shifted sums sum w (x - shift), sum w (x - shift)^2 accumulated in registers
+// by the thread that owns each field entry; one partial per point chunk,
+// summed in a fixed order afterwards (deterministic, no floating atomics).
 struct MomArgs {
   IfaceArgs ia;
   const double* X;
   const double* T;
   const double* proj;
   const double* w;
-  double* mom;          // [3][len]: shift, S1, S2 (offsets by field)
-  int64_t off_p, off_f, len_p, len_f, sub_p0, sub_f0;
-  int64_t mom_len_total;
-  int mode;             // 0: write shifts from point 0; 1: accumulate
-  int rt;               // rows per CTA
-  const int64_t* cell_off;  // per subdomain first cell in the Darcy pressure field
-  const int64_t* face_off;  // per subdomain first face in the Darcy flux field
+  double* shift;            // [len_d] shifts (the field at point 0 of the first batch)
+  double* part;             // [n_chunks][2][len_d] partial sums of this batch
+  int64_t len_d;            // Darcy entries: all cell pressures, then all face velocities
+  int64_t off_f;            // first face-velocity entry
+  const int64_t* cell_off;  // per subdomain first cell
+  const int64_t* face_off;  // per subdomain first face
+  int mode;                 // 0: write the shifts from point 0; 1: accumulate
+  int rt;                   // grid rows per CTA
+  int n_chunks;
 };
 
-__device__ __forceinline__ void mom_add(double* mom, int64_t L, int64_t idx, double v, double w, int mode) {
-  if (mode == 0) { mom[idx] = v; return; }
-  const double d = v - mom[idx];
-  mom[L + idx] += w * d;
-  mom[2 * L + idx] += w * d * d;
+constexpr int kMomT = 256;   // threads of the Darcy moments kernel
+constexpr int kMaxE = 8;     // field entries owned per thread
+
+__device__ __forceinline__ double darcy_value(const SubDev& S, const MomArgs& m, int64_t e_loc, int r0, int r1,
+                                              int h0, const double* Tx, const double* Ty, const double* Z,
+                                              const double* Cf, int q, int C) {
+  const int nx = S.nx, ny = S.ny, R = S.R;
+  const int np = (r1 - r0) * nx, nxf = (r1 - r0) * (nx + 1);
+  if (e_loc < np) {
+    const int c = (r0 - h0) * nx + (int)e_loc;
+    return Z[c * kTP + q];
+  }
+  if (e_loc < np + nxf) {
+    const int f = (int)(e_loc - np);
+    const int rr_ = r0 + f / (nx + 1), ix = f % (nx + 1);
+    const int zrow = (rr_ - h0) * nx;
+    const double t = Tx[(int64_t)rr_ * (nx + 1) + ix];
+    if (ix > 0 && ix < nx) return t * (Z[(zrow + ix - 1) * kTP + q] - Z[(zrow + ix) * kTP + q]) / S.hy;
+    const int side = ix == 0 ? 3 : 1;
+    if (S.side_type[side] == SIDE_NOFLOW) return 0.0;
+    double gb = S.side_val[side];
+    if (S.side_type[side] == SIDE_IFACE) {
+      const double* P = m.proj + S.proj_off[side] + (int64_t)rr_ * R;
+      gb = 0.0;
+      for (int i = 0; i < R; ++i) gb += P[i] * Cf[q * C + i];
+    }
+    const double F = t * (Z[(zrow + (ix == 0 ? 0 : nx - 1)) * kTP + q] - gb);
+    return (ix == 0 ? -F : F) / S.hy;
+  }
+  const int f = (int)(e_loc - np - nxf);
+  const int j = r0 + f / nx, ix = f % nx;
+  const double t = Ty[(int64_t)j * nx + ix];
+  if (j > 0 && j < ny) return t * (Z[((j - 1 - h0) * nx + ix) * kTP + q] - Z[((j - h0) * nx + ix) * kTP + q]) / S.hx;
+  const int side = j == 0 ? 0 : 2;
+  if (S.side_type[side] == SIDE_NOFLOW) return 0.0;
+  double gb = S.side_val[side];
+  if (S.side_type[side] == SIDE_IFACE) {
+    const double* P = m.proj + S.proj_off[side] + (int64_t)ix * R;
+    gb = 0.0;
+    for (int i = 0; i < R; ++i) gb += P[i] * Cf[q * C + i];
+  }
+  const double F = t * (Z[((j == 0 ? 0 : ny - 1) - h0) * nx * kTP + ix * kTP + q] - gb);
+  return (j == 0 ? -F : F) / S.hx;
 }
 
-// One CTA per (row tile, subdomain). For every local realization k and every
-// tile of the points that use it: pressures z = X^k [R lambda; 1] on the tile
-// rows plus one halo row below, then pressures and face velocities.
-__global__ void __launch_bounds__(256) darcy_moments_kernel(MomArgs m) {
+// Global entry index of a tile-local entry.
+__device__ __forceinline__ int64_t darcy_entry(const SubDev& S, const MomArgs& m, int s, int64_t e_loc, int r0,
+                                               int r1) {
+  const int nx = S.nx, ny = S.ny;
+  const int np = (r1 - r0) * nx, nxf = (r1 - r0) * (nx + 1);
+  if (e_loc < np) return m.cell_off[s] + (int64_t)r0 * nx + e_loc;
+  if (e_loc < np + nxf) return m.off_f + m.face_off[s] + (int64_t)r0 * (nx + 1) + (e_loc - np);
+  return m.off_f + m.face_off[s] + (int64_t)ny * (nx + 1) + (int64_t)r0 * nx + (e_loc - np - nxf);
+}
+
+__global__ void __launch_bounds__(kMomT) darcy_moments_kernel(MomArgs m) {
   extern __shared__ __align__(16) double sm[];
   const IfaceArgs& a = m.ia;
-  const int s = blockIdx.y;
+  const int s = blockIdx.y, ch = blockIdx.z;
   const SubDev S = a.subs[s];
-  const int nx = S.nx, ny = S.ny, R = S.R, C = R + 1;
+  const int nx = S.nx, ny = S.ny, R = S.R, C = R + 1, nc = nx * ny;
   const int r0 = blockIdx.x * m.rt;
   if (r0 >= ny) return;
+  if (m.mode == 0 && ch != 0) return;
   const int r1 = min(ny, r0 + m.rt);
-  const int h0 = max(0, r0 - 1);            // first row evaluated (halo)
-  const int nrows = r1 - h0;
-  const int ncell = nrows * nx;
-  double* Cf = sm;                          // [kTP][C] coefficients
-  double* Z = Cf + kTP * C;                 // [ncell][kTP]
-  double* Wt = Z + ncell * kTP;             // [kTP]
-  const int64_t L = m.mom_len_total;
+  const int h0 = max(0, r0 - 1);
+  const int ncell = (r1 - h0) * nx;
+  const int n_ent = (r1 - r0) * nx + (r1 - r0) * (nx + 1) + ((r1 == ny ? ny + 1 : r1) - r0) * nx;
+  double* Cf = sm;                  // [kTP][C]
+  double* Z = Cf + kTP * C;         // [ncell][kTP]
+  double* Wt = Z + ncell * kTP;     // [kTP]
   const int64_t* gd = a.gdof + S.gdof_off;
-  const int mode = m.mode;
-  for (int t = 0; t < a.n_tiles[s]; ++t) {
-    {
-      const int* tl = a.tiles + 3 * ((int64_t)s * a.max_tiles + t);
-      const int k = tl[0];
-      const ItemOff off = a.off[S.item0 + k];
-      const double* X = m.X + off.x;
-      const double* Tx = m.T + off.t;
-      const double* Ty = Tx + (int64_t)ny * (nx + 1);
-      const int q0 = tl[1];
-      int cntp = tl[2];
-      const int* pts = a.grp_pts + (int64_t)s * a.pts_ld + q0;
-      if (mode == 0) {
-        // only point 0 defines the shifts
-        int has0 = -1;
-        for (int q = 0; q < cntp; ++q) if (pts[q] == 0) has0 = q;
-        if (has0 < 0) continue;
-        pts += has0;
-        cntp = 1;
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < cntp * C; e += blockDim.x) {
-        const int q = e / C, i = e - q * C;
-        const int64_t l = pts[q];
-        Cf[e] = i < R ? a.lam[l * a.n_lambda + gd[i]] : 1.0;
-      }
-      for (int q = threadIdx.x; q < cntp; q += blockDim.x) Wt[q] = m.w[pts[q]];
-      __syncthreads();
-      for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
-        const double* xr = X + ((int64_t)h0 * nx + c) * C;
-        double acc[kTP];
+  double sh[kMaxE], acc1[kMaxE], acc2[kMaxE];
 #pragma unroll
-        for (int q = 0; q < kTP; ++q) acc[q] = 0.0;
-        for (int i = 0; i < C; ++i) {
-          const double xv = xr[i];
+  for (int q = 0; q < kMaxE; ++q) {
+    const int64_t el = threadIdx.x + (int64_t)q * kMomT;
+    sh[q] = (m.mode == 1 && el < n_ent) ? m.shift[darcy_entry(S, m, s, el, r0, r1)] : 0.0;
+    acc1[q] = 0.0;
+    acc2[q] = 0.0;
+  }
+  for (int t = ch; t < a.n_tiles[s]; t += m.n_chunks) {
+    const int* tl = a.tiles + 3 * ((int64_t)s * a.max_tiles + t);
+    const int k = tl[0];
+    const ItemOff off = a.off[S.item0 + k];
+    const double* X = m.X + off.x;
+    const double* Tx = m.T + off.t;
+    const double* Ty = Tx + (int64_t)ny * (nx + 1);
+    int cntp = tl[2];
+    const int* pts = a.grp_pts + (int64_t)s * a.pts_ld + tl[1];
+    if (m.mode == 0) {
+      int has0 = -1;
+      for (int q = 0; q < cntp; ++q)
+        if (pts[q] == 0) has0 = q;
+      if (has0 < 0) continue;
+      pts += has0;
+      cntp = 1;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < cntp * C; e += blockDim.x) {
+      const int q = e / C, i = e - q * C;
+      Cf[e] = i < R ? a.lam[(int64_t)pts[q] * a.n_lambda + gd[i]] : 1.0;
+    }
+    for (int q = threadIdx.x; q < kTP; q += blockDim.x) Wt[q] = q < cntp ? m.w[pts[q]] : 0.0;
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+      const double* xr = X + (int64_t)h0 * nx + c;
+      double z[kTP];
 #pragma unroll
-          for (int q = 0; q < kTP; ++q) acc[q] = fma(xv, Cf[q * C + i], acc[q]);
-        }
+      for (int q = 0; q < kTP; ++q) z[q] = 0.0;
+      for (int i = 0; i < C; ++i) {
+        const double xv = xr[(int64_t)i * nc];
 #pragma unroll
-        for (int q = 0; q < kTP; ++q) Z[c * kTP + q] = acc[q];
+        for (int q = 0; q < kTP; ++q) z[q] = fma(xv, Cf[q * C + i], z[q]);
       }
-      __syncthreads();
-      // pressures of the owned rows
-      for (int c = threadIdx.x; c < (r1 - r0) * nx; c += blockDim.x) {
-        const int zc = (r0 - h0) * nx + c;
-        const int64_t idx = m.off_p + m.cell_off[s] + (int64_t)r0 * nx + c;
-        for (int q = 0; q < cntp; ++q) mom_add(m.mom, L, idx, Z[zc * kTP + q], Wt[q], mode);
-      }
-      // x-face velocities of the owned rows
-      for (int f = threadIdx.x; f < (r1 - r0) * (nx + 1); f += blockDim.x) {
-        const int rr_ = r0 + f / (nx + 1), ix = f % (nx + 1);
-        const int zrow = (rr_ - h0) * nx;
-        const double t = Tx[(int64_t)rr_ * (nx + 1) + ix];
-        const int64_t idx = m.off_f + m.face_off[s] + (int64_t)rr_ * (nx + 1) + ix;
-        for (int q = 0; q < cntp; ++q) {
-          double v;
-          if (ix > 0 && ix < nx) {
-            v = t * (Z[(zrow + ix - 1) * kTP + q] - Z[(zrow + ix) * kTP + q]) / S.hy;
-          } else {
-            const int side = ix == 0 ? 3 : 1;
-            const int cell = ix == 0 ? 0 : nx - 1;
-            double gb = 0.0;
-            if (S.side_type[side] == SIDE_IFACE) {
-              const double* P = m.proj + S.proj_off[side] + (int64_t)rr_ * R;
-              for (int i = 0; i < R; ++i) gb += P[i] * Cf[q * C + i];
-            } else if (S.side_type[side] == SIDE_DIRICHLET) {
-              gb = S.side_val[side];
-            }
-            const double F = S.side_type[side] == SIDE_NOFLOW ? 0.0 : t * (Z[(zrow + cell) * kTP + q] - gb);
-            v = (ix == 0 ? -F : F) / S.hy;
-          }
-          mom_add(m.mom, L, idx, v, Wt[q], mode);
+#pragma unroll
+      for (int q = 0; q < kTP; ++q) Z[c * kTP + q] = z[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kMaxE; ++j) {
+      const int64_t el = threadIdx.x + (int64_t)j * kMomT;
+      if (el >= n_ent) break;
+      for (int q = 0; q < cntp; ++q) {
+        const double v = darcy_value(S, m, el, r0, r1, h0, Tx, Ty, Z, Cf, q, C);
+        if (m.mode == 0) {
+          sh[j] = v;
+        } else {
+          const double d = v - sh[j];
+          acc1[j] = fma(Wt[q], d, acc1[j]);
+          acc2[j] = fma(Wt[q] * d, d, acc2[j]);
         }
       }
-      // y-face velocities: faces r0..r1-1 (face j lies below row j), plus the top one
-      const int ftop = (r1 == ny) ? ny + 1 : r1;
-      for (int f = threadIdx.x; f < (ftop - r0) * nx; f += blockDim.x) {
-        const int j = r0 + f / nx, ix = f % nx;
-        const double t = Ty[(int64_t)j * nx + ix];
-        const int64_t idx = m.off_f + m.face_off[s] + (int64_t)ny * (nx + 1) + (int64_t)j * nx + ix;
-        for (int q = 0; q < cntp; ++q) {
-          double v;
-          if (j > 0 && j < ny) {
-            v = t * (Z[((j - 1 - h0) * nx + ix) * kTP + q] - Z[((j - h0) * nx + ix) * kTP + q]) / S.hx;
-          } else {
-            const int side = j == 0 ? 0 : 2;
-            const int zr = j == 0 ? 0 - h0 : ny - 1 - h0;
-            double gb = 0.0;
-            if (S.side_type[side] == SIDE_IFACE) {
-              const double* P = m.proj + S.proj_off[side] + (int64_t)ix * R;
-              for (int i = 0; i < R; ++i) gb += P[i] * Cf[q * C + i];
-            } else if (S.side_type[side] == SIDE_DIRICHLET) {
-              gb = S.side_val[side];
-            }
-            const double F = S.side_type[side] == SIDE_NOFLOW ? 0.0 : t * (Z[(zr * nx + ix) * kTP + q] - gb);
-            v = (j == 0 ? -F : F) / S.hx;
-          }
-          mom_add(m.mom, L, idx, v, Wt[q], mode);
-        }
-      }
-      if (mode == 0) break;
+    }
+    if (m.mode == 0) break;
+  }
+#pragma unroll
+  for (int j = 0; j < kMaxE; ++j) {
+    const int64_t el = threadIdx.x + (int64_t)j * kMomT;
+    if (el >= n_ent) break;
+    const int64_t ge = darcy_entry(S, m, s, el, r0, r1);
+    if (m.mode == 0) {
+      m.shift[ge] = sh[j];
+    } else {
+      m.part[((int64_t)ch * 2) * m.len_d + ge] = acc1[j];
+      m.part[((int64_t)ch * 2 + 1) * m.len_d + ge] = acc2[j];
     }
   }
 }
 
-// Stokes velocity and pressure moments: one thread per field entry, every
-// point in order: x = U_s [R_s lambda; 1].
-__global__ void __launch_bounds__(256) stokes_moments_kernel(MomArgs m, const double* U, int n_u, const double* Pm,
-                                                              int n_p, int64_t off_u, int64_t off_pp) {
-  extern __shared__ __align__(16) double sm[];
-  const IfaceArgs& a = m.ia;
+// S1 += sum over chunks of the partials, S2 likewise (fixed order).
+__global__ void reduce_partials(const double* part, int n_chunks, int64_t len, double* S1, double* S2) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+    double a1 = 0.0, a2 = 0.0;
+    for (int c = 0; c < n_chunks; ++c) {
+      a1 += part[(int64_t)(2 * c) * len + e];
+      a2 += part[(int64_t)(2 * c + 1) * len + e];
+    }
+    S1[e] += a1;
+    S2[e] += a2;
+  }
+}
+
+// Stokes fields: x_l = U [R_s lambda_l; 1] for every entry, so with
+// d_l = c_l - c_0 (c_0: the coefficients of point 0 of the first batch) the
+// shifted sums are U m and diag(U M U^T) with m = sum w d, M = sum w d d^T.
+// One CTA per row a of M; threads over columns; points in order.
+__global__ void stokes_cov_kernel(const IfaceArgs a, const double* w, int first, double* c0, double* mvec,
+                                  double* Mmat) {
   const int Rs = a.Rs, Cs = Rs + 1;
-  const int64_t L = m.mom_len_total;
-  double* Cf = sm;            // [kTP][Cs]
-  double* Wt = Cf + kTP * Cs;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = e < n_u + n_p;
-  const double* row = valid ? (e < n_u ? U + (int64_t)e * Cs : Pm + (int64_t)(e - n_u) * Cs) : U;
-  const int64_t idx = e < n_u ? off_u + e : off_pp + (e - n_u);
-  const int64_t npts = m.mode == 0 ? 1 : a.n_pts;
-  for (int64_t q0 = 0; q0 < npts; q0 += kTP) {
-    const int cntp = (int)(npts - q0 < kTP ? npts - q0 : kTP);
-    __syncthreads();
-    for (int t = threadIdx.x; t < cntp * Cs; t += blockDim.x) {
-      const int q = t / Cs, i = t - q * Cs;
-      Cf[t] = i < Rs ? a.lam[(q0 + q) * a.n_lambda + a.sgdof[i]] : 1.0;
+  const int ra = blockIdx.x;
+  if (ra >= Cs) return;
+  __shared__ double c0s[kMaxCols];
+  for (int i = threadIdx.x; i < Cs; i += blockDim.x) {
+    const double v = i < Rs ? a.lam[a.sgdof[i]] : 1.0;   // point 0
+    if (first) c0s[i] = v;
+    else c0s[i] = c0[i];
+  }
+  __syncthreads();
+  if (first && ra == 0)
+    for (int i = threadIdx.x; i < Cs; i += blockDim.x) c0[i] = c0s[i];
+  for (int b = threadIdx.x; b < Cs; b += blockDim.x) {
+    double acc = 0.0, acc1 = 0.0;
+    for (int64_t l = 0; l < a.n_pts; ++l) {
+      const double* ll = a.lam + l * a.n_lambda;
+      const double da = (ra < Rs ? ll[a.sgdof[ra]] : 1.0) - c0s[ra];
+      const double db = (b < Rs ? ll[a.sgdof[b]] : 1.0) - c0s[b];
+      acc = fma(w[l] * da, db, acc);
+      if (b == 0) acc1 = fma(w[l], da, acc1);
     }
-    for (int q = threadIdx.x; q < cntp; q += blockDim.x) Wt[q] = m.w[q0 + q];
-    __syncthreads();
-    if (!valid) continue;
-    double acc[kTP];
-#pragma unroll
-    for (int q = 0; q < kTP; ++q) acc[q] = 0.0;
-    for (int i = 0; i < Cs; ++i) {
-      const double xv = row[i];
-#pragma unroll
-      for (int q = 0; q < kTP; ++q) acc[q] = fma(xv, Cf[q * Cs + i], acc[q]);
-    }
-    for (int q = 0; q < cntp; ++q) mom_add(m.mom, L, idx, acc[q], Wt[q], m.mode);
+    Mmat[(int64_t)ra * Cs + b] += acc;
+    if (b == 0) mvec[ra] += acc1;
   }
 }
 
@@ -492,10 +524,37 @@ __global__ void weight_sum(const double* w, int64_t n, double* out) {
 }
 
 // mean = shift W + S1, var = S2 - 2 (mean - shift) S1 + (mean - shift)^2 W
-__global__ void finalize_moments(const double* mom, int64_t L, int64_t off, int64_t n, const double* W,
-                                 double* mean, double* var) {
+__global__ void finalize_darcy(const double* shift, const double* S1, const double* S2, int64_t off, int64_t n,
+                               const double* W, double* mean, double* var) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const double sh = mom[off + e], s1 = mom[L + off + e], s2 = mom[2 * L + off + e], w = W[0];
+    const double sh = shift[off + e], s1 = S1[off + e], s2 = S2[off + e], w = W[0];
+    const double mu = sh * w + s1;
+    const double dm = mu - sh;
+    mean[e] = mu;
+    var[e] = s2 - 2.0 * dm * s1 + dm * dm * w;
+  }
+}
+
+// Stokes: shift = U_e c0, S1 = U_e m, S2 = U_e M U_e^T; one warp per entry.
+__global__ void finalize_stokes(const double* U, int64_t n, int Cs, const double* c0, const double* mvec,
+                                const double* Mmat, const double* W, double* mean, double* var) {
+  const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (e >= n) return;
+  const double* u = U + e * Cs;
+  double sh = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int i = lane; i < Cs; i += 32) {
+    sh = fma(u[i], c0[i], sh);
+    s1 = fma(u[i], mvec[i], s1);
+    double row = 0.0;
+    for (int j = 0; j < Cs; ++j) row = fma(Mmat[(int64_t)i * Cs + j], u[j], row);
+    s2 = fma(u[i], row, s2);
+  }
+  sh = warp_sum(sh);
+  s1 = warp_sum(s1);
+  s2 = warp_sum(s2);
+  if (lane == 0) {
+    const double w = W[0];
     const double mu = sh * w + s1;
     const double dm = mu - sh;
     mean[e] = mu;
@@ -573,7 +632,7 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   const size_t smv = sizeof(double) * ((size_t)maxR * maxR + (size_t)kTP * maxR);
   CK(cudaFuncSetAttribute(matvec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv));
   dim3 mgrid(c->max_tiles, nu);
-  const int chunk = 8;
+  const int chunk = c->opt_cg_chunk;
   int it = 0;
   for (; it < max_it;) {
     for (int q = 0; q < chunk && it < max_it; ++q, ++it) {
@@ -608,29 +667,35 @@ sfb_status moments_accumulate_device(sfb_ctx* c, int64_t n_pts) {
 #define CK(x) do { e = (x); if (e != cudaSuccess) { c->err = std::string("moments: ") + cudaGetErrorString(e); return SFB_ERR_CUDA; } } while (0)
   MomArgs m;
   m.ia = make_args(c, n_pts);
-  m.X = d.X; m.T = d.T; m.proj = d.proj; m.w = d.w; m.mom = d.mom;
-  m.off_p = c->mom_off[0]; m.off_f = c->mom_off[1]; m.len_p = c->mom_len[0]; m.len_f = c->mom_len[1];
-  m.mom_len_total = c->mom_off[3] + c->mom_len[3];
-  m.rt = 4;
+  m.X = d.X; m.T = d.T; m.proj = d.proj; m.w = d.w;
+  m.len_d = c->mom_len[0] + c->mom_len[1];
+  m.off_f = c->mom_len[0];
+  m.shift = d.mom; m.part = d.mom_part;
   m.cell_off = d.cell_off; m.face_off = d.face_off;
   int max_ny = 0, max_nx = 0, maxC = 0;
   for (const HostSub& S : c->subs) {
     max_ny = std::max(max_ny, S.ny); max_nx = std::max(max_nx, S.nx);
     maxC = std::max(maxC, (int)S.dofs.size() + 1);
   }
+  // rows per CTA: about 512 cells, so the owned entries fit kMaxE per thread
+  m.rt = std::max(1, std::min(max_ny, 512 / max_nx));
+  m.n_chunks = c->mom_chunks;
   const size_t smd = sizeof(double) * ((size_t)kTP * maxC + (size_t)(m.rt + 1) * max_nx * kTP + kTP);
   CK(cudaFuncSetAttribute(darcy_moments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd));
-  const int Cs = (int)c->stokes.dofs.size() + 1;
-  const size_t sms = sizeof(double) * ((size_t)kTP * Cs + kTP);
-  const int n_se = c->stokes.n_u + c->stokes.n_p;
-  dim3 dgrid((max_ny + m.rt - 1) / m.rt, ns);
-  for (int mode = c->mom_shift_set ? 1 : 0; mode <= 1; ++mode) {
-    m.mode = mode;
-    darcy_moments_kernel<<<dgrid, 256, smd, st>>>(m);
-    stokes_moments_kernel<<<(n_se + 255) / 256, 256, sms, st>>>(m, d.s_U, c->stokes.n_u, d.s_P, c->stokes.n_p,
-                                                               c->mom_off[2], c->mom_off[3]);
+  const int row_tiles = (max_ny + m.rt - 1) / m.rt;
+  const int first = c->mom_shift_set ? 0 : 1;
+  if (first) {
+    m.mode = 0;
+    darcy_moments_kernel<<<dim3(row_tiles, ns, 1), kMomT, smd, st>>>(m);
     CK(cudaGetLastError());
   }
+  m.mode = 1;
+  darcy_moments_kernel<<<dim3(row_tiles, ns, m.n_chunks), kMomT, smd, st>>>(m);
+  CK(cudaGetLastError());
+  reduce_partials<<<256, 256, 0, st>>>(d.mom_part, m.n_chunks, m.len_d, d.mom + m.len_d, d.mom + 2 * m.len_d);
+  const int Cs = (int)c->stokes.dofs.size() + 1;
+  stokes_cov_kernel<<<Cs, 128, 0, st>>>(m.ia, d.w, first, d.st_c0, d.st_m, d.st_M);
+  CK(cudaGetLastError());
   c->mom_shift_set = true;
   weight_sum<<<1, 32, 0, st>>>(d.w, n_pts, d.mom_w);
   CK(cudaGetLastError());
@@ -639,9 +704,19 @@ sfb_status moments_accumulate_device(sfb_ctx* c, int64_t n_pts) {
 }
 
 sfb_status moments_finalize_device(sfb_ctx* c, int field, double* mean_d, double* var_d) {
-  const int64_t L = c->mom_off[3] + c->mom_len[3];
-  finalize_moments<<<256, 256, 0, c->stream>>>(c->dev.mom, L, c->mom_off[field], c->mom_len[field], c->dev.mom_w,
-                                               mean_d, var_d);
+  Dev& d = c->dev;
+  const int64_t len_d = c->mom_len[0] + c->mom_len[1];
+  if (field <= 1) {
+    const int64_t off = field == 0 ? 0 : c->mom_len[0];
+    finalize_darcy<<<256, 256, 0, c->stream>>>(d.mom, d.mom + len_d, d.mom + 2 * len_d, off, c->mom_len[field],
+                                               d.mom_w, mean_d, var_d);
+  } else {
+    const int Cs = (int)c->stokes.dofs.size() + 1;
+    const double* U = field == 2 ? d.s_U : d.s_P;
+    const int64_t n = c->mom_len[field];
+    finalize_stokes<<<(int)((n * 32 + 255) / 256), 256, 0, c->stream>>>(U, n, Cs, d.st_c0, d.st_m, d.st_M,
+                                                                          d.mom_w, mean_d, var_d);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return SFB_ERR_CUDA; }
   return SFB_OK;

@@ -61,6 +61,9 @@ struct Dev {
   void* Z = nullptr;
   double* phi = nullptr;
   double* D = nullptr;
+  void* S = nullptr;
+  double* errest = nullptr;
+  long long* cycles = nullptr;
   int* status = nullptr;
   double* resid = nullptr;
   double* corr1 = nullptr;
@@ -109,8 +112,12 @@ struct Dev {
   int64_t* face_off = nullptr;// per subdomain first face in the Darcy flux field
   double* fin = nullptr;      // [2][max field length] finalised mean / variance
   // moments
-  double* mom = nullptr;      // per field entry: shift, S1, S2
+  double* mom = nullptr;      // Darcy entries: shift, S1, S2
   double* mom_w = nullptr;
+  double* mom_part = nullptr; // [chunks][2][Darcy entries] partial sums of a batch
+  double* st_c0 = nullptr;    // Stokes: coefficients of the shift point
+  double* st_m = nullptr;     // Stokes: sum w (c - c0)
+  double* st_M = nullptr;     // Stokes: sum w (c - c0)(c - c0)^T
 };
 
 }  // namespace sfb
@@ -150,4 +157,9 @@ struct sfb_ctx {
   int64_t mom_len[4] = {0, 0, 0, 0};
   int64_t mom_off[4] = {0, 0, 0, 0};
   bool mom_shift_set = false;
+  int mom_chunks = 1;
+  // options (sfb_set_option)
+  double opt_refine_tol = 1e-10;
+  int opt_refine_max = 8;
+  int opt_cg_chunk = 8;
 };

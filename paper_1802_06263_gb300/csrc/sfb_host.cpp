@@ -145,7 +145,8 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   Dev& d = c->dev;
   const int ns = (int)c->subs.size();
   const size_t gsz = prec == SFB_FP64 ? sizeof(double) : sizeof(float);
-  int64_t n_items = 0, nX = 0, nT = 0, nG = 0, nPhi = 0, nD = 0, nproj = 0, ninfo = 0, nkl = 0, nyl = 0, ngd = 0;
+  int64_t n_items = 0, nX = 0, nZ = 0, nT = 0, nG = 0, nPhi = 0, nD = 0, nproj = 0, ninfo = 0, nkl = 0, nyl = 0,
+          ngd = 0;
   int64_t n_loc_tot = 0;
   c->offs.clear();
   for (int s = 0; s < ns; ++s) {
@@ -154,11 +155,14 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
     const int nl = c->n_local.empty() ? 0 : c->n_local[s];
     for (int k = 0; k < nl; ++k) {
       ItemOff o;
-      o.x = nX; o.z = nX; nX += (int64_t)nc * C;
+      const int64_t npad_ = (S.nx + 7) & ~7, cpad_ = (C + 3) & ~3;
+      o.x = nX; nX += (int64_t)nc * C;
+      o.z = nZ; nZ += (int64_t)S.ny * npad_ * cpad_;   // row blocks in the shared-memory layout
       o.t = nT; nT += (int64_t)S.ny * (S.nx + 1) + (int64_t)(S.ny + 1) * S.nx;
-      o.g = nG; nG += (int64_t)S.ny * S.nx * S.nx;
+      const int64_t npad = (S.nx + 7) & ~7;  // identity-padded block size of the factor
+      o.g = nG; nG += (int64_t)S.ny * npad * npad;
       o.phi = nPhi; nPhi += (int64_t)R * R + R;
-      o.diag = nD; nD += nc;
+      o.diag = nD; o.sc = nD; nD += nc;
       c->offs.push_back(o);
     }
     n_items += nl;
@@ -182,12 +186,15 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   d.X = cv.take<double>(nX);
   d.T = cv.take<double>(nT);
   d.G = cv.take<char>(nG * gsz);
-  d.Z = cv.take<char>(nX * gsz);
+  d.Z = cv.take<char>(nZ * gsz);
   d.phi = cv.take<double>(nPhi);
   d.D = cv.take<double>(nD);
+  d.S = cv.take<char>(nD * gsz);
   d.status = cv.take<int>(n_items);
   d.resid = cv.take<double>(n_items);
   d.corr1 = cv.take<double>(n_items);
+  d.errest = cv.take<double>(n_items);
+  d.cycles = cv.take<long long>(4 * n_items);
   d.nref = cv.take<int>(n_items);
   // Stokes
   const StokesHost& St = c->stokes;
@@ -260,8 +267,22 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   c->mom_len[0] = np_; c->mom_len[1] = nf_; c->mom_len[2] = St.n_u; c->mom_len[3] = St.n_p;
   int64_t mo = 0;
   for (int f = 0; f < 4; ++f) { c->mom_off[f] = mo; mo += c->mom_len[f]; }
-  d.mom = cv.take<double>((size_t)3 * mo);
+  // Darcy accumulators and per-chunk partials; Stokes coefficient moments
+  const int64_t len_d = np_ + nf_;
+  int row_tiles = 0;
+  {
+    int max_ny = 1, max_nx = 1;
+    for (const HostSub& S : c->subs) { max_ny = std::max(max_ny, S.ny); max_nx = std::max(max_nx, S.nx); }
+    const int rt = std::max(1, std::min(max_ny, 512 / max_nx));
+    row_tiles = ns * ((max_ny + rt - 1) / rt);
+  }
+  c->mom_chunks = std::max(1, std::min(16, (4 * 152 + row_tiles - 1) / std::max(row_tiles, 1)));
+  d.mom = cv.take<double>((size_t)3 * len_d);
   d.mom_w = cv.take<double>(2);
+  d.mom_part = cv.take<double>((size_t)2 * c->mom_chunks * len_d);
+  d.st_c0 = cv.take<double>(Rs + 1);
+  d.st_m = cv.take<double>(Rs + 1);
+  d.st_M = cv.take<double>((size_t)(Rs + 1) * (Rs + 1));
   d.fin = cv.take<double>((size_t)2 * std::max(std::max(np_, nf_), (int64_t)std::max(St.n_u, St.n_p)));
   return cv.used + 256;
 }
@@ -501,10 +522,7 @@ sfb_status sfb_set_workspace(sfb_ctx* c, void* ptr, size_t bytes) {
   Carver cv;
   cv.base = c->ws;
   layout(c, cv, c->ws_prec, c->ws_pts);
-  const int64_t L = c->mom_off[3] + c->mom_len[3];
-  SFB_CUDA(cudaMemsetAsync(c->dev.mom, 0, sizeof(double) * 3 * L, c->stream), "memset");
-  SFB_CUDA(cudaMemsetAsync(c->dev.mom_w, 0, sizeof(double) * 2, c->stream), "memset");
-  return SFB_OK;
+  return sfb_moments_reset(c);
 }
 
 
@@ -629,14 +647,16 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   SFB_CUDA(cudaMemsetAsync(d.status, 0, sizeof(int) * n, st), "memset");
   SFB_CUDA(cudaMemsetAsync(d.resid, 0, sizeof(double) * n, st), "memset");
   SFB_CUDA(cudaMemsetAsync(d.corr1, 0, sizeof(double) * n, st), "memset");
+  SFB_CUDA(cudaMemsetAsync(d.errest, 0, sizeof(double) * n, st), "memset");
   SFB_CUDA(cudaMemsetAsync(d.nref, 0, sizeof(int) * n, st), "memset");
   BasisArgs a;
   a.subs = d.subs; a.proj = d.proj; a.dofinfo = d.dofinfo; a.kl = d.kl; a.yloc = d.yloc;
   a.item_sub = d.item_sub; a.item_k = d.item_k; a.off = d.off; a.n_items = n;
-  a.X = d.X; a.T = d.T; a.G = d.G; a.Z = d.Z; a.phi = d.phi; a.D = d.D;
-  a.status = d.status; a.resid = d.resid; a.corr1 = d.corr1; a.nref = d.nref;
-  a.max_refine = 10;
-  a.refine_tol = 1e-13;
+  a.X = d.X; a.T = d.T; a.G = d.G; a.Z = d.Z; a.S = d.S; a.phi = d.phi; a.D = d.D;
+  a.status = d.status; a.resid = d.resid; a.corr1 = d.corr1; a.errest = d.errest; a.nref = d.nref;
+  a.cycles = d.cycles;
+  a.max_refine = c->opt_refine_max;
+  a.refine_tol = c->opt_refine_tol;
   cudaEvent_t e0, e1;
   SFB_CUDA(cudaEventCreate(&e0), "event");
   SFB_CUDA(cudaEventCreate(&e1), "event");
@@ -649,11 +669,14 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_fail(c, e, "flux epilogue"); }
   SFB_CUDA(cudaEventRecord(e1, st), "event");
   std::vector<int> status(n), nref(n);
-  std::vector<double> resid(n), corr(n);
+  std::vector<double> resid(n), corr(n), est(n);
+  std::vector<long long> cyc(4 * (size_t)n);
   SFB_CUDA(cudaMemcpyAsync(status.data(), d.status, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "stats");
   SFB_CUDA(cudaMemcpyAsync(nref.data(), d.nref, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "stats");
   SFB_CUDA(cudaMemcpyAsync(resid.data(), d.resid, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "stats");
   SFB_CUDA(cudaMemcpyAsync(corr.data(), d.corr1, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "stats");
+  SFB_CUDA(cudaMemcpyAsync(est.data(), d.errest, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "stats");
+  SFB_CUDA(cudaMemcpyAsync(cyc.data(), d.cycles, sizeof(long long) * 4 * n, cudaMemcpyDeviceToHost, st), "stats");
   SFB_CUDA(cudaStreamSynchronize(st), "basis build");
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
@@ -670,12 +693,19 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
     stats->n_not_converged = n_nc;
     stats->max_rel_residual = n ? *std::max_element(resid.begin(), resid.end()) : 0.0;
     stats->max_first_correction = n ? *std::max_element(corr.begin(), corr.end()) : 0.0;
+    stats->max_error_estimate = n ? *std::max_element(est.begin(), est.end()) : 0.0;
+    for (int q = 0; q < 4; ++q) {
+      double acc = 0.0;
+      for (int i = 0; i < n; ++i) acc += (double)cyc[4 * (size_t)i + q];
+      stats->phase_cycles[q] = n ? acc / n : 0.0;
+    }
     stats->ms = ms;
   }
   c->basis_done = true;
   c->basis_prec = prec;
   if (any & ST_NONFINITE) return fail(c, SFB_ERR_NONFINITE, "non-finite permeability or solution");
   if (any & ST_NOT_SPD) return fail(c, SFB_ERR_NOT_SPD, "non-positive pivot in a block factorization");
+  if (any & ST_TIMEOUT) return fail(c, SFB_ERR_TIMEOUT, "a bulk copy did not complete within the wait limit");
   if (any & ST_NOT_CONVERGED) return fail(c, SFB_ERR_NOT_CONVERGED, "iterative refinement stopped above tolerance");
   return SFB_OK;
 }
@@ -703,7 +733,7 @@ sfb_status sfb_get_basis(sfb_ctx* c, int32_t sub, int32_t k, double* phi, double
   if (phi) SFB_CUDA(cudaMemcpyAsync(phi, c->dev.phi + o.phi, sizeof(double) * R * R, cudaMemcpyDefault, st), "copy");
   if (g) SFB_CUDA(cudaMemcpyAsync(g, c->dev.phi + o.phi + (int64_t)R * R, sizeof(double) * R, cudaMemcpyDefault, st), "copy");
   if (x) SFB_CUDA(cudaMemcpyAsync(x, c->dev.X + o.x, sizeof(double) * (size_t)S.nx * S.ny * (R + 1),
-                                  cudaMemcpyDefault, st), "copy");
+                                  cudaMemcpyDefault, st), "copy");  // [R+1][n_cells]
   SFB_CUDA(cudaStreamSynchronize(st), "copy");
   return SFB_OK;
 }
@@ -749,12 +779,34 @@ sfb_status sfb_moments(sfb_ctx* c, int32_t field, double* mean_out, double* var_
   return SFB_OK;
 }
 
+sfb_status sfb_set_option(sfb_ctx* c, const char* name, double value) {
+  if (!c || !name) return SFB_ERR_ARG;
+  const std::string n(name);
+  if (n == "refine_tol") {
+    if (!(value > 0 && value < 1)) return fail(c, SFB_ERR_ARG, "refine_tol must lie in (0, 1)");
+    c->opt_refine_tol = value;
+  } else if (n == "refine_max") {
+    if (!(value >= 1 && value <= 50)) return fail(c, SFB_ERR_ARG, "refine_max must lie in [1, 50]");
+    c->opt_refine_max = (int)value;
+  } else if (n == "cg_check_every") {
+    if (!(value >= 1 && value <= 1000)) return fail(c, SFB_ERR_ARG, "cg_check_every must lie in [1, 1000]");
+    c->opt_cg_chunk = (int)value;
+  } else {
+    return fail(c, SFB_ERR_ARG, "unknown option " + n);
+  }
+  return SFB_OK;
+}
+
 sfb_status sfb_moments_reset(sfb_ctx* c) {
   if (!c) return SFB_ERR_ARG;
   if (!c->ws) return fail(c, SFB_ERR_WORKSPACE, "no workspace set");
-  const int64_t L = c->mom_off[3] + c->mom_len[3];
-  SFB_CUDA(cudaMemsetAsync(c->dev.mom, 0, sizeof(double) * 3 * L, c->stream), "memset");
+  const int64_t len_d = c->mom_len[0] + c->mom_len[1];
+  const int64_t Cs = (int64_t)c->stokes.dofs.size() + 1;
+  SFB_CUDA(cudaMemsetAsync(c->dev.mom, 0, sizeof(double) * 3 * len_d, c->stream), "memset");
   SFB_CUDA(cudaMemsetAsync(c->dev.mom_w, 0, sizeof(double) * 2, c->stream), "memset");
+  SFB_CUDA(cudaMemsetAsync(c->dev.st_c0, 0, sizeof(double) * Cs, c->stream), "memset");
+  SFB_CUDA(cudaMemsetAsync(c->dev.st_m, 0, sizeof(double) * Cs, c->stream), "memset");
+  SFB_CUDA(cudaMemsetAsync(c->dev.st_M, 0, sizeof(double) * Cs * Cs, c->stream), "memset");
   c->mom_shift_set = false;
   c->n_solved = 0;
   return SFB_OK;

@@ -19,6 +19,7 @@ enum : int {
   ST_NOT_SPD = 2,
   ST_NOT_CONVERGED = 4,
   ST_BAD_INDEX = 8,
+  ST_TIMEOUT = 16,
 };
 
 // One Darcy subdomain. Side order: 0 bottom, 1 right, 2 top, 3 left; the
@@ -38,12 +39,13 @@ struct SubDev {
 
 // Per-item storage offsets (elements) into the basis store arrays.
 struct ItemOff {
-  int64_t x;    // X: [n_cells][R+1] FP64 pressure responses
+  int64_t x;    // X: [R+1][n_cells] FP64 pressure responses (column-major)
   int64_t t;    // T: x-faces [ny][nx+1] then y-faces [ny+1][nx] FP64 transmissibilities
   int64_t g;    // G: [ny][nx][nx] inverse Schur blocks (FP64 or FP32)
-  int64_t z;    // Z: [n_cells][R+1] solve scratch (factor precision)
+  int64_t z;    // Z: [R+1][n_cells] solve scratch (factor precision)
   int64_t phi;  // Phi: [R][R] then g: [R]
-  int64_t diag; // D: [n_cells] FP64 diagonal of A (mixed form scaling)
+  int64_t diag; // D: [n_cells] FP64 diagonal of A
+  int64_t sc;   // S: [n_cells] diag(A)^{-1/2} in the factor precision
 };
 
 struct BasisArgs {
@@ -59,13 +61,16 @@ struct BasisArgs {
   double* X;
   double* T;
   void* G;
-  void* Z;                 // [n_cells][R+1] solve scratch in the factor precision
+  void* Z;                 // [R+1][n_cells] solve scratch in the factor precision
+  void* S;                 // [n_cells] diagonal scaling in the factor precision
   double* phi;
   double* D;
   int* status;             // per item
-  double* resid;           // per item: final relative residual
+  double* resid;           // per item: last relative residual ||B - A X|| / ||B||
   double* corr1;           // per item: relative size of the first correction
+  double* errest;          // per item: estimated relative error of the final X
   int* nref;               // per item: refinement steps taken
+  long long* cycles;       // per item: SM cycles in [setup, factor, forward, backward]
   int max_refine;
   double refine_tol;
 };
