@@ -152,6 +152,7 @@ def run_ours(args):
         basis = np.mean([e[0].elapsed_time(e[1]) for _, e in phases])
         solve = np.mean([e[1].elapsed_time(e[2]) for _, e in phases])
         kern = np.mean([p[0]["ms"] for p in phases])
+        timed.solve_phases = s.solve_timings()
         if world > 1:
             tt = torch.tensor([total], device="cuda")
             torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
@@ -161,6 +162,7 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     t_mixed, b_mixed, s_mixed, k_mixed, st_mixed = timed(sfb.MIXED, args.steps)
+    mixed_phases = dict(timed.solve_phases)
     mean_mixed = {f: s.moments(f) for f in sfb.FIELDS}
     iters = it_d.cpu().numpy()
     t_fp64, b_fp64, s_fp64, k_fp64, st_fp64 = timed(sfb.FP64, args.steps)
@@ -224,7 +226,8 @@ def run_ours(args):
                        "max_refine_steps": st_mixed["max_refine_steps"],
                        "unrefined_fp32_rel_error": st_mixed["max_first_correction"],
                        "final_rel_residual": st_mixed["max_rel_residual"],
-                       "cg_iters_min_max": [int(iters.min()), int(iters.max())]},
+                       "cg_iters_min_max": [int(iters.min()), int(iters.max())],
+                       "solve_phases_ms": mixed_phases},
         "mixed_vs_fp64_rel": agree,
         "speedup_mixed_vs_fp64": t_fp64 / t_mixed,
         "e2e": {"value": world * n_pts / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,

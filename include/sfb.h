@@ -195,6 +195,13 @@ sfb_status sfb_interface_solve_batch(sfb_ctx* ctx, const double* y, const double
 sfb_status sfb_moments(sfb_ctx* ctx, int32_t field, double* mean_out, double* var_out);
 sfb_status sfb_moments_reset(sfb_ctx* ctx);
 
+/* Device time (ms, CUDA events) of the phases of the last
+ * sfb_interface_solve_batch: [0] global-to-local index conversion and
+ * grouping, [1] the CG iterations, [2] status bookkeeping, [3] Darcy
+ * recovery and moments, [4] Stokes moments; cg_iterations (nullable) gets the
+ * number of lockstep CG iterations run. Synchronises the stream. */
+sfb_status sfb_solve_timings(sfb_ctx* ctx, double* ms_out, int32_t* cg_iterations);
+
 /* Tuning knobs (no counterpart in the paper):
  *   "refine_tol"     mixed form: stop refining when the predicted relative
  *                    error of X is below this (default 1e-10);

@@ -82,6 +82,7 @@ _SIGS = {
     "sfb_moments": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "sfb_moments_reset": (ctypes.c_int, [ctypes.c_void_p]),
     "sfb_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_double]),
+    "sfb_solve_timings": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _i32p]),
 }
 
 _lib = None
@@ -306,6 +307,13 @@ class Solver:
         mean, var = np.zeros(n), np.zeros(n)
         self._check(self.lib.sfb_moments(self.h, FIELDS[field], mean.ctypes.data, var.ctypes.data))
         return mean, var
+
+    def solve_timings(self):
+        ms = np.zeros(5)
+        it = ctypes.c_int32()
+        self._check(self.lib.sfb_solve_timings(self.h, ms.ctypes.data, ctypes.byref(it)))
+        return {"index_ms": ms[0], "cg_ms": ms[1], "status_ms": ms[2], "darcy_moments_ms": ms[3],
+                "stokes_moments_ms": ms[4], "cg_iterations": it.value}
 
     def set_option(self, name, value):
         self._check(self.lib.sfb_set_option(self.h, name.encode(), float(value)))

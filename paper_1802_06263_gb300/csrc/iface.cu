@@ -23,7 +23,8 @@ namespace sfb {
 
 namespace {
 
-constexpr int kTP = 8;  // points per matvec / moments tile
+constexpr int kTP = 8;   // points per moments sub-tile
+constexpr int kTG = 32;  // points per group tile (CG products, moments tiles)
 
 __host__ __device__ inline uint64_t mix_key(uint64_t h, int64_t v) {
   h ^= (uint64_t)v;
@@ -109,10 +110,10 @@ __global__ void __launch_bounds__(256) group_kernel(const int* kmap, int64_t n_p
     int nt_ = 0;
     for (int k = 0; k < nl; ++k) {
       const int c0 = start[k], c1 = cnt[k];  // cnt now holds the end of group k
-      for (int q = c0; q < c1 && nt_ < max_tiles; q += kTP) {
+      for (int q = c0; q < c1 && nt_ < max_tiles; q += kTG) {
         tiles[3 * ((int64_t)s * max_tiles + nt_) + 0] = k;
         tiles[3 * ((int64_t)s * max_tiles + nt_) + 1] = q;
-        tiles[3 * ((int64_t)s * max_tiles + nt_) + 2] = min(kTP, c1 - q);
+        tiles[3 * ((int64_t)s * max_tiles + nt_) + 2] = min(kTG, c1 - q);
         ++nt_;
       }
     }
@@ -126,11 +127,11 @@ __global__ void stokes_group_kernel(int64_t n_pts, int unit, int* grp_pts, int64
   int* pts = grp_pts + (int64_t)unit * pts_ld;
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n_pts; l += (int64_t)gridDim.x * blockDim.x)
     pts[l] = (int)l;
-  const int nt_ = (int)((n_pts + kTP - 1) / kTP);
+  const int nt_ = (int)((n_pts + kTG - 1) / kTG);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt_ && t < max_tiles; t += gridDim.x * blockDim.x) {
     tiles[3 * ((int64_t)unit * max_tiles + t) + 0] = 0;
-    tiles[3 * ((int64_t)unit * max_tiles + t) + 1] = t * kTP;
-    tiles[3 * ((int64_t)unit * max_tiles + t) + 2] = (int)(n_pts - (int64_t)t * kTP < kTP ? n_pts - (int64_t)t * kTP : kTP);
+    tiles[3 * ((int64_t)unit * max_tiles + t) + 1] = t * kTG;
+    tiles[3 * ((int64_t)unit * max_tiles + t) + 2] = (int)(n_pts - (int64_t)t * kTG < kTG ? n_pts - (int64_t)t * kTG : kTG);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) n_tiles[unit] = min(nt_, max_tiles);
 }
@@ -207,36 +208,96 @@ __global__ void init_kernel(IfaceArgs a) {
   }
 }
 
-// Y[l][ybase_u + :] = Phi_u^k (R_u p_l) for the points of one tile.
-__global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a) {
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Y[l][ybase_u + :] = Phi_u^k (R_u p_l) for the (active) points of one tile of
+// up to kTG points that share the stored basis Phi_u^k. Phi arrives in shared
+// memory by one bulk copy (mbarrier completion, bounded wait); the product is
+// computed in FP64 with 2 x 4 register tiles (two rows of Phi, four points).
+__global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, int* err) {
   extern __shared__ __align__(16) double smv[];
+  __shared__ __align__(8) uint64_t bar;
   const int u = blockIdx.y;
   const int t = blockIdx.x;
   if (t >= a.n_tiles[u]) return;
   const int* tl = a.tiles + 3 * ((int64_t)u * a.max_tiles + t);
   const int k = tl[0], q0 = tl[1], cntp = tl[2];
+  const int* pts = a.grp_pts + (int64_t)u * a.pts_ld + q0;
+  const int act = threadIdx.x < cntp ? (a.pstat[pts[threadIdx.x]] == 0) : 0;
+  if (!__syncthreads_or(act)) return;  // every point of the tile has converged
   int R;
   const double* ph = unit_phi(a, u, k, R);
   const int64_t* gd = u == a.ns ? a.sgdof : a.gdof + a.subs[u].gdof_off;
-  double* Ph = smv;             // [R][R]
-  double* Pv = smv + R * R;     // [kTP][R]
-  const int* pts = a.grp_pts + (int64_t)u * a.pts_ld + q0;
-  for (int e = threadIdx.x; e < R * R; e += blockDim.x) Ph[e] = ph[e];
-  for (int e = threadIdx.x; e < cntp * R; e += blockDim.x) {
-    const int q = e / R, i = e - q * R;
-    const int64_t l = pts[q];
-    Pv[e] = a.pstat[l] == 0 ? a.p[l * a.n_lambda + gd[i]] : 0.0;
+  const int rr2 = (R * R + 1) & ~1;
+  double* Ph = smv;            // [R][R]
+  double* Pv = smv + rr2;      // [R][kTG + 1]
+  const uint32_t bytes = (uint32_t)((R * R * 8 + 15) & ~15);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(Ph)),
+                 "l"(ph), "r"(bytes), "r"(smem_u32(&bar))
+                 : "memory");
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < cntp * R; e += blockDim.x) {
+  __syncthreads();  // the initialised barrier is visible to every thread
+  for (int e = threadIdx.x; e < kTG * R; e += blockDim.x) {
     const int q = e / R, i = e - q * R;
-    const int64_t l = pts[q];
-    if (a.pstat[l] != 0) continue;
-    const double* row = Ph + i * R;
-    const double* v = Pv + q * R;
-    double acc = 0.0;
-    for (int j = 0; j < R; ++j) acc = fma(row[j], v[j], acc);
-    a.Y[l * a.NY + a.ybase[u] + i] = acc;
+    double v = 0.0;
+    if (q < cntp) {
+      const int64_t l = pts[q];
+      if (a.pstat[l] == 0) v = a.p[l * a.n_lambda + gd[i]];
+    }
+    Pv[i * (kTG + 1) + q] = v;
+  }
+  uint32_t ok = 0;
+  for (int it = 0; it < (1 << 22) && !ok; ++it)
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(smem_u32(&bar))
+                 : "memory");
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) {
+      atomicOr(err, 1);
+      // a bounded second chance for the copy in flight before the CTA exits
+      for (int it = 0; it < (1 << 22) && !ok; ++it)
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok)
+                     : "r"(smem_u32(&bar))
+                     : "memory");
+    }
+    __syncthreads();
+    return;
+  }
+  const int nrp = (R + 1) >> 1;
+  for (int tt = threadIdx.x; tt < nrp * (kTG / 4); tt += blockDim.x) {
+    const int r0 = (tt / (kTG / 4)) * 2, c0 = (tt % (kTG / 4)) * 4;
+    const bool two = r0 + 1 < R;
+    double acc[2][4] = {};
+    const double* p0 = Ph + r0 * R;
+    const double* p1 = Ph + (two ? r0 + 1 : r0) * R;
+    for (int j = 0; j < R; ++j) {
+      const double f0 = p0[j], f1 = p1[j];
+      const double* v = Pv + j * (kTG + 1) + c0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        acc[0][q] = fma(f0, v[q], acc[0][q]);
+        acc[1][q] = fma(f1, v[q], acc[1][q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (c0 + q >= cntp) break;
+      const int64_t l = pts[c0 + q];
+      if (a.pstat[l] != 0) continue;
+      double* y = a.Y + l * a.NY + a.ybase[u];
+      y[r0] = acc[0][q];
+      if (two) y[r0 + 1] = acc[1][q];
+    }
   }
 }
 
@@ -327,7 +388,7 @@ constexpr int kMaxE = 8;     // field entries owned per thread
 
 __device__ __forceinline__ double darcy_value(const SubDev& S, const MomArgs& m, int64_t e_loc, int r0, int r1,
                                               int h0, const double* Tx, const double* Ty, const double* Z,
-                                              const double* Cf, int q, int C) {
+                                              const double* Cf, int q, int C, double ihx, double ihy) {
   const int nx = S.nx, ny = S.ny, R = S.R;
   const int np = (r1 - r0) * nx, nxf = (r1 - r0) * (nx + 1);
   if (e_loc < np) {
@@ -339,7 +400,7 @@ __device__ __forceinline__ double darcy_value(const SubDev& S, const MomArgs& m,
     const int rr_ = r0 + f / (nx + 1), ix = f % (nx + 1);
     const int zrow = (rr_ - h0) * nx;
     const double t = Tx[(int64_t)rr_ * (nx + 1) + ix];
-    if (ix > 0 && ix < nx) return t * (Z[(zrow + ix - 1) * kTP + q] - Z[(zrow + ix) * kTP + q]) / S.hy;
+    if (ix > 0 && ix < nx) return t * ihy * (Z[(zrow + ix - 1) * kTP + q] - Z[(zrow + ix) * kTP + q]);
     const int side = ix == 0 ? 3 : 1;
     if (S.side_type[side] == SIDE_NOFLOW) return 0.0;
     double gb = S.side_val[side];
@@ -348,13 +409,13 @@ __device__ __forceinline__ double darcy_value(const SubDev& S, const MomArgs& m,
       gb = 0.0;
       for (int i = 0; i < R; ++i) gb += P[i] * Cf[q * C + i];
     }
-    const double F = t * (Z[(zrow + (ix == 0 ? 0 : nx - 1)) * kTP + q] - gb);
-    return (ix == 0 ? -F : F) / S.hy;
+    const double F = t * ihy * (Z[(zrow + (ix == 0 ? 0 : nx - 1)) * kTP + q] - gb);
+    return ix == 0 ? -F : F;
   }
   const int f = (int)(e_loc - np - nxf);
   const int j = r0 + f / nx, ix = f % nx;
   const double t = Ty[(int64_t)j * nx + ix];
-  if (j > 0 && j < ny) return t * (Z[((j - 1 - h0) * nx + ix) * kTP + q] - Z[((j - h0) * nx + ix) * kTP + q]) / S.hx;
+  if (j > 0 && j < ny) return t * ihx * (Z[((j - 1 - h0) * nx + ix) * kTP + q] - Z[((j - h0) * nx + ix) * kTP + q]);
   const int side = j == 0 ? 0 : 2;
   if (S.side_type[side] == SIDE_NOFLOW) return 0.0;
   double gb = S.side_val[side];
@@ -363,8 +424,8 @@ __device__ __forceinline__ double darcy_value(const SubDev& S, const MomArgs& m,
     gb = 0.0;
     for (int i = 0; i < R; ++i) gb += P[i] * Cf[q * C + i];
   }
-  const double F = t * (Z[((j == 0 ? 0 : ny - 1) - h0) * nx * kTP + ix * kTP + q] - gb);
-  return (j == 0 ? -F : F) / S.hx;
+  const double F = t * ihx * (Z[((j == 0 ? 0 : ny - 1) - h0) * nx * kTP + ix * kTP + q] - gb);
+  return j == 0 ? -F : F;
 }
 
 // Global entry index of a tile-local entry.
@@ -402,6 +463,7 @@ __global__ void __launch_bounds__(kMomT) darcy_moments_kernel(MomArgs m) {
     acc1[q] = 0.0;
     acc2[q] = 0.0;
   }
+  const double ihx = 1.0 / S.hx, ihy = 1.0 / S.hy;
   for (int t = ch; t < a.n_tiles[s]; t += m.n_chunks) {
     const int* tl = a.tiles + 3 * ((int64_t)s * a.max_tiles + t);
     const int k = tl[0];
@@ -409,49 +471,54 @@ __global__ void __launch_bounds__(kMomT) darcy_moments_kernel(MomArgs m) {
     const double* X = m.X + off.x;
     const double* Tx = m.T + off.t;
     const double* Ty = Tx + (int64_t)ny * (nx + 1);
-    int cntp = tl[2];
-    const int* pts = a.grp_pts + (int64_t)s * a.pts_ld + tl[1];
+    const int cnt_tile = tl[2];
+    const int* tpts = a.grp_pts + (int64_t)s * a.pts_ld + tl[1];
+    int q_begin = 0, q_end = cnt_tile;
     if (m.mode == 0) {
       int has0 = -1;
-      for (int q = 0; q < cntp; ++q)
-        if (pts[q] == 0) has0 = q;
+      for (int q = 0; q < cnt_tile; ++q)
+        if (tpts[q] == 0) has0 = q;
       if (has0 < 0) continue;
-      pts += has0;
-      cntp = 1;
+      q_begin = has0;
+      q_end = has0 + 1;
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < cntp * C; e += blockDim.x) {
-      const int q = e / C, i = e - q * C;
-      Cf[e] = i < R ? a.lam[(int64_t)pts[q] * a.n_lambda + gd[i]] : 1.0;
-    }
-    for (int q = threadIdx.x; q < kTP; q += blockDim.x) Wt[q] = q < cntp ? m.w[pts[q]] : 0.0;
-    __syncthreads();
-    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
-      const double* xr = X + (int64_t)h0 * nx + c;
-      double z[kTP];
-#pragma unroll
-      for (int q = 0; q < kTP; ++q) z[q] = 0.0;
-      for (int i = 0; i < C; ++i) {
-        const double xv = xr[(int64_t)i * nc];
-#pragma unroll
-        for (int q = 0; q < kTP; ++q) z[q] = fma(xv, Cf[q * C + i], z[q]);
+    for (int qs = q_begin; qs < q_end; qs += kTP) {
+      const int* pts = tpts + qs;
+      const int cntp = min(kTP, q_end - qs);
+      __syncthreads();
+      for (int e = threadIdx.x; e < cntp * C; e += blockDim.x) {
+        const int q = e / C, i = e - q * C;
+        Cf[e] = i < R ? a.lam[(int64_t)pts[q] * a.n_lambda + gd[i]] : 1.0;
       }
+      for (int q = threadIdx.x; q < kTP; q += blockDim.x) Wt[q] = q < cntp ? m.w[pts[q]] : 0.0;
+      __syncthreads();
+      for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+        const double* xr = X + (int64_t)h0 * nx + c;
+        double z[kTP];
 #pragma unroll
-      for (int q = 0; q < kTP; ++q) Z[c * kTP + q] = z[q];
-    }
-    __syncthreads();
+        for (int q = 0; q < kTP; ++q) z[q] = 0.0;
+        for (int i = 0; i < C; ++i) {
+          const double xv = xr[(int64_t)i * nc];
 #pragma unroll
-    for (int j = 0; j < kMaxE; ++j) {
-      const int64_t el = threadIdx.x + (int64_t)j * kMomT;
-      if (el >= n_ent) break;
-      for (int q = 0; q < cntp; ++q) {
-        const double v = darcy_value(S, m, el, r0, r1, h0, Tx, Ty, Z, Cf, q, C);
-        if (m.mode == 0) {
-          sh[j] = v;
-        } else {
-          const double d = v - sh[j];
-          acc1[j] = fma(Wt[q], d, acc1[j]);
-          acc2[j] = fma(Wt[q] * d, d, acc2[j]);
+          for (int q = 0; q < kTP; ++q) z[q] = fma(xv, Cf[q * C + i], z[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < kTP; ++q) Z[c * kTP + q] = z[q];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < kMaxE; ++j) {
+        const int64_t el = threadIdx.x + (int64_t)j * kMomT;
+        if (el >= n_ent) break;
+        for (int q = 0; q < cntp; ++q) {
+          const double v = darcy_value(S, m, el, r0, r1, h0, Tx, Ty, Z, Cf, q, C, ihx, ihy);
+          if (m.mode == 0) {
+            sh[j] = v;
+          } else {
+            const double d = v - sh[j];
+            acc1[j] = fma(Wt[q], d, acc1[j]);
+            acc2[j] = fma(Wt[q] * d, d, acc2[j]);
+          }
         }
       }
     }
@@ -613,7 +680,11 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   const int nu = ns + 1;
   cudaError_t e;
 #define CK(x) do { e = (x); if (e != cudaSuccess) { c->err = std::string("interface solve: ") + cudaGetErrorString(e); return SFB_ERR_CUDA; } } while (0)
+  for (int q = 0; q < 6; ++q)
+    if (!c->ev[q]) CK(cudaEventCreate(&c->ev[q]));
+  CK(cudaEventRecord(c->ev[0], st));
   CK(cudaMemsetAsync(d.pstat, 0, sizeof(int) * n_pts, st));
+  CK(cudaMemsetAsync(d.active, 0, sizeof(int) * 4, st));
   const int64_t tot = n_pts * ns;
   kmap_kernel<<<(int)std::min<int64_t>((tot + 255) / 256, 8192), 256, 0, st>>>(
       d.y, n_pts, c->grid.n_dim, d.subs, ns, d.dim_off, d.yloc, d.hash, d.hash_off, d.hash_cap, d.kmap, d.pstat);
@@ -623,20 +694,21 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   stokes_group_kernel<<<64, 256, 0, st>>>(n_pts, ns, d.grp_pts, c->ws_pts, d.tiles, c->max_tiles, d.n_tiles);
   CK(cudaGetLastError());
   IfaceArgs a = make_args(c, n_pts);
+  CK(cudaEventRecord(c->ev[1], st));
   const int warps_per_block = 8;
   const int ublocks = (int)((n_pts + warps_per_block - 1) / warps_per_block);
   init_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a);
   CK(cudaGetLastError());
   int maxR = (int)c->stokes.dofs.size();
   for (const HostSub& S : c->subs) maxR = std::max(maxR, (int)S.dofs.size());
-  const size_t smv = sizeof(double) * ((size_t)maxR * maxR + (size_t)kTP * maxR);
+  const size_t smv = sizeof(double) * ((size_t)((maxR * maxR + 1) & ~1) + (size_t)(kTG + 1) * maxR);
   CK(cudaFuncSetAttribute(matvec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv));
   dim3 mgrid(c->max_tiles, nu);
   const int chunk = c->opt_cg_chunk;
   int it = 0;
   for (; it < max_it;) {
     for (int q = 0; q < chunk && it < max_it; ++q, ++it) {
-      matvec_kernel<<<mgrid, 256, smv, st>>>(a);
+      matvec_kernel<<<mgrid, 256, smv, st>>>(a, d.active + 2);
       update_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, it, rtol);
     }
     CK(cudaGetLastError());
@@ -647,14 +719,20 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
     CK(cudaStreamSynchronize(st));
     if (h_active == 0) break;
   }
+  c->cg_iters_run = it;
+  CK(cudaEventRecord(c->ev[2], st));
   finish_status<<<std::min(1024, (int)((n_pts + 255) / 256)), 256, 0, st>>>(d.pstat, n_pts, max_it, nullptr);
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(d.active + 1, 0, sizeof(int), st));
   count_failed<<<std::min(1024, (int)((n_pts + 255) / 256)), 256, 0, st>>>(d.pstat, n_pts, d.active + 1);
-  int h_failed = 0;
-  CK(cudaMemcpyAsync(&h_failed, d.active + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  int h_flags[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(h_flags, d.active, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  *n_failed = h_failed;
+  *n_failed = h_flags[1];
+  if (h_flags[2]) {
+    c->err = "interface solve: a bulk copy of a basis did not complete within the wait limit";
+    return SFB_ERR_TIMEOUT;
+  }
   return SFB_OK;
 #undef CK
 }
@@ -684,6 +762,7 @@ sfb_status moments_accumulate_device(sfb_ctx* c, int64_t n_pts) {
   CK(cudaFuncSetAttribute(darcy_moments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd));
   const int row_tiles = (max_ny + m.rt - 1) / m.rt;
   const int first = c->mom_shift_set ? 0 : 1;
+  CK(cudaEventRecord(c->ev[3], st));
   if (first) {
     m.mode = 0;
     darcy_moments_kernel<<<dim3(row_tiles, ns, 1), kMomT, smd, st>>>(m);
@@ -693,12 +772,14 @@ sfb_status moments_accumulate_device(sfb_ctx* c, int64_t n_pts) {
   darcy_moments_kernel<<<dim3(row_tiles, ns, m.n_chunks), kMomT, smd, st>>>(m);
   CK(cudaGetLastError());
   reduce_partials<<<256, 256, 0, st>>>(d.mom_part, m.n_chunks, m.len_d, d.mom + m.len_d, d.mom + 2 * m.len_d);
+  CK(cudaEventRecord(c->ev[4], st));
   const int Cs = (int)c->stokes.dofs.size() + 1;
   stokes_cov_kernel<<<Cs, 128, 0, st>>>(m.ia, d.w, first, d.st_c0, d.st_m, d.st_M);
   CK(cudaGetLastError());
   c->mom_shift_set = true;
   weight_sum<<<1, 32, 0, st>>>(d.w, n_pts, d.mom_w);
   CK(cudaGetLastError());
+  CK(cudaEventRecord(c->ev[5], st));
   return SFB_OK;
 #undef CK
 }

@@ -162,4 +162,11 @@ struct sfb_ctx {
   double opt_refine_tol = 1e-10;
   int opt_refine_max = 8;
   int opt_cg_chunk = 8;
+  // device-time phase markers of the last interface solve (CUDA events)
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int cg_iters_run = 0;
+  ~sfb_ctx() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  }
 };

@@ -161,7 +161,7 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
       o.t = nT; nT += (int64_t)S.ny * (S.nx + 1) + (int64_t)(S.ny + 1) * S.nx;
       const int64_t npad = (S.nx + 7) & ~7;  // identity-padded block size of the factor
       o.g = nG; nG += (int64_t)S.ny * npad * npad;
-      o.phi = nPhi; nPhi += (int64_t)R * R + R;
+      o.phi = nPhi; nPhi += ((int64_t)R * R + R + 1) & ~int64_t(1);   // 16-byte aligned items
       o.diag = nD; o.sc = nD; nD += nc;
       c->offs.push_back(o);
     }
@@ -221,7 +221,7 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   c->NY = c->ybase[nu];
   int max_local = 1;
   for (int nl : c->n_local) max_local = std::max(max_local, nl);
-  c->max_tiles = (int)std::min<int64_t>(max_pts, (int64_t)max_local + (max_pts + 7) / 8);
+  c->max_tiles = (int)std::min<int64_t>(max_pts, (int64_t)max_local + (max_pts + 31) / 32);
   c->max_tiles = std::max(c->max_tiles, 1);
   const int ndim = c->grid.n_dim;
   int64_t hash_tot = 0;
@@ -251,7 +251,7 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   d.rr = cv.take<double>(P);
   d.gn = cv.take<double>(P);
   d.pstat = cv.take<int>(P);
-  d.active = cv.take<int>(2);
+  d.active = cv.take<int>(4);
   d.s_gdof = cv.take<int64_t>(std::max(Rs, 1));
   d.ybase = cv.take<int64_t>(nu + 1);
   d.dim_off = cv.take<int>(ns);
@@ -776,6 +776,21 @@ sfb_status sfb_moments(sfb_ctx* c, int32_t field, double* mean_out, double* var_
   if (mean_out) SFB_CUDA(cudaMemcpyAsync(mean_out, c->dev.fin, sizeof(double) * n, cudaMemcpyDefault, c->stream), "copy");
   if (var_out) SFB_CUDA(cudaMemcpyAsync(var_out, c->dev.fin + n, sizeof(double) * n, cudaMemcpyDefault, c->stream), "copy");
   SFB_CUDA(cudaStreamSynchronize(c->stream), "moments");
+  return SFB_OK;
+}
+
+sfb_status sfb_solve_timings(sfb_ctx* c, double* ms_out, int32_t* cg_iterations) {
+  if (!c || !ms_out) return SFB_ERR_ARG;
+  if (c->n_solved == 0 || !c->ev[5]) return fail(c, SFB_ERR_STATE, "no interface solve yet");
+  SFB_CUDA(cudaEventSynchronize(c->ev[5]), "timings");
+  float t[5];
+  for (int q = 0; q < 5; ++q) SFB_CUDA(cudaEventElapsedTime(&t[q], c->ev[q], c->ev[q + 1]), "timings");
+  ms_out[0] = t[0];          // index conversion and grouping
+  ms_out[1] = t[1];          // CG iterations
+  ms_out[2] = t[2];          // status bookkeeping
+  ms_out[3] = t[3];          // Darcy moments
+  ms_out[4] = t[4];          // Stokes moments and weights
+  if (cg_iterations) *cg_iterations = c->cg_iters_run;
   return SFB_OK;
 }
 
