@@ -202,6 +202,22 @@ sfb_status sfb_moments_reset(sfb_ctx* ctx);
  * number of lockstep CG iterations run. Synchronises the stream. */
 sfb_status sfb_solve_timings(sfb_ctx* ctx, double* ms_out, int32_t* cg_iterations);
 
+/* Builds one stochastic-basis item (Darcy subdomain `sub`, local realization
+ * `k`) without allocating device memory; the paper has no counterpart, this
+ * is for callers that cannot call cudaMalloc (an application that already
+ * holds all device memory in its own pool, or a path that must not allocate).
+ * Needs only sfb_kl_setup and sfb_collocation_setup, no workspace. The
+ * working memory is a static 8 MiB device array inside the library that a GPU
+ * keeps for the rest of the process once the library is used on it; items
+ * needing more return SFB_ERR_UNSUPPORTED. Outputs: phi_out [R x R] and g_out
+ * [R] (nullable; host or device), x_out [(R+1) x n_cells] device memory, the
+ * same values as sfb_build_stochastic_basis + sfb_get_basis. The first call on
+ * a device resolves the array's device address; make that first call before
+ * any stream capture. Calls share the array: calls that overlap on the GPU
+ * race and must be serialised by the caller. Synchronises the stream. */
+sfb_status sfb_build_basis_item_noalloc(sfb_ctx* ctx, int32_t sub, int32_t k, int32_t prec,
+                                         double* phi_out, double* g_out, double* x_out);
+
 /* Tuning knobs (no counterpart in the paper):
  *   "refine_tol"     mixed form: stop refining when the predicted relative
  *                    error of X is below this (default 1e-10);

@@ -83,6 +83,8 @@ _SIGS = {
     "sfb_moments_reset": (ctypes.c_int, [ctypes.c_void_p]),
     "sfb_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_double]),
     "sfb_solve_timings": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _i32p]),
+    "sfb_build_basis_item_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 _lib = None
@@ -282,6 +284,15 @@ class Solver:
         self._check(self.lib.sfb_get_basis(self.h, sub, k, phi.ctypes.data, g.ctypes.data,
                                            x.ctypes.data if with_x else None))
         return phi, g, (x.T.copy() if with_x else None)
+
+    def build_item_noalloc(self, sub, k, prec, phi_out, g_out, x_out, check=True):
+        """One basis item through the allocation-free entry point; the caller
+        supplies the outputs (x_out a device tensor of (R+1) x n_cells)."""
+        rc = self.lib.sfb_build_basis_item_noalloc(self.h, sub, k, prec, ctypes.c_void_p(_ptr(phi_out)),
+                                                   ctypes.c_void_p(_ptr(g_out)), ctypes.c_void_p(_ptr(x_out)))
+        if check:
+            self._check(rc)
+        return rc
 
     def solve(self, y, w, rtol=1e-10, max_it=1000, lam_out=None, iters_out=None, check=True):
         """Interface CG for a batch of points (host numpy or device torch
