@@ -222,7 +222,10 @@ sfb_status sfb_build_basis_item_noalloc(sfb_ctx* ctx, int32_t sub, int32_t k, in
  *   "refine_tol"     mixed form: stop refining when the predicted relative
  *                    error of X is below this (default 1e-10);
  *   "refine_max"     mixed form: at most this many FP64 residual passes (8);
- *   "cg_check_every" CG iterations between convergence checks on the host (8).
+ *   "cg_check_every" CG iterations between convergence checks on the host (8);
+ *   "moments_group_factor"  groups of more than factor * (R+1) points enter
+ *                    the moments through their coefficient second moments,
+ *                    smaller ones point by point; 0 = always point by point (2).
  * SFB_ERR_ARG for an unknown name or a value out of range. */
 sfb_status sfb_set_option(sfb_ctx* ctx, const char* name, double value);
 

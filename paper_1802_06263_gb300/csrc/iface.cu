@@ -381,7 +381,19 @@ struct MomArgs {
   int mode;                 // 0: write the shifts from point 0; 1: accumulate
   int rt;                   // grid rows per CTA
   int n_chunks;
+  // groups larger than big_factor * (R+1) points go through their coefficient moments
+  int big_factor;
+  const int* grp_start;     // per (subdomain, local realization): first sorted point
+  const int* grp_end;       // ... and one past the last
+  const int64_t* loc_off;   // per subdomain offset into the group arrays
+  double* gmom;             // per group: W | cbar[C] | m[C] | M[C][C]
+  int64_t gmom_stride;
 };
+
+__device__ __forceinline__ bool big_group(const MomArgs& m, const SubDev& S, int s, int k) {
+  const int64_t g = m.loc_off[s] + k;
+  return m.big_factor > 0 && (m.grp_end[g] - m.grp_start[g]) > m.big_factor * (S.R + 1);
+}
 
 constexpr int kMomT = 256;   // threads of the Darcy moments kernel
 constexpr int kMaxE = 8;     // field entries owned per thread
@@ -467,6 +479,7 @@ __global__ void __launch_bounds__(kMomT) darcy_moments_kernel(MomArgs m) {
   for (int t = ch; t < a.n_tiles[s]; t += m.n_chunks) {
     const int* tl = a.tiles + 3 * ((int64_t)s * a.max_tiles + t);
     const int k = tl[0];
+    if (m.mode == 1 && big_group(m, S, s, k)) continue;  // handled by its coefficient moments
     const ItemOff off = a.off[S.item0 + k];
     const double* X = m.X + off.x;
     const double* Tx = m.T + off.t;
@@ -535,6 +548,210 @@ __global__ void __launch_bounds__(kMomT) darcy_moments_kernel(MomArgs m) {
       m.part[((int64_t)ch * 2) * m.len_d + ge] = acc1[j];
       m.part[((int64_t)ch * 2 + 1) * m.len_d + ge] = acc2[j];
     }
+  }
+}
+
+constexpr int kGChunks = 16;   // point chunks per large group (partials reduced in order)
+
+// Partial coefficient moments of one large group k of subdomain s over point
+// chunk blockIdx.z, about the coefficients cbar of the group's first point:
+// W = sum w, m = sum w d, M = sum w d d^T with d = [R lambda_l; 1] - cbar.
+// M is computed in 4 x 4 register tiles; points are staged 16 at a time.
+__global__ void __launch_bounds__(256) group_moments_kernel(MomArgs m, double* part) {
+  __shared__ double Dl[16][kMaxCols + 3];
+  __shared__ double Wl[16];
+  __shared__ double cbar[kMaxCols];
+  const IfaceArgs& a = m.ia;
+  const int k = blockIdx.x, s = blockIdx.y, ch = blockIdx.z;
+  const SubDev& S = a.subs[s];
+  if (k >= S.n_local || !big_group(m, S, s, k)) return;
+  const int R = S.R, C = R + 1;
+  const int64_t g = m.loc_off[s] + k;
+  const int g0 = m.grp_start[g], g1 = m.grp_end[g];
+  const int per = (g1 - g0 + kGChunks - 1) / kGChunks;
+  const int p0 = g0 + ch * per, p1 = min(g1, p0 + per);
+  const int* pts = a.grp_pts + (int64_t)s * a.pts_ld;
+  const int64_t* gd = a.gdof + S.gdof_off;
+  for (int i = threadIdx.x; i < C; i += blockDim.x)
+    cbar[i] = i < R ? a.lam[(int64_t)pts[g0] * a.n_lambda + gd[i]] : 1.0;
+  const int nt4 = (C + 3) >> 2;
+  const int ntile = nt4 * nt4;
+  double* out = part + ((int64_t)g * kGChunks + ch) * m.gmom_stride;
+  for (int tb = 0; tb < ntile; tb += blockDim.x) {
+    const int t = tb + threadIdx.x;
+    const int a0 = (t / nt4) * 4, b0 = (t % nt4) * 4;
+    double acc[4][4] = {};
+    double accm = 0.0, accW = 0.0;
+    for (int q0 = p0; q0 < p1; q0 += 16) {
+      const int nq = min(16, p1 - q0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < nq * (C + 3); e += blockDim.x) {
+        const int q = e / (C + 3), i = e - q * (C + 3);
+        double v = 0.0;
+        if (i < C) {
+          const int64_t l = pts[q0 + q];
+          v = (i < R ? a.lam[l * a.n_lambda + gd[i]] : 1.0) - cbar[i];
+        }
+        Dl[q][i] = v;
+      }
+      for (int q = threadIdx.x; q < nq; q += blockDim.x) Wl[q] = m.w[pts[q0 + q]];
+      __syncthreads();
+      if (t < ntile) {
+        for (int q = 0; q < nq; ++q) {
+          const double wq = Wl[q];
+          double da[4], db[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) { da[i] = wq * Dl[q][a0 + i]; db[i] = Dl[q][b0 + i]; }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(da[i], db[j], acc[i][j]);
+          if (tb == 0 && threadIdx.x < C) accm = fma(wq, Dl[q][threadIdx.x], accm);
+          if (tb == 0 && threadIdx.x == 0) accW += wq;
+        }
+      }
+    }
+    if (t < ntile)
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (a0 + i < C && b0 + j < C) out[1 + 2 * C + (a0 + i) * C + b0 + j] = acc[i][j];
+    if (tb == 0) {
+      if (threadIdx.x < C) { out[1 + threadIdx.x] = cbar[threadIdx.x]; out[1 + C + threadIdx.x] = accm; }
+      if (threadIdx.x == 0) out[0] = accW;
+    }
+  }
+}
+
+// gmom[g] = sum over the point chunks of the partial moments (fixed order).
+__global__ void group_moments_reduce(MomArgs m, const double* part) {
+  const IfaceArgs& a = m.ia;
+  const int k = blockIdx.x, s = blockIdx.y;
+  const SubDev& S = a.subs[s];
+  if (k >= S.n_local || !big_group(m, S, s, k)) return;
+  const int C = S.R + 1;
+  const int64_t g = m.loc_off[s] + k;
+  const int n = 1 + 2 * C + C * C;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    double v = 0.0;
+    if (e >= 1 + C && e < 1 + 2 * C || e == 0 || e >= 1 + 2 * C) {
+      for (int c = 0; c < kGChunks; ++c) v += part[((int64_t)g * kGChunks + c) * m.gmom_stride + e];
+    } else {
+      v = part[((int64_t)g * kGChunks) * m.gmom_stride + e];  // cbar: the same in every chunk
+    }
+    m.gmom[g * m.gmom_stride + e] = v;
+  }
+}
+
+constexpr int kBigT = 128;   // threads of the large-group moments kernel
+constexpr int kBigE = 16;    // field entries owned per thread
+
+// Coefficient of column a in the affine map from [R lambda; 1] to the value of
+// tile-local entry e_loc (cell pressure or face velocity) for basis item X.
+__device__ __forceinline__ double entry_coef(const SubDev& S, const MomArgs& m, int64_t e_loc, int r0, int r1,
+                                             const double* X, const double* Tx, const double* Ty, int a,
+                                             double ihx, double ihy) {
+  const int nx = S.nx, ny = S.ny, R = S.R, nc = nx * ny;
+  const double* xa = X + (int64_t)a * nc;
+  const int np = (r1 - r0) * nx, nxf = (r1 - r0) * (nx + 1);
+  if (e_loc < np) return xa[(int64_t)r0 * nx + e_loc];
+  if (e_loc < np + nxf) {
+    const int f = (int)(e_loc - np);
+    const int row = r0 + f / (nx + 1), ix = f % (nx + 1);
+    const double t = Tx[(int64_t)row * (nx + 1) + ix] * ihy;
+    if (ix > 0 && ix < nx) return t * (xa[row * nx + ix - 1] - xa[row * nx + ix]);
+    const int side = ix == 0 ? 3 : 1;
+    if (S.side_type[side] == SIDE_NOFLOW) return 0.0;
+    double gb = 0.0;
+    if (S.side_type[side] == SIDE_IFACE) gb = a < R ? m.proj[S.proj_off[side] + (int64_t)row * R + a] : 0.0;
+    else gb = a == R ? S.side_val[side] : 0.0;
+    const double F = t * (xa[row * nx + (ix == 0 ? 0 : nx - 1)] - gb);
+    return ix == 0 ? -F : F;
+  }
+  const int f = (int)(e_loc - np - nxf);
+  const int j = r0 + f / nx, ix = f % nx;
+  const double t = Ty[(int64_t)j * nx + ix] * ihx;
+  if (j > 0 && j < ny) return t * (xa[(j - 1) * nx + ix] - xa[j * nx + ix]);
+  const int side = j == 0 ? 0 : 2;
+  if (S.side_type[side] == SIDE_NOFLOW) return 0.0;
+  double gb = 0.0;
+  if (S.side_type[side] == SIDE_IFACE) gb = a < R ? m.proj[S.proj_off[side] + (int64_t)ix * R + a] : 0.0;
+  else gb = a == R ? S.side_val[side] : 0.0;
+  const double F = t * (xa[(j == 0 ? 0 : ny - 1) * nx + ix] - gb);
+  return j == 0 ? -F : F;
+}
+
+// Large groups: with F the entry's coefficient row and v = F c,
+// sum_l w (v_l - s) = F m + W (F cbar - s) and
+// sum_l w (v_l - s)^2 = F M F^T + 2 (F cbar - s) F m + W (F cbar - s)^2.
+// Writes partial slot `slot` for every entry of the tile (zeros when the
+// subdomain has no large group).
+__global__ void __launch_bounds__(kBigT) bigroup_moments_kernel(MomArgs m, int slot) {
+  extern __shared__ __align__(16) double smb[];
+  const IfaceArgs& a = m.ia;
+  const int s = blockIdx.y;
+  const SubDev S = a.subs[s];
+  const int nx = S.nx, ny = S.ny, R = S.R, C = R + 1;
+  const int r0 = blockIdx.x * m.rt;
+  if (r0 >= ny) return;
+  const int r1 = min(ny, r0 + m.rt);
+  const int n_ent = (r1 - r0) * nx + (r1 - r0) * (nx + 1) + ((r1 == ny ? ny + 1 : r1) - r0) * nx;
+  double* Ms = smb;                 // [C][C]
+  double* cb = Ms + C * C;          // [C]
+  double* mv = cb + C;              // [C]
+  double* Fs = mv + C;              // [C][kBigT]
+  const double ihx = 1.0 / S.hx, ihy = 1.0 / S.hy;
+  double sh[kBigE], acc1[kBigE], acc2[kBigE];
+#pragma unroll
+  for (int j = 0; j < kBigE; ++j) {
+    const int64_t el = threadIdx.x + (int64_t)j * kBigT;
+    sh[j] = el < n_ent ? m.shift[darcy_entry(S, m, s, el, r0, r1)] : 0.0;
+    acc1[j] = 0.0;
+    acc2[j] = 0.0;
+  }
+  for (int k = 0; k < S.n_local; ++k) {
+    if (!big_group(m, S, s, k)) continue;
+    const double* gm = m.gmom + (m.loc_off[s] + k) * m.gmom_stride;
+    const ItemOff off = a.off[S.item0 + k];
+    const double* X = m.X + off.x;
+    const double* Tx = m.T + off.t;
+    const double* Ty = Tx + (int64_t)ny * (nx + 1);
+    __syncthreads();
+    for (int e = threadIdx.x; e < C * C; e += blockDim.x) Ms[e] = gm[1 + 2 * C + e];
+    for (int e = threadIdx.x; e < C; e += blockDim.x) { cb[e] = gm[1 + e]; mv[e] = gm[1 + C + e]; }
+    const double W = gm[0];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kBigE; ++j) {
+      const int64_t el = threadIdx.x + (int64_t)j * kBigT;
+      if (el >= n_ent) break;
+      double fc = 0.0, fm = 0.0;
+      for (int ia = 0; ia < C; ++ia) {
+        const double f = entry_coef(S, m, el, r0, r1, X, Tx, Ty, ia, ihx, ihy);
+        Fs[ia * kBigT + threadIdx.x] = f;
+        fc = fma(f, cb[ia], fc);
+        fm = fma(f, mv[ia], fm);
+      }
+      double q = 0.0;
+      for (int ia = 0; ia < C; ++ia) {
+        double row = 0.0;
+        const double* Mr = Ms + ia * C;
+        for (int ib = 0; ib < C; ++ib) row = fma(Mr[ib], Fs[ib * kBigT + threadIdx.x], row);
+        q = fma(Fs[ia * kBigT + threadIdx.x], row, q);
+      }
+      const double dv = fc - sh[j];
+      acc1[j] += fm + W * dv;
+      acc2[j] += q + 2.0 * dv * fm + W * dv * dv;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kBigE; ++j) {
+    const int64_t el = threadIdx.x + (int64_t)j * kBigT;
+    if (el >= n_ent) break;
+    const int64_t ge = darcy_entry(S, m, s, el, r0, r1);
+    m.part[((int64_t)slot * 2) * m.len_d + ge] = acc1[j];
+    m.part[((int64_t)slot * 2 + 1) * m.len_d + ge] = acc2[j];
   }
 }
 
@@ -758,6 +975,9 @@ sfb_status moments_accumulate_device(sfb_ctx* c, int64_t n_pts) {
   // rows per CTA: about 512 cells, so the owned entries fit kMaxE per thread
   m.rt = std::max(1, std::min(max_ny, 512 / max_nx));
   m.n_chunks = c->mom_chunks;
+  m.big_factor = c->opt_big_factor;
+  m.grp_start = d.grp_start; m.grp_end = d.grp_count; m.loc_off = d.loc_off;
+  m.gmom = d.gmom; m.gmom_stride = c->gmom_stride;
   const size_t smd = sizeof(double) * ((size_t)kTP * maxC + (size_t)(m.rt + 1) * max_nx * kTP + kTP);
   CK(cudaFuncSetAttribute(darcy_moments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd));
   const int row_tiles = (max_ny + m.rt - 1) / m.rt;
@@ -771,7 +991,15 @@ sfb_status moments_accumulate_device(sfb_ctx* c, int64_t n_pts) {
   m.mode = 1;
   darcy_moments_kernel<<<dim3(row_tiles, ns, m.n_chunks), kMomT, smd, st>>>(m);
   CK(cudaGetLastError());
-  reduce_partials<<<256, 256, 0, st>>>(d.mom_part, m.n_chunks, m.len_d, d.mom + m.len_d, d.mom + 2 * m.len_d);
+  int max_local = 1;
+  for (int nl : c->n_local) max_local = std::max(max_local, nl);
+  group_moments_kernel<<<dim3(max_local, ns, kGChunks), 256, 0, st>>>(m, d.gmom_part);
+  group_moments_reduce<<<dim3(max_local, ns), 256, 0, st>>>(m, d.gmom_part);
+  const size_t smb = sizeof(double) * ((size_t)maxC * maxC + 2 * (size_t)maxC + (size_t)maxC * kBigT);
+  CK(cudaFuncSetAttribute(bigroup_moments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+  bigroup_moments_kernel<<<dim3(row_tiles, ns), kBigT, smb, st>>>(m, m.n_chunks);
+  CK(cudaGetLastError());
+  reduce_partials<<<256, 256, 0, st>>>(d.mom_part, m.n_chunks + 1, m.len_d, d.mom + m.len_d, d.mom + 2 * m.len_d);
   CK(cudaEventRecord(c->ev[4], st));
   const int Cs = (int)c->stokes.dofs.size() + 1;
   stokes_cov_kernel<<<Cs, 128, 0, st>>>(m.ia, d.w, first, d.st_c0, d.st_m, d.st_M);

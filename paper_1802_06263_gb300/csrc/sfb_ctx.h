@@ -118,6 +118,8 @@ struct Dev {
   double* st_c0 = nullptr;    // Stokes: coefficients of the shift point
   double* st_m = nullptr;     // Stokes: sum w (c - c0)
   double* st_M = nullptr;     // Stokes: sum w (c - c0)(c - c0)^T
+  double* gmom = nullptr;     // per group: W | cbar | m | M (large groups)
+  double* gmom_part = nullptr;// per group and point chunk: partial moments
 };
 
 }  // namespace sfb
@@ -158,10 +160,12 @@ struct sfb_ctx {
   int64_t mom_off[4] = {0, 0, 0, 0};
   bool mom_shift_set = false;
   int mom_chunks = 1;
+  int64_t gmom_stride = 1;
   // options (sfb_set_option)
   double opt_refine_tol = 1e-10;
   int opt_refine_max = 8;
   int opt_cg_chunk = 8;
+  int opt_big_factor = 2;   // groups above this many times (R+1) points use coefficient moments
   // device-time phase markers of the last interface solve (CUDA events)
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int cg_iters_run = 0;

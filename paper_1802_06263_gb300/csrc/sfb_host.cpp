@@ -279,7 +279,14 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   c->mom_chunks = std::max(1, std::min(16, (4 * 152 + row_tiles - 1) / std::max(row_tiles, 1)));
   d.mom = cv.take<double>((size_t)3 * len_d);
   d.mom_w = cv.take<double>(2);
-  d.mom_part = cv.take<double>((size_t)2 * c->mom_chunks * len_d);
+  d.mom_part = cv.take<double>((size_t)2 * (c->mom_chunks + 1) * len_d);   // + the large-group slot
+  {
+    int maxC = 1;
+    for (const HostSub& S : c->subs) maxC = std::max(maxC, (int)S.dofs.size() + 1);
+    c->gmom_stride = 1 + 2 * (int64_t)maxC + (int64_t)maxC * maxC;
+  }
+  d.gmom = cv.take<double>((size_t)std::max<int64_t>(n_loc_tot, 1) * c->gmom_stride);
+  d.gmom_part = cv.take<double>((size_t)std::max<int64_t>(n_loc_tot, 1) * 16 * c->gmom_stride);
   d.st_c0 = cv.take<double>(Rs + 1);
   d.st_m = cv.take<double>(Rs + 1);
   d.st_M = cv.take<double>((size_t)(Rs + 1) * (Rs + 1));
@@ -803,6 +810,9 @@ sfb_status sfb_set_option(sfb_ctx* c, const char* name, double value) {
   } else if (n == "refine_max") {
     if (!(value >= 1 && value <= 50)) return fail(c, SFB_ERR_ARG, "refine_max must lie in [1, 50]");
     c->opt_refine_max = (int)value;
+  } else if (n == "moments_group_factor") {
+    if (!(value >= 0 && value <= 1e6)) return fail(c, SFB_ERR_ARG, "moments_group_factor must lie in [0, 1e6]");
+    c->opt_big_factor = (int)value;
   } else if (n == "cg_check_every") {
     if (!(value >= 1 && value <= 1000)) return fail(c, SFB_ERR_ARG, "cg_check_every must lie in [1, 1000]");
     c->opt_cg_chunk = (int)value;
