@@ -97,6 +97,55 @@ def _dist():
     return world, rank, local
 
 
+def max_over_ranks(value, device="cpu"):
+    """Largest value over the ranks of the default process group (the value
+    itself without one): the step time a multi-GPU run reports."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# FP32 SIMT peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2
+# flop per FMA x 2070 MHz; FP64 the nominal 1.25 TFLOP/s of the part.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+
+
+def basis_algorithmic_flops(solver, wl):
+    """Algorithmic flops of one basis build: per (subdomain, local
+    realization) item (7/3) nx^3 ny for the block factorization plus
+    6 nx^2 ny R for the R multi-RHS solves (block Cholesky count)."""
+    tot = 0.0
+    for sub, (nx, ny) in enumerate(wl["darcy_grid"]):
+        R = len(solver.subdomain_dofs(sub))
+        n_loc = len(solver.local_points(sub))
+        tot += n_loc * (7.0 / 3.0 * nx ** 3 * ny + 6.0 * nx ** 2 * ny * R)
+    return tot
+
+
+def profiled_traffic(kernel_file, summary):
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    kernel source changed after the counters were taken."""
+    import hashlib
+    try:
+        txt = open(os.path.join(ROOT, "profiles", summary)).read()
+        src = open(os.path.join(ROOT, "paper_1802_06263_gb300", "csrc", kernel_file), "rb").read()
+    except OSError:
+        return None
+    h = hashlib.sha256(src).hexdigest()
+    rec_hash, rec_bytes = None, None
+    for line in txt.splitlines():
+        if line.startswith("source_sha256:"):
+            rec_hash = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            rec_bytes = float(line.split(":", 1)[1].strip())
+    return rec_bytes if rec_hash == h else None
+
+
 def run_ours(args):
     import torch
     import paper_1802_06263_gb300 as sfb
@@ -151,17 +200,16 @@ def run_ours(args):
         total = t0.elapsed_time(t1) / k
         basis = np.mean([e[0].elapsed_time(e[1]) for _, e in phases])
         solve = np.mean([e[1].elapsed_time(e[2]) for _, e in phases])
-        kern = np.mean([p[0]["ms"] for p in phases])
+        kern = np.mean([p[0]["kernel_ms"] for p in phases])
         timed.solve_phases = s.solve_timings()
-        if world > 1:
-            tt = torch.tensor([total], device="cuda")
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            total = float(tt.item())
+        total = max_over_ranks(total, "cuda")
         return total, basis, solve, kern, phases[-1][0]
 
     clocks = ClockSampler(local)
     clocks.start()
+    launches0 = s.launch_count()
     t_mixed, b_mixed, s_mixed, k_mixed, st_mixed = timed(sfb.MIXED, args.steps)
+    launches = s.launch_count() - launches0
     mixed_phases = dict(timed.solve_phases)
     mean_mixed = {f: s.moments(f) for f in sfb.FIELDS}
     iters = it_d.cpu().numpy()
@@ -196,16 +244,17 @@ def run_ours(args):
             m, v = s.moments(f)
             mom_bytes += m.nbytes + v.nbytes
     torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    if world > 1:
-        tt = torch.tensor([e2e_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, "cuda")
 
-    # roofline of the dominant kernel: see the design doc for the flop model
+    # roofline of the dominant kernel (the basis kernel): algorithmic flops of
+    # one launch over its event-timed duration on the context's stream
     n_items = st_mixed["n_items"]
     fr = st_mixed["n_flux_responses"]
     peaks = _peaks()
+    flops = basis_algorithmic_flops(s, wl)
+    ach = flops / (k_mixed * 1e-3) / 1e12
+    ach64 = flops / (k_fp64 * 1e-3) / 1e12
+    traffic = profiled_traffic("basis.cu", "basis_kernel_mixed_precision.md")
     out = {
         "metric": METRIC, "value": world * n_pts / (t_mixed * 1e-3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_mixed,
@@ -234,9 +283,18 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(y.nbytes + wt.nbytes),
                 "d2h_bytes_per_step": int(lam_h.numel() * 8 + it_h.numel() * 4 + mom_bytes)},
         "clocks": clk,
-        "peaks_source": "MEASURED_PEAKS.json" if peaks else "fallback",
+        "roofline": {"bound": "alu", "kernel": "basis_kernel<float> (mixed form)", "achieved": ach,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                     "traffic": traffic, "algorithmic_flops_per_launch": flops,
+                     "kernel_ms": k_mixed,
+                     "peak_source": "unit counts: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+        "roofline_fp64_form": {"bound": "alu", "kernel": "basis_kernel<double>", "achieved": ach64,
+                               "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS,
+                               "kernel_ms": k_fp64, "peak_source": "nominal FP64 of the part"},
+        "peaks_source": "MEASURED_PEAKS.json (HBM, bf16 only)" if peaks else "fallback",
+        "gpu_launches": int(launches),
+        "gpu_launches_per_step": launches / args.steps,
     }
-    out["gpu_launches"] = None
     return out, rank
 
 

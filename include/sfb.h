@@ -124,6 +124,7 @@ typedef struct {
   double phase_cycles[4];     /* mean SM cycles per item in: permeability and     */
                               /* assembly, factorization, forward sweeps,         */
                               /* backward sweeps (clock64 in the kernel)          */
+  double kernel_ms;           /* device time of the basis kernel alone            */
 } sfb_basis_stats;
 
 typedef struct sfb_ctx sfb_ctx;
@@ -194,6 +195,9 @@ sfb_status sfb_interface_solve_batch(sfb_ctx* ctx, const double* y, const double
  * length). SFB_ERR_STATE if nothing was solved. */
 sfb_status sfb_moments(sfb_ctx* ctx, int32_t field, double* mean_out, double* var_out);
 sfb_status sfb_moments_reset(sfb_ctx* ctx);
+
+/* Number of CUDA kernels this context has launched so far. */
+sfb_status sfb_launch_count(const sfb_ctx* ctx, int64_t* n);
 
 /* Device time (ms, CUDA events) of the phases of the last
  * sfb_interface_solve_batch: [0] global-to-local index conversion and

@@ -54,7 +54,7 @@ class BasisStats(ctypes.Structure):
                 ("max_refine_steps", ctypes.c_int32), ("n_not_converged", ctypes.c_int32),
                 ("max_rel_residual", ctypes.c_double), ("max_first_correction", ctypes.c_double),
                 ("max_error_estimate", ctypes.c_double), ("ms", ctypes.c_double),
-                ("phase_cycles", ctypes.c_double * 4)]
+                ("phase_cycles", ctypes.c_double * 4), ("kernel_ms", ctypes.c_double)]
 
 
 _SIGS = {
@@ -83,6 +83,7 @@ _SIGS = {
     "sfb_moments_reset": (ctypes.c_int, [ctypes.c_void_p]),
     "sfb_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_double]),
     "sfb_solve_timings": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _i32p]),
+    "sfb_launch_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "sfb_build_basis_item_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
@@ -318,6 +319,11 @@ class Solver:
         mean, var = np.zeros(n), np.zeros(n)
         self._check(self.lib.sfb_moments(self.h, FIELDS[field], mean.ctypes.data, var.ctypes.data))
         return mean, var
+
+    def launch_count(self):
+        n = ctypes.c_int64()
+        self._check(self.lib.sfb_launch_count(self.h, ctypes.byref(n)))
+        return n.value
 
     def solve_timings(self):
         ms = np.zeros(5)

@@ -905,16 +905,20 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   const int64_t tot = n_pts * ns;
   kmap_kernel<<<(int)std::min<int64_t>((tot + 255) / 256, 8192), 256, 0, st>>>(
       d.y, n_pts, c->grid.n_dim, d.subs, ns, d.dim_off, d.yloc, d.hash, d.hash_off, d.hash_cap, d.kmap, d.pstat);
+  ++c->launches;
   CK(cudaGetLastError());
   group_kernel<<<ns, 256, 0, st>>>(d.kmap, n_pts, ns, d.subs, d.loc_off, d.grp_count, d.grp_start, d.grp_pts,
                                    c->ws_pts, d.tiles, c->max_tiles, d.n_tiles);
+  ++c->launches;
   stokes_group_kernel<<<64, 256, 0, st>>>(n_pts, ns, d.grp_pts, c->ws_pts, d.tiles, c->max_tiles, d.n_tiles);
+  ++c->launches;
   CK(cudaGetLastError());
   IfaceArgs a = make_args(c, n_pts);
   CK(cudaEventRecord(c->ev[1], st));
   const int warps_per_block = 8;
   const int ublocks = (int)((n_pts + warps_per_block - 1) / warps_per_block);
   init_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a);
+  ++c->launches;
   CK(cudaGetLastError());
   int maxR = (int)c->stokes.dofs.size();
   for (const HostSub& S : c->subs) maxR = std::max(maxR, (int)S.dofs.size());
@@ -926,11 +930,14 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   for (; it < max_it;) {
     for (int q = 0; q < chunk && it < max_it; ++q, ++it) {
       matvec_kernel<<<mgrid, 256, smv, st>>>(a, d.active + 2);
+      ++c->launches;
       update_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, it, rtol);
+      ++c->launches;
     }
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(d.active, 0, sizeof(int), st));
     count_active<<<std::min(1024, (int)((n_pts + 255) / 256)), 256, 0, st>>>(d.pstat, n_pts, d.active);
+    ++c->launches;
     int h_active = 0;
     CK(cudaMemcpyAsync(&h_active, d.active, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -939,9 +946,11 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   c->cg_iters_run = it;
   CK(cudaEventRecord(c->ev[2], st));
   finish_status<<<std::min(1024, (int)((n_pts + 255) / 256)), 256, 0, st>>>(d.pstat, n_pts, max_it, nullptr);
+  ++c->launches;
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(d.active + 1, 0, sizeof(int), st));
   count_failed<<<std::min(1024, (int)((n_pts + 255) / 256)), 256, 0, st>>>(d.pstat, n_pts, d.active + 1);
+  ++c->launches;
   int h_flags[4] = {0, 0, 0, 0};
   CK(cudaMemcpyAsync(h_flags, d.active, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -986,26 +995,34 @@ sfb_status moments_accumulate_device(sfb_ctx* c, int64_t n_pts) {
   if (first) {
     m.mode = 0;
     darcy_moments_kernel<<<dim3(row_tiles, ns, 1), kMomT, smd, st>>>(m);
+    ++c->launches;
     CK(cudaGetLastError());
   }
   m.mode = 1;
   darcy_moments_kernel<<<dim3(row_tiles, ns, m.n_chunks), kMomT, smd, st>>>(m);
+  ++c->launches;
   CK(cudaGetLastError());
   int max_local = 1;
   for (int nl : c->n_local) max_local = std::max(max_local, nl);
   group_moments_kernel<<<dim3(max_local, ns, kGChunks), 256, 0, st>>>(m, d.gmom_part);
+  ++c->launches;
   group_moments_reduce<<<dim3(max_local, ns), 256, 0, st>>>(m, d.gmom_part);
+  ++c->launches;
   const size_t smb = sizeof(double) * ((size_t)maxC * maxC + 2 * (size_t)maxC + (size_t)maxC * kBigT);
   CK(cudaFuncSetAttribute(bigroup_moments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
   bigroup_moments_kernel<<<dim3(row_tiles, ns), kBigT, smb, st>>>(m, m.n_chunks);
+  ++c->launches;
   CK(cudaGetLastError());
   reduce_partials<<<256, 256, 0, st>>>(d.mom_part, m.n_chunks + 1, m.len_d, d.mom + m.len_d, d.mom + 2 * m.len_d);
+  ++c->launches;
   CK(cudaEventRecord(c->ev[4], st));
   const int Cs = (int)c->stokes.dofs.size() + 1;
   stokes_cov_kernel<<<Cs, 128, 0, st>>>(m.ia, d.w, first, d.st_c0, d.st_m, d.st_M);
+  ++c->launches;
   CK(cudaGetLastError());
   c->mom_shift_set = true;
   weight_sum<<<1, 32, 0, st>>>(d.w, n_pts, d.mom_w);
+  ++c->launches;
   CK(cudaGetLastError());
   CK(cudaEventRecord(c->ev[5], st));
   return SFB_OK;
@@ -1019,12 +1036,14 @@ sfb_status moments_finalize_device(sfb_ctx* c, int field, double* mean_d, double
     const int64_t off = field == 0 ? 0 : c->mom_len[0];
     finalize_darcy<<<256, 256, 0, c->stream>>>(d.mom, d.mom + len_d, d.mom + 2 * len_d, off, c->mom_len[field],
                                                d.mom_w, mean_d, var_d);
+    ++c->launches;
   } else {
     const int Cs = (int)c->stokes.dofs.size() + 1;
     const double* U = field == 2 ? d.s_U : d.s_P;
     const int64_t n = c->mom_len[field];
     finalize_stokes<<<(int)((n * 32 + 255) / 256), 256, 0, c->stream>>>(U, n, Cs, d.st_c0, d.st_m, d.st_M,
                                                                           d.mom_w, mean_d, var_d);
+    ++c->launches;
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return SFB_ERR_CUDA; }

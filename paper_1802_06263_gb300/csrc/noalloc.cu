@@ -159,6 +159,7 @@ extern "C" sfb_status sfb_build_basis_item_noalloc(sfb_ctx* c, int32_t sub, int3
   if (prec == SFB_FP64) NA_CK(launch_basis_fp64(a, nx, C, st));
   else NA_CK(launch_basis_mixed(a, nx, C, prec == SFB_MIXED ? a.max_refine : 0, st));
   NA_CK(launch_flux_epilogue(a, R, st));
+  c->launches += 2;
   NA_CK(cudaMemcpyAsync(phi_out, d_phi, sizeof(double) * R * R, cudaMemcpyDefault, st));
   if (g_out) NA_CK(cudaMemcpyAsync(g_out, d_phi + (size_t)R * R, sizeof(double) * R, cudaMemcpyDefault, st));
   int status = 0;

@@ -139,6 +139,7 @@ struct sfb_ctx {
   bool kl_done = false, coll_done = false, basis_done = false;
   int basis_prec = -1;
   int64_t n_solved = 0;
+  int64_t launches = 0;   // kernels launched by this context
   // collocation
   sfb::Grid grid;
   std::vector<std::vector<double>> loc_y;  // per region [n_local][nt]

@@ -672,7 +672,11 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   if (prec == SFB_FP64) e = launch_basis_fp64(a, c->max_nx, c->max_cols, st);
   else e = launch_basis_mixed(a, c->max_nx, c->max_cols, prec == SFB_MIXED ? a.max_refine : 0, st);
   if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_fail(c, e, "basis kernel"); }
+  cudaEvent_t ek;
+  SFB_CUDA(cudaEventCreate(&ek), "event");
+  SFB_CUDA(cudaEventRecord(ek, st), "event");
   e = launch_flux_epilogue(a, c->max_R, st);
+  c->launches += 2;
   if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_fail(c, e, "flux epilogue"); }
   SFB_CUDA(cudaEventRecord(e1, st), "event");
   std::vector<int> status(n), nref(n);
@@ -685,10 +689,12 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   SFB_CUDA(cudaMemcpyAsync(est.data(), d.errest, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "stats");
   SFB_CUDA(cudaMemcpyAsync(cyc.data(), d.cycles, sizeof(long long) * 4 * n, cudaMemcpyDeviceToHost, st), "stats");
   SFB_CUDA(cudaStreamSynchronize(st), "basis build");
-  float ms = 0.f;
+  float ms = 0.f, kms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventElapsedTime(&kms, e0, ek);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  cudaEventDestroy(ek);
   int any = 0, n_nc = 0;
   for (int i = 0; i < n; ++i) { any |= status[i]; n_nc += (status[i] & ST_NOT_CONVERGED) != 0; }
   if (stats) {
@@ -707,6 +713,7 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
       stats->phase_cycles[q] = n ? acc / n : 0.0;
     }
     stats->ms = ms;
+    stats->kernel_ms = kms;
   }
   c->basis_done = true;
   c->basis_prec = prec;
@@ -783,6 +790,12 @@ sfb_status sfb_moments(sfb_ctx* c, int32_t field, double* mean_out, double* var_
   if (mean_out) SFB_CUDA(cudaMemcpyAsync(mean_out, c->dev.fin, sizeof(double) * n, cudaMemcpyDefault, c->stream), "copy");
   if (var_out) SFB_CUDA(cudaMemcpyAsync(var_out, c->dev.fin + n, sizeof(double) * n, cudaMemcpyDefault, c->stream), "copy");
   SFB_CUDA(cudaStreamSynchronize(c->stream), "moments");
+  return SFB_OK;
+}
+
+sfb_status sfb_launch_count(const sfb_ctx* c, int64_t* n) {
+  if (!c || !n) return SFB_ERR_ARG;
+  *n = c->launches;
   return SFB_OK;
 }
 

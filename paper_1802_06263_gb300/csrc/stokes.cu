@@ -226,32 +226,40 @@ cudaError_t stokes_solve_device(sfb_ctx* c) {
   const int64_t nnz = (int64_t)S.tr_val.size();
   scatter_triplets<<<(int)std::min<int64_t>((nnz + 255) / 256, 4096), 256, 0, st>>>(d.s_mat, n, d.s_tr_row,
                                                                                     d.s_tr_col, d.s_tr_val, nnz);
+  ++c->launches;
   CK(cudaGetLastError());
   for (int j0 = 0; j0 < n; j0 += kNB) {
     const int jb = std::min(kNB, n - j0);
     lu_panel<<<1, 1024, 0, st>>>(d.s_mat, n, j0, jb, d.s_piv, d.s_status);
+    ++c->launches;
     lu_swap<<<(n + 255) / 256, 256, 0, st>>>(d.s_mat, n, j0, jb, d.s_piv);
+    ++c->launches;
     const int rest = n - j0 - jb;
     if (rest > 0) {
       double* A11 = d.s_mat + (int64_t)j0 * n + j0;
       trsm_unit_lower<<<(rest + 127) / 128, 128, 0, st>>>(A11, n, A11 + jb, n, jb, rest);
+      ++c->launches;
       dim3 grid((rest + 63) / 64, (rest + 63) / 64);
       gemm_sub<<<grid, 256, 0, st>>>(A11 + (int64_t)jb * n, n, A11 + jb, n, A11 + (int64_t)jb * n + jb, n, rest,
                                       rest, jb);
+      ++c->launches;
     }
     CK(cudaGetLastError());
   }
   // solve: P L U X = B
   apply_pivots<<<(Cs + 63) / 64, 64, 0, st>>>(d.s_rhs, Cs, n, Cs, d.s_piv);
+  ++c->launches;
   for (int j0 = 0; j0 < n; j0 += kNB) {
     const int jb = std::min(kNB, n - j0);
     double* A11 = d.s_mat + (int64_t)j0 * n + j0;
     double* B1 = d.s_rhs + (int64_t)j0 * Cs;
     trsm_unit_lower<<<(Cs + 63) / 64, 64, 0, st>>>(A11, n, B1, Cs, jb, Cs);
+    ++c->launches;
     const int rest = n - j0 - jb;
     if (rest > 0) {
       dim3 grid((Cs + 63) / 64, (rest + 63) / 64);
       gemm_sub<<<grid, 256, 0, st>>>(A11 + (int64_t)jb * n, n, B1, Cs, B1 + (int64_t)jb * Cs, Cs, rest, Cs, jb);
+      ++c->launches;
     }
   }
   for (int j0 = ((n - 1) / kNB) * kNB; j0 >= 0; j0 -= kNB) {
@@ -259,15 +267,20 @@ cudaError_t stokes_solve_device(sfb_ctx* c) {
     double* A11 = d.s_mat + (int64_t)j0 * n + j0;
     double* B1 = d.s_rhs + (int64_t)j0 * Cs;
     trsm_upper<<<(Cs + 63) / 64, 64, 0, st>>>(A11, n, B1, Cs, jb, Cs);
+    ++c->launches;
     if (j0 > 0) {
       dim3 grid((Cs + 63) / 64, (j0 + 63) / 64);
       gemm_sub<<<grid, 256, 0, st>>>(d.s_mat + j0, n, B1, Cs, d.s_rhs, Cs, j0, Cs, jb);
+      ++c->launches;
     }
   }
   CK(cudaGetLastError());
   expand_solution<<<256, 256, 0, st>>>(d.s_rhs, Cs, n, d.s_free_to_full, S.n_u, d.s_dir, d.s_U, d.s_P, S.n_p);
+  ++c->launches;
   expand_free<<<256, 256, 0, st>>>(d.s_rhs, Cs, n, d.s_free_to_full, S.n_u, d.s_U, d.s_P);
+  ++c->launches;
   stokes_flux<<<64, 256, 0, st>>>(d.s_nb, d.s_nb_node, (int)S.nb_node.size(), Rs, d.s_U, S.n_nodes, d.s_phi);
+  ++c->launches;
   CK(cudaGetLastError());
 #undef CK
   return cudaSuccess;
