@@ -167,13 +167,18 @@ def run_ours(args):
     it_d = torch.empty(n_pts, dtype=torch.int32, device="cuda")
     rtol, max_it = 1e-10, 2000
 
+    def krylov(prec):
+        # the mixed form runs the interface CG on FP32 products with FP64
+        # residual replacement; the FP64 form runs plain FP64 CG
+        return sfb.CG_MIXED if prec == sfb.MIXED else sfb.CG
+
     def step(prec):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         ev[0].record(stream)
         st = s.build_basis(prec)
         ev[1].record(stream)
         s.moments_reset()
-        s.solve(yd, wd, rtol, max_it, lam_d, it_d)
+        s.solve(yd, wd, rtol, max_it, lam_d, it_d, krylov=krylov(prec))
         ev[2].record(stream)
         ev[3].record(stream)
         return st, ev
@@ -238,7 +243,7 @@ def run_ours(args):
     for _ in range(args.steps):
         s.build_basis(sfb.MIXED)
         s.moments_reset()
-        s.solve(y_h, w_h, rtol, max_it, lam_h, it_h)
+        s.solve(y_h, w_h, rtol, max_it, lam_h, it_h, krylov=sfb.CG_MIXED)
         mom_bytes = 0
         for f in sfb.FIELDS:
             m, v = s.moments(f)

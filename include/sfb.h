@@ -60,7 +60,17 @@ typedef enum {
   SFB_FP32_NOREFINE = 2  /* FP32 factor/solve only: diagnostics of the unrefined error */
 } sfb_precision;
 
-typedef enum { SFB_CG = 0 } sfb_krylov;
+/* Interface Krylov solver (Section 5.4 Step 5, reading of Eq. 5.10 as an SPD
+ * coefficient system).
+ * SFB_CG:       CG in FP64 throughout.
+ * SFB_CG_MIXED: CG whose products S p use the bases rounded to FP32, with FP64
+ *               inner products, updates and iterates; every cg_reliable_every
+ *               iterations, and before a point is declared converged, the
+ *               residual is replaced by the FP64 residual g - S lambda, so the
+ *               stopping test ||g - S lambda|| <= rtol ||g|| holds in FP64. Not in
+ *               the paper: an operator-precision choice for GPUs whose FP64 rate
+ *               is a small fraction of FP32. */
+typedef enum { SFB_CG = 0, SFB_CG_MIXED = 1 } sfb_krylov;
 
 typedef enum {
   SFB_FIELD_DARCY_P = 0,     /* cell pressures, subdomain by subdomain, c = iy*nx+ix    */
@@ -185,7 +195,8 @@ sfb_status sfb_get_basis(sfb_ctx* ctx, int32_t sub, int32_t k, double* phi, doub
  * ||r|| <= rtol ||g||, recovery and accumulation of the moments. Outputs
  * (nullable, host or device): lambda_out [n_pts x n_lambda], iters_out
  * [n_pts] (negative: not converged). Returns SFB_ERR_NOT_CONVERGED with all
- * outputs filled if a point did not converge within max_it. */
+ * outputs filled if a point did not converge within max_it. An empty batch
+ * (n_pts = 0, y and w may be NULL) returns SFB_OK and changes nothing. */
 sfb_status sfb_interface_solve_batch(sfb_ctx* ctx, const double* y, const double* w, int64_t n_pts,
                                      int32_t krylov, double rtol, int32_t max_it,
                                      double* lambda_out, int32_t* iters_out);
@@ -227,6 +238,8 @@ sfb_status sfb_build_basis_item_noalloc(sfb_ctx* ctx, int32_t sub, int32_t k, in
  *                    error of X is below this (default 1e-10);
  *   "refine_max"     mixed form: at most this many FP64 residual passes (8);
  *   "cg_check_every" CG iterations between convergence checks on the host (8);
+ *   "cg_reliable_every"  SFB_CG_MIXED: iterations between FP64 residual
+ *                    replacements of every iterating point (16);
  *   "moments_group_factor"  groups of more than factor * (R+1) points enter
  *                    the moments through their coefficient second moments,
  *                    smaller ones point by point; 0 = always point by point (2).

@@ -19,6 +19,7 @@ from ._build import LIB as _LIB_PATH, build  # noqa: F401
 SFB_OK = 0
 SFB_ERR_NOT_CONVERGED = 6
 FP64, MIXED, FP32_NOREFINE = 0, 1, 2
+CG, CG_MIXED = 0, 1
 FIELDS = {"darcy_p": 0, "darcy_flux": 1, "stokes_u": 2, "stokes_p": 3}
 STATUS = {0: "OK", 1: "ARG", 2: "STATE", 3: "CUDA", 4: "WORKSPACE", 5: "NONFINITE",
           6: "NOT_CONVERGED", 7: "NOT_SPD", 8: "UNSUPPORTED", 9: "TIMEOUT"}
@@ -295,23 +296,24 @@ class Solver:
             self._check(rc)
         return rc
 
-    def solve(self, y, w, rtol=1e-10, max_it=1000, lam_out=None, iters_out=None, check=True):
+    def solve(self, y, w, rtol=1e-10, max_it=1000, lam_out=None, iters_out=None, check=True, krylov=CG):
         """Interface CG for a batch of points (host numpy or device torch
-        arrays); outputs go to the given buffers (host or device)."""
+        arrays); outputs go to the given buffers (host or device). ``krylov``
+        is CG (FP64) or CG_MIXED (FP32 products, FP64 residuals)."""
         y = np.ascontiguousarray(y, dtype=np.float64) if isinstance(y, np.ndarray) else y
         w = np.ascontiguousarray(w, dtype=np.float64) if isinstance(w, np.ndarray) else w
         n = int(y.shape[0])
-        rc = self.lib.sfb_interface_solve_batch(self.h, ctypes.c_void_p(_ptr(y)), ctypes.c_void_p(_ptr(w)), n, 0,
+        rc = self.lib.sfb_interface_solve_batch(self.h, ctypes.c_void_p(_ptr(y)), ctypes.c_void_p(_ptr(w)), n, krylov,
                                                 rtol, max_it, ctypes.c_void_p(_ptr(lam_out)),
                                                 ctypes.c_void_p(_ptr(iters_out)))
         if check and rc not in (SFB_OK,):
             self._check(rc)
         return rc
 
-    def solve_host(self, y, w, rtol=1e-10, max_it=1000, check=True):
+    def solve_host(self, y, w, rtol=1e-10, max_it=1000, check=True, krylov=CG):
         lam = np.zeros((len(y), self.n_lambda))
         it = np.zeros(len(y), dtype=np.int32)
-        rc = self.solve(y, w, rtol, max_it, lam, it, check=check)
+        rc = self.solve(y, w, rtol, max_it, lam, it, check=check, krylov=krylov)
         return lam, it, rc
 
     def moments(self, field):

@@ -720,8 +720,10 @@ __global__ void flux_epilogue_kernel(BasisArgs a) {
       const double pj = (j < R) ? P[(int64_t)f * R + j] : 0.0;
       acc += pl * t * (X[(int64_t)j * nc + cell] - pj);
     }
-    if (j < R) phi[l * R + j] = -acc;
-    else phi[R * R + l] = acc;
+    const int64_t o = j < R ? (int64_t)l * R + j : (int64_t)R * R + l;
+    const double v = j < R ? -acc : acc;
+    phi[o] = v;
+    if (a.phi32) a.phi32[off.phi + o] = (float)v;
   }
 }
 

@@ -142,6 +142,8 @@ struct IfaceArgs {
   const ItemOff* off;
   const double* phi;    // Darcy basis store
   const double* s_phi;  // Stokes basis
+  const float* phi32;   // the same, rounded to FP32 (operator of the mixed CG)
+  const float* s_phi32;
   int Rs;
   const int64_t* gdof;  // Darcy local -> global
   const int64_t* sgdof; // Stokes local -> global
@@ -170,6 +172,34 @@ __device__ __forceinline__ const double* unit_phi(const IfaceArgs& a, int u, int
   const SubDev& S = a.subs[u];
   R = S.R;
   return a.phi + a.off[S.item0 + k].phi;
+}
+
+template <typename T>
+__device__ __forceinline__ const T* unit_phi_t(const IfaceArgs& a, int u, int k, int& R);
+template <>
+__device__ __forceinline__ const double* unit_phi_t<double>(const IfaceArgs& a, int u, int k, int& R) {
+  return unit_phi(a, u, k, R);
+}
+template <>
+__device__ __forceinline__ const float* unit_phi_t<float>(const IfaceArgs& a, int u, int k, int& R) {
+  if (u == a.ns) { R = a.Rs; return a.s_phi32; }
+  const SubDev& S = a.subs[u];
+  R = S.R;
+  return a.phi32 + a.off[S.item0 + k].phi;
+}
+
+// Point states (pstat): 0 iterating; it > 0 converged after `it` iterations;
+// -it stopped without convergence; kBadIdx a global point whose projection is
+// not a local realization. The mixed CG marks a point kPending | it when its
+// recursive residual meets the tolerance; an FP64 residual then confirms it
+// (converged) or sends it back to iterating.
+constexpr int kPending = 0x20000000;
+constexpr int kBadIdx = 0x40000000;
+__device__ __forceinline__ bool is_pending(int s) { return (s & (kPending | kBadIdx)) == kPending; }
+// Point selection of a product: 0 iterating points, 1 iterating and pending
+// points, 2 pending points only.
+__device__ __forceinline__ bool selected(int s, int sel) {
+  return sel == 0 ? s == 0 : (sel == 1 ? (s == 0 || is_pending(s)) : is_pending(s));
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -212,12 +242,17 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Y[l][ybase_u + :] = Phi_u^k (R_u p_l) for the (active) points of one tile of
-// up to kTG points that share the stored basis Phi_u^k. Phi arrives in shared
-// memory by one bulk copy (mbarrier completion, bounded wait); the product is
-// computed in FP64 with 2 x 4 register tiles (two rows of Phi, four points).
-__global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, int* err) {
-  extern __shared__ __align__(16) double smv[];
+// Y[l][ybase_u + :] = Phi_u^k (R_u v_l) for the selected points of one tile
+// of up to kTG points that share the stored basis Phi_u^k. Phi arrives in
+// shared memory by one bulk copy (mbarrier completion, bounded wait); the
+// product runs in T (FP64, or FP32 on the rounded copy of Phi for the inner
+// products of the mixed CG) with 2 x 4 register tiles (two rows of Phi, four
+// points). The bulk copy rounds R*R*sizeof(T) up to 16 bytes; the extra bytes
+// lie inside the same item (its g block follows Phi).
+template <typename T>
+__global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, const double* __restrict__ vin, int sel,
+                                                     int* err) {
+  extern __shared__ __align__(16) unsigned char smv_raw[];
   __shared__ __align__(8) uint64_t bar;
   const int u = blockIdx.y;
   const int t = blockIdx.x;
@@ -225,15 +260,15 @@ __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, int* err) {
   const int* tl = a.tiles + 3 * ((int64_t)u * a.max_tiles + t);
   const int k = tl[0], q0 = tl[1], cntp = tl[2];
   const int* pts = a.grp_pts + (int64_t)u * a.pts_ld + q0;
-  const int act = threadIdx.x < cntp ? (a.pstat[pts[threadIdx.x]] == 0) : 0;
-  if (!__syncthreads_or(act)) return;  // every point of the tile has converged
+  const int act = threadIdx.x < cntp ? selected(a.pstat[pts[threadIdx.x]], sel) : 0;
+  if (!__syncthreads_or(act)) return;  // no point of the tile is selected
   int R;
-  const double* ph = unit_phi(a, u, k, R);
+  const T* ph = unit_phi_t<T>(a, u, k, R);
   const int64_t* gd = u == a.ns ? a.sgdof : a.gdof + a.subs[u].gdof_off;
-  const int rr2 = (R * R + 1) & ~1;
-  double* Ph = smv;            // [R][R]
-  double* Pv = smv + rr2;      // [R][kTG + 1]
-  const uint32_t bytes = (uint32_t)((R * R * 8 + 15) & ~15);
+  const int rr4 = (R * R + 3) & ~3;
+  T* Ph = reinterpret_cast<T*>(smv_raw);   // [R][R]
+  T* Pv = Ph + rr4;                        // [R][kTG + 1]
+  const uint32_t bytes = (uint32_t)((R * R * (int)sizeof(T) + 15) & ~15);
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -250,9 +285,9 @@ __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, int* err) {
     double v = 0.0;
     if (q < cntp) {
       const int64_t l = pts[q];
-      if (a.pstat[l] == 0) v = a.p[l * a.n_lambda + gd[i]];
+      if (selected(a.pstat[l], sel)) v = vin[l * a.n_lambda + gd[i]];
     }
-    Pv[i * (kTG + 1) + q] = v;
+    Pv[i * (kTG + 1) + q] = T(v);
   }
   uint32_t ok = 0;
   for (int it = 0; it < (1 << 22) && !ok; ++it)
@@ -277,12 +312,12 @@ __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, int* err) {
   for (int tt = threadIdx.x; tt < nrp * (kTG / 4); tt += blockDim.x) {
     const int r0 = (tt / (kTG / 4)) * 2, c0 = (tt % (kTG / 4)) * 4;
     const bool two = r0 + 1 < R;
-    double acc[2][4] = {};
-    const double* p0 = Ph + r0 * R;
-    const double* p1 = Ph + (two ? r0 + 1 : r0) * R;
+    T acc[2][4] = {};
+    const T* p0 = Ph + r0 * R;
+    const T* p1 = Ph + (two ? r0 + 1 : r0) * R;
     for (int j = 0; j < R; ++j) {
-      const double f0 = p0[j], f1 = p1[j];
-      const double* v = Pv + j * (kTG + 1) + c0;
+      const T f0 = p0[j], f1 = p1[j];
+      const T* v = Pv + j * (kTG + 1) + c0;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         acc[0][q] = fma(f0, v[q], acc[0][q]);
@@ -293,16 +328,16 @@ __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, int* err) {
     for (int q = 0; q < 4; ++q) {
       if (c0 + q >= cntp) break;
       const int64_t l = pts[c0 + q];
-      if (a.pstat[l] != 0) continue;
+      if (!selected(a.pstat[l], sel)) continue;
       double* y = a.Y + l * a.NY + a.ybase[u];
-      y[r0] = acc[0][q];
-      if (two) y[r0 + 1] = acc[1][q];
+      y[r0] = (double)acc[0][q];
+      if (two) y[r0 + 1] = (double)acc[1][q];
     }
   }
 }
 
 // q = S p from the per-unit products, then the CG update; one warp per point.
-__global__ void update_kernel(IfaceArgs a, int it, double rtol) {
+__global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed) {
   const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (l >= a.n_pts) return;
@@ -338,7 +373,49 @@ __global__ void update_kernel(IfaceArgs a, int it, double rtol) {
   __syncwarp();
   if (lane == 0) {
     a.rr[l] = rn;
-    if (done) a.pstat[l] = pq > 0.0 ? it + 1 : -(it + 1);
+    if (done) a.pstat[l] = mixed ? (kPending | (it + 1)) : (pq > 0.0 ? it + 1 : -(it + 1));
+  }
+}
+
+// FP64 residual replacement of the mixed CG, one warp per selected point, on
+// the FP64 products Y = Phi (R lambda): r = g - S lambda. A pending point is
+// confirmed when ||r|| <= rtol ||g||, otherwise it restarts from r (p = r);
+// an iterating point continues with the replaced residual (same p).
+__global__ void reliable_kernel(IfaceArgs a, int sel, double rtol, int it) {
+  const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (l >= a.n_pts) return;
+  const int s = a.pstat[l];
+  if (!selected(s, sel)) return;
+  const double* Yl = a.Y + l * a.NY;
+  double* rl = a.r + l * a.n_lambda;
+  double rn = 0.0;
+  for (int64_t d = lane; d < a.n_lambda; d += 32) {
+    double g = 0.0, q = 0.0;
+    for (int side = 0; side < 2; ++side) {
+      const int u = a.ldof[4 * d + 2 * side], loc = a.ldof[4 * d + 2 * side + 1];
+      const int k = u < a.ns ? a.kmap[l * a.ns + u] : 0;
+      int R;
+      const double* ph = unit_phi(a, u, k, R);
+      g += ph[R * R + loc];
+      q += Yl[a.ybase[u] + loc];
+    }
+    const double rv = g - q;
+    rl[d] = rv;
+    rn += rv * rv;
+  }
+  rn = warp_sum(rn);
+  const bool conv = sqrt(rn) <= rtol * a.gn[l];
+  const bool restart = is_pending(s) && !conv;
+  if (restart) {
+    double* pl = a.p + l * a.n_lambda;
+    for (int64_t d = lane; d < a.n_lambda; d += 32) pl[d] = rl[d];
+  }
+  __syncwarp();
+  if (lane == 0) {
+    a.rr[l] = rn;
+    if (conv) a.pstat[l] = is_pending(s) ? (s & ~kPending) : it;
+    else if (restart) a.pstat[l] = 0;
   }
 }
 
@@ -382,7 +459,7 @@ struct MomArgs {
   int rt;                   // grid rows per CTA
   int n_chunks;
   // groups larger than big_factor * (R+1) points go through their coefficient moments
-  int big_factor;
+  double big_factor;
   const int* grp_start;     // per (subdomain, local realization): first sorted point
   const int* grp_end;       // ... and one past the last
   const int64_t* loc_off;   // per subdomain offset into the group arrays
@@ -392,7 +469,7 @@ struct MomArgs {
 
 __device__ __forceinline__ bool big_group(const MomArgs& m, const SubDev& S, int s, int k) {
   const int64_t g = m.loc_off[s] + k;
-  return m.big_factor > 0 && (m.grp_end[g] - m.grp_start[g]) > m.big_factor * (S.R + 1);
+  return m.big_factor > 0.0 && (double)(m.grp_end[g] - m.grp_start[g]) > m.big_factor * (S.R + 1);
 }
 
 constexpr int kMomT = 256;   // threads of the Darcy moments kernel
@@ -875,6 +952,7 @@ static IfaceArgs make_args(sfb_ctx* c, int64_t n_pts) {
   Dev& d = c->dev;
   IfaceArgs a;
   a.subs = d.subs; a.ns = (int)c->subs.size(); a.off = d.off; a.phi = d.phi; a.s_phi = d.s_phi;
+  a.phi32 = d.phi32; a.s_phi32 = d.s_phi32;
   a.Rs = (int)c->stokes.dofs.size(); a.gdof = d.gdof; a.sgdof = d.s_gdof; a.ybase = d.ybase; a.NY = c->NY;
   a.ldof = d.ldof; a.n_lambda = c->n_lambda; a.kmap = d.kmap; a.grp_pts = d.grp_pts; a.pts_ld = c->ws_pts;
   a.tiles = d.tiles; a.max_tiles = c->max_tiles; a.n_tiles = d.n_tiles; a.lam = d.lam; a.r = d.r; a.p = d.p;
@@ -890,7 +968,7 @@ __global__ void count_failed(const int* pstat, int64_t n, int* out) {
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
-sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it, int* n_failed) {
+sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it, int krylov, int* n_failed) {
   Dev& d = c->dev;
   cudaStream_t st = c->stream;
   const int ns = (int)c->subs.size();
@@ -922,16 +1000,31 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   CK(cudaGetLastError());
   int maxR = (int)c->stokes.dofs.size();
   for (const HostSub& S : c->subs) maxR = std::max(maxR, (int)S.dofs.size());
-  const size_t smv = sizeof(double) * ((size_t)((maxR * maxR + 1) & ~1) + (size_t)(kTG + 1) * maxR);
-  CK(cudaFuncSetAttribute(matvec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv));
+  const size_t smv = sizeof(double) * ((size_t)((maxR * maxR + 3) & ~3) + (size_t)(kTG + 1) * maxR);
+  const size_t smv32 = sizeof(float) * ((size_t)((maxR * maxR + 3) & ~3) + (size_t)(kTG + 1) * maxR);
+  CK(cudaFuncSetAttribute(matvec_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv));
+  CK(cudaFuncSetAttribute(matvec_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv32));
   dim3 mgrid(c->max_tiles, nu);
   const int chunk = c->opt_cg_chunk;
-  int it = 0;
+  const bool mixed = krylov == SFB_CG_MIXED;
+  int it = 0, since_full = 0;
   for (; it < max_it;) {
     for (int q = 0; q < chunk && it < max_it; ++q, ++it) {
-      matvec_kernel<<<mgrid, 256, smv, st>>>(a, d.active + 2);
+      if (mixed) matvec_kernel<float><<<mgrid, 256, smv32, st>>>(a, d.p, 0, d.active + 2);
+      else matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.p, 0, d.active + 2);
       ++c->launches;
-      update_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, it, rtol);
+      update_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, it, rtol, mixed ? 1 : 0);
+      ++c->launches;
+      ++since_full;
+    }
+    if (mixed) {
+      // FP64 residuals: every iterating point once per reliable_every
+      // iterations, pending points at every check
+      const int sel = since_full >= c->opt_cg_reliable ? 1 : 2;
+      if (sel == 1) since_full = 0;
+      matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.lam, sel, d.active + 2);
+      ++c->launches;
+      reliable_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, sel, rtol, it);
       ++c->launches;
     }
     CK(cudaGetLastError());

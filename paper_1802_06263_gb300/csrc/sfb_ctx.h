@@ -60,6 +60,7 @@ struct Dev {
   void* G = nullptr;
   void* Z = nullptr;
   double* phi = nullptr;
+  float* phi32 = nullptr;    // FP32 copy of phi for the FP32 interface products
   double* D = nullptr;
   void* S = nullptr;
   double* errest = nullptr;
@@ -75,6 +76,7 @@ struct Dev {
   double* s_U = nullptr;     // [n_u][Cs]
   double* s_P = nullptr;     // [n_p][Cs]
   double* s_phi = nullptr;   // [Rs][Rs] then g [Rs]
+  float* s_phi32 = nullptr;  // FP32 copy of s_phi
   double* s_dir = nullptr;
   double* s_nb = nullptr;
   int* s_nb_node = nullptr;
@@ -166,7 +168,8 @@ struct sfb_ctx {
   double opt_refine_tol = 1e-10;
   int opt_refine_max = 8;
   int opt_cg_chunk = 8;
-  int opt_big_factor = 2;   // groups above this many times (R+1) points use coefficient moments
+  int opt_cg_reliable = 16;   // iterations between FP64 residual replacements (mixed CG)
+  double opt_big_factor = 2.0;   // groups above this many times (R+1) points use coefficient moments
   // device-time phase markers of the last interface solve (CUDA events)
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int cg_iters_run = 0;

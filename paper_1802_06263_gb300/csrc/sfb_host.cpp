@@ -14,7 +14,7 @@ namespace sfb {
 void stokes_assemble_host(sfb_ctx* c);
 size_t basis_smem_bytes(int prec_fp64, int max_nx, int max_cols);
 cudaError_t stokes_solve_device(sfb_ctx* c);
-sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it, int* n_failed);
+sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it, int krylov, int* n_failed);
 sfb_status moments_finalize_device(sfb_ctx* c, int field, double* mean_d, double* var_d);
 void build_hash_tables(sfb_ctx* c, std::vector<int>& table, std::vector<int64_t>& off, std::vector<int>& cap);
 sfb_status moments_accumulate_device(sfb_ctx* c, int64_t n_pts);
@@ -161,7 +161,7 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
       o.t = nT; nT += (int64_t)S.ny * (S.nx + 1) + (int64_t)(S.ny + 1) * S.nx;
       const int64_t npad = (S.nx + 7) & ~7;  // identity-padded block size of the factor
       o.g = nG; nG += (int64_t)S.ny * npad * npad;
-      o.phi = nPhi; nPhi += ((int64_t)R * R + R + 1) & ~int64_t(1);   // 16-byte aligned items
+      o.phi = nPhi; nPhi += ((int64_t)R * R + R + 3) & ~int64_t(3);   // 16-byte aligned in FP32 and FP64
       o.diag = nD; o.sc = nD; nD += nc;
       c->offs.push_back(o);
     }
@@ -188,6 +188,7 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   d.G = cv.take<char>(nG * gsz);
   d.Z = cv.take<char>(nZ * gsz);
   d.phi = cv.take<double>(nPhi);
+  d.phi32 = cv.take<float>(nPhi);
   d.D = cv.take<double>(nD);
   d.S = cv.take<char>(nD * gsz);
   d.status = cv.take<int>(n_items);
@@ -205,6 +206,7 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   d.s_U = cv.take<double>((size_t)St.n_u * Cs);
   d.s_P = cv.take<double>((size_t)St.n_p * Cs);
   d.s_phi = cv.take<double>((size_t)Rs * Rs + Rs);
+  d.s_phi32 = cv.take<float>(((size_t)Rs * Rs + Rs + 3) & ~size_t(3));
   d.s_dir = cv.take<double>(St.n_u);
   d.s_nb = cv.take<double>(St.nb.size());
   d.s_nb_node = cv.take<int>(St.nb_node.size());
@@ -659,7 +661,7 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   BasisArgs a;
   a.subs = d.subs; a.proj = d.proj; a.dofinfo = d.dofinfo; a.kl = d.kl; a.yloc = d.yloc;
   a.item_sub = d.item_sub; a.item_k = d.item_k; a.off = d.off; a.n_items = n;
-  a.X = d.X; a.T = d.T; a.G = d.G; a.Z = d.Z; a.S = d.S; a.phi = d.phi; a.D = d.D;
+  a.X = d.X; a.T = d.T; a.G = d.G; a.Z = d.Z; a.S = d.S; a.phi = d.phi; a.phi32 = d.phi32; a.D = d.D;
   a.status = d.status; a.resid = d.resid; a.corr1 = d.corr1; a.errest = d.errest; a.nref = d.nref;
   a.cycles = d.cycles;
   a.max_refine = c->opt_refine_max;
@@ -756,8 +758,10 @@ sfb_status sfb_interface_solve_batch(sfb_ctx* c, const double* y, const double* 
                                      double rtol, int32_t max_it, double* lambda_out, int32_t* iters_out) {
   if (!c) return SFB_ERR_ARG;
   if (!c->basis_done) return fail(c, SFB_ERR_STATE, "sfb_build_stochastic_basis must come first");
-  if (!y || !w || n_pts < 1 || krylov != SFB_CG || !(rtol > 0) || max_it < 1)
+  if (n_pts < 0 || (krylov != SFB_CG && krylov != SFB_CG_MIXED) || !(rtol > 0) || max_it < 1)
     return fail(c, SFB_ERR_ARG, "bad interface solve arguments");
+  if (n_pts == 0) return SFB_OK;  // an empty batch changes nothing
+  if (!y || !w) return fail(c, SFB_ERR_ARG, "bad interface solve arguments");
   if (n_pts > c->ws_pts) return fail(c, SFB_ERR_WORKSPACE, "batch larger than the workspace was sized for");
   Dev& d = c->dev;
   cudaStream_t st = c->stream;
@@ -766,7 +770,7 @@ sfb_status sfb_interface_solve_batch(sfb_ctx* c, const double* y, const double* 
       !host_or_device_copy(d.w, w, sizeof(double) * n_pts, st))
     return fail(c, SFB_ERR_CUDA, "copy of the points");
   int n_failed = 0;
-  sfb_status s = iface_solve_device(c, n_pts, rtol, max_it, &n_failed);
+  sfb_status s = iface_solve_device(c, n_pts, rtol, max_it, krylov, &n_failed);
   if (s != SFB_OK) return s;
   s = moments_accumulate_device(c, n_pts);
   if (s != SFB_OK) return s;
@@ -825,10 +829,13 @@ sfb_status sfb_set_option(sfb_ctx* c, const char* name, double value) {
     c->opt_refine_max = (int)value;
   } else if (n == "moments_group_factor") {
     if (!(value >= 0 && value <= 1e6)) return fail(c, SFB_ERR_ARG, "moments_group_factor must lie in [0, 1e6]");
-    c->opt_big_factor = (int)value;
+    c->opt_big_factor = value;
   } else if (n == "cg_check_every") {
     if (!(value >= 1 && value <= 1000)) return fail(c, SFB_ERR_ARG, "cg_check_every must lie in [1, 1000]");
     c->opt_cg_chunk = (int)value;
+  } else if (n == "cg_reliable_every") {
+    if (!(value >= 1 && value <= 1000)) return fail(c, SFB_ERR_ARG, "cg_reliable_every must lie in [1, 1000]");
+    c->opt_cg_reliable = (int)value;
   } else {
     return fail(c, SFB_ERR_ARG, "unknown option " + n);
   }

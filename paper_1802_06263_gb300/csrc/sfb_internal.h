@@ -43,7 +43,7 @@ struct ItemOff {
   int64_t t;    // T: x-faces [ny][nx+1] then y-faces [ny+1][nx] FP64 transmissibilities
   int64_t g;    // G: [ny][nx][nx] inverse Schur blocks (FP64 or FP32)
   int64_t z;    // Z: [R+1][n_cells] solve scratch (factor precision)
-  int64_t phi;  // Phi: [R][R] then g: [R]
+  int64_t phi;  // Phi: [R][R] then g: [R], padded to a multiple of 4 elements
   int64_t diag; // D: [n_cells] FP64 diagonal of A
   int64_t sc;   // S: [n_cells] diag(A)^{-1/2} in the factor precision
 };
@@ -64,6 +64,7 @@ struct BasisArgs {
   void* Z;                 // [R+1][n_cells] solve scratch in the factor precision
   void* S;                 // [n_cells] diagonal scaling in the factor precision
   double* phi;
+  float* phi32;            // Phi and g rounded to FP32 (same offsets)
   double* D;
   int* status;             // per item
   double* resid;           // per item: last relative residual ||B - A X|| / ||B||

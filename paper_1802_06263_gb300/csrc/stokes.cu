@@ -192,14 +192,16 @@ __global__ void expand_free(const double* sol, int Cs, int n_free, const int* fr
 
 // Phi_s[l][j] = -sum_b nb[b][l] U[(y, node_b)][j], g_s[l] = sum_b nb[b][l] U[(y, node_b)][Rs]
 __global__ void stokes_flux(const double* nb, const int* nb_node, int nbn, int Rs, const double* U, int n_nodes,
-                            double* phi) {
+                            double* phi, float* phi32) {
   const int Cs = Rs + 1;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Rs * Cs; e += gridDim.x * blockDim.x) {
     const int l = e / Cs, j = e % Cs;
     double acc = 0.0;
     for (int b = 0; b < nbn; ++b) acc += nb[b * Rs + l] * U[(int64_t)(n_nodes + nb_node[b]) * Cs + j];
-    if (j < Rs) phi[l * Rs + j] = -acc;
-    else phi[Rs * Rs + l] = acc;
+    const int o = j < Rs ? l * Rs + j : Rs * Rs + l;
+    const double v = j < Rs ? -acc : acc;
+    phi[o] = v;
+    phi32[o] = (float)v;
   }
 }
 
@@ -279,7 +281,8 @@ cudaError_t stokes_solve_device(sfb_ctx* c) {
   ++c->launches;
   expand_free<<<256, 256, 0, st>>>(d.s_rhs, Cs, n, d.s_free_to_full, S.n_u, d.s_U, d.s_P);
   ++c->launches;
-  stokes_flux<<<64, 256, 0, st>>>(d.s_nb, d.s_nb_node, (int)S.nb_node.size(), Rs, d.s_U, S.n_nodes, d.s_phi);
+  stokes_flux<<<64, 256, 0, st>>>(d.s_nb, d.s_nb_node, (int)S.nb_node.size(), Rs, d.s_U, S.n_nodes, d.s_phi,
+                                 d.s_phi32);
   ++c->launches;
   CK(cudaGetLastError());
 #undef CK

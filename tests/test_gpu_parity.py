@@ -46,12 +46,16 @@ def test_basis_parity(key, prec):
     print(key, prec, "worst basis rel err", worst, st)
 
 
+@pytest.mark.parametrize("krylov", [0, 1])
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("key", CASES)
-def test_interface_and_moments_parity(key, prec):
+def test_interface_and_moments_parity(key, prec, krylov):
+    """krylov 0: FP64 CG; 1: CG with FP32 products and FP64 residual
+    replacement, which must reach the same FP64 residual tolerance."""
     p, y, wt, lams, mom = oracle_case(key)
     s, _ = _solver(key, prec)
-    lam, it, rc = s.solve_host(y, wt, rtol=1e-14, max_it=5000, check=False)
+    rtol = 1e-14 if krylov == 0 else 1e-13
+    lam, it, rc = s.solve_host(y, wt, rtol=rtol, max_it=5000, check=False, krylov=krylov)
     assert np.all(it != 0)
     tol = TOL[prec]
     assert rel(lam, lams) < tol * 10
