@@ -431,7 +431,7 @@ __global__ void finish_status(int* pstat, int64_t n, int max_it, int* iters_out)
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x) {
     int s = pstat[l];
     if (s == 0) s = -max_it;
-    else if (s & 0x40000000) s = -max_it;
+    else if (s & (kBadIdx | kPending)) s = -max_it;
     pstat[l] = s;
     if (iters_out) iters_out[l] = s;
   }
