@@ -64,12 +64,14 @@ typedef enum {
  * coefficient system).
  * SFB_CG:       CG in FP64 throughout.
  * SFB_CG_MIXED: CG whose products S p use the bases rounded to FP32, with FP64
- *               inner products, updates and iterates; every cg_reliable_every
- *               iterations, and before a point is declared converged, the
- *               residual is replaced by the FP64 residual g - S lambda, so the
- *               stopping test ||g - S lambda|| <= rtol ||g|| holds in FP64. Not in
- *               the paper: an operator-precision choice for GPUs whose FP64 rate
- *               is a small fraction of FP32. */
+ *               inner products, updates and iterates. The recursive residual
+ *               is replaced by the FP64 residual g - S lambda whenever it has
+ *               dropped by cg_replace_ratio since the last replacement, and
+ *               before a point is declared converged, so the stopping test
+ *               ||g - S lambda|| <= rtol ||g|| holds in FP64 (residual
+ *               replacement in the manner of reliable-update Krylov methods).
+ *               Not in the paper: an operator-precision choice for GPUs whose
+ *               FP64 rate is a small fraction of FP32. */
 typedef enum { SFB_CG = 0, SFB_CG_MIXED = 1 } sfb_krylov;
 
 typedef enum {
@@ -238,8 +240,10 @@ sfb_status sfb_build_basis_item_noalloc(sfb_ctx* ctx, int32_t sub, int32_t k, in
  *                    error of X is below this (default 1e-10);
  *   "refine_max"     mixed form: at most this many FP64 residual passes (8);
  *   "cg_check_every" CG iterations between convergence checks on the host (8);
- *   "cg_reliable_every"  SFB_CG_MIXED: iterations between FP64 residual
- *                    replacements of every iterating point (16);
+ *   "cg_replace_ratio"  SFB_CG_MIXED: a point's residual is replaced by the
+ *                    FP64 residual at the next check once the recursive one
+ *                    has dropped by this factor since the last replacement,
+ *                    and the point pauses at a tenth of it (0.1);
  *   "moments_group_factor"  groups of more than factor * (R+1) points enter
  *                    the moments through their coefficient second moments,
  *                    smaller ones point by point; 0 = always point by point (2).

@@ -163,6 +163,8 @@ struct IfaceArgs {
   double* Y;
   double* rr;
   double* gn;
+  double* rlast;        // mixed CG: norm of the last FP64 residual
+  int* rflag;           // mixed CG: FP64 residual due at the next check
   int* pstat;
   int64_t n_pts;
 };
@@ -190,16 +192,17 @@ __device__ __forceinline__ const float* unit_phi_t<float>(const IfaceArgs& a, in
 
 // Point states (pstat): 0 iterating; it > 0 converged after `it` iterations;
 // -it stopped without convergence; kBadIdx a global point whose projection is
-// not a local realization. The mixed CG marks a point kPending | it when its
-// recursive residual meets the tolerance; an FP64 residual then confirms it
-// (converged) or sends it back to iterating.
+// not a local realization. The mixed CG pauses a point (kPending | it, plus
+// kRestart after a breakdown p.Sp <= 0) until its next FP64 residual.
+constexpr int kRestart = 0x10000000;
 constexpr int kPending = 0x20000000;
 constexpr int kBadIdx = 0x40000000;
+constexpr int kItMask = 0x0fffffff;
 __device__ __forceinline__ bool is_pending(int s) { return (s & (kPending | kBadIdx)) == kPending; }
-// Point selection of a product: 0 iterating points, 1 iterating and pending
-// points, 2 pending points only.
-__device__ __forceinline__ bool selected(int s, int sel) {
-  return sel == 0 ? s == 0 : (sel == 1 ? (s == 0 || is_pending(s)) : is_pending(s));
+// Point selection of a product: 0 iterating points; 1 points due for an FP64
+// residual (paused, or iterating with the replacement flag set).
+__device__ __forceinline__ bool selected(const IfaceArgs& a, int64_t l, int s, int sel) {
+  return sel == 0 ? s == 0 : (is_pending(s) || (s == 0 && a.rflag[l]));
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -232,6 +235,8 @@ __global__ void init_kernel(IfaceArgs a) {
   if (lane == 0) {
     a.rr[l] = s2;
     a.gn[l] = sqrt(s2);
+    a.rlast[l] = sqrt(s2);
+    a.rflag[l] = 0;
     int st = a.pstat[l] & 0x40000000;  // keep a bad-index mark
     if (!st && s2 == 0.0) st = 1;       // zero data: converged with lambda = 0
     a.pstat[l] = st;
@@ -260,7 +265,7 @@ __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, const double* 
   const int* tl = a.tiles + 3 * ((int64_t)u * a.max_tiles + t);
   const int k = tl[0], q0 = tl[1], cntp = tl[2];
   const int* pts = a.grp_pts + (int64_t)u * a.pts_ld + q0;
-  const int act = threadIdx.x < cntp ? selected(a.pstat[pts[threadIdx.x]], sel) : 0;
+  const int act = threadIdx.x < cntp ? selected(a, pts[threadIdx.x], a.pstat[pts[threadIdx.x]], sel) : 0;
   if (!__syncthreads_or(act)) return;  // no point of the tile is selected
   int R;
   const T* ph = unit_phi_t<T>(a, u, k, R);
@@ -285,7 +290,7 @@ __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, const double* 
     double v = 0.0;
     if (q < cntp) {
       const int64_t l = pts[q];
-      if (selected(a.pstat[l], sel)) v = vin[l * a.n_lambda + gd[i]];
+      if (selected(a, l, a.pstat[l], sel)) v = vin[l * a.n_lambda + gd[i]];
     }
     Pv[i * (kTG + 1) + q] = T(v);
   }
@@ -328,7 +333,7 @@ __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, const double* 
     for (int q = 0; q < 4; ++q) {
       if (c0 + q >= cntp) break;
       const int64_t l = pts[c0 + q];
-      if (!selected(a.pstat[l], sel)) continue;
+      if (!selected(a, l, a.pstat[l], sel)) continue;
       double* y = a.Y + l * a.NY + a.ybase[u];
       y[r0] = (double)acc[0][q];
       if (two) y[r0 + 1] = (double)acc[1][q];
@@ -337,7 +342,13 @@ __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, const double* 
 }
 
 // q = S p from the per-unit products, then the CG update; one warp per point.
-__global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed) {
+// Mixed CG (products from the FP32 bases): once the recursive residual falls
+// below replace_ratio times the last FP64 residual the point asks for an FP64
+// residual at the next check and keeps iterating; it pauses when it falls
+// below pause_ratio times that residual, or below the tolerance, so that the
+// recursive and the true residual never drift far apart before replacement.
+__global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed, double replace_ratio,
+                              double pause_ratio) {
   const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (l >= a.n_pts) return;
@@ -354,7 +365,8 @@ __global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed) {
   }
   pq = warp_sum(pq);
   const double rr = a.rr[l];
-  const double alpha = pq > 0.0 ? rr / pq : 0.0;
+  const bool brk = !(pq > 0.0);
+  const double alpha = brk ? 0.0 : rr / pq;
   double rn = 0.0;
   for (int64_t d = lane; d < a.n_lambda; d += 32) {
     const int ua = a.ldof[4 * d], la = a.ldof[4 * d + 1], ub = a.ldof[4 * d + 2], lb = a.ldof[4 * d + 3];
@@ -365,28 +377,38 @@ __global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed) {
     rn += rv * rv;
   }
   rn = warp_sum(rn);
-  const bool done = sqrt(rn) <= rtol * a.gn[l] || !(pq > 0.0);
-  if (!done) {
+  const double rnorm = sqrt(rn);
+  bool done, pause = false, flag = false;
+  if (mixed) {
+    done = false;
+    pause = brk || rnorm <= fmax(rtol * a.gn[l], pause_ratio * a.rlast[l]);
+    flag = rnorm <= replace_ratio * a.rlast[l];
+  } else {
+    done = rnorm <= rtol * a.gn[l] || brk;
+  }
+  if (!done && !brk) {
     const double beta = rn / rr;
     for (int64_t d = lane; d < a.n_lambda; d += 32) pl[d] = rl[d] + beta * pl[d];
   }
   __syncwarp();
   if (lane == 0) {
     a.rr[l] = rn;
-    if (done) a.pstat[l] = mixed ? (kPending | (it + 1)) : (pq > 0.0 ? it + 1 : -(it + 1));
+    if (done) a.pstat[l] = brk ? -(it + 1) : it + 1;
+    else if (pause) a.pstat[l] = kPending | (brk ? kRestart : 0) | (it + 1);
+    else if (flag) a.rflag[l] = 1;
   }
 }
 
-// FP64 residual replacement of the mixed CG, one warp per selected point, on
-// the FP64 products Y = Phi (R lambda): r = g - S lambda. A pending point is
-// confirmed when ||r|| <= rtol ||g||, otherwise it restarts from r (p = r);
-// an iterating point continues with the replaced residual (same p).
-__global__ void reliable_kernel(IfaceArgs a, int sel, double rtol, int it) {
+// FP64 residual replacement of the mixed CG, one warp per point due (paused
+// or flagged), on the FP64 products Y = Phi (R lambda): r = g - S lambda. The
+// point has converged if ||r|| <= rtol ||g||; otherwise it continues from the
+// replaced residual with the same direction p (p = r after a breakdown).
+__global__ void reliable_kernel(IfaceArgs a, double rtol, int it) {
   const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (l >= a.n_pts) return;
   const int s = a.pstat[l];
-  if (!selected(s, sel)) return;
+  if (!selected(a, l, s, 1)) return;
   const double* Yl = a.Y + l * a.NY;
   double* rl = a.r + l * a.n_lambda;
   double rn = 0.0;
@@ -406,16 +428,16 @@ __global__ void reliable_kernel(IfaceArgs a, int sel, double rtol, int it) {
   }
   rn = warp_sum(rn);
   const bool conv = sqrt(rn) <= rtol * a.gn[l];
-  const bool restart = is_pending(s) && !conv;
-  if (restart) {
+  if (!conv && (s & kRestart)) {
     double* pl = a.p + l * a.n_lambda;
     for (int64_t d = lane; d < a.n_lambda; d += 32) pl[d] = rl[d];
   }
   __syncwarp();
   if (lane == 0) {
+    a.rflag[l] = 0;
     a.rr[l] = rn;
-    if (conv) a.pstat[l] = is_pending(s) ? (s & ~kPending) : it;
-    else if (restart) a.pstat[l] = 0;
+    a.rlast[l] = sqrt(rn);
+    a.pstat[l] = conv ? (s != 0 ? (s & kItMask) : it) : 0;
   }
 }
 
@@ -956,7 +978,7 @@ static IfaceArgs make_args(sfb_ctx* c, int64_t n_pts) {
   a.Rs = (int)c->stokes.dofs.size(); a.gdof = d.gdof; a.sgdof = d.s_gdof; a.ybase = d.ybase; a.NY = c->NY;
   a.ldof = d.ldof; a.n_lambda = c->n_lambda; a.kmap = d.kmap; a.grp_pts = d.grp_pts; a.pts_ld = c->ws_pts;
   a.tiles = d.tiles; a.max_tiles = c->max_tiles; a.n_tiles = d.n_tiles; a.lam = d.lam; a.r = d.r; a.p = d.p;
-  a.Y = d.Y; a.rr = d.rr; a.gn = d.gn; a.pstat = d.pstat; a.n_pts = n_pts;
+  a.Y = d.Y; a.rr = d.rr; a.gn = d.gn; a.rlast = d.rlast; a.rflag = d.rflag; a.pstat = d.pstat; a.n_pts = n_pts;
   return a;
 }
 
@@ -1007,24 +1029,22 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   dim3 mgrid(c->max_tiles, nu);
   const int chunk = c->opt_cg_chunk;
   const bool mixed = krylov == SFB_CG_MIXED;
-  int it = 0, since_full = 0;
+  const double replace_ratio = c->opt_cg_replace, pause_ratio = 0.1 * c->opt_cg_replace;
+  int it = 0;
   for (; it < max_it;) {
     for (int q = 0; q < chunk && it < max_it; ++q, ++it) {
       if (mixed) matvec_kernel<float><<<mgrid, 256, smv32, st>>>(a, d.p, 0, d.active + 2);
       else matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.p, 0, d.active + 2);
       ++c->launches;
-      update_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, it, rtol, mixed ? 1 : 0);
+      update_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, it, rtol, mixed ? 1 : 0, replace_ratio,
+                                                              pause_ratio);
       ++c->launches;
-      ++since_full;
     }
     if (mixed) {
-      // FP64 residuals: every iterating point once per reliable_every
-      // iterations, pending points at every check
-      const int sel = since_full >= c->opt_cg_reliable ? 1 : 2;
-      if (sel == 1) since_full = 0;
-      matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.lam, sel, d.active + 2);
+      // FP64 residuals of the points that asked for one
+      matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.lam, 1, d.active + 2);
       ++c->launches;
-      reliable_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, sel, rtol, it);
+      reliable_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, rtol, it);
       ++c->launches;
     }
     CK(cudaGetLastError());

@@ -104,6 +104,8 @@ struct Dev {
   double* Y = nullptr;        // [n_pts][NY]
   double* rr = nullptr;
   double* gn = nullptr;
+  double* rlast = nullptr;
+  int* rflag = nullptr;
   int* pstat = nullptr;       // per point: iterations (>0 converged, <0 active/failed)
   int* active = nullptr;
   int64_t* s_gdof = nullptr;  // Stokes local -> global mortar DOF
@@ -168,7 +170,7 @@ struct sfb_ctx {
   double opt_refine_tol = 1e-10;
   int opt_refine_max = 8;
   int opt_cg_chunk = 8;
-  int opt_cg_reliable = 16;   // iterations between FP64 residual replacements (mixed CG)
+  double opt_cg_replace = 0.1;  // mixed CG: FP64 residual once the recursive one drops by this factor
   double opt_big_factor = 2.0;   // groups above this many times (R+1) points use coefficient moments
   // device-time phase markers of the last interface solve (CUDA events)
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};

@@ -252,6 +252,8 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   d.Y = cv.take<double>((size_t)P * c->NY);
   d.rr = cv.take<double>(P);
   d.gn = cv.take<double>(P);
+  d.rlast = cv.take<double>(P);
+  d.rflag = cv.take<int>(P);
   d.pstat = cv.take<int>(P);
   d.active = cv.take<int>(4);
   d.s_gdof = cv.take<int64_t>(std::max(Rs, 1));
@@ -833,9 +835,9 @@ sfb_status sfb_set_option(sfb_ctx* c, const char* name, double value) {
   } else if (n == "cg_check_every") {
     if (!(value >= 1 && value <= 1000)) return fail(c, SFB_ERR_ARG, "cg_check_every must lie in [1, 1000]");
     c->opt_cg_chunk = (int)value;
-  } else if (n == "cg_reliable_every") {
-    if (!(value >= 1 && value <= 1000)) return fail(c, SFB_ERR_ARG, "cg_reliable_every must lie in [1, 1000]");
-    c->opt_cg_reliable = (int)value;
+  } else if (n == "cg_replace_ratio") {
+    if (!(value >= 1e-4 && value < 1)) return fail(c, SFB_ERR_ARG, "cg_replace_ratio must lie in [1e-4, 1)");
+    c->opt_cg_replace = value;
   } else {
     return fail(c, SFB_ERR_ARG, "unknown option " + n);
   }
