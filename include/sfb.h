@@ -137,6 +137,13 @@ typedef struct {
                               /* assembly, factorization, forward sweeps,         */
                               /* backward sweeps (clock64 in the kernel)          */
   double kernel_ms;           /* device time of the basis kernel alone            */
+  double flops_fp32;          /* algorithmic flops of the build by precision, per */
+  double flops_fp64;          /* item: factor (7/3) nx^3 ny (block Cholesky       */
+                              /* count), each multi-RHS solve 6 nx^2 ny (R+1),    */
+                              /* each FP64 refinement pass 11 nx ny (R+1)         */
+                              /* (5-point residual and update). FP64 form: all in */
+                              /* flops_fp64; mixed: factor and 1 + n_refine       */
+                              /* solves in flops_fp32, the passes in flops_fp64   */
 } sfb_basis_stats;
 
 typedef struct sfb_ctx sfb_ctx;

@@ -541,13 +541,12 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
           const int i = e % nx, c = e / nx;
           const int64_t cell = (int64_t)b * nx + i;
           const double* xc = X + (int64_t)c * nc;
-          double r = rhs_entry(S, g, a.proj, b, i, c);
-          double ax = Dg[cell] * xc[cell];
-          if (i > 0) ax = fma(-Tx[b * (nx + 1) + i], xc[cell - 1], ax);
-          if (i < nx - 1) ax = fma(-Tx[b * (nx + 1) + i + 1], xc[cell + 1], ax);
-          if (b > 0) ax = fma(-Ty[b * nx + i], xc[cell - nx], ax);
-          if (b < ny - 1) ax = fma(-Ty[(b + 1) * nx + i], xc[cell + nx], ax);
-          r -= ax;
+          // r = B - A x as five FP64 FMAs: B - D x, then + T x over the neighbours
+          double r = fma(-Dg[cell], xc[cell], rhs_entry(S, g, a.proj, b, i, c));
+          if (i > 0) r = fma(Tx[b * (nx + 1) + i], xc[cell - 1], r);
+          if (i < nx - 1) r = fma(Tx[b * (nx + 1) + i + 1], xc[cell + 1], r);
+          if (b > 0) r = fma(Ty[b * nx + i], xc[cell - nx], r);
+          if (b < ny - 1) r = fma(Ty[(b + 1) * nx + i], xc[cell + nx], r);
           const T rt = T(r);
           const float rf = (float)rt;
           rr = fmaf(rf, rf, rr);

@@ -150,6 +150,7 @@ struct IfaceArgs {
   const int64_t* ybase; // per unit offset into a point's Y row
   int64_t NY;
   const int* ldof;      // per global DOF: unit_a, local_a, unit_b, local_b
+  const int* yoff;      // per global DOF: ybase[unit_a] + local_a, ybase[unit_b] + local_b
   int64_t n_lambda;
   const int* kmap;
   const int* grp_pts;
@@ -265,8 +266,17 @@ __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, const double* 
   const int* tl = a.tiles + 3 * ((int64_t)u * a.max_tiles + t);
   const int k = tl[0], q0 = tl[1], cntp = tl[2];
   const int* pts = a.grp_pts + (int64_t)u * a.pts_ld + q0;
+  __shared__ int sidx[kTG];   // tile slots of the selected points, in order
+  __shared__ int nsel_s;
   const int act = threadIdx.x < cntp ? selected(a, pts[threadIdx.x], a.pstat[pts[threadIdx.x]], sel) : 0;
+  if (threadIdx.x < 32) {     // kTG == 32: warp 0 holds one slot per lane
+    const unsigned mask = __ballot_sync(0xffffffffu, act);
+    if (act) sidx[__popc(mask & ((1u << threadIdx.x) - 1u))] = threadIdx.x;
+    if (threadIdx.x == 0) nsel_s = __popc(mask);
+  }
   if (!__syncthreads_or(act)) return;  // no point of the tile is selected
+  const int nsel = nsel_s;
+  const int nsel4 = (nsel + 3) & ~3;   // columns computed: the selected points, padded to 4
   int R;
   const T* ph = unit_phi_t<T>(a, u, k, R);
   const int64_t* gd = u == a.ns ? a.sgdof : a.gdof + a.subs[u].gdof_off;
@@ -285,13 +295,10 @@ __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, const double* 
                  : "memory");
   }
   __syncthreads();  // the initialised barrier is visible to every thread
-  for (int e = threadIdx.x; e < kTG * R; e += blockDim.x) {
+  for (int e = threadIdx.x; e < nsel4 * R; e += blockDim.x) {
     const int q = e / R, i = e - q * R;
     double v = 0.0;
-    if (q < cntp) {
-      const int64_t l = pts[q];
-      if (selected(a, l, a.pstat[l], sel)) v = vin[l * a.n_lambda + gd[i]];
-    }
+    if (q < nsel) v = vin[(int64_t)pts[sidx[q]] * a.n_lambda + gd[i]];
     Pv[i * (kTG + 1) + q] = T(v);
   }
   uint32_t ok = 0;
@@ -314,8 +321,9 @@ __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, const double* 
     return;
   }
   const int nrp = (R + 1) >> 1;
-  for (int tt = threadIdx.x; tt < nrp * (kTG / 4); tt += blockDim.x) {
-    const int r0 = (tt / (kTG / 4)) * 2, c0 = (tt % (kTG / 4)) * 4;
+  const int ncg = nsel4 >> 2;
+  for (int tt = threadIdx.x; tt < nrp * ncg; tt += blockDim.x) {
+    const int r0 = (tt / ncg) * 2, c0 = (tt % ncg) * 4;
     const bool two = r0 + 1 < R;
     T acc[2][4] = {};
     const T* p0 = Ph + r0 * R;
@@ -331,9 +339,8 @@ __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, const double* 
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      if (c0 + q >= cntp) break;
-      const int64_t l = pts[c0 + q];
-      if (!selected(a, l, a.pstat[l], sel)) continue;
+      if (c0 + q >= nsel) break;
+      const int64_t l = pts[sidx[c0 + q]];
       double* y = a.Y + l * a.NY + a.ybase[u];
       y[r0] = (double)acc[0][q];
       if (two) y[r0 + 1] = (double)acc[1][q];
@@ -347,6 +354,9 @@ __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, const double* 
 // residual at the next check and keeps iterating; it pauses when it falls
 // below pause_ratio times that residual, or below the tolerance, so that the
 // recursive and the true residual never drift far apart before replacement.
+constexpr int kUpd = 8;   // DOFs per lane held in registers by the update (n_lambda <= 256)
+
+template <bool kRegs>
 __global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed, double replace_ratio,
                               double pause_ratio) {
   const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -357,24 +367,52 @@ __global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed, doubl
   double* pl = a.p + l * a.n_lambda;
   double* rl = a.r + l * a.n_lambda;
   double* ll = a.lam + l * a.n_lambda;
+  const int n = (int)a.n_lambda;
+  // q = S p on this lane's DOFs (kept in registers when n <= 32 kUpd)
+  double qv[kRegs ? kUpd : 1], pv[kRegs ? kUpd : 1];
   double pq = 0.0;
-  for (int64_t d = lane; d < a.n_lambda; d += 32) {
-    const int ua = a.ldof[4 * d], la = a.ldof[4 * d + 1], ub = a.ldof[4 * d + 2], lb = a.ldof[4 * d + 3];
-    const double q = Yl[a.ybase[ua] + la] + Yl[a.ybase[ub] + lb];
-    pq += pl[d] * q;
+  if (kRegs) {
+#pragma unroll
+    for (int j = 0; j < kUpd; ++j) {
+      const int d = lane + 32 * j;
+      qv[j] = 0.0;
+      pv[j] = 0.0;
+      if (d < n) {
+        qv[j] = Yl[a.yoff[2 * d]] + Yl[a.yoff[2 * d + 1]];
+        pv[j] = pl[d];
+        pq = fma(pv[j], qv[j], pq);
+      }
+    }
+  } else {
+    for (int d = lane; d < n; d += 32) pq += pl[d] * (Yl[a.yoff[2 * d]] + Yl[a.yoff[2 * d + 1]]);
   }
   pq = warp_sum(pq);
   const double rr = a.rr[l];
   const bool brk = !(pq > 0.0);
   const double alpha = brk ? 0.0 : rr / pq;
   double rn = 0.0;
-  for (int64_t d = lane; d < a.n_lambda; d += 32) {
-    const int ua = a.ldof[4 * d], la = a.ldof[4 * d + 1], ub = a.ldof[4 * d + 2], lb = a.ldof[4 * d + 3];
-    const double q = Yl[a.ybase[ua] + la] + Yl[a.ybase[ub] + lb];
-    ll[d] += alpha * pl[d];
-    const double rv = rl[d] - alpha * q;
-    rl[d] = rv;
-    rn += rv * rv;
+  double rv_keep[kRegs ? kUpd : 1];
+  if (kRegs) {
+#pragma unroll
+    for (int j = 0; j < kUpd; ++j) {
+      const int d = lane + 32 * j;
+      rv_keep[j] = 0.0;
+      if (d < n) {
+        ll[d] = fma(alpha, pv[j], ll[d]);
+        const double rv = fma(-alpha, qv[j], rl[d]);
+        rl[d] = rv;
+        rv_keep[j] = rv;
+        rn = fma(rv, rv, rn);
+      }
+    }
+  } else {
+    for (int d = lane; d < n; d += 32) {
+      const double q = Yl[a.yoff[2 * d]] + Yl[a.yoff[2 * d + 1]];
+      ll[d] += alpha * pl[d];
+      const double rv = rl[d] - alpha * q;
+      rl[d] = rv;
+      rn += rv * rv;
+    }
   }
   rn = warp_sum(rn);
   const double rnorm = sqrt(rn);
@@ -388,7 +426,15 @@ __global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed, doubl
   }
   if (!done && !brk) {
     const double beta = rn / rr;
-    for (int64_t d = lane; d < a.n_lambda; d += 32) pl[d] = rl[d] + beta * pl[d];
+    if (kRegs) {
+#pragma unroll
+      for (int j = 0; j < kUpd; ++j) {
+        const int d = lane + 32 * j;
+        if (d < n) pl[d] = fma(beta, pv[j], rv_keep[j]);
+      }
+    } else {
+      for (int d = lane; d < n; d += 32) pl[d] = rl[d] + beta * pl[d];
+    }
   }
   __syncwarp();
   if (lane == 0) {
@@ -575,7 +621,9 @@ __global__ void __launch_bounds__(kMomT) darcy_moments_kernel(MomArgs m) {
     acc2[q] = 0.0;
   }
   const double ihx = 1.0 / S.hx, ihy = 1.0 / S.hy;
-  for (int t = ch; t < a.n_tiles[s]; t += m.n_chunks) {
+  // mode 0 scans every tile for point 0; mode 1 takes every n_chunks-th tile
+  const int t_step = m.mode == 0 ? 1 : m.n_chunks;
+  for (int t = m.mode == 0 ? 0 : ch; t < a.n_tiles[s]; t += t_step) {
     const int* tl = a.tiles + 3 * ((int64_t)s * a.max_tiles + t);
     const int k = tl[0];
     if (m.mode == 1 && big_group(m, S, s, k)) continue;  // handled by its coefficient moments
@@ -976,7 +1024,7 @@ static IfaceArgs make_args(sfb_ctx* c, int64_t n_pts) {
   a.subs = d.subs; a.ns = (int)c->subs.size(); a.off = d.off; a.phi = d.phi; a.s_phi = d.s_phi;
   a.phi32 = d.phi32; a.s_phi32 = d.s_phi32;
   a.Rs = (int)c->stokes.dofs.size(); a.gdof = d.gdof; a.sgdof = d.s_gdof; a.ybase = d.ybase; a.NY = c->NY;
-  a.ldof = d.ldof; a.n_lambda = c->n_lambda; a.kmap = d.kmap; a.grp_pts = d.grp_pts; a.pts_ld = c->ws_pts;
+  a.ldof = d.ldof; a.yoff = d.yoff; a.n_lambda = c->n_lambda; a.kmap = d.kmap; a.grp_pts = d.grp_pts; a.pts_ld = c->ws_pts;
   a.tiles = d.tiles; a.max_tiles = c->max_tiles; a.n_tiles = d.n_tiles; a.lam = d.lam; a.r = d.r; a.p = d.p;
   a.Y = d.Y; a.rr = d.rr; a.gn = d.gn; a.rlast = d.rlast; a.rflag = d.rflag; a.pstat = d.pstat; a.n_pts = n_pts;
   return a;
@@ -1036,8 +1084,12 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
       if (mixed) matvec_kernel<float><<<mgrid, 256, smv32, st>>>(a, d.p, 0, d.active + 2);
       else matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.p, 0, d.active + 2);
       ++c->launches;
-      update_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, it, rtol, mixed ? 1 : 0, replace_ratio,
-                                                              pause_ratio);
+      if (c->n_lambda <= 32 * kUpd)
+        update_kernel<true><<<ublocks, 32 * warps_per_block, 0, st>>>(a, it, rtol, mixed ? 1 : 0, replace_ratio,
+                                                                      pause_ratio);
+      else
+        update_kernel<false><<<ublocks, 32 * warps_per_block, 0, st>>>(a, it, rtol, mixed ? 1 : 0, replace_ratio,
+                                                                       pause_ratio);
       ++c->launches;
     }
     if (mixed) {

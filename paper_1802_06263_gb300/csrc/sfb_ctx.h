@@ -98,6 +98,7 @@ struct Dev {
   int* tiles = nullptr;       // per subdomain [max_tiles][3]
   int* n_tiles = nullptr;     // per subdomain (+ Stokes)
   int* ldof = nullptr;        // per global DOF: 2 (unit, local) pairs
+  int* yoff = nullptr;        // per global DOF: its 2 offsets into a point's Y row
   double* lam = nullptr;
   double* r = nullptr;
   double* p = nullptr;

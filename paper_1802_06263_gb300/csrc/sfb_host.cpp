@@ -246,6 +246,7 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   d.tiles = cv.take<int>((size_t)nu * c->max_tiles * 3);
   d.n_tiles = cv.take<int>(nu);
   d.ldof = cv.take<int>((size_t)c->n_lambda * 4);
+  d.yoff = cv.take<int>((size_t)c->n_lambda * 2);
   d.lam = cv.take<double>((size_t)P * c->n_lambda);
   d.r = cv.take<double>((size_t)P * c->n_lambda);
   d.p = cv.take<double>((size_t)P * c->n_lambda);
@@ -606,6 +607,9 @@ sfb_status upload_tables(sfb_ctx* c) {
   for (size_t a = 0; a < c->stokes.dofs.size(); ++a) put(c->stokes.dofs[a], ns, (int)a);
   for (int64_t g = 0; g < c->n_lambda; ++g)
     if (fill[g] != 2) return fail(c, SFB_ERR_ARG, "a mortar DOF is not shared by exactly two subdomains");
+  std::vector<int> yoff(2 * c->n_lambda);
+  for (int64_t g = 0; g < c->n_lambda; ++g)
+    for (int f = 0; f < 2; ++f) yoff[2 * g + f] = (int)(c->ybase[ldof[4 * g + 2 * f]] + ldof[4 * g + 2 * f + 1]);
   std::vector<int> dim_off(c->dim_off.begin(), c->dim_off.end());
   std::vector<int64_t> loc_off(ns, 0), cell_off(ns, 0), face_off(ns, 0);
   for (int s = 1; s < ns; ++s) {
@@ -620,7 +624,7 @@ sfb_status upload_tables(sfb_ctx* c) {
   UP(d.subs, sd); UP(d.proj, proj); UP(d.dofinfo, info); UP(d.kl, kl); UP(d.yloc, yloc); UP(d.gdof, gdof);
   UP(d.item_sub, item_sub); UP(d.item_k, item_k); UP(d.off, c->offs);
   UP(d.s_gdof, c->stokes.dofs); UP(d.ybase, c->ybase); UP(d.dim_off, dim_off); UP(d.loc_off, loc_off);
-  UP(d.cell_off, cell_off); UP(d.face_off, face_off); UP(d.ldof, ldof); UP(d.hash, htab); UP(d.hash_off, hoff);
+  UP(d.cell_off, cell_off); UP(d.face_off, face_off); UP(d.ldof, ldof); UP(d.yoff, yoff); UP(d.hash, htab); UP(d.hash_off, hoff);
   UP(d.hash_cap, hcap);
 #undef UP
   SFB_CUDA(cudaStreamSynchronize(st), "upload");
@@ -718,6 +722,23 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
     }
     stats->ms = ms;
     stats->kernel_ms = kms;
+    double f32 = 0.0, f64 = 0.0;
+    int64_t id = 0;
+    for (int s = 0; s < (int)c->subs.size(); ++s) {
+      const HostSub& H = c->subs[s];
+      const double nx = H.nx, ny = H.ny, C = (double)H.dofs.size() + 1.0;
+      const double fac = 7.0 / 3.0 * nx * nx * nx * ny, sol = 6.0 * nx * nx * ny * C, pass = 11.0 * nx * ny * C;
+      for (int k = 0; k < c->n_local[s]; ++k, ++id) {
+        if (prec == SFB_FP64) {
+          f64 += fac + sol;
+        } else {
+          f32 += fac + (1.0 + nref[id]) * sol;
+          f64 += nref[id] * pass;
+        }
+      }
+    }
+    stats->flops_fp32 = f32;
+    stats->flops_fp64 = f64;
   }
   c->basis_done = true;
   c->basis_prec = prec;
