@@ -253,7 +253,7 @@ sfb_status sfb_build_basis_item_noalloc(sfb_ctx* ctx, int32_t sub, int32_t k, in
  *                    and the point pauses at a tenth of it (0.1);
  *   "moments_group_factor"  groups of more than factor * (R+1) points enter
  *                    the moments through their coefficient second moments,
- *                    smaller ones point by point; 0 = always point by point (2).
+ *                    smaller ones point by point; 0 = always point by point (1).
  * SFB_ERR_ARG for an unknown name or a value out of range. */
 sfb_status sfb_set_option(sfb_ctx* ctx, const char* name, double value);
 

@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
     // first forward solve row: u_b = s_b B_b + dlo_b z_{b-1}
     for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
       const int i = e % nx, c = e / nx;
-      T u = sc[i] * T(rhs_entry(S, g, a.proj, b, i, c));
+      T u = sc[i] * from_f64<T>(rhs_entry(S, g, a.proj, b, i, c));
       if (b > 0) u = fma(dlo[i], Zs[i * Cp + c], u);
       Us[i * Cp + c] = u;
     }
@@ -547,8 +547,8 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
           if (i < nx - 1) r = fma(Tx[b * (nx + 1) + i + 1], xc[cell + 1], r);
           if (b > 0) r = fma(Ty[b * nx + i], xc[cell - nx], r);
           if (b < ny - 1) r = fma(Ty[(b + 1) * nx + i], xc[cell + nx], r);
-          const T rt = T(r);
-          const float rf = (float)rt;
+          const T rt = from_f64<T>(r);
+          const float rf = to_f32(rt);
           rr = fmaf(rf, rf, rr);
           T u = sc[i] * rt;
           if (b > 0) u = fma(dlo[i], Zs[i * Cp + c], u);
@@ -581,7 +581,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
       float bb = 0.f;
       for (int e = threadIdx.x; e < nc * C; e += blockDim.x) {
         const int c = e / nc, cell = e - c * nc;
-        const float v = (float)rhs_entry(S, g, a.proj, cell / nx, cell % nx, c);
+        const float v = f64_to_f32_bits(rhs_entry(S, g, a.proj, cell / nx, cell % nx, c));
         bb = fmaf(v, v, bb);
       }
       bnorm2 = block_sum((double)bb, red);
@@ -631,10 +631,10 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
         const int i = e % nx, c = e / nx;
         const int64_t idx = (int64_t)c * nc + (int64_t)b * nx + i;
         const T dt = sc[i] * Zs[i * Cp + c];
-        const float df = (float)dt;
+        const float df = to_f32(dt);
         dn2f = fmaf(df, df, dn2f);
-        if (it == 0) X[idx] = (double)dt;
-        else X[idx] += (double)dt;
+        if (it == 0) X[idx] = to_f64(dt);
+        else X[idx] += to_f64(dt);
       }
       __syncthreads();
     }

@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, const double* 
     const int q = e / R, i = e - q * R;
     double v = 0.0;
     if (q < nsel) v = vin[(int64_t)pts[sidx[q]] * a.n_lambda + gd[i]];
-    Pv[i * (kTG + 1) + q] = T(v);
+    Pv[i * (kTG + 1) + q] = from_f64<T>(v);
   }
   uint32_t ok = 0;
   for (int it = 0; it < (1 << 22) && !ok; ++it)
@@ -342,8 +342,8 @@ __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, const double* 
       if (c0 + q >= nsel) break;
       const int64_t l = pts[sidx[c0 + q]];
       double* y = a.Y + l * a.NY + a.ybase[u];
-      y[r0] = (double)acc[0][q];
-      if (two) y[r0 + 1] = (double)acc[1][q];
+      y[r0] = to_f64(acc[0][q]);
+      if (two) y[r0 + 1] = to_f64(acc[1][q]);
     }
   }
 }
@@ -792,7 +792,7 @@ __global__ void group_moments_reduce(MomArgs m, const double* part) {
 }
 
 constexpr int kBigT = 128;   // threads of the large-group moments kernel
-constexpr int kBigE = 16;    // field entries owned per thread
+constexpr int kBigE = 2;     // field entries per thread
 
 // Coefficient of column a in the affine map from [R lambda; 1] to the value of
 // tile-local entry e_loc (cell pressure or face velocity) for basis item X.
@@ -831,32 +831,35 @@ __device__ __forceinline__ double entry_coef(const SubDev& S, const MomArgs& m, 
 
 // Large groups: with F the entry's coefficient row and v = F c,
 // sum_l w (v_l - s) = F m + W (F cbar - s) and
-// sum_l w (v_l - s)^2 = F M F^T + 2 (F cbar - s) F m + W (F cbar - s)^2.
-// Writes partial slot `slot` for every entry of the tile (zeros when the
-// subdomain has no large group).
+// sum_l w (v_l - s)^2 = F M F^T + 2 (F cbar - s) F m + W (F cbar - s)^2,
+// F M F^T summed over the upper triangle of the symmetric M. A CTA owns
+// kBigT * kBigE consecutive entries of one subdomain (cells, x-faces, y-faces)
+// and writes partial slot `slot` for each of them (zeros when the subdomain
+// has no large group).
 __global__ void __launch_bounds__(kBigT) bigroup_moments_kernel(MomArgs m, int slot) {
   extern __shared__ __align__(16) double smb[];
   const IfaceArgs& a = m.ia;
   const int s = blockIdx.y;
   const SubDev S = a.subs[s];
   const int nx = S.nx, ny = S.ny, R = S.R, C = R + 1;
-  const int r0 = blockIdx.x * m.rt;
-  if (r0 >= ny) return;
-  const int r1 = min(ny, r0 + m.rt);
-  const int n_ent = (r1 - r0) * nx + (r1 - r0) * (nx + 1) + ((r1 == ny ? ny + 1 : r1) - r0) * nx;
+  const int n_ent = ny * nx + ny * (nx + 1) + (ny + 1) * nx;
+  const int nt = blockDim.x;   // kBigT, or fewer when C*C + C*kBigT doubles exceed shared memory
+  const int64_t e0 = (int64_t)blockIdx.x * nt * kBigE;
+  if (e0 >= n_ent) return;
   double* Ms = smb;                 // [C][C]
   double* cb = Ms + C * C;          // [C]
   double* mv = cb + C;              // [C]
-  double* Fs = mv + C;              // [C][kBigT]
+  double* Fs = mv + C;              // [C][nt]
   const double ihx = 1.0 / S.hx, ihy = 1.0 / S.hy;
   double sh[kBigE], acc1[kBigE], acc2[kBigE];
 #pragma unroll
   for (int j = 0; j < kBigE; ++j) {
-    const int64_t el = threadIdx.x + (int64_t)j * kBigT;
-    sh[j] = el < n_ent ? m.shift[darcy_entry(S, m, s, el, r0, r1)] : 0.0;
+    const int64_t el = e0 + threadIdx.x + (int64_t)j * nt;
+    sh[j] = el < n_ent ? m.shift[darcy_entry(S, m, s, el, 0, ny)] : 0.0;
     acc1[j] = 0.0;
     acc2[j] = 0.0;
   }
+  double* Fc = Fs + threadIdx.x;    // this thread's column of F, stride nt
   for (int k = 0; k < S.n_local; ++k) {
     if (!big_group(m, S, s, k)) continue;
     const double* gm = m.gmom + (m.loc_off[s] + k) * m.gmom_stride;
@@ -871,21 +874,22 @@ __global__ void __launch_bounds__(kBigT) bigroup_moments_kernel(MomArgs m, int s
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < kBigE; ++j) {
-      const int64_t el = threadIdx.x + (int64_t)j * kBigT;
+      const int64_t el = e0 + threadIdx.x + (int64_t)j * nt;
       if (el >= n_ent) break;
       double fc = 0.0, fm = 0.0;
       for (int ia = 0; ia < C; ++ia) {
-        const double f = entry_coef(S, m, el, r0, r1, X, Tx, Ty, ia, ihx, ihy);
-        Fs[ia * kBigT + threadIdx.x] = f;
+        const double f = entry_coef(S, m, el, 0, ny, X, Tx, Ty, ia, ihx, ihy);
+        Fc[ia * nt] = f;
         fc = fma(f, cb[ia], fc);
         fm = fma(f, mv[ia], fm);
       }
       double q = 0.0;
       for (int ia = 0; ia < C; ++ia) {
-        double row = 0.0;
         const double* Mr = Ms + ia * C;
-        for (int ib = 0; ib < C; ++ib) row = fma(Mr[ib], Fs[ib * kBigT + threadIdx.x], row);
-        q = fma(Fs[ia * kBigT + threadIdx.x], row, q);
+        double row = 0.0;
+        for (int ib = ia + 1; ib < C; ++ib) row = fma(Mr[ib], Fc[ib * nt], row);
+        const double fa = Fc[ia * nt];
+        q = fma(fa, fma(2.0, row, Mr[ia] * fa), q);
       }
       const double dv = fc - sh[j];
       acc1[j] += fm + W * dv;
@@ -894,9 +898,9 @@ __global__ void __launch_bounds__(kBigT) bigroup_moments_kernel(MomArgs m, int s
   }
 #pragma unroll
   for (int j = 0; j < kBigE; ++j) {
-    const int64_t el = threadIdx.x + (int64_t)j * kBigT;
+    const int64_t el = e0 + threadIdx.x + (int64_t)j * nt;
     if (el >= n_ent) break;
-    const int64_t ge = darcy_entry(S, m, s, el, r0, r1);
+    const int64_t ge = darcy_entry(S, m, s, el, 0, ny);
     m.part[((int64_t)slot * 2) * m.len_d + ge] = acc1[j];
     m.part[((int64_t)slot * 2 + 1) * m.len_d + ge] = acc2[j];
   }
@@ -1173,9 +1177,14 @@ sfb_status moments_accumulate_device(sfb_ctx* c, int64_t n_pts) {
   ++c->launches;
   group_moments_reduce<<<dim3(max_local, ns), 256, 0, st>>>(m, d.gmom_part);
   ++c->launches;
-  const size_t smb = sizeof(double) * ((size_t)maxC * maxC + 2 * (size_t)maxC + (size_t)maxC * kBigT);
+  int big_t = kBigT;
+  auto smb_of = [&](int t) { return sizeof(double) * ((size_t)maxC * maxC + 2 * (size_t)maxC + (size_t)maxC * t); };
+  while (big_t > 32 && smb_of(big_t) > 227 * 1024) big_t >>= 1;
+  const size_t smb = smb_of(big_t);
   CK(cudaFuncSetAttribute(bigroup_moments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
-  bigroup_moments_kernel<<<dim3(row_tiles, ns), kBigT, smb, st>>>(m, m.n_chunks);
+  int max_ent = 0;
+  for (const HostSub& S : c->subs) max_ent = std::max(max_ent, S.ny * S.nx + S.ny * (S.nx + 1) + (S.ny + 1) * S.nx);
+  bigroup_moments_kernel<<<dim3((max_ent + big_t * kBigE - 1) / (big_t * kBigE), ns), big_t, smb, st>>>(m, m.n_chunks);
   ++c->launches;
   CK(cudaGetLastError());
   reduce_partials<<<256, 256, 0, st>>>(d.mom_part, m.n_chunks + 1, m.len_d, d.mom + m.len_d, d.mom + 2 * m.len_d);

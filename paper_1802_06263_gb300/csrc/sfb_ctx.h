@@ -172,7 +172,7 @@ struct sfb_ctx {
   int opt_refine_max = 8;
   int opt_cg_chunk = 8;
   double opt_cg_replace = 0.1;  // mixed CG: FP64 residual once the recursive one drops by this factor
-  double opt_big_factor = 2.0;   // groups above this many times (R+1) points use coefficient moments
+  double opt_big_factor = 1.0;   // groups above this many times (R+1) points use coefficient moments
   // device-time phase markers of the last interface solve (CUDA events)
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int cg_iters_run = 0;

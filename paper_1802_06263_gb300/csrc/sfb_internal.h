@@ -37,6 +37,46 @@ struct SubDev {
   int64_t item0;             // first basis item of this subdomain (items k = 0..n_local-1)
 };
 
+#ifdef __CUDACC__
+// Conversions between binary64 and binary32 on the integer pipe, from the
+// IEEE 754 formats (exponent biases 1023 and 127, 52 and 23 fraction bits).
+// The conversion instructions issue on the FP64 pipe, which on this part runs
+// at 1/64 of the FP32 rate, and the mixed form converts every residual entry
+// and every correction once per refinement pass.
+// binary64 -> binary32: fraction truncated (round toward zero, relative error
+// below 2^-23), magnitudes below the binary32 normal range give zero, above it
+// (and non-finite values) NaN.
+__device__ __forceinline__ float f64_to_f32_bits(double v) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  unsigned bits = hi & 0x80000000u;
+  if (e > 1150u) bits = 0x7fc00000u;
+  else if (e >= 897u) bits |= ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  return __uint_as_float(bits);
+}
+// binary32 -> binary64, exact for normal values; subnormals give zero,
+// non-finite values NaN.
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  unsigned hi = b & 0x80000000u, lo = 0u;
+  if (e == 255u) hi = 0x7ff80000u;
+  else if (e != 0u) { hi |= ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3); lo = b << 29; }
+  return __hiloint2double((int)hi, (int)lo);
+}
+template <typename T>
+__device__ __forceinline__ T from_f64(double v);
+template <>
+__device__ __forceinline__ float from_f64<float>(double v) { return f64_to_f32_bits(v); }
+template <>
+__device__ __forceinline__ double from_f64<double>(double v) { return v; }
+__device__ __forceinline__ double to_f64(float v) { return f32_to_f64_bits(v); }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(double v) { return f64_to_f32_bits(v); }
+
+#endif  // __CUDACC__
+
 // Per-item storage offsets (elements) into the basis store arrays.
 struct ItemOff {
   int64_t x;    // X: [R+1][n_cells] FP64 pressure responses (column-major)
