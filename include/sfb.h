@@ -133,9 +133,15 @@ typedef struct {
   double max_error_estimate;  /* mixed form: max predicted relative error of X    */
                               /* from the contraction of successive corrections   */
   double ms;                  /* device time of the build (CUDA events)           */
-  double phase_cycles[4];     /* mean SM cycles per item in: permeability and     */
+  double phase_cycles[16];    /* mean SM cycles per item in: permeability and     */
                               /* assembly, factorization, forward sweeps,         */
-                              /* backward sweeps (clock64 in the kernel)          */
+                              /* backward sweeps (clock64 in the kernel); then    */
+                              /* sub-phases of the row steps up to each barrier:  */
+                              /* factor [4] row set-up [5] block inversion [6]    */
+                              /* G store and right-hand side [7] product;         */
+                              /* forward [8] set-up [9] residual and G wait [10]  */
+                              /* product; backward [11] set-up [12] scaled input  */
+                              /* [13] z and G waits [14] product [15] X update    */
   double kernel_ms;           /* device time of the basis kernel alone            */
   double flops_fp32;          /* algorithmic flops of the build by precision, per */
   double flops_fp64;          /* item: factor (7/3) nx^3 ny (block Cholesky       */

@@ -55,7 +55,7 @@ class BasisStats(ctypes.Structure):
                 ("max_refine_steps", ctypes.c_int32), ("n_not_converged", ctypes.c_int32),
                 ("max_rel_residual", ctypes.c_double), ("max_first_correction", ctypes.c_double),
                 ("max_error_estimate", ctypes.c_double), ("ms", ctypes.c_double),
-                ("phase_cycles", ctypes.c_double * 4), ("kernel_ms", ctypes.c_double),
+                ("phase_cycles", ctypes.c_double * 16), ("kernel_ms", ctypes.c_double),
                 ("flops_fp32", ctypes.c_double), ("flops_fp64", ctypes.c_double)]
 
 

@@ -409,7 +409,18 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
   }
   int st = 0;
   long long t_mark = clock64(), t_fwd = 0, t_bwd = 0;
-  long long* cyc = a.cycles + 4 * (int64_t)id;
+  long long* cyc = a.cycles + kCycSlots * (int64_t)id;
+  // thread 0's clock between barriers: sub-phases of the factor, forward and
+  // backward row steps (slots 4-15 of the per-item cycle record)
+  long long sub[12] = {}, t_sub = t_mark;
+#define SFB_MARK(k)                                          \
+  do {                                                       \
+    if (threadIdx.x == 0) {                                  \
+      const long long t_ = clock64();                        \
+      sub[k] += t_ - t_sub;                                  \
+      t_sub = t_;                                            \
+    }                                                        \
+  } while (0)
   for (int e = threadIdx.x; e < np * Cp; e += blockDim.x) { Us[e] = T(0); Zs[e] = T(0); }
   for (int e = threadIdx.x; e < np; e += blockDim.x) { sc[e] = T(0); dlo[e] = T(0); dup[e] = T(0); txh[e] = T(0); }
   __syncthreads();
@@ -477,8 +488,10 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
       dlo[i] = b > 0 ? T((double)Sg[(b - 1) * nx + i] * Ty[b * nx + i] * si) : T(0);
     }
     __syncthreads();
+    SFB_MARK(0);
     form_block<T, MT, NT>(areg, b, nx, ntr, txh, dlo);
     blocked_sweep<T, MT, NT>(areg, np, ntr, VT, W, Ablk, &bad_spd);
+    SFB_MARK(1);
     T* Gs = Gs0 + (b % GB) * np * np;
     if (threadIdx.x == 0) bulk_wait_read();   // the store that last read Gs / Zs is done
     __syncthreads();
@@ -501,10 +514,12 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
     }
     fence_async_shared();
     __syncthreads();
+    SFB_MARK(2);
     if (threadIdx.x == 0) bulk_store(Gg + (int64_t)b * np * np, Gs, gbytes);
     gemm_g<T>(Gs, Us, Zs, false, np, Cp, C);
     fence_async_shared();
     __syncthreads();
+    SFB_MARK(3);
     if (threadIdx.x == 0) bulk_store(Zg + (int64_t)b * np * Cp, Zs, zbytes);
   }
   if (threadIdx.x == 0) {
@@ -512,7 +527,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
     fence_async_global();
   }
   __syncthreads();
-  if (threadIdx.x == 0) { const long long t = clock64(); cyc[1] = t - t_mark; t_mark = t; }
+  if (threadIdx.x == 0) { const long long t = clock64(); cyc[1] = t - t_mark; t_mark = t; t_sub = t; }
 
   // ---- 3./4. backward sweep, then refine with FP64 residuals --------------------------
   double xref2 = 0.0, prev_corr = 0.0, est = 1.0, bnorm2 = 0.0;
@@ -532,6 +547,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
           dlo[i] = b > 0 ? T((double)Sg[(b - 1) * nx + i] * Ty[b * nx + i] * si) : T(0);
         }
         __syncthreads();
+        SFB_MARK(4);
         if (GB == 2 && threadIdx.x == 0 && b + 1 < ny) {
           fence_async_shared();
           bulk_load(Gs0 + (cur ^ 1) * np * np, Gg + (int64_t)(b + 1) * np * np, gbytes, &gbar[cur ^ 1]);
@@ -559,9 +575,11 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
         const bool ok = mbar_wait(&gbar[cur], gph[cur]);
         gph[cur] ^= 1u;
         if (__syncthreads_or(!ok)) { timeout = true; break; }
+        SFB_MARK(5);
         gemm_g<T>(Gs, Us, Zs, false, np, Cp, C);
         fence_async_shared();
         __syncthreads();
+        SFB_MARK(6);
         if (threadIdx.x == 0) {
           bulk_store(Zg + (int64_t)b * np * Cp, Zs, zbytes);
           if (GB == 1 && b + 1 < ny) { fence_async_shared(); bulk_load(Gs0, Gg + (int64_t)(b + 1) * np * np, gbytes, &gbar[0]); }
@@ -575,7 +593,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
       if (timeout) break;
       const double rnorm2 = block_sum((double)rr, red);
       if (threadIdx.x == 0) a.resid[id] = sqrt(rnorm2 / fmax(bnorm2, 1e-300));
-      if (threadIdx.x == 0) { const long long t = clock64(); t_fwd += t - t_mark; t_mark = t; }
+      if (threadIdx.x == 0) { const long long t = clock64(); t_fwd += t - t_mark; t_mark = t; t_sub = t; }
     } else {
       // |B|^2 for the relative residual
       float bb = 0.f;
@@ -602,6 +620,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
         dup[i] = b < ny - 1 ? T(si * Ty[(b + 1) * nx + i] * (double)Sg[(b + 1) * nx + i]) : T(0);
       }
       __syncthreads();
+      SFB_MARK(7);
       if (threadIdx.x == 0 && b < ny - 1) {
         fence_async_shared();
         if (GB == 2 && b >= 1)   // prefetch G_{b-1}
@@ -616,6 +635,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
       }
       fence_async_shared();
       __syncthreads();
+      SFB_MARK(8);
       if (threadIdx.x == 0) bulk_load(Zs, Zg + (int64_t)b * np * Cp, zbytes, &zbar);
       bool ok = mbar_wait(&zbar, zph);
       zph ^= 1u;
@@ -624,8 +644,10 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
         gph[cur] ^= 1u;
       }
       if (__syncthreads_or(!ok)) { timeout = true; break; }
+      SFB_MARK(9);
       if (b < ny - 1) gemm_g<T>(Gs, Us, Zs, true, np, Cp, C);
       __syncthreads();
+      SFB_MARK(10);
 #pragma unroll 4
       for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
         const int i = e % nx, c = e / nx;
@@ -637,10 +659,11 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
         else X[idx] += to_f64(dt);
       }
       __syncthreads();
+      SFB_MARK(11);
     }
     if (timeout) break;
     const double dn2 = block_sum((double)dn2f, red);
-    if (threadIdx.x == 0) { const long long t = clock64(); t_bwd += t - t_mark; t_mark = t; }
+    if (threadIdx.x == 0) { const long long t = clock64(); t_bwd += t - t_mark; t_mark = t; t_sub = t; }
     if (it == 0) {
       xref2 = dn2;  // ||x_0||^2
       prev_corr = 1.0;
@@ -676,6 +699,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
     bulk_wait_all();
     cyc[2] = t_fwd;
     cyc[3] = t_bwd;
+    for (int q = 0; q < 12; ++q) cyc[4 + q] = sub[q];
     a.nref[id] = n_done;
     a.errest[id] = refine > 0 ? est : 0.0;
   }
@@ -685,6 +709,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
   __syncthreads();
   if (bad_spd) st |= ST_NOT_SPD;
   if (st) atomicOr(&a.status[id], st);
+#undef SFB_MARK
 }
 
 // Phi[l][j] = -sum_e P[e][l] T_e (X[c_e][j] - P[e][j]) (j < R) and

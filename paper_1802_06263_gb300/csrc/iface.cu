@@ -595,6 +595,28 @@ __device__ __forceinline__ int64_t darcy_entry(const SubDev& S, const MomArgs& m
   return m.off_f + m.face_off[s] + (int64_t)ny * (nx + 1) + (int64_t)r0 * nx + (e_loc - np - nxf);
 }
 
+// Z[c][q] = sum_i X[c][i] Cf[q][i] for the cells c < ncell of a row tile
+// (X column-major with column stride nc) and the first NQ points of the
+// sub-tile; FP64, one cell per thread.
+template <int NQ>
+__device__ __forceinline__ void field_rows(const double* __restrict__ X, int nc, int C, int ncell,
+                                           const double* Cf, double* Z) {
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+    const double* xr = X + c;
+    double z[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) z[q] = 0.0;
+#pragma unroll 4
+    for (int i = 0; i < C; ++i) {
+      const double xv = xr[(int64_t)i * nc];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) z[q] = fma(xv, Cf[q * C + i], z[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) Z[c * kTP + q] = z[q];
+  }
+}
+
 __global__ void __launch_bounds__(kMomT) darcy_moments_kernel(MomArgs m) {
   extern __shared__ __align__(16) double sm[];
   const IfaceArgs& a = m.ia;
@@ -652,19 +674,11 @@ __global__ void __launch_bounds__(kMomT) darcy_moments_kernel(MomArgs m) {
       }
       for (int q = threadIdx.x; q < kTP; q += blockDim.x) Wt[q] = q < cntp ? m.w[pts[q]] : 0.0;
       __syncthreads();
-      for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
-        const double* xr = X + (int64_t)h0 * nx + c;
-        double z[kTP];
-#pragma unroll
-        for (int q = 0; q < kTP; ++q) z[q] = 0.0;
-        for (int i = 0; i < C; ++i) {
-          const double xv = xr[(int64_t)i * nc];
-#pragma unroll
-          for (int q = 0; q < kTP; ++q) z[q] = fma(xv, Cf[q * C + i], z[q]);
-        }
-#pragma unroll
-        for (int q = 0; q < kTP; ++q) Z[c * kTP + q] = z[q];
-      }
+      // only the sub-tile's points: 1, 2, 4 or kTP columns
+      if (cntp == 1) field_rows<1>(X + (int64_t)h0 * nx, nc, C, ncell, Cf, Z);
+      else if (cntp == 2) field_rows<2>(X + (int64_t)h0 * nx, nc, C, ncell, Cf, Z);
+      else if (cntp <= 4) field_rows<4>(X + (int64_t)h0 * nx, nc, C, ncell, Cf, Z);
+      else field_rows<kTP>(X + (int64_t)h0 * nx, nc, C, ncell, Cf, Z);
       __syncthreads();
 #pragma unroll
       for (int j = 0; j < kMaxE; ++j) {
@@ -922,40 +936,90 @@ __global__ void reduce_partials(const double* part, int n_chunks, int64_t len, d
 // Stokes fields: x_l = U [R_s lambda_l; 1] for every entry, so with
 // d_l = c_l - c_0 (c_0: the coefficients of point 0 of the first batch) the
 // shifted sums are U m and diag(U M U^T) with m = sum w d, M = sum w d d^T.
-// One CTA per row a of M; threads over columns; points in order.
-__global__ void stokes_cov_kernel(const IfaceArgs a, const double* w, int first, double* c0, double* mvec,
-                                  double* Mmat) {
+// One CTA per point chunk: partial m and M (4 x 4 register tiles of M, points
+// staged 16 at a time), summed over the chunks in order by stokes_cov_reduce.
+__global__ void __launch_bounds__(256) stokes_cov_kernel(const IfaceArgs a, const double* w, int first, double* c0,
+                                                         double* part) {
   const int Rs = a.Rs, Cs = Rs + 1;
-  const int ra = blockIdx.x;
-  if (ra >= Cs) return;
+  const int ch = blockIdx.x;
   __shared__ double c0s[kMaxCols];
+  __shared__ double Dl[16][kMaxCols + 3];
+  __shared__ double Wl[16];
   for (int i = threadIdx.x; i < Cs; i += blockDim.x) {
     const double v = i < Rs ? a.lam[a.sgdof[i]] : 1.0;   // point 0
-    if (first) c0s[i] = v;
-    else c0s[i] = c0[i];
+    c0s[i] = first ? v : c0[i];
   }
   __syncthreads();
-  if (first && ra == 0)
+  if (first && ch == 0)
     for (int i = threadIdx.x; i < Cs; i += blockDim.x) c0[i] = c0s[i];
-  for (int b = threadIdx.x; b < Cs; b += blockDim.x) {
-    double acc = 0.0, acc1 = 0.0;
-    for (int64_t l = 0; l < a.n_pts; ++l) {
-      const double* ll = a.lam + l * a.n_lambda;
-      const double da = (ra < Rs ? ll[a.sgdof[ra]] : 1.0) - c0s[ra];
-      const double db = (b < Rs ? ll[a.sgdof[b]] : 1.0) - c0s[b];
-      acc = fma(w[l] * da, db, acc);
-      if (b == 0) acc1 = fma(w[l], da, acc1);
+  const int64_t per = (a.n_pts + kStokesChunks - 1) / kStokesChunks;
+  const int64_t p0 = ch * per, p1 = min(a.n_pts, p0 + per);
+  double* out = part + (int64_t)ch * (Cs + (int64_t)Cs * Cs);
+  const int nt4 = (Cs + 3) >> 2;
+  const int ntile = nt4 * nt4;
+  for (int tb = 0; tb < ntile; tb += blockDim.x) {
+    const int t = tb + threadIdx.x;
+    const int a0 = (t / nt4) * 4, b0 = (t % nt4) * 4;
+    double acc[4][4] = {};
+    double accm = 0.0;
+    for (int64_t q0 = p0; q0 < p1; q0 += 16) {
+      const int nq = (int)min((int64_t)16, p1 - q0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < nq * (Cs + 3); e += blockDim.x) {
+        const int q = e / (Cs + 3), i = e - q * (Cs + 3);
+        double v = 0.0;
+        if (i < Cs) v = (i < Rs ? a.lam[(q0 + q) * a.n_lambda + a.sgdof[i]] : 1.0) - c0s[i];
+        Dl[q][i] = v;
+      }
+      for (int q = threadIdx.x; q < nq; q += blockDim.x) Wl[q] = w[q0 + q];
+      __syncthreads();
+      if (t < ntile) {
+        for (int q = 0; q < nq; ++q) {
+          const double wq = Wl[q];
+          double da[4], db[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) { da[i] = wq * Dl[q][a0 + i]; db[i] = Dl[q][b0 + i]; }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(da[i], db[j], acc[i][j]);
+          if (tb == 0 && threadIdx.x < Cs) accm = fma(wq, Dl[q][threadIdx.x], accm);
+        }
+      }
     }
-    Mmat[(int64_t)ra * Cs + b] += acc;
-    if (b == 0) mvec[ra] += acc1;
+    if (t < ntile)
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (a0 + i < Cs && b0 + j < Cs) out[Cs + (a0 + i) * Cs + b0 + j] = acc[i][j];
+    if (tb == 0 && threadIdx.x < Cs) out[threadIdx.x] = accm;
   }
 }
 
+// m += sum of the chunk partials of m, M likewise, in chunk order.
+__global__ void stokes_cov_reduce(const double* part, int Cs, double* mvec, double* Mmat) {
+  const int64_t len = Cs + (int64_t)Cs * Cs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len; e += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int c = 0; c < kStokesChunks; ++c) v += part[c * len + e];
+    if (e < Cs) mvec[e] += v;
+    else Mmat[e - Cs] += v;
+  }
+}
+
+// out += sum of the weights (one CTA; strided partial sums, then a fixed tree).
 __global__ void weight_sum(const double* w, int64_t n, double* out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  __shared__ double red[256];
   double s = 0.0;
-  for (int64_t l = 0; l < n; ++l) s += w[l];
-  out[0] += s;
+  for (int64_t l = threadIdx.x; l < n; l += blockDim.x) s += w[l];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] += red[0];
 }
 
 // mean = shift W + S1, var = S2 - 2 (mean - shift) S1 + (mean - shift)^2 W
@@ -1191,11 +1255,13 @@ sfb_status moments_accumulate_device(sfb_ctx* c, int64_t n_pts) {
   ++c->launches;
   CK(cudaEventRecord(c->ev[4], st));
   const int Cs = (int)c->stokes.dofs.size() + 1;
-  stokes_cov_kernel<<<Cs, 128, 0, st>>>(m.ia, d.w, first, d.st_c0, d.st_m, d.st_M);
+  stokes_cov_kernel<<<kStokesChunks, 256, 0, st>>>(m.ia, d.w, first, d.st_c0, d.st_part);
+  ++c->launches;
+  stokes_cov_reduce<<<32, 256, 0, st>>>(d.st_part, Cs, d.st_m, d.st_M);
   ++c->launches;
   CK(cudaGetLastError());
   c->mom_shift_set = true;
-  weight_sum<<<1, 32, 0, st>>>(d.w, n_pts, d.mom_w);
+  weight_sum<<<1, 256, 0, st>>>(d.w, n_pts, d.mom_w);
   ++c->launches;
   CK(cudaGetLastError());
   CK(cudaEventRecord(c->ev[5], st));

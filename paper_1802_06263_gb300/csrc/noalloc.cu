@@ -102,7 +102,7 @@ extern "C" sfb_status sfb_build_basis_item_noalloc(sfb_ctx* c, int32_t sub, int3
   double* d_phi = cv.take<double>((size_t)R * R + R);
   int* d_status = cv.take<int>(2);
   double* d_diag = cv.take<double>(3);
-  long long* d_cyc = cv.take<long long>(4);
+  long long* d_cyc = cv.take<long long>(kCycSlots);
   if (cv.used > kNoAllocBytes) {
     c->err = "item needs " + std::to_string(cv.used) + " bytes of scratch; the no-alloc entry point has " +
              std::to_string(kNoAllocBytes);

@@ -123,6 +123,7 @@ struct Dev {
   double* st_c0 = nullptr;    // Stokes: coefficients of the shift point
   double* st_m = nullptr;     // Stokes: sum w (c - c0)
   double* st_M = nullptr;     // Stokes: sum w (c - c0)(c - c0)^T
+  double* st_part = nullptr;  // Stokes: per point chunk partials of st_m, st_M
   double* gmom = nullptr;     // per group: W | cbar | m | M (large groups)
   double* gmom_part = nullptr;// per group and point chunk: partial moments
 };

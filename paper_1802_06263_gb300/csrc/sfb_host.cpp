@@ -195,7 +195,7 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   d.resid = cv.take<double>(n_items);
   d.corr1 = cv.take<double>(n_items);
   d.errest = cv.take<double>(n_items);
-  d.cycles = cv.take<long long>(4 * n_items);
+  d.cycles = cv.take<long long>(kCycSlots * n_items);
   d.nref = cv.take<int>(n_items);
   // Stokes
   const StokesHost& St = c->stokes;
@@ -295,6 +295,7 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   d.st_c0 = cv.take<double>(Rs + 1);
   d.st_m = cv.take<double>(Rs + 1);
   d.st_M = cv.take<double>((size_t)(Rs + 1) * (Rs + 1));
+  d.st_part = cv.take<double>((size_t)kStokesChunks * ((Rs + 1) + (size_t)(Rs + 1) * (Rs + 1)));
   d.fin = cv.take<double>((size_t)2 * std::max(std::max(np_, nf_), (int64_t)std::max(St.n_u, St.n_p)));
   return cv.used + 256;
 }
@@ -689,13 +690,13 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   SFB_CUDA(cudaEventRecord(e1, st), "event");
   std::vector<int> status(n), nref(n);
   std::vector<double> resid(n), corr(n), est(n);
-  std::vector<long long> cyc(4 * (size_t)n);
+  std::vector<long long> cyc(kCycSlots * (size_t)n);
   SFB_CUDA(cudaMemcpyAsync(status.data(), d.status, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "stats");
   SFB_CUDA(cudaMemcpyAsync(nref.data(), d.nref, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "stats");
   SFB_CUDA(cudaMemcpyAsync(resid.data(), d.resid, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "stats");
   SFB_CUDA(cudaMemcpyAsync(corr.data(), d.corr1, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "stats");
   SFB_CUDA(cudaMemcpyAsync(est.data(), d.errest, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "stats");
-  SFB_CUDA(cudaMemcpyAsync(cyc.data(), d.cycles, sizeof(long long) * 4 * n, cudaMemcpyDeviceToHost, st), "stats");
+  SFB_CUDA(cudaMemcpyAsync(cyc.data(), d.cycles, sizeof(long long) * kCycSlots * n, cudaMemcpyDeviceToHost, st), "stats");
   SFB_CUDA(cudaStreamSynchronize(st), "basis build");
   float ms = 0.f, kms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
@@ -715,9 +716,9 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
     stats->max_rel_residual = n ? *std::max_element(resid.begin(), resid.end()) : 0.0;
     stats->max_first_correction = n ? *std::max_element(corr.begin(), corr.end()) : 0.0;
     stats->max_error_estimate = n ? *std::max_element(est.begin(), est.end()) : 0.0;
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kCycSlots; ++q) {
       double acc = 0.0;
-      for (int i = 0; i < n; ++i) acc += (double)cyc[4 * (size_t)i + q];
+      for (int i = 0; i < n; ++i) acc += (double)cyc[kCycSlots * (size_t)i + q];
       stats->phase_cycles[q] = n ? acc / n : 0.0;
     }
     stats->ms = ms;

@@ -77,6 +77,13 @@ __device__ __forceinline__ float to_f32(double v) { return f64_to_f32_bits(v); }
 
 #endif  // __CUDACC__
 
+// SM-cycle record per basis item: setup, factor, forward sweeps, backward
+// sweeps, then 12 sub-phases of the row steps (see sfb_basis_stats).
+constexpr int kCycSlots = 16;
+
+// Point chunks of the Stokes coefficient moments (partials summed in order).
+constexpr int kStokesChunks = 32;
+
 // Per-item storage offsets (elements) into the basis store arrays.
 struct ItemOff {
   int64_t x;    // X: [R+1][n_cells] FP64 pressure responses (column-major)
