@@ -219,6 +219,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 
 constexpr int kP = 8;  // pivots per panel of the blocked sweep
 
+// L2 prefetch of grid row b of all C columns of X (column-major, nx doubles
+// per row segment): one 128-byte line per thread.
+__device__ __forceinline__ void prefetch_x_row(const double* X, int64_t nc, int nx, int b, int C) {
+  const int lines = (nx * 8 + 127) >> 7;
+  for (int t = threadIdx.x; t < lines * C; t += blockDim.x) {
+    const int c = t / lines, q = t - c * lines;
+    const double* p = X + (int64_t)c * nc + (int64_t)b * nx + q * 16;
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+  }
+}
+
 // Block row b of the scaled matrix into the register tiles of the sweep:
 // S_b = Ahat_bb - D_{b-1} G_{b-1} D_{b-1}; on entry the tiles hold -G_{b-1}.
 // Rows / columns nx..np-1 are an identity padding.
@@ -384,6 +395,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
   double* X = a.X + off.x;
   double* Dg = a.D + off.diag;
   T* Sg = reinterpret_cast<T*>(a.S) + off.sc;
+  T* DLg = reinterpret_cast<T*>(a.DL) + off.sc;  // [ny][nx] scaled couplings to the row below
   T* Gg = reinterpret_cast<T*>(a.G) + off.g;   // [ny][np][np]
   T* Zg = reinterpret_cast<T*>(a.Z) + off.z;   // [ny][np][Cp], the shared-memory image of a row block
 
@@ -474,6 +486,12 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
       Sg[c] = T(1.0 / sqrt(d));
     }
     __syncthreads();
+    // D_{b-1} of the scaled matrix: s_{b-1,i} Ty[b][i] s_{b,i} (zero for row 0)
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+      const int b = c / nx, i = c - b * nx;
+      DLg[c] = b > 0 ? T(Ty[b * nx + i] / sqrt(Dg[c] * Dg[c - nx])) : T(0);
+    }
+    __syncthreads();
   }
   if (threadIdx.x == 0) { const long long t = clock64(); cyc[0] = t - t_mark; t_mark = t; }
 
@@ -485,7 +503,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
       const double si = (double)Sg[b * nx + i];
       sc[i] = T(si);
       txh[i] = i > 0 ? T(-Tx[b * (nx + 1) + i] * si * (double)Sg[b * nx + i - 1]) : T(0);
-      dlo[i] = b > 0 ? T((double)Sg[(b - 1) * nx + i] * Ty[b * nx + i] * si) : T(0);
+      dlo[i] = DLg[b * nx + i];
     }
     __syncthreads();
     SFB_MARK(0);
@@ -538,14 +556,19 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
     if (it > 0) {
       // forward sweep: r_b = B_b - (A x)_b in FP64; u_b = s_b r_b + dlo_b z_{b-1}
       if (threadIdx.x == 0) { fence_async_shared(); bulk_load(Gs0, Gg, gbytes, &gbar[0]); }
+      // row scalings of the next row travel in registers while a row runs
+      T nsc = threadIdx.x < nx ? Sg[threadIdx.x] : T(0), ndl = threadIdx.x < nx ? DLg[threadIdx.x] : T(0);
+      prefetch_x_row(X, nc, nx, 0, C);
+      if (ny > 1) prefetch_x_row(X, nc, nx, 1, C);
       for (int b = 0; b < ny; ++b) {
         const int cur = GB == 2 ? (b & 1) : 0;
         T* Gs = Gs0 + cur * np * np;
-        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-          const double si = (double)Sg[b * nx + i];
-          sc[i] = T(si);
-          dlo[i] = b > 0 ? T((double)Sg[(b - 1) * nx + i] * Ty[b * nx + i] * si) : T(0);
+        if (threadIdx.x < nx) {
+          sc[threadIdx.x] = nsc;
+          dlo[threadIdx.x] = ndl;
+          if (b + 1 < ny) { nsc = Sg[(b + 1) * nx + threadIdx.x]; ndl = DLg[(b + 1) * nx + threadIdx.x]; }
         }
+        if (b + 2 < ny) prefetch_x_row(X, nc, nx, b + 2, C);   // the residual of row b + 1 reads it
         __syncthreads();
         SFB_MARK(4);
         if (GB == 2 && threadIdx.x == 0 && b + 1 < ny) {
@@ -611,14 +634,16 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
       fence_async_shared();
       bulk_load(Gs0, Gg + (int64_t)(ny - 2) * np * np, gbytes, &gbar[0]);
     }
+    T bsc = threadIdx.x < nx ? Sg[(ny - 1) * nx + threadIdx.x] : T(0), bdu = T(0);
     for (int b = ny - 1; b >= 0; --b) {
       const int cur = GB == 2 ? ((ny - 2 - b) & 1) : 0;   // buffer of G_b (b <= ny-2)
       T* Gs = Gs0 + cur * np * np;
-      for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        const double si = (double)Sg[b * nx + i];
-        sc[i] = T(si);
-        dup[i] = b < ny - 1 ? T(si * Ty[(b + 1) * nx + i] * (double)Sg[(b + 1) * nx + i]) : T(0);
+      if (threadIdx.x < nx) {
+        sc[threadIdx.x] = bsc;
+        dup[threadIdx.x] = bdu;   // D_b = the coupling to row b + 1
+        if (b > 0) { bsc = Sg[(b - 1) * nx + threadIdx.x]; bdu = DLg[b * nx + threadIdx.x]; }
       }
+      if (it > 0) prefetch_x_row(X, nc, nx, b, C);   // updated after the product below
       __syncthreads();
       SFB_MARK(7);
       if (threadIdx.x == 0 && b < ny - 1) {

@@ -617,10 +617,10 @@ __device__ __forceinline__ void field_rows(const double* __restrict__ X, int nc,
   }
 }
 
-__global__ void __launch_bounds__(kMomT) darcy_moments_kernel(MomArgs m) {
-  extern __shared__ __align__(16) double sm[];
+// Row tile blockIdx.x of subdomain s, point chunk ch: mode 0 writes the shifts
+// (the fields at point 0), mode 1 the partial sums of chunk ch.
+__device__ __forceinline__ void darcy_moments_tile(const MomArgs& m, double* sm, int s, int ch) {
   const IfaceArgs& a = m.ia;
-  const int s = blockIdx.y, ch = blockIdx.z;
   const SubDev S = a.subs[s];
   const int nx = S.nx, ny = S.ny, R = S.R, C = R + 1, nc = nx * ny;
   const int r0 = blockIdx.x * m.rt;
@@ -709,6 +709,18 @@ __global__ void __launch_bounds__(kMomT) darcy_moments_kernel(MomArgs m) {
       m.part[((int64_t)ch * 2) * m.len_d + ge] = acc1[j];
       m.part[((int64_t)ch * 2 + 1) * m.len_d + ge] = acc2[j];
     }
+  }
+}
+
+// Mode 0: grid (row tiles, subdomains). Mode 1: grid (row tiles, 1, chunks);
+// every CTA walks all subdomains, taking every n_chunks-th tile of each, so
+// the point-by-point work spreads over all CTAs whichever subdomains hold it.
+__global__ void __launch_bounds__(kMomT) darcy_moments_kernel(MomArgs m) {
+  extern __shared__ __align__(16) double sm[];
+  if (m.mode == 0) {
+    darcy_moments_tile(m, sm, blockIdx.y, 0);
+  } else {
+    for (int s = 0; s < m.ia.ns; ++s) darcy_moments_tile(m, sm, s, blockIdx.z);
   }
 }
 
@@ -808,39 +820,59 @@ __global__ void group_moments_reduce(MomArgs m, const double* part) {
 constexpr int kBigT = 128;   // threads of the large-group moments kernel
 constexpr int kBigE = 2;     // field entries per thread
 
-// Coefficient of column a in the affine map from [R lambda; 1] to the value of
-// tile-local entry e_loc (cell pressure or face velocity) for basis item X.
-__device__ __forceinline__ double entry_coef(const SubDev& S, const MomArgs& m, int64_t e_loc, int r0, int r1,
-                                             const double* X, const double* Tx, const double* Ty, int a,
-                                             double ihx, double ihy) {
-  const int nx = S.nx, ny = S.ny, R = S.R, nc = nx * ny;
-  const double* xa = X + (int64_t)a * nc;
-  const int np = (r1 - r0) * nx, nxf = (r1 - r0) * (nx + 1);
-  if (e_loc < np) return xa[(int64_t)r0 * nx + e_loc];
+// Affine map of one Darcy entry onto the columns a of X (item with
+// transmissibilities Tx, Ty): v_a = t (X[a][c1] - X[a][c2]) for interior faces,
+// t (X[a][c1] - g_a) for faces on a Dirichlet or interface side (g_a the
+// mortar projection P[a] for a < R, or the side value in column R), X[a][c1]
+// for cells (t = 1, no second term); t carries the face sign and is zero on
+// no-flow sides.
+struct EntryMap {
+  int c1, c2;          // cells; c2 < 0: boundary or cell entry
+  double t;
+  const double* P;     // interface side: projection row of the face (length R)
+  double dval;         // Dirichlet side: value carried by column R
+};
+
+__device__ __forceinline__ EntryMap entry_map(const SubDev& S, const MomArgs& m, int64_t e_loc, const double* Tx,
+                                              const double* Ty, double ihx, double ihy) {
+  const int nx = S.nx, ny = S.ny, R = S.R;
+  const int np = ny * nx, nxf = ny * (nx + 1);
+  EntryMap em;
+  em.c2 = -1; em.P = nullptr; em.dval = 0.0;
+  if (e_loc < np) { em.c1 = (int)e_loc; em.t = 1.0; return em; }
+  int side, cell;
+  double t;
   if (e_loc < np + nxf) {
     const int f = (int)(e_loc - np);
-    const int row = r0 + f / (nx + 1), ix = f % (nx + 1);
-    const double t = Tx[(int64_t)row * (nx + 1) + ix] * ihy;
-    if (ix > 0 && ix < nx) return t * (xa[row * nx + ix - 1] - xa[row * nx + ix]);
-    const int side = ix == 0 ? 3 : 1;
-    if (S.side_type[side] == SIDE_NOFLOW) return 0.0;
-    double gb = 0.0;
-    if (S.side_type[side] == SIDE_IFACE) gb = a < R ? m.proj[S.proj_off[side] + (int64_t)row * R + a] : 0.0;
-    else gb = a == R ? S.side_val[side] : 0.0;
-    const double F = t * (xa[row * nx + (ix == 0 ? 0 : nx - 1)] - gb);
-    return ix == 0 ? -F : F;
+    const int row = f / (nx + 1), ix = f % (nx + 1);
+    t = Tx[(int64_t)row * (nx + 1) + ix] * ihy;
+    if (ix > 0 && ix < nx) { em.c1 = row * nx + ix - 1; em.c2 = row * nx + ix; em.t = t; return em; }
+    side = ix == 0 ? 3 : 1;
+    cell = row * nx + (ix == 0 ? 0 : nx - 1);
+    if (S.side_type[side] == SIDE_IFACE) em.P = m.proj + S.proj_off[side] + (int64_t)row * R;
+  } else {
+    const int f = (int)(e_loc - np - nxf);
+    const int j = f / nx, ix = f % nx;
+    t = Ty[(int64_t)j * nx + ix] * ihx;
+    if (j > 0 && j < ny) { em.c1 = (j - 1) * nx + ix; em.c2 = j * nx + ix; em.t = t; return em; }
+    side = j == 0 ? 0 : 2;
+    cell = (j == 0 ? 0 : ny - 1) * nx + ix;
+    if (S.side_type[side] == SIDE_IFACE) em.P = m.proj + S.proj_off[side] + (int64_t)ix * R;
   }
-  const int f = (int)(e_loc - np - nxf);
-  const int j = r0 + f / nx, ix = f % nx;
-  const double t = Ty[(int64_t)j * nx + ix] * ihx;
-  if (j > 0 && j < ny) return t * (xa[(j - 1) * nx + ix] - xa[j * nx + ix]);
-  const int side = j == 0 ? 0 : 2;
-  if (S.side_type[side] == SIDE_NOFLOW) return 0.0;
-  double gb = 0.0;
-  if (S.side_type[side] == SIDE_IFACE) gb = a < R ? m.proj[S.proj_off[side] + (int64_t)ix * R + a] : 0.0;
-  else gb = a == R ? S.side_val[side] : 0.0;
-  const double F = t * (xa[(j == 0 ? 0 : ny - 1) * nx + ix] - gb);
-  return j == 0 ? -F : F;
+  em.c1 = cell;
+  if (S.side_type[side] == SIDE_NOFLOW) t = 0.0;
+  if (S.side_type[side] == SIDE_DIRICHLET) em.dval = S.side_val[side];
+  em.t = (side == 0 || side == 3) ? -t : t;
+  return em;
+}
+
+__device__ __forceinline__ double entry_map_coef(const EntryMap& em, const double* X, int64_t nc, int R, int a) {
+  const double x1 = X[(int64_t)a * nc + em.c1];
+  double x2;
+  if (em.c2 >= 0) x2 = X[(int64_t)a * nc + em.c2];
+  else if (em.P) x2 = a < R ? em.P[a] : 0.0;
+  else x2 = a == R ? em.dval : 0.0;
+  return em.t * (x1 - x2);
 }
 
 // Large groups: with F the entry's coefficient row and v = F c,
@@ -890,9 +922,11 @@ __global__ void __launch_bounds__(kBigT) bigroup_moments_kernel(MomArgs m, int s
     for (int j = 0; j < kBigE; ++j) {
       const int64_t el = e0 + threadIdx.x + (int64_t)j * nt;
       if (el >= n_ent) break;
+      const EntryMap em = entry_map(S, m, el, Tx, Ty, ihx, ihy);
       double fc = 0.0, fm = 0.0;
+#pragma unroll 4
       for (int ia = 0; ia < C; ++ia) {
-        const double f = entry_coef(S, m, el, 0, ny, X, Tx, Ty, ia, ihx, ihy);
+        const double f = entry_map_coef(em, X, (int64_t)nx * ny, R, ia);
         Fc[ia * nt] = f;
         fc = fma(f, cb[ia], fc);
         fm = fma(f, mv[ia], fm);
@@ -1232,7 +1266,7 @@ sfb_status moments_accumulate_device(sfb_ctx* c, int64_t n_pts) {
     CK(cudaGetLastError());
   }
   m.mode = 1;
-  darcy_moments_kernel<<<dim3(row_tiles, ns, m.n_chunks), kMomT, smd, st>>>(m);
+  darcy_moments_kernel<<<dim3(row_tiles, 1, m.n_chunks), kMomT, smd, st>>>(m);
   ++c->launches;
   CK(cudaGetLastError());
   int max_local = 1;

@@ -97,6 +97,7 @@ extern "C" sfb_status sfb_build_basis_item_noalloc(sfb_ctx* c, int32_t sub, int3
   double* d_T = cv.take<double>((size_t)ny * (nx + 1) + (size_t)(ny + 1) * nx);
   double* d_D = cv.take<double>(nc);
   char* d_S = cv.take<char>((size_t)nc * gsz);
+  char* d_DL = cv.take<char>((size_t)nc * gsz);
   char* d_G = cv.take<char>((size_t)ny * np * np * gsz);
   char* d_Z = cv.take<char>((size_t)ny * np * cp * gsz);
   double* d_phi = cv.take<double>((size_t)R * R + R);
@@ -151,7 +152,7 @@ extern "C" sfb_status sfb_build_basis_item_noalloc(sfb_ctx* c, int32_t sub, int3
   BasisArgs a;
   a.subs = d_sub; a.proj = d_proj; a.dofinfo = d_info; a.kl = d_kl; a.yloc = d_yloc;
   a.item_sub = d_item; a.item_k = d_item + 1; a.off = d_off; a.n_items = 1;
-  a.X = x_out; a.T = d_T; a.G = d_G; a.Z = d_Z; a.S = d_S; a.phi = d_phi; a.phi32 = nullptr; a.D = d_D;
+  a.X = x_out; a.T = d_T; a.G = d_G; a.Z = d_Z; a.S = d_S; a.DL = d_DL; a.phi = d_phi; a.phi32 = nullptr; a.D = d_D;
   a.status = d_status; a.resid = d_diag; a.corr1 = d_diag + 1; a.errest = d_diag + 2; a.nref = d_status + 1;
   a.cycles = d_cyc;
   a.max_refine = c->opt_refine_max;

@@ -63,6 +63,7 @@ struct Dev {
   float* phi32 = nullptr;    // FP32 copy of phi for the FP32 interface products
   double* D = nullptr;
   void* S = nullptr;
+  void* DL = nullptr;
   double* errest = nullptr;
   long long* cycles = nullptr;
   int* status = nullptr;

@@ -191,6 +191,7 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   d.phi32 = cv.take<float>(nPhi);
   d.D = cv.take<double>(nD);
   d.S = cv.take<char>(nD * gsz);
+  d.DL = cv.take<char>(nD * gsz);
   d.status = cv.take<int>(n_items);
   d.resid = cv.take<double>(n_items);
   d.corr1 = cv.take<double>(n_items);
@@ -281,7 +282,9 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
     const int rt = std::max(1, std::min(max_ny, 512 / max_nx));
     row_tiles = ns * ((max_ny + rt - 1) / rt);
   }
-  c->mom_chunks = std::max(1, std::min(16, (4 * 152 + row_tiles - 1) / std::max(row_tiles, 1)));
+  // point chunks of the per-point Darcy moments: about 4 CTAs per SM over the
+  // row tiles of one subdomain (every CTA walks all subdomains)
+  c->mom_chunks = std::max(1, std::min(64, (4 * 152 * ns + row_tiles - 1) / std::max(row_tiles, 1)));
   d.mom = cv.take<double>((size_t)3 * len_d);
   d.mom_w = cv.take<double>(2);
   d.mom_part = cv.take<double>((size_t)2 * (c->mom_chunks + 1) * len_d);   // + the large-group slot
@@ -668,7 +671,7 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   BasisArgs a;
   a.subs = d.subs; a.proj = d.proj; a.dofinfo = d.dofinfo; a.kl = d.kl; a.yloc = d.yloc;
   a.item_sub = d.item_sub; a.item_k = d.item_k; a.off = d.off; a.n_items = n;
-  a.X = d.X; a.T = d.T; a.G = d.G; a.Z = d.Z; a.S = d.S; a.phi = d.phi; a.phi32 = d.phi32; a.D = d.D;
+  a.X = d.X; a.T = d.T; a.G = d.G; a.Z = d.Z; a.S = d.S; a.DL = d.DL; a.phi = d.phi; a.phi32 = d.phi32; a.D = d.D;
   a.status = d.status; a.resid = d.resid; a.corr1 = d.corr1; a.errest = d.errest; a.nref = d.nref;
   a.cycles = d.cycles;
   a.max_refine = c->opt_refine_max;

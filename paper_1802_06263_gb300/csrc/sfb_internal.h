@@ -110,6 +110,7 @@ struct BasisArgs {
   void* G;
   void* Z;                 // [R+1][n_cells] solve scratch in the factor precision
   void* S;                 // [n_cells] diagonal scaling in the factor precision
+  void* DL;                // [n_cells] scaled row couplings s_{b-1,i} Ty[b][i] s_{b,i} (row 0: 0), same offsets as S
   double* phi;
   float* phi32;            // Phi and g rounded to FP32 (same offsets)
   double* D;
