@@ -603,23 +603,41 @@ __device__ __forceinline__ void field_rows(const double* __restrict__ X, int nc,
                                            const double* Cf, double* Z) {
   for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
     const double* xr = X + c;
-    double z[NQ];
+    // at least four independent FMA chains: NQ accumulators, each split over
+    // 4 / NQ interleaved column ranges when NQ < 4
+    constexpr int NS = NQ >= 4 ? 1 : 4 / NQ;
+    double z[NS][NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) z[q] = 0.0;
-#pragma unroll 4
-    for (int i = 0; i < C; ++i) {
+    for (int u = 0; u < NS; ++u)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) z[u][q] = 0.0;
+    int i = 0;
+    for (; i + NS <= C; i += NS) {
+#pragma unroll
+      for (int u = 0; u < NS; ++u) {
+        const double xv = xr[(int64_t)(i + u) * nc];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) z[u][q] = fma(xv, Cf[q * C + i + u], z[u][q]);
+      }
+    }
+    for (; i < C; ++i) {
       const double xv = xr[(int64_t)i * nc];
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) z[q] = fma(xv, Cf[q * C + i], z[q]);
+      for (int q = 0; q < NQ; ++q) z[0][q] = fma(xv, Cf[q * C + i], z[0][q]);
     }
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) Z[c * kTP + q] = z[q];
+    for (int q = 0; q < NQ; ++q) {
+      double v = z[0][q];
+#pragma unroll
+      for (int u = 1; u < NS; ++u) v += z[u][q];
+      Z[c * kTP + q] = v;
+    }
   }
 }
 
 // Row tile blockIdx.x of subdomain s, point chunk ch: mode 0 writes the shifts
 // (the fields at point 0), mode 1 the partial sums of chunk ch.
-__device__ __forceinline__ void darcy_moments_tile(const MomArgs& m, double* sm, int s, int ch) {
+__device__ __forceinline__ void darcy_moments_tile(const MomArgs& m, double* sm, int s, int ch, int& gsub) {
   const IfaceArgs& a = m.ia;
   const SubDev S = a.subs[s];
   const int nx = S.nx, ny = S.ny, R = S.R, C = R + 1, nc = nx * ny;
@@ -643,9 +661,10 @@ __device__ __forceinline__ void darcy_moments_tile(const MomArgs& m, double* sm,
     acc2[q] = 0.0;
   }
   const double ihx = 1.0 / S.hx, ihy = 1.0 / S.hy;
-  // mode 0 scans every tile for point 0; mode 1 takes every n_chunks-th tile
-  const int t_step = m.mode == 0 ? 1 : m.n_chunks;
-  for (int t = m.mode == 0 ? 0 : ch; t < a.n_tiles[s]; t += t_step) {
+  // mode 0 scans every tile for point 0; mode 1 takes every n_chunks-th
+  // sub-tile of kTP points in a running count over all subdomains (gsub), so
+  // large tiles spread over several CTAs
+  for (int t = 0; t < a.n_tiles[s]; ++t) {
     const int* tl = a.tiles + 3 * ((int64_t)s * a.max_tiles + t);
     const int k = tl[0];
     if (m.mode == 1 && big_group(m, S, s, k)) continue;  // handled by its coefficient moments
@@ -665,6 +684,7 @@ __device__ __forceinline__ void darcy_moments_tile(const MomArgs& m, double* sm,
       q_end = has0 + 1;
     }
     for (int qs = q_begin; qs < q_end; qs += kTP) {
+      if (m.mode == 1 && (gsub++ % m.n_chunks) != ch) continue;
       const int* pts = tpts + qs;
       const int cntp = min(kTP, q_end - qs);
       __syncthreads();
@@ -717,10 +737,11 @@ __device__ __forceinline__ void darcy_moments_tile(const MomArgs& m, double* sm,
 // the point-by-point work spreads over all CTAs whichever subdomains hold it.
 __global__ void __launch_bounds__(kMomT) darcy_moments_kernel(MomArgs m) {
   extern __shared__ __align__(16) double sm[];
+  int gsub = 0;
   if (m.mode == 0) {
-    darcy_moments_tile(m, sm, blockIdx.y, 0);
+    darcy_moments_tile(m, sm, blockIdx.y, 0, gsub);
   } else {
-    for (int s = 0; s < m.ia.ns; ++s) darcy_moments_tile(m, sm, s, blockIdx.z);
+    for (int s = 0; s < m.ia.ns; ++s) darcy_moments_tile(m, sm, s, blockIdx.z, gsub);
   }
 }
 
@@ -931,13 +952,22 @@ __global__ void __launch_bounds__(kBigT) bigroup_moments_kernel(MomArgs m, int s
         fc = fma(f, cb[ia], fc);
         fm = fma(f, mv[ia], fm);
       }
+      // F M F^T over the upper triangle; four partial sums per row keep four
+      // independent FP64 FMA chains in flight
       double q = 0.0;
       for (int ia = 0; ia < C; ++ia) {
         const double* Mr = Ms + ia * C;
-        double row = 0.0;
-        for (int ib = ia + 1; ib < C; ++ib) row = fma(Mr[ib], Fc[ib * nt], row);
+        double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
+        int ib = ia + 1;
+        for (; ib + 3 < C; ib += 4) {
+          r0 = fma(Mr[ib], Fc[ib * nt], r0);
+          r1 = fma(Mr[ib + 1], Fc[(ib + 1) * nt], r1);
+          r2 = fma(Mr[ib + 2], Fc[(ib + 2) * nt], r2);
+          r3 = fma(Mr[ib + 3], Fc[(ib + 3) * nt], r3);
+        }
+        for (; ib < C; ++ib) r0 = fma(Mr[ib], Fc[ib * nt], r0);
         const double fa = Fc[ia * nt];
-        q = fma(fa, fma(2.0, row, Mr[ia] * fa), q);
+        q = fma(fa, fma(2.0, (r0 + r1) + (r2 + r3), Mr[ia] * fa), q);
       }
       const double dv = fc - sh[j];
       acc1[j] += fm + W * dv;
