@@ -253,9 +253,6 @@ sfb_status sfb_build_basis_item_noalloc(sfb_ctx* ctx, int32_t sub, int32_t k, in
  *                    error of X is below this (default 1e-10);
  *   "refine_max"     mixed form: at most this many FP64 residual passes (8);
  *   "cg_check_every" CG iterations between convergence checks on the host (8);
- *   "cg_fused"       SFB_CG_MIXED: 1 runs each FP32 iteration as one kernel
- *                    over tiles of points, 0 as separate product and update
- *                    kernels (1);
  *   "cg_replace_ratio"  SFB_CG_MIXED: a point's residual is replaced by the
  *                    FP64 residual at the next check once the recursive one
  *                    has dropped by this factor since the last replacement,

@@ -772,9 +772,7 @@ __global__ void flux_epilogue_kernel(BasisArgs a) {
     const int64_t o = j < R ? (int64_t)l * R + j : (int64_t)R * R + l;
     const double v = j < R ? -acc : acc;
     phi[o] = v;
-    // the FP32 copy is stored transposed (Phi^T in the R x R block): the fused
-    // CG iteration reads it column by column, coalesced over the rows
-    if (a.phi32) a.phi32[off.phi + (j < R ? (int64_t)j * R + l : o)] = (float)v;
+    if (a.phi32) a.phi32[off.phi + o] = (float)v;
   }
 }
 

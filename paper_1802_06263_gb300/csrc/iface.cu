@@ -445,145 +445,6 @@ __global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed, doubl
   }
 }
 
-// ---- fused FP32 iteration of the mixed CG -------------------------------------------
-// One CTA per kPT consecutive points does a whole inner iteration: the
-// products q = S32 p of its iterating points, unit by unit and basis by basis,
-// into shared memory, then the FP64 CG update of each point (the same update
-// as update_kernel in its mixed form). Work pairs (unit, stored basis) come
-// from a warp match over the points' local indices; each warp takes a pair,
-// gathers the pair's p entries in FP32 and forms y = Phi p reading the
-// transposed FP32 basis column by column (coalesced over the rows).
-constexpr int kPT = 16;
-
-struct CgPair {
-  int u, k;
-  unsigned mask;   // tile slots of the points that use basis k of unit u
-};
-
-__device__ __forceinline__ void cg_point_update(const IfaceArgs& a, int64_t l, const float* Yq, int it, double rtol,
-                                                double replace_ratio, double pause_ratio) {
-  const int lane = threadIdx.x & 31;
-  double* pl = a.p + l * a.n_lambda;
-  double* rl = a.r + l * a.n_lambda;
-  double* ll = a.lam + l * a.n_lambda;
-  const int n = (int)a.n_lambda;
-  double pq = 0.0;
-  for (int d = lane; d < n; d += 32) pq = fma(pl[d], to_f64(Yq[a.yoff[2 * d]] + Yq[a.yoff[2 * d + 1]]), pq);
-  pq = warp_sum(pq);
-  const double rr = a.rr[l];
-  const bool brk = !(pq > 0.0);
-  const double alpha = brk ? 0.0 : rr / pq;
-  double rn = 0.0;
-  for (int d = lane; d < n; d += 32) {
-    const double q = to_f64(Yq[a.yoff[2 * d]] + Yq[a.yoff[2 * d + 1]]);
-    ll[d] = fma(alpha, pl[d], ll[d]);
-    const double rv = fma(-alpha, q, rl[d]);
-    rl[d] = rv;
-    rn = fma(rv, rv, rn);
-  }
-  rn = warp_sum(rn);
-  const double rnorm = sqrt(rn);
-  const bool pause = brk || rnorm <= fmax(rtol * a.gn[l], pause_ratio * a.rlast[l]);
-  const bool flag = rnorm <= replace_ratio * a.rlast[l];
-  if (!brk) {
-    const double beta = rn / rr;
-    for (int d = lane; d < n; d += 32) pl[d] = fma(beta, pl[d], rl[d]);
-  }
-  __syncwarp();
-  if (lane == 0) {
-    a.rr[l] = rn;
-    if (pause) a.pstat[l] = kPending | (brk ? kRestart : 0) | (it + 1);
-    else if (flag) a.rflag[l] = 1;
-  }
-}
-
-__global__ void __launch_bounds__(256) cg32_iter_kernel(IfaceArgs a, int it, double rtol, double replace_ratio,
-                                                        double pause_ratio, int max_r) {
-  extern __shared__ __align__(16) unsigned char sraw[];
-  __shared__ int npairs_s;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int64_t l0 = (int64_t)blockIdx.x * kPT;
-  const int NY = (int)a.NY;
-  float* Yt = reinterpret_cast<float*>(sraw);                          // [kPT][NY]
-  float* Pw = Yt + (((int64_t)kPT * NY + 3) & ~int64_t(3));            // [nwarps][max_r][kPT]
-  int* slots = reinterpret_cast<int*>(Pw + (int64_t)nwarps * max_r * kPT);   // [nwarps][kPT]
-  CgPair* pairs = reinterpret_cast<CgPair*>(slots + nwarps * kPT);     // [(ns + 1) kPT]
-  int act = 0;
-  if (threadIdx.x < kPT) {
-    const int64_t l = l0 + threadIdx.x;
-    act = l < a.n_pts && a.pstat[l] == 0;
-  }
-  if (!__syncthreads_or(act)) return;
-  if (warp == 0) {
-    const int64_t l = l0 + lane;
-    const bool al = lane < kPT && l < a.n_pts && a.pstat[l] == 0;
-    int cnt = 0;
-    for (int u = 0; u <= a.ns; ++u) {
-      const int k = al ? (u < a.ns ? a.kmap[l * a.ns + u] : 0) : -1;
-      const unsigned m = __match_any_sync(0xffffffffu, k);
-      const bool leader = al && (__ffs(m) - 1) == lane;
-      const unsigned lm = __ballot_sync(0xffffffffu, leader);
-      if (leader) {
-        CgPair pr;
-        pr.u = u; pr.k = k; pr.mask = m;
-        pairs[cnt + __popc(lm & ((1u << lane) - 1u))] = pr;
-      }
-      cnt += __popc(lm);
-    }
-    if (lane == 0) npairs_s = cnt;
-  }
-  __syncthreads();
-  const int npairs = npairs_s;
-  float* P = Pw + (int64_t)warp * max_r * kPT;
-  int* sl = slots + warp * kPT;
-  for (int pi = warp; pi < npairs; pi += nwarps) {
-    const CgPair pr = pairs[pi];
-    int R;
-    const float* phT = unit_phi_t<float>(a, pr.u, pr.k, R);   // phT[j R + r] = Phi[r][j]
-    const int64_t* gd = pr.u == a.ns ? a.sgdof : a.gdof + a.subs[pr.u].gdof_off;
-    const int yb = (int)a.ybase[pr.u];
-    const int npt = __popc(pr.mask);
-    if (lane < kPT && ((pr.mask >> lane) & 1u)) sl[__popc(pr.mask & ((1u << lane) - 1u))] = lane;
-    __syncwarp();
-    for (int e = lane; e < R * npt; e += 32) {
-      const int qq = e / R, j = e - qq * R;
-      P[j * kPT + qq] = f64_to_f32_bits(a.p[(l0 + sl[qq]) * a.n_lambda + gd[j]]);
-    }
-    __syncwarp();
-    for (int r0 = 0; r0 < R; r0 += 32) {
-      const int r = r0 + lane;
-      float acc[kPT];
-#pragma unroll
-      for (int qq = 0; qq < kPT; ++qq) acc[qq] = 0.f;
-      if (r < R) {
-#pragma unroll 4
-        for (int j = 0; j < R; ++j) {
-          const float f = phT[(int64_t)j * R + r];
-          const float* Pj = P + j * kPT;
-#pragma unroll
-          for (int qq = 0; qq < kPT; ++qq)
-            if (qq < npt) acc[qq] = fmaf(f, Pj[qq], acc[qq]);
-        }
-#pragma unroll
-        for (int qq = 0; qq < kPT; ++qq)
-          if (qq < npt) Yt[sl[qq] * NY + yb + r] = acc[qq];
-      }
-    }
-    __syncwarp();
-  }
-  __syncthreads();
-  for (int q = warp; q < kPT; q += nwarps) {
-    const int64_t l = l0 + q;
-    if (l >= a.n_pts || a.pstat[l] != 0) continue;
-    cg_point_update(a, l, Yt + q * NY, it, rtol, replace_ratio, pause_ratio);
-  }
-}
-
-size_t cg32_smem(const sfb_ctx* c, int max_r, int nwarps) {
-  return sizeof(float) * ((((size_t)kPT * c->NY + 3) & ~size_t(3)) + (size_t)nwarps * max_r * kPT) +
-         sizeof(int) * (size_t)nwarps * kPT + sizeof(CgPair) * (size_t)(c->subs.size() + 1) * kPT;
-}
-
 // FP64 residual replacement of the mixed CG, one warp per point due (paused
 // or flagged), on the FP64 products Y = Phi (R lambda): r = g - S lambda. The
 // point has converged if ||r|| <= rtol ||g||; otherwise it continues from the
@@ -1349,19 +1210,9 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   const int chunk = c->opt_cg_chunk;
   const bool mixed = krylov == SFB_CG_MIXED;
   const double replace_ratio = c->opt_cg_replace, pause_ratio = 0.1 * c->opt_cg_replace;
-  // the mixed CG runs its FP32 iterations as one fused kernel when the tile fits
-  const size_t smf = cg32_smem(c, maxR, 8);
-  const bool fused = mixed && c->opt_cg_fused && smf <= 200 * 1024;
-  if (fused) CK(cudaFuncSetAttribute(cg32_iter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf));
   int it = 0;
   for (; it < max_it;) {
     for (int q = 0; q < chunk && it < max_it; ++q, ++it) {
-      if (fused) {
-        cg32_iter_kernel<<<(int)((n_pts + kPT - 1) / kPT), 256, smf, st>>>(a, it, rtol, replace_ratio, pause_ratio,
-                                                                          maxR);
-        ++c->launches;
-        continue;
-      }
       if (mixed) matvec_kernel<float><<<mgrid, 256, smv32, st>>>(a, d.p, 0, d.active + 2);
       else matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.p, 0, d.active + 2);
       ++c->launches;

@@ -860,9 +860,6 @@ sfb_status sfb_set_option(sfb_ctx* c, const char* name, double value) {
   } else if (n == "cg_check_every") {
     if (!(value >= 1 && value <= 1000)) return fail(c, SFB_ERR_ARG, "cg_check_every must lie in [1, 1000]");
     c->opt_cg_chunk = (int)value;
-  } else if (n == "cg_fused") {
-    if (!(value == 0 || value == 1)) return fail(c, SFB_ERR_ARG, "cg_fused must be 0 or 1");
-    c->opt_cg_fused = (int)value;
   } else if (n == "cg_replace_ratio") {
     if (!(value >= 1e-4 && value < 1)) return fail(c, SFB_ERR_ARG, "cg_replace_ratio must lie in [1e-4, 1)");
     c->opt_cg_replace = value;

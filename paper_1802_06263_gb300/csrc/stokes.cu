@@ -201,7 +201,7 @@ __global__ void stokes_flux(const double* nb, const int* nb_node, int nbn, int R
     const int o = j < Rs ? l * Rs + j : Rs * Rs + l;
     const double v = j < Rs ? -acc : acc;
     phi[o] = v;
-    phi32[j < Rs ? j * Rs + l : o] = (float)v;   // transposed FP32 copy
+    phi32[o] = (float)v;
   }
 }
 

@@ -106,21 +106,3 @@ def test_not_converged_is_reported():
     lam, it, rc = s.solve_host(y, wt, rtol=1e-14, max_it=2, check=False)
     assert rc == sfb.SFB_ERR_NOT_CONVERGED
     assert np.all(it == -2)
-
-
-@pytest.mark.parametrize("fused", [0, 1])
-@pytest.mark.parametrize("key", ["medium", "ragged"])
-def test_mixed_cg_kernels_agree(key, fused):
-    """The mixed CG reaches the FP64 tolerance with its FP32 iterations fused
-    into one kernel per tile of points and with separate product and update
-    kernels."""
-    p, y, wt, lams, mom = oracle_case(key)
-    s, _ = _solver(key, 0)
-    s.set_option("cg_fused", fused)
-    lam, it, rc = s.solve_host(y, wt, rtol=1e-13, max_it=5000, krylov=1)
-    assert rc == 0 and np.all(it > 0)
-    assert rel(lam, lams) < 1e-9
-    for f in ("darcy_p", "stokes_u"):
-        m, v = s.moments(f)
-        assert rel(m, mom[f][0]) < 1e-9
-        assert rel(v, mom[f][1]) < 1e-8
