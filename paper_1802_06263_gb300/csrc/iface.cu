@@ -389,7 +389,11 @@ __global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed, doubl
   pq = warp_sum(pq);
   const double rr = a.rr[l];
   const bool brk = !(pq > 0.0);
-  const double alpha = brk ? 0.0 : rr / pq;
+  // scalar FP64 divisions and roots once per point (lane 0), then broadcast:
+  // on this part FP64 issues at 1/64 of the FP32 rate
+  double alpha = 0.0;
+  if (lane == 0 && !brk) alpha = rr / pq;
+  alpha = __shfl_sync(0xffffffffu, alpha, 0);
   double rn = 0.0;
   double rv_keep[kRegs ? kUpd : 1];
   if (kRegs) {
@@ -415,17 +419,22 @@ __global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed, doubl
     }
   }
   rn = warp_sum(rn);
-  const double rnorm = sqrt(rn);
-  bool done, pause = false, flag = false;
-  if (mixed) {
-    done = false;
-    pause = brk || rnorm <= fmax(rtol * a.gn[l], pause_ratio * a.rlast[l]);
-    flag = rnorm <= replace_ratio * a.rlast[l];
-  } else {
-    done = rnorm <= rtol * a.gn[l] || brk;
+  int dec = 0;   // bit 0 done, bit 1 pause, bit 2 flag
+  double beta = 0.0;
+  if (lane == 0) {
+    const double rnorm = sqrt(rn);
+    if (mixed) {
+      dec |= (brk || rnorm <= fmax(rtol * a.gn[l], pause_ratio * a.rlast[l])) ? 2 : 0;
+      dec |= rnorm <= replace_ratio * a.rlast[l] ? 4 : 0;
+    } else {
+      dec |= (rnorm <= rtol * a.gn[l] || brk) ? 1 : 0;
+    }
+    if (!(dec & 1) && !brk) beta = rn / rr;
   }
+  dec = __shfl_sync(0xffffffffu, dec, 0);
+  beta = __shfl_sync(0xffffffffu, beta, 0);
+  const bool done = dec & 1, pause = dec & 2, flag = dec & 4;
   if (!done && !brk) {
-    const double beta = rn / rr;
     if (kRegs) {
 #pragma unroll
       for (int j = 0; j < kUpd; ++j) {
@@ -738,10 +747,141 @@ __device__ __forceinline__ void darcy_moments_tile(const MomArgs& m, double* sm,
 __global__ void __launch_bounds__(kMomT) darcy_moments_kernel(MomArgs m) {
   extern __shared__ __align__(16) double sm[];
   int gsub = 0;
-  if (m.mode == 0) {
-    darcy_moments_tile(m, sm, blockIdx.y, 0, gsub);
-  } else {
-    for (int s = 0; s < m.ia.ns; ++s) darcy_moments_tile(m, sm, s, blockIdx.z, gsub);
+  darcy_moments_tile(m, sm, blockIdx.y, 0, gsub);
+}
+
+// The point-by-point sub-tiles of kTP points of every subdomain, in
+// subdomain order: work[i] = (subdomain, tile, first point in the tile).
+// One CTA: per subdomain a block scan of the sub-tile counts of its tiles.
+__global__ void __launch_bounds__(256) moments_worklist_kernel(MomArgs m, int4* work, int* nwork) {
+  __shared__ int wsum[32];
+  __shared__ int base_s;
+  const IfaceArgs& a = m.ia;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  if (threadIdx.x == 0) base_s = 0;
+  __syncthreads();
+  for (int s = 0; s < a.ns; ++s) {
+    const SubDev& S = a.subs[s];
+    const int nt = a.n_tiles[s];
+    for (int t0 = 0; t0 < nt; t0 += blockDim.x) {
+      const int t = t0 + threadIdx.x;
+      int cnt = 0;
+      if (t < nt) {
+        const int* tl = a.tiles + 3 * ((int64_t)s * a.max_tiles + t);
+        if (!big_group(m, S, s, tl[0])) cnt = (tl[2] + kTP - 1) / kTP;
+      }
+      int v = cnt;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
+      }
+      if (lane == 31) wsum[warp] = v;
+      __syncthreads();
+      if (warp == 0) {
+        int w = lane < nwarps ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int n = __shfl_up_sync(0xffffffffu, w, o);
+          if (lane >= o) w += n;
+        }
+        if (lane < nwarps) wsum[lane] = w;
+      }
+      __syncthreads();
+      const int excl = v - cnt + (warp > 0 ? wsum[warp - 1] : 0);
+      const int total = wsum[nwarps - 1];
+      const int base = base_s;
+      for (int q = 0; q < cnt; ++q) work[base + excl + q] = make_int4(s, t, q * kTP, 0);
+      __syncthreads();
+      if (threadIdx.x == 0) base_s = base + total;
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) *nwork = base_s;
+}
+
+// Mode-1 accumulation over the work list: CTA (row tile, chunk) takes every
+// n_chunks-th sub-tile of the list and keeps register accumulators for the
+// entries of its row tile of the current subdomain, writing them to partial
+// slot `chunk` when the list moves to the next subdomain. Slots of
+// (subdomain, chunk) pairs without work stay at the zeros written before.
+__global__ void __launch_bounds__(kMomT) darcy_moments_list_kernel(MomArgs m, const int4* work, const int* nwork) {
+  extern __shared__ __align__(16) double sm[];
+  const IfaceArgs& a = m.ia;
+  const int ch = blockIdx.z;
+  const int nw = *nwork;
+  int cur = -1;
+  bool valid = false;
+  SubDev S;
+  int nx = 0, ny = 0, R = 0, C = 0, nc = 0, r0 = 0, r1 = 0, h0 = 0, ncell = 0, n_ent = 0;
+  double ihx = 0.0, ihy = 0.0;
+  double sh[kMaxE], acc1[kMaxE], acc2[kMaxE];
+  for (int e = ch;; e += m.n_chunks) {
+    const int4 w = e < nw ? work[e] : make_int4(-1, 0, 0, 0);
+    if (w.x != cur) {
+      if (cur >= 0 && valid) {
+#pragma unroll
+        for (int j = 0; j < kMaxE; ++j) {
+          const int64_t el = threadIdx.x + (int64_t)j * kMomT;
+          if (el >= n_ent) break;
+          const int64_t ge = darcy_entry(S, m, cur, el, r0, r1);
+          m.part[((int64_t)ch * 2) * m.len_d + ge] = acc1[j];
+          m.part[((int64_t)ch * 2 + 1) * m.len_d + ge] = acc2[j];
+        }
+      }
+      if (w.x < 0) break;
+      cur = w.x;
+      S = a.subs[cur];
+      nx = S.nx; ny = S.ny; R = S.R; C = R + 1; nc = nx * ny;
+      r0 = blockIdx.x * m.rt;
+      valid = r0 < ny;
+      r1 = min(ny, r0 + m.rt);
+      h0 = max(0, r0 - 1);
+      ncell = (r1 - h0) * nx;
+      n_ent = valid ? (r1 - r0) * nx + (r1 - r0) * (nx + 1) + ((r1 == ny ? ny + 1 : r1) - r0) * nx : 0;
+      ihx = 1.0 / S.hx; ihy = 1.0 / S.hy;
+#pragma unroll
+      for (int q = 0; q < kMaxE; ++q) {
+        const int64_t el = threadIdx.x + (int64_t)q * kMomT;
+        sh[q] = el < n_ent ? m.shift[darcy_entry(S, m, cur, el, r0, r1)] : 0.0;
+        acc1[q] = 0.0;
+        acc2[q] = 0.0;
+      }
+    }
+    if (!valid) continue;
+    const int* tl = a.tiles + 3 * ((int64_t)cur * a.max_tiles + w.y);
+    const int k = tl[0];
+    const ItemOff off = a.off[S.item0 + k];
+    const double* X = m.X + off.x;
+    const double* Tx = m.T + off.t;
+    const double* Ty = Tx + (int64_t)ny * (nx + 1);
+    const int* pts = a.grp_pts + (int64_t)cur * a.pts_ld + tl[1] + w.z;
+    const int cntp = min(kTP, tl[2] - w.z);
+    const int64_t* gd = a.gdof + S.gdof_off;
+    double* Cf = sm;                  // [kTP][C]
+    double* Z = Cf + kTP * C;         // [ncell][kTP]
+    double* Wt = Z + ncell * kTP;     // [kTP]
+    __syncthreads();
+    for (int e2 = threadIdx.x; e2 < cntp * C; e2 += blockDim.x) {
+      const int q = e2 / C, i = e2 - q * C;
+      Cf[e2] = i < R ? a.lam[(int64_t)pts[q] * a.n_lambda + gd[i]] : 1.0;
+    }
+    for (int q = threadIdx.x; q < kTP; q += blockDim.x) Wt[q] = q < cntp ? m.w[pts[q]] : 0.0;
+    __syncthreads();
+    if (cntp == 1) field_rows<1>(X + (int64_t)h0 * nx, nc, C, ncell, Cf, Z);
+    else if (cntp == 2) field_rows<2>(X + (int64_t)h0 * nx, nc, C, ncell, Cf, Z);
+    else if (cntp <= 4) field_rows<4>(X + (int64_t)h0 * nx, nc, C, ncell, Cf, Z);
+    else field_rows<kTP>(X + (int64_t)h0 * nx, nc, C, ncell, Cf, Z);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kMaxE; ++j) {
+      const int64_t el = threadIdx.x + (int64_t)j * kMomT;
+      if (el >= n_ent) break;
+      for (int q = 0; q < cntp; ++q) {
+        const double v = darcy_value(S, m, el, r0, r1, h0, Tx, Ty, Z, Cf, q, C, ihx, ihy);
+        const double d = v - sh[j];
+        acc1[j] = fma(Wt[q], d, acc1[j]);
+        acc2[j] = fma(Wt[q] * d, d, acc2[j]);
+      }
+    }
   }
 }
 
@@ -1296,7 +1436,11 @@ sfb_status moments_accumulate_device(sfb_ctx* c, int64_t n_pts) {
     CK(cudaGetLastError());
   }
   m.mode = 1;
-  darcy_moments_kernel<<<dim3(row_tiles, 1, m.n_chunks), kMomT, smd, st>>>(m);
+  CK(cudaFuncSetAttribute(darcy_moments_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd));
+  CK(cudaMemsetAsync(d.mom_part, 0, sizeof(double) * 2 * (size_t)m.n_chunks * m.len_d, st));
+  moments_worklist_kernel<<<1, 256, 0, st>>>(m, d.mom_work, d.active + 3);
+  ++c->launches;
+  darcy_moments_list_kernel<<<dim3(row_tiles, 1, m.n_chunks), kMomT, smd, st>>>(m, d.mom_work, d.active + 3);
   ++c->launches;
   CK(cudaGetLastError());
   int max_local = 1;

@@ -121,6 +121,7 @@ struct Dev {
   double* mom = nullptr;      // Darcy entries: shift, S1, S2
   double* mom_w = nullptr;
   double* mom_part = nullptr; // [chunks][2][Darcy entries] partial sums of a batch
+  int4* mom_work = nullptr;   // point-by-point moment sub-tiles (subdomain, tile, first point)
   double* st_c0 = nullptr;    // Stokes: coefficients of the shift point
   double* st_m = nullptr;     // Stokes: sum w (c - c0)
   double* st_M = nullptr;     // Stokes: sum w (c - c0)(c - c0)^T

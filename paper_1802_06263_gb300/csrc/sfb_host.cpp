@@ -288,6 +288,7 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   d.mom = cv.take<double>((size_t)3 * len_d);
   d.mom_w = cv.take<double>(2);
   d.mom_part = cv.take<double>((size_t)2 * (c->mom_chunks + 1) * len_d);   // + the large-group slot
+  d.mom_work = cv.take<int4>((size_t)ns * ((std::max<int64_t>(max_pts, 1) + 7) / 8 + c->max_tiles + 1));
   {
     int maxC = 1;
     for (const HostSub& S : c->subs) maxC = std::max(maxC, (int)S.dofs.size() + 1);
