@@ -16,6 +16,7 @@
 //          fixed order (deterministic, no atomics on floating point).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "sfb_ctx.h"
 
@@ -753,7 +754,8 @@ __global__ void __launch_bounds__(kMomT) darcy_moments_kernel(MomArgs m) {
 // The point-by-point sub-tiles of kTP points of every subdomain, in
 // subdomain order: work[i] = (subdomain, tile, first point in the tile).
 // One CTA: per subdomain a block scan of the sub-tile counts of its tiles.
-__global__ void __launch_bounds__(256) moments_worklist_kernel(MomArgs m, int4* work, int* nwork) {
+__global__ void __launch_bounds__(256) moments_worklist_kernel(MomArgs m, int4* work, int* nwork, int cap,
+                                                                int* err) {
   __shared__ int wsum[32];
   __shared__ int base_s;
   const IfaceArgs& a = m.ia;
@@ -789,13 +791,16 @@ __global__ void __launch_bounds__(256) moments_worklist_kernel(MomArgs m, int4* 
       const int excl = v - cnt + (warp > 0 ? wsum[warp - 1] : 0);
       const int total = wsum[nwarps - 1];
       const int base = base_s;
-      for (int q = 0; q < cnt; ++q) work[base + excl + q] = make_int4(s, t, q * kTP, 0);
+      for (int q = 0; q < cnt; ++q) {
+        if (base + excl + q < cap) work[base + excl + q] = make_int4(s, t, q * kTP, 0);
+        else atomicOr(err, 4);   // list longer than its buffer: the entry is dropped
+      }
       __syncthreads();
       if (threadIdx.x == 0) base_s = base + total;
       __syncthreads();
     }
   }
-  if (threadIdx.x == 0) *nwork = base_s;
+  if (threadIdx.x == 0) *nwork = min(base_s, cap);
 }
 
 // Mode-1 accumulation over the work list: CTA (row tile, chunk) takes every
@@ -803,7 +808,8 @@ __global__ void __launch_bounds__(256) moments_worklist_kernel(MomArgs m, int4* 
 // entries of its row tile of the current subdomain, writing them to partial
 // slot `chunk` when the list moves to the next subdomain. Slots of
 // (subdomain, chunk) pairs without work stay at the zeros written before.
-__global__ void __launch_bounds__(kMomT) darcy_moments_list_kernel(MomArgs m, const int4* work, const int* nwork) {
+__global__ void __launch_bounds__(kMomT) darcy_moments_list_kernel(MomArgs m, const int4* work, const int* nwork,
+                                                                  int* err) {
   extern __shared__ __align__(16) double sm[];
   const IfaceArgs& a = m.ia;
   const int ch = blockIdx.z;
@@ -814,20 +820,27 @@ __global__ void __launch_bounds__(kMomT) darcy_moments_list_kernel(MomArgs m, co
   int nx = 0, ny = 0, R = 0, C = 0, nc = 0, r0 = 0, r1 = 0, h0 = 0, ncell = 0, n_ent = 0;
   double ihx = 0.0, ihy = 0.0;
   double sh[kMaxE], acc1[kMaxE], acc2[kMaxE];
-  for (int e = ch;; e += m.n_chunks) {
-    const int4 w = e < nw ? work[e] : make_int4(-1, 0, 0, 0);
-    if (w.x != cur) {
-      if (cur >= 0 && valid) {
+  // the accumulators of the current subdomain's row tile into slot ch
+  auto flush = [&]() {
+    if (cur < 0 || !valid) return;
 #pragma unroll
-        for (int j = 0; j < kMaxE; ++j) {
-          const int64_t el = threadIdx.x + (int64_t)j * kMomT;
-          if (el >= n_ent) break;
-          const int64_t ge = darcy_entry(S, m, cur, el, r0, r1);
-          m.part[((int64_t)ch * 2) * m.len_d + ge] = acc1[j];
-          m.part[((int64_t)ch * 2 + 1) * m.len_d + ge] = acc2[j];
-        }
+    for (int j = 0; j < kMaxE; ++j) {
+      const int64_t el = threadIdx.x + (int64_t)j * kMomT;
+      if (el >= n_ent) break;
+      const int64_t ge = darcy_entry(S, m, cur, el, r0, r1);
+      m.part[((int64_t)ch * 2) * m.len_d + ge] = acc1[j];
+      m.part[((int64_t)ch * 2 + 1) * m.len_d + ge] = acc2[j];
+    }
+  };
+  for (int e = ch; e < nw; e += m.n_chunks) {
+    const int4 w = work[e];
+    if (w.x != cur) {
+      flush();
+      if (w.x < 0 || w.x >= a.ns) {   // a malformed list entry ends this CTA's walk and is reported
+        if (threadIdx.x == 0) atomicOr(err, 8);
+        cur = -1;
+        break;
       }
-      if (w.x < 0) break;
       cur = w.x;
       S = a.subs[cur];
       nx = S.nx; ny = S.ny; R = S.R; C = R + 1; nc = nx * ny;
@@ -847,8 +860,16 @@ __global__ void __launch_bounds__(kMomT) darcy_moments_list_kernel(MomArgs m, co
       }
     }
     if (!valid) continue;
+    if (w.y < 0 || w.y >= a.n_tiles[cur]) {   // a malformed list entry is skipped and reported
+      if (threadIdx.x == 0) atomicOr(err, 8);
+      continue;
+    }
     const int* tl = a.tiles + 3 * ((int64_t)cur * a.max_tiles + w.y);
     const int k = tl[0];
+    if (k < 0 || k >= S.n_local || w.z < 0 || w.z >= tl[2] || tl[1] < 0 || tl[1] + tl[2] > a.n_pts) {
+      if (threadIdx.x == 0) atomicOr(err, 16);
+      continue;
+    }
     const ItemOff off = a.off[S.item0 + k];
     const double* X = m.X + off.x;
     const double* Tx = m.T + off.t;
@@ -883,6 +904,7 @@ __global__ void __launch_bounds__(kMomT) darcy_moments_list_kernel(MomArgs m, co
       }
     }
   }
+  flush();
 }
 
 constexpr int kGChunks = 16;   // point chunks per large group (partials reduced in order)
@@ -1406,6 +1428,20 @@ sfb_status moments_accumulate_device(sfb_ctx* c, int64_t n_pts) {
   const int ns = (int)c->subs.size();
   cudaError_t e;
 #define CK(x) do { e = (x); if (e != cudaSuccess) { c->err = std::string("moments: ") + cudaGetErrorString(e); return SFB_ERR_CUDA; } } while (0)
+  // SFB_SYNC_CHECK=1: synchronise after every launch and name the kernel that failed
+  static const bool sync_check = getenv("SFB_SYNC_CHECK") && getenv("SFB_SYNC_CHECK")[0] == '1';
+#define LAUNCHED(name)                                                                         \
+  do {                                                                                         \
+    ++c->launches;                                                                             \
+    if (sync_check) {                                                                          \
+      e = cudaStreamSynchronize(st);                                                           \
+      if (e == cudaSuccess) e = cudaGetLastError();                                            \
+      if (e != cudaSuccess) {                                                                  \
+        c->err = std::string("moments kernel ") + name + ": " + cudaGetErrorString(e);         \
+        return SFB_ERR_CUDA;                                                                   \
+      }                                                                                        \
+    }                                                                                          \
+  } while (0)
   MomArgs m;
   m.ia = make_args(c, n_pts);
   m.X = d.X; m.T = d.T; m.proj = d.proj; m.w = d.w;
@@ -1432,23 +1468,24 @@ sfb_status moments_accumulate_device(sfb_ctx* c, int64_t n_pts) {
   if (first) {
     m.mode = 0;
     darcy_moments_kernel<<<dim3(row_tiles, ns, 1), kMomT, smd, st>>>(m);
-    ++c->launches;
+    LAUNCHED("darcy_moments_kernel");
     CK(cudaGetLastError());
   }
   m.mode = 1;
   CK(cudaFuncSetAttribute(darcy_moments_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd));
   CK(cudaMemsetAsync(d.mom_part, 0, sizeof(double) * 2 * (size_t)m.n_chunks * m.len_d, st));
-  moments_worklist_kernel<<<1, 256, 0, st>>>(m, d.mom_work, d.active + 3);
-  ++c->launches;
-  darcy_moments_list_kernel<<<dim3(row_tiles, 1, m.n_chunks), kMomT, smd, st>>>(m, d.mom_work, d.active + 3);
-  ++c->launches;
+  moments_worklist_kernel<<<1, 256, 0, st>>>(m, d.mom_work, d.active + 3, c->mom_work_cap, d.active + 2);
+  LAUNCHED("moments_worklist_kernel");
+  darcy_moments_list_kernel<<<dim3(row_tiles, 1, m.n_chunks), kMomT, smd, st>>>(m, d.mom_work, d.active + 3,
+                                                                               d.active + 2);
+  LAUNCHED("darcy_moments_list_kernel");
   CK(cudaGetLastError());
   int max_local = 1;
   for (int nl : c->n_local) max_local = std::max(max_local, nl);
   group_moments_kernel<<<dim3(max_local, ns, kGChunks), 256, 0, st>>>(m, d.gmom_part);
-  ++c->launches;
+  LAUNCHED("group_moments_kernel");
   group_moments_reduce<<<dim3(max_local, ns), 256, 0, st>>>(m, d.gmom_part);
-  ++c->launches;
+  LAUNCHED("group_moments_reduce");
   int big_t = kBigT;
   auto smb_of = [&](int t) { return sizeof(double) * ((size_t)maxC * maxC + 2 * (size_t)maxC + (size_t)maxC * t); };
   while (big_t > 32 && smb_of(big_t) > 227 * 1024) big_t >>= 1;
@@ -1457,23 +1494,24 @@ sfb_status moments_accumulate_device(sfb_ctx* c, int64_t n_pts) {
   int max_ent = 0;
   for (const HostSub& S : c->subs) max_ent = std::max(max_ent, S.ny * S.nx + S.ny * (S.nx + 1) + (S.ny + 1) * S.nx);
   bigroup_moments_kernel<<<dim3((max_ent + big_t * kBigE - 1) / (big_t * kBigE), ns), big_t, smb, st>>>(m, m.n_chunks);
-  ++c->launches;
+  LAUNCHED("bigroup_moments_kernel");
   CK(cudaGetLastError());
   reduce_partials<<<256, 256, 0, st>>>(d.mom_part, m.n_chunks + 1, m.len_d, d.mom + m.len_d, d.mom + 2 * m.len_d);
-  ++c->launches;
+  LAUNCHED("reduce_partials");
   CK(cudaEventRecord(c->ev[4], st));
   const int Cs = (int)c->stokes.dofs.size() + 1;
   stokes_cov_kernel<<<kStokesChunks, 256, 0, st>>>(m.ia, d.w, first, d.st_c0, d.st_part);
-  ++c->launches;
+  LAUNCHED("stokes_cov_kernel");
   stokes_cov_reduce<<<32, 256, 0, st>>>(d.st_part, Cs, d.st_m, d.st_M);
-  ++c->launches;
+  LAUNCHED("stokes_cov_reduce");
   CK(cudaGetLastError());
   c->mom_shift_set = true;
   weight_sum<<<1, 256, 0, st>>>(d.w, n_pts, d.mom_w);
-  ++c->launches;
+  LAUNCHED("weight_sum");
   CK(cudaGetLastError());
   CK(cudaEventRecord(c->ev[5], st));
   return SFB_OK;
+#undef LAUNCHED
 #undef CK
 }
 

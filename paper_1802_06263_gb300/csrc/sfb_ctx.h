@@ -169,6 +169,7 @@ struct sfb_ctx {
   int64_t mom_off[4] = {0, 0, 0, 0};
   bool mom_shift_set = false;
   int mom_chunks = 1;
+  int mom_work_cap = 0;       // entries of dev.mom_work
   int64_t gmom_stride = 1;
   // options (sfb_set_option)
   double opt_refine_tol = 1e-10;

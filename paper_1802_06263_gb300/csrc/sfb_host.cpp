@@ -288,7 +288,8 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   d.mom = cv.take<double>((size_t)3 * len_d);
   d.mom_w = cv.take<double>(2);
   d.mom_part = cv.take<double>((size_t)2 * (c->mom_chunks + 1) * len_d);   // + the large-group slot
-  d.mom_work = cv.take<int4>((size_t)ns * ((std::max<int64_t>(max_pts, 1) + 7) / 8 + c->max_tiles + 1));
+  c->mom_work_cap = (int)((int64_t)ns * ((std::max<int64_t>(max_pts, 1) + 7) / 8 + c->max_tiles + 1));
+  d.mom_work = cv.take<int4>((size_t)c->mom_work_cap);
   {
     int maxC = 1;
     for (const HostSub& S : c->subs) maxC = std::max(maxC, (int)S.dofs.size() + 1);
@@ -807,7 +808,11 @@ sfb_status sfb_interface_solve_batch(sfb_ctx* c, const double* y, const double* 
              "copy lambda");
   if (iters_out)
     SFB_CUDA(cudaMemcpyAsync(iters_out, d.pstat, sizeof(int) * n_pts, cudaMemcpyDefault, st), "copy iters");
+  int mflags = 0;
+  SFB_CUDA(cudaMemcpyAsync(&mflags, d.active + 2, sizeof(int), cudaMemcpyDeviceToHost, st), "copy flags");
   SFB_CUDA(cudaStreamSynchronize(st), "interface solve");
+  if (mflags & (4 | 8 | 16))
+    return fail(c, SFB_ERR_CUDA, "moments: malformed point-by-point work list (flags " + std::to_string(mflags) + ")");
   c->n_solved += n_pts;
   if (n_failed) return fail(c, SFB_ERR_NOT_CONVERGED, std::to_string(n_failed) + " points did not converge");
   return SFB_OK;
