@@ -167,6 +167,7 @@ struct IfaceArgs {
   double* gn;
   double* rlast;        // mixed CG: norm of the last FP64 residual
   int* rflag;           // mixed CG: FP64 residual due at the next check
+  double* dinv;         // Jacobi preconditioner: 1 / diag(S^l) per point, or null (plain CG)
   int* pstat;
   int64_t n_pts;
 };
@@ -213,13 +214,15 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // r = g = sum_i R_i^T g_i^{k_i(l)}, p = r, lambda = 0; one warp per point.
+// With the Jacobi preconditioner dinv = 1 / diag(S^l), z = dinv r, p = z and
+// rr holds r.z; without it z = r and rr = r.r.
 __global__ void init_kernel(IfaceArgs a) {
   const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (l >= a.n_pts) return;
-  double s2 = 0.0;
+  double s2 = 0.0, rz = 0.0;
   for (int64_t d = lane; d < a.n_lambda; d += 32) {
-    double g = 0.0;
+    double g = 0.0, dg = 0.0;
     for (int side = 0; side < 2; ++side) {
       const int u = a.ldof[4 * d + 2 * side], loc = a.ldof[4 * d + 2 * side + 1];
       int R;
@@ -227,15 +230,24 @@ __global__ void init_kernel(IfaceArgs a) {
       if (k < 0) continue;
       const double* ph = unit_phi(a, u, k, R);
       g += ph[R * R + loc];
+      dg += ph[loc * R + loc];
+    }
+    double z = g;
+    if (a.dinv) {
+      const double di = dg > 0.0 ? 1.0 / dg : 1.0;
+      a.dinv[l * a.n_lambda + d] = di;
+      z = di * g;
     }
     a.r[l * a.n_lambda + d] = g;
-    a.p[l * a.n_lambda + d] = g;
+    a.p[l * a.n_lambda + d] = z;
     a.lam[l * a.n_lambda + d] = 0.0;
     s2 += g * g;
+    rz += g * z;
   }
   s2 = warp_sum(s2);
+  rz = warp_sum(rz);
   if (lane == 0) {
-    a.rr[l] = s2;
+    a.rr[l] = rz;
     a.gn[l] = sqrt(s2);
     a.rlast[l] = sqrt(s2);
     a.rflag[l] = 0;
@@ -284,6 +296,12 @@ __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, const double* 
   const int rr4 = (R * R + 3) & ~3;
   T* Ph = reinterpret_cast<T*>(smv_raw);   // [R][R]
   T* Pv = Ph + rr4;                        // [R][kTG + 1]
+  // the selected points' indices and the unit's global DOFs, staged once so
+  // that each gathered entry is a single dependent global load
+  __shared__ int64_t spt[kTG];
+  __shared__ int sgd[kMaxCols];
+  if (threadIdx.x < nsel) spt[threadIdx.x] = pts[sidx[threadIdx.x]];
+  for (int i = threadIdx.x; i < R; i += blockDim.x) sgd[i] = (int)gd[i];
   const uint32_t bytes = (uint32_t)((R * R * (int)sizeof(T) + 15) & ~15);
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
@@ -295,11 +313,11 @@ __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, const double* 
                  "l"(ph), "r"(bytes), "r"(smem_u32(&bar))
                  : "memory");
   }
-  __syncthreads();  // the initialised barrier is visible to every thread
+  __syncthreads();  // the initialised barrier, spt and sgd are visible to every thread
   for (int e = threadIdx.x; e < nsel4 * R; e += blockDim.x) {
     const int q = e / R, i = e - q * R;
     double v = 0.0;
-    if (q < nsel) v = vin[(int64_t)pts[sidx[q]] * a.n_lambda + gd[i]];
+    if (q < nsel) v = vin[spt[q] * a.n_lambda + sgd[i]];
     Pv[i * (kTG + 1) + q] = from_f64<T>(v);
   }
   uint32_t ok = 0;
@@ -341,8 +359,7 @@ __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, const double* 
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (c0 + q >= nsel) break;
-      const int64_t l = pts[sidx[c0 + q]];
-      double* y = a.Y + l * a.NY + a.ybase[u];
+      double* y = a.Y + spt[c0 + q] * a.NY + a.ybase[u];
       y[r0] = to_f64(acc[0][q]);
       if (two) y[r0 + 1] = to_f64(acc[1][q]);
     }
@@ -395,7 +412,9 @@ __global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed, doubl
   double alpha = 0.0;
   if (lane == 0 && !brk) alpha = rr / pq;
   alpha = __shfl_sync(0xffffffffu, alpha, 0);
-  double rn = 0.0;
+  // rn = r.r (stopping test), rz = r.z with z = dinv r (= rn without preconditioner)
+  double rn = 0.0, rz = 0.0;
+  const double* dl = a.dinv ? a.dinv + l * a.n_lambda : nullptr;
   double rv_keep[kRegs ? kUpd : 1];
   if (kRegs) {
 #pragma unroll
@@ -406,8 +425,10 @@ __global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed, doubl
         ll[d] = fma(alpha, pv[j], ll[d]);
         const double rv = fma(-alpha, qv[j], rl[d]);
         rl[d] = rv;
-        rv_keep[j] = rv;
         rn = fma(rv, rv, rn);
+        const double zv = dl ? dl[d] * rv : rv;
+        rv_keep[j] = zv;
+        rz = fma(rv, zv, rz);
       }
     }
   } else {
@@ -417,9 +438,11 @@ __global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed, doubl
       const double rv = rl[d] - alpha * q;
       rl[d] = rv;
       rn += rv * rv;
+      rz += rv * (dl ? dl[d] * rv : rv);
     }
   }
   rn = warp_sum(rn);
+  rz = dl ? warp_sum(rz) : rn;
   int dec = 0;   // bit 0 done, bit 1 pause, bit 2 flag
   double beta = 0.0;
   if (lane == 0) {
@@ -430,7 +453,7 @@ __global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed, doubl
     } else {
       dec |= (rnorm <= rtol * a.gn[l] || brk) ? 1 : 0;
     }
-    if (!(dec & 1) && !brk) beta = rn / rr;
+    if (!(dec & 1) && !brk) beta = rz / rr;
   }
   dec = __shfl_sync(0xffffffffu, dec, 0);
   beta = __shfl_sync(0xffffffffu, beta, 0);
@@ -443,12 +466,12 @@ __global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed, doubl
         if (d < n) pl[d] = fma(beta, pv[j], rv_keep[j]);
       }
     } else {
-      for (int d = lane; d < n; d += 32) pl[d] = rl[d] + beta * pl[d];
+      for (int d = lane; d < n; d += 32) pl[d] = (dl ? dl[d] * rl[d] : rl[d]) + beta * pl[d];
     }
   }
   __syncwarp();
   if (lane == 0) {
-    a.rr[l] = rn;
+    a.rr[l] = rz;
     if (done) a.pstat[l] = brk ? -(it + 1) : it + 1;
     else if (pause) a.pstat[l] = kPending | (brk ? kRestart : 0) | (it + 1);
     else if (flag) a.rflag[l] = 1;
@@ -467,7 +490,7 @@ __global__ void reliable_kernel(IfaceArgs a, double rtol, int it) {
   if (!selected(a, l, s, 1)) return;
   const double* Yl = a.Y + l * a.NY;
   double* rl = a.r + l * a.n_lambda;
-  double rn = 0.0;
+  double rn = 0.0, rz = 0.0;
   for (int64_t d = lane; d < a.n_lambda; d += 32) {
     double g = 0.0, q = 0.0;
     for (int side = 0; side < 2; ++side) {
@@ -481,17 +504,19 @@ __global__ void reliable_kernel(IfaceArgs a, double rtol, int it) {
     const double rv = g - q;
     rl[d] = rv;
     rn += rv * rv;
+    rz += rv * (a.dinv ? a.dinv[l * a.n_lambda + d] * rv : rv);
   }
   rn = warp_sum(rn);
+  rz = warp_sum(rz);
   const bool conv = sqrt(rn) <= rtol * a.gn[l];
   if (!conv && (s & kRestart)) {
     double* pl = a.p + l * a.n_lambda;
-    for (int64_t d = lane; d < a.n_lambda; d += 32) pl[d] = rl[d];
+    for (int64_t d = lane; d < a.n_lambda; d += 32) pl[d] = a.dinv ? a.dinv[l * a.n_lambda + d] * rl[d] : rl[d];
   }
   __syncwarp();
   if (lane == 0) {
     a.rflag[l] = 0;
-    a.rr[l] = rn;
+    a.rr[l] = rz;
     a.rlast[l] = sqrt(rn);
     a.pstat[l] = conv ? (s != 0 ? (s & kItMask) : it) : 0;
   }
@@ -1321,6 +1346,7 @@ static IfaceArgs make_args(sfb_ctx* c, int64_t n_pts) {
   a.ldof = d.ldof; a.yoff = d.yoff; a.n_lambda = c->n_lambda; a.kmap = d.kmap; a.grp_pts = d.grp_pts; a.pts_ld = c->ws_pts;
   a.tiles = d.tiles; a.max_tiles = c->max_tiles; a.n_tiles = d.n_tiles; a.lam = d.lam; a.r = d.r; a.p = d.p;
   a.Y = d.Y; a.rr = d.rr; a.gn = d.gn; a.rlast = d.rlast; a.rflag = d.rflag; a.pstat = d.pstat; a.n_pts = n_pts;
+  a.dinv = c->opt_cg_jacobi ? d.dinv : nullptr;
   return a;
 }
 

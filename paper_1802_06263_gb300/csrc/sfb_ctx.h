@@ -107,6 +107,7 @@ struct Dev {
   double* rr = nullptr;
   double* gn = nullptr;
   double* rlast = nullptr;
+  double* dinv = nullptr;     // Jacobi preconditioner of the interface CG, per point
   int* rflag = nullptr;
   int* pstat = nullptr;       // per point: iterations (>0 converged, <0 active/failed)
   int* active = nullptr;
@@ -175,6 +176,7 @@ struct sfb_ctx {
   double opt_refine_tol = 1e-10;
   int opt_refine_max = 8;
   int opt_cg_chunk = 8;
+  int opt_cg_jacobi = 1;        // diagonal (Jacobi) preconditioning of the interface CG
   double opt_cg_replace = 0.1;  // mixed CG: FP64 residual once the recursive one drops by this factor
   double opt_big_factor = 1.0;   // groups above this many times (R+1) points use coefficient moments
   // device-time phase markers of the last interface solve (CUDA events)

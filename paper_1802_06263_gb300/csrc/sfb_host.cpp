@@ -255,6 +255,7 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   d.rr = cv.take<double>(P);
   d.gn = cv.take<double>(P);
   d.rlast = cv.take<double>(P);
+  d.dinv = cv.take<double>((size_t)P * c->n_lambda);
   d.rflag = cv.take<int>(P);
   d.pstat = cv.take<int>(P);
   d.active = cv.take<int>(4);
@@ -866,6 +867,9 @@ sfb_status sfb_set_option(sfb_ctx* c, const char* name, double value) {
   } else if (n == "cg_check_every") {
     if (!(value >= 1 && value <= 1000)) return fail(c, SFB_ERR_ARG, "cg_check_every must lie in [1, 1000]");
     c->opt_cg_chunk = (int)value;
+  } else if (n == "cg_jacobi") {
+    if (!(value == 0 || value == 1)) return fail(c, SFB_ERR_ARG, "cg_jacobi must be 0 or 1");
+    c->opt_cg_jacobi = (int)value;
   } else if (n == "cg_replace_ratio") {
     if (!(value >= 1e-4 && value < 1)) return fail(c, SFB_ERR_ARG, "cg_replace_ratio must lie in [1e-4, 1)");
     c->opt_cg_replace = value;
