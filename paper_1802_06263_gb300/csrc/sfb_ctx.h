@@ -162,6 +162,12 @@ struct sfb_ctx {
   sfb::Dev dev;
   int64_t n_items = 0;
   int max_nx = 0, max_cols = 0, max_R = 0;
+  // basis items come in decreasing cost; the first n_wide have nx > 64 and run
+  // with the wide-grid kernel variant, the rest with the narrow one
+  int64_t n_wide = 0;
+  int wide_nx = 0, wide_cols = 0, narrow_nx = 0, narrow_cols = 0;
+  cudaStream_t side = nullptr;          // second stream for the narrow items
+  cudaEvent_t fork = nullptr, join = nullptr;
   std::vector<sfb::ItemOff> offs;
   std::vector<int64_t> ybase;              // per unit (Darcy subs, then Stokes) offset into Y
   int64_t NY = 0;
@@ -185,5 +191,8 @@ struct sfb_ctx {
   ~sfb_ctx() {
     for (cudaEvent_t e : ev)
       if (e) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (side) cudaStreamDestroy(side);
   }
 };

@@ -601,6 +601,21 @@ sfb_status upload_tables(sfb_ctx* c) {
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
   std::vector<int> item_sub(c->n_items), item_k(c->n_items);
   for (int64_t i = 0; i < c->n_items; ++i) { item_sub[i] = isub[order[i]]; item_k[i] = ik[order[i]]; }
+  // size classes of the item list (wide grids first, since cost grows as nx^3)
+  c->n_wide = 0; c->wide_nx = c->wide_cols = c->narrow_nx = c->narrow_cols = 0;
+  for (int64_t i = 0; i < c->n_items; ++i) {
+    const SubDev& D = sd[item_sub[i]];
+    if (D.nx > 64) {
+      c->n_wide = i + 1;
+      c->wide_nx = std::max(c->wide_nx, D.nx);
+      c->wide_cols = std::max(c->wide_cols, D.R + 1);
+    } else {
+      c->narrow_nx = std::max(c->narrow_nx, D.nx);
+      c->narrow_cols = std::max(c->narrow_cols, D.R + 1);
+    }
+  }
+  for (int64_t i = c->n_wide; i < c->n_items; ++i)
+    if (sd[item_sub[i]].nx > 64) return fail(c, SFB_ERR_ARG, "basis items out of size-class order");
   // interface-solve maps
   const int nu = ns + 1;
   std::vector<int> ldof(4 * c->n_lambda, 0);
@@ -683,15 +698,44 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   SFB_CUDA(cudaEventCreate(&e0), "event");
   SFB_CUDA(cudaEventCreate(&e1), "event");
   SFB_CUDA(cudaEventRecord(e0, st), "event");
-  cudaError_t e;
-  if (prec == SFB_FP64) e = launch_basis_fp64(a, c->max_nx, c->max_cols, st);
-  else e = launch_basis_mixed(a, c->max_nx, c->max_cols, prec == SFB_MIXED ? a.max_refine : 0, st);
+  cudaError_t e = cudaSuccess;
+  {
+    // one launch per size class: wide grids (nx > 64) on the context stream,
+    // narrow grids concurrently on a side stream joined before the epilogue
+    const int refine = prec == SFB_MIXED ? a.max_refine : 0;
+    auto launch = [&](const BasisArgs& aa, int mnx, int mcols, cudaStream_t s2) {
+      return prec == SFB_FP64 ? launch_basis_fp64(aa, mnx, mcols, s2) : launch_basis_mixed(aa, mnx, mcols, refine, s2);
+    };
+    BasisArgs aw = a, an = a;
+    aw.n_items = (int)c->n_wide;
+    an.item_sub = a.item_sub + c->n_wide;
+    an.item_k = a.item_k + c->n_wide;
+    an.n_items = n - (int)c->n_wide;
+    if (c->n_wide == 0) {
+      e = launch(an, c->narrow_nx, c->narrow_cols, st);
+      c->launches += 1;
+    } else if (an.n_items == 0) {
+      e = launch(aw, c->wide_nx, c->wide_cols, st);
+      c->launches += 1;
+    } else {
+      if (!c->side) SFB_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "stream");
+      if (!c->fork) SFB_CUDA(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming), "event");
+      if (!c->join) SFB_CUDA(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming), "event");
+      SFB_CUDA(cudaEventRecord(c->fork, st), "event");
+      SFB_CUDA(cudaStreamWaitEvent(c->side, c->fork, 0), "event");
+      e = launch(aw, c->wide_nx, c->wide_cols, st);
+      if (e == cudaSuccess) e = launch(an, c->narrow_nx, c->narrow_cols, c->side);
+      SFB_CUDA(cudaEventRecord(c->join, c->side), "event");
+      SFB_CUDA(cudaStreamWaitEvent(st, c->join, 0), "event");
+      c->launches += 2;
+    }
+  }
   if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_fail(c, e, "basis kernel"); }
   cudaEvent_t ek;
   SFB_CUDA(cudaEventCreate(&ek), "event");
   SFB_CUDA(cudaEventRecord(ek, st), "event");
   e = launch_flux_epilogue(a, c->max_R, st);
-  c->launches += 2;
+  c->launches += 1;
   if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_fail(c, e, "flux epilogue"); }
   SFB_CUDA(cudaEventRecord(e1, st), "event");
   std::vector<int> status(n), nref(n);
