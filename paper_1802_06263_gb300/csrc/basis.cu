@@ -30,6 +30,8 @@
 // the products G_b U read float4 rows of G_b (symmetric) and of U.
 #include <math.h>
 
+#include <algorithm>
+
 #include "sfb_internal.h"
 
 namespace sfb {
@@ -217,7 +219,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-constexpr int kP = 8;  // pivots per panel of the blocked sweep
+constexpr int kP = kPanel;  // pivots per panel of the blocked sweep
 
 // L2 prefetch of grid row b of all C columns of X (column-major, nx doubles
 // per row segment): one 128-byte line per thread.
@@ -261,14 +263,20 @@ __device__ __forceinline__ void form_block(T (&areg)[MT][4][4], int b, int nx, i
 // Blocked symmetric sweep of the np x np SPD matrix held in register tiles:
 // for each panel K of kP pivots, A_KK -> -A_KK^{-1}, A_KJ -> A_KK^{-1} A_KJ,
 // A_JK -> A_JK A_KK^{-1}, A_JJ -> A_JJ - A_JK A_KK^{-1} A_KJ (the composition
-// of kP single-pivot sweeps). On exit the tiles hold -S^{-1}. The kP x kP
-// inverse is a sweep by warp 0; the rank-kP update reads VT (panel columns)
-// and W = A_KK^{-1} A_K* with 4-wide shared-memory loads.
+// of kP single-pivot sweeps). On exit the tiles hold -S^{-1}.
+// Per panel: (a) the panel columns go to VT; (b) every warp sweeps the kP x kP
+// pivot block in registers (lane p % kP holds row p; the pivot row arrives
+// by shuffles) and forms its share of W = A_KK^{-1} A_K* from VT; (c) the
+// register tiles take the rank-kP update. Three barriers per panel.
 template <typename T, int MT, int NT>
 __device__ __forceinline__ void blocked_sweep(T (&areg)[MT][4][4], int np, int ntr, T* VT, T* W, T* Ablk,
                                               int* bad) {
+  static_assert(kP == 16, "the pivot-block layout puts one row per half-warp lane");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int nwarp = NT / 32;
+  const int p = lane & (kP - 1), half = lane >> 4;
   for (int k0 = 0; k0 < np; k0 += kP) {
-    // (a) panel columns: VT[p][i] = A[i][k0 + p]
+    // (a) panel columns: VT[q][i] = A[i][k0 + q]
 #pragma unroll
     for (int m = 0; m < MT; ++m) {
       const int t = threadIdx.x + m * NT;
@@ -281,56 +289,42 @@ __device__ __forceinline__ void blocked_sweep(T (&areg)[MT][4][4], int np, int n
           for (int q = 0; q < 4; ++q) VT[(j0 + q - k0) * np + i0 + a] = areg[m][a][q];
     }
     __syncthreads();
-    // (b) warp 0: sweep of the kP x kP block A_KK (Ablk = -A_KK^{-1})
-    if (threadIdx.x < 32) {
-      const int lane = threadIdx.x;
-      for (int e = lane; e < kP * kP; e += 32) {
-        const int p = e / kP, q = e % kP;
-        Ablk[e] = VT[q * np + k0 + p];
+    // (b) row p of the pivot block, A_KK[p][q] = A[k0 + q][k0 + p], swept in
+    // registers to row p of -A_KK^{-1}
+    T row[kP];
+#pragma unroll
+    for (int q = 0; q < kP; ++q) row[q] = VT[q * np + k0 + p];
+#pragma unroll
+    for (int kk = 0; kk < kP; ++kk) {
+      T piv = __shfl_sync(0xffffffffu, row[kk], kk);
+      if (!(piv > T(0))) {
+        if (lane == 0 && warp == 0) *bad = 1;
+        piv = T(1);
       }
-      __syncwarp();
-      for (int kk = 0; kk < kP; ++kk) {
-        T piv = Ablk[kk * kP + kk];
-        if (!(piv > T(0))) {
-          if (lane == 0) *bad = 1;
-          piv = T(1);
-        }
-        const T inv = T(1) / piv;
-        T nv[(kP * kP + 31) / 32];
+      const T inv = T(1) / piv;
+      const T colk = row[kk];
 #pragma unroll
-        for (int r = 0; r < (kP * kP + 31) / 32; ++r) {
-          const int e = lane + 32 * r;
-          const int p = e / kP, q = e % kP;
-          const T own = Ablk[e], rowk = Ablk[kk * kP + q], colk = Ablk[p * kP + kk];
-          T v;
-          if (p == kk && q == kk) v = -inv;
-          else if (p == kk) v = rowk * inv;
-          else if (q == kk) v = colk * inv;
-          else v = fma(-colk, rowk * inv, own);
-          nv[r] = v;
-        }
-        __syncwarp();
-#pragma unroll
-        for (int r = 0; r < (kP * kP + 31) / 32; ++r) Ablk[lane + 32 * r] = nv[r];
-        __syncwarp();
+      for (int q = 0; q < kP; ++q) {
+        const T rowk = __shfl_sync(0xffffffffu, row[q], kk);
+        T v;
+        if (p == kk) v = q == kk ? -inv : rowk * inv;
+        else v = q == kk ? colk * inv : fma(-colk, rowk * inv, row[q]);
+        row[q] = v;
       }
     }
-    __syncthreads();
-    // (c) W[p][j] = sum_q A_KK^{-1}[p][q] VT[q][j]
-    for (int j = threadIdx.x; j < np; j += NT) {
-      T col[kP];
+    if (warp == 0 && half == 0)
 #pragma unroll
-      for (int q = 0; q < kP; ++q) col[q] = VT[q * np + j];
+      for (int q = 0; q < kP; ++q) Ablk[p * kP + q] = row[q];
+    // W[p][j] = sum_q A_KK^{-1}[p][q] A[k0 + q][j] for this warp's columns j
+    const int cpw = np / nwarp;
+    for (int j = warp * cpw + half; j < (warp + 1) * cpw; j += 2) {
+      T w = T(0);
 #pragma unroll
-      for (int p = 0; p < kP; ++p) {
-        T w = T(0);
-#pragma unroll
-        for (int q = 0; q < kP; ++q) w = fma(-Ablk[p * kP + q], col[q], w);
-        W[p * np + j] = w;
-      }
+      for (int q = 0; q < kP; ++q) w = fma(-row[q], VT[q * np + j], w);
+      W[p * np + j] = w;
     }
     __syncthreads();
-    // (d) update the register tiles
+    // (c) update the register tiles
 #pragma unroll
     for (int m = 0; m < MT; ++m) {
       const int t = threadIdx.x + m * NT;
@@ -339,10 +333,10 @@ __device__ __forceinline__ void blocked_sweep(T (&areg)[MT][4][4], int np, int n
       const bool rk = i0 >= k0 && i0 < k0 + kP, ck = j0 >= k0 && j0 < k0 + kP;
       if (!rk && !ck) {
 #pragma unroll
-        for (int p = 0; p < kP; ++p) {
+        for (int pp = 0; pp < kP; ++pp) {
           T v4[4], w4[4];
-          load4(VT + p * np + i0, v4);
-          load4(W + p * np + j0, w4);
+          load4(VT + pp * np + i0, v4);
+          load4(W + pp * np + j0, w4);
 #pragma unroll
           for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -399,14 +393,17 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
   T* Gg = reinterpret_cast<T*>(a.G) + off.g;   // [ny][np][np]
   T* Zg = reinterpret_cast<T*>(a.Z) + off.z;   // [ny][np][Cp], the shared-memory image of a row block
 
-  // smem: Gs[GB][np*np] | Us[np*Cp] | Zs[np*Cp] | VT[kP*np] | W[kP*np] | Ablk[kP*kP] | sc | dlo | dup | txh
+  // smem: Gs[GB][np*np] | U region | Zs[np*Cp] | sc | dlo | dup | txh, the U region
+  // holding Us[np*Cp] in the solves and VT[kP*np] | W[kP*np] | Ablk[kP*kP]
+  // during the block inversions (never both at once)
+  const int ureg = max(np * Cp, 2 * kP * np + kP * kP);
   T* Gs0 = reinterpret_cast<T*>(smem_raw);
   T* Us = Gs0 + GB * np * np;
-  T* Zs = Us + np * Cp;
-  T* VT = Zs + np * Cp;
+  T* VT = Us;
   T* W = VT + kP * np;
   T* Ablk = W + kP * np;
-  T* sc = Ablk + kP * kP;
+  T* Zs = Us + ureg;
+  T* sc = Zs + np * Cp;
   T* dlo = sc + np;
   T* dup = dlo + np;
   T* txh = dup + np;
@@ -785,7 +782,7 @@ template <typename T>
 size_t basis_smem(int max_nx, int max_cols) {
   const size_t cp = (max_cols + 3) & ~3;
   const size_t np = (max_nx + kP - 1) & ~(kP - 1);
-  return sizeof(T) * (g_buffers<T>() * np * np + 2 * np * cp + 2 * kP * np + kP * kP + 4 * np);
+  return sizeof(T) * (g_buffers<T>() * np * np + std::max(np * cp, 2 * kP * np + kP * kP) + np * cp + 4 * np);
 }
 
 template <typename T, int MT, int NT, int MINB>
@@ -805,8 +802,8 @@ template <typename T>
 cudaError_t launch_basis(const BasisArgs& a, int max_nx, int max_cols, int refine, cudaStream_t st) {
   const size_t smem = basis_smem<T>(max_nx, max_cols);
   if (max_nx <= 64) return launch_one<T, 1, 256, sizeof(T) == 4 ? 3 : 2>(a, smem, refine, st);
-  if (sizeof(T) == 4) return launch_one<T, 4, 256, 1>(a, smem, refine, st);
-  return launch_one<T, 2, 512, 1>(a, smem, refine, st);
+  if constexpr (sizeof(T) == 4) return launch_one<T, 4, 256, 1>(a, smem, refine, st);
+  else return launch_one<T, 2, 512, 1>(a, smem, refine, st);
 }
 
 }  // namespace

@@ -72,7 +72,7 @@ extern "C" sfb_status sfb_build_basis_item_noalloc(sfb_ctx* c, int32_t sub, int3
   }
   const HostSub& H = c->subs[sub];
   const int nx = H.nx, ny = H.ny, nc = nx * ny, R = (int)H.dofs.size(), C = R + 1, nt = H.n_term;
-  const int64_t np = (nx + 7) & ~7, cp = (C + 3) & ~3;
+  const int64_t np = (nx + kPanel - 1) / kPanel * kPanel, cp = (C + 3) & ~3;
   const size_t gsz = prec == SFB_FP64 ? sizeof(double) : sizeof(float);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

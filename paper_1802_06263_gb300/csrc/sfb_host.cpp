@@ -155,11 +155,11 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
     const int nl = c->n_local.empty() ? 0 : c->n_local[s];
     for (int k = 0; k < nl; ++k) {
       ItemOff o;
-      const int64_t npad_ = (S.nx + 7) & ~7, cpad_ = (C + 3) & ~3;
+      const int64_t npad_ = (S.nx + kPanel - 1) / kPanel * kPanel, cpad_ = (C + 3) & ~3;
       o.x = nX; nX += (int64_t)nc * C;
       o.z = nZ; nZ += (int64_t)S.ny * npad_ * cpad_;   // row blocks in the shared-memory layout
       o.t = nT; nT += (int64_t)S.ny * (S.nx + 1) + (int64_t)(S.ny + 1) * S.nx;
-      const int64_t npad = (S.nx + 7) & ~7;  // identity-padded block size of the factor
+      const int64_t npad = (S.nx + kPanel - 1) / kPanel * kPanel;  // identity-padded block size of the factor
       o.g = nG; nG += (int64_t)S.ny * npad * npad;
       o.phi = nPhi; nPhi += ((int64_t)R * R + R + 3) & ~int64_t(3);   // 16-byte aligned in FP32 and FP64
       o.diag = nD; o.sc = nD; nD += nc;

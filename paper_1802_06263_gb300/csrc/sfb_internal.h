@@ -81,6 +81,10 @@ __device__ __forceinline__ float to_f32(double v) { return f64_to_f32_bits(v); }
 // sweeps, then 12 sub-phases of the row steps (see sfb_basis_stats).
 constexpr int kCycSlots = 16;
 
+// Pivots per panel of the blocked block inversion; the diagonal blocks are
+// identity-padded to a multiple of it.
+constexpr int kPanel = 16;
+
 // Point chunks of the Stokes coefficient moments (partials summed in order).
 constexpr int kStokesChunks = 32;
 
