@@ -219,7 +219,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-constexpr int kP = kPanel;  // pivots per panel of the blocked sweep
+// Pivots per panel of the blocked sweep: 16 in the FP32 factor (register-resident
+// pivot-block inverse in every warp), 8 in the FP64 one (one inverse by warp 0).
+template <typename T>
+__host__ __device__ constexpr int panel_of() { return sizeof(T) == 4 ? 16 : 8; }
 
 // L2 prefetch of grid row b of all C columns of X (column-major, nx doubles
 // per row segment): one 128-byte line per thread.
@@ -268,7 +271,7 @@ __device__ __forceinline__ void form_block(T (&areg)[MT][4][4], int b, int nx, i
 // pivot block in registers (lane p % kP holds row p; the pivot row arrives
 // by shuffles) and forms its share of W = A_KK^{-1} A_K* from VT; (c) the
 // register tiles take the rank-kP update. Three barriers per panel.
-template <typename T, int MT, int NT>
+template <typename T, int MT, int NT, int kP>
 __device__ __forceinline__ void blocked_sweep(T (&areg)[MT][4][4], int np, int ntr, T* VT, T* W, T* Ablk,
                                               int* bad) {
   static_assert(kP == 16, "the pivot-block layout puts one row per half-warp lane");
@@ -363,6 +366,114 @@ __device__ __forceinline__ void blocked_sweep(T (&areg)[MT][4][4], int np, int n
   }
 }
 
+// The same blocked sweep with the kP x kP pivot-block inverse done once, by
+// warp 0 in shared memory, and W formed by the threads j < np: the FP64 form,
+// where a redundant inverse in every warp would multiply the scarce FP64 work.
+template <typename T, int MT, int NT, int kP>
+__device__ __forceinline__ void blocked_sweep_w0(T (&areg)[MT][4][4], int np, int ntr, T* VT, T* W, T* Ablk,
+                                                 int* bad) {
+  for (int k0 = 0; k0 < np; k0 += kP) {
+    // (a) panel columns: VT[p][i] = A[i][k0 + p]
+#pragma unroll
+    for (int m = 0; m < MT; ++m) {
+      const int t = threadIdx.x + m * NT;
+      if (t >= ntr * ntr) break;
+      const int i0 = (t / ntr) * 4, j0 = (t % ntr) * 4;
+      if (j0 >= k0 && j0 < k0 + kP)
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) VT[(j0 + q - k0) * np + i0 + a] = areg[m][a][q];
+    }
+    __syncthreads();
+    // (b) warp 0: sweep of the kP x kP block A_KK (Ablk = -A_KK^{-1})
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      for (int e = lane; e < kP * kP; e += 32) {
+        const int p = e / kP, q = e % kP;
+        Ablk[e] = VT[q * np + k0 + p];
+      }
+      __syncwarp();
+      for (int kk = 0; kk < kP; ++kk) {
+        T piv = Ablk[kk * kP + kk];
+        if (!(piv > T(0))) {
+          if (lane == 0) *bad = 1;
+          piv = T(1);
+        }
+        const T inv = T(1) / piv;
+        T nv[(kP * kP + 31) / 32];
+#pragma unroll
+        for (int r = 0; r < (kP * kP + 31) / 32; ++r) {
+          const int e = lane + 32 * r;
+          const int p = e / kP, q = e % kP;
+          const T own = Ablk[e], rowk = Ablk[kk * kP + q], colk = Ablk[p * kP + kk];
+          T v;
+          if (p == kk && q == kk) v = -inv;
+          else if (p == kk) v = rowk * inv;
+          else if (q == kk) v = colk * inv;
+          else v = fma(-colk, rowk * inv, own);
+          nv[r] = v;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < (kP * kP + 31) / 32; ++r) Ablk[lane + 32 * r] = nv[r];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // (c) W[p][j] = sum_q A_KK^{-1}[p][q] VT[q][j]
+    for (int j = threadIdx.x; j < np; j += NT) {
+      T col[kP];
+#pragma unroll
+      for (int q = 0; q < kP; ++q) col[q] = VT[q * np + j];
+#pragma unroll
+      for (int p = 0; p < kP; ++p) {
+        T w = T(0);
+#pragma unroll
+        for (int q = 0; q < kP; ++q) w = fma(-Ablk[p * kP + q], col[q], w);
+        W[p * np + j] = w;
+      }
+    }
+    __syncthreads();
+    // (d) update the register tiles
+#pragma unroll
+    for (int m = 0; m < MT; ++m) {
+      const int t = threadIdx.x + m * NT;
+      if (t >= ntr * ntr) break;
+      const int i0 = (t / ntr) * 4, j0 = (t % ntr) * 4;
+      const bool rk = i0 >= k0 && i0 < k0 + kP, ck = j0 >= k0 && j0 < k0 + kP;
+      if (!rk && !ck) {
+#pragma unroll
+        for (int p = 0; p < kP; ++p) {
+          T v4[4], w4[4];
+          load4(VT + p * np + i0, v4);
+          load4(W + p * np + j0, w4);
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) areg[m][a][q] = fma(-v4[a], w4[q], areg[m][a][q]);
+        }
+      } else if (rk && !ck) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) areg[m][a][q] = W[(i0 + a - k0) * np + j0 + q];
+      } else if (!rk && ck) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) areg[m][a][q] = W[(j0 + q - k0) * np + i0 + a];
+      } else {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) areg[m][a][q] = Ablk[(i0 + a - k0) * kP + (j0 + q - k0)];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <typename T, int MT, int NT, int MINB, int GB>
 __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -379,7 +490,8 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
   Geo g;
   g.nx = S.nx; g.ny = S.ny; g.R = S.R; g.C = S.R + 1; g.Cp = (g.C + 3) & ~3; g.nc = S.nx * S.ny;
   const int nx = g.nx, ny = g.ny, nc = g.nc, C = g.C, Cp = g.Cp;
-  const int np = (nx + kP - 1) & ~(kP - 1);  // identity-padded block size
+  constexpr int kP = panel_of<T>();
+  const int np = (nx + kPanel - 1) & ~(kPanel - 1);  // identity-padded block size
   const int ntr = np >> 2;
   const uint32_t gbytes = (uint32_t)(np * np * sizeof(T));
   const uint32_t zbytes = (uint32_t)(np * Cp * sizeof(T));
@@ -505,7 +617,8 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
     __syncthreads();
     SFB_MARK(0);
     form_block<T, MT, NT>(areg, b, nx, ntr, txh, dlo);
-    blocked_sweep<T, MT, NT>(areg, np, ntr, VT, W, Ablk, &bad_spd);
+    if constexpr (sizeof(T) == 4) blocked_sweep<T, MT, NT, panel_of<T>()>(areg, np, ntr, VT, W, Ablk, &bad_spd);
+    else blocked_sweep_w0<T, MT, NT, panel_of<T>()>(areg, np, ntr, VT, W, Ablk, &bad_spd);
     SFB_MARK(1);
     T* Gs = Gs0 + (b % GB) * np * np;
     if (threadIdx.x == 0) bulk_wait_read();   // the store that last read Gs / Zs is done
@@ -781,7 +894,8 @@ constexpr int g_buffers() { return sizeof(T) == 4 ? 2 : 1; }
 template <typename T>
 size_t basis_smem(int max_nx, int max_cols) {
   const size_t cp = (max_cols + 3) & ~3;
-  const size_t np = (max_nx + kP - 1) & ~(kP - 1);
+  constexpr size_t kP = panel_of<T>();
+  const size_t np = (max_nx + kPanel - 1) & ~size_t(kPanel - 1);
   return sizeof(T) * (g_buffers<T>() * np * np + std::max(np * cp, 2 * kP * np + kP * kP) + np * cp + 4 * np);
 }
 
