@@ -253,9 +253,6 @@ sfb_status sfb_build_basis_item_noalloc(sfb_ctx* ctx, int32_t sub, int32_t k, in
  *                    error of X is below this (default 1e-10);
  *   "refine_max"     mixed form: at most this many FP64 residual passes (8);
  *   "cg_check_every" CG iterations between convergence checks on the host (8);
- *   "basis_wide_kernel"  mixed form: 1 builds every item with the 256-thread
- *                    kernel; 0 uses the 128-thread kernel (five CTAs per SM)
- *                    for items with nx <= 64 and R + 1 <= 68 (0);
  *   "cg_jacobi"      1: CG preconditioned by diag(S^l) (Jacobi), 0: plain CG
  *                    as the paper states it; the same solution and the same
  *                    stopping test on the unpreconditioned residual (1);

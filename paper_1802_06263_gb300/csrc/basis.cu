@@ -847,413 +847,6 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
 #undef SFB_MARK
 }
 
-// ---- lean FP32 variant for narrow grids ----------------------------------------------------
-// The mixed form for items with np <= 64 and R + 1 <= 68, laid out so that five
-// CTAs share an SM and a typical build (a few hundred items) is resident in
-// one wave: 128 threads (two 4 x 4 sweep tiles each), one G buffer (G_{b+1}
-// is fetched while row b finishes), and one row block Zb in shared memory that
-// takes each right-hand side in place. A product keeps its output tiles in
-// registers until every thread has read the row block, then writes them to
-// Zb and, as vector stores, to the z rows in global memory.
-constexpr int kLeanNT = 128;
-constexpr int kLeanMT = 2;      // sweep tiles per thread: (64 / 4)^2 = 256 = 2 x 128
-constexpr int kLeanTiles = 3;   // product tiles per thread: (64 / 4) x (68 / 4) = 272 <= 3 x 128
-constexpr int kLeanMaxNp = 64, kLeanMaxCp = 68;
-
-// acc[m] = G U on the output tile t = threadIdx.x + m * kLeanNT (np x Cp in
-// 4 x 4 tiles; G symmetric with pitch np, U pitch Cp)
-__device__ __forceinline__ void lean_product(const float* __restrict__ G, const float* __restrict__ U, int np, int Cp,
-                                             float (&acc)[kLeanTiles][4][4]) {
-  const int nct = Cp >> 2, ntot = (np >> 2) * nct;
-#pragma unroll
-  for (int m = 0; m < kLeanTiles; ++m) {
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[m][a][q] = 0.f;
-    const int t = threadIdx.x + m * kLeanNT;
-    if (t < ntot) {
-      const int i0 = (t / nct) * 4, c0 = (t % nct) * 4;
-#pragma unroll 2
-      for (int k = 0; k < np; ++k) {
-        float gv[4], uv[4];
-        load4(G + k * np + i0, gv);
-        load4(U + k * Cp + c0, uv);
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int q = 0; q < 4; ++q) acc[m][a][q] = fmaf(gv[a], uv[q], acc[m][a][q]);
-      }
-    }
-  }
-}
-
-// Zb (and zrow, when given) = acc (+ base, when given), tile by tile
-__device__ __forceinline__ void lean_store(const float (&acc)[kLeanTiles][4][4], float* Zb, float* zrow,
-                                           const float* base, int np, int Cp) {
-  const int nct = Cp >> 2, ntot = (np >> 2) * nct;
-#pragma unroll
-  for (int m = 0; m < kLeanTiles; ++m) {
-    const int t = threadIdx.x + m * kLeanNT;
-    if (t >= ntot) break;
-    const int i0 = (t / nct) * 4, c0 = (t % nct) * 4;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      float4 v = make_float4(acc[m][a][0], acc[m][a][1], acc[m][a][2], acc[m][a][3]);
-      const int o = (i0 + a) * Cp + c0;
-      if (base) {
-        const float4 z = *reinterpret_cast<const float4*>(base + o);
-        v.x += z.x; v.y += z.y; v.z += z.z; v.w += z.w;
-      }
-      *reinterpret_cast<float4*>(Zb + o) = v;
-      if (zrow) *reinterpret_cast<float4*>(zrow + o) = v;
-    }
-  }
-}
-
-// S_b = Ahat_bb - D_{b-1} G_{b-1} D_{b-1} into the sweep tiles, G_{b-1} read
-// from shared memory; rows and columns nx..np-1 are an identity padding
-__device__ __forceinline__ void lean_form_block(float (&areg)[kLeanMT][4][4], int b, int nx, int np, int ntr,
-                                                const float* txh, const float* dlo, const float* Gs) {
-#pragma unroll
-  for (int m = 0; m < kLeanMT; ++m) {
-    const int t = threadIdx.x + m * kLeanNT;
-    if (t >= ntr * ntr) break;
-    const int i0 = (t / ntr) * 4, j0 = (t % ntr) * 4;
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = i0 + a, j = j0 + q;
-        float v;
-        if (i >= nx || j >= nx) {
-          v = (i == j) ? 1.f : 0.f;
-        } else {
-          v = (i == j) ? 1.f : (j == i + 1 ? txh[j] : (j == i - 1 ? txh[i] : 0.f));
-          if (b > 0) v = fmaf(-dlo[i] * Gs[i * np + j], dlo[j], v);
-        }
-        areg[m][a][q] = v;
-      }
-  }
-}
-
-// L1 prefetch of one z row block [np][Cp] in global memory
-__device__ __forceinline__ void prefetch_z_row(const float* z, int bytes) {
-  for (int o = threadIdx.x * 128; o < bytes; o += blockDim.x * 128)
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char*>(z) + o));
-}
-
-__global__ void __launch_bounds__(kLeanNT, 5) basis_kernel_lean(BasisArgs a, int refine) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[32];
-  __shared__ int bad_spd;
-  __shared__ __align__(8) uint64_t gbar;
-  const int item = blockIdx.x;
-  if (item >= a.n_items) return;
-  const int s = a.item_sub[item], kk = a.item_k[item];
-  const SubDev S = a.subs[s];
-  const int id = (int)S.item0 + kk;
-  const ItemOff off = a.off[id];
-  Geo g;
-  g.nx = S.nx; g.ny = S.ny; g.R = S.R; g.C = S.R + 1; g.Cp = (g.C + 3) & ~3; g.nc = S.nx * S.ny;
-  const int nx = g.nx, ny = g.ny, nc = g.nc, C = g.C, Cp = g.Cp;
-  constexpr int kP = panel_of<float>();
-  const int np = (nx + kPanel - 1) & ~(kPanel - 1);
-  const int ntr = np >> 2;
-  const uint32_t gbytes = (uint32_t)(np * np * sizeof(float));
-  double* Tx = a.T + off.t;
-  double* Ty = Tx + (int64_t)ny * (nx + 1);
-  g.Tx = Tx; g.Ty = Ty;
-  double* X = a.X + off.x;
-  double* Dg = a.D + off.diag;
-  float* Sg = reinterpret_cast<float*>(a.S) + off.sc;
-  float* DLg = reinterpret_cast<float*>(a.DL) + off.sc;
-  float* Gg = reinterpret_cast<float*>(a.G) + off.g;   // [ny][np][np]
-  float* Zg = reinterpret_cast<float*>(a.Z) + off.z;   // [ny][np][Cp]
-
-  // smem: Gs[np*np] | Zb[np*Cp] | VT[kP*np] | W[kP*np] | Ablk[kP*kP] | sc | dlo | dup | txh
-  float* Gs = reinterpret_cast<float*>(smem_raw);
-  float* Zb = Gs + np * np;
-  float* VT = Zb + np * Cp;
-  float* W = VT + kP * np;
-  float* Ablk = W + kP * np;
-  float* sc = Ablk + kP * kP;
-  float* dlo = sc + np;
-  float* dup = dlo + np;
-  float* txh = dup + np;
-  uint32_t gph = 0u;
-
-  if (threadIdx.x == 0) {
-    bad_spd = 0;
-    mbar_init(&gbar, 1);
-    fence_barrier_init();
-  }
-  int st = 0;
-  long long t_mark = clock64(), t_fwd = 0, t_bwd = 0;
-  long long* cyc = a.cycles + kCycSlots * (int64_t)id;
-  for (int e = threadIdx.x; e < np * Cp; e += blockDim.x) Zb[e] = 0.f;
-  for (int e = threadIdx.x; e < np * np; e += blockDim.x) Gs[e] = 0.f;
-  for (int e = threadIdx.x; e < np; e += blockDim.x) { sc[e] = 0.f; dlo[e] = 0.f; dup[e] = 0.f; txh[e] = 0.f; }
-  __syncthreads();
-
-  // ---- 1. permeability, transmissibilities, diagonal and scaling ------------
-  {
-    const int nt = S.n_term;
-    const double* slam = a.kl + S.kl_off;
-    const double* fx = slam + nt;
-    const double* fy = fx + (int64_t)nt * nx;
-    const double* yl = a.yloc + S.yloc_off + (int64_t)kk * nt;
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-      const int ix = c % nx, iy = c / nx;
-      double Y = S.mean_y;
-      for (int j = 0; j < nt; ++j) Y += slam[j] * yl[j] * fx[j * nx + ix] * fy[j * ny + iy];
-      const double K = exp(Y);
-      if (!(K > 0.0) || !isfinite(K)) st |= ST_NONFINITE;
-      X[c] = K;  // scratch: X is written only after the factorization
-    }
-    __syncthreads();
-    const double nu = S.nu;
-    for (int f = threadIdx.x; f < ny * (nx + 1); f += blockDim.x) {
-      const int iy = f / (nx + 1), ix = f - iy * (nx + 1);
-      double t;
-      if (ix == 0) t = S.side_type[3] != SIDE_NOFLOW ? 2.0 * X[iy * nx] * S.hy / (nu * S.hx) : 0.0;
-      else if (ix == nx)
-        t = S.side_type[1] != SIDE_NOFLOW ? 2.0 * X[iy * nx + nx - 1] * S.hy / (nu * S.hx) : 0.0;
-      else {
-        const double ka = X[iy * nx + ix - 1], kb = X[iy * nx + ix];
-        t = (S.hy / S.hx) * 2.0 * ka * kb / (nu * (ka + kb));
-      }
-      Tx[f] = t;
-    }
-    for (int f = threadIdx.x; f < (ny + 1) * nx; f += blockDim.x) {
-      const int iy = f / nx, ix = f - iy * nx;
-      double t;
-      if (iy == 0) t = S.side_type[0] != SIDE_NOFLOW ? 2.0 * X[ix] * S.hx / (nu * S.hy) : 0.0;
-      else if (iy == ny)
-        t = S.side_type[2] != SIDE_NOFLOW ? 2.0 * X[(ny - 1) * nx + ix] * S.hx / (nu * S.hy) : 0.0;
-      else {
-        const double ka = X[(iy - 1) * nx + ix], kb = X[iy * nx + ix];
-        t = (S.hx / S.hy) * 2.0 * ka * kb / (nu * (ka + kb));
-      }
-      Ty[f] = t;
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-      const int b = c / nx, i = c - b * nx;
-      const double d = Tx[b * (nx + 1) + i] + Tx[b * (nx + 1) + i + 1] + Ty[b * nx + i] + Ty[(b + 1) * nx + i];
-      Dg[c] = d;
-      Sg[c] = (float)(1.0 / sqrt(d));
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-      const int b = c / nx, i = c - b * nx;
-      DLg[c] = b > 0 ? (float)(Ty[b * nx + i] / sqrt(Dg[c] * Dg[c - nx])) : 0.f;
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) { const long long t = clock64(); cyc[0] = t - t_mark; t_mark = t; }
-
-  // ---- 2. factorization, fused with the first forward solve ------------------
-  float areg[kLeanMT][4][4];
-  float acc[kLeanTiles][4][4];
-  for (int b = 0; b < ny; ++b) {
-    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-      const double si = (double)Sg[b * nx + i];
-      sc[i] = (float)si;
-      txh[i] = i > 0 ? (float)(-Tx[b * (nx + 1) + i] * si * (double)Sg[b * nx + i - 1]) : 0.f;
-      dlo[i] = DLg[b * nx + i];
-    }
-    __syncthreads();
-    lean_form_block(areg, b, nx, np, ntr, txh, dlo, Gs);
-    blocked_sweep<float, kLeanMT, kLeanNT, kP>(areg, np, ntr, VT, W, Ablk, &bad_spd);
-    if (threadIdx.x == 0) bulk_wait_read();   // the store of G_{b-1} has read Gs
-    __syncthreads();
-#pragma unroll
-    for (int m = 0; m < kLeanMT; ++m) {
-      const int t = threadIdx.x + m * kLeanNT;
-      if (t >= ntr * ntr) break;
-      const int i0 = (t / ntr) * 4, j0 = (t % ntr) * 4;
-#pragma unroll
-      for (int a2 = 0; a2 < 4; ++a2)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) Gs[(i0 + a2) * np + j0 + q] = -areg[m][a2][q];
-    }
-    // first forward solve row, in place: Zb = s_b B_b + dlo_b z_{b-1}
-    for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
-      const int i = e % nx, c = e / nx;
-      float u = sc[i] * f64_to_f32_bits(rhs_entry(S, g, a.proj, b, i, c));
-      if (b > 0) u = fmaf(dlo[i], Zb[i * Cp + c], u);
-      Zb[i * Cp + c] = u;
-    }
-    fence_async_shared();
-    __syncthreads();
-    if (threadIdx.x == 0) bulk_store(Gg + (int64_t)b * np * np, Gs, gbytes);
-    lean_product(Gs, Zb, np, Cp, acc);
-    __syncthreads();
-    lean_store(acc, Zb, Zg + (int64_t)b * np * Cp, nullptr, np, Cp);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    bulk_wait_all();
-    fence_async_global();
-  }
-  __threadfence_block();
-  __syncthreads();
-  if (threadIdx.x == 0) { const long long t = clock64(); cyc[1] = t - t_mark; t_mark = t; }
-
-  // ---- 3./4. backward sweep, then refine with FP64 residuals --------------------------
-  double xref2 = 0.0, prev_corr = 0.0, est = 1.0, bnorm2 = 0.0;
-  int n_done = 0;
-  bool timeout = false;
-  for (int it = 0; it <= refine && !timeout; ++it) {
-    float rr = 0.f;
-    if (it > 0) {
-      // forward sweep: Zb = s_b r_b + dlo_b z_{b-1} in place, r_b = B_b - (A x)_b in FP64
-      if (threadIdx.x == 0) { fence_async_shared(); bulk_load(Gs, Gg, gbytes, &gbar); }
-      float nsc = threadIdx.x < nx ? Sg[threadIdx.x] : 0.f, ndl = threadIdx.x < nx ? DLg[threadIdx.x] : 0.f;
-      prefetch_x_row(X, nc, nx, 0, C);
-      if (ny > 1) prefetch_x_row(X, nc, nx, 1, C);
-      for (int b = 0; b < ny; ++b) {
-        if (threadIdx.x < nx) {
-          sc[threadIdx.x] = nsc;
-          dlo[threadIdx.x] = ndl;
-          if (b + 1 < ny) { nsc = Sg[(b + 1) * nx + threadIdx.x]; ndl = DLg[(b + 1) * nx + threadIdx.x]; }
-        }
-        if (b + 2 < ny) prefetch_x_row(X, nc, nx, b + 2, C);
-        __syncthreads();
-#pragma unroll 2
-        for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
-          const int i = e % nx, c = e / nx;
-          const int64_t cell = (int64_t)b * nx + i;
-          const double* xc = X + (int64_t)c * nc;
-          double r = fma(-Dg[cell], xc[cell], rhs_entry(S, g, a.proj, b, i, c));
-          if (i > 0) r = fma(Tx[b * (nx + 1) + i], xc[cell - 1], r);
-          if (i < nx - 1) r = fma(Tx[b * (nx + 1) + i + 1], xc[cell + 1], r);
-          if (b > 0) r = fma(Ty[b * nx + i], xc[cell - nx], r);
-          if (b < ny - 1) r = fma(Ty[(b + 1) * nx + i], xc[cell + nx], r);
-          const float rt = f64_to_f32_bits(r);
-          rr = fmaf(rt, rt, rr);
-          float u = sc[i] * rt;
-          if (b > 0) u = fmaf(dlo[i], Zb[i * Cp + c], u);
-          Zb[i * Cp + c] = u;
-        }
-        const bool ok = mbar_wait(&gbar, gph);
-        gph ^= 1u;
-        if (__syncthreads_or(!ok)) { timeout = true; break; }
-        lean_product(Gs, Zb, np, Cp, acc);
-        __syncthreads();
-        if (threadIdx.x == 0 && b + 1 < ny) {
-          fence_async_shared();
-          bulk_load(Gs, Gg + (int64_t)(b + 1) * np * np, gbytes, &gbar);
-        }
-        lean_store(acc, Zb, Zg + (int64_t)b * np * Cp, nullptr, np, Cp);
-        __syncthreads();
-      }
-      if (timeout) break;
-      const double rnorm2 = block_sum((double)rr, red);
-      if (threadIdx.x == 0) a.resid[id] = sqrt(rnorm2 / fmax(bnorm2, 1e-300));
-      if (threadIdx.x == 0) { const long long t = clock64(); t_fwd += t - t_mark; t_mark = t; }
-    } else {
-      float bb = 0.f;
-      for (int e = threadIdx.x; e < nc * C; e += blockDim.x) {
-        const int c = e / nc, cell = e - c * nc;
-        const float v = f64_to_f32_bits(rhs_entry(S, g, a.proj, cell / nx, cell % nx, c));
-        bb = fmaf(v, v, bb);
-      }
-      bnorm2 = block_sum((double)bb, red);
-    }
-    // backward sweep: d_b = z_b + G_b (dup_b .* d_{b+1}); x_b += s_b d_b. Zb holds
-    // z_{ny-1} = d_{ny-1} on entry; G_b is fetched one row ahead.
-    float dn2f = 0.f;
-    __threadfence_block();
-    if (threadIdx.x == 0 && ny >= 2) {
-      fence_async_shared();
-      bulk_load(Gs, Gg + (int64_t)(ny - 2) * np * np, gbytes, &gbar);
-    }
-    float bsc = threadIdx.x < nx ? Sg[(ny - 1) * nx + threadIdx.x] : 0.f, bdu = 0.f;
-    for (int b = ny - 1; b >= 0; --b) {
-      if (threadIdx.x < nx) {
-        sc[threadIdx.x] = bsc;
-        dup[threadIdx.x] = bdu;
-        if (b > 0) { bsc = Sg[(b - 1) * nx + threadIdx.x]; bdu = DLg[b * nx + threadIdx.x]; }
-      }
-      if (it > 0) prefetch_x_row(X, nc, nx, b, C);
-      __syncthreads();
-      if (b < ny - 1) {
-        prefetch_z_row(Zg + (int64_t)b * np * Cp, np * Cp * (int)sizeof(float));
-        for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
-          const int i = e % nx, c = e / nx;
-          Zb[i * Cp + c] *= dup[i];
-        }
-        const bool ok = mbar_wait(&gbar, gph);
-        gph ^= 1u;
-        if (__syncthreads_or(!ok)) { timeout = true; break; }
-        lean_product(Gs, Zb, np, Cp, acc);
-        __syncthreads();
-        if (threadIdx.x == 0 && b >= 1) {
-          fence_async_shared();
-          bulk_load(Gs, Gg + (int64_t)(b - 1) * np * np, gbytes, &gbar);
-        }
-        lean_store(acc, Zb, nullptr, Zg + (int64_t)b * np * Cp, np, Cp);
-        __syncthreads();
-      }
-#pragma unroll 4
-      for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
-        const int i = e % nx, c = e / nx;
-        const int64_t idx = (int64_t)c * nc + (int64_t)b * nx + i;
-        const float dt = sc[i] * Zb[i * Cp + c];
-        dn2f = fmaf(dt, dt, dn2f);
-        if (it == 0) X[idx] = f32_to_f64_bits(dt);
-        else X[idx] += f32_to_f64_bits(dt);
-      }
-      __syncthreads();
-    }
-    if (timeout) break;
-    const double dn2 = block_sum((double)dn2f, red);
-    if (threadIdx.x == 0) { const long long t = clock64(); t_bwd += t - t_mark; t_mark = t; }
-    if (it == 0) {
-      xref2 = dn2;
-      prev_corr = 1.0;
-      est = 1.0;
-    } else {
-      const double corr = sqrt(dn2 / fmax(xref2, 1e-300));
-      const double rho = corr / fmax(prev_corr, 1e-300);
-      est = rho < 1.0 ? rho / (1.0 - rho) * corr : 1.0;
-      if (threadIdx.x == 0 && it == 1) a.corr1[id] = corr;
-      prev_corr = corr;
-      n_done = it;
-      if (est <= a.refine_tol) break;
-      if (rho > 0.5) {
-        st |= ST_NOT_CONVERGED;
-        break;
-      }
-      if (it == refine) st |= ST_NOT_CONVERGED;
-    }
-  }
-  if (timeout) {
-    if (threadIdx.x == 0) {
-      mbar_wait(&gbar, gph);
-      bulk_wait_all();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) atomicOr(&a.status[id], ST_TIMEOUT);
-    return;
-  }
-  if (threadIdx.x == 0) {
-    bulk_wait_all();
-    cyc[2] = t_fwd;
-    cyc[3] = t_bwd;
-    for (int q = 4; q < kCycSlots; ++q) cyc[q] = 0;
-    a.nref[id] = n_done;
-    a.errest[id] = refine > 0 ? est : 0.0;
-  }
-  for (int e = threadIdx.x; e < nc * C; e += blockDim.x)
-    if (!isfinite(X[e])) st |= ST_NONFINITE;
-  __syncthreads();
-  if (bad_spd) st |= ST_NOT_SPD;
-  if (st) atomicOr(&a.status[id], st);
-}
-
 // Phi[l][j] = -sum_e P[e][l] T_e (X[c_e][j] - P[e][j]) (j < R) and
 // g[l] = sum_e P[e][l] T_e X[c_e][R], the sum running over the faces e of the
 // side that carries mortar DOF l and lying in the support of xi_l.
@@ -1333,19 +926,7 @@ cudaError_t launch_basis_fp64(const BasisArgs& a, int max_nx, int max_cols, cuda
   return launch_basis<double>(a, max_nx, max_cols, 0, st);
 }
 
-// The lean 128-thread variant whenever the items fit it (np <= 64, R + 1 <= 68)
-// unless `wide_only` asks for the 256-thread kernel.
-cudaError_t launch_basis_mixed(const BasisArgs& a, int max_nx, int max_cols, int refine, cudaStream_t st,
-                               int wide_only) {
-  const int np = (max_nx + kPanel - 1) & ~(kPanel - 1), cp = (max_cols + 3) & ~3;
-  if (!wide_only && np <= kLeanMaxNp && cp <= kLeanMaxCp) {
-    constexpr int kP = panel_of<float>();
-    const size_t smem = sizeof(float) * ((size_t)np * np + (size_t)np * cp + 2 * kP * np + kP * kP + 4 * np);
-    cudaError_t e = cudaFuncSetAttribute(basis_kernel_lean, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    basis_kernel_lean<<<a.n_items, kLeanNT, smem, st>>>(a, refine);
-    return cudaGetLastError();
-  }
+cudaError_t launch_basis_mixed(const BasisArgs& a, int max_nx, int max_cols, int refine, cudaStream_t st) {
   return launch_basis<float>(a, max_nx, max_cols, refine, st);
 }
 

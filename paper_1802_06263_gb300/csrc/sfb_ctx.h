@@ -182,7 +182,6 @@ struct sfb_ctx {
   double opt_refine_tol = 1e-10;
   int opt_refine_max = 8;
   int opt_cg_chunk = 8;
-  int opt_basis_wide = 0;        // 1: the 256-thread FP32 basis kernel even where the lean one fits
   int opt_cg_jacobi = 1;        // diagonal (Jacobi) preconditioning of the interface CG
   double opt_cg_replace = 0.1;  // mixed CG: FP64 residual once the recursive one drops by this factor
   double opt_big_factor = 1.0;   // groups above this many times (R+1) points use coefficient moments

@@ -704,8 +704,7 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
     // narrow grids concurrently on a side stream joined before the epilogue
     const int refine = prec == SFB_MIXED ? a.max_refine : 0;
     auto launch = [&](const BasisArgs& aa, int mnx, int mcols, cudaStream_t s2) {
-      return prec == SFB_FP64 ? launch_basis_fp64(aa, mnx, mcols, s2)
-                              : launch_basis_mixed(aa, mnx, mcols, refine, s2, c->opt_basis_wide);
+      return prec == SFB_FP64 ? launch_basis_fp64(aa, mnx, mcols, s2) : launch_basis_mixed(aa, mnx, mcols, refine, s2);
     };
     BasisArgs aw = a, an = a;
     aw.n_items = (int)c->n_wide;
@@ -912,9 +911,6 @@ sfb_status sfb_set_option(sfb_ctx* c, const char* name, double value) {
   } else if (n == "cg_check_every") {
     if (!(value >= 1 && value <= 1000)) return fail(c, SFB_ERR_ARG, "cg_check_every must lie in [1, 1000]");
     c->opt_cg_chunk = (int)value;
-  } else if (n == "basis_wide_kernel") {
-    if (!(value == 0 || value == 1)) return fail(c, SFB_ERR_ARG, "basis_wide_kernel must be 0 or 1");
-    c->opt_basis_wide = (int)value;
   } else if (n == "cg_jacobi") {
     if (!(value == 0 || value == 1)) return fail(c, SFB_ERR_ARG, "cg_jacobi must be 0 or 1");
     c->opt_cg_jacobi = (int)value;

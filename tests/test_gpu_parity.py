@@ -127,29 +127,3 @@ def test_plain_and_jacobi_cg_reach_the_same_solution(jacobi, krylov):
         s.set_option("cg_jacobi", 1)
         _, it_j, _ = s.solve_host(y, wt, rtol=1e-13, max_it=5000, krylov=krylov)
         assert it_j.max() < it.max()
-
-
-@pytest.mark.parametrize("key", ["ragged", "medium"])
-def test_mixed_basis_kernel_variants_agree(key):
-    """The mixed form built with the 256-thread kernel and with the lean
-    128-thread kernel both meet the mixed-form tolerance against the oracle."""
-    import paper_1802_06263_gb300 as sfb
-    p, y, wt, lams, mom = oracle_case(key)
-    s = sfb.Solver(make_workload(key))
-    s.allocate(sfb.FP64)
-    out = {}
-    for wide in (1, 0):
-        s.set_option("basis_wide_kernel", wide)
-        st = s.build_basis(sfb.MIXED)
-        assert st["n_not_converged"] == 0
-        for i in range(len(p.subs)):
-            loc = p.local_realizations(i, y)[0]
-            for k in (0, len(loc) - 1):
-                phi_o, g_o, X_o, _ = p.darcy_basis(i, loc[k])
-                phi, g, X = s.get_basis(i, k, with_x=True)
-                assert rel(phi, phi_o) < TOL[1], (wide, i, k)
-                assert rel(X, X_o) < TOL[1], (wide, i, k)
-                out[(wide, i, k)] = phi
-    for (wide, i, k), phi in out.items():
-        if wide == 0:
-            assert rel(phi, out[(1, i, k)]) < TOL[1]
