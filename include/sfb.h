@@ -253,9 +253,13 @@ sfb_status sfb_build_basis_item_noalloc(sfb_ctx* ctx, int32_t sub, int32_t k, in
  *                    error of X is below this (default 1e-10);
  *   "refine_max"     mixed form: at most this many FP64 residual passes (8);
  *   "cg_check_every" CG iterations between convergence checks on the host (8);
- *   "cg_jacobi"      1: CG preconditioned by diag(S^l) (Jacobi), 0: plain CG
- *                    as the paper states it; the same solution and the same
- *                    stopping test on the unpreconditioned residual (1);
+ *   "cg_precond"     interface CG preconditioner: 0 none (CG as the paper
+ *                    states it), 1 Jacobi (diag(S^l)), 2 interface blocks
+ *                    (the diagonal block of S^l on each mortar interface's
+ *                    DOFs, inverted per point, applied in FP32; interfaces of
+ *                    more than 32 DOFs fall back to Jacobi). The same solution
+ *                    and the same stopping test on the unpreconditioned
+ *                    residual in every case (2);
  *   "cg_replace_ratio"  SFB_CG_MIXED: a point's residual is replaced by the
  *                    FP64 residual at the next check once the recursive one
  *                    has dropped by this factor since the last replacement,

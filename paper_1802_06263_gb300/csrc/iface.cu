@@ -168,6 +168,16 @@ struct IfaceArgs {
   double* rlast;        // mixed CG: norm of the last FP64 residual
   int* rflag;           // mixed CG: FP64 residual due at the next check
   double* dinv;         // Jacobi preconditioner: 1 / diag(S^l) per point, or null (plain CG)
+  // interface block-Jacobi preconditioner (when minv is set, it replaces dinv):
+  // per point and mortar interface e the inverse of the diagonal block of S^l on
+  // e's DOFs [if_off[e], if_off[e] + if_n[e]), FP32, at minv + l * minv_ld + if_moff[e]
+  float* minv;
+  int64_t minv_ld;
+  int n_if;
+  const int* if_off;
+  const int* if_n;
+  const int* if_moff;
+  const int* dof_if;    // per global DOF: its interface
   int* pstat;
   int64_t n_pts;
 };
@@ -214,12 +224,82 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // r = g = sum_i R_i^T g_i^{k_i(l)}, p = r, lambda = 0; one warp per point.
+constexpr int kBlkMax = 32;   // largest interface block of the block-Jacobi preconditioner
+
+// One warp per (point, interface): the interface's diagonal block of S^l,
+// B[i][j] = sum over the two units sharing the interface of their basis
+// entries, inverted by the symmetric sweep with one column per lane (the
+// pivot column by shuffles) and stored in FP32.
+__global__ void bjacobi_setup_kernel(IfaceArgs a) {
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t l = wid / a.n_if;
+  const int e = (int)(wid - l * a.n_if);
+  if (l >= a.n_pts) return;
+  if (a.pstat[l] & kBadIdx) return;
+  const int n = a.if_n[e], d0 = a.if_off[e];
+  double col[kBlkMax];
+#pragma unroll
+  for (int i = 0; i < kBlkMax; ++i) {
+    double v = 0.0;
+    if (lane < n && i < n) {
+      const int di = d0 + i, dj = d0 + lane;
+      for (int side = 0; side < 2; ++side) {
+        const int u = a.ldof[4 * di + 2 * side], li = a.ldof[4 * di + 2 * side + 1];
+        const int lj = a.ldof[4 * dj + 2 * side + 1];
+        const int k = u < a.ns ? a.kmap[l * a.ns + u] : 0;
+        int R;
+        const double* ph = unit_phi(a, u, k, R);
+        v += ph[li * R + lj];
+      }
+    } else if (i == lane) {
+      v = 1.0;   // identity outside the block
+    }
+    col[i] = v;
+  }
+#pragma unroll
+  for (int kk = 0; kk < kBlkMax; ++kk) {
+    if (kk >= n) break;
+    double piv = __shfl_sync(0xffffffffu, col[kk], kk);
+    if (!(piv > 0.0)) piv = 1.0;
+    const double inv = 1.0 / piv;
+    const double rowk = col[kk];
+#pragma unroll
+    for (int i = 0; i < kBlkMax; ++i) {
+      const double colk = __shfl_sync(0xffffffffu, col[i], kk);
+      double v;
+      if (i == kk) v = lane == kk ? -inv : rowk * inv;
+      else v = lane == kk ? colk * inv : fma(-colk, rowk * inv, col[i]);
+      col[i] = v;
+    }
+  }
+  if (lane < n) {
+    float* M = a.minv + l * a.minv_ld + a.if_moff[e];
+#pragma unroll
+    for (int i = 0; i < kBlkMax; ++i)
+      if (i < n) M[i * n + lane] = (float)(-col[i]);
+  }
+}
+
+// z = M^{-1} r for the DOFs d = lane + 32 j of one point (warp-wide): r is
+// staged in FP32 in the warp's shared buffer stage[n_lambda]; returns z_d.
+__device__ __forceinline__ double bjacobi_apply(const IfaceArgs& a, int64_t l, const float* stage, int d) {
+  const int e = a.dof_if[d];
+  const int n = a.if_n[e], d0 = a.if_off[e], i = d - d0;
+  const float* M = a.minv + l * a.minv_ld + a.if_moff[e] + i * n;
+  float z = 0.f;
+  for (int j = 0; j < n; ++j) z = fmaf(M[j], stage[d0 + j], z);
+  return (double)z;
+}
+
 // With the Jacobi preconditioner dinv = 1 / diag(S^l), z = dinv r, p = z and
 // rr holds r.z; without it z = r and rr = r.r.
 __global__ void init_kernel(IfaceArgs a) {
+  extern __shared__ float stage_all[];   // [warps][n_lambda] (block preconditioner)
   const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (l >= a.n_pts) return;
+  float* stage = stage_all + (threadIdx.x >> 5) * a.n_lambda;
   double s2 = 0.0, rz = 0.0;
   for (int64_t d = lane; d < a.n_lambda; d += 32) {
     double g = 0.0, dg = 0.0;
@@ -238,11 +318,21 @@ __global__ void init_kernel(IfaceArgs a) {
       a.dinv[l * a.n_lambda + d] = di;
       z = di * g;
     }
+    if (a.minv) stage[d] = f64_to_f32_bits(g);
     a.r[l * a.n_lambda + d] = g;
     a.p[l * a.n_lambda + d] = z;
     a.lam[l * a.n_lambda + d] = 0.0;
     s2 += g * g;
     rz += g * z;
+  }
+  if (a.minv) {   // z = M^{-1} g with the interface blocks
+    __syncwarp();
+    rz = 0.0;
+    for (int64_t d = lane; d < a.n_lambda; d += 32) {
+      const double z = bjacobi_apply(a, l, stage, (int)d);
+      a.p[l * a.n_lambda + d] = z;
+      rz += a.r[l * a.n_lambda + d] * z;
+    }
   }
   s2 = warp_sum(s2);
   rz = warp_sum(rz);
@@ -377,9 +467,11 @@ constexpr int kUpd = 8;   // DOFs per lane held in registers by the update (n_la
 template <bool kRegs>
 __global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed, double replace_ratio,
                               double pause_ratio) {
+  extern __shared__ float stage_all[];   // [warps][n_lambda] (block preconditioner)
   const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (l >= a.n_pts) return;
+  float* stage = stage_all + (threadIdx.x >> 5) * a.n_lambda;
   if (a.pstat[l] != 0) return;
   const double* Yl = a.Y + l * a.NY;
   double* pl = a.p + l * a.n_lambda;
@@ -426,9 +518,26 @@ __global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed, doubl
         const double rv = fma(-alpha, qv[j], rl[d]);
         rl[d] = rv;
         rn = fma(rv, rv, rn);
-        const double zv = dl ? dl[d] * rv : rv;
-        rv_keep[j] = zv;
-        rz = fma(rv, zv, rz);
+        if (a.minv) {
+          stage[d] = f64_to_f32_bits(rv);
+          rv_keep[j] = rv;
+        } else {
+          const double zv = dl ? dl[d] * rv : rv;
+          rv_keep[j] = zv;
+          rz = fma(rv, zv, rz);
+        }
+      }
+    }
+    if (a.minv) {   // z = M^{-1} r with the interface blocks (r staged in FP32)
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < kUpd; ++j) {
+        const int d = lane + 32 * j;
+        if (d < n) {
+          const double zv = bjacobi_apply(a, l, stage, d);
+          rz = fma(rv_keep[j], zv, rz);
+          rv_keep[j] = zv;
+        }
       }
     }
   } else {
@@ -438,11 +547,16 @@ __global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed, doubl
       const double rv = rl[d] - alpha * q;
       rl[d] = rv;
       rn += rv * rv;
-      rz += rv * (dl ? dl[d] * rv : rv);
+      if (a.minv) stage[d] = f64_to_f32_bits(rv);
+      else rz += rv * (dl ? dl[d] * rv : rv);
+    }
+    if (a.minv) {
+      __syncwarp();
+      for (int d = lane; d < n; d += 32) rz += rl[d] * bjacobi_apply(a, l, stage, d);
     }
   }
   rn = warp_sum(rn);
-  rz = dl ? warp_sum(rz) : rn;
+  rz = (dl || a.minv) ? warp_sum(rz) : rn;
   int dec = 0;   // bit 0 done, bit 1 pause, bit 2 flag
   double beta = 0.0;
   if (lane == 0) {
@@ -466,7 +580,8 @@ __global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed, doubl
         if (d < n) pl[d] = fma(beta, pv[j], rv_keep[j]);
       }
     } else {
-      for (int d = lane; d < n; d += 32) pl[d] = (dl ? dl[d] * rl[d] : rl[d]) + beta * pl[d];
+      for (int d = lane; d < n; d += 32)
+        pl[d] = (a.minv ? bjacobi_apply(a, l, stage, d) : (dl ? dl[d] * rl[d] : rl[d])) + beta * pl[d];
     }
   }
   __syncwarp();
@@ -483,9 +598,11 @@ __global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed, doubl
 // point has converged if ||r|| <= rtol ||g||; otherwise it continues from the
 // replaced residual with the same direction p (p = r after a breakdown).
 __global__ void reliable_kernel(IfaceArgs a, double rtol, int it) {
+  extern __shared__ float stage_all[];   // [warps][n_lambda] (block preconditioner)
   const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (l >= a.n_pts) return;
+  float* stage = stage_all + (threadIdx.x >> 5) * a.n_lambda;
   const int s = a.pstat[l];
   if (!selected(a, l, s, 1)) return;
   const double* Yl = a.Y + l * a.NY;
@@ -504,14 +621,20 @@ __global__ void reliable_kernel(IfaceArgs a, double rtol, int it) {
     const double rv = g - q;
     rl[d] = rv;
     rn += rv * rv;
-    rz += rv * (a.dinv ? a.dinv[l * a.n_lambda + d] * rv : rv);
+    if (a.minv) stage[d] = f64_to_f32_bits(rv);
+    else rz += rv * (a.dinv ? a.dinv[l * a.n_lambda + d] * rv : rv);
+  }
+  if (a.minv) {
+    __syncwarp();
+    for (int64_t d = lane; d < a.n_lambda; d += 32) rz += rl[d] * bjacobi_apply(a, l, stage, (int)d);
   }
   rn = warp_sum(rn);
   rz = warp_sum(rz);
   const bool conv = sqrt(rn) <= rtol * a.gn[l];
   if (!conv && (s & kRestart)) {
     double* pl = a.p + l * a.n_lambda;
-    for (int64_t d = lane; d < a.n_lambda; d += 32) pl[d] = a.dinv ? a.dinv[l * a.n_lambda + d] * rl[d] : rl[d];
+    for (int64_t d = lane; d < a.n_lambda; d += 32)
+      pl[d] = a.minv ? bjacobi_apply(a, l, stage, (int)d) : (a.dinv ? a.dinv[l * a.n_lambda + d] * rl[d] : rl[d]);
   }
   __syncwarp();
   if (lane == 0) {
@@ -1346,7 +1469,13 @@ static IfaceArgs make_args(sfb_ctx* c, int64_t n_pts) {
   a.ldof = d.ldof; a.yoff = d.yoff; a.n_lambda = c->n_lambda; a.kmap = d.kmap; a.grp_pts = d.grp_pts; a.pts_ld = c->ws_pts;
   a.tiles = d.tiles; a.max_tiles = c->max_tiles; a.n_tiles = d.n_tiles; a.lam = d.lam; a.r = d.r; a.p = d.p;
   a.Y = d.Y; a.rr = d.rr; a.gn = d.gn; a.rlast = d.rlast; a.rflag = d.rflag; a.pstat = d.pstat; a.n_pts = n_pts;
-  a.dinv = c->opt_cg_jacobi ? d.dinv : nullptr;
+  // interface blocks wider than kBlkMax DOFs fall back to the Jacobi preconditioner
+  const bool blocks = c->opt_cg_precond == 2 && c->max_if_dof <= kBlkMax;
+  a.dinv = (c->opt_cg_precond == 1 || (c->opt_cg_precond == 2 && !blocks)) ? d.dinv : nullptr;
+  a.minv = blocks ? d.minv : nullptr;
+  a.minv_ld = c->minv_ld;
+  a.n_if = (int)c->ifaces.size();
+  a.if_off = d.if_off; a.if_n = d.if_n; a.if_moff = d.if_moff; a.dof_if = d.dof_if;
   return a;
 }
 
@@ -1385,7 +1514,20 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   CK(cudaEventRecord(c->ev[1], st));
   const int warps_per_block = 8;
   const int ublocks = (int)((n_pts + warps_per_block - 1) / warps_per_block);
-  init_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a);
+  const size_t stg = a.minv ? sizeof(float) * warps_per_block * (size_t)c->n_lambda : 0;
+  if (stg > 48 * 1024) {
+    CK(cudaFuncSetAttribute(init_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stg));
+    CK(cudaFuncSetAttribute(update_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stg));
+    CK(cudaFuncSetAttribute(update_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stg));
+    CK(cudaFuncSetAttribute(reliable_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stg));
+  }
+  if (a.minv) {
+    const int64_t warps = n_pts * a.n_if;
+    bjacobi_setup_kernel<<<(int)((warps + 7) / 8), 256, 0, st>>>(a);
+    ++c->launches;
+    CK(cudaGetLastError());
+  }
+  init_kernel<<<ublocks, 32 * warps_per_block, stg, st>>>(a);
   ++c->launches;
   CK(cudaGetLastError());
   int maxR = (int)c->stokes.dofs.size();
@@ -1405,10 +1547,10 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
       else matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.p, 0, d.active + 2);
       ++c->launches;
       if (c->n_lambda <= 32 * kUpd)
-        update_kernel<true><<<ublocks, 32 * warps_per_block, 0, st>>>(a, it, rtol, mixed ? 1 : 0, replace_ratio,
+        update_kernel<true><<<ublocks, 32 * warps_per_block, stg, st>>>(a, it, rtol, mixed ? 1 : 0, replace_ratio,
                                                                       pause_ratio);
       else
-        update_kernel<false><<<ublocks, 32 * warps_per_block, 0, st>>>(a, it, rtol, mixed ? 1 : 0, replace_ratio,
+        update_kernel<false><<<ublocks, 32 * warps_per_block, stg, st>>>(a, it, rtol, mixed ? 1 : 0, replace_ratio,
                                                                        pause_ratio);
       ++c->launches;
     }
@@ -1416,7 +1558,7 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
       // FP64 residuals of the points that asked for one
       matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.lam, 1, d.active + 2);
       ++c->launches;
-      reliable_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, rtol, it);
+      reliable_kernel<<<ublocks, 32 * warps_per_block, stg, st>>>(a, rtol, it);
       ++c->launches;
     }
     CK(cudaGetLastError());

@@ -108,6 +108,11 @@ struct Dev {
   double* gn = nullptr;
   double* rlast = nullptr;
   double* dinv = nullptr;     // Jacobi preconditioner of the interface CG, per point
+  float* minv = nullptr;      // interface block-Jacobi inverses, per point [minv_ld]
+  int* if_off = nullptr;      // per interface: first global DOF, DOF count, offset of its block
+  int* if_n = nullptr;
+  int* if_moff = nullptr;
+  int* dof_if = nullptr;      // per global DOF: its interface
   int* rflag = nullptr;
   int* pstat = nullptr;       // per point: iterations (>0 converged, <0 active/failed)
   int* active = nullptr;
@@ -177,12 +182,14 @@ struct sfb_ctx {
   bool mom_shift_set = false;
   int mom_chunks = 1;
   int mom_work_cap = 0;       // entries of dev.mom_work
+  int64_t minv_ld = 0;        // sum over interfaces of (DOF count)^2
+  int max_if_dof = 0;         // largest interface DOF count
   int64_t gmom_stride = 1;
   // options (sfb_set_option)
   double opt_refine_tol = 1e-10;
   int opt_refine_max = 8;
   int opt_cg_chunk = 8;
-  int opt_cg_jacobi = 1;        // diagonal (Jacobi) preconditioning of the interface CG
+  int opt_cg_precond = 2;       // interface CG preconditioner: 0 none, 1 Jacobi, 2 interface blocks
   double opt_cg_replace = 0.1;  // mixed CG: FP64 residual once the recursive one drops by this factor
   double opt_big_factor = 1.0;   // groups above this many times (R+1) points use coefficient moments
   // device-time phase markers of the last interface solve (CUDA events)

@@ -256,6 +256,13 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   d.gn = cv.take<double>(P);
   d.rlast = cv.take<double>(P);
   d.dinv = cv.take<double>((size_t)P * c->n_lambda);
+  c->minv_ld = 0; c->max_if_dof = 0;
+  for (const HostIface& f : c->ifaces) { c->minv_ld += (int64_t)f.n_dof * f.n_dof; c->max_if_dof = std::max(c->max_if_dof, f.n_dof); }
+  d.minv = cv.take<float>((size_t)P * std::max<int64_t>(c->minv_ld, 1));
+  d.if_off = cv.take<int>(std::max<size_t>(c->ifaces.size(), 1));
+  d.if_n = cv.take<int>(std::max<size_t>(c->ifaces.size(), 1));
+  d.if_moff = cv.take<int>(std::max<size_t>(c->ifaces.size(), 1));
+  d.dof_if = cv.take<int>((size_t)std::max<int64_t>(c->n_lambda, 1));
   d.rflag = cv.take<int>(P);
   d.pstat = cv.take<int>(P);
   d.active = cv.take<int>(4);
@@ -629,6 +636,18 @@ sfb_status upload_tables(sfb_ctx* c) {
   for (size_t a = 0; a < c->stokes.dofs.size(); ++a) put(c->stokes.dofs[a], ns, (int)a);
   for (int64_t g = 0; g < c->n_lambda; ++g)
     if (fill[g] != 2) return fail(c, SFB_ERR_ARG, "a mortar DOF is not shared by exactly two subdomains");
+  std::vector<int> if_off, if_n, if_moff, dof_if(c->n_lambda, 0);
+  {
+    int mo = 0;
+    for (size_t e = 0; e < c->ifaces.size(); ++e) {
+      const HostIface& f = c->ifaces[e];
+      if_off.push_back((int)f.off);
+      if_n.push_back(f.n_dof);
+      if_moff.push_back(mo);
+      mo += f.n_dof * f.n_dof;
+      for (int i = 0; i < f.n_dof; ++i) dof_if[f.off + i] = (int)e;
+    }
+  }
   std::vector<int> yoff(2 * c->n_lambda);
   for (int64_t g = 0; g < c->n_lambda; ++g)
     for (int f = 0; f < 2; ++f) yoff[2 * g + f] = (int)(c->ybase[ldof[4 * g + 2 * f]] + ldof[4 * g + 2 * f + 1]);
@@ -646,7 +665,8 @@ sfb_status upload_tables(sfb_ctx* c) {
   UP(d.subs, sd); UP(d.proj, proj); UP(d.dofinfo, info); UP(d.kl, kl); UP(d.yloc, yloc); UP(d.gdof, gdof);
   UP(d.item_sub, item_sub); UP(d.item_k, item_k); UP(d.off, c->offs);
   UP(d.s_gdof, c->stokes.dofs); UP(d.ybase, c->ybase); UP(d.dim_off, dim_off); UP(d.loc_off, loc_off);
-  UP(d.cell_off, cell_off); UP(d.face_off, face_off); UP(d.ldof, ldof); UP(d.yoff, yoff); UP(d.hash, htab); UP(d.hash_off, hoff);
+  UP(d.cell_off, cell_off); UP(d.face_off, face_off); UP(d.ldof, ldof); UP(d.yoff, yoff);
+  UP(d.if_off, if_off); UP(d.if_n, if_n); UP(d.if_moff, if_moff); UP(d.dof_if, dof_if); UP(d.hash, htab); UP(d.hash_off, hoff);
   UP(d.hash_cap, hcap);
 #undef UP
   SFB_CUDA(cudaStreamSynchronize(st), "upload");
@@ -911,9 +931,9 @@ sfb_status sfb_set_option(sfb_ctx* c, const char* name, double value) {
   } else if (n == "cg_check_every") {
     if (!(value >= 1 && value <= 1000)) return fail(c, SFB_ERR_ARG, "cg_check_every must lie in [1, 1000]");
     c->opt_cg_chunk = (int)value;
-  } else if (n == "cg_jacobi") {
-    if (!(value == 0 || value == 1)) return fail(c, SFB_ERR_ARG, "cg_jacobi must be 0 or 1");
-    c->opt_cg_jacobi = (int)value;
+  } else if (n == "cg_precond") {
+    if (!(value == 0 || value == 1 || value == 2)) return fail(c, SFB_ERR_ARG, "cg_precond must be 0, 1 or 2");
+    c->opt_cg_precond = (int)value;
   } else if (n == "cg_replace_ratio") {
     if (!(value >= 1e-4 && value < 1)) return fail(c, SFB_ERR_ARG, "cg_replace_ratio must lie in [1e-4, 1)");
     c->opt_cg_replace = value;

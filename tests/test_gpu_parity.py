@@ -109,21 +109,22 @@ def test_not_converged_is_reported():
 
 
 @pytest.mark.parametrize("krylov", [0, 1])
-@pytest.mark.parametrize("jacobi", [0, 1])
-def test_plain_and_jacobi_cg_reach_the_same_solution(jacobi, krylov):
-    """CG as the paper states it (no preconditioner) and CG preconditioned by
-    diag(S^l) stop on the same unpreconditioned residual and give the same
-    mortar solution and moments; the preconditioned one in fewer iterations."""
+@pytest.mark.parametrize("precond", [0, 1, 2])
+def test_cg_preconditioners_reach_the_same_solution(precond, krylov):
+    """CG as the paper states it (no preconditioner), with the Jacobi and with
+    the interface block-Jacobi preconditioner stop on the same
+    unpreconditioned residual and give the same mortar solution and moments;
+    each preconditioner in fewer iterations than the one before."""
     p, y, wt, lams, mom = oracle_case("medium")
     s, _ = _solver("medium", 0)
-    s.set_option("cg_jacobi", jacobi)
+    s.set_option("cg_precond", precond)
     lam, it, rc = s.solve_host(y, wt, rtol=1e-13, max_it=5000, krylov=krylov)
     assert rc == 0 and np.all(it > 0)
     assert rel(lam, lams) < 1e-9
     m, v = s.moments("darcy_flux")
     assert rel(m, mom["darcy_flux"][0]) < 1e-9
     assert rel(v, mom["darcy_flux"][1]) < 1e-8
-    if jacobi == 0:
-        s.set_option("cg_jacobi", 1)
-        _, it_j, _ = s.solve_host(y, wt, rtol=1e-13, max_it=5000, krylov=krylov)
-        assert it_j.max() < it.max()
+    if precond < 2:
+        s.set_option("cg_precond", precond + 1)
+        _, it_next, _ = s.solve_host(y, wt, rtol=1e-13, max_it=5000, krylov=krylov)
+        assert it_next.max() < it.max()
