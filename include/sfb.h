@@ -259,7 +259,7 @@ sfb_status sfb_build_basis_item_noalloc(sfb_ctx* ctx, int32_t sub, int32_t k, in
  *                    DOFs, inverted per point, applied in FP32; interfaces of
  *                    more than 32 DOFs fall back to Jacobi). The same solution
  *                    and the same stopping test on the unpreconditioned
- *                    residual in every case (2);
+ *                    residual in every case (1);
  *   "cg_replace_ratio"  SFB_CG_MIXED: a point's residual is replaced by the
  *                    FP64 residual at the next check once the recursive one
  *                    has dropped by this factor since the last replacement,

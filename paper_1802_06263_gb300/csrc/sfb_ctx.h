@@ -189,7 +189,7 @@ struct sfb_ctx {
   double opt_refine_tol = 1e-10;
   int opt_refine_max = 8;
   int opt_cg_chunk = 8;
-  int opt_cg_precond = 2;       // interface CG preconditioner: 0 none, 1 Jacobi, 2 interface blocks
+  int opt_cg_precond = 1;       // interface CG preconditioner: 0 none, 1 Jacobi, 2 interface blocks
   double opt_cg_replace = 0.1;  // mixed CG: FP64 residual once the recursive one drops by this factor
   double opt_big_factor = 1.0;   // groups above this many times (R+1) points use coefficient moments
   // device-time phase markers of the last interface solve (CUDA events)
