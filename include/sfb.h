@@ -232,6 +232,14 @@ sfb_status sfb_launch_count(const sfb_ctx* ctx, int64_t* n);
  * number of lockstep CG iterations run. Synchronises the stream. */
 sfb_status sfb_solve_timings(sfb_ctx* ctx, double* ms_out, int32_t* cg_iterations);
 
+/* SM cycles per CTA of the last interface CG in one cooperative launch
+ * ("cg_persistent" 1), by step: [0] tile products of the iterations, [1] the
+ * grid barrier after them, [2] point updates, [3] the barrier after them,
+ * [4] FP64 products of the mixed CG's checks, [5] the rest of the checks
+ * (FP64 residual replacement, iterating-point count, their barriers).
+ * cycles_out holds 6 values; all zero after a CG of one launch per step. */
+sfb_status sfb_cg_phase_cycles(const sfb_ctx* ctx, double* cycles_out);
+
 /* Builds one stochastic-basis item (Darcy subdomain `sub`, local realization
  * `k`) without allocating device memory; the paper has no counterpart, this
  * is for callers that cannot call cudaMalloc (an application that already
@@ -252,7 +260,15 @@ sfb_status sfb_build_basis_item_noalloc(sfb_ctx* ctx, int32_t sub, int32_t k, in
  *   "refine_tol"     mixed form: stop refining when the predicted relative
  *                    error of X is below this (default 1e-10);
  *   "refine_max"     mixed form: at most this many FP64 residual passes (8);
- *   "cg_check_every" CG iterations between convergence checks on the host (8);
+ *   "cg_check_every" CG iterations between convergence checks (8);
+ *   "cg_persistent"  1: the whole CG in one cooperative launch (grid barriers
+ *                    between the product and update steps, convergence checks
+ *                    on the device; bit-identical results); 0: one launch per
+ *                    step with a host check every cg_check_every iterations.
+ *                    The one-launch form falls back to the other when the
+ *                    device cannot launch it, and for SFB_CG_MIXED when each
+ *                    CTA cannot keep its share of the FP32 bases (three
+ *                    tiles) in shared memory (1);
  *   "cg_precond"     interface CG preconditioner: 0 none (CG as the paper
  *                    states it), 1 Jacobi (diag(S^l)), 2 interface blocks
  *                    (the diagonal block of S^l on each mortar interface's

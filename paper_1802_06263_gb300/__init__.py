@@ -85,6 +85,7 @@ _SIGS = {
     "sfb_moments_reset": (ctypes.c_int, [ctypes.c_void_p]),
     "sfb_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_double]),
     "sfb_solve_timings": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _i32p]),
+    "sfb_cg_phase_cycles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sfb_launch_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "sfb_build_basis_item_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -334,6 +335,13 @@ class Solver:
         self._check(self.lib.sfb_solve_timings(self.h, ms.ctypes.data, ctypes.byref(it)))
         return {"index_ms": ms[0], "cg_ms": ms[1], "status_ms": ms[2], "darcy_moments_ms": ms[3],
                 "stokes_moments_ms": ms[4], "cg_iterations": it.value}
+
+    def cg_phase_cycles(self):
+        """SM cycles per CTA of the last one-launch CG by step (tile products,
+        barrier, updates, barrier, FP64 check products, rest of the checks)."""
+        cyc = np.zeros(6)
+        self._check(self.lib.sfb_cg_phase_cycles(self.h, cyc.ctypes.data))
+        return dict(zip(("tiles", "tiles_barrier", "update", "update_barrier", "check_tiles", "check_rest"), cyc))
 
     def set_option(self, name, value):
         self._check(self.lib.sfb_set_option(self.h, name.encode(), float(value)))

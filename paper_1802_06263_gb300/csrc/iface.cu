@@ -17,6 +17,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <cstring>
+#include <vector>
 
 #include "sfb_ctx.h"
 
@@ -357,78 +359,78 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 // product runs in T (FP64, or FP32 on the rounded copy of Phi for the inner
 // products of the mixed CG) with 2 x 4 register tiles (two rows of Phi, four
 // points). The bulk copy rounds R*R*sizeof(T) up to 16 bytes; the extra bytes
-// lie inside the same item (its g block follows Phi).
-template <typename T>
-__global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, const double* __restrict__ vin, int sel,
-                                                     int* err) {
-  extern __shared__ __align__(16) unsigned char smv_raw[];
-  __shared__ __align__(8) uint64_t bar;
-  const int u = blockIdx.y;
-  const int t = blockIdx.x;
-  if (t >= a.n_tiles[u]) return;
-  const int* tl = a.tiles + 3 * ((int64_t)u * a.max_tiles + t);
-  const int k = tl[0], q0 = tl[1], cntp = tl[2];
-  const int* pts = a.grp_pts + (int64_t)u * a.pts_ld + q0;
-  __shared__ int sidx[kTG];   // tile slots of the selected points, in order
-  __shared__ int nsel_s;
+// lie inside the same item (its g block follows Phi). The steps below serve
+// matvec_kernel (one CTA per tile) and the persistent CG kernel (each CTA
+// walks a strided share of all tiles) alike.
+struct TileScratch {
+  int sidx[kTG];        // tile slots of the selected points, in order
+  int nsel;
+  int64_t spt[kTG];     // the selected points' indices
+  int sgd[kMaxCols];    // the unit's global DOFs
+};
+
+__device__ __forceinline__ void mbar_init1(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// One thread: `bytes` of a basis into dst, completing on bar. The proxy fence
+// orders earlier generic reads of dst before the asynchronous write.
+__device__ __forceinline__ void phi_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// Bounded wait for the phase of bar with the given parity; false after the limit.
+__device__ __forceinline__ bool phi_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok = 0;
+  for (int it = 0; it < (1 << 22) && !ok; ++it)
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+  return ok != 0;
+}
+
+// The tile's selected points (a block-uniform count; every thread calls it).
+__device__ __forceinline__ int tile_select(const IfaceArgs& a, const int* pts, int cntp, int sel, TileScratch& ts) {
   const int act = threadIdx.x < cntp ? selected(a, pts[threadIdx.x], a.pstat[pts[threadIdx.x]], sel) : 0;
   if (threadIdx.x < 32) {     // kTG == 32: warp 0 holds one slot per lane
     const unsigned mask = __ballot_sync(0xffffffffu, act);
-    if (act) sidx[__popc(mask & ((1u << threadIdx.x) - 1u))] = threadIdx.x;
-    if (threadIdx.x == 0) nsel_s = __popc(mask);
+    if (act) ts.sidx[__popc(mask & ((1u << threadIdx.x) - 1u))] = threadIdx.x;
+    if (threadIdx.x == 0) ts.nsel = __popc(mask);
   }
-  if (!__syncthreads_or(act)) return;  // no point of the tile is selected
-  const int nsel = nsel_s;
-  const int nsel4 = (nsel + 3) & ~3;   // columns computed: the selected points, padded to 4
-  int R;
-  const T* ph = unit_phi_t<T>(a, u, k, R);
+  if (!__syncthreads_or(act)) return 0;
+  return ts.nsel;
+}
+
+// Pv[i][q] = v_{l_q}[gdof_u(i)] in T for the nsel selected points, padded to
+// a multiple of 4 points with zeros; the points' indices and the unit's global
+// DOFs are staged once so that each gathered entry is one dependent load.
+template <typename T>
+__device__ __forceinline__ void tile_gather(const IfaceArgs& a, const double* __restrict__ vin, const int* pts, int u,
+                                            int R, int nsel, TileScratch& ts, T* Pv) {
   const int64_t* gd = u == a.ns ? a.sgdof : a.gdof + a.subs[u].gdof_off;
-  const int rr4 = (R * R + 3) & ~3;
-  T* Ph = reinterpret_cast<T*>(smv_raw);   // [R][R]
-  T* Pv = Ph + rr4;                        // [R][kTG + 1]
-  // the selected points' indices and the unit's global DOFs, staged once so
-  // that each gathered entry is a single dependent global load
-  __shared__ int64_t spt[kTG];
-  __shared__ int sgd[kMaxCols];
-  if (threadIdx.x < nsel) spt[threadIdx.x] = pts[sidx[threadIdx.x]];
-  for (int i = threadIdx.x; i < R; i += blockDim.x) sgd[i] = (int)gd[i];
-  const uint32_t bytes = (uint32_t)((R * R * (int)sizeof(T) + 15) & ~15);
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar)), "r"(bytes)
-                 : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(Ph)),
-                 "l"(ph), "r"(bytes), "r"(smem_u32(&bar))
-                 : "memory");
-  }
-  __syncthreads();  // the initialised barrier, spt and sgd are visible to every thread
+  if (threadIdx.x < nsel) ts.spt[threadIdx.x] = pts[ts.sidx[threadIdx.x]];
+  for (int i = threadIdx.x; i < R; i += blockDim.x) ts.sgd[i] = (int)gd[i];
+  __syncthreads();
+  const int nsel4 = (nsel + 3) & ~3;
   for (int e = threadIdx.x; e < nsel4 * R; e += blockDim.x) {
     const int q = e / R, i = e - q * R;
     double v = 0.0;
-    if (q < nsel) v = vin[spt[q] * a.n_lambda + sgd[i]];
+    if (q < nsel) v = vin[ts.spt[q] * a.n_lambda + ts.sgd[i]];
     Pv[i * (kTG + 1) + q] = from_f64<T>(v);
   }
-  uint32_t ok = 0;
-  for (int it = 0; it < (1 << 22) && !ok; ++it)
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(ok)
-                 : "r"(smem_u32(&bar))
-                 : "memory");
-  if (__syncthreads_or(!ok)) {
-    if (threadIdx.x == 0) {
-      atomicOr(err, 1);
-      // a bounded second chance for the copy in flight before the CTA exits
-      for (int it = 0; it < (1 << 22) && !ok; ++it)
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(ok)
-                     : "r"(smem_u32(&bar))
-                     : "memory");
-    }
-    __syncthreads();
-    return;
-  }
+}
+
+// Y rows of the selected points = Ph Pv.
+template <typename T>
+__device__ __forceinline__ void tile_product(const IfaceArgs& a, int u, int R, int nsel, const TileScratch& ts,
+                                             const T* Ph, const T* Pv) {
+  const int nsel4 = (nsel + 3) & ~3;
   const int nrp = (R + 1) >> 1;
   const int ncg = nsel4 >> 2;
   for (int tt = threadIdx.x; tt < nrp * ncg; tt += blockDim.x) {
@@ -449,11 +451,48 @@ __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, const double* 
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (c0 + q >= nsel) break;
-      double* y = a.Y + spt[c0 + q] * a.NY + a.ybase[u];
+      double* y = a.Y + ts.spt[c0 + q] * a.NY + a.ybase[u];
       y[r0] = to_f64(acc[0][q]);
       if (two) y[r0 + 1] = to_f64(acc[1][q]);
     }
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, const double* __restrict__ vin, int sel,
+                                                     int* err) {
+  extern __shared__ __align__(16) unsigned char smv_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ TileScratch ts;
+  const int u = blockIdx.y;
+  const int t = blockIdx.x;
+  if (t >= a.n_tiles[u]) return;
+  const int* tl = a.tiles + 3 * ((int64_t)u * a.max_tiles + t);
+  const int k = tl[0], q0 = tl[1], cntp = tl[2];
+  const int* pts = a.grp_pts + (int64_t)u * a.pts_ld + q0;
+  const int nsel = tile_select(a, pts, cntp, sel, ts);
+  if (nsel == 0) return;   // no point of the tile is selected
+  int R;
+  const T* ph = unit_phi_t<T>(a, u, k, R);
+  const int rr4 = (R * R + 3) & ~3;
+  T* Ph = reinterpret_cast<T*>(smv_raw);   // [R][R]
+  T* Pv = Ph + rr4;                        // [R][kTG + 1]
+  const uint32_t bytes = (uint32_t)((R * R * (int)sizeof(T) + 15) & ~15);
+  if (threadIdx.x == 0) {
+    mbar_init1(&bar);
+    phi_load(Ph, ph, bytes, &bar);
+  }
+  tile_gather<T>(a, vin, pts, u, R, nsel, ts, Pv);   // its barrier publishes the initialised mbarrier
+  const bool ok = phi_wait(&bar, 0);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) {
+      atomicOr(err, 1);
+      phi_wait(&bar, 0);   // a bounded second chance for the copy in flight before the CTA exits
+    }
+    __syncthreads();
+    return;
+  }
+  tile_product<T>(a, u, R, nsel, ts, Ph, Pv);
 }
 
 // q = S p from the per-unit products, then the CG update; one warp per point.
@@ -464,14 +503,11 @@ __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, const double* 
 // recursive and the true residual never drift far apart before replacement.
 constexpr int kUpd = 8;   // DOFs per lane held in registers by the update (n_lambda <= 256)
 
+// The update of point l by its warp; stage is the warp's FP32 buffer of
+// n_lambda entries (block preconditioner).
 template <bool kRegs>
-__global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed, double replace_ratio,
-                              double pause_ratio) {
-  extern __shared__ float stage_all[];   // [warps][n_lambda] (block preconditioner)
-  const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (l >= a.n_pts) return;
-  float* stage = stage_all + (threadIdx.x >> 5) * a.n_lambda;
+__device__ __forceinline__ void update_point(const IfaceArgs& a, int64_t l, int lane, float* stage, int it,
+                                             double rtol, int mixed, double replace_ratio, double pause_ratio) {
   if (a.pstat[l] != 0) return;
   const double* Yl = a.Y + l * a.NY;
   double* pl = a.p + l * a.n_lambda;
@@ -593,16 +629,22 @@ __global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed, doubl
   }
 }
 
+template <bool kRegs>
+__global__ void update_kernel(IfaceArgs a, int it, double rtol, int mixed, double replace_ratio,
+                              double pause_ratio) {
+  extern __shared__ float stage_all[];   // [warps][n_lambda] (block preconditioner)
+  const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (l >= a.n_pts) return;
+  update_point<kRegs>(a, l, threadIdx.x & 31, stage_all + (threadIdx.x >> 5) * a.n_lambda, it, rtol, mixed,
+                      replace_ratio, pause_ratio);
+}
+
 // FP64 residual replacement of the mixed CG, one warp per point due (paused
 // or flagged), on the FP64 products Y = Phi (R lambda): r = g - S lambda. The
 // point has converged if ||r|| <= rtol ||g||; otherwise it continues from the
 // replaced residual with the same direction p (p = r after a breakdown).
-__global__ void reliable_kernel(IfaceArgs a, double rtol, int it) {
-  extern __shared__ float stage_all[];   // [warps][n_lambda] (block preconditioner)
-  const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (l >= a.n_pts) return;
-  float* stage = stage_all + (threadIdx.x >> 5) * a.n_lambda;
+__device__ __forceinline__ void reliable_point(const IfaceArgs& a, int64_t l, int lane, float* stage, double rtol,
+                                               int it) {
   const int s = a.pstat[l];
   if (!selected(a, l, s, 1)) return;
   const double* Yl = a.Y + l * a.NY;
@@ -645,6 +687,13 @@ __global__ void reliable_kernel(IfaceArgs a, double rtol, int it) {
   }
 }
 
+__global__ void reliable_kernel(IfaceArgs a, double rtol, int it) {
+  extern __shared__ float stage_all[];   // [warps][n_lambda] (block preconditioner)
+  const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (l >= a.n_pts) return;
+  reliable_point(a, l, threadIdx.x & 31, stage_all + (threadIdx.x >> 5) * a.n_lambda, rtol, it);
+}
+
 __global__ void count_active(const int* pstat, int64_t n, int* out) {
   int c = 0;
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x)
@@ -661,6 +710,377 @@ __global__ void finish_status(int* pstat, int64_t n, int max_it, int* iters_out)
     pstat[l] = s;
     if (iters_out) iters_out[l] = s;
   }
+}
+
+// ---- persistent CG ----------------------------------------------------------------
+// The whole CG of a batch in one cooperative launch. Every CTA takes a strided
+// share of the product tiles, then a strided share of the points (one warp per
+// point), with a grid barrier between the two; the checks of the launch-per-step
+// loop (FP64 residuals of the mixed CG, the count of iterating points) come
+// every `chunk` iterations as there. The per-point and per-tile arithmetic is
+// the same code in the same order, so the results are identical; what goes are
+// two launches per iteration and the host round trip per check. The grid holds
+// no more CTAs than fit on the device at once (a cooperative launch checks
+// it), so a CTA waiting at a barrier waits only for CTAs that are running.
+struct PcgCtl {
+  unsigned* bar;   // [0] arrivals, [1] generation; both zero at launch
+  int* abort;      // set when a barrier or copy wait runs out; zero at launch
+  int* act;        // [4] iterating-point counts, a ring over the checks; zero at launch
+  int* iters;      // iterations run
+  int* err;        // bit 0: a bulk copy of a basis did not complete within the wait limit
+  unsigned long long* cyc;   // [6] SM cycles summed over the CTAs: tile products, barrier after them,
+                             // updates, barrier after them, FP64 check products, the rest of the checks
+};
+constexpr int kPcgUnits = 64;                                // units (subdomains + Stokes) it handles
+constexpr unsigned long long kBarrierNs = 1000000000ull;     // 1 s, far above any CG step
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid barrier, called by every thread of every CTA: one arrival counter (an
+// acquire-release add by each CTA's thread 0 after the CTA's barrier), the
+// release by a generation number (counted per CTA in gen) that the last
+// arrival stores with release semantics and the others load with acquire
+// semantics. A wait ends after kBarrierNs, or when another CTA has set abort.
+// False, for the whole CTA, once abort is set.
+__device__ bool grid_sync(const PcgCtl& c, unsigned& gen) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned target = gen + 1;
+    if (atom_add_acq_rel(&c.bar[0], 1u) == gridDim.x - 1) {
+      atomicExch(&c.bar[0], 0u);
+      st_release(&c.bar[1], target);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (ld_acquire(&c.bar[1]) != target) {
+        if (*((volatile int*)c.abort)) { ok = 0; break; }
+        if (global_ns() - t0 > kBarrierNs) {
+          atomicExch(c.abort, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(20);
+      }
+    }
+    if (*((volatile int*)c.abort)) ok = 0;
+    gen = target;
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// Tile f of the flat list: unit u with tpre[u] <= f < tpre[u + 1], tile t.
+__device__ __forceinline__ void tile_locate(const int* tpre, int f, int& u, int& t) {
+  u = 0;
+  while (tpre[u + 1] <= f) ++u;
+  t = f - tpre[u];
+}
+
+// One product step over all tiles: CTA b takes the flat tiles b, b + G, ...
+// With two buffers (dbl) the basis of its next tile is in flight while one
+// tile is applied; with one (Ph[0] == Ph[1]) the next copy starts once the
+// tile is done. False (block-uniform) when a copy did not complete; the
+// copies still in flight get a bounded wait first.
+template <typename T>
+__device__ bool tiles_phase(const IfaceArgs& a, const double* __restrict__ vin, int sel, const int* tpre, int nu,
+                            T* const (&Ph)[2], bool dbl, T* Pv, TileScratch& ts, uint64_t* tbar, uint32_t (&par)[2],
+                            const PcgCtl& c) {
+  const int ntot = tpre[nu];
+  int f = blockIdx.x;
+  if (f >= ntot) return true;
+  auto issue = [&](int ff, int buf) {
+    int u, t;
+    tile_locate(tpre, ff, u, t);
+    int R;
+    const T* ph = unit_phi_t<T>(a, u, a.tiles[3 * ((int64_t)u * a.max_tiles + t)], R);
+    phi_load(Ph[buf], ph, (uint32_t)((R * R * (int)sizeof(T) + 15) & ~15), &tbar[buf]);
+  };
+  if (threadIdx.x == 0) issue(f, 0);
+  int cur = 0;
+  for (; f < ntot; f += gridDim.x, cur ^= 1) {
+    const int fn = f + gridDim.x;
+    // with two buffers the other one was released at the end of the last tile
+    if (dbl && threadIdx.x == 0 && fn < ntot) issue(fn, cur ^ 1);
+    int u, t;
+    tile_locate(tpre, f, u, t);
+    const int* tl = a.tiles + 3 * ((int64_t)u * a.max_tiles + t);
+    const int q0 = tl[1], cntp = tl[2];
+    const int* pts = a.grp_pts + (int64_t)u * a.pts_ld + q0;
+    const int R = u == a.ns ? a.Rs : a.subs[u].R;
+    const int nsel = tile_select(a, pts, cntp, sel, ts);
+    if (nsel > 0) tile_gather<T>(a, vin, pts, u, R, nsel, ts, Pv);
+    const bool ok = phi_wait(&tbar[cur], par[cur]);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(c.err, 1);
+        atomicExch(c.abort, 1);
+        phi_wait(&tbar[cur], par[cur]);
+        if (dbl && fn < ntot) phi_wait(&tbar[cur ^ 1], par[cur ^ 1]);
+      }
+      __syncthreads();
+      return false;
+    }
+    par[cur] ^= 1u;
+    if (nsel > 0) tile_product<T>(a, u, R, nsel, ts, Ph[cur], Pv);
+    __syncthreads();   // Ph[cur], Pv and ts are free again
+    if (!dbl && threadIdx.x == 0 && fn < ntot) issue(fn, cur ^ 1);
+  }
+  return true;
+}
+
+// Resident tiles of the mixed CG's FP32 products: a CTA's tiles stay in its
+// shared memory for the whole solve (the transposed bases, the point lists
+// and the units' global DOFs), so that an iteration is one selection pass,
+// one gather pass and one product pass over all of them. The products are
+// 4 x 4 register tiles fed by float4 loads; every entry accumulates
+// Phi[r][j] v_j over j in ascending order from zero, as tile_product does,
+// so the results are the same.
+constexpr int kResMax = 8;     // resident tiles per CTA (capacity of ResTiles)
+constexpr int kResMax3 = 3;    // the resident tiles a CTA is given (shared memory for two CTAs per SM)
+constexpr int kPvS = 36;       // row stride of a resident gathered block (floats)
+
+// Shared-memory layout of the persistent CG (byte offsets into the dynamic
+// allocation), set by the host.
+struct PcgLayout {
+  int phi_bytes;   // per streaming basis buffer (an FP64 basis of R_max^2)
+  int nbuf;        // streaming buffers: 2 (prefetch) or 1
+  int pv_off;      // streaming gathered vectors, R_max x (kTG + 1) doubles
+  int stage_off;   // FP32 stage of n_lambda entries per warp (block preconditioner)
+  int resident;    // 1: the iteration products use resident tiles
+  int r4;          // R_max rounded up to a multiple of 4
+  int rphi_off;    // kResMax-capped m_max x r4 x r4 floats: transposed bases
+  int rpv_off;     // m_max x r4 x kPvS floats: gathered vectors
+  int rpts_off;    // m_max x kTG ints: the tile's points
+  int rspt_off;    // m_max x kTG int64: the selected points
+  int rgd_off;     // m_max x r4 ints: the unit's global DOFs
+  const int* part; // resident: CTA b holds the flat tiles [part[b], part[b + 1])
+};
+
+struct ResTiles {
+  int m;                   // tiles of this CTA
+  int u[kResMax], R[kResMax], cnt[kResMax], nsel[kResMax];
+  float* phiT;             // [m][r4][r4]
+  float* pv;               // [m][r4][kPvS]
+  int* pts;                // [m][kTG]
+  int64_t* spt;            // [m][kTG]
+  int* gd;                 // [m][r4]
+  int r4;
+};
+
+// Once per launch: this CTA's tiles [part[b], part[b + 1]) into shared
+// memory (a contiguous range of the flat tile list, balanced by cost on the
+// host; at most kResMax tiles).
+__device__ void resident_setup(const IfaceArgs& a, const int* tpre, int nu, const int* part, ResTiles& rt) {
+  const int ntot = tpre[nu];
+  const int f0 = min(part[blockIdx.x], ntot), f1 = min(part[blockIdx.x + 1], ntot);
+  const int m = max(0, min(f1 - f0, kResMax));
+  if (threadIdx.x == 0) rt.m = m;
+  for (int j = 0; j < m; ++j) {
+    const int f = f0 + j;
+    int u, t;
+    tile_locate(tpre, f, u, t);
+    const int* tl = a.tiles + 3 * ((int64_t)u * a.max_tiles + t);
+    const int k = tl[0], q0 = tl[1], cnt = tl[2];
+    int R;
+    const float* ph = unit_phi_t<float>(a, u, k, R);
+    const int64_t* gd = u == a.ns ? a.sgdof : a.gdof + a.subs[u].gdof_off;
+    const int* pts = a.grp_pts + (int64_t)u * a.pts_ld + q0;
+    if (threadIdx.x == 0) { rt.u[j] = u; rt.R[j] = R; rt.cnt[j] = cnt; }
+    const int r4 = rt.r4;
+    float* phT = rt.phiT + (int64_t)j * r4 * r4;
+    for (int e = threadIdx.x; e < r4 * r4; e += blockDim.x) {
+      const int jj = e / r4, r = e - jj * r4;   // phT[jj][r] = Phi[r][jj]
+      phT[e] = (jj < R && r < R) ? ph[r * R + jj] : 0.f;
+    }
+    for (int q = threadIdx.x; q < kTG; q += blockDim.x) rt.pts[j * kTG + q] = q < cnt ? pts[q] : 0;
+    for (int i = threadIdx.x; i < r4; i += blockDim.x) rt.gd[j * r4 + i] = i < R ? (int)gd[i] : 0;
+  }
+  __syncthreads();
+}
+
+// One FP32 product step over the resident tiles (selection: iterating points).
+__device__ void resident_products(const IfaceArgs& a, ResTiles& rt) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  const int m = rt.m, r4 = rt.r4;
+  for (int j = warp; j < m; j += wpb) {   // one warp per tile (kTG == 32)
+    const int cnt = rt.cnt[j];
+    const int pt = rt.pts[j * kTG + lane];
+    const bool act = lane < cnt && a.pstat[pt] == 0;
+    const unsigned mask = __ballot_sync(0xffffffffu, act);
+    if (act) rt.spt[j * kTG + __popc(mask & ((1u << lane) - 1u))] = pt;
+    if (lane == 0) rt.nsel[j] = __popc(mask);
+  }
+  __syncthreads();
+  for (int j = 0; j < m; ++j) {
+    const int nsel = rt.nsel[j], R = rt.R[j], nsel4 = (nsel + 3) & ~3;
+    const int64_t* spt = rt.spt + j * kTG;
+    const int* gd = rt.gd + j * r4;
+    float* pv = rt.pv + (int64_t)j * r4 * kPvS;
+    for (int e = threadIdx.x; e < nsel4 * R; e += blockDim.x) {
+      const int q = e / R, i = e - q * R;
+      float v = 0.f;
+      if (q < nsel) v = from_f64<float>(a.p[spt[q] * a.n_lambda + gd[i]]);
+      pv[i * kPvS + q] = v;
+    }
+  }
+  __syncthreads();
+  int total = 0;
+  for (int j = 0; j < m; ++j) total += (((rt.R[j] + 3) >> 2) * ((rt.nsel[j] + 3) >> 2));
+  for (int w = threadIdx.x; w < total; w += blockDim.x) {
+    int j = 0, w0 = w;
+    for (;;) {
+      const int nj = ((rt.R[j] + 3) >> 2) * ((rt.nsel[j] + 3) >> 2);
+      if (w0 < nj) break;
+      w0 -= nj;
+      ++j;
+    }
+    const int R = rt.R[j], nsel = rt.nsel[j], ncg = (nsel + 3) >> 2;
+    const int r0 = (w0 / ncg) * 4, c0 = (w0 % ncg) * 4;
+    const float* phT = rt.phiT + (int64_t)j * r4 * r4 + r0;
+    const float* pv = rt.pv + (int64_t)j * r4 * kPvS + c0;
+    float acc[4][4] = {};
+    for (int jj = 0; jj < R; ++jj) {
+      const float4 f = *reinterpret_cast<const float4*>(phT + jj * r4);
+      const float4 v = *reinterpret_cast<const float4*>(pv + jj * kPvS);
+      const float fr[4] = {f.x, f.y, f.z, f.w}, vq[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int ra = 0; ra < 4; ++ra)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[ra][q] = fmaf(fr[ra], vq[q], acc[ra][q]);
+    }
+    const int64_t* spt = rt.spt + j * kTG;
+    const int64_t yb = a.ybase[rt.u[j]];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (c0 + q >= nsel) break;
+      double* y = a.Y + spt[c0 + q] * a.NY + yb;
+#pragma unroll
+      for (int ra = 0; ra < 4; ++ra)
+        if (r0 + ra < R) y[r0 + ra] = to_f64(acc[ra][q]);
+    }
+  }
+}
+
+// Grid of at most the co-resident CTAs of 256 threads; dynamic shared memory
+// as PcgLayout sets it. T is the product type of the iterations (float: the
+// mixed CG, whose checks take FP64 products; double: the FP64 CG).
+template <typename T, bool kRegs>
+__global__ void __launch_bounds__(256) cg_persistent_kernel(IfaceArgs a, PcgCtl c, double rtol, int max_it,
+                                                            int chunk, double replace_ratio, double pause_ratio,
+                                                            PcgLayout L) {
+  extern __shared__ __align__(16) unsigned char pcg_raw[];
+  __shared__ __align__(8) uint64_t tbar[2];
+  __shared__ TileScratch ts;
+  __shared__ int tpre[kPcgUnits + 1];
+  __shared__ ResTiles rt;
+  constexpr bool kMixed = sizeof(T) == 4;
+  const bool resident = kMixed && L.resident;
+  const int nu = a.ns + 1;
+  unsigned char* buf0 = pcg_raw;
+  unsigned char* buf1 = pcg_raw + (L.nbuf == 2 ? L.phi_bytes : 0);
+  unsigned char* pvb = pcg_raw + L.pv_off;
+  float* stage_all = reinterpret_cast<float*>(pcg_raw + L.stage_off);
+  T* const PhT[2] = {reinterpret_cast<T*>(buf0), reinterpret_cast<T*>(buf1)};
+  double* const PhD[2] = {reinterpret_cast<double*>(buf0), reinterpret_cast<double*>(buf1)};
+  const bool dbl = L.nbuf == 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  float* stage = stage_all + warp * a.n_lambda;
+  if (threadIdx.x == 0) {
+    mbar_init1(&tbar[0]);
+    mbar_init1(&tbar[1]);
+    tpre[0] = 0;
+    for (int u = 0; u < nu; ++u) tpre[u + 1] = tpre[u] + min(a.n_tiles[u], a.max_tiles);
+    rt.r4 = L.r4;
+    rt.phiT = reinterpret_cast<float*>(pcg_raw + L.rphi_off);
+    rt.pv = reinterpret_cast<float*>(pcg_raw + L.rpv_off);
+    rt.pts = reinterpret_cast<int*>(pcg_raw + L.rpts_off);
+    rt.spt = reinterpret_cast<int64_t*>(pcg_raw + L.rspt_off);
+    rt.gd = reinterpret_cast<int*>(pcg_raw + L.rgd_off);
+  }
+  __syncthreads();
+  if (resident) resident_setup(a, tpre, nu, L.part, rt);
+  uint32_t par[2] = {0u, 0u};
+  unsigned gen = 0;
+  int it = 0, chk = 0;
+  bool ok = true;
+  // thread 0's clock between the steps
+  long long cyc[6] = {0, 0, 0, 0, 0, 0}, t_last = clock64();
+  auto mark = [&](int k) {
+    if (threadIdx.x == 0) {
+      const long long t = clock64();
+      cyc[k] += t - t_last;
+      t_last = t;
+    }
+  };
+  while (it < max_it) {
+    for (int q = 0; q < chunk && it < max_it; ++q, ++it) {
+      if (resident) {
+        resident_products(a, rt);
+        ok = true;
+      } else {
+        ok = tiles_phase<T>(a, a.p, 0, tpre, nu, PhT, dbl, reinterpret_cast<T*>(pvb), ts, tbar, par, c);
+      }
+      mark(0);
+      ok = grid_sync(c, gen) && ok;
+      mark(1);
+      if (!ok) break;
+      // point l to CTA l mod G: every CTA (and SM) gets its share of the FP64 updates
+      for (int64_t l = (int64_t)warp * gridDim.x + blockIdx.x; l < a.n_pts; l += (int64_t)gridDim.x * wpb)
+        update_point<kRegs>(a, l, lane, stage, it, rtol, kMixed ? 1 : 0, replace_ratio, pause_ratio);
+      mark(2);
+      ok = grid_sync(c, gen);
+      mark(3);
+      if (!ok) break;
+    }
+    if (!ok) break;
+    if (kMixed) {   // FP64 residuals of the points that asked for one
+      ok = tiles_phase<double>(a, a.lam, 1, tpre, nu, PhD, dbl, reinterpret_cast<double*>(pvb), ts, tbar, par, c);
+      mark(4);
+      ok = grid_sync(c, gen) && ok;
+      if (!ok) break;
+      for (int64_t l = (int64_t)warp * gridDim.x + blockIdx.x; l < a.n_pts; l += (int64_t)gridDim.x * wpb)
+        reliable_point(a, l, lane, stage, rtol, it);
+      ok = grid_sync(c, gen);
+      if (!ok) break;
+    }
+    // iterating points; the slot two checks ahead is cleared for reuse (every
+    // CTA has read it: it has passed barriers since)
+    int* slot = c.act + (chk & 3);
+    if (blockIdx.x == 0 && threadIdx.x == 0) c.act[(chk + 2) & 3] = 0;
+    int cnt = 0;
+    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < a.n_pts; l += (int64_t)gridDim.x * blockDim.x)
+      cnt += a.pstat[l] == 0;
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0 && cnt) atomicAdd(slot, cnt);
+    ok = grid_sync(c, gen);
+    mark(5);
+    if (!ok) break;
+    ++chk;
+    if (*((volatile int*)slot) == 0) break;
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 6; ++k) atomicAdd(&c.cyc[k], (unsigned long long)cyc[k]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *c.iters = it;
 }
 
 // ---- moments ---------------------------------------------------------------------
@@ -1540,13 +1960,139 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   const int chunk = c->opt_cg_chunk;
   const bool mixed = krylov == SFB_CG_MIXED;
   const double replace_ratio = c->opt_cg_replace, pause_ratio = 0.1 * c->opt_cg_replace;
+  const bool regs = c->n_lambda <= 32 * kUpd;
+  // the persistent CG: one cooperative launch when the device supports it and
+  // its shared memory fits (for the mixed CG: when its FP32 tiles can stay
+  // resident); otherwise one launch per step below
+  bool persistent = false;
+  if (c->opt_cg_persistent && nu <= kPcgUnits) {
+    int dev = 0, coop = 0, n_sm = 0, smem_max = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const void* fn = mixed ? (regs ? (const void*)cg_persistent_kernel<float, true> : (const void*)cg_persistent_kernel<float, false>)
+                           : (regs ? (const void*)cg_persistent_kernel<double, true> : (const void*)cg_persistent_kernel<double, false>);
+    // the flat tile list and each tile's cost (4 x 4 product items times R,
+    // plus its gather), for the resident partition of the mixed CG
+    int ntot = 0;
+    std::vector<double> cost;
+    if (mixed && coop) {
+      std::vector<int> h_nt((size_t)nu), h_tl((size_t)nu * c->max_tiles * 3);
+      CK(cudaMemcpyAsync(h_nt.data(), d.n_tiles, sizeof(int) * nu, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(h_tl.data(), d.tiles, sizeof(int) * h_tl.size(), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int u = 0; u < nu; ++u) {
+        const int R = u == ns ? (int)c->stokes.dofs.size() : (int)c->subs[(size_t)u].dofs.size();
+        const int R4 = (R + 3) & ~3;
+        for (int t = 0; t < std::min(h_nt[(size_t)u], c->max_tiles); ++t) {
+          const int cnt = h_tl[3 * ((size_t)u * c->max_tiles + t) + 2];
+          const int c4 = (cnt + 3) & ~3;
+          cost.push_back((double)R4 * c4 * R / 16.0 + (double)R * cnt / 8.0 + 64.0);
+        }
+      }
+      ntot = (int)cost.size();
+    }
+    // contiguous ranges of at most cap tiles for grid CTAs, the largest range
+    // cost as small as the greedy cut allows (bisection on the bound)
+    auto partition = [&](int grid, int cap, std::vector<int>& starts) -> bool {
+      auto cut = [&](double bound) -> bool {
+        starts.assign(1, 0);
+        double acc = 0.0;
+        int n = 0;
+        for (int j = 0; j < ntot; ++j) {
+          if (n > 0 && (acc + cost[(size_t)j] > bound || n == cap)) {
+            starts.push_back(j);
+            if ((int)starts.size() > grid) return false;
+            acc = 0.0;
+            n = 0;
+          }
+          acc += cost[(size_t)j];
+          ++n;
+        }
+        while ((int)starts.size() <= grid) starts.push_back(ntot);
+        return true;
+      };
+      double lo = 0.0, hi = 0.0;
+      for (double v : cost) { lo = std::max(lo, v); hi += v; }
+      if (!cut(hi)) return false;
+      for (int k = 0; k < 40; ++k) {
+        const double mid = 0.5 * (lo + hi);
+        if (cut(mid)) hi = mid; else lo = mid;
+      }
+      return cut(hi);
+    };
+    auto layout = [&](int grid, bool res, int nbuf, PcgLayout& L) -> size_t {
+      size_t off = 0;
+      auto put = [&](size_t bytes) {
+        off = (off + 15) & ~(size_t)15;
+        const size_t o = off;
+        off += bytes;
+        return (int)o;
+      };
+      L.phi_bytes = (int)((sizeof(double) * (size_t)maxR * maxR + 15) & ~(size_t)15);
+      L.nbuf = nbuf;
+      put((size_t)nbuf * L.phi_bytes);
+      L.r4 = (maxR + 3) & ~3;
+      L.resident = res ? 1 : 0;
+      L.part = d.pcg_part;
+      const int m = res ? kResMax3 : 0;
+      const size_t pv64 = sizeof(double) * (size_t)maxR * (kTG + 1);
+      const size_t rpv = sizeof(float) * (size_t)m * L.r4 * kPvS;
+      L.rphi_off = put(sizeof(float) * (size_t)m * L.r4 * L.r4);
+      L.rpv_off = put(std::max(rpv, pv64));
+      L.pv_off = L.rpv_off;   // the streaming vectors reuse the resident ones (never live at once)
+      L.rpts_off = put(sizeof(int) * (size_t)m * kTG);
+      L.rspt_off = put(sizeof(int64_t) * (size_t)m * kTG);
+      L.rgd_off = put(sizeof(int) * (size_t)m * L.r4);
+      L.stage_off = put(stg);
+      return off;
+    };
+    // candidates, best first: CTAs per SM, resident tiles, streaming buffers
+    const int cand[7][3] = {{2, 1, 2}, {2, 1, 1}, {1, 1, 2}, {1, 1, 1}, {2, 0, 2}, {1, 0, 2}, {1, 0, 1}};
+    for (int ci = 0; ci < 7 && coop && !persistent; ++ci) {
+      const int per = cand[ci][0], nbuf = cand[ci][2];
+      const bool res = cand[ci][1] == 1;
+      if (res && !(mixed && ntot > 0)) continue;
+      // the mixed CG's streaming form measured slower than a launch per step
+      if (mixed && !res) continue;
+      const int grid = n_sm * per;
+      std::vector<int>& starts = c->pcg_starts;
+      if (res && (grid > kPcgMaxGrid || !partition(grid, kResMax3, starts))) continue;
+      PcgLayout L;
+      const size_t smp = layout(grid, res, nbuf, L);
+      if (smp + 4096 > (size_t)smem_max) continue;
+      CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
+      int per_sm = 0;
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smp));
+      if (per_sm < per) continue;
+      PcgCtl ctl;
+      ctl.bar = reinterpret_cast<unsigned*>(d.active + 4);
+      ctl.abort = d.active + 6;
+      ctl.iters = d.active + 7;
+      ctl.act = d.active + 8;
+      ctl.err = d.active + 2;
+      ctl.cyc = reinterpret_cast<unsigned long long*>(d.active + 16);
+      CK(cudaMemsetAsync(d.active + 4, 0, sizeof(int) * 28, st));
+      if (res)
+        CK(cudaMemcpyAsync(d.pcg_part, starts.data(), sizeof(int) * (grid + 1), cudaMemcpyHostToDevice, st));
+      c->pcg_grid = grid;
+      c->pcg_mode = (res ? 1 : 0) + 2 * (nbuf - 1);
+      double rt_ = rtol, rr_ = replace_ratio, pr_ = pause_ratio;
+      int mi = max_it, ch = chunk;
+      void* args[] = {&a, &ctl, &rt_, &mi, &ch, &rr_, &pr_, &L};
+      CK(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, smp, st));
+      ++c->launches;
+      persistent = true;
+    }
+  }
   int it = 0;
-  for (; it < max_it;) {
+  for (; it < max_it && !persistent;) {
     for (int q = 0; q < chunk && it < max_it; ++q, ++it) {
       if (mixed) matvec_kernel<float><<<mgrid, 256, smv32, st>>>(a, d.p, 0, d.active + 2);
       else matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.p, 0, d.active + 2);
       ++c->launches;
-      if (c->n_lambda <= 32 * kUpd)
+      if (regs)
         update_kernel<true><<<ublocks, 32 * warps_per_block, stg, st>>>(a, it, rtol, mixed ? 1 : 0, replace_ratio,
                                                                       pause_ratio);
       else
@@ -1570,7 +2116,6 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
     CK(cudaStreamSynchronize(st));
     if (h_active == 0) break;
   }
-  c->cg_iters_run = it;
   CK(cudaEventRecord(c->ev[2], st));
   finish_status<<<std::min(1024, (int)((n_pts + 255) / 256)), 256, 0, st>>>(d.pstat, n_pts, max_it, nullptr);
   ++c->launches;
@@ -1578,12 +2123,23 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   CK(cudaMemsetAsync(d.active + 1, 0, sizeof(int), st));
   count_failed<<<std::min(1024, (int)((n_pts + 255) / 256)), 256, 0, st>>>(d.pstat, n_pts, d.active + 1);
   ++c->launches;
-  int h_flags[4] = {0, 0, 0, 0};
-  CK(cudaMemcpyAsync(h_flags, d.active, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+  int h_flags[32] = {};
+  CK(cudaMemcpyAsync(h_flags, d.active, sizeof(int) * 32, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  for (int k = 0; k < 6; ++k) {
+    unsigned long long v;
+    std::memcpy(&v, h_flags + 16 + 2 * k, sizeof(v));
+    c->pcg_cycles[k] = persistent ? (double)v / c->pcg_grid : 0.0;
+  }
   *n_failed = h_flags[1];
+  c->cg_iters_run = persistent ? h_flags[7] : it;
+  c->cg_persistent_run = persistent;
   if (h_flags[2]) {
     c->err = "interface solve: a bulk copy of a basis did not complete within the wait limit";
+    return SFB_ERR_TIMEOUT;
+  }
+  if (persistent && h_flags[6]) {
+    c->err = "interface solve: a grid barrier of the persistent CG did not complete within the wait limit";
     return SFB_ERR_TIMEOUT;
   }
   return SFB_OK;

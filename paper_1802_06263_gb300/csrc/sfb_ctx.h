@@ -116,6 +116,7 @@ struct Dev {
   int* rflag = nullptr;
   int* pstat = nullptr;       // per point: iterations (>0 converged, <0 active/failed)
   int* active = nullptr;
+  int* pcg_part = nullptr;    // persistent CG: per-CTA ranges of resident tiles
   int64_t* s_gdof = nullptr;  // Stokes local -> global mortar DOF
   int64_t* ybase = nullptr;   // per unit offset into a point's Y row
   int* dim_off = nullptr;     // per region first stochastic dimension
@@ -189,12 +190,18 @@ struct sfb_ctx {
   double opt_refine_tol = 1e-10;
   int opt_refine_max = 8;
   int opt_cg_chunk = 8;
+  int opt_cg_persistent = 1;    // interface CG in one cooperative launch (0: one launch per step)
   int opt_cg_precond = 1;       // interface CG preconditioner: 0 none, 1 Jacobi, 2 interface blocks
   double opt_cg_replace = 0.1;  // mixed CG: FP64 residual once the recursive one drops by this factor
   double opt_big_factor = 1.0;   // groups above this many times (R+1) points use coefficient moments
   // device-time phase markers of the last interface solve (CUDA events)
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int cg_iters_run = 0;
+  bool cg_persistent_run = false;
+  int pcg_grid = 1;
+  std::vector<int> pcg_starts;   // host copy of the last resident partition
+  int pcg_mode = 0;   // last persistent CG: bit 0 resident tiles, bit 1 two streaming buffers
+  double pcg_cycles[6] = {0, 0, 0, 0, 0, 0};   // per CTA, last persistent CG
   ~sfb_ctx() {
     for (cudaEvent_t e : ev)
       if (e) cudaEventDestroy(e);

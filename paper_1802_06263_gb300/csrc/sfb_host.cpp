@@ -265,7 +265,8 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   d.dof_if = cv.take<int>((size_t)std::max<int64_t>(c->n_lambda, 1));
   d.rflag = cv.take<int>(P);
   d.pstat = cv.take<int>(P);
-  d.active = cv.take<int>(4);
+  d.active = cv.take<int>(32);   // flags and counts; [4, 32) the persistent CG's barrier, counters, clocks
+  d.pcg_part = cv.take<int>(kPcgMaxGrid + 1);
   d.s_gdof = cv.take<int64_t>(std::max(Rs, 1));
   d.ybase = cv.take<int64_t>(nu + 1);
   d.dim_off = cv.take<int>(ns);
@@ -916,6 +917,12 @@ sfb_status sfb_solve_timings(sfb_ctx* c, double* ms_out, int32_t* cg_iterations)
   return SFB_OK;
 }
 
+sfb_status sfb_cg_phase_cycles(const sfb_ctx* c, double* cycles_out) {
+  if (!c || !cycles_out) return SFB_ERR_ARG;
+  for (int k = 0; k < 6; ++k) cycles_out[k] = c->pcg_cycles[k];
+  return SFB_OK;
+}
+
 sfb_status sfb_set_option(sfb_ctx* c, const char* name, double value) {
   if (!c || !name) return SFB_ERR_ARG;
   const std::string n(name);
@@ -934,6 +941,9 @@ sfb_status sfb_set_option(sfb_ctx* c, const char* name, double value) {
   } else if (n == "cg_precond") {
     if (!(value == 0 || value == 1 || value == 2)) return fail(c, SFB_ERR_ARG, "cg_precond must be 0, 1 or 2");
     c->opt_cg_precond = (int)value;
+  } else if (n == "cg_persistent") {
+    if (!(value == 0 || value == 1)) return fail(c, SFB_ERR_ARG, "cg_persistent must be 0 or 1");
+    c->opt_cg_persistent = (int)value;
   } else if (n == "cg_replace_ratio") {
     if (!(value >= 1e-4 && value < 1)) return fail(c, SFB_ERR_ARG, "cg_replace_ratio must lie in [1e-4, 1)");
     c->opt_cg_replace = value;

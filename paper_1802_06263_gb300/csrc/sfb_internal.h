@@ -85,6 +85,10 @@ constexpr int kCycSlots = 16;
 // identity-padded to a multiple of it.
 constexpr int kPanel = 16;
 
+// Largest grid of the persistent interface CG with resident tiles (the
+// per-CTA tile ranges live in the workspace).
+constexpr int kPcgMaxGrid = 2048;
+
 // Point chunks of the Stokes coefficient moments (partials summed in order).
 constexpr int kStokesChunks = 32;
 

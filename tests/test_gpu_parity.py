@@ -128,3 +128,35 @@ def test_cg_preconditioners_reach_the_same_solution(precond, krylov):
         s.set_option("cg_precond", precond + 1)
         _, it_next, _ = s.solve_host(y, wt, rtol=1e-13, max_it=5000, krylov=krylov)
         assert it_next.max() < it.max()
+
+
+FIELD_NAMES = ("darcy_p", "darcy_flux", "stokes_u", "stokes_p")
+
+
+@pytest.mark.parametrize("key,krylov,precond", [("medium", 0, 0), ("medium", 0, 1), ("medium", 0, 2),
+                                                ("medium", 1, 0), ("medium", 1, 1), ("medium", 1, 2),
+                                                ("ragged", 0, 1), ("ragged", 1, 1), ("tiny", 1, 2)])
+def test_persistent_cg_matches_per_step_launches(key, krylov, precond):
+    """The CG in one cooperative launch runs the same per-point and per-tile
+    arithmetic in the same order as the loop of one launch per step: the
+    mortar solutions, iteration counts and moments are bit-identical, with a
+    handful of launches instead of two per iteration."""
+    p, y, wt, lams, mom = oracle_case(key)
+    s, _ = _solver(key, krylov)
+    s.set_option("cg_precond", precond)
+    res = {}
+    for pers in (0, 1):
+        s.set_option("cg_persistent", pers)
+        s.moments_reset()
+        n0 = s.launch_count()
+        lam, it, rc = s.solve_host(y, wt, rtol=1e-12, max_it=5000, krylov=krylov)
+        n_launch = s.launch_count() - n0
+        res[pers] = (lam, it, rc, n_launch, s.solve_timings()["cg_iterations"],
+                     {f: s.moments(f) for f in FIELD_NAMES})
+    (l0, i0, r0, n0, c0, m0), (l1, i1, r1, n1, c1, m1) = res[0], res[1]
+    assert r0 == 0 and r1 == 0 and np.all(i0 > 0)
+    assert np.array_equal(l0, l1) and np.array_equal(i0, i1) and c0 == c1
+    for f in FIELD_NAMES:
+        assert np.array_equal(m0[f][0], m1[f][0]) and np.array_equal(m0[f][1], m1[f][1]), f
+    assert rel(l1, lams) < 1e-9
+    assert n0 > 2 * c0 and n1 < 30, (n0, n1, c0)
