@@ -261,6 +261,31 @@ def run_ours(args):
     rl_mixed = alu_roofline(st_mixed["flops_fp32"], st_mixed["flops_fp64"], k_mixed * 1e-3)
     rl_fp64 = alu_roofline(st_fp64["flops_fp32"], st_fp64["flops_fp64"], k_fp64 * 1e-3)
     traffic = profiled_traffic("basis.cu", "basis_kernel_mixed_precision.md")
+    # the other steps of the mixed step, from algorithmic counts:
+    # a11 (CG): 2 sum_u R_u^2 FP32 flops per point and iteration for the
+    # products, 10 FP64 flops per mortar DOF for the update (the FP64 check
+    # products are left out, so the achieved rate is a lower bound);
+    # a12 (Darcy moments): every item's field responses X (8 n_c (R+1) bytes)
+    # read once
+    r_units = [len(s.subdomain_dofs(i)) for i in range(s.n_darcy)] + [len(s.subdomain_dofs(-1))]
+    sum_r2 = float(sum(r * r for r in r_units))
+    it_sum = float(np.abs(iters).sum())
+    cg_s = mixed_phases["cg_ms"] * 1e-3
+    rl_cg = alu_roofline(it_sum * 2.0 * sum_r2, it_sum * 10.0 * s.n_lambda, cg_s)
+    x_bytes = 0.0
+    for i in range(s.n_darcy):
+        nx_, ny_ = wl["darcy_grid"][i]
+        x_bytes += 8.0 * nx_ * ny_ * (r_units[i] + 1) * len(s.local_points(i))
+    mom_s = mixed_phases["darcy_moments_ms"] * 1e-3
+    hbm = peaks.get("hbm_gbs") if peaks else None
+    hbm = hbm or 6800.0
+    steps_rl = {
+        "a11_interface_cg": dict({"bound": "alu", "unit": "TFLOP/s", "ms": cg_s * 1e3,
+                                  "note": "lower bound: FP64 check products not counted"}, **rl_cg),
+        "a12_darcy_moments": {"bound": "hbm", "unit": "GB/s", "ms": mom_s * 1e3, "bytes": x_bytes,
+                              "achieved": x_bytes / mom_s / 1e9, "peak": hbm, "frac": x_bytes / mom_s / 1e9 / hbm,
+                              "note": "the large groups' quadratic forms make it FP64-bound in fact"},
+    }
     out = {
         "metric": METRIC, "value": world * n_pts / (t_mixed * 1e-3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_mixed,
@@ -298,6 +323,7 @@ def run_ours(args):
                                          "FP32+FP64 mix at the binding pipe's rate"}, **rl_mixed),
         "roofline_fp64_form": dict({"bound": "alu", "kernel": "basis_kernel<double>", "unit": "TFLOP/s",
                                     "flops_fp64": st_fp64["flops_fp64"], "kernel_ms": k_fp64}, **rl_fp64),
+        "roofline_steps": steps_rl,
         "peaks_source": "MEASURED_PEAKS.json (HBM, bf16 only)" if peaks else "fallback",
         "gpu_launches": int(launches),
         "gpu_launches_per_step": launches / args.steps,

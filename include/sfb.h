@@ -280,6 +280,13 @@ sfb_status sfb_build_basis_item_noalloc(sfb_ctx* ctx, int32_t sub, int32_t k, in
  *                    FP64 residual at the next check once the recursive one
  *                    has dropped by this factor since the last replacement,
  *                    and the point pauses at a tenth of it (0.1);
+ *   "moments_double_float"  after a mixed-form basis build: 1 runs the
+ *                    moment contractions that reuse a field response for four
+ *                    or more points (recovery of 4-8 point sub-tiles, the large
+ *                    groups' quadratic forms) in double-float, an FP32 hi/lo
+ *                    pair with error-free products and sums (about 1e-14
+ *                    relative), on the FP32 pipe; 0 keeps them in FP64. The
+ *                    FP64 form always uses FP64 (1);
  *   "moments_group_factor"  groups of more than factor * (R+1) points enter
  *                    the moments through their coefficient second moments,
  *                    smaller ones point by point; 0 = always point by point (1).

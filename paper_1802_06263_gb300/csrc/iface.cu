@@ -1111,7 +1111,45 @@ struct MomArgs {
   const int64_t* loc_off;   // per subdomain offset into the group arrays
   double* gmom;             // per group: W | cbar[C] | m[C] | M[C][C]
   int64_t gmom_stride;
+  int df;                   // 1: the contractions in double-float (mixed form), 0: FP64
 };
+
+// Double-float arithmetic: a value as an FP32 pair hi + lo (about 48
+// significant bits), with the error-free product by FMA and Knuth's
+// error-free sum, so that the mixed form's moment contractions run on the
+// FP32 pipe (FP64 issues at 1/64 of its rate here). The explicit _rn
+// intrinsics keep the compiler from contracting the error terms.
+__device__ __forceinline__ void df_split(double x, float& h, float& l) {
+  h = f64_to_f32_bits(x);
+  l = f64_to_f32_bits(x - f32_to_f64_bits(h));
+}
+// (sh, sl) += (ah + al)(bh + bl), the al bl term dropped
+__device__ __forceinline__ void df_mac(float ah, float al, float bh, float bl, float& sh, float& sl) {
+  const float p = __fmul_rn(ah, bh);
+  const float pe = __fmaf_rn(ah, bh, -p);
+  const float x = __fmaf_rn(ah, bl, __fmul_rn(al, bh));
+  const float sum = __fadd_rn(sh, p);
+  const float v = __fsub_rn(sum, sh);
+  const float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(sum, v)), __fsub_rn(p, v));
+  sh = sum;
+  sl = __fadd_rn(sl, __fadd_rn(e, __fadd_rn(pe, x)));
+}
+// hi the rounded value of hi + lo
+__device__ __forceinline__ void df_renorm(float& h, float& l) {
+  const float t = __fadd_rn(h, l);
+  l = __fsub_rn(l, __fsub_rn(t, h));
+  h = t;
+}
+// (ah, al) += (bh, bl), renormalized
+__device__ __forceinline__ void df_add(float& ah, float& al, float bh, float bl) {
+  const float sum = __fadd_rn(ah, bh);
+  const float v = __fsub_rn(sum, ah);
+  const float e = __fadd_rn(__fsub_rn(ah, __fsub_rn(sum, v)), __fsub_rn(bh, v));
+  ah = sum;
+  al = __fadd_rn(e, __fadd_rn(al, bl));
+  df_renorm(ah, al);
+}
+__device__ __forceinline__ double df_value(float h, float l) { return f32_to_f64_bits(h) + f32_to_f64_bits(l); }
 
 __device__ __forceinline__ bool big_group(const MomArgs& m, const SubDev& S, int s, int k) {
   const int64_t g = m.loc_off[s] + k;
@@ -1210,6 +1248,28 @@ __device__ __forceinline__ void field_rows(const double* __restrict__ X, int nc,
       for (int u = 1; u < NS; ++u) v += z[u][q];
       Z[c * kTP + q] = v;
     }
+  }
+}
+
+// field_rows in double-float: Z = X rows times the points' coefficients,
+// each X entry split once (one FP64 subtraction) for NQ points.
+template <int NQ>
+__device__ __forceinline__ void field_rows_df(const double* __restrict__ X, int nc, int C, int ncell,
+                                              const float* Cfh, const float* Cfl, double* Z) {
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+    const double* xr = X + c;
+    float sh[NQ], sl[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) { sh[q] = 0.f; sl[q] = 0.f; }
+#pragma unroll 4
+    for (int i = 0; i < C; ++i) {
+      float xh, xl;
+      df_split(xr[(int64_t)i * nc], xh, xl);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) df_mac(xh, xl, Cfh[q * C + i], Cfl[q * C + i], sh[q], sl[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) Z[c * kTP + q] = df_value(sh[q], sl[q]);
   }
 }
 
@@ -1448,15 +1508,22 @@ __global__ void __launch_bounds__(kMomT) darcy_moments_list_kernel(MomArgs m, co
     double* Cf = sm;                  // [kTP][C]
     double* Z = Cf + kTP * C;         // [ncell][kTP]
     double* Wt = Z + ncell * kTP;     // [kTP]
+    float* Cfh = reinterpret_cast<float*>(Wt + kTP);   // [kTP][C] double-float split of Cf
+    float* Cfl = Cfh + kTP * C;
+    const bool dfp = m.df && cntp > 2;   // double-float once an X entry serves 4 or more points
     __syncthreads();
-    for (int e2 = threadIdx.x; e2 < cntp * C; e2 += blockDim.x) {
+    for (int e2 = threadIdx.x; e2 < kTP * C; e2 += blockDim.x) {
       const int q = e2 / C, i = e2 - q * C;
-      Cf[e2] = i < R ? a.lam[(int64_t)pts[q] * a.n_lambda + gd[i]] : 1.0;
+      const double v = q < cntp ? (i < R ? a.lam[(int64_t)pts[q] * a.n_lambda + gd[i]] : 1.0) : 0.0;
+      if (q < cntp) Cf[e2] = v;
+      if (dfp) df_split(v, Cfh[e2], Cfl[e2]);
     }
     for (int q = threadIdx.x; q < kTP; q += blockDim.x) Wt[q] = q < cntp ? m.w[pts[q]] : 0.0;
     __syncthreads();
     if (cntp == 1) field_rows<1>(X + (int64_t)h0 * nx, nc, C, ncell, Cf, Z);
     else if (cntp == 2) field_rows<2>(X + (int64_t)h0 * nx, nc, C, ncell, Cf, Z);
+    else if (dfp && cntp <= 4) field_rows_df<4>(X + (int64_t)h0 * nx, nc, C, ncell, Cfh, Cfl, Z);
+    else if (dfp) field_rows_df<kTP>(X + (int64_t)h0 * nx, nc, C, ncell, Cfh, Cfl, Z);
     else if (cntp <= 4) field_rows<4>(X + (int64_t)h0 * nx, nc, C, ncell, Cf, Z);
     else field_rows<kTP>(X + (int64_t)h0 * nx, nc, C, ncell, Cf, Z);
     __syncthreads();
@@ -1665,7 +1732,13 @@ __global__ void __launch_bounds__(kBigT) bigroup_moments_kernel(MomArgs m, int s
     const double* Tx = m.T + off.t;
     const double* Ty = Tx + (int64_t)ny * (nx + 1);
     __syncthreads();
-    for (int e = threadIdx.x; e < C * C; e += blockDim.x) Ms[e] = gm[1 + 2 * C + e];
+    // M in FP64, or split into FP32 hi and lo halves (the same bytes) for double-float
+    float* MsH = reinterpret_cast<float*>(Ms);
+    float* MsL = MsH + C * C;
+    for (int e = threadIdx.x; e < C * C; e += blockDim.x) {
+      if (m.df) df_split(gm[1 + 2 * C + e], MsH[e], MsL[e]);
+      else Ms[e] = gm[1 + 2 * C + e];
+    }
     for (int e = threadIdx.x; e < C; e += blockDim.x) { cb[e] = gm[1 + e]; mv[e] = gm[1 + C + e]; }
     const double W = gm[0];
     __syncthreads();
@@ -1675,16 +1748,50 @@ __global__ void __launch_bounds__(kBigT) bigroup_moments_kernel(MomArgs m, int s
       if (el >= n_ent) break;
       const EntryMap em = entry_map(S, m, el, Tx, Ty, ihx, ihy);
       double fc = 0.0, fm = 0.0;
+      float2* Fc2 = reinterpret_cast<float2*>(Fc);
 #pragma unroll 4
       for (int ia = 0; ia < C; ++ia) {
         const double f = entry_map_coef(em, X, (int64_t)nx * ny, R, ia);
-        Fc[ia * nt] = f;
+        if (m.df) {
+          float fh, fl;
+          df_split(f, fh, fl);
+          Fc2[ia * nt] = make_float2(fh, fl);
+        } else {
+          Fc[ia * nt] = f;
+        }
         fc = fma(f, cb[ia], fc);
         fm = fma(f, mv[ia], fm);
       }
+      double q = 0.0;
+      if (m.df) {
+        // F M F^T in double-float: per row the upper-triangle sum in two
+        // chains, then row = M_aa F_a + 2 r and q += F_a row
+        float qh = 0.f, ql = 0.f;
+        for (int ia = 0; ia < C; ++ia) {
+          const float* Mh = MsH + ia * C;
+          const float* Ml = MsL + ia * C;
+          float r0h = 0.f, r0l = 0.f, r1h = 0.f, r1l = 0.f;
+          int ib = ia + 1;
+          for (; ib + 1 < C; ib += 2) {
+            const float2 f0 = Fc2[ib * nt], f1 = Fc2[(ib + 1) * nt];
+            df_mac(Mh[ib], Ml[ib], f0.x, f0.y, r0h, r0l);
+            df_mac(Mh[ib + 1], Ml[ib + 1], f1.x, f1.y, r1h, r1l);
+          }
+          if (ib < C) {
+            const float2 f0 = Fc2[ib * nt];
+            df_mac(Mh[ib], Ml[ib], f0.x, f0.y, r0h, r0l);
+          }
+          df_add(r0h, r0l, r1h, r1l);
+          const float2 fa = Fc2[ia * nt];
+          float rowh = 2.f * r0h, rowl = 2.f * r0l;   // exact
+          df_mac(Mh[ia], Ml[ia], fa.x, fa.y, rowh, rowl);
+          df_renorm(rowh, rowl);
+          df_mac(fa.x, fa.y, rowh, rowl, qh, ql);
+        }
+        q = df_value(qh, ql);
+      } else {
       // F M F^T over the upper triangle; four partial sums per row keep four
       // independent FP64 FMA chains in flight
-      double q = 0.0;
       for (int ia = 0; ia < C; ++ia) {
         const double* Mr = Ms + ia * C;
         double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
@@ -1698,6 +1805,7 @@ __global__ void __launch_bounds__(kBigT) bigroup_moments_kernel(MomArgs m, int s
         for (; ib < C; ++ib) r0 = fma(Mr[ib], Fc[ib * nt], r0);
         const double fa = Fc[ia * nt];
         q = fma(fa, fma(2.0, (r0 + r1) + (r2 + r3), Mr[ia] * fa), q);
+      }
       }
       const double dv = fc - sh[j];
       acc1[j] += fm + W * dv;
@@ -2184,7 +2292,10 @@ sfb_status moments_accumulate_device(sfb_ctx* c, int64_t n_pts) {
   m.big_factor = c->opt_big_factor;
   m.grp_start = d.grp_start; m.grp_end = d.grp_count; m.loc_off = d.loc_off;
   m.gmom = d.gmom; m.gmom_stride = c->gmom_stride;
-  const size_t smd = sizeof(double) * ((size_t)kTP * maxC + (size_t)(m.rt + 1) * max_nx * kTP + kTP);
+  m.df = (c->basis_prec == SFB_MIXED && c->opt_mom_df) ? 1 : 0;
+  // Cf | Z | Wt | the double-float split of Cf (two float blocks of kTP x C)
+  const size_t smd = sizeof(double) * ((size_t)kTP * maxC + (size_t)(m.rt + 1) * max_nx * kTP + kTP) +
+                     2 * sizeof(float) * (size_t)kTP * maxC;
   CK(cudaFuncSetAttribute(darcy_moments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd));
   const int row_tiles = (max_ny + m.rt - 1) / m.rt;
   const int first = c->mom_shift_set ? 0 : 1;

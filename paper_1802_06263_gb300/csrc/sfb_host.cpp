@@ -941,6 +941,9 @@ sfb_status sfb_set_option(sfb_ctx* c, const char* name, double value) {
   } else if (n == "cg_precond") {
     if (!(value == 0 || value == 1 || value == 2)) return fail(c, SFB_ERR_ARG, "cg_precond must be 0, 1 or 2");
     c->opt_cg_precond = (int)value;
+  } else if (n == "moments_double_float") {
+    if (!(value == 0 || value == 1)) return fail(c, SFB_ERR_ARG, "moments_double_float must be 0 or 1");
+    c->opt_mom_df = (int)value;
   } else if (n == "cg_persistent") {
     if (!(value == 0 || value == 1)) return fail(c, SFB_ERR_ARG, "cg_persistent must be 0 or 1");
     c->opt_cg_persistent = (int)value;
