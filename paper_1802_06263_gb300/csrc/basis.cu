@@ -783,15 +783,28 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
       if (b < ny - 1) gemm_g<T>(Gs, Us, Zs, true, np, Cp, C);
       __syncthreads();
       SFB_MARK(10);
-#pragma unroll 4
-      for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
-        const int i = e % nx, c = e / nx;
-        const int64_t idx = (int64_t)c * nc + (int64_t)b * nx + i;
-        const T dt = sc[i] * Zs[i * Cp + c];
-        const float df = to_f32(dt);
-        dn2f = fmaf(df, df, dn2f);
-        if (it == 0) X[idx] = to_f64(dt);
-        else X[idx] += to_f64(dt);
+      // x_b += s d_b: the X entries of four iterations are loaded before any
+      // of them is stored, so that the loads overlap
+      constexpr int kXU = 4;
+      for (int e0 = threadIdx.x; e0 < nx * C; e0 += kXU * blockDim.x) {
+        double xo[kXU];
+#pragma unroll
+        for (int u = 0; u < kXU; ++u) {
+          const int e = e0 + u * blockDim.x;
+          const int i = e % nx, c = e / nx;
+          xo[u] = (it > 0 && e < nx * C) ? X[(int64_t)c * nc + (int64_t)b * nx + i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kXU; ++u) {
+          const int e = e0 + u * blockDim.x;
+          if (e >= nx * C) break;
+          const int i = e % nx, c = e / nx;
+          const int64_t idx = (int64_t)c * nc + (int64_t)b * nx + i;
+          const T dt = sc[i] * Zs[i * Cp + c];
+          const float df = to_f32(dt);
+          dn2f = fmaf(df, df, dn2f);
+          X[idx] = it == 0 ? to_f64(dt) : xo[u] + to_f64(dt);
+        }
       }
       __syncthreads();
       SFB_MARK(11);
