@@ -160,3 +160,27 @@ def test_persistent_cg_matches_per_step_launches(key, krylov, precond):
         assert np.array_equal(m0[f][0], m1[f][0]) and np.array_equal(m0[f][1], m1[f][1]), f
     assert rel(l1, lams) < 1e-9
     assert n0 > 2 * c0 and n1 < 30, (n0, n1, c0)
+
+
+@pytest.mark.parametrize("factor", [1.0, 0.01])
+def test_double_float_moments_match_fp64_contractions(factor):
+    """After a mixed-form build the moments' contractions run in double-float
+    (FP32 hi/lo pairs with error-free products and sums), about 1e-14 relative
+    to the field values. The variances subtract the shift s, which scales that
+    error by |v| / |v - s| (3e-12 measured on the face fluxes); both forms
+    match the oracle. factor 0.01 sends every group through the quadratic
+    forms."""
+    p, y, wt, lams, mom = oracle_case("medium")
+    s, _ = _solver("medium", 1)
+    s.set_option("moments_group_factor", factor)
+    res = {}
+    for dfm in (0, 1):
+        s.set_option("moments_double_float", dfm)
+        s.moments_reset()
+        s.solve_host(y, wt, rtol=1e-12, max_it=5000, krylov=1)
+        res[dfm] = {f: s.moments(f) for f in FIELD_NAMES}
+    for f in FIELD_NAMES:
+        for j in (0, 1):
+            assert rel(res[1][f][j], res[0][f][j]) < 1e-10, (f, j)
+    assert rel(res[1]["darcy_flux"][0], mom["darcy_flux"][0]) < 1e-8
+    assert rel(res[1]["darcy_p"][1], mom["darcy_p"][1]) < 1e-8
