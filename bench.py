@@ -284,7 +284,8 @@ def run_ours(args):
                                   "note": "lower bound: FP64 check products not counted"}, **rl_cg),
         "a12_darcy_moments": {"bound": "hbm", "unit": "GB/s", "ms": mom_s * 1e3, "bytes": x_bytes,
                               "achieved": x_bytes / mom_s / 1e9, "peak": hbm, "frac": x_bytes / mom_s / 1e9 / hbm,
-                              "note": "the large groups' quadratic forms make it FP64-bound in fact"},
+                              "note": "far from the bytes bound: its contractions are ALU work (double-float "
+                                      "on the FP32 pipe after a mixed build, FP64 otherwise)"},
     }
     out = {
         "metric": METRIC, "value": world * n_pts / (t_mixed * 1e-3), "unit": UNIT,
