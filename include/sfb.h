@@ -276,6 +276,10 @@ sfb_status sfb_build_basis_item_noalloc(sfb_ctx* ctx, int32_t sub, int32_t k, in
  *                    more than 32 DOFs fall back to Jacobi). The same solution
  *                    and the same stopping test on the unpreconditioned
  *                    residual in every case (1);
+ *   "cg_test_barrier_timeout"  test hook: 1 makes CTA 0 of the next one-launch
+ *                    CG skip its first grid barrier, so that the other CTAs'
+ *                    waits run out (1 s). The solve returns SFB_ERR_TIMEOUT and
+ *                    the context stays usable. Cleared by that solve (0);
  *   "cg_replace_ratio"  SFB_CG_MIXED: a point's residual is replaced by the
  *                    FP64 residual at the next check once the recursive one
  *                    has dropped by this factor since the last replacement,

@@ -18,6 +18,7 @@ from ._build import LIB as _LIB_PATH, build  # noqa: F401
 
 SFB_OK = 0
 SFB_ERR_NOT_CONVERGED = 6
+SFB_ERR_TIMEOUT = 9
 FP64, MIXED, FP32_NOREFINE = 0, 1, 2
 CG, CG_MIXED = 0, 1
 FIELDS = {"darcy_p": 0, "darcy_flux": 1, "stokes_u": 2, "stokes_p": 3}

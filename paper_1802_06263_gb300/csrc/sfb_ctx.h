@@ -199,6 +199,7 @@ struct sfb_ctx {
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int cg_iters_run = 0;
   bool cg_persistent_run = false;
+  int test_barrier_skip = 0;   // test hook of the next one-launch CG (see cg_test_barrier_timeout)
   int pcg_grid = 1;
   std::vector<int> pcg_starts;   // host copy of the last resident partition
   int pcg_mode = 0;   // last persistent CG: bit 0 resident tiles, bit 1 two streaming buffers

@@ -944,6 +944,9 @@ sfb_status sfb_set_option(sfb_ctx* c, const char* name, double value) {
   } else if (n == "moments_double_float") {
     if (!(value == 0 || value == 1)) return fail(c, SFB_ERR_ARG, "moments_double_float must be 0 or 1");
     c->opt_mom_df = (int)value;
+  } else if (n == "cg_test_barrier_timeout") {
+    if (!(value == 0 || value == 1)) return fail(c, SFB_ERR_ARG, "cg_test_barrier_timeout must be 0 or 1");
+    c->test_barrier_skip = (int)value;
   } else if (n == "cg_persistent") {
     if (!(value == 0 || value == 1)) return fail(c, SFB_ERR_ARG, "cg_persistent must be 0 or 1");
     c->opt_cg_persistent = (int)value;

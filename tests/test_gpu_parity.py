@@ -184,3 +184,28 @@ def test_double_float_moments_match_fp64_contractions(factor):
             assert rel(res[1][f][j], res[0][f][j]) < 1e-10, (f, j)
     assert rel(res[1]["darcy_flux"][0], mom["darcy_flux"][0]) < 1e-8
     assert rel(res[1]["darcy_p"][1], mom["darcy_p"][1]) < 1e-8
+
+
+def test_persistent_cg_barrier_wait_runs_out_and_the_context_recovers():
+    """Failure detection without a fault: with the test hook, CTA 0 of the
+    one-launch CG skips its first grid barrier. The other CTAs' bounded waits
+    run out after 1 s, set the abort word, and every CTA leaves; the solve
+    reports SFB_ERR_TIMEOUT with the barrier named, and the next solve on the
+    same context gives the same mortar solution as before."""
+    import time
+    import paper_1802_06263_gb300 as sfb
+    p, y, wt, lams, mom = oracle_case("medium")
+    s, _ = _solver("medium", 0)
+    lam0, it0, rc0 = s.solve_host(y, wt, rtol=1e-12, max_it=5000, krylov=0)
+    assert rc0 == 0
+    s.set_option("cg_test_barrier_timeout", 1)
+    s.moments_reset()
+    t0 = time.time()
+    _, _, rc = s.solve_host(y, wt, rtol=1e-12, max_it=5000, check=False, krylov=0)
+    dt = time.time() - t0
+    assert rc == sfb.SFB_ERR_TIMEOUT, rc
+    assert "grid barrier" in s.lib.sfb_last_error(s.h).decode()
+    assert 0.9 < dt < 60, dt
+    s.moments_reset()
+    lam1, it1, rc1 = s.solve_host(y, wt, rtol=1e-12, max_it=5000, krylov=0)
+    assert rc1 == 0 and np.array_equal(lam1, lam0) and np.array_equal(it1, it0)
