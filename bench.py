@@ -296,7 +296,7 @@ def run_ours(args):
                                "8 linear mortar elements/edge (224 DOFs), Smolyak L2 over 32 dims "
                                "(2,049 points), Stokes 32x32",
                    "n_points": n_pts, "n_basis_items": n_items, "flux_responses": fr,
-                   "cg_rtol": rtol, "cg_preconditioner": "Jacobi (diagonal of S^l)",
+                   "cg_rtol": rtol, "cg_preconditioner": "interface block-Jacobi (diagonal blocks of S^l per mortar interface)",
                    "l2": "working set larger than L2 (basis store %.2f GB)"
                    % (s.workspace_bytes(sfb.MIXED, n_pts) / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -275,7 +275,7 @@ sfb_status sfb_build_basis_item_noalloc(sfb_ctx* ctx, int32_t sub, int32_t k, in
  *                    DOFs, inverted per point, applied in FP32; interfaces of
  *                    more than 32 DOFs fall back to Jacobi). The same solution
  *                    and the same stopping test on the unpreconditioned
- *                    residual in every case (1);
+ *                    residual in every case (2);
  *   "cg_test_barrier_timeout"  test hook: 1 makes CTA 0 of the next one-launch
  *                    CG skip its first grid barrier, so that the other CTAs'
  *                    waits run out (1 s). The solve returns SFB_ERR_TIMEOUT and

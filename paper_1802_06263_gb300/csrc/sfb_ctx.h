@@ -191,7 +191,7 @@ struct sfb_ctx {
   int opt_refine_max = 8;
   int opt_cg_chunk = 8;
   int opt_cg_persistent = 1;    // interface CG in one cooperative launch (0: one launch per step)
-  int opt_cg_precond = 1;       // interface CG preconditioner: 0 none, 1 Jacobi, 2 interface blocks
+  int opt_cg_precond = 2;       // interface CG preconditioner: 0 none, 1 Jacobi, 2 interface blocks
   double opt_cg_replace = 0.1;  // mixed CG: FP64 residual once the recursive one drops by this factor
   int opt_mom_df = 1;           // mixed form: moment contractions in double-float (0: FP64)
   double opt_big_factor = 1.0;   // groups above this many times (R+1) points use coefficient moments
