@@ -309,7 +309,8 @@ def run_ours(args):
                        "unrefined_fp32_rel_error": st_mixed["max_first_correction"],
                        "final_rel_residual": st_mixed["max_rel_residual"],
                        "cg_iters_min_max": [int(iters.min()), int(iters.max())],
-                       "solve_phases_ms": mixed_phases},
+                       "solve_phases_ms": mixed_phases,
+                       "basis_launch": basis_launch(sfb, sfb.MIXED, st_mixed)},
         "mixed_vs_fp64_rel": agree,
         "speedup_mixed_vs_fp64": t_fp64 / t_mixed,
         "e2e": {"value": world * n_pts / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
@@ -330,6 +331,20 @@ def run_ours(args):
         "gpu_launches_per_step": launches / args.steps,
     }
     return out, rank
+
+
+def basis_launch(sfb, prec, st):
+    """Launch shape of each size class of the basis build (threads, CTAs per
+    SM, G buffers), the autotuner's timings and whether a graph replayed it."""
+    out = {"graph_replay": bool(st["graph"])}
+    for q, cls in enumerate(("wide_grids", "narrow_grids")):
+        v = st["launch_shape"][q]
+        if v < 0:
+            continue
+        t, c, g = sfb.basis_launch_shape(prec, q == 0, v)
+        out[cls] = {"shape": v, "threads": t, "ctas_per_sm": c, "g_buffers": g,
+                    "autotune_ms": [m for m in st["tune_ms"][q] if m > 0]}
+    return out
 
 
 def cpu_baseline_sample(n_items=8, n_pts=24):

@@ -150,6 +150,15 @@ typedef struct {
                               /* (5-point residual and update). FP64 form: all in */
                               /* flops_fp64; mixed: factor and 1 + n_refine       */
                               /* solves in flops_fp32, the passes in flops_fp64   */
+  int32_t launch_shape[2];    /* launch shape of the basis kernel per size class: */
+                              /* [0] grids wider than 64 cells, [1] the rest     */
+                              /* (sfb_basis_launch_shape); -1: class is empty     */
+  int32_t graph;              /* 1: the launches of all size classes ran as one   */
+                              /* replayed CUDA graph                              */
+  int32_t reserved;
+  double tune_ms[2][4];       /* autotuner, per size class and launch shape: the  */
+                              /* shorter of two timed launches of the class's     */
+                              /* items (ms); 0: not timed                         */
 } sfb_basis_stats;
 
 typedef struct sfb_ctx sfb_ctx;
@@ -197,6 +206,20 @@ sfb_status sfb_set_workspace(sfb_ctx* ctx, void* dev_ptr, size_t bytes);
  * with g[l] = <u_bar.n, xi_l>; also the deterministic Stokes basis (Section
  * 5.4: N_real = 1 for Stokes subdomains). stats_out is nullable. */
 sfb_status sfb_build_stochastic_basis(sfb_ctx* ctx, int32_t prec, sfb_basis_stats* stats_out);
+
+/* Launch shapes of the basis kernel (no counterpart in the paper: how the
+ * items of Section 5.4 Steps 1-2 map onto the GPU). The items fall into two
+ * size classes, grids more than 64 cells wide (wide = 1) and the rest; each
+ * class is one launch, the two run concurrently. prec selects the factor
+ * precision (SFB_FP64: one shape per class; SFB_MIXED, SFB_FP32_NOREFINE: two).
+ * Writes the shape's threads per CTA, the CTAs per SM its register budget is
+ * compiled for and its number of shared-memory G_b buffers (2: the next block
+ * row's inverse is prefetched). Pointers are host memory and nullable.
+ * SFB_ERR_ARG for a shape index out of range. By default the first build of
+ * each precision times every shape of each class on that class's own items
+ * and keeps the fastest (option "basis_autotune"). */
+sfb_status sfb_basis_launch_shape(int32_t prec, int32_t wide, int32_t shape, int32_t* threads,
+                                  int32_t* ctas_per_sm, int32_t* g_buffers);
 
 /* Read-back of one stored basis item (host or device buffers): phi [R x R]
  * row-major, g [R], x [(R+1) x n_cells] (pressure responses, column j is the
@@ -276,6 +299,17 @@ sfb_status sfb_build_basis_item_noalloc(sfb_ctx* ctx, int32_t sub, int32_t k, in
  *                    more than 32 DOFs fall back to Jacobi). The same solution
  *                    and the same stopping test on the unpreconditioned
  *                    residual in every case (2);
+ *   "basis_autotune" 1: the next build of each precision first times every
+ *                    launch shape of each size class (sfb_basis_launch_shape)
+ *                    and keeps the fastest; setting it (0 or 1) forgets
+ *                    earlier choices. 0: shape 0 everywhere (1);
+ *   "basis_shape"    forces launch shape n for every size class that has it
+ *                    (shape 0 for the others) and turns the autotuner off;
+ *   "basis_graph"    1: the launches of all size classes are captured once as
+ *                    a CUDA graph (on a private stream) and replayed while the
+ *                    workspace, refinement options and shapes stay the same;
+ *                    plain launches when the context stream is itself being
+ *                    captured. 0: plain launches (1);
  *   "cg_test_barrier_timeout"  test hook: 1 makes CTA 0 of the next one-launch
  *                    CG skip its first grid barrier, so that the other CTAs'
  *                    waits run out (1 s). The solve returns SFB_ERR_TIMEOUT and

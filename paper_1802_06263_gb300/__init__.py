@@ -57,7 +57,9 @@ class BasisStats(ctypes.Structure):
                 ("max_rel_residual", ctypes.c_double), ("max_first_correction", ctypes.c_double),
                 ("max_error_estimate", ctypes.c_double), ("ms", ctypes.c_double),
                 ("phase_cycles", ctypes.c_double * 16), ("kernel_ms", ctypes.c_double),
-                ("flops_fp32", ctypes.c_double), ("flops_fp64", ctypes.c_double)]
+                ("flops_fp32", ctypes.c_double), ("flops_fp64", ctypes.c_double),
+                ("launch_shape", ctypes.c_int32 * 2), ("graph", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("tune_ms", (ctypes.c_double * 4) * 2)]
 
 
 _SIGS = {
@@ -88,6 +90,7 @@ _SIGS = {
     "sfb_solve_timings": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _i32p]),
     "sfb_cg_phase_cycles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sfb_launch_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "sfb_basis_launch_shape": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p]),
     "sfb_build_basis_item_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
@@ -112,6 +115,17 @@ def load():
             fn.argtypes = args
         _lib = lib
     return _lib
+
+
+def basis_launch_shape(prec, wide, shape):
+    """(threads per CTA, CTAs per SM, G buffers) of a basis-kernel launch
+    shape, or None when the precision has no such shape for that size class."""
+    lib = load()
+    t, c, g = (ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32())
+    rc = lib.sfb_basis_launch_shape(prec, int(bool(wide)), shape, ctypes.byref(t), ctypes.byref(c), ctypes.byref(g))
+    if rc != SFB_OK:
+        return None
+    return t.value, c.value, g.value
 
 
 class SfbError(RuntimeError):
@@ -273,6 +287,9 @@ class Solver:
             self._check(rc)
         out = {k: getattr(st, k) for k, _ in BasisStats._fields_}
         out["phase_cycles"] = list(st.phase_cycles)
+        out["launch_shape"] = list(st.launch_shape)
+        out["tune_ms"] = [list(r) for r in st.tune_ms]
+        del out["reserved"]
         out["status"] = rc
         return out
 

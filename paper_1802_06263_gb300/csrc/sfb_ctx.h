@@ -174,6 +174,7 @@ struct sfb_ctx {
   int wide_nx = 0, wide_cols = 0, narrow_nx = 0, narrow_cols = 0;
   cudaStream_t side = nullptr;          // second stream for the narrow items
   cudaEvent_t fork = nullptr, join = nullptr;
+  cudaStream_t gcap = nullptr;          // private stream on which the basis graph is captured
   std::vector<sfb::ItemOff> offs;
   std::vector<int64_t> ybase;              // per unit (Darcy subs, then Stokes) offset into Y
   int64_t NY = 0;
@@ -195,6 +196,28 @@ struct sfb_ctx {
   double opt_cg_replace = 0.1;  // mixed CG: FP64 residual once the recursive one drops by this factor
   int opt_mom_df = 1;           // mixed form: moment contractions in double-float (0: FP64)
   double opt_big_factor = 1.0;   // groups above this many times (R+1) points use coefficient moments
+  int opt_basis_graph = 1;      // basis launches of every size class replayed as one CUDA graph
+  int opt_basis_autotune = 1;   // time the launch shapes of each size class on the first build
+  // basis build: launch shape per precision (sfb_precision) and size class
+  // ([0] grids wider than 64 cells, [1] the rest), the autotuner's timings of
+  // each candidate (ms, 0 = not timed), and the captured graph per precision
+  int bshape[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  bool btuned[3] = {false, false, false};
+  double btune_ms[3][2][4] = {};
+  struct GraphKey {
+    const char* ws = nullptr;
+    int refine = 0;
+    double refine_tol = 0.0;
+    int shape[2] = {0, 0};
+    bool operator==(const GraphKey& o) const {
+      return ws == o.ws && refine == o.refine && refine_tol == o.refine_tol && shape[0] == o.shape[0] &&
+             shape[1] == o.shape[1];
+    }
+  };
+  cudaGraphExec_t bgraph[3] = {nullptr, nullptr, nullptr};
+  GraphKey bkey[3];
+  int bgraph_kernels[3] = {0, 0, 0};
+  bool last_build_graph = false;
   // device-time phase markers of the last interface solve (CUDA events)
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int cg_iters_run = 0;
@@ -207,8 +230,11 @@ struct sfb_ctx {
   ~sfb_ctx() {
     for (cudaEvent_t e : ev)
       if (e) cudaEventDestroy(e);
+    for (cudaGraphExec_t g : bgraph)
+      if (g) cudaGraphExecDestroy(g);
     if (fork) cudaEventDestroy(fork);
     if (join) cudaEventDestroy(join);
     if (side) cudaStreamDestroy(side);
+    if (gcap) cudaStreamDestroy(gcap);
   }
 };

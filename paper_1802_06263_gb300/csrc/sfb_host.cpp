@@ -542,6 +542,12 @@ sfb_status sfb_set_workspace(sfb_ctx* c, void* ptr, size_t bytes) {
   if (bytes < need) return fail(c, SFB_ERR_WORKSPACE, "workspace smaller than sfb_workspace_size()");
   c->ws = reinterpret_cast<char*>(ptr);
   c->ws_bytes = bytes;
+  // captured basis graphs hold the old workspace's addresses
+  for (int q = 0; q < 3; ++q)
+    if (c->bgraph[q]) {
+      cudaGraphExecDestroy(c->bgraph[q]);
+      c->bgraph[q] = nullptr;
+    }
   c->basis_done = false;
   c->basis_prec = -1;
   c->n_solved = 0;
@@ -674,6 +680,60 @@ sfb_status upload_tables(sfb_ctx* c) {
   return SFB_OK;
 }
 
+// The basis build's autotuner. For each non-empty size class with more than
+// one launch shape, every shape that keeps at least one CTA resident at the
+// class's largest grid and column count runs the class's own items alone on
+// the context stream: once untimed, then twice timed by CUDA events. The
+// shape with the shorter of its two times is kept for later builds of this
+// precision. The trial launches write the same outputs as the build that
+// follows, which overwrites them and clears the per-item status first.
+sfb_status autotune_basis(sfb_ctx* c, int prec, const BasisArgs* cls, const int* cls_nx, const int* cls_cols,
+                          int refine) {
+  const int fp64 = prec == SFB_FP64 ? 1 : 0;
+  const int ns = basis_shape_count(fp64);
+  cudaStream_t st = c->stream;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaError_t e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+    for (int v = 0; v < 4; ++v) c->btune_ms[prec][q][v] = 0.0;
+    c->bshape[prec][q] = 0;
+    if (cls[q].n_items == 0 || ns < 2) continue;
+    int best = -1;
+    for (int v = 0; v < ns && v < 4 && e == cudaSuccess; ++v) {
+      int ctas = 0;
+      e = basis_shape_ctas(fp64, q == 0, v, cls_nx[q], cls_cols[q], &ctas);
+      if (e != cudaSuccess || ctas < 1) {
+        // a shape that does not fit at these sizes is skipped, not an error
+        cudaGetLastError();
+        e = cudaSuccess;
+        continue;
+      }
+      float ms_min = 0.f;
+      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        if (rep > 0) e = cudaEventRecord(t0, st);
+        if (e == cudaSuccess) e = launch_basis_shape(cls[q], fp64, q == 0, v, cls_nx[q], cls_cols[q], refine, st);
+        c->launches += 1;
+        if (rep == 0 || e != cudaSuccess) continue;
+        e = cudaEventRecord(t1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+        if (e == cudaSuccess && (rep == 1 || ms < ms_min)) ms_min = ms;
+      }
+      if (e != cudaSuccess) break;
+      c->btune_ms[prec][q][v] = ms_min;
+      if (best < 0 || ms_min < c->btune_ms[prec][q][best]) best = v;
+    }
+    if (best >= 0) c->bshape[prec][q] = best;
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (e != cudaSuccess) return cuda_fail(c, e, "basis autotuner");
+  c->btuned[prec] = true;
+  return SFB_OK;
+}
+
 bool host_or_device_copy(void* dst, const void* src, size_t bytes, cudaStream_t st) {
   return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st) == cudaSuccess;
 }
@@ -702,11 +762,6 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
     c->basis_prec = 99;  // tables and Stokes basis present
   }
   const int n = (int)c->n_items;
-  SFB_CUDA(cudaMemsetAsync(d.status, 0, sizeof(int) * n, st), "memset");
-  SFB_CUDA(cudaMemsetAsync(d.resid, 0, sizeof(double) * n, st), "memset");
-  SFB_CUDA(cudaMemsetAsync(d.corr1, 0, sizeof(double) * n, st), "memset");
-  SFB_CUDA(cudaMemsetAsync(d.errest, 0, sizeof(double) * n, st), "memset");
-  SFB_CUDA(cudaMemsetAsync(d.nref, 0, sizeof(int) * n, st), "memset");
   BasisArgs a;
   a.subs = d.subs; a.proj = d.proj; a.dofinfo = d.dofinfo; a.kl = d.kl; a.yloc = d.yloc;
   a.item_sub = d.item_sub; a.item_k = d.item_k; a.off = d.off; a.n_items = n;
@@ -715,42 +770,100 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   a.cycles = d.cycles;
   a.max_refine = c->opt_refine_max;
   a.refine_tol = c->opt_refine_tol;
+  // size classes: [0] grids wider than 64 cells (the first n_wide items), [1] the rest
+  const int fp64 = prec == SFB_FP64 ? 1 : 0;
+  const int refine = prec == SFB_MIXED ? a.max_refine : 0;
+  BasisArgs cls[2] = {a, a};
+  cls[0].n_items = (int)c->n_wide;
+  cls[1].item_sub = a.item_sub + c->n_wide;
+  cls[1].item_k = a.item_k + c->n_wide;
+  cls[1].n_items = n - (int)c->n_wide;
+  const int cls_nx[2] = {c->wide_nx, c->narrow_nx}, cls_cols[2] = {c->wide_cols, c->narrow_cols};
+  if (c->opt_basis_autotune && !c->btuned[prec]) {
+    sfb_status s = autotune_basis(c, prec, cls, cls_nx, cls_cols, refine);
+    if (s != SFB_OK) return s;
+  }
+  SFB_CUDA(cudaMemsetAsync(d.status, 0, sizeof(int) * n, st), "memset");
+  SFB_CUDA(cudaMemsetAsync(d.resid, 0, sizeof(double) * n, st), "memset");
+  SFB_CUDA(cudaMemsetAsync(d.corr1, 0, sizeof(double) * n, st), "memset");
+  SFB_CUDA(cudaMemsetAsync(d.errest, 0, sizeof(double) * n, st), "memset");
+  SFB_CUDA(cudaMemsetAsync(d.nref, 0, sizeof(int) * n, st), "memset");
+  const int shp[2] = {c->bshape[prec][0], c->bshape[prec][1]};
+  const bool two = cls[0].n_items > 0 && cls[1].n_items > 0;
+  if (two) {
+    if (!c->side) SFB_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "stream");
+    if (!c->fork) SFB_CUDA(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming), "event");
+    if (!c->join) SFB_CUDA(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming), "event");
+  }
+  // One launch per size class: wide grids on the main stream, narrow grids
+  // concurrently on a side stream joined back before the epilogue.
+  auto issue = [&](cudaStream_t s0, int* nk) -> cudaError_t {
+    if (!two) {
+      const int q = cls[0].n_items > 0 ? 0 : 1;
+      *nk = 1;
+      return launch_basis_shape(cls[q], fp64, q == 0, shp[q], cls_nx[q], cls_cols[q], refine, s0);
+    }
+    *nk = 2;
+    cudaError_t e = cudaEventRecord(c->fork, s0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->fork, 0);
+    if (e == cudaSuccess) e = launch_basis_shape(cls[0], fp64, 1, shp[0], cls_nx[0], cls_cols[0], refine, s0);
+    if (e == cudaSuccess) e = launch_basis_shape(cls[1], fp64, 0, shp[1], cls_nx[1], cls_cols[1], refine, c->side);
+    if (e == cudaSuccess) e = cudaEventRecord(c->join, c->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, c->join, 0);
+    return e;
+  };
+  // The launches of all size classes as one CUDA graph, captured on a private
+  // stream (the context stream may be the legacy default stream, which cannot
+  // capture) and replayed on the context stream while the workspace, the
+  // refinement options and the launch shapes stay the same. A context stream
+  // that is itself being captured (the caller's graph) gets the plain launches.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  SFB_CUDA(cudaStreamIsCapturing(st, &cap), "capture status");
+  const bool graph = c->opt_basis_graph && cap == cudaStreamCaptureStatusNone;
+  if (graph) {
+    sfb_ctx::GraphKey key;
+    key.ws = c->ws;
+    key.refine = refine;
+    key.refine_tol = a.refine_tol;
+    key.shape[0] = shp[0];
+    key.shape[1] = shp[1];
+    if (c->bgraph[prec] && !(c->bkey[prec] == key)) {
+      cudaGraphExecDestroy(c->bgraph[prec]);
+      c->bgraph[prec] = nullptr;
+    }
+    if (!c->bgraph[prec]) {
+      if (!c->gcap) SFB_CUDA(cudaStreamCreateWithFlags(&c->gcap, cudaStreamNonBlocking), "stream");
+      cudaGraph_t g = nullptr;
+      int nk = 0;
+      cudaError_t e = cudaStreamBeginCapture(c->gcap, cudaStreamCaptureModeRelaxed);
+      if (e == cudaSuccess) {
+        const cudaError_t el = issue(c->gcap, &nk);
+        const cudaError_t ec = cudaStreamEndCapture(c->gcap, &g);
+        e = el != cudaSuccess ? el : ec;
+      }
+      cudaGraphExec_t ex = nullptr;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(c, e, "basis graph capture");
+      c->bgraph[prec] = ex;
+      c->bkey[prec] = key;
+      c->bgraph_kernels[prec] = nk;
+    }
+  }
   cudaEvent_t e0, e1;
   SFB_CUDA(cudaEventCreate(&e0), "event");
   SFB_CUDA(cudaEventCreate(&e1), "event");
   SFB_CUDA(cudaEventRecord(e0, st), "event");
   cudaError_t e = cudaSuccess;
-  {
-    // one launch per size class: wide grids (nx > 64) on the context stream,
-    // narrow grids concurrently on a side stream joined before the epilogue
-    const int refine = prec == SFB_MIXED ? a.max_refine : 0;
-    auto launch = [&](const BasisArgs& aa, int mnx, int mcols, cudaStream_t s2) {
-      return prec == SFB_FP64 ? launch_basis_fp64(aa, mnx, mcols, s2) : launch_basis_mixed(aa, mnx, mcols, refine, s2);
-    };
-    BasisArgs aw = a, an = a;
-    aw.n_items = (int)c->n_wide;
-    an.item_sub = a.item_sub + c->n_wide;
-    an.item_k = a.item_k + c->n_wide;
-    an.n_items = n - (int)c->n_wide;
-    if (c->n_wide == 0) {
-      e = launch(an, c->narrow_nx, c->narrow_cols, st);
-      c->launches += 1;
-    } else if (an.n_items == 0) {
-      e = launch(aw, c->wide_nx, c->wide_cols, st);
-      c->launches += 1;
-    } else {
-      if (!c->side) SFB_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "stream");
-      if (!c->fork) SFB_CUDA(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming), "event");
-      if (!c->join) SFB_CUDA(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming), "event");
-      SFB_CUDA(cudaEventRecord(c->fork, st), "event");
-      SFB_CUDA(cudaStreamWaitEvent(c->side, c->fork, 0), "event");
-      e = launch(aw, c->wide_nx, c->wide_cols, st);
-      if (e == cudaSuccess) e = launch(an, c->narrow_nx, c->narrow_cols, c->side);
-      SFB_CUDA(cudaEventRecord(c->join, c->side), "event");
-      SFB_CUDA(cudaStreamWaitEvent(st, c->join, 0), "event");
-      c->launches += 2;
-    }
+  if (graph) {
+    e = cudaGraphLaunch(c->bgraph[prec], st);
+    c->launches += c->bgraph_kernels[prec];
+  } else {
+    int nk = 0;
+    e = issue(st, &nk);
+    c->launches += nk;
   }
+  c->last_build_graph = graph;
   if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_fail(c, e, "basis kernel"); }
   cudaEvent_t ek;
   SFB_CUDA(cudaEventCreate(&ek), "event");
@@ -811,6 +924,12 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
     }
     stats->flops_fp32 = f32;
     stats->flops_fp64 = f64;
+    for (int q = 0; q < 2; ++q) {
+      stats->launch_shape[q] = cls[q].n_items > 0 ? shp[q] : -1;
+      for (int v = 0; v < 4; ++v) stats->tune_ms[q][v] = c->btune_ms[prec][q][v];
+    }
+    stats->graph = graph ? 1 : 0;
+    stats->reserved = 0;
   }
   c->basis_done = true;
   c->basis_prec = prec;
@@ -818,6 +937,17 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   if (any & ST_NOT_SPD) return fail(c, SFB_ERR_NOT_SPD, "non-positive pivot in a block factorization");
   if (any & ST_TIMEOUT) return fail(c, SFB_ERR_TIMEOUT, "a bulk copy did not complete within the wait limit");
   if (any & ST_NOT_CONVERGED) return fail(c, SFB_ERR_NOT_CONVERGED, "iterative refinement stopped above tolerance");
+  return SFB_OK;
+}
+
+sfb_status sfb_basis_launch_shape(int32_t prec, int32_t wide, int32_t shape, int32_t* threads,
+                                  int32_t* ctas_per_sm, int32_t* g_buffers) {
+  if (prec < 0 || prec > 2 || (wide != 0 && wide != 1)) return SFB_ERR_ARG;
+  BasisShape d;
+  if (!basis_shape_desc(prec == SFB_FP64, wide, shape, &d)) return SFB_ERR_ARG;
+  if (threads) *threads = d.threads;
+  if (ctas_per_sm) *ctas_per_sm = d.min_ctas;
+  if (g_buffers) *g_buffers = d.g_buffers;
   return SFB_OK;
 }
 
@@ -950,6 +1080,27 @@ sfb_status sfb_set_option(sfb_ctx* c, const char* name, double value) {
   } else if (n == "cg_persistent") {
     if (!(value == 0 || value == 1)) return fail(c, SFB_ERR_ARG, "cg_persistent must be 0 or 1");
     c->opt_cg_persistent = (int)value;
+  } else if (n == "basis_autotune") {
+    if (!(value == 0 || value == 1)) return fail(c, SFB_ERR_ARG, "basis_autotune must be 0 or 1");
+    c->opt_basis_autotune = (int)value;
+    for (int p = 0; p < 3; ++p) {
+      c->btuned[p] = false;
+      c->bshape[p][0] = c->bshape[p][1] = 0;
+    }
+  } else if (n == "basis_shape") {
+    if (!(value >= 0 && value < 4 && value == (int)value)) return fail(c, SFB_ERR_ARG, "basis_shape must be 0..3");
+    const int v = (int)value;
+    if (v >= basis_shape_count(0) && v >= basis_shape_count(1))
+      return fail(c, SFB_ERR_ARG, "no precision has launch shape " + std::to_string(v));
+    c->opt_basis_autotune = 0;
+    for (int p = 0; p < 3; ++p) {
+      const int cnt = basis_shape_count(p == SFB_FP64);
+      c->bshape[p][0] = c->bshape[p][1] = v < cnt ? v : 0;
+      c->btuned[p] = true;
+    }
+  } else if (n == "basis_graph") {
+    if (!(value == 0 || value == 1)) return fail(c, SFB_ERR_ARG, "basis_graph must be 0 or 1");
+    c->opt_basis_graph = (int)value;
   } else if (n == "cg_replace_ratio") {
     if (!(value >= 1e-4 && value < 1)) return fail(c, SFB_ERR_ARG, "cg_replace_ratio must lie in [1e-4, 1)");
     c->opt_cg_replace = value;

@@ -138,4 +138,18 @@ cudaError_t launch_basis_mixed(const BasisArgs& a, int max_nx, int max_cols, int
                                cudaStream_t st);
 cudaError_t launch_flux_epilogue(const BasisArgs& a, int max_R, cudaStream_t st);
 
+// Launch shapes of the basis kernel per precision (fp64 0/1) and size class
+// (wide: grids more than 64 cells wide); the autotuner's candidates.
+struct BasisShape {
+  int threads;    // threads per CTA
+  int min_ctas;   // CTAs per SM the register budget is compiled for
+  int g_buffers;  // shared-memory buffers of G_b (2: the next block row is prefetched)
+};
+int basis_shape_count(int fp64);
+bool basis_shape_desc(int fp64, int wide, int shape, BasisShape* out);
+// Resident CTAs per SM of a shape at the class's largest grid and column count.
+cudaError_t basis_shape_ctas(int fp64, int wide, int shape, int max_nx, int max_cols, int* ctas);
+cudaError_t launch_basis_shape(const BasisArgs& a, int fp64, int wide, int shape, int max_nx, int max_cols,
+                               int refine, cudaStream_t st);
+
 }  // namespace sfb

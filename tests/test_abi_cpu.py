@@ -78,3 +78,27 @@ def test_workspace_size_grows_with_batch():
     b = s.workspace_bytes(sfb.FP64, 289)
     c = s.workspace_bytes(sfb.MIXED, 289)
     assert a < b and c < b
+
+
+def test_basis_launch_shapes_and_options():
+    """The launch-shape table the autotuner chooses from, and the options
+    that steer it, are host logic: no kernel runs."""
+    sfb = _lib()
+    assert sfb.basis_launch_shape(sfb.MIXED, 0, 0) == (256, 4, 1)
+    assert sfb.basis_launch_shape(sfb.MIXED, 0, 1) == (256, 3, 2)
+    assert sfb.basis_launch_shape(sfb.MIXED, 1, 0) == (256, 1, 2)
+    assert sfb.basis_launch_shape(sfb.MIXED, 1, 1) == (256, 2, 1)
+    assert sfb.basis_launch_shape(sfb.FP64, 0, 0) == (256, 2, 1)
+    assert sfb.basis_launch_shape(sfb.FP64, 1, 0) == (512, 1, 1)
+    assert sfb.basis_launch_shape(sfb.FP64, 0, 1) is None
+    assert sfb.basis_launch_shape(sfb.MIXED, 0, 2) is None
+    assert sfb.basis_launch_shape(sfb.MIXED, 0, -1) is None
+    assert sfb.basis_launch_shape(5, 0, 0) is None
+    s = sfb.Solver(W.tiny())
+    for name, ok, bad in (("basis_autotune", (0, 1), (2, -1)), ("basis_graph", (0, 1), (0.5, 3)),
+                          ("basis_shape", (0, 1), (2, 1.5, -1))):
+        for v in ok:
+            s.set_option(name, v)
+        for v in bad:
+            with pytest.raises(sfb.SfbError):
+                s.set_option(name, v)
