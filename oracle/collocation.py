@@ -3,7 +3,7 @@ local index conversion of Method S3 (Section 5.4, Step 4).
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-Readings:
+Readings of the paper taken here:
 
 * A3: the random variables are N(0,1) (Section 2.1), so the 1-D rules are the
   probabilists' Gauss-Hermite rules (zeros of He_m) with weights normalised

@@ -77,7 +77,7 @@ class Problem:
         for sub in self.subs:
             sub.finalize()
         self.stokes.finalize()
-        # KL regions: one per Darcy subdomain (Section 6 configs)
+        # KL regions: one per Darcy subdomain (as in the test cases of Section 6)
         klw = w["kl"]
         self.n_term = list(klw["n_term"])
         self.dims = collocation.region_dims(self.n_term)

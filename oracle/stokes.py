@@ -10,7 +10,7 @@ u.tau, v.tau>_{Gamma_sd}``, ``b(v, q) = -(div v, q)``, right-hand side
 sits above the Darcy region, so on the interface ``n = (0, -1)`` and
 ``tau = (1, 0)``.
 
-Readings: A6 boundary data (parabolic inflow on the left,
+Readings of the paper taken here: A6 boundary data (parabolic inflow on the left,
 no slip on top, zero stress on the right); A7 ``K_l = 1`` in the BJS term, so
 the Stokes basis is deterministic; A8 every rectangle is split along its
 SW-NE diagonal.

@@ -900,10 +900,11 @@ __global__ void flux_epilogue_kernel(BasisArgs a) {
 }
 
 // G buffers: two (prefetch of the next block row) where shared memory allows,
-// one where it would limit residency: the FP64 factor, and the FP32 factor of
-// grids up to 64 cells wide, which runs 4 CTAs per SM instead of 3 (648 items
-// of the precision workload in 1.07 waves instead of 1.42; measured 17.7 ms
-// against 18.0 ms, the lost prefetch and 64 registers included).
+// one where it would limit residency: the FP64 factor, and the default FP32
+// shape for grids up to 64 cells wide, which runs 4 CTAs per SM instead of 3
+// (648 items of 64x64 cells in 1.07 waves instead of 1.42; measured 17.8 ms
+// against 18.0 ms, the lost prefetch and 64 registers included). The
+// autotuner times both FP32 shapes of each size class (kShape below).
 template <typename T>
 size_t basis_smem(int max_nx, int max_cols, int gb) {
   const size_t cp = (max_cols + 3) & ~3;

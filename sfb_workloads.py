@@ -6,8 +6,8 @@ It holds none of the method's arithmetic, so both the CPU oracle (``oracle/``)
 and the CUDA path (``paper_1802_06263_gb300``) can consume it without sharing
 any computation.
 
-Geometry convention (the paper's test cases, Section 6, with the readings
-listed in DESIGN.md):
+Geometry convention (the paper's test cases, Section 6; where the paper is
+silent, the reading stated with each item):
 
 * The Darcy region ``darcy_box = (x0, x1, y0, y1)`` is tiled by a ``px x py``
   array of rectangular subdomains of equal size. Subdomain ``s = iy * px + ix``
