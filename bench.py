@@ -5,14 +5,17 @@ One step = the whole hot path over one batch: the stochastic basis for every
 block factorization, R+1 solves, flux projection) plus the interface CG for
 every global collocation point and the moment accumulation.
 
-Workload: 4x2 Darcy subdomains of 64x64 cells, N_term = 4 per region
-(81 local realizations each, 648 basis items), sigma^2 = 2, 8 linear mortar
-elements per edge (224 mortar DOFs), Smolyak level 2 over 32 dimensions
-(2,049 global points), Stokes 32x32 Taylor-Hood. Metric: collocation
+Default workload ("precision"): 4x2 Darcy subdomains of 64x64 cells,
+N_term = 4 per region (81 local realizations each, 648 basis items),
+sigma^2 = 2, 8 linear mortar elements per edge (224 mortar DOFs), Smolyak
+level 2 over 32 dimensions (2,049 global points), Stokes 32x32 Taylor-Hood.
+--workload tiny | medium | batched times the other workloads the same way
+(batched: its batch of the first 2,000 points). Metric: collocation
 realizations per second (mixed form: FP32 factor + FP64 refinement), with
 the FP64 form and the mortar flux responses per second beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME]
 """
 
 import argparse
@@ -157,12 +160,14 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    wl = W.ALL[WORKLOAD]()
+    wl = W.ALL[args.workload]()
     stream = torch.cuda.current_stream()
     s = sfb.Solver(wl, stream=stream)
-    s.allocate(sfb.FP64)            # the FP64 layout also holds the mixed form
     y, wt = s.points()
+    if wl.get("n_batch"):
+        y, wt = y[:wl["n_batch"]], wt[:wl["n_batch"]]
     n_pts = len(y)
+    s.allocate(sfb.FP64, max_pts=n_pts)   # the FP64 layout also holds the mixed form
     yd = torch.tensor(y, device="cuda")
     wd = torch.tensor(wt, device="cuda")
     lam_d = torch.empty((n_pts, s.n_lambda), dtype=torch.float64, device="cuda")
@@ -260,7 +265,8 @@ def run_ours(args):
     peaks = _peaks()
     rl_mixed = alu_roofline(st_mixed["flops_fp32"], st_mixed["flops_fp64"], k_mixed * 1e-3)
     rl_fp64 = alu_roofline(st_fp64["flops_fp32"], st_fp64["flops_fp64"], k_fp64 * 1e-3)
-    traffic = profiled_traffic("basis.cu", "basis_kernel_mixed_precision.md")
+    # the committed ncu summary covers the default workload's launch only
+    traffic = profiled_traffic("basis.cu", "basis_kernel_mixed_precision.md") if args.workload == WORKLOAD else None
     # the other steps of the mixed step, from algorithmic counts:
     # a11 (CG): 2 sum_u R_u^2 FP32 flops per point and iteration for the
     # products, 10 FP64 flops per mortar DOF for the update (the FP64 check
@@ -291,10 +297,8 @@ def run_ours(args):
         "metric": METRIC, "value": world * n_pts / (t_mixed * 1e-3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_mixed,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-        "data": "synthetic (seeded KL/Smolyak inputs of the precision workload; no paper datasets)",
-        "config": {"workload": "precision: 4x2 Darcy subdomains 64x64, N_term=4 (81 local), sigma^2=2, "
-                               "8 linear mortar elements/edge (224 DOFs), Smolyak L2 over 32 dims "
-                               "(2,049 points), Stokes 32x32",
+        "data": "synthetic (seeded KL/Smolyak inputs of the %s workload; no paper datasets)" % args.workload,
+        "config": {"workload": describe(wl, s, n_pts),
                    "n_points": n_pts, "n_basis_items": n_items, "flux_responses": fr,
                    "cg_rtol": rtol, "cg_preconditioner": "interface block-Jacobi (diagonal blocks of S^l per mortar interface)",
                    "l2": "working set larger than L2 (basis store %.2f GB)"
@@ -347,9 +351,26 @@ def basis_launch(sfb, prec, st):
     return out
 
 
-def cpu_baseline_sample(n_items=8, n_pts=24):
+def describe(wl, s, n_pts):
+    """One-line description of a workload with its sizes."""
+    if wl["name"] == "precision":
+        return ("precision: 4x2 Darcy subdomains 64x64, N_term=4 (81 local), sigma^2=2, "
+                "8 linear mortar elements/edge (224 DOFs), Smolyak L2 over 32 dims (2,049 points), Stokes 32x32")
+    grids = sorted(set(tuple(g) for g in wl["darcy_grid"]))
+    nt = sorted(set(wl["kl"]["n_term"]))
+    col = wl["collocation"]
+    cdesc = ("tensor %d-point" % col["m"]) if col["kind"] == "tensor" else ("Smolyak L%d" % col["lmax"])
+    return ("%s: %dx%d Darcy subdomains, grids %s, N_term %s, sigma^2=%g, %s mortars (%d DOFs), %s, "
+            "%d points, Stokes %dx%d" % (wl["name"], wl["px"], wl["py"], "/".join("%dx%d" % g for g in grids),
+                                          "/".join(map(str, nt)), wl["kl"]["sigma2"],
+                                          "linear" if wl["mortar_degree"] == 1 else "quadratic", s.n_lambda,
+                                          cdesc, n_pts, wl["stokes_grid"][0], wl["stokes_grid"][1]))
+
+
+def cpu_baseline_sample(n_items=16, n_pts=48, workload=WORKLOAD):
     """The oracle as it stands on a bounded sample of the workload, single
-    threaded, extrapolated linearly to the whole step."""
+    threaded, extrapolated linearly to the whole step (for the batched
+    workload, its batch of points)."""
     code = r"""
 import json, sys, time, numpy as np
 sys.path.insert(0, %r)
@@ -358,26 +379,32 @@ from oracle import coupled
 p = coupled.Problem(W.ALL[%r]())
 y, w = p.grid()
 t0 = time.perf_counter()
-items = 0
+items, basis_s = 0, 0.0
 for s in range(len(p.subs)):
     loc, _ = p.local_realizations(s, y)
-    for k in range(%d // len(p.subs)):
+    m = min(len(loc), max(1, %d // len(p.subs)))
+    ts = time.perf_counter()
+    for k in range(m):
         p.darcy_basis(s, loc[k]); items += 1
+    # this subdomain's items, extrapolated from its own sample
+    basis_s += (time.perf_counter() - ts) / m * len(loc)
 t1 = time.perf_counter()
-sel = np.linspace(0, len(y) - 1, %d).astype(int)
+nb = p.w.get("n_batch") or len(y)
+sel = np.unique(np.linspace(0, nb - 1, %d).astype(int))
 lams, mom = coupled.solve_all(p, y[sel], w[sel])
 t2 = time.perf_counter()
 n_items_total = sum(len(p.local_realizations(s, y)[0]) for s in range(len(p.subs)))
-# solve_all rebuilds the bases it needs; subtract that share
-print(json.dumps({"basis_s": t1 - t0, "items": items, "points_s": t2 - t1, "points": len(sel),
-                  "n_items_total": n_items_total, "n_pts": len(y)}))
-""" % (ROOT, WORKLOAD, n_items, n_pts)
+print(json.dumps({"basis_s": basis_s, "items": items, "points_s": t2 - t1, "points": len(sel),
+                  "n_items_total": n_items_total, "n_pts": nb}))
+""" % (ROOT, workload, n_items, n_pts)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0 or not r.stdout.strip():
+        raise RuntimeError("oracle sample failed for the %s workload:\n%s" % (workload, r.stderr[-2000:]))
     d = json.loads(r.stdout.strip().splitlines()[-1])
-    per_item = d["basis_s"] / d["items"]
-    # the points leg includes building the bases its points reference
-    t_step = per_item * d["n_items_total"] + d["points_s"] / d["points"] * d["n_pts"]
+    # basis_s is already the whole build, extrapolated per subdomain; the
+    # points leg includes building the bases its points reference
+    t_step = d["basis_s"] + d["points_s"] / d["points"] * d["n_pts"]
     return {"value": d["n_pts"] / t_step, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d of %d basis items and %d of %d points, single thread, extrapolated linearly"
                       % (d["items"], d["n_items_total"], d["points"], d["n_pts"]),
@@ -391,7 +418,7 @@ def run_reference(args):
     vals = []
     t0 = time.perf_counter()
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline_sample(n_items=8, n_pts=8)
+        cb = cpu_baseline_sample(n_items=8, n_pts=8, workload=args.workload)
         if i >= args.warmup:
             vals.append(cb)
     wall = time.perf_counter() - t0
@@ -401,7 +428,7 @@ def run_reference(args):
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["step_s_extrapolated"] * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "precision (same as the GPU arm)"},
+            "data": "synthetic", "config": {"workload": "%s (same as the GPU arm)" % args.workload},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
@@ -414,6 +441,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["tiny", "medium", WORKLOAD, "batched"])
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)
@@ -423,7 +451,7 @@ def main():
     out, rank = run_ours(args)
     if rank == 0:
         if not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline_sample()
+            out["cpu_baseline"] = cpu_baseline_sample(workload=args.workload)
         print(json.dumps(out))
 
 

@@ -1,0 +1,26 @@
+"""Host-side legs of the benchmark that need no GPU: the oracle's CPU
+baseline sample runs on every workload the benchmark accepts (each sampled
+subdomain has enough local realizations, the batched workload samples its
+batch), and the workload descriptions carry their sizes."""
+
+import pytest
+
+import sfb_workloads as W
+
+
+@pytest.mark.parametrize("workload", ["tiny", "medium", "batched"])
+def test_cpu_baseline_sample_runs_on_every_workload(workload):
+    import bench
+    cb = bench.cpu_baseline_sample(n_items=16, n_pts=4, workload=workload)
+    assert cb["value"] > 0 and cb["cores"] == 1 and cb["kind"] == "oracle"
+    n_batch = W.ALL[workload]().get("n_batch")
+    if n_batch:
+        assert ("of %d points" % n_batch) in cb["sample"]
+
+
+def test_reference_arm_names_the_workload():
+    import argparse
+    import bench
+    out = bench.run_reference(argparse.Namespace(warmup=0, steps=1, workload="tiny"))
+    assert out["impl"] == "reference" and out["config"]["workload"].startswith("tiny")
+    assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["value"] == out["cpu_baseline"]["value"]
