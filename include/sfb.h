@@ -106,13 +106,24 @@ typedef struct {
   double eta1, eta2;          /* correlation lengths                               */
   double mean_y;              /* E[Y]                                              */
   int32_t n_term;             /* kept modes: the n_term largest products           */
+  int32_t n_modes_x;          /* > 0 with n_modes_y > 0: keep instead the tensor  */
+  int32_t n_modes_y;          /* set of the n_modes_x largest 1-D modes in x      */
+                              /* times the n_modes_y largest in y (the paper's    */
+                              /* "N_term = 2 x 1" form, Section 6.1); n_term must */
+                              /* equal their product. Modes are ordered by        */
+                              /* decreasing eigenvalue, ties by (a + b, a). Both  */
+                              /* 0: the n_term largest products                   */
 } sfb_kl_region;
 
 /* Collocation (Section 4): tensor grid of m-point rules, or the Smolyak
  * combination formula of level lmax with 1-D rule sizes rule[p]
  * (n_rule == 0: the paper's 2^(p+1)-1). local_tensor = 1 builds every
- * region's basis on the full local tensor grid of the largest 1-D rule;
- * 0 on the distinct projections of the global grid. */
+ * region's basis on the full local tensor grid of the largest 1-D rule (of
+ * the region's own rules for an anisotropic tensor grid); 0 on the distinct
+ * projections of the global grid. m_dim (tensor only, nullable, host): the
+ * anisotropic tensor rule of Section 4.1, m_dim[kappa] points in global
+ * stochastic dimension kappa (sum of n_term entries, regions in order, each
+ * in [1, 32]); NULL: m points in every dimension. */
 typedef struct {
   int32_t kind;               /* 0 tensor, 1 Smolyak */
   int32_t m;
@@ -120,6 +131,7 @@ typedef struct {
   int32_t n_rule;
   const int32_t* rule;
   int32_t local_tensor;
+  const int32_t* m_dim;
 } sfb_collocation;
 
 typedef struct {

@@ -118,10 +118,22 @@ def smolyak_grid(n_dim, lmax, rule):
     return y, w
 
 
+def tensor_sizes(spec, n_dim):
+    """Points per global stochastic dimension of a tensor spec (Section 4.1):
+    an isotropic ``m``, or the anisotropic multi-index ``m`` given as one count
+    per dimension (``m(kappa(i, j)) = m(i, j)``, regions in order)."""
+    m = spec["m"]
+    if isinstance(m, (list, tuple)):
+        if len(m) != n_dim:
+            raise ValueError("anisotropic tensor rule of %d dims for %d stochastic dims" % (len(m), n_dim))
+        return [int(v) for v in m]
+    return [int(m)] * n_dim
+
+
 def global_grid(spec, n_dim):
     """Global collocation grid for a workload's ``collocation`` spec."""
     if spec["kind"] == "tensor":
-        return tensor_grid([spec["m"]] * n_dim)
+        return tensor_grid(tensor_sizes(spec, n_dim))
     if spec["kind"] == "smolyak":
         return smolyak_grid(n_dim, spec["lmax"], spec["rule"])
     raise ValueError(spec["kind"])
@@ -137,18 +149,22 @@ def region_dims(n_terms):
     return out
 
 
-def local_grid(spec, n_local):
+def local_grid(spec, n_local, dims=None):
     """The set of local realizations of one region (Section 5.4, Steps 1-2).
 
     ``spec["local"] == "tensor"`` (the workloads' reading): the full tensor
-    grid of the largest 1-D rule in the sequence over the region's dims (3^N
-    for the rule {1, 3, 3}), in lexicographic order. Otherwise ``None``: the
-    local set is the set of distinct projections of the global points, as in
-    the paper's own experiments (Section 6.1: 51 local points of 101)."""
+    grid over the region's dims, in lexicographic order. On a tensor grid it
+    uses the region's own 1-D rules (its entries of an anisotropic ``m``,
+    picked by the region's global dims ``dims``); on a sparse grid, the largest
+    1-D rule of the sequence (3^N for the rule {1, 3, 3}). Otherwise ``None``:
+    the local set is the set of distinct projections of the global points, as
+    in the paper's own experiments (Section 6.1: 51 local points of 101)."""
     if spec.get("local", "projections") != "tensor":
         return None
     if spec["kind"] == "tensor":
         m = spec["m"]
+        if isinstance(m, (list, tuple)):
+            return tensor_grid([int(m[d]) for d in dims])[0]
     else:
         m = max(rule_size(p, spec["rule"]) for p in range(spec["lmax"] + 1))
     return tensor_grid([m] * n_local)[0]

@@ -85,11 +85,12 @@ class Problem:
         self.kl = []
         for s, sub in enumerate(self.subs):
             xc, yc = sub.cell_centres()
-            lam, f = kl.kl_region_fields(sub.rect, klw["sigma2"], klw["eta"], self.n_term[s], xc, yc)
+            modes = (klw.get("modes") or [None] * len(self.n_term))[s]
+            lam, f = kl.kl_region_fields(sub.rect, klw["sigma2"], klw["eta"], self.n_term[s], xc, yc, modes)
             self.kl.append((lam, f))
         self.mean_y = klw["mean_Y"]
         spec = w["collocation"]
-        self.local_grids = [collocation.local_grid(spec, n) for n in self.n_term]
+        self.local_grids = [collocation.local_grid(spec, n, d) for n, d in zip(self.n_term, self.dims)]
         self._stokes_basis = None
         self.n_solves = np.zeros(len(self.subs) + 1, dtype=np.int64)
 

@@ -88,36 +88,48 @@ def kl_1d_eval(x, length, omega, parity):
     return out
 
 
-def kl_2d_modes(lx, ly, sigma2, eta, n_term):
-    """The ``n_term`` largest 2-D modes of Eq. 6.1 on an ``lx x ly`` region.
+def kl_2d_modes(lx, ly, sigma2, eta, n_term, modes=None):
+    """2-D modes of Eq. 6.1 on an ``lx x ly`` region.
 
     Separability gives eigenvalues ``sigma2 * lamx[a] * lamy[b]`` with
-    eigenfunctions ``fx_a(x) fy_b(y)``. The largest products are kept; ties
-    are broken by ``(a + b, a)`` (reading A2). Returns a list of
-    ``(lam, a, b)`` plus the 1-D data ``(omx, parx, omy, pary)``.
+    eigenfunctions ``fx_a(x) fy_b(y)``. Without ``modes`` the ``n_term``
+    largest products are kept (reading A2). With ``modes = (n1, n2)`` the
+    kept set is every product of the n1 largest 1-D modes in x with the n2
+    largest in y: the paper's ``N_term = n1 x n2`` form (Section 6.1, e.g.
+    "2 x 1 = 2"), so ``n_term`` must be ``n1 * n2``. Either way the kept modes
+    are ordered by decreasing eigenvalue with ties broken by ``(a + b, a)``.
+    Returns a list of ``(lam, a, b)`` plus the 1-D data
+    ``(omx, parx, omy, pary)``.
     """
-    omx, lamx, parx = kl_1d(lx, eta[0], n_term)
-    omy, lamy, pary = kl_1d(ly, eta[1], n_term)
+    if modes is None:
+        na = nb = n_term
+    else:
+        na, nb = modes
+        if na * nb != n_term:
+            raise ValueError("n1 x n2 mode set of %d modes, n_term %d" % (na * nb, n_term))
+    omx, lamx, parx = kl_1d(lx, eta[0], na)
+    omy, lamy, pary = kl_1d(ly, eta[1], nb)
     cand = []
-    for a in range(n_term):
-        for b in range(n_term):
+    for a in range(na):
+        for b in range(nb):
             cand.append((-(sigma2 * lamx[a] * lamy[b]), a + b, a, b))
     cand.sort()
-    modes = [(-c[0], c[2], c[3]) for c in cand[:n_term]]
-    return modes, (omx, parx, omy, pary)
+    out = [(-c[0], c[2], c[3]) for c in cand[:n_term]]
+    return out, (omx, parx, omy, pary)
 
 
-def kl_region_fields(rect, sigma2, eta, n_term, xc, yc):
+def kl_region_fields(rect, sigma2, eta, n_term, xc, yc, modes=None):
     """Eigenvalues and eigenfunction values of one KL region at points.
 
     ``rect = (x0, x1, y0, y1)`` is the region; ``xc, yc`` are physical point
     coordinates (the region's own cell centres, reading A11). Returns
     ``lam[n_term]`` and ``f[n_term, npts]`` with ``f_j = fx_a fy_b`` evaluated in
-    region-centred coordinates (Eq. 2.12 truncated as Eq. 2.13).
+    region-centred coordinates (Eq. 2.12 truncated as Eq. 2.13). ``modes``
+    selects an ``n1 x n2`` tensor set as in ``kl_2d_modes``.
     """
     x0, x1, y0, y1 = rect
     lx, ly = x1 - x0, y1 - y0
-    modes, (omx, parx, omy, pary) = kl_2d_modes(lx, ly, sigma2, eta, n_term)
+    modes, (omx, parx, omy, pary) = kl_2d_modes(lx, ly, sigma2, eta, n_term, modes)
     fx = kl_1d_eval(np.asarray(xc) - 0.5 * (x0 + x1), lx, omx, parx)
     fy = kl_1d_eval(np.asarray(yc) - 0.5 * (y0 + y1), ly, omy, pary)
     lam = np.array([m[0] for m in modes])

@@ -43,12 +43,14 @@ class Problem(ctypes.Structure):
 
 class KLRegion(ctypes.Structure):
     _fields_ = [("sigma2", ctypes.c_double), ("eta1", ctypes.c_double), ("eta2", ctypes.c_double),
-                ("mean_y", ctypes.c_double), ("n_term", ctypes.c_int32)]
+                ("mean_y", ctypes.c_double), ("n_term", ctypes.c_int32),
+                ("n_modes_x", ctypes.c_int32), ("n_modes_y", ctypes.c_int32)]
 
 
 class Collocation(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("m", ctypes.c_int32), ("lmax", ctypes.c_int32),
-                ("n_rule", ctypes.c_int32), ("rule", _i32p), ("local_tensor", ctypes.c_int32)]
+                ("n_rule", ctypes.c_int32), ("rule", _i32p), ("local_tensor", ctypes.c_int32),
+                ("m_dim", _i32p)]
 
 
 class BasisStats(ctypes.Structure):
@@ -201,13 +203,23 @@ class Solver:
             regs[s].eta1, regs[s].eta2 = kl["eta"]
             regs[s].mean_y = kl["mean_Y"]
             regs[s].n_term = kl["n_term"][s]
+            modes = (kl.get("modes") or [None] * self.n_darcy)[s]
+            if modes is not None:
+                regs[s].n_modes_x, regs[s].n_modes_y = modes
         self.n_dim = int(sum(kl["n_term"]))
         self.eigvals = np.zeros(self.n_dim)
         self._check(self.lib.sfb_kl_setup(self.h, regs, self.n_darcy, self.eigvals.ctypes.data))
         col = w["collocation"]
         C = Collocation()
         C.kind = 0 if col["kind"] == "tensor" else 1
-        C.m = col.get("m", 0)
+        m = col.get("m", 0)
+        if isinstance(m, (list, tuple)):
+            # anisotropic tensor rule: points per global stochastic dimension
+            m_dim = _i32(m)
+            self._keep.append(m_dim)
+            C.m_dim = m_dim.ctypes.data_as(_i32p)
+            m = 0
+        C.m = m
         C.lmax = col.get("lmax", 0)
         rule = col.get("rule", [])
         if rule == "paper":

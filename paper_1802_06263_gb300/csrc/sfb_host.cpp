@@ -404,17 +404,24 @@ sfb_status sfb_kl_setup(sfb_ctx* c, const sfb_kl_region* regions, int32_t n_regi
     const sfb_kl_region& r = regions[s];
     if (r.n_term < 1 || r.n_term > 64 || !(r.sigma2 >= 0) || !(r.eta1 > 0) || !(r.eta2 > 0))
       return fail(c, SFB_ERR_ARG, "bad KL region");
+    const bool tensor_set = r.n_modes_x > 0 || r.n_modes_y > 0;
+    if (tensor_set && (r.n_modes_x < 1 || r.n_modes_y < 1 || r.n_modes_x * r.n_modes_y != r.n_term))
+      return fail(c, SFB_ERR_ARG, "KL region: n_modes_x * n_modes_y must equal n_term");
     HostSub& S = c->subs[s];
     S.n_term = r.n_term; S.sigma2 = r.sigma2; S.eta1 = r.eta1; S.eta2 = r.eta2; S.mean_y = r.mean_y;
     const double Lx = S.x1 - S.x0, Ly = S.y1 - S.y0;
+    // candidate 1-D modes per direction: all n_term of each (largest
+    // products), or exactly n_modes_x and n_modes_y (tensor set)
+    const int na = tensor_set ? r.n_modes_x : r.n_term, nb = tensor_set ? r.n_modes_y : r.n_term;
     std::vector<double> omx, lx, omy, ly;
     std::vector<int> parx, pary;
-    kl_1d_host(Lx, r.eta1, r.n_term, omx, lx, parx);
-    kl_1d_host(Ly, r.eta2, r.n_term, omy, ly, pary);
-    // the n_term largest products, ties broken by (a + b, a)
+    kl_1d_host(Lx, r.eta1, na, omx, lx, parx);
+    kl_1d_host(Ly, r.eta2, nb, omy, ly, pary);
+    // by decreasing eigenvalue, ties broken by (a + b, a); the first n_term
+    // are kept (all of them for a tensor set)
     std::vector<std::tuple<double, int, int>> cand;
-    for (int a = 0; a < r.n_term; ++a)
-      for (int b = 0; b < r.n_term; ++b) cand.emplace_back(r.sigma2 * lx[a] * ly[b], a, b);
+    for (int a = 0; a < na; ++a)
+      for (int b = 0; b < nb; ++b) cand.emplace_back(r.sigma2 * lx[a] * ly[b], a, b);
     std::stable_sort(cand.begin(), cand.end(), [](const auto& p, const auto& q) {
       if (std::get<0>(p) != std::get<0>(q)) return std::get<0>(p) > std::get<0>(q);
       const int sp = std::get<1>(p) + std::get<2>(p), sq = std::get<1>(q) + std::get<2>(q);
@@ -453,12 +460,21 @@ sfb_status sfb_collocation_setup(sfb_ctx* c, const sfb_collocation* spec, int64_
     if (!spec->rule) return fail(c, SFB_ERR_ARG, "rule missing");
     rule.assign(spec->rule, spec->rule + spec->n_rule);
   }
+  // points per global dimension of a tensor grid (Section 4.1: isotropic m,
+  // or the anisotropic multi-index m_dim)
+  std::vector<int> ms;
   if (spec->kind == 0) {
-    if (spec->m < 1 || spec->m > 32) return fail(c, SFB_ERR_ARG, "bad tensor rule size");
-    double npts = std::pow((double)spec->m, n_dim);
+    if (spec->m_dim) ms.assign(spec->m_dim, spec->m_dim + n_dim);
+    else ms.assign(n_dim, spec->m);
+    double npts = 1.0;
+    for (int m : ms) {
+      if (m < 1 || m > 32) return fail(c, SFB_ERR_ARG, "bad tensor rule size");
+      npts *= m;
+    }
     if (npts > 5e7) return fail(c, SFB_ERR_UNSUPPORTED, "tensor grid too large");
-    tensor_grid_host(std::vector<int>(n_dim, spec->m), c->grid);
+    tensor_grid_host(ms, c->grid);
   } else if (spec->kind == 1) {
+    if (spec->m_dim) return fail(c, SFB_ERR_ARG, "m_dim applies to tensor grids only");
     if (spec->lmax < 0 || spec->lmax > 6) return fail(c, SFB_ERR_ARG, "bad Smolyak level");
     smolyak_grid_host(n_dim, spec->lmax, rule, c->grid);
   } else {
@@ -471,11 +487,18 @@ sfb_status sfb_collocation_setup(sfb_ctx* c, const sfb_collocation* spec, int64_
   for (int s = 0; s < ns; ++s) {
     const int nt = c->subs[s].n_term;
     if (spec->local_tensor) {
-      int m = spec->kind == 0 ? spec->m : 1;
-      if (spec->kind == 1)
+      // the region's own rules on a tensor grid; the largest 1-D rule of the
+      // sequence on a Smolyak grid
+      std::vector<int> lm;
+      if (spec->kind == 0) {
+        lm.assign(ms.begin() + c->dim_off[s], ms.begin() + c->dim_off[s] + nt);
+      } else {
+        int m = 1;
         for (int p = 0; p <= spec->lmax; ++p) m = std::max(m, rule_size_host(p, rule));
+        lm.assign(nt, m);
+      }
       Grid lg;
-      tensor_grid_host(std::vector<int>(nt, m), lg);
+      tensor_grid_host(lm, lg);
       if (lg.n_pts() > 1000000) return fail(c, SFB_ERR_UNSUPPORTED, "local tensor grid too large");
       c->loc_y[s] = lg.y;
       c->n_local[s] = (int)lg.n_pts();

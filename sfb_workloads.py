@@ -133,5 +133,20 @@ def small_test(nx=12, ny=10, px=2, py=2, n_sd=3, n_dd=2, n_term=2, degree=1,
     return w
 
 
+def anisotropic():
+    """Two 10x6 Darcy subdomains whose KL regions keep the paper's n1 x n2
+    mode sets (2 x 1 and 2 x 2, as written in Section 6.1), on an anisotropic
+    tensor grid (Section 4.1) with 2, 1, 3, 1, 2, 2 points in the six
+    stochastic dimensions (24 global points; 2 and 12 local ones). A 1-point
+    rule fixes its dimension at the mean."""
+    w = small_test(nx=10, ny=6, px=2, py=1, n_sd=2, n_dd=2, n_term=2, degree=1, stokes=(6, 5),
+                   sigma2=1.5, eta=(0.3, 0.15),
+                   collocation={"kind": "tensor", "m": [2, 1, 3, 1, 2, 2], "local": "tensor"},
+                   name="anisotropic")
+    w["kl"]["n_term"] = [2, 4]
+    w["kl"]["modes"] = [(2, 1), (2, 2)]
+    return w
+
+
 ALL = {"tiny": tiny, "medium": medium, "precision": precision,
-       "batched": batched, "large": large}
+       "batched": batched, "large": large, "anisotropic": anisotropic}

@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, n), n
 
 
-@pytest.mark.parametrize("name", ["tiny", "medium", "batched"])
+@pytest.mark.parametrize("name", ["tiny", "medium", "batched", "anisotropic"])
 def test_host_setup_matches_oracle(name):
     sfb = _lib()
     from oracle import coupled

@@ -137,3 +137,43 @@ def test_paper_counts(row):
     assert (s3 - 2 * nreal) % nloc == 0
     r_from_s3 = (s3 - 2 * nreal) // nloc
     assert r_from_s2 == r_from_s3
+
+
+def test_anisotropic_tensor_rule():
+    """Section 4.1's anisotropic tensor rule with m = (2, 1, 3, 4) points per
+    dimension: Prod m points with weights summing to one, and in each
+    dimension the moments of that dimension's own Gauss-Hermite rule, which
+    are closed forms: the 1-point rule sits at the mean (E[y^2] = 0), the
+    2-point rule at +-1 (E[y^4] = 1), the 3-point rule at {0, +-sqrt 3} with
+    weights {2/3, 1/6, 1/6} (E[y^4] = 3, E[y^6] = 9), and the 4-point rule is
+    exact to degree 7 (E[y^6] = 15). A reversed or shifted m fails these."""
+    spec = {"kind": "tensor", "m": [2, 1, 3, 4]}
+    y, w = collocation.global_grid(spec, 4)
+    assert y.shape == (24, 4) and abs(w.sum() - 1.0) < 1e-15
+    E = lambda f: float(np.dot(w, f))           # noqa: E731
+    assert abs(E(y[:, 0] ** 2) - 1) < 1e-14 and abs(E(y[:, 0] ** 4) - 1) < 1e-14
+    assert abs(E(y[:, 1] ** 2)) < 1e-15
+    assert abs(E(y[:, 2] ** 4) - 3) < 1e-13 and abs(E(y[:, 2] ** 6) - 9) < 1e-12
+    assert abs(E(y[:, 3] ** 6) - 15) < 1e-12
+    assert abs(E(y[:, 0] ** 2 * y[:, 3] ** 2) - 1) < 1e-14
+    iso = collocation.global_grid({"kind": "tensor", "m": 3}, 2)
+    aniso = collocation.global_grid({"kind": "tensor", "m": [3, 3]}, 2)
+    assert np.array_equal(iso[0], aniso[0]) and np.array_equal(iso[1], aniso[1])
+    with pytest.raises(ValueError):
+        collocation.global_grid(spec, 3)
+
+
+def test_anisotropic_local_grids_are_the_projections():
+    """On an anisotropic tensor grid each region's local tensor grid (its own
+    rules) is exactly the set of distinct projections of the global points,
+    and every global point maps onto it (Section 5.4 Step 4)."""
+    spec = {"kind": "tensor", "m": [2, 1, 3, 1, 2, 2], "local": "tensor"}
+    dims = collocation.region_dims([2, 4])
+    y, _ = collocation.global_grid(spec, 6)
+    for d, count in zip(dims, (2, 12)):
+        grid = collocation.local_grid(spec, len(d), d)
+        assert len(grid) == count
+        loc, kmap = collocation.local_points(y, d, grid)
+        assert np.allclose(loc[kmap], y[:, d], atol=1e-15)
+        proj = {tuple(np.round(r, 12)) for r in y[:, d]}
+        assert proj == {tuple(np.round(r, 12)) for r in grid}

@@ -120,3 +120,34 @@ def test_log_permeability_linear_in_y():
     y = np.array([1.0, -2.0])
     expect = 0.3 + math.sqrt(0.5) * f[0] * 1.0 + math.sqrt(0.25) * f[1] * -2.0
     assert np.allclose(kl.log_permeability(lam, f, y, 0.3), expect)
+
+
+def test_tensor_mode_sets_of_the_paper():
+    """The paper's "N_term = n1 x n2" mode sets (Section 6.1). On a KL region
+    the kept set is the full product of the n1 leading x-modes and the n2
+    leading y-modes, so (i) the pointwise variance of the truncated field
+    factorises into the two 1-D truncated variances and the eigenvalue sum
+    into the two 1-D sums, and (ii) in "2 x 1" both modes share the leading
+    y-mode: the ratio f_1 / f_0 does not depend on y. A selection by largest
+    products, or n1 and n2 swapped, fails (i) or (ii) on this region."""
+    rect, sigma2, eta = (0.0, 1.0, 0.0, 0.4), 1.0, (0.1, 0.1)   # Case 1, KL region 1
+    lx, ly = 1.0, 0.4
+    xs = np.linspace(0.03, 0.97, 7)
+    ys = np.linspace(0.01, 0.39, 5)
+    X, Y = np.meshgrid(xs, ys, indexing="ij")
+    for n1, n2 in ((2, 1), (3, 3), (1, 4)):
+        lam, f = kl.kl_region_fields(rect, sigma2, eta, n1 * n2, X.ravel(), Y.ravel(), modes=(n1, n2))
+        omx, lamx, parx = kl.kl_1d(lx, eta[0], n1)
+        omy, lamy, pary = kl.kl_1d(ly, eta[1], n2)
+        assert abs(lam.sum() - sigma2 * lamx.sum() * lamy.sum()) < 1e-14
+        assert np.all(np.diff(lam) <= 0)
+        vx = (lamx[:, None] * kl.kl_1d_eval(xs - 0.5, lx, omx, parx) ** 2).sum(0)
+        vy = (lamy[:, None] * kl.kl_1d_eval(ys - 0.2, ly, omy, pary) ** 2).sum(0)
+        var = (lam[:, None] * f ** 2).sum(0).reshape(X.shape)
+        assert np.allclose(var, sigma2 * vx[:, None] * vy[None, :], rtol=1e-13, atol=0)
+    lam, f = kl.kl_region_fields(rect, sigma2, eta, 2, X.ravel(), Y.ravel(), modes=(2, 1))
+    ratio = (f[1] / f[0]).reshape(X.shape)
+    assert np.allclose(ratio, ratio[:, :1], rtol=1e-12, atol=1e-12)
+    assert np.ptp(ratio[:, 0]) > 0.1            # and it does depend on x
+    with pytest.raises(ValueError):
+        kl.kl_2d_modes(lx, ly, sigma2, eta, 3, modes=(2, 2))
