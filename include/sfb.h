@@ -198,12 +198,39 @@ sfb_status sfb_field_size(const sfb_ctx* ctx, int32_t field, int64_t* n);
 sfb_status sfb_kl_setup(sfb_ctx* ctx, const sfb_kl_region* regions, int32_t n_regions,
                         double* eigvals_out);
 
+/* The same on KL regions that may each cover several Darcy subdomains
+ * (Section 2.1: the Darcy region is split into statistically independent KL
+ * regions, each a union of subdomains; the paper's Case 1, Section 6.1, has
+ * two regions of two subdomains each). Region r is regions[r] on the
+ * rectangle rects[4r .. 4r+3] = (x0, x1, y0, y1); region_of[s] (length: the
+ * Darcy subdomain count) is subdomain s's region, and the subdomain must lie
+ * inside it. Every region needs at least one subdomain. The modes are those
+ * of the region's rectangle, evaluated at each subdomain's cell centres in
+ * the region's centred coordinates. Region r's stochastic dimensions follow
+ * those of regions 0..r-1, and all subdomains of a region share its local
+ * realizations. eigvals_out (nullable, host) receives sum(n_term) eigenvalues,
+ * region by region. SFB_ERR_ARG on an empty region, a subdomain outside its
+ * region or a bad region. sfb_kl_setup is this call with one region per
+ * subdomain on the subdomain's own rectangle. All arrays are host memory. */
+sfb_status sfb_kl_setup_regions(sfb_ctx* ctx, const sfb_kl_region* regions, int32_t n_regions,
+                                const double* rects, const int32_t* region_of, double* eigvals_out);
+
 /* Global grid (Section 4.1 / 4.2) and every region's local realizations
  * (Section 5.4 Steps 1-2). n_pts_out receives the global point count. */
 sfb_status sfb_collocation_setup(sfb_ctx* ctx, const sfb_collocation* spec, int64_t* n_pts_out);
 /* Copies the global grid to host buffers y_out [n_pts x n_dim] and w_out [n_pts]. */
 sfb_status sfb_collocation_points(const sfb_ctx* ctx, double* y_out, double* w_out);
-/* Local realization count and coordinates [n_local x n_term] of a region. */
+/* Read-back of the KL tables that the basis kernel evaluates for Darcy
+ * subdomain `sub` (set-up data of Eq. 2.13, no realization): sqrt_lambda
+ * [n_term], and the 1-D eigenfunction factors at the subdomain's cell
+ * centres, fx [n_term x nx] and fy [n_term x ny], so that mode j at cell
+ * (ix, iy) is fx[j][ix] * fy[j][iy]. Host buffers, each nullable.
+ * SFB_ERR_STATE before sfb_kl_setup. */
+sfb_status sfb_kl_tables(const sfb_ctx* ctx, int32_t sub, double* sqrt_lambda, double* fx, double* fy);
+
+/* Local realization count and coordinates [n_local x n_term] of the KL region
+ * of Darcy subdomain `region` (its own region unless sfb_kl_setup_regions
+ * gave it a shared one; the items of the subdomain are these realizations). */
 sfb_status sfb_local_points(const sfb_ctx* ctx, int32_t region, int32_t* n_local, double* y_out);
 
 /* Device bytes needed for precision `prec` and batches of up to max_pts

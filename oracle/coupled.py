@@ -77,16 +77,23 @@ class Problem:
         for sub in self.subs:
             sub.finalize()
         self.stokes.finalize()
-        # KL regions: one per Darcy subdomain (as in the test cases of Section 6)
+        # KL regions (Section 2.1): statistically independent, each a union of
+        # subdomains. By default one per Darcy subdomain; a workload may give
+        # region rectangles ("regions") and each subdomain's region
+        # ("region_of"), as in Case 1 of Section 6.1 (two regions of two
+        # subdomains). n_term, modes and the stochastic dims are per region.
         klw = w["kl"]
         self.n_term = list(klw["n_term"])
+        rects = klw.get("regions") or [sub.rect for sub in self.subs]
+        self.region_of = list(klw.get("region_of") or range(len(self.subs)))
         self.dims = collocation.region_dims(self.n_term)
         self.n_dim = sum(self.n_term)
         self.kl = []
         for s, sub in enumerate(self.subs):
+            r = self.region_of[s]
             xc, yc = sub.cell_centres()
-            modes = (klw.get("modes") or [None] * len(self.n_term))[s]
-            lam, f = kl.kl_region_fields(sub.rect, klw["sigma2"], klw["eta"], self.n_term[s], xc, yc, modes)
+            modes = (klw.get("modes") or [None] * len(self.n_term))[r]
+            lam, f = kl.kl_region_fields(rects[r], klw["sigma2"], klw["eta"], self.n_term[r], xc, yc, modes)
             self.kl.append((lam, f))
         self.mean_y = klw["mean_Y"]
         spec = w["collocation"]
@@ -101,10 +108,11 @@ class Problem:
     def local_realizations(self, s, ys):
         """Local realizations of subdomain ``s``'s KL region and the map from
         the global points ``ys`` to them (Section 5.4, Steps 1-2 and 4)."""
-        return collocation.local_points(np.asarray(ys), self.dims[s], self.local_grids[s])
+        r = self.region_of[s]
+        return collocation.local_points(np.asarray(ys), self.dims[r], self.local_grids[r])
 
     def local_y(self, s, y_global):
-        return np.asarray(y_global)[self.dims[s]]
+        return np.asarray(y_global)[self.dims[self.region_of[s]]]
 
     def permeability(self, s, y_local):
         lam, f = self.kl[s]

@@ -73,6 +73,10 @@ _SIGS = {
     "sfb_subdomain_dofs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, _i32p, ctypes.c_void_p]),
     "sfb_field_size": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]),
     "sfb_kl_setup": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(KLRegion), ctypes.c_int32, ctypes.c_void_p]),
+    "sfb_kl_tables": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p]),
+    "sfb_kl_setup_regions": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(KLRegion), ctypes.c_int32,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "sfb_collocation_setup": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Collocation),
                                              ctypes.POINTER(ctypes.c_int64)]),
     "sfb_collocation_points": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -197,18 +201,28 @@ class Solver:
         self.lib.sfb_sizes(self.h, ctypes.byref(n_l), ctypes.byref(n_d))
         self.n_lambda, self.n_darcy = n_l.value, n_d.value
         kl = w["kl"]
-        regs = (KLRegion * self.n_darcy)()
-        for s in range(self.n_darcy):
-            regs[s].sigma2 = kl["sigma2"]
-            regs[s].eta1, regs[s].eta2 = kl["eta"]
-            regs[s].mean_y = kl["mean_Y"]
-            regs[s].n_term = kl["n_term"][s]
-            modes = (kl.get("modes") or [None] * self.n_darcy)[s]
+        # KL regions: one per Darcy subdomain, or the workload's rectangles
+        # ("regions") with each subdomain's region ("region_of")
+        n_reg = len(kl["n_term"])
+        regs = (KLRegion * n_reg)()
+        for r in range(n_reg):
+            regs[r].sigma2 = kl["sigma2"]
+            regs[r].eta1, regs[r].eta2 = kl["eta"]
+            regs[r].mean_y = kl["mean_Y"]
+            regs[r].n_term = kl["n_term"][r]
+            modes = (kl.get("modes") or [None] * n_reg)[r]
             if modes is not None:
-                regs[s].n_modes_x, regs[s].n_modes_y = modes
+                regs[r].n_modes_x, regs[r].n_modes_y = modes
         self.n_dim = int(sum(kl["n_term"]))
         self.eigvals = np.zeros(self.n_dim)
-        self._check(self.lib.sfb_kl_setup(self.h, regs, self.n_darcy, self.eigvals.ctypes.data))
+        if kl.get("regions"):
+            rects = np.ascontiguousarray(np.asarray(kl["regions"], dtype=np.float64).reshape(n_reg, 4))
+            region_of = _i32(kl["region_of"])
+            self._keep += [rects, region_of]
+            self._check(self.lib.sfb_kl_setup_regions(self.h, regs, n_reg, rects.ctypes.data, region_of.ctypes.data,
+                                                      self.eigvals.ctypes.data))
+        else:
+            self._check(self.lib.sfb_kl_setup(self.h, regs, n_reg, self.eigvals.ctypes.data))
         col = w["collocation"]
         C = Collocation()
         C.kind = 0 if col["kind"] == "tensor" else 1
@@ -266,11 +280,24 @@ class Solver:
         self._check(self.lib.sfb_collocation_points(self.h, y.ctypes.data, w.ctypes.data))
         return y, w
 
-    def local_points(self, region):
+    def kl_tables(self, sub):
+        """(sqrt(lambda) [n_term], fx [n_term x nx], fy [n_term x ny]) that the
+        basis kernel evaluates for Darcy subdomain ``sub``."""
+        kl = self.w["kl"]
+        nt = kl["n_term"][(kl.get("region_of") or list(range(self.n_darcy)))[sub]]
+        nx, ny = self.w["darcy_grid"][sub]
+        sl, fx, fy = np.zeros(nt), np.zeros((nt, nx)), np.zeros((nt, ny))
+        self._check(self.lib.sfb_kl_tables(self.h, sub, sl.ctypes.data, fx.ctypes.data, fy.ctypes.data))
+        return sl, fx, fy
+
+    def local_points(self, sub):
+        """Local realizations [n_local x n_term] of Darcy subdomain ``sub``'s KL region."""
+        kl = self.w["kl"]
+        region = (kl.get("region_of") or list(range(self.n_darcy)))[sub]
         n = ctypes.c_int32()
-        self._check(self.lib.sfb_local_points(self.h, region, ctypes.byref(n), None))
-        y = np.zeros((n.value, self.w["kl"]["n_term"][region]))
-        self._check(self.lib.sfb_local_points(self.h, region, ctypes.byref(n), y.ctypes.data))
+        self._check(self.lib.sfb_local_points(self.h, sub, ctypes.byref(n), None))
+        y = np.zeros((n.value, kl["n_term"][region]))
+        self._check(self.lib.sfb_local_points(self.h, sub, ctypes.byref(n), y.ctypes.data))
         return y
 
     # ---- workspace and the hot path ------------------------------------------------------

@@ -119,7 +119,7 @@ struct Dev {
   int* pcg_part = nullptr;    // persistent CG: per-CTA ranges of resident tiles
   int64_t* s_gdof = nullptr;  // Stokes local -> global mortar DOF
   int64_t* ybase = nullptr;   // per unit offset into a point's Y row
-  int* dim_off = nullptr;     // per region first stochastic dimension
+  int* dim_off = nullptr;     // per subdomain: its KL region's first stochastic dimension
   int64_t* loc_off = nullptr; // per region offset into grp_count / grp_start
   int64_t* cell_off = nullptr;// per subdomain first cell in the Darcy pressure field
   int64_t* face_off = nullptr;// per subdomain first face in the Darcy flux field
@@ -159,7 +159,9 @@ struct sfb_ctx {
   sfb::Grid grid;
   std::vector<std::vector<double>> loc_y;  // per region [n_local][nt]
   std::vector<int> n_local;
-  std::vector<int> dim_off;                // kappa(i, 0) per region
+  std::vector<int> dim_off;                // kappa(i, 0) of each subdomain's KL region
+  std::vector<int> region_of;              // KL region of each Darcy subdomain
+  int n_regions = 0;
   // workspace
   char* ws = nullptr;
   size_t ws_bytes = 0;

@@ -396,65 +396,125 @@ sfb_status sfb_field_size(const sfb_ctx* c, int32_t field, int64_t* n) {
   return SFB_OK;
 }
 
-sfb_status sfb_kl_setup(sfb_ctx* c, const sfb_kl_region* regions, int32_t n_regions, double* eig) {
+sfb_status sfb_kl_setup_regions(sfb_ctx* c, const sfb_kl_region* regions, int32_t n_regions, const double* rects,
+                                const int32_t* region_of, double* eig) {
   if (!c) return SFB_ERR_ARG;
-  if (!regions || n_regions != (int)c->subs.size()) return fail(c, SFB_ERR_ARG, "one KL region per Darcy subdomain");
+  const int ns = (int)c->subs.size();
+  if (!regions || !rects || !region_of || n_regions < 1 || n_regions > ns)
+    return fail(c, SFB_ERR_ARG, "KL regions: 1..n_darcy regions with rectangles and a region per subdomain");
+  std::vector<int> members(n_regions, 0);
+  for (int s = 0; s < ns; ++s) {
+    const int r = region_of[s];
+    if (r < 0 || r >= n_regions) return fail(c, SFB_ERR_ARG, "KL regions: subdomain without a valid region");
+    const double* R = rects + 4 * r;
+    const HostSub& S = c->subs[s];
+    const double tol = 1e-12 * std::max(1.0, std::max(std::fabs(R[1] - R[0]), std::fabs(R[3] - R[2])));
+    if (!(R[1] > R[0]) || !(R[3] > R[2]) || S.x0 < R[0] - tol || S.x1 > R[1] + tol || S.y0 < R[2] - tol ||
+        S.y1 > R[3] + tol)
+      return fail(c, SFB_ERR_ARG, "KL regions: subdomain " + std::to_string(s) + " is not inside its region");
+    ++members[r];
+  }
+  for (int r = 0; r < n_regions; ++r)
+    if (!members[r]) return fail(c, SFB_ERR_ARG, "KL regions: region " + std::to_string(r) + " has no subdomain");
+  // per region: the kept 2-D modes (eigenvalue, x index, y index) and the 1-D data
+  struct RegionModes {
+    std::vector<std::tuple<double, int, int>> modes;
+    std::vector<double> omx, omy;
+    std::vector<int> parx, pary;
+  };
+  std::vector<RegionModes> rm(n_regions);
   int64_t w = 0;
-  for (int s = 0; s < n_regions; ++s) {
-    const sfb_kl_region& r = regions[s];
+  for (int q = 0; q < n_regions; ++q) {
+    const sfb_kl_region& r = regions[q];
     if (r.n_term < 1 || r.n_term > 64 || !(r.sigma2 >= 0) || !(r.eta1 > 0) || !(r.eta2 > 0))
       return fail(c, SFB_ERR_ARG, "bad KL region");
     const bool tensor_set = r.n_modes_x > 0 || r.n_modes_y > 0;
     if (tensor_set && (r.n_modes_x < 1 || r.n_modes_y < 1 || r.n_modes_x * r.n_modes_y != r.n_term))
       return fail(c, SFB_ERR_ARG, "KL region: n_modes_x * n_modes_y must equal n_term");
-    HostSub& S = c->subs[s];
-    S.n_term = r.n_term; S.sigma2 = r.sigma2; S.eta1 = r.eta1; S.eta2 = r.eta2; S.mean_y = r.mean_y;
-    const double Lx = S.x1 - S.x0, Ly = S.y1 - S.y0;
+    const double Lx = rects[4 * q + 1] - rects[4 * q], Ly = rects[4 * q + 3] - rects[4 * q + 2];
     // candidate 1-D modes per direction: all n_term of each (largest
     // products), or exactly n_modes_x and n_modes_y (tensor set)
     const int na = tensor_set ? r.n_modes_x : r.n_term, nb = tensor_set ? r.n_modes_y : r.n_term;
-    std::vector<double> omx, lx, omy, ly;
-    std::vector<int> parx, pary;
-    kl_1d_host(Lx, r.eta1, na, omx, lx, parx);
-    kl_1d_host(Ly, r.eta2, nb, omy, ly, pary);
+    std::vector<double> lx, ly;
+    kl_1d_host(Lx, r.eta1, na, rm[q].omx, lx, rm[q].parx);
+    kl_1d_host(Ly, r.eta2, nb, rm[q].omy, ly, rm[q].pary);
     // by decreasing eigenvalue, ties broken by (a + b, a); the first n_term
     // are kept (all of them for a tensor set)
-    std::vector<std::tuple<double, int, int>> cand;
+    std::vector<std::tuple<double, int, int>>& cand = rm[q].modes;
     for (int a = 0; a < na; ++a)
       for (int b = 0; b < nb; ++b) cand.emplace_back(r.sigma2 * lx[a] * ly[b], a, b);
-    std::stable_sort(cand.begin(), cand.end(), [](const auto& p, const auto& q) {
-      if (std::get<0>(p) != std::get<0>(q)) return std::get<0>(p) > std::get<0>(q);
-      const int sp = std::get<1>(p) + std::get<2>(p), sq = std::get<1>(q) + std::get<2>(q);
+    std::stable_sort(cand.begin(), cand.end(), [](const auto& p, const auto& q2) {
+      if (std::get<0>(p) != std::get<0>(q2)) return std::get<0>(p) > std::get<0>(q2);
+      const int sp = std::get<1>(p) + std::get<2>(p), sq = std::get<1>(q2) + std::get<2>(q2);
       if (sp != sq) return sp < sq;
-      return std::get<1>(p) < std::get<1>(q);
+      return std::get<1>(p) < std::get<1>(q2);
     });
+    cand.resize(r.n_term);
+    for (int j = 0; j < r.n_term; ++j)
+      if (eig) eig[w++] = std::get<0>(cand[j]);
+  }
+  // every subdomain evaluates its region's modes at its own cell centres, in
+  // the region's centred coordinates
+  for (int s = 0; s < ns; ++s) {
+    const int q = region_of[s];
+    const sfb_kl_region& r = regions[q];
+    const double* R = rects + 4 * q;
+    const double Lx = R[1] - R[0], Ly = R[3] - R[2], cx = 0.5 * (R[0] + R[1]), cy = 0.5 * (R[2] + R[3]);
+    HostSub& S = c->subs[s];
+    S.n_term = r.n_term; S.sigma2 = r.sigma2; S.eta1 = r.eta1; S.eta2 = r.eta2; S.mean_y = r.mean_y;
     S.lam.assign(r.n_term, 0.0); S.slam.assign(r.n_term, 0.0);
     S.fx.assign((size_t)r.n_term * S.nx, 0.0); S.fy.assign((size_t)r.n_term * S.ny, 0.0);
-    const double cx = 0.5 * (S.x0 + S.x1), cy = 0.5 * (S.y0 + S.y1);
     for (int j = 0; j < r.n_term; ++j) {
-      const int a = std::get<1>(cand[j]), b = std::get<2>(cand[j]);
-      S.lam[j] = std::get<0>(cand[j]);
+      const auto& md = rm[q].modes[j];
+      const int a = std::get<1>(md), b = std::get<2>(md);
+      S.lam[j] = std::get<0>(md);
       S.slam[j] = std::sqrt(S.lam[j]);
       for (int i = 0; i < S.nx; ++i)
-        S.fx[(size_t)j * S.nx + i] = kl_1d_eval_host(S.x0 + (i + 0.5) * S.hx - cx, Lx, omx[a], parx[a]);
+        S.fx[(size_t)j * S.nx + i] =
+            kl_1d_eval_host(S.x0 + (i + 0.5) * S.hx - cx, Lx, rm[q].omx[a], rm[q].parx[a]);
       for (int i = 0; i < S.ny; ++i)
-        S.fy[(size_t)j * S.ny + i] = kl_1d_eval_host(S.y0 + (i + 0.5) * S.hy - cy, Ly, omy[b], pary[b]);
-      if (eig) eig[w++] = S.lam[j];
+        S.fy[(size_t)j * S.ny + i] =
+            kl_1d_eval_host(S.y0 + (i + 0.5) * S.hy - cy, Ly, rm[q].omy[b], rm[q].pary[b]);
     }
   }
+  c->region_of.assign(region_of, region_of + ns);
+  c->n_regions = n_regions;
   c->kl_done = true;
   c->coll_done = false;
   c->basis_done = false;
   return SFB_OK;
 }
 
+sfb_status sfb_kl_setup(sfb_ctx* c, const sfb_kl_region* regions, int32_t n_regions, double* eig) {
+  if (!c) return SFB_ERR_ARG;
+  if (!regions || n_regions != (int)c->subs.size()) return fail(c, SFB_ERR_ARG, "one KL region per Darcy subdomain");
+  // one region per subdomain, on the subdomain's own rectangle
+  std::vector<double> rects(4 * (size_t)n_regions);
+  std::vector<int32_t> region_of(n_regions);
+  for (int s = 0; s < n_regions; ++s) {
+    const HostSub& S = c->subs[s];
+    rects[4 * s] = S.x0; rects[4 * s + 1] = S.x1; rects[4 * s + 2] = S.y0; rects[4 * s + 3] = S.y1;
+    region_of[s] = s;
+  }
+  return sfb_kl_setup_regions(c, regions, n_regions, rects.data(), region_of.data(), eig);
+}
+
 sfb_status sfb_collocation_setup(sfb_ctx* c, const sfb_collocation* spec, int64_t* n_pts_out) {
   if (!c || !spec) return SFB_ERR_ARG;
   if (!c->kl_done) return fail(c, SFB_ERR_STATE, "sfb_kl_setup must come first");
   const int ns = (int)c->subs.size();
+  // region r's stochastic dimensions follow those of regions 0..r-1 (Section
+  // 2.1); a subdomain takes its region's
   int n_dim = 0;
+  std::vector<int> reg_off(c->n_regions, 0);
+  for (int r = 0; r < c->n_regions; ++r) {
+    int s0 = 0;
+    while (c->region_of[s0] != r) ++s0;
+    reg_off[r] = n_dim;
+    n_dim += c->subs[s0].n_term;
+  }
   c->dim_off.assign(ns, 0);
-  for (int s = 0; s < ns; ++s) { c->dim_off[s] = n_dim; n_dim += c->subs[s].n_term; }
+  for (int s = 0; s < ns; ++s) c->dim_off[s] = reg_off[c->region_of[s]];
   std::vector<int> rule;
   if (spec->kind == 1 && spec->n_rule > 0) {
     if (!spec->rule) return fail(c, SFB_ERR_ARG, "rule missing");
@@ -529,6 +589,16 @@ sfb_status sfb_collocation_points(const sfb_ctx* c, double* y_out, double* w_out
   if (!c->coll_done) return SFB_ERR_STATE;
   if (y_out) std::copy(c->grid.y.begin(), c->grid.y.end(), y_out);
   if (w_out) std::copy(c->grid.w.begin(), c->grid.w.end(), w_out);
+  return SFB_OK;
+}
+
+sfb_status sfb_kl_tables(const sfb_ctx* c, int32_t sub, double* sqrt_lambda, double* fx, double* fy) {
+  if (!c || sub < 0 || sub >= (int)c->subs.size()) return SFB_ERR_ARG;
+  if (!c->kl_done) return SFB_ERR_STATE;
+  const HostSub& S = c->subs[sub];
+  if (sqrt_lambda) std::copy(S.slam.begin(), S.slam.end(), sqrt_lambda);
+  if (fx) std::copy(S.fx.begin(), S.fx.end(), fx);
+  if (fy) std::copy(S.fy.begin(), S.fy.end(), fy);
   return SFB_OK;
 }
 

@@ -12,7 +12,9 @@ silent, the reading stated with each item):
 * The Darcy region ``darcy_box = (x0, x1, y0, y1)`` is tiled by a ``px x py``
   array of rectangular subdomains of equal size. Subdomain ``s = iy * px + ix``
   (bottom row first) has an ``nx x ny`` cell grid ``darcy_grid[s]`` and is its
-  own KL region.
+  own KL region, unless ``kl["regions"]`` lists region rectangles and
+  ``kl["region_of"]`` each subdomain's region (``n_term`` and ``modes`` are
+  then per region).
 * One Stokes subdomain covers ``stokes_box = (x0, x1, y1, y2)`` directly above
   the Darcy region, with an ``Sx x Sy`` rectangle grid (two triangles each).
 * Interfaces: one Stokes-Darcy edge per top-row Darcy subdomain, one vertical
@@ -148,5 +150,20 @@ def anisotropic():
     return w
 
 
+def kl_regions():
+    """2x2 Darcy subdomains of 8x6 cells whose KL regions are the two rows,
+    (0,1)x(0,0.25) and (0,1)x(0.25,0.5), each spanning two subdomains, as in
+    Case 1 of Section 6.1. The bottom region keeps the paper's 2 x 1 mode set,
+    the top one its 3 largest modes. Tensor 2-point rule: 32 global points,
+    4 and 8 local ones per region (shared by its two subdomains)."""
+    w = small_test(nx=8, ny=6, px=2, py=2, n_sd=2, n_dd=2, n_term=2, degree=1, stokes=(6, 5),
+                   sigma2=1.0, eta=(0.2, 0.1), name="kl_regions")
+    w["kl"]["n_term"] = [2, 3]
+    w["kl"]["modes"] = [(2, 1), None]
+    w["kl"]["regions"] = [(0.0, 1.0, 0.0, 0.25), (0.0, 1.0, 0.25, 0.5)]
+    w["kl"]["region_of"] = [0, 0, 1, 1]
+    return w
+
+
 ALL = {"tiny": tiny, "medium": medium, "precision": precision,
-       "batched": batched, "large": large, "anisotropic": anisotropic}
+       "batched": batched, "large": large, "anisotropic": anisotropic, "kl_regions": kl_regions}

@@ -31,6 +31,8 @@ def make_workload(key):
         return W.medium()
     if key == "anisotropic":
         return W.anisotropic()
+    if key == "kl_regions":
+        return W.kl_regions()
     if key == "ragged":
         return W.small_test(nx=13, ny=9, px=3, py=2, n_sd=3, n_dd=2, n_term=2, degree=2, stokes=(7, 5),
                             bottom_pressure=0.5, source=[0.3, -0.2, 0.1, 0.7, -0.4, 0.2],

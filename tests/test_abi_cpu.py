@@ -34,15 +34,25 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, n), n
 
 
-@pytest.mark.parametrize("name", ["tiny", "medium", "batched", "anisotropic"])
+@pytest.mark.parametrize("name", ["tiny", "medium", "batched", "anisotropic", "kl_regions"])
 def test_host_setup_matches_oracle(name):
     sfb = _lib()
     from oracle import coupled
     w = W.ALL[name]()
     s = sfb.Solver(w)
     p = coupled.Problem(w)
-    lam_o = np.concatenate([p.kl[i][0] for i in range(len(p.subs))])
+    # eigenvalues region by region (each region's first subdomain carries them)
+    first = [p.region_of.index(r) for r in range(len(p.n_term))]
+    lam_o = np.concatenate([p.kl[i][0] for i in first])
     assert np.allclose(s.eigvals, lam_o, rtol=1e-13)
+    # the tables the kernel evaluates: sqrt(lambda_j) and fx_j(x) fy_j(y) at
+    # every cell centre, against the oracle's mode values (cells by y-rows)
+    for i, sub in enumerate(p.subs):
+        sl, fx, fy = s.kl_tables(i)
+        lam, f = p.kl[i]
+        assert np.allclose(sl ** 2, lam, rtol=1e-13)
+        modes = np.einsum("jy,jx->jyx", fy, fx).reshape(len(lam), -1)
+        assert np.allclose(modes, f, rtol=1e-12, atol=1e-13), i
     assert s.n_lambda == p.n_lambda
     y, wt = s.points()
     yo, wo = p.grid()
@@ -52,7 +62,7 @@ def test_host_setup_matches_oracle(name):
         assert abs(ref[tuple(np.round(r, 10))] - v) < 1e-12
     for i in range(len(p.subs)):
         assert list(s.subdomain_dofs(i)) == p.subs[i].dofs
-        assert np.allclose(s.local_points(i), p.local_grids[i], atol=1e-15)
+        assert np.allclose(s.local_points(i), p.local_realizations(i, yo)[0], atol=1e-15)
     assert list(s.subdomain_dofs(-1)) == p.stokes.dofs
     assert s.field_size("darcy_p") == sum(sub.n_cells for sub in p.subs)
     assert s.field_size("stokes_u") == 2 * p.stokes.n_nodes

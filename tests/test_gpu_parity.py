@@ -9,7 +9,7 @@ from gpu_common import TOL, make_workload, oracle_case, rel
 
 pytestmark = pytest.mark.gpu
 
-CASES = ["tiny", "ragged", "ragged_tensor", "medium", "anisotropic"]
+CASES = ["tiny", "ragged", "ragged_tensor", "medium", "anisotropic", "kl_regions"]
 
 
 def _solver(key, prec):

@@ -90,3 +90,51 @@ def test_moments_definition():
     mean, var = coupled.moments(v, w)
     assert np.allclose(mean, sum(w[i] * v[i] for i in range(7)))
     assert np.allclose(var, sum(w[i] * v[i] ** 2 for i in range(7)) - mean ** 2)
+
+
+def test_kl_region_spanning_subdomains_is_one_field():
+    """A KL region that spans two subdomains (Section 2.1; Case 1 of Section
+    6.1) carries one random field: on every cell its log-permeability equals
+    that of a problem where the same rectangle is a single subdomain with
+    the union's cells, for the same local coordinates. Evaluating the modes
+    in each subdomain's own coordinates instead fails this."""
+    wl = W.kl_regions()
+    prob = coupled.Problem(wl)
+    one = W.small_test(nx=16, ny=6, px=1, py=2, n_sd=2, n_dd=2, n_term=2, degree=1, stokes=(6, 5),
+                       sigma2=1.0, eta=(0.2, 0.1))
+    one["kl"]["n_term"] = [2, 3]
+    one["kl"]["modes"] = [(2, 1), None]
+    ref = coupled.Problem(one)
+    rng = np.random.default_rng(7)
+    for r, (left, right) in enumerate(((0, 1), (2, 3))):
+        y = rng.normal(size=prob.n_term[r])
+        whole = np.log(ref.permeability(r, y)).reshape(6, 16)
+        assert np.allclose(np.log(prob.permeability(left, y)).reshape(6, 8), whole[:, :8], rtol=1e-13, atol=1e-13)
+        assert np.allclose(np.log(prob.permeability(right, y)).reshape(6, 8), whole[:, 8:], rtol=1e-13, atol=1e-13)
+    # subdomains of a region share its local realizations and dimensions
+    ys, _ = prob.grid()
+    assert ys.shape == (32, 5)
+    for a, b in ((0, 1), (2, 3)):
+        la, ka = prob.local_realizations(a, ys)
+        lb, kb = prob.local_realizations(b, ys)
+        assert np.array_equal(la, lb) and np.array_equal(ka, kb)
+
+
+def test_methods_agree_on_shared_kl_regions():
+    """Monolithic solve, dense interface reduction and Methods S1, S2, S3
+    agree when KL regions span subdomains; S3's count of Eq. 5.13 uses the
+    region's local realizations for each of its subdomains."""
+    prob = coupled.Problem(W.kl_regions())
+    ys, ws = prob.grid()
+    sel = ys[::5]
+    l1, it1, c1 = coupled.method_s1(prob, sel, rtol=1e-13)
+    l2, _, c2 = coupled.method_s2(prob, sel, rtol=1e-13)
+    l3, _, c3 = coupled.method_s3(prob, sel, rtol=1e-13)
+    dense = np.array([prob.interface_dense(y)[0] for y in sel])
+    mono = np.array([prob.monolithic(y)[0] for y in sel])
+    assert _rel(dense, mono) < 1e-10
+    for lam in (l1, l2, l3):
+        assert _rel(lam, dense) < 1e-10
+    for s, sub in enumerate(prob.subs):
+        loc, _ = prob.local_realizations(s, sel)
+        assert c3[s] == len(sub.dofs) * len(loc) + 2 * len(sel)
