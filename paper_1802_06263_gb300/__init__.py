@@ -283,6 +283,7 @@ class Solver:
     def kl_tables(self, sub):
         """(sqrt(lambda) [n_term], fx [n_term x nx], fy [n_term x ny]) that the
         basis kernel evaluates for Darcy subdomain ``sub``."""
+        self._check(self.lib.sfb_kl_tables(self.h, sub, None, None, None))   # validates sub
         kl = self.w["kl"]
         nt = kl["n_term"][(kl.get("region_of") or list(range(self.n_darcy)))[sub]]
         nx, ny = self.w["darcy_grid"][sub]

@@ -112,3 +112,34 @@ def test_basis_launch_shapes_and_options():
         for v in bad:
             with pytest.raises(sfb.SfbError):
                 s.set_option(name, v)
+
+
+def test_bad_kl_regions_and_rules_are_rejected():
+    """Host-side checks of the region map, the mode sets and the anisotropic
+    rule: each failure is an SfbError, not a crash."""
+    sfb = _lib()
+    bad = []
+    w = W.kl_regions()
+    w["kl"]["region_of"] = [0, 0, 0, 0]            # region 1 has no subdomain
+    bad.append(w)
+    w = W.kl_regions()
+    w["kl"]["regions"] = [(0.0, 0.5, 0.0, 0.25), (0.0, 1.0, 0.25, 0.5)]   # subdomain 1 outside region 0
+    bad.append(w)
+    w = W.kl_regions()
+    w["kl"]["region_of"] = [0, 0, 1, 2]            # no region 2
+    bad.append(w)
+    w = W.anisotropic()
+    w["kl"]["modes"] = [(2, 2), (2, 2)]            # 4 modes for n_term 2
+    bad.append(w)
+    w = W.anisotropic()
+    w["collocation"]["m"] = [2, 1, 3, 1, 2, 0]     # a 0-point rule
+    bad.append(w)
+    w = W.anisotropic()
+    w["collocation"] = {"kind": "smolyak", "lmax": 1, "rule": [1, 3], "m": [2, 2, 2, 2, 2, 2]}
+    bad.append(w)                                  # per-dimension sizes on a sparse grid
+    for w in bad:
+        with pytest.raises(sfb.SfbError):
+            sfb.Solver(w)
+    s = sfb.Solver(W.tiny())
+    with pytest.raises(sfb.SfbError):
+        s.kl_tables(5)
