@@ -138,3 +138,46 @@ def test_methods_agree_on_shared_kl_regions():
     for s, sub in enumerate(prob.subs):
         loc, _ = prob.local_realizations(s, sel)
         assert c3[s] == len(sub.dofs) * len(loc) + 2 * len(sel)
+
+
+def _simpson_edge(u, h):
+    """Integral along an edge of a continuous piecewise-quadratic function with
+    nodal values ``u`` at the vertices and midpoints (2k+1 values, segments of
+    length h): Simpson's rule, exact for quadratics."""
+    u = np.asarray(u)
+    return float(sum(h / 6.0 * (u[2 * k] + 4.0 * u[2 * k + 1] + u[2 * k + 2]) for k in range((len(u) - 1) // 2)))
+
+
+@pytest.mark.parametrize("wl", [
+    W.tiny(),
+    W.small_test(nx=7, ny=9, px=3, py=1, n_sd=2, n_dd=3, degree=2, stokes=(9, 4)),
+    W.small_test(nx=13, ny=9, px=3, py=2, n_sd=3, n_dd=2, n_term=2, degree=2, stokes=(7, 5)),
+    W.kl_regions(),
+], ids=["tiny", "quadratic", "ragged", "kl_regions"])
+def test_global_mass_balance(wl):
+    """Exact discrete conservation of the coupled scheme without sources: the
+    Taylor-Hood pressure space holds the constants, so the Stokes boundary
+    flux sums to zero; RT0 conserves mass cell by cell; and the mortar spaces
+    hold a constant on every mortar element, so the interface fluxes cancel
+    on each interface. Hence the Stokes inflow on the left equals the Stokes
+    outflow on the right plus the Darcy outflow through the bottom, to solver
+    precision, for every realization. A mortar projection that loses flux, a
+    misplaced interface face or a wrong boundary face breaks it."""
+    prob = coupled.Problem(wl)
+    ys, _ = prob.grid()
+    st = prob.stokes
+    for y in ys[:3]:
+        lam, f = prob.monolithic(y)
+        u = f["stokes_u"]
+        ux = u[:st.n_nodes].reshape(st.NY, st.NX)
+        inflow = _simpson_edge(ux[:, 0], st.hy)
+        out_right = _simpson_edge(ux[:, -1], st.hy)
+        out_bottom, off = 0.0, 0
+        for sub in prob.subs:
+            n_ux = sub.ny * (sub.nx + 1)
+            uy = f["darcy_flux"][off + n_ux: off + n_ux + (sub.ny + 1) * sub.nx].reshape(sub.ny + 1, sub.nx)
+            if sub.rect[2] == wl["darcy_box"][2]:
+                out_bottom += float(-uy[0, :].sum() * sub.hx)
+            off += n_ux + (sub.ny + 1) * sub.nx
+        assert inflow > 0.1 and out_bottom > 0.0 and out_right > 0.0
+        assert abs(inflow - out_right - out_bottom) < 1e-11 * inflow, (inflow, out_right, out_bottom)
