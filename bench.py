@@ -411,6 +411,87 @@ print(json.dumps({"basis_s": basis_s, "items": items, "points_s": t2 - t1, "poin
             "step_s_extrapolated": t_step}
 
 
+# Worker side of the all-cores oracle baseline: spawned processes import this
+# module and call these (a function defined in a "python -c" string cannot be
+# unpickled by a spawned worker).
+_ORACLE = {}
+
+
+def _oracle_worker_setup(workload):
+    import sfb_workloads as W_
+    from oracle import coupled
+    p = coupled.Problem(W_.ALL[workload]())
+    y, w = p.grid()
+    _ORACLE.update(p=p, y=y, w=w)
+
+
+def _oracle_ready(_):
+    return "p" in _ORACLE
+
+
+def _oracle_item_task(sk):
+    p, y = _ORACLE["p"], _ORACLE["y"]
+    s, k = sk
+    loc, _ = p.local_realizations(s, y)
+    p.darcy_basis(s, loc[k])
+    return 1
+
+
+def _oracle_point_task(idx):
+    from oracle import coupled
+    coupled.solve_all(_ORACLE["p"], _ORACLE["y"][idx], _ORACLE["w"][idx])
+    return len(idx)
+
+
+def cpu_baseline_all_cores(workload=WORKLOAD, items_per_core=2, pts_per_core=48, cores=None):
+    """The oracle as it stands on every host core: one spawned process per
+    core, each timing its own share of a bounded sample (basis items spread
+    over the subdomains, evenly spaced points), all started together. The
+    whole step is extrapolated linearly from the sample's throughput, as in
+    the single-thread baseline (the build weighted by each subdomain's
+    nx^3 ny factorization cost)."""
+    cores = cores or os.cpu_count() or 1
+    code = r"""
+import json, multiprocessing as mp, sys, time
+import numpy as np
+sys.path.insert(0, %r)
+import bench
+import sfb_workloads as W
+from oracle import coupled
+WL, CORES, IPC, PPC = %r, %d, %d, %d
+p = coupled.Problem(W.ALL[WL]())
+y, _ = p.grid()
+nb = p.w.get("n_batch") or len(y)
+n_loc = [len(p.local_realizations(s, y)[0]) for s in range(len(p.subs))]
+ns = len(p.subs)
+items = [(j %% ns, (j // ns) %% n_loc[j %% ns]) for j in range(CORES * IPC)]
+sel = np.unique(np.linspace(0, nb - 1, CORES * PPC).astype(int))
+chunks = [c for c in np.array_split(sel, CORES) if len(c)]
+with mp.get_context("spawn").Pool(CORES, initializer=bench._oracle_worker_setup, initargs=(WL,)) as pool:
+    assert all(pool.map(bench._oracle_ready, range(CORES), chunksize=1))
+    t0 = time.perf_counter()
+    pool.map(bench._oracle_item_task, items, chunksize=1)
+    t1 = time.perf_counter()
+    pool.map(bench._oracle_point_task, chunks, chunksize=1)
+    t2 = time.perf_counter()
+cost = [float(p.subs[s].nx) ** 3 * p.subs[s].ny for s in range(ns)]
+basis_s = (t1 - t0) * sum(cost[s] * n for s, n in enumerate(n_loc)) / sum(cost[s] for s, _ in items)
+t_step = basis_s + (t2 - t1) * nb / len(sel)
+print(json.dumps({"t_step": t_step, "items": len(items), "points": int(len(sel)), "n_items_total": int(sum(n_loc)),
+                  "n_pts": int(nb), "wall_s": t2 - t0}))
+""" % (ROOT, workload, cores, items_per_core, pts_per_core)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=240)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:   # a reported extra: its failure must not cost the bench line
+        return {"error": "%s: %s" % (type(e).__name__, str(e)[:200]), "cores": cores}
+    return {"value": d["n_pts"] / d["t_step"], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d of %d basis items and %d of %d points, one spawned process per core, "
+                      "extrapolated linearly" % (d["items"], d["n_items_total"], d["points"], d["n_pts"]),
+            "step_s_extrapolated": d["t_step"], "wall_s": d["wall_s"]}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -452,6 +533,7 @@ def main():
     if rank == 0:
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline_sample(workload=args.workload)
+            out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(workload=args.workload)
         print(json.dumps(out))
 
 

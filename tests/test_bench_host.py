@@ -24,3 +24,12 @@ def test_reference_arm_names_the_workload():
     out = bench.run_reference(argparse.Namespace(warmup=0, steps=1, workload="tiny"))
     assert out["impl"] == "reference" and out["config"]["workload"].startswith("tiny")
     assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["value"] == out["cpu_baseline"]["value"]
+
+
+def test_cpu_baseline_all_cores_runs_spawned_workers():
+    """The all-cores oracle baseline (one spawned process per core) returns a
+    throughput with the core count it used, not an error record."""
+    import bench
+    cb = bench.cpu_baseline_all_cores(workload="tiny", items_per_core=1, pts_per_core=4, cores=2)
+    assert "error" not in cb, cb
+    assert cb["value"] > 0 and cb["cores"] == 2 and cb["kind"] == "oracle"
