@@ -724,7 +724,6 @@ sfb_status upload_tables(sfb_ctx* c) {
   for (int64_t i = c->n_wide; i < c->n_items; ++i)
     if (sd[item_sub[i]].nx > 64) return fail(c, SFB_ERR_ARG, "basis items out of size-class order");
   // interface-solve maps
-  const int nu = ns + 1;
   std::vector<int> ldof(4 * c->n_lambda, 0);
   std::vector<int> fill(c->n_lambda, 0);
   auto put = [&](int64_t g, int unit, int loc) {
@@ -943,9 +942,18 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
       c->bgraph_kernels[prec] = nk;
     }
   }
-  cudaEvent_t e0, e1;
+  // timing events, released on every return
+  struct Events {
+    cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+    ~Events() {
+      for (cudaEvent_t x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } evs;
+  cudaEvent_t &e0 = evs.e[0], &e1 = evs.e[1], &ek = evs.e[2];
   SFB_CUDA(cudaEventCreate(&e0), "event");
   SFB_CUDA(cudaEventCreate(&e1), "event");
+  SFB_CUDA(cudaEventCreate(&ek), "event");
   SFB_CUDA(cudaEventRecord(e0, st), "event");
   cudaError_t e = cudaSuccess;
   if (graph) {
@@ -957,13 +965,11 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
     c->launches += nk;
   }
   c->last_build_graph = graph;
-  if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_fail(c, e, "basis kernel"); }
-  cudaEvent_t ek;
-  SFB_CUDA(cudaEventCreate(&ek), "event");
+  if (e != cudaSuccess) return cuda_fail(c, e, "basis kernel");
   SFB_CUDA(cudaEventRecord(ek, st), "event");
   e = launch_flux_epilogue(a, c->max_R, st);
   c->launches += 1;
-  if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_fail(c, e, "flux epilogue"); }
+  if (e != cudaSuccess) return cuda_fail(c, e, "flux epilogue");
   SFB_CUDA(cudaEventRecord(e1, st), "event");
   std::vector<int> status(n), nref(n);
   std::vector<double> resid(n), corr(n), est(n);
@@ -978,9 +984,6 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   float ms = 0.f, kms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventElapsedTime(&kms, e0, ek);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaEventDestroy(ek);
   int any = 0, n_nc = 0;
   for (int i = 0; i < n; ++i) { any |= status[i]; n_nc += (status[i] & ST_NOT_CONVERGED) != 0; }
   if (stats) {
