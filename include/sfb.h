@@ -100,7 +100,8 @@ typedef struct {
   const double* source;       /* [px*py] constant q_d per subdomain, or NULL      */
 } sfb_problem;
 
-/* One KL region per Darcy subdomain, covariance Eq. 6.1 on its rectangle. */
+/* One KL region, covariance Eq. 6.1 on its rectangle (sfb_kl_setup: one per
+ * Darcy subdomain, on the subdomain; sfb_kl_setup_regions: on given rectangles). */
 typedef struct {
   double sigma2;              /* multiplies the kernel (the variance of Y)         */
   double eta1, eta2;          /* correlation lengths                               */
