@@ -499,7 +499,8 @@ def run_reference(args):
     vals = []
     t0 = time.perf_counter()
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline_sample(n_items=8, n_pts=8, workload=args.workload)
+        # the same bounded sample as the GPU arm's cpu_baseline, so the two agree
+        cb = cpu_baseline_sample(workload=args.workload)
         if i >= args.warmup:
             vals.append(cb)
     wall = time.perf_counter() - t0
