@@ -443,6 +443,23 @@ def _oracle_point_task(idx):
     return len(idx)
 
 
+def host_cores(cap=32):
+    """Cores this process may use: its CPU affinity set, reduced by a cgroup
+    CPU quota if one is set (a container can see more CPUs than it may use),
+    and capped so the all-cores baseline stays bounded."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        n = os.cpu_count() or 1
+    try:
+        quota, period = open("/sys/fs/cgroup/cpu.max").read().split()[:2]
+        if quota != "max":
+            n = min(n, max(1, int(int(quota) // int(period))))
+    except (OSError, ValueError):
+        pass
+    return max(1, min(n, cap))
+
+
 def cpu_baseline_all_cores(workload=WORKLOAD, items_per_core=2, pts_per_core=48, cores=None):
     """The oracle as it stands on every host core: one spawned process per
     core, each timing its own share of a bounded sample (basis items spread
@@ -450,7 +467,7 @@ def cpu_baseline_all_cores(workload=WORKLOAD, items_per_core=2, pts_per_core=48,
     whole step is extrapolated linearly from the sample's throughput, as in
     the single-thread baseline (the build weighted by each subdomain's
     nx^3 ny factorization cost)."""
-    cores = cores or os.cpu_count() or 1
+    cores = cores or host_cores()
     code = r"""
 import json, multiprocessing as mp, sys, time
 import numpy as np

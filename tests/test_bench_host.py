@@ -33,3 +33,10 @@ def test_cpu_baseline_all_cores_runs_spawned_workers():
     cb = bench.cpu_baseline_all_cores(workload="tiny", items_per_core=1, pts_per_core=4, cores=2)
     assert "error" not in cb, cb
     assert cb["value"] > 0 and cb["cores"] == 2 and cb["kind"] == "oracle"
+
+
+def test_host_cores_is_bounded():
+    import bench
+    n = bench.host_cores()
+    assert 1 <= n <= 32
+    assert bench.host_cores(cap=1) == 1
