@@ -72,6 +72,9 @@ def _multi_indices(n_dim, total):
 
 
 def rule_size(p, rule):
+    """Points of the 1-D rule of sparse-grid level ``p``: the paper's
+    Gauss-Hermite ``2^(p+1) - 1`` (Section 4.2) or a given sequence (reading
+    A4)."""
     if rule == "paper":
         return 2 ** (p + 1) - 1
     return rule[p] if p < len(rule) else rule[-1]
@@ -131,7 +134,8 @@ def tensor_sizes(spec, n_dim):
 
 
 def global_grid(spec, n_dim):
-    """Global collocation grid for a workload's ``collocation`` spec."""
+    """Global collocation grid for a workload's ``collocation`` spec: the
+    tensor rule of Section 4.1 or the sparse grid of Section 4.2."""
     if spec["kind"] == "tensor":
         return tensor_grid(tensor_sizes(spec, n_dim))
     if spec["kind"] == "smolyak":

@@ -103,6 +103,7 @@ class Problem:
 
     # ---- stochastic inputs -------------------------------------------------
     def grid(self):
+        """Global collocation points and weights (Section 4)."""
         return collocation.global_grid(self.w["collocation"], self.n_dim)
 
     def local_realizations(self, s, ys):
@@ -112,21 +113,29 @@ class Problem:
         return collocation.local_points(np.asarray(ys), self.dims[r], self.local_grids[r])
 
     def local_y(self, s, y_global):
+        """Coordinates of a global point in subdomain ``s``'s KL region: its
+        dims kappa(i, j) (Section 2.1; Section 5.4 Step 4)."""
         return np.asarray(y_global)[self.dims[self.region_of[s]]]
 
     def permeability(self, s, y_local):
+        """Cell permeabilities ``K = exp(Y)`` with ``Y`` the truncated local KL
+        sum of Eq. 2.13 at the cell centres (reading A11)."""
         lam, f = self.kl[s]
         return np.exp(kl.log_permeability(lam, f, y_local, self.mean_y))
 
     # ---- bases ---------------------------------------------------------------
     def darcy_basis(self, s, y_local):
-        """(Phi_i, g_i, X_i, K) of Darcy subdomain ``s`` for one local realization."""
+        """(Phi_i, g_i, X_i, K) of Darcy subdomain ``s`` for one local
+        realization: the multiscale flux basis of Section 5.3 Step 2 built per
+        local realization as in Section 5.4 Step 2."""
         K = self.permeability(s, y_local)
         phi, g, X = self.subs[s].flux_basis(K)
         self.n_solves[s] += len(self.subs[s].dofs) + 1
         return phi, g, X, K
 
     def stokes_basis(self):
+        """The Stokes subdomain's velocity-response basis (Section 5.3 Step 2),
+        built once: Section 5.4 sets N_real = 1 for Stokes (reading A7)."""
         if self._stokes_basis is None:
             self._stokes_basis = self.stokes.flux_basis()
             self.n_solves[-1] += len(self.stokes.dofs) + 1
@@ -148,8 +157,9 @@ class Problem:
         return S, g
 
     def interface_dense(self, y_global):
-        """Dense interface solve for one global point: returns
-        ``(lambda, S, g, per-subdomain (Phi, g, X, K))``."""
+        """Dense interface solve for one global point: ``S lambda = g`` of
+        Eqs. 5.9-5.10 with ``S`` assembled from the flux bases and solved
+        directly. Returns ``(lambda, S, g, per-subdomain (Phi, g, X, K))``."""
         bs = [self.darcy_basis(s, self.local_y(s, y_global)) for s in range(len(self.subs))]
         S, g = self.assemble_interface([(b[0], b[1]) for b in bs])
         lam = np.linalg.solve(S, g)
@@ -392,7 +402,8 @@ def moments(values, weights):
 
 def solve_all(prob, ys, ws):
     """Reference result for a set of global points: per-point mortar solution
-    and fields from the dense interface solve, then the moments of each field."""
+    and fields from the dense interface solve (Section 5.4 Steps 3-6), then
+    the mean (Eq. 2.1) and variance of each field (reading A12)."""
     lams = []
     fields = {"darcy_p": [], "darcy_flux": [], "stokes_u": [], "stokes_p": []}
     cache = {}

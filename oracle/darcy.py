@@ -78,7 +78,8 @@ class DarcySub:
 
     def boundary_trans(self, K, side):
         """Half-cell transmissibility ``2 K |e| / (nu h_perp)`` of the faces of a
-        side (RT0 + trapezoid on the half cell next to the boundary)."""
+        side (RT0 + trapezoid on the half cell next to the boundary; the
+        lowest-order RT discretisation of Section 3.3 for Eqs. 2.5-2.7)."""
         cells, _ = self.side_faces(side)
         if side in ("bottom", "top"):
             return 2.0 * K[cells] * self.hx / (self.nu * self.hy)
@@ -86,7 +87,8 @@ class DarcySub:
 
     def interior_trans(self, K):
         """Interior transmissibilities ``(|e|/h) 2 / (nu (1/K_a + 1/K_b))``
-        (harmonic mean of the two cell permeabilities)."""
+        (harmonic mean of the two cell permeabilities: RT0 with the trapezoidal
+        rule on the two half cells, Section 3.3)."""
         Kc = K.reshape(self.ny, self.nx)
         tx = (self.hy / self.hx) * 2.0 / (self.nu * (1.0 / Kc[:, :-1] + 1.0 / Kc[:, 1:]))
         ty = (self.hx / self.hy) * 2.0 / (self.nu * (1.0 / Kc[:-1, :] + 1.0 / Kc[1:, :]))
@@ -94,7 +96,8 @@ class DarcySub:
 
     def projection(self, side):
         """``P`` of one interface side restricted to the subdomain's local
-        mortar DOFs: ``(n_faces, len(dofs))``."""
+        mortar DOFs, ``(n_faces, len(dofs))``: the L2 projection of the mortar
+        basis onto the normal traces (Section 5.2, step 1 of the S_H action)."""
         kind = self.sides[side]
         _, faces = self.side_faces(side)
         p = np.zeros((len(faces), len(self.dofs)))
@@ -108,7 +111,7 @@ class DarcySub:
     def assemble(self, K):
         """5-point matrix ``A`` (sparse), interface RHS block ``B = E^T D_T P``
         (``n_cells x R``) and the particular RHS ``b_bar`` (source plus outer
-        Dirichlet data)."""
+        Dirichlet data): Eqs. 5.5-5.6 and 5.7-5.8 in cell-centred form."""
         nx, ny, n = self.nx, self.ny, self.n_cells
         tx, ty = self.interior_trans(K)
         rows, cols, vals = [], [], []
@@ -143,7 +146,8 @@ class DarcySub:
     def interface_flux(self, K, X, C):
         """Flux functionals ``<u.n, xi_l>`` (rows ``l`` over local DOFs) of the
         solutions ``X`` (columns) with interface data ``C`` (local mortar
-        coefficients, same columns): ``sum_e T_e (x_c - (P c)_e) P[e, l]``."""
+        coefficients, same columns): ``sum_e T_e (x_c - (P c)_e) P[e, l]``
+        (Section 5.2, step 3 of the S_H action)."""
         out = np.zeros((len(self.dofs), X.shape[1]))
         for side in SIDES:
             if self.sides[side][0] != "iface":
@@ -180,7 +184,8 @@ class DarcySub:
 
     def fields(self, K, p, c_local):
         """Normal velocities on all faces for cell pressures ``p`` and
-        interface data ``c_local``: ``ux (ny, nx+1)``, ``uy (ny+1, nx)``."""
+        interface data ``c_local``: ``ux (ny, nx+1)``, ``uy (ny+1, nx)``
+        (the RT0 velocity of Eq. 2.5, recovered as in Section 5.1)."""
         nx, ny = self.nx, self.ny
         Pc = p.reshape(ny, nx)
         tx, ty = self.interior_trans(K)

@@ -37,7 +37,10 @@ def _bisect(f, lo, hi, iters=200):
 
 def kl_1d(length, eta, n_modes):
     """First ``n_modes`` eigenpairs of ``exp(-|x-x'|/eta)`` on a segment of the
-    given length, centred at 0, in decreasing eigenvalue order.
+    given length, centred at 0, in decreasing eigenvalue order: the 1-D
+    factors of the Fredholm problem Eq. 2.11 for the separable covariance
+    Eq. 6.1, from the textbook transcendental equations of the exponential
+    kernel (even and odd modes).
 
     Returns ``(omega, lam, parity)`` with ``parity`` 0 for even (cosine) and 1
     for odd (sine) modes. Roots come from bisection on sign-regular forms of
@@ -70,7 +73,8 @@ def kl_1d(length, eta, n_modes):
 
 
 def kl_1d_eval(x, length, omega, parity):
-    """Normalised 1-D eigenfunctions at points ``x`` (centred coordinates).
+    """Normalised 1-D eigenfunctions at points ``x`` (centred coordinates), the
+    factors of the eigenfunctions in Eqs. 2.12-2.13.
 
     ``cos(w x) / sqrt(a + sin(2wa)/(2w))`` for even modes and
     ``sin(w x) / sqrt(a - sin(2wa)/(2w))`` for odd modes, which have unit

@@ -25,7 +25,8 @@ _GL_W = np.array([5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0])
 
 def lagrange_1d(deg, t):
     """Lagrange basis of degree 1 or 2 on [0, 1] at equally spaced nodes,
-    evaluated at ``t``; returns ``(deg+1, len(t))``."""
+    evaluated at ``t``; returns ``(deg+1, len(t))``. The local shapes of the
+    discontinuous mortar space of Section 3.3 (reading A5)."""
     t = np.asarray(t, dtype=np.float64)
     if deg == 1:
         return np.array([1.0 - t, t])
@@ -50,8 +51,9 @@ class Interface:
         return list(range(self.offset, self.offset + self.n_dof))
 
     def basis_at(self, s):
-        """Values of all mortar basis functions of this interface at points
-        ``s`` inside ``[s0, s1]``: returns ``(n_dof, len(s))``."""
+        """Values of all mortar basis functions xi_l of this interface (the
+        basis of Section 5.3 Step 2) at points ``s`` inside ``[s0, s1]``:
+        returns ``(n_dof, len(s))``."""
         s = np.asarray(s, dtype=np.float64)
         h = (self.s1 - self.s0) / self.n_el
         e = np.clip(np.floor((s - self.s0) / h).astype(int), 0, self.n_el - 1)
@@ -87,7 +89,8 @@ class Interface:
 
     def face_projection(self, faces):
         """L2 projection onto piecewise constants on the fine faces ``faces``
-        (list of ``(f0, f1)``): ``P[e, l] = (1/|e|) int_e xi_l ds``."""
+        (list of ``(f0, f1)``): ``P[e, l] = (1/|e|) int_e xi_l ds`` (the
+        projection onto the Darcy normal traces, Section 5.2 step 1)."""
         p = np.zeros((len(faces), self.n_dof))
         for r, (f0, f1) in enumerate(faces):
             p[r] = self.integrate(f0, f1, lambda s: np.ones_like(s)) / (f1 - f0)

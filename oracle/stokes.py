@@ -92,7 +92,9 @@ class StokesSub:
                         self.node(i, j + 1)], [psw, pne, pnw], [xsw, xne, xnw])
 
     def assemble(self):
-        """Velocity block ``A`` (with BJS) and divergence block ``B``."""
+        """Velocity block ``A`` (``2 nu_s (D u, D v)`` plus the BJS term of Eq.
+        2.10 on Gamma_sd) and divergence block ``B`` of the Taylor-Hood
+        discretisation of Eqs. 2.2-2.4 (Section 3.3)."""
         nn = self.n_nodes
         ar, ac, av, br, bc, bv = [], [], [], [], [], []
         nu = self.nu
@@ -153,7 +155,8 @@ class StokesSub:
 
     def dirichlet(self):
         """Dirichlet DOFs and values: inflow ``u = (u_in 4 s (1 - s), 0)`` on the
-        left edge (``s`` the normalised height), no slip on the top edge."""
+        left edge (``s`` the normalised height), no slip on the top edge (the
+        outer data of Section 6.1, reading A6)."""
         nn = self.n_nodes
         mask = np.zeros(2 * nn, dtype=bool)
         val = np.zeros(2 * nn)
@@ -198,8 +201,9 @@ class StokesSub:
         return full[:nu_], full[nu_:]
 
     def flux_basis(self):
-        """Stokes multiscale basis: for each local mortar DOF ``j`` the velocity
-        response to normal stress ``xi_j``; ``Phi_s[l, j] = -<u(xi_j).n, xi_l>``,
+        """Stokes multiscale basis (Section 5.3 Step 2; Eqs. 5.1-5.4): for each
+        local mortar DOF ``j`` the velocity response to normal stress ``xi_j``;
+        ``Phi_s[l, j] = -<u(xi_j).n, xi_l>``,
         ``g_s[l] = <u_bar.n, xi_l>`` for the inflow-driven particular solution;
         ``U`` (velocity x (R+1)) and ``Pp`` (pressure x (R+1)) responses."""
         N = self.neumann_matrix()
