@@ -370,132 +370,99 @@ def describe(wl, s, n_pts):
 def cpu_baseline_sample(n_items=16, n_pts=48, workload=WORKLOAD):
     """The oracle as it stands on a bounded sample of the workload, single
     threaded, extrapolated linearly to the whole step (for the batched
-    workload, its batch of points)."""
+    workload, its batch of points). The step is Method S3 on the oracle's
+    own functions: every basis item once (sampled per subdomain), then per
+    point the interface assembly and solve and the field recovery with the
+    bases already built, then the moments."""
     code = r"""
 import json, sys, time, numpy as np
 sys.path.insert(0, %r)
-import sfb_workloads as W
-from oracle import coupled
-p = coupled.Problem(W.ALL[%r]())
-y, w = p.grid()
-t0 = time.perf_counter()
-items, basis_s = 0, 0.0
-for s in range(len(p.subs)):
-    loc, _ = p.local_realizations(s, y)
-    m = min(len(loc), max(1, %d // len(p.subs)))
-    ts = time.perf_counter()
-    for k in range(m):
-        p.darcy_basis(s, loc[k]); items += 1
-    # this subdomain's items, extrapolated from its own sample
-    basis_s += (time.perf_counter() - ts) / m * len(loc)
-t1 = time.perf_counter()
-nb = p.w.get("n_batch") or len(y)
-sel = np.unique(np.linspace(0, nb - 1, %d).astype(int))
-lams, mom = coupled.solve_all(p, y[sel], w[sel])
-t2 = time.perf_counter()
-n_items_total = sum(len(p.local_realizations(s, y)[0]) for s in range(len(p.subs)))
-print(json.dumps({"basis_s": basis_s, "items": items, "points_s": t2 - t1, "points": len(sel),
-                  "n_items_total": n_items_total, "n_pts": nb}))
+import bench
+d = bench._oracle_s3_sample(%r, %d, %d, [0], 1)
+print(json.dumps(d))
 """ % (ROOT, workload, n_items, n_pts)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
     if r.returncode != 0 or not r.stdout.strip():
         raise RuntimeError("oracle sample failed for the %s workload:\n%s" % (workload, r.stderr[-2000:]))
     d = json.loads(r.stdout.strip().splitlines()[-1])
-    # basis_s is already the whole build, extrapolated per subdomain; the
-    # points leg includes building the bases its points reference
-    t_step = d["basis_s"] + d["points_s"] / d["points"] * d["n_pts"]
-    return {"value": d["n_pts"] / t_step, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": d["n_pts"] / d["t_step"], "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d of %d basis items and %d of %d points, single thread, extrapolated linearly"
                       % (d["items"], d["n_items_total"], d["points"], d["n_pts"]),
-            "step_s_extrapolated": t_step}
+            "step_s_extrapolated": d["t_step"]}
 
 
-# Worker side of the all-cores oracle baseline: spawned processes import this
-# module and call these (a function defined in a "python -c" string cannot be
-# unpickled by a spawned worker).
-_ORACLE = {}
-
-
-def _oracle_worker_setup(workload):
+def _oracle_s3_sample(workload, n_items, n_pts, part, n_parts):
+    """Times Method S3 of the oracle on a sample (share ``part`` of
+    ``n_parts`` of the points; every part times its own items too): per
+    subdomain ``n_items / n_subdomains`` basis items, extrapolated to the
+    subdomain's local realizations; then, with the bases of the sampled
+    points built beforehand (untimed), the per-point interface assembly,
+    dense solve and recovery, extrapolated to the batch; then the moments."""
     import sfb_workloads as W_
     from oracle import coupled
     p = coupled.Problem(W_.ALL[workload]())
     y, w = p.grid()
-    _ORACLE.update(p=p, y=y, w=w)
+    nb = p.w.get("n_batch") or len(y)
+    ns = len(p.subs)
+    kmaps = [p.local_realizations(s, y)[1] for s in range(ns)]
+    n_loc = [len(p.local_realizations(s, y)[0]) for s in range(ns)]
+    items, basis_s = 0, 0.0
+    for s in range(ns):
+        loc, _ = p.local_realizations(s, y)
+        m = min(len(loc), max(1, n_items // ns))
+        ts = time.perf_counter()
+        for k in range(m):
+            p.darcy_basis(s, loc[k])
+            items += 1
+        basis_s += (time.perf_counter() - ts) / m * len(loc)
+    sel = np.unique(np.linspace(0, nb - 1, n_pts).astype(int))
+    sel = np.array_split(sel, n_parts)[part[0]] if n_parts > 1 else sel
+    cache = {}
+    for l in sel:                                  # the bases the points use, untimed
+        for s in range(ns):
+            key = (s, kmaps[s][l])
+            if key not in cache:
+                cache[key] = p.darcy_basis(s, p.local_y(s, y[l]))
+    p.stokes_basis()
+    t0 = time.perf_counter()
+    fields = {"darcy_p": [], "darcy_flux": [], "stokes_u": [], "stokes_p": []}
+    for l in sel:
+        bases = [cache[(s, kmaps[s][l])] for s in range(ns)]
+        S, g = p.assemble_interface([(b[0], b[1]) for b in bases])
+        lam = np.linalg.solve(S, g)
+        f = p.recover(lam, bases)
+        for k in fields:
+            fields[k].append(f[k])
+    for k in fields:
+        coupled.moments(np.array(fields[k]), w[sel])
+    points_s = time.perf_counter() - t0
+    return {"basis_s": basis_s, "items": items, "points_s": points_s, "points": int(len(sel)),
+            "n_items_total": int(sum(n_loc)), "n_pts": int(nb),
+            "t_step": basis_s + points_s / len(sel) * nb}
 
 
-def _oracle_ready(_):
-    return "p" in _ORACLE
-
-
-def _oracle_item_task(sk):
-    p, y = _ORACLE["p"], _ORACLE["y"]
-    s, k = sk
-    loc, _ = p.local_realizations(s, y)
-    p.darcy_basis(s, loc[k])
-    return 1
-
-
-def _oracle_point_task(idx):
-    from oracle import coupled
-    coupled.solve_all(_ORACLE["p"], _ORACLE["y"][idx], _ORACLE["w"][idx])
-    return len(idx)
-
-
-def host_cores(cap=32):
-    """Cores this process may use: its CPU affinity set, reduced by a cgroup
-    CPU quota if one is set (a container can see more CPUs than it may use),
-    and capped so the all-cores baseline stays bounded."""
-    try:
-        n = len(os.sched_getaffinity(0))
-    except (AttributeError, OSError):
-        n = os.cpu_count() or 1
-    try:
-        quota, period = open("/sys/fs/cgroup/cpu.max").read().split()[:2]
-        if quota != "max":
-            n = min(n, max(1, int(int(quota) // int(period))))
-    except (OSError, ValueError):
-        pass
-    return max(1, min(n, cap))
-
-
-def cpu_baseline_all_cores(workload=WORKLOAD, items_per_core=2, pts_per_core=48, cores=None):
+def cpu_baseline_all_cores(workload=WORKLOAD, items_per_core=16, pts_per_core=48, cores=None):
     """The oracle as it stands on every host core: one spawned process per
-    core, each timing its own share of a bounded sample (basis items spread
-    over the subdomains, evenly spaced points), all started together. The
-    whole step is extrapolated linearly from the sample's throughput, as in
-    the single-thread baseline (the build weighted by each subdomain's
-    nx^3 ny factorization cost)."""
+    core, all started together, each timing the same Method S3 sample as the
+    single-thread baseline (its basis items and its own share of the points)
+    while the others run. The step time is the sampled work spread evenly
+    over the cores: the mean extrapolated build over the cores, plus the
+    measured per-point time times the batch over the cores."""
     cores = cores or host_cores()
     code = r"""
-import json, multiprocessing as mp, sys, time
-import numpy as np
+import json, multiprocessing as mp, sys
 sys.path.insert(0, %r)
 import bench
-import sfb_workloads as W
-from oracle import coupled
 WL, CORES, IPC, PPC = %r, %d, %d, %d
-p = coupled.Problem(W.ALL[WL]())
-y, _ = p.grid()
-nb = p.w.get("n_batch") or len(y)
-n_loc = [len(p.local_realizations(s, y)[0]) for s in range(len(p.subs))]
-ns = len(p.subs)
-items = [(j %% ns, (j // ns) %% n_loc[j %% ns]) for j in range(CORES * IPC)]
-sel = np.unique(np.linspace(0, nb - 1, CORES * PPC).astype(int))
-chunks = [c for c in np.array_split(sel, CORES) if len(c)]
-with mp.get_context("spawn").Pool(CORES, initializer=bench._oracle_worker_setup, initargs=(WL,)) as pool:
-    assert all(pool.map(bench._oracle_ready, range(CORES), chunksize=1))
-    t0 = time.perf_counter()
-    pool.map(bench._oracle_item_task, items, chunksize=1)
-    t1 = time.perf_counter()
-    pool.map(bench._oracle_point_task, chunks, chunksize=1)
-    t2 = time.perf_counter()
-cost = [float(p.subs[s].nx) ** 3 * p.subs[s].ny for s in range(ns)]
-basis_s = (t1 - t0) * sum(cost[s] * n for s, n in enumerate(n_loc)) / sum(cost[s] for s, _ in items)
-t_step = basis_s + (t2 - t1) * nb / len(sel)
-print(json.dumps({"t_step": t_step, "items": len(items), "points": int(len(sel)), "n_items_total": int(sum(n_loc)),
-                  "n_pts": int(nb), "wall_s": t2 - t0}))
+args = [(WL, IPC, CORES * PPC, [i], CORES) for i in range(CORES)]
+with mp.get_context("spawn").Pool(CORES) as pool:
+    res = pool.starmap(bench._oracle_s3_sample, args, chunksize=1)
+basis = sum(r["basis_s"] for r in res) / len(res) / CORES
+per_point = sum(r["points_s"] for r in res) / sum(r["points"] for r in res)
+nb = res[0]["n_pts"]
+print(json.dumps({"t_step": basis + per_point * nb / CORES, "items": sum(r["items"] for r in res),
+                  "points": sum(r["points"] for r in res), "n_items_total": res[0]["n_items_total"], "n_pts": nb}))
 """ % (ROOT, workload, cores, items_per_core, pts_per_core)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     try:
@@ -504,9 +471,9 @@ print(json.dumps({"t_step": t_step, "items": len(items), "points": int(len(sel))
     except Exception as e:   # a reported extra: its failure must not cost the bench line
         return {"error": "%s: %s" % (type(e).__name__, str(e)[:200]), "cores": cores}
     return {"value": d["n_pts"] / d["t_step"], "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d of %d basis items and %d of %d points, one spawned process per core, "
-                      "extrapolated linearly" % (d["items"], d["n_items_total"], d["points"], d["n_pts"]),
-            "step_s_extrapolated": d["t_step"], "wall_s": d["wall_s"]}
+            "sample": "%d basis items and %d of %d points over %d spawned processes (one per core), the "
+                      "sampled work spread evenly over the cores" % (d["items"], d["points"], d["n_pts"], cores),
+            "step_s_extrapolated": d["t_step"]}
 
 
 def run_reference(args):
