@@ -442,6 +442,23 @@ def _oracle_s3_sample(workload, n_items, n_pts, part, n_parts):
             "t_step": basis_s + points_s / len(sel) * nb}
 
 
+def host_cores(cap=32):
+    """Cores this process may use: its CPU affinity set, reduced by a cgroup
+    CPU quota if one is set (a container can see more CPUs than it may use),
+    and capped so the all-cores baseline stays bounded."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        n = os.cpu_count() or 1
+    try:
+        quota, period = open("/sys/fs/cgroup/cpu.max").read().split()[:2]
+        if quota != "max":
+            n = min(n, max(1, int(int(quota) // int(period))))
+    except (OSError, ValueError):
+        pass
+    return max(1, min(n, cap))
+
+
 def cpu_baseline_all_cores(workload=WORKLOAD, items_per_core=16, pts_per_core=48, cores=None):
     """The oracle as it stands on every host core: one spawned process per
     core, all started together, each timing the same Method S3 sample as the
