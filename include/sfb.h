@@ -235,7 +235,10 @@ sfb_status sfb_kl_tables(const sfb_ctx* ctx, int32_t sub, double* sqrt_lambda, d
 sfb_status sfb_local_points(const sfb_ctx* ctx, int32_t region, int32_t* n_local, double* y_out);
 
 /* Device bytes needed for precision `prec` and batches of up to max_pts
- * points, and the hand-over of that memory (256-byte aligned). */
+ * points, and the hand-over of that memory (256-byte aligned). A KL or
+ * collocation set-up call made after sfb_set_workspace outdates the
+ * workspace's layout and tables: sfb_build_stochastic_basis then returns
+ * SFB_ERR_STATE until sfb_workspace_size and sfb_set_workspace run again. */
 sfb_status sfb_workspace_size(const sfb_ctx* ctx, int32_t prec, int64_t max_pts, size_t* bytes);
 sfb_status sfb_set_workspace(sfb_ctx* ctx, void* dev_ptr, size_t bytes);
 

@@ -152,6 +152,7 @@ struct sfb_ctx {
   sfb::StokesHost stokes;
   // state
   bool kl_done = false, coll_done = false, basis_done = false;
+  bool ws_stale = false;   // a set-up call came after the workspace was set
   int basis_prec = -1;
   int64_t n_solved = 0;
   int64_t launches = 0;   // kernels launched by this context

@@ -482,6 +482,7 @@ sfb_status sfb_kl_setup_regions(sfb_ctx* c, const sfb_kl_region* regions, int32_
   c->kl_done = true;
   c->coll_done = false;
   c->basis_done = false;
+  if (c->ws) c->ws_stale = true;   // its layout and tables describe the old set-up
   return SFB_OK;
 }
 
@@ -580,6 +581,7 @@ sfb_status sfb_collocation_setup(sfb_ctx* c, const sfb_collocation* spec, int64_
   }
   c->coll_done = true;
   c->basis_done = false;
+  if (c->ws) c->ws_stale = true;   // its layout and tables describe the old set-up
   if (n_pts_out) *n_pts_out = np_;
   return SFB_OK;
 }
@@ -635,6 +637,7 @@ sfb_status sfb_set_workspace(sfb_ctx* c, void* ptr, size_t bytes) {
   if (bytes < need) return fail(c, SFB_ERR_WORKSPACE, "workspace smaller than sfb_workspace_size()");
   c->ws = reinterpret_cast<char*>(ptr);
   c->ws_bytes = bytes;
+  c->ws_stale = false;
   // captured basis graphs hold the old workspace's addresses
   for (int q = 0; q < 3; ++q)
     if (c->bgraph[q]) {
@@ -838,6 +841,9 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   if (!c) return SFB_ERR_ARG;
   if (prec < 0 || prec > 2) return fail(c, SFB_ERR_ARG, "bad precision");
   if (!c->ws) return fail(c, SFB_ERR_WORKSPACE, "no workspace set");
+  if (c->ws_stale)
+    return fail(c, SFB_ERR_STATE, "set-up changed after sfb_set_workspace: call sfb_workspace_size and "
+                                  "sfb_set_workspace again");
   if (prec == SFB_FP64 && c->ws_prec != SFB_FP64)
     return fail(c, SFB_ERR_WORKSPACE, "workspace was sized for the FP32 factor; FP64 needs more");
   Dev& d = c->dev;
