@@ -143,3 +143,35 @@ def test_bad_kl_regions_and_rules_are_rejected():
     s = sfb.Solver(W.tiny())
     with pytest.raises(sfb.SfbError):
         s.kl_tables(5)
+
+
+def test_calls_out_of_order_return_status_codes():
+    """The C ABI's error conventions for calls made out of order or with bad
+    arguments, all decided on the host before any device work: SFB_ERR_STATE
+    (2) for a step before its prerequisite, SFB_ERR_WORKSPACE (4) without a
+    workspace, SFB_ERR_ARG (1) for bad arguments. No exception crosses the
+    ABI; each failure leaves a message."""
+    import ctypes
+    sfb = _lib()
+    lib = sfb.load()
+    s = sfb.Solver(W.tiny())
+    h = s.h
+    st = sfb.BasisStats()
+    assert lib.sfb_build_stochastic_basis(h, sfb.MIXED, ctypes.byref(st)) == 4      # no workspace
+    assert b"workspace" in lib.sfb_last_error(h)
+    assert lib.sfb_build_stochastic_basis(h, 7, ctypes.byref(st)) == 1             # bad precision
+    y, w = s.points()
+    assert lib.sfb_interface_solve_batch(h, y.ctypes.data, w.ctypes.data, len(y), 0, 1e-10, 100,
+                                         None, None) == 2                          # before any build
+    assert lib.sfb_get_basis(h, 0, 0, None, None, None) == 2
+    mean = np.zeros(s.field_size("darcy_p"))
+    assert lib.sfb_moments(h, 0, mean.ctypes.data, mean.ctypes.data) == 2          # before any solve
+    assert lib.sfb_set_option(h, b"no_such_option", 1.0) == 1
+    assert lib.sfb_set_option(h, b"refine_tol", 2.0) == 1
+    assert lib.sfb_set_option(h, b"cg_precond", 3.0) == 1
+    n = ctypes.c_int64()
+    assert lib.sfb_field_size(h, 9, ctypes.byref(n)) == 1
+    nb = ctypes.c_size_t()
+    assert lib.sfb_workspace_size(h, 5, 16, ctypes.byref(nb)) != 0                # bad precision
+    assert lib.sfb_local_points(h, 7, None, None) == 1
+    assert lib.sfb_build_basis_item_noalloc(h, 0, 99, 0, None, None, None) == 1    # no such item
