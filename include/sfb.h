@@ -18,7 +18,9 @@
  *    every pointer it passes.
  *  - Device memory comes only from the caller: sfb_workspace_size() says how
  *    much, sfb_set_workspace() hands it over (the caller frees it after
- *    sfb_destroy). All device work is ordered on the stream given to
+ *    sfb_destroy). The one exception is the allocation-free entry point
+ *    sfb_build_basis_item_noalloc, whose scratch is a static array of the
+ *    library. All device work is ordered on the stream given to
  *    sfb_create() / sfb_set_stream(); entry points that return host data
  *    synchronise that stream.
  *  - "host or device" arguments are detected with cudaPointerGetAttributes;
@@ -286,9 +288,14 @@ sfb_status sfb_interface_solve_batch(sfb_ctx* ctx, const double* y, const double
  * over every point solved since the last reset (host buffers of the field's
  * length). SFB_ERR_STATE if nothing was solved. */
 sfb_status sfb_moments(sfb_ctx* ctx, int32_t field, double* mean_out, double* var_out);
+/* Starts a new accumulation of the moments: the next batches' points are the
+ * only ones counted (so one collocation grid can be solved in several
+ * batches, or several grids one after another). SFB_ERR_WORKSPACE without a
+ * workspace. */
 sfb_status sfb_moments_reset(sfb_ctx* ctx);
 
-/* Number of CUDA kernels this context has launched so far. */
+/* Number of CUDA kernels this context has launched so far (a replayed basis
+ * graph counts its kernels). Host memory; no synchronisation. */
 sfb_status sfb_launch_count(const sfb_ctx* ctx, int64_t* n);
 
 /* Device time (ms, CUDA events) of the phases of the last
