@@ -5,6 +5,7 @@
  * runs the host set-up calls and prints what they return. It makes no call
  * that needs a GPU. tests/test_c_abi_program.py builds it with gcc and
  * compares its output with the Python binding's. */
+#include <stddef.h>
 #include <stdio.h>
 #include <stdlib.h>
 
@@ -64,6 +65,11 @@ int main(void) {
   printf("workspace_fp64 %zu\n", ws_fp64);
   printf("workspace_mixed %zu\n", ws_mixed);
   printf("shape %d %d %d\n", (int)threads, (int)ctas, (int)gbuf);
+  /* struct layouts, for the binding's mirrors: size and the last member's offset */
+  printf("layout_problem %zu %zu\n", sizeof(sfb_problem), offsetof(sfb_problem, source));
+  printf("layout_kl_region %zu %zu\n", sizeof(sfb_kl_region), offsetof(sfb_kl_region, n_modes_y));
+  printf("layout_collocation %zu %zu\n", sizeof(sfb_collocation), offsetof(sfb_collocation, m_dim));
+  printf("layout_basis_stats %zu %zu\n", sizeof(sfb_basis_stats), offsetof(sfb_basis_stats, tune_ms));
   /* an out-of-order call is an error status, not a crash */
   if (sfb_moments(ctx, SFB_FIELD_DARCY_P, y, w) == SFB_OK) {
     fprintf(stderr, "moments before any solve should fail\n");

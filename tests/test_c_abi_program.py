@@ -39,3 +39,11 @@ def test_c_program_uses_the_abi():
     assert int(out["workspace_fp64"][0]) == s.workspace_bytes(sfb.FP64, s.n_pts)
     assert int(out["workspace_mixed"][0]) == s.workspace_bytes(sfb.MIXED, s.n_pts)
     assert tuple(int(v) for v in out["shape"]) == sfb.basis_launch_shape(sfb.MIXED, 0, 0)
+    # the binding's ctypes mirrors have the C layouts
+    import ctypes
+    for key, cls, last in (("layout_problem", sfb.Problem, "source"), ("layout_kl_region", sfb.KLRegion, "n_modes_y"),
+                           ("layout_collocation", sfb.Collocation, "m_dim"),
+                           ("layout_basis_stats", sfb.BasisStats, "tune_ms")):
+        size, off = (int(v) for v in out[key])
+        assert ctypes.sizeof(cls) == size, key
+        assert getattr(cls, last).offset == off, key
