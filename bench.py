@@ -310,6 +310,7 @@ def run_ours(args):
         "mixed_form": {"ms_per_step": t_mixed, "basis_ms": b_mixed, "basis_kernel_ms": k_mixed,
                        "solve_moments_ms": s_mixed, "flux_responses_per_s": world * fr / (b_mixed * 1e-3),
                        "max_refine_steps": st_mixed["max_refine_steps"],
+                       "mean_refine_steps": st_mixed["mean_refine_steps"],
                        "unrefined_fp32_rel_error": st_mixed["max_first_correction"],
                        "final_rel_residual": st_mixed["max_rel_residual"],
                        "cg_iters_min_max": [int(iters.min()), int(iters.max())],

@@ -174,6 +174,7 @@ typedef struct {
   double tune_ms[2][4];       /* autotuner, per size class and launch shape: the  */
                               /* shorter of two timed launches of the class's     */
                               /* items (ms); 0: not timed                         */
+  double mean_refine_steps;   /* mixed form: refinement passes, mean over items   */
 } sfb_basis_stats;
 
 typedef struct sfb_ctx sfb_ctx;

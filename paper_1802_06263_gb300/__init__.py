@@ -61,7 +61,7 @@ class BasisStats(ctypes.Structure):
                 ("phase_cycles", ctypes.c_double * 16), ("kernel_ms", ctypes.c_double),
                 ("flops_fp32", ctypes.c_double), ("flops_fp64", ctypes.c_double),
                 ("launch_shape", ctypes.c_int32 * 2), ("graph", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("tune_ms", (ctypes.c_double * 4) * 2)]
+                ("tune_ms", (ctypes.c_double * 4) * 2), ("mean_refine_steps", ctypes.c_double)]
 
 
 _SIGS = {

@@ -998,6 +998,9 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
     for (int s = 0; s < (int)c->subs.size(); ++s) fr += (int64_t)c->subs[s].dofs.size() * c->n_local[s];
     stats->n_flux_responses = fr;
     stats->max_refine_steps = n ? *std::max_element(nref.begin(), nref.end()) : 0;
+    double nref_sum = 0.0;
+    for (int i = 0; i < n; ++i) nref_sum += nref[i];
+    stats->mean_refine_steps = n ? nref_sum / n : 0.0;
     stats->n_not_converged = n_nc;
     stats->max_rel_residual = n ? *std::max_element(resid.begin(), resid.end()) : 0.0;
     stats->max_first_correction = n ? *std::max_element(corr.begin(), corr.end()) : 0.0;

@@ -69,7 +69,7 @@ int main(void) {
   printf("layout_problem %zu %zu\n", sizeof(sfb_problem), offsetof(sfb_problem, source));
   printf("layout_kl_region %zu %zu\n", sizeof(sfb_kl_region), offsetof(sfb_kl_region, n_modes_y));
   printf("layout_collocation %zu %zu\n", sizeof(sfb_collocation), offsetof(sfb_collocation, m_dim));
-  printf("layout_basis_stats %zu %zu\n", sizeof(sfb_basis_stats), offsetof(sfb_basis_stats, tune_ms));
+  printf("layout_basis_stats %zu %zu\n", sizeof(sfb_basis_stats), offsetof(sfb_basis_stats, mean_refine_steps));
   /* an out-of-order call is an error status, not a crash */
   if (sfb_moments(ctx, SFB_FIELD_DARCY_P, y, w) == SFB_OK) {
     fprintf(stderr, "moments before any solve should fail\n");

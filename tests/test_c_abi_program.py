@@ -43,7 +43,7 @@ def test_c_program_uses_the_abi():
     import ctypes
     for key, cls, last in (("layout_problem", sfb.Problem, "source"), ("layout_kl_region", sfb.KLRegion, "n_modes_y"),
                            ("layout_collocation", sfb.Collocation, "m_dim"),
-                           ("layout_basis_stats", sfb.BasisStats, "tune_ms")):
+                           ("layout_basis_stats", sfb.BasisStats, "mean_refine_steps")):
         size, off = (int(v) for v in out[key])
         assert ctypes.sizeof(cls) == size, key
         assert getattr(cls, last).offset == off, key
