@@ -200,3 +200,63 @@ def test_projection_is_face_average():
             coef[e * 3 + a] = t ** 2
     avg = np.array([(f1 ** 3 - f0 ** 3) / (3 * (f1 - f0)) for f0, f1 in faces])
     assert np.allclose(P @ coef, avg, atol=1e-14)
+
+
+_NORMALS = {"bottom": (0, -1), "top": (0, 1), "left": (-1, 0), "right": (1, 0)}
+
+
+@pytest.mark.parametrize("case", ["harmonic", "layered"])
+def test_manufactured_solutions_converge_at_the_expected_orders(case):
+    """Mesh refinement against exact solutions of div(K grad p) = 0 on the
+    unit square, with quadratic mortars on all four sides (refined with the
+    grid, 4 cells per mortar element):
+    - "harmonic": K = 2, p = x^2 - y^2 + 0.3 x y, whose boundary trace the
+      quadratic mortars hold exactly;
+    - "layered": K = e^x, p = e^-x (K p_x is constant), K sampled at the
+      cell centres.
+    The cell-centre pressure converges at second order and the flux
+    functionals <u.n, xi_l> at first order (the lowest-order RT flux), on
+    grids of 8 to 64 cells per side. An inconsistent boundary
+    transmissibility, projection or stencil stalls one of the rates."""
+    nu = 1.0
+    rect = (0.0, 1.0, 0.0, 1.0)
+    if case == "harmonic":
+        p = lambda x, y: x ** 2 - y ** 2 + 0.3 * x * y             # noqa: E731
+        grad = lambda x, y: (2 * x + 0.3 * y, -2 * y + 0.3 * x)      # noqa: E731
+        Kf = lambda x, y: np.full_like(x, 2.0)                       # noqa: E731
+    else:
+        p = lambda x, y: np.exp(-x) + 0 * y                          # noqa: E731
+        grad = lambda x, y: (-np.exp(-x), 0 * y)                     # noqa: E731
+        Kf = lambda x, y: np.exp(x) + 0 * y                          # noqa: E731
+    e_p, e_f = [], []
+    for n in (8, 16, 32, 64):
+        sub, itfs = _sub_with_ifaces(rect, n, n, nu, n // 4, 2)
+        coef = _nodal_coeffs(sub, itfs, p, rect)
+        xc, yc = sub.cell_centres()
+        K = Kf(xc, yc)
+        X, C = sub.solve(K, coef[:, None], with_particular=False)
+        e_p.append(np.abs(X[:, 0] - p(xc, yc)).max())
+        flux = sub.interface_flux(K, X, C)[:, 0]
+        expect = np.zeros(len(sub.dofs))
+        for s, itf in itfs.items():
+            nx_, ny_ = _NORMALS[s]
+
+            def un(t, s=s, nx_=nx_, ny_=ny_):
+                x, y = {"bottom": (t, 0.0 * t), "top": (t, 1.0 + 0.0 * t),
+                        "left": (0.0 * t, t), "right": (1.0 + 0.0 * t, t)}[s]
+                gx, gy = grad(x, y)
+                return -(Kf(x, y) / nu) * (gx * nx_ + gy * ny_)
+            if case == "harmonic":
+                ints = itf.integrate(itf.s0, itf.s1, un)    # u.n is linear along each side
+            else:
+                # K p_x = -1 everywhere, so u.n is constant along each side
+                c0 = float(un(np.array([0.5]))[0])
+                ints = itf.integrate(itf.s0, itf.s1, lambda t, c0=c0: np.full_like(t, c0))
+            for k, g in enumerate(itf.dofs()):
+                expect[sub.local[g]] = ints[k]
+        e_f.append(np.abs(flux - expect).max() / np.abs(expect).max())
+    rate_p = [e_p[i] / e_p[i + 1] for i in range(3)]
+    rate_f = [e_f[i] / e_f[i + 1] for i in range(3)]
+    assert min(rate_p) > 3.3 and rate_p[-1] > 3.8, rate_p
+    assert min(rate_f) > 1.9, rate_f
+    assert e_p[-1] < 1e-4
