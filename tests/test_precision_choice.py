@@ -1,0 +1,104 @@
+"""Why the mixed form factors in FP32 on the SIMT pipe rather than in TF32 on
+the tensor cores: a CPU emulation of the basis kernel's block recurrence
+(explicit block inverses G_b of the diagonally scaled 5-point matrix) and of
+its block sweeps, with the operands of every product rounded to TF32 (10
+mantissa bits), to FP32, or split as 3xTF32 (hi*hi + hi*lo + lo*hi), and
+FP32 sums, inside FP64-residual iterative refinement. The matrix is the
+oracle's assembly of the precision workload's hardest item (subdomain 0,
+local realization 80, condition number about 3.4e3).
+
+Pinned facts:
+- FP32 and 3xTF32 reach 1e-12 after one refinement pass;
+- TF32 products in the solves with an FP32 factor still converge, one pass
+  behind;
+- TF32 for the whole recurrence converges slowly (each pass gains a factor
+  of 10-40, against about 1e5 for FP32), so 1e-10 costs several extra FP64
+  residual passes."""
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import sfb_workloads as W
+
+
+def _round(a, bits):
+    m, e = np.frexp(np.asarray(a, dtype=np.float64))
+    scale = 2.0 ** (bits + 1)
+    return np.ldexp(np.round(m * scale) / scale, e)
+
+
+def _f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def _product(G, U, mode):
+    if mode == "fp32":
+        return _f32(_f32(G) @ _f32(U))
+    gh, uh = _round(G, 10), _round(U, 10)
+    if mode == "tf32":
+        return _f32(gh @ uh)
+    gl, ul = _round(_f32(G) - gh, 10), _round(_f32(U) - uh, 10)
+    return _f32(gh @ uh + gh @ ul + gl @ uh)
+
+
+@pytest.fixture(scope="module")
+def item():
+    from oracle import coupled
+    p = coupled.Problem(W.precision())
+    y, _ = p.grid()
+    loc = p.local_realizations(0, y)[0]
+    sub = p.subs[0]
+    A, B, _ = sub.assemble(p.permeability(0, loc[80]))
+    A = sp.csr_matrix(A).toarray()
+    d = np.sqrt(np.diag(A))
+    Ah = A / d[:, None] / d[None, :]
+    B = B.toarray() if sp.issparse(B) else np.asarray(B)
+    rhs = B[:, :8] / d[:, None]
+    return Ah, rhs, sub.nx, sub.ny
+
+
+def _refine(Ah, rhs, nx, ny, factor_mode, solve_mode, passes):
+    D = [None] + [np.diag(np.diag(Ah[b * nx:(b + 1) * nx, (b - 1) * nx:b * nx])) for b in range(1, ny)]
+    G = []
+    for b in range(ny):
+        S = Ah[b * nx:(b + 1) * nx, b * nx:(b + 1) * nx]
+        if b:
+            S = S - D[b] @ G[-1] @ D[b]
+        if factor_mode == "tf32":
+            G.append(_round(np.linalg.inv(_round(S, 10)), 10))
+        else:
+            G.append(_f32(np.linalg.inv(_f32(S))))
+
+    def solve(r):
+        z = []
+        for b in range(ny):
+            u = r[b * nx:(b + 1) * nx] - (D[b] @ z[-1] if b else 0.0)
+            z.append(_product(G[b], u, solve_mode))
+        x = [None] * ny
+        for b in range(ny - 1, -1, -1):
+            x[b] = z[b] if b == ny - 1 else z[b] + _product(G[b], -(D[b + 1] @ x[b + 1]), solve_mode)
+        return np.concatenate(x)
+
+    exact = np.linalg.solve(Ah, rhs)
+    x = solve(rhs)
+    errs = [np.linalg.norm(x - exact) / np.linalg.norm(exact)]
+    for _ in range(passes):
+        x = x + solve(rhs - Ah @ x)            # FP64 residual
+        errs.append(np.linalg.norm(x - exact) / np.linalg.norm(exact))
+    return errs
+
+
+def test_tf32_factor_costs_extra_refinement_passes(item):
+    Ah, rhs, nx, ny = item
+    fp32 = _refine(Ah, rhs, nx, ny, "fp32", "fp32", 2)
+    split = _refine(Ah, rhs, nx, ny, "fp32", "3xtf32", 2)
+    tf32_solves = _refine(Ah, rhs, nx, ny, "fp32", "tf32", 4)
+    tf32_all = _refine(Ah, rhs, nx, ny, "tf32", "tf32", 4)
+    assert fp32[1] < 1e-11 and split[1] < 1e-11               # one pass past 1e-10
+    assert split[0] < 2 * fp32[0]                              # 3xTF32 keeps FP32 accuracy
+    assert tf32_solves[1] > 1e-7 and tf32_solves[3] < 1e-9     # converges one pass behind
+    assert tf32_all[0] > 1e-3                                  # the TF32 factor itself
+    assert tf32_all[2] > 1e-6                                  # still far off after two passes
+    rates = [tf32_all[i + 1] / tf32_all[i] for i in range(4)]
+    assert max(rates) < 0.2 and min(rates) > 0.01              # converging, but by < 100x a pass
