@@ -8,7 +8,7 @@ oracle's assembly of the precision workload's hardest item (subdomain 0,
 local realization 80, condition number about 3.4e3).
 
 Pinned facts:
-- FP32 and 3xTF32 reach 1e-12 after one refinement pass;
+- FP32 and 3xTF32 are below 1e-11 after one refinement pass;
 - TF32 products in the solves with an FP32 factor still converge, one pass
   behind;
 - TF32 for the whole recurrence converges slowly (each pass gains a factor
