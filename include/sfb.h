@@ -25,6 +25,12 @@
  *    synchronise that stream.
  *  - "host or device" arguments are detected with cudaPointerGetAttributes;
  *    host buffers are copied inside the call.
+ *  - Call order: sfb_create; sfb_kl_setup (or sfb_kl_setup_regions);
+ *    sfb_collocation_setup; sfb_workspace_size and sfb_set_workspace; then,
+ *    per basis build, sfb_build_stochastic_basis; per batch of points,
+ *    sfb_interface_solve_batch (after sfb_moments_reset for a new
+ *    accumulation); sfb_moments at any time after a solve; sfb_destroy. A
+ *    call out of order returns SFB_ERR_STATE.
  *  - Geometry: the Darcy box is tiled by px x py subdomains (s = iy*px + ix,
  *    bottom row first); one Stokes subdomain sits on top. Global mortar DOFs:
  *    Stokes-Darcy edges left to right, then vertical Darcy-Darcy edges row by
