@@ -34,11 +34,22 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, n), n
 
 
-@pytest.mark.parametrize("name", ["tiny", "medium", "batched", "anisotropic", "kl_regions"])
+def _reordered_regions():
+    """kl_regions with the region list in the other order: region 0 (whose
+    stochastic dims come first) is the top row of subdomains."""
+    w = W.kl_regions()
+    w["kl"]["regions"] = [(0.0, 1.0, 0.25, 0.5), (0.0, 1.0, 0.0, 0.25)]
+    w["kl"]["region_of"] = [1, 1, 0, 0]
+    w["kl"]["n_term"] = [3, 2]
+    w["kl"]["modes"] = [None, (2, 1)]
+    return w
+
+
+@pytest.mark.parametrize("name", ["tiny", "medium", "batched", "anisotropic", "kl_regions", "reordered_regions"])
 def test_host_setup_matches_oracle(name):
     sfb = _lib()
     from oracle import coupled
-    w = W.ALL[name]()
+    w = _reordered_regions() if name == "reordered_regions" else W.ALL[name]()
     s = sfb.Solver(w)
     p = coupled.Problem(w)
     # eigenvalues region by region (each region's first subdomain carries them)
