@@ -45,11 +45,18 @@ def _reordered_regions():
     return w
 
 
-@pytest.mark.parametrize("name", ["tiny", "medium", "batched", "anisotropic", "kl_regions", "reordered_regions"])
+@pytest.mark.parametrize("name", ["tiny", "medium", "batched", "anisotropic", "kl_regions", "reordered_regions",
+                                  "ragged", "ragged_tensor"])
 def test_host_setup_matches_oracle(name):
     sfb = _lib()
     from oracle import coupled
-    w = _reordered_regions() if name == "reordered_regions" else W.ALL[name]()
+    from gpu_common import make_workload
+    if name == "reordered_regions":
+        w = _reordered_regions()
+    elif name.startswith("ragged"):
+        w = make_workload(name)     # projections as local sets, quadratic mortars, sources
+    else:
+        w = W.ALL[name]()
     s = sfb.Solver(w)
     p = coupled.Problem(w)
     # eigenvalues region by region (each region's first subdomain carries them)
