@@ -188,7 +188,11 @@ typedef struct sfb_ctx sfb_ctx;
 /* Creates a context for one problem on the current CUDA device; stream is a
  * cudaStream_t (NULL = legacy default stream). Copies the descriptor and
  * assembles the host-side geometry (interfaces, mortar DOF maps, face
- * projections of Section 5.2 step 1). No device memory is touched. */
+ * projections of Section 5.2 step 1). It loads the library's device module on
+ * the current device, which reserves the static array of
+ * sfb_build_basis_item_noalloc there (a caller that reserves its own device
+ * memory pool should create its contexts first); no other device memory is
+ * touched. Without a usable device this step is skipped. */
 sfb_status sfb_create(const sfb_problem* prob, void* stream, sfb_ctx** out);
 void sfb_destroy(sfb_ctx* ctx);
 const char* sfb_last_error(const sfb_ctx* ctx);
@@ -326,19 +330,25 @@ sfb_status sfb_cg_phase_cycles(const sfb_ctx* ctx, double* cycles_out);
  * holds all device memory in its own pool, or a path that must not allocate).
  * Needs only sfb_kl_setup and sfb_collocation_setup, no workspace. The
  * working memory is a static 8 MiB device array inside the library that a GPU
- * keeps for the rest of the process once the library is used on it; items
- * needing more return SFB_ERR_UNSUPPORTED. Outputs: phi_out [R x R] and g_out
+ * keeps for the rest of the process once sfb_create has run with that device
+ * current (or this call first ran on it); items needing more return
+ * SFB_ERR_UNSUPPORTED before any copy or launch. Outputs: phi_out [R x R] and g_out
  * [R] (nullable; host or device), x_out [(R+1) x n_cells] device memory, the
- * same values as sfb_build_stochastic_basis + sfb_get_basis. The first call on
- * a device resolves the array's device address; make that first call before
- * any stream capture. Calls share the array: calls that overlap on the GPU
+ * same values as sfb_build_stochastic_basis + sfb_get_basis. Each call looks
+ * up the array's device address on the current device; if the module was not
+ * loaded there yet (no sfb_create with that device current), the first call
+ * loads it, so make that first call before any stream capture. Calls share
+ * the array: calls that overlap on the GPU
  * race and must be serialised by the caller. Synchronises the stream. */
 sfb_status sfb_build_basis_item_noalloc(sfb_ctx* ctx, int32_t sub, int32_t k, int32_t prec,
                                          double* phi_out, double* g_out, double* x_out);
 
 /* Tuning knobs (no counterpart in the paper):
  *   "refine_tol"     mixed form: stop refining when the predicted relative
- *                    error of X is below this (default 1e-10);
+ *                    error of X is below this (default 1e-11: the flux
+ *                    responses Phi come from boundary values of X less the
+ *                    mortar data, which cancel, so Phi keeps less relative
+ *                    accuracy than X);
  *   "refine_max"     mixed form: at most this many FP64 residual passes (8);
  *   "cg_check_every" CG iterations between convergence checks (8);
  *   "cg_persistent"  1: the whole CG in one cooperative launch (grid barriers

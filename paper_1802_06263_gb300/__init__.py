@@ -349,8 +349,31 @@ class Solver:
 
     def build_item_noalloc(self, sub, k, prec, phi_out, g_out, x_out, check=True):
         """One basis item through the allocation-free entry point; the caller
-        supplies the outputs (x_out a device tensor of (R+1) x n_cells)."""
-        rc = self.lib.sfb_build_basis_item_noalloc(self.h, sub, k, prec, ctypes.c_void_p(_ptr(phi_out)),
+        supplies the outputs (x_out a device tensor of (R+1) x n_cells).
+        Raises ValueError, before any call into the library, for outputs of
+        the wrong type, layout or size."""
+        R = len(self.subdomain_dofs(sub))
+        nx, ny = self.w["darcy_grid"][sub]
+
+        def _check_out(a, n, name, device):
+            if a is None:
+                return
+            if isinstance(a, np.ndarray):
+                ok = a.dtype == np.float64 and a.flags["C_CONTIGUOUS"] and a.size == n and not device
+            else:
+                import torch
+                ok = (a.dtype == torch.float64 and a.is_contiguous() and a.numel() == n
+                      and (a.is_cuda or not device))
+            if not ok:
+                raise ValueError("%s must be a contiguous float64 %sarray of %d elements"
+                                 % (name, "device " if device else "", n))
+
+        if x_out is None or phi_out is None:
+            raise ValueError("phi_out and x_out are required")
+        _check_out(phi_out, R * R, "phi_out", False)
+        _check_out(g_out, R, "g_out", False)
+        _check_out(x_out, (R + 1) * nx * ny, "x_out", True)
+        rc =self.lib.sfb_build_basis_item_noalloc(self.h, sub, k, prec, ctypes.c_void_p(_ptr(phi_out)),
                                                    ctypes.c_void_p(_ptr(g_out)), ctypes.c_void_p(_ptr(x_out)))
         if check:
             self._check(rc)

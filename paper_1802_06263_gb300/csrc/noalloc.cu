@@ -8,12 +8,13 @@
 // input context and the output buffers.
 //
 // The array is kNoAllocBytes (8 MiB) and, once the module is loaded on a GPU,
-// stays allocated there until the process exits. Every call shares it and it
-// keeps the previous call's contents, so the call clears the words that must
-// start at zero itself. Calls that overlap on the GPU (other streams or host
-// threads using the same device) race on the array; serialise them.
-#include <map>
-#include <mutex>
+// stays allocated there until the process exits. The module (and with it the
+// array) is loaded on the device that is current when sfb_create runs, so a
+// caller that reserves its own memory pool should create its contexts first.
+// Every call shares the array and it keeps the previous call's contents, so
+// the call clears the words that must start at zero itself. Calls that
+// overlap on the GPU (other streams or host threads using the same device)
+// race on the array; serialise them.
 #include <string>
 
 #include "sfb_ctx.h"
@@ -26,27 +27,26 @@ constexpr size_t kNoAllocBytes = size_t(8) << 20;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-std::mutex g_addr_mutex;
-std::map<int, void*> g_addr;  // device ordinal -> device address of the array
-
-// The host-side name of the array is not a device address: resolve it once per
-// device, with that device current, and cache the result.
-cudaError_t scratch_address(int dev, void** out) {
-  std::lock_guard<std::mutex> lock(g_addr_mutex);
-  auto it = g_addr.find(dev);
-  if (it != g_addr.end()) {
-    *out = it->second;
-    return cudaSuccess;
-  }
-  void* p = nullptr;
-  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-  if (e != cudaSuccess) return e;
-  g_addr[dev] = p;
-  *out = p;
-  return cudaSuccess;
+// The host-side name of the array is not a device address: look the address up
+// with the device current. It is looked up again on every call (cheap once the
+// module is loaded), so a context torn down and created again on the device
+// never leaves a stale address behind.
+cudaError_t scratch_address(void** out) {
+  *out = nullptr;
+  return cudaGetSymbolAddress(out, g_noalloc_scratch);
 }
 
 }  // namespace
+
+// Loads this file's module on the current device, which reserves the static
+// array there, and checks that its address resolves. Called by sfb_create;
+// on a machine without a usable device it does nothing (the entry point below
+// then reports the CUDA error itself).
+void noalloc_preload() {
+  int dev = 0;
+  void* p = nullptr;
+  if (cudaGetDevice(&dev) != cudaSuccess || scratch_address(&p) != cudaSuccess) cudaGetLastError();
+}
 
 }  // namespace sfb
 
@@ -74,10 +74,8 @@ extern "C" sfb_status sfb_build_basis_item_noalloc(sfb_ctx* c, int32_t sub, int3
   const int nx = H.nx, ny = H.ny, nc = nx * ny, R = (int)H.dofs.size(), C = R + 1, nt = H.n_term;
   const int64_t np = (nx + kPanel - 1) / kPanel * kPanel, cp = (C + 3) & ~3;
   const size_t gsz = prec == SFB_FP64 ? sizeof(double) : sizeof(float);
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
   void* base = nullptr;
-  if (e == cudaSuccess) e = scratch_address(dev, &base);
+  cudaError_t e = scratch_address(&base);
   if (e != cudaSuccess) {
     c->err = std::string("no-alloc scratch: ") + cudaGetErrorString(e);
     return SFB_ERR_CUDA;

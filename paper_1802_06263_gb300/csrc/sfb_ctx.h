@@ -191,7 +191,7 @@ struct sfb_ctx {
   int max_if_dof = 0;         // largest interface DOF count
   int64_t gmom_stride = 1;
   // options (sfb_set_option)
-  double opt_refine_tol = 1e-10;
+  double opt_refine_tol = 1e-11;
   int opt_refine_max = 8;
   int opt_cg_chunk = 8;
   int opt_cg_persistent = 1;    // interface CG in one cooperative launch (0: one launch per step)

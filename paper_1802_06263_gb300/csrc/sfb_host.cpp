@@ -355,6 +355,7 @@ sfb_status sfb_create(const sfb_problem* prob, void* stream, sfb_ctx** out) {
     return s;
   }
   stokes_assemble_host(c);
+  noalloc_preload();
   *out = c;
   return SFB_OK;
 }

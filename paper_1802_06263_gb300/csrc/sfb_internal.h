@@ -134,6 +134,8 @@ struct BasisArgs {
 
 // Launchers (basis.cu).
 cudaError_t launch_basis_fp64(const BasisArgs& a, int max_nx, int max_cols, cudaStream_t st);
+// loads the allocation-free entry point's module (and its static array) on the current device
+void noalloc_preload();
 cudaError_t launch_basis_mixed(const BasisArgs& a, int max_nx, int max_cols, int refine,
                                cudaStream_t st);
 cudaError_t launch_flux_epilogue(const BasisArgs& a, int max_R, cudaStream_t st);

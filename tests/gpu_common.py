@@ -13,6 +13,23 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def assert_close(a, b, tol, what=""):
+    """Relative agreement within ``tol`` twice over: in the 2-norm of the whole
+    array, and entry by entry against the array's scale,
+    ``|a_e - b_e| <= tol * max_e |b_e|``, so that a wrong small entry (a
+    low-variance cell) cannot hide in the norm of the large ones. An all-zero
+    reference needs ``|a_e| <= tol``."""
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    assert a.shape == b.shape, (what, a.shape, b.shape)
+    scale = float(np.abs(b).max()) if b.size else 0.0
+    err = float(np.abs(a - b).max()) if b.size else 0.0
+    if scale == 0.0:
+        assert err <= tol, (what, "absolute", err)
+        return
+    r = rel(a, b)
+    assert r < tol and err <= tol * scale, (what, "rel2", r, "max-entry", err / scale)
+
+
 @functools.lru_cache(maxsize=None)
 def oracle_case(key):
     """Oracle basis, per-point solutions and moments for a named workload."""
@@ -37,6 +54,12 @@ def make_workload(key):
         return W.small_test(nx=13, ny=9, px=3, py=2, n_sd=3, n_dd=2, n_term=2, degree=2, stokes=(7, 5),
                             bottom_pressure=0.5, source=[0.3, -0.2, 0.1, 0.7, -0.4, 0.2],
                             collocation={"kind": "smolyak", "lmax": 1, "rule": "paper"})
+    if key == "paper_l2":
+        # the paper's 1-D rule sequence 2^(p+1) - 1 (1, 3, 7 points) at level 2,
+        # where it differs from {1, 3, 3}: 57 points, 21 local realizations
+        return W.small_test(nx=9, ny=7, px=2, py=1, n_sd=2, n_dd=2, n_term=2, degree=1, stokes=(6, 5),
+                            sigma2=1.5, collocation={"kind": "smolyak", "lmax": 2, "rule": "paper"},
+                            name="paper_l2")
     if key == "ragged_tensor":
         return W.small_test(nx=10, ny=7, px=2, py=2, n_sd=2, n_dd=3, n_term=2, degree=1, stokes=(6, 5),
                             sigma2=2.0)
