@@ -237,6 +237,7 @@ class Problem:
         A_s, B_s = st.assemble()
         N = st.neumann_matrix()
         ds = np.array(st.dofs)
+        rhs[off_u:off_p] = st.load()
         mask, val = st.dirichlet()
         add(A_s, off_u, off_u)
         add(B_s.T, off_u, off_p)

@@ -24,12 +24,20 @@ import scipy.sparse.linalg as spla
 SIDES = ("bottom", "right", "top", "left")
 
 
+_G3_X = np.array([-np.sqrt(0.6), 0.0, np.sqrt(0.6)])
+_G3_W = np.array([5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0])
+
+
 class DarcySub:
     """Geometry and boundary description of one Darcy subdomain.
 
     ``sides[s]`` is ``("iface", Interface)``, ``("noflow",)`` or
-    ``("dirichlet", value)``. ``dofs`` are the subdomain's mortar DOFs (sorted
-    global indices); ``R_i`` of the paper is the restriction to them.
+    ``("dirichlet", value)``; ``value`` is a constant or a function of the
+    point ``(x, y)`` on the side (the outer pressure data of Eqs. 2.5-2.7,
+    entering through its face averages). ``source`` is the constant ``q_d``
+    or a function ``q_d(x, y)``, entering through its cell integrals. ``dofs``
+    are the subdomain's mortar DOFs (sorted global indices); ``R_i`` of the
+    paper is the restriction to them.
     """
 
     def __init__(self, sid, rect, nx, ny, nu, source=0.0):
@@ -75,6 +83,41 @@ class DarcySub:
             cells = np.arange(ny) * nx + nx - 1
             faces = [(y0 + j * self.hy, y0 + (j + 1) * self.hy) for j in range(ny)]
         return cells, faces
+
+    def source_integrals(self):
+        """Cell integrals of the source ``q_d`` (3 x 3 Gauss-Legendre per cell
+        for a function; ``q_d h_x h_y`` for a constant): the right-hand side of
+        the mass balance Eq. 2.7 in cell-centred form."""
+        if not callable(self.source):
+            return np.full(self.n_cells, self.source * self.hx * self.hy)
+        xc, yc = self.cell_centres()
+        tot = np.zeros(self.n_cells)
+        for a, wa in zip(_G3_X, _G3_W):
+            for b, wb in zip(_G3_X, _G3_W):
+                tot += wa * wb * self.source(xc + 0.5 * a * self.hx, yc + 0.5 * b * self.hy)
+        return tot * 0.25 * self.hx * self.hy
+
+    def dirichlet_values(self, side):
+        """Face averages of a side's Dirichlet pressure (3-point Gauss-Legendre
+        per face for a function, the constant itself otherwise)."""
+        val = self.sides[side][1]
+        cells, faces = self.side_faces(side)
+        if not callable(val):
+            return np.full(len(cells), float(val))
+        x0, x1, y0, y1 = self.rect
+        out = np.zeros(len(faces))
+        for q, (a, b) in enumerate(faces):
+            s = 0.5 * (a + b) + 0.5 * (b - a) * _G3_X
+            if side == "bottom":
+                v = val(s, np.full(3, y0))
+            elif side == "top":
+                v = val(s, np.full(3, y1))
+            elif side == "left":
+                v = val(np.full(3, x0), s)
+            else:
+                v = val(np.full(3, x1), s)
+            out[q] = 0.5 * (_G3_W @ v)
+        return out
 
     def boundary_trans(self, K, side):
         """Half-cell transmissibility ``2 K |e| / (nu h_perp)`` of the faces of a
@@ -126,7 +169,7 @@ class DarcySub:
         rows += [a_, b_]; cols += [b_, a_]; vals += [-t, -t]
         np.add.at(diag, a_, t); np.add.at(diag, b_, t)
         B = np.zeros((n, len(self.dofs)))
-        bbar = np.full(n, self.source * self.hx * self.hy)
+        bbar = self.source_integrals()
         for side in SIDES:
             kind = self.sides[side]
             if kind[0] == "noflow":
@@ -137,7 +180,7 @@ class DarcySub:
             if kind[0] == "iface":
                 B[cells] += tb[:, None] * self.projection(side)
             else:
-                bbar[cells] += tb * kind[1]
+                bbar[cells] += tb * self.dirichlet_values(side)
         rows.append(np.arange(n)); cols.append(np.arange(n)); vals.append(diag)
         A = sp.csc_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                           shape=(n, n))
@@ -202,7 +245,7 @@ class DarcySub:
             if kind[0] == "iface":
                 g = self.projection(side) @ c_local
             else:
-                g = np.full(len(cells), kind[1])
+                g = self.dirichlet_values(side)
             F = tb * (p[cells] - g)  # outward flux through each face
             if side == "left":
                 ux[:, 0] = -F / self.hy

@@ -30,6 +30,25 @@ _GL_X = np.array([-np.sqrt(0.6), 0.0, np.sqrt(0.6)])
 _GL_W = np.array([5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0])
 # edge-midpoint rule on a triangle: exact for quadratics
 _TRI_Q = np.array([[0.5, 0.5, 0.0], [0.0, 0.5, 0.5], [0.5, 0.0, 0.5]])
+# 7-point rule on a triangle, exact for degree 5 (Radon's rule, as tabulated
+# by Strang and Fix): barycentric points and weights (relative to the area)
+_R7_A1, _R7_B1 = 0.059715871789770, 0.470142064105115
+_R7_A2, _R7_B2 = 0.797426985353087, 0.101286507323456
+_TRI_R7 = np.array([[1 / 3, 1 / 3, 1 / 3],
+                    [_R7_A1, _R7_B1, _R7_B1], [_R7_B1, _R7_A1, _R7_B1], [_R7_B1, _R7_B1, _R7_A1],
+                    [_R7_A2, _R7_B2, _R7_B2], [_R7_B2, _R7_A2, _R7_B2], [_R7_B2, _R7_B2, _R7_A2]])
+_TRI_R7_W = np.array([0.225] + [0.132394152788506] * 3 + [0.125939180544827] * 3)
+
+
+def _p2_values(L):
+    """The six P2 basis functions (vertices 0..2, then edges 01, 12, 20) at
+    barycentric point ``L``."""
+    v = np.empty(6)
+    for i in range(3):
+        v[i] = L[i] * (2.0 * L[i] - 1.0)
+    for k, (i, j) in enumerate(((0, 1), (1, 2), (2, 0))):
+        v[3 + k] = 4.0 * L[i] * L[j]
+    return v
 
 
 def _p2_grads(L, gl):
@@ -47,6 +66,12 @@ class StokesSub:
     def __init__(self, rect, sx, sy, nu, alpha, u_in, k_bjs=1.0):
         self.rect, self.sx, self.sy = rect, sx, sy
         self.nu, self.alpha, self.u_in, self.k_bjs = nu, alpha, u_in, k_bjs
+        # optional data of Eqs. 2.2-2.4 beyond the test cases' (zero force,
+        # parabolic inflow): a body force f_s(x, y) -> (f_x, f_y), and a velocity
+        # u(x, y) -> (u_x, u_y) imposed on the sides listed in dirichlet_sides
+        self.force = None
+        self.u_exact = None
+        self.dirichlet_sides = ("left", "top")
         x0, x1, y0, y1 = rect
         self.hx, self.hy = (x1 - x0) / sx, (y1 - y0) / sy
         self.NX, self.NY = 2 * sx + 1, 2 * sy + 1
@@ -153,13 +178,45 @@ class StokesSub:
                         N[nn + nid, self.local[g]] += -vals[a]   # n = (0, -1)
         return N
 
+    def load(self):
+        """Load vector ``(f_s, v)`` of the body force over the velocity DOFs
+        (Eq. 2.2), by the 7-point degree-5 rule on every triangle; zero
+        without a force."""
+        nn = self.n_nodes
+        F = np.zeros(2 * nn)
+        if self.force is None:
+            return F
+        for nodes, _, xy in self.triangles():
+            (xa, ya), (xb, yb), (xc, yc) = xy
+            area = 0.5 * abs((xb - xa) * (yc - ya) - (xc - xa) * (yb - ya))
+            for L, w in zip(_TRI_R7, _TRI_R7_W):
+                x = L[0] * xa + L[1] * xb + L[2] * xc
+                y = L[0] * ya + L[1] * yb + L[2] * yc
+                fx, fy = self.force(np.array([x]), np.array([y]))
+                phi = _p2_values(L) * (w * area)
+                F[nodes] += phi * float(fx[0])
+                F[[nn + n for n in nodes]] += phi * float(fy[0])
+        return F
+
     def dirichlet(self):
         """Dirichlet DOFs and values: inflow ``u = (u_in 4 s (1 - s), 0)`` on the
         left edge (``s`` the normalised height), no slip on the top edge (the
-        outer data of Section 6.1, reading A6)."""
+        outer data of Section 6.1, reading A6); or, with ``u_exact`` set, that
+        velocity on the sides in ``dirichlet_sides``."""
         nn = self.n_nodes
         mask = np.zeros(2 * nn, dtype=bool)
         val = np.zeros(2 * nn)
+        if self.u_exact is not None:
+            xs, ys = self.node_xy()
+            ux, uy = self.u_exact(xs, ys)
+            sel = {"left": [self.node(0, j) for j in range(self.NY)],
+                   "right": [self.node(self.NX - 1, j) for j in range(self.NY)],
+                   "top": [self.node(i, self.NY - 1) for i in range(self.NX)]}
+            for side in self.dirichlet_sides:
+                for n in sel[side]:
+                    mask[n] = mask[nn + n] = True
+                    val[n], val[nn + n] = ux[n], uy[n]
+            return mask, val
         for j in range(self.NY):
             n = self.node(0, j)
             s = j / (self.NY - 1)
