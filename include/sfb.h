@@ -79,8 +79,18 @@ typedef enum {
  *               ||g - S lambda|| <= rtol ||g|| holds in FP64 (residual
  *               replacement in the manner of reliable-update Krylov methods).
  *               Not in the paper: an operator-precision choice for GPUs whose
- *               FP64 rate is a small fraction of FP32. */
-typedef enum { SFB_CG = 0, SFB_CG_MIXED = 1 } sfb_krylov;
+ *               FP64 rate is a small fraction of FP32.
+ * SFB_GMRES:    restarted GMRES(m) in FP64 (m = option "gmres_restart",
+ *               default 30), right-preconditioned with the CG's
+ *               preconditioner (option "cg_precond", applied in FP64) so that
+ *               its residual is the unpreconditioned one; classical
+ *               Gram-Schmidt with one re-orthogonalization pass, Givens
+ *               rotations; a cycle ends when the least-squares residual
+ *               reaches rtol ||g|| or after m steps, and a point is accepted
+ *               only on its FP64 true residual ||g - S lambda|| <= rtol ||g||
+ *               (otherwise the next cycle starts from it). The iteration
+ *               count is the number of Arnoldi steps. */
+typedef enum { SFB_CG = 0, SFB_CG_MIXED = 1, SFB_GMRES = 2 } sfb_krylov;
 
 typedef enum {
   SFB_FIELD_DARCY_P = 0,     /* cell pressures, subdomain by subdomain, c = iy*nx+ix    */
@@ -269,13 +279,17 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* ctx, int32_t prec, sfb_basis_stat
  * class is one launch, the two run concurrently. prec selects the factor
  * precision (SFB_FP64: one shape per class; SFB_MIXED, SFB_FP32_NOREFINE: two).
  * Writes the shape's threads per CTA, the CTAs per SM its register budget is
- * compiled for and its number of shared-memory G_b buffers (2: the next block
- * row's inverse is prefetched). Pointers are host memory and nullable.
- * SFB_ERR_ARG for a shape index out of range. By default the first build of
- * each precision times every shape of each class on that class's own items
- * and keeps the fastest (option "basis_autotune"). */
+ * compiled for, its number of shared-memory G_b buffers (2: the next block
+ * row's inverse is prefetched) and whether it runs the block-row products on
+ * the tensor cores (tcgen05 = 1: SFB_MIXED / SFB_FP32_NOREFINE shape 2, grids
+ * up to 64 cells wide; tcgen05.mma kind::tf32 with every operand split into
+ * two TF32 parts and FP32 accumulation, the block inverses fed by TMA tensor
+ * copies). Pointers are host memory and nullable. SFB_ERR_ARG for a shape that
+ * the precision and class do not have. By default the first build of each
+ * precision times every shape of each class on that class's own items and
+ * keeps the fastest (option "basis_autotune"). */
 sfb_status sfb_basis_launch_shape(int32_t prec, int32_t wide, int32_t shape, int32_t* threads,
-                                  int32_t* ctas_per_sm, int32_t* g_buffers);
+                                  int32_t* ctas_per_sm, int32_t* g_buffers, int32_t* tcgen05);
 
 /* Read-back of one stored basis item (host or device buffers): phi [R x R]
  * row-major, g [R], x [(R+1) x n_cells] (pressure responses, column j is the
@@ -381,6 +395,7 @@ sfb_status sfb_build_basis_item_noalloc(sfb_ctx* ctx, int32_t sub, int32_t k, in
  *                    CG skip its first grid barrier, so that the other CTAs'
  *                    waits run out (1 s). The solve returns SFB_ERR_TIMEOUT and
  *                    the context stays usable. Cleared by that solve (0);
+ *   "gmres_restart"  SFB_GMRES: restart length m, 1..30 (30);
  *   "cg_replace_ratio"  SFB_CG_MIXED: a point's residual is replaced by the
  *                    FP64 residual at the next check once the recursive one
  *                    has dropped by this factor since the last replacement,

@@ -20,7 +20,7 @@ SFB_OK = 0
 SFB_ERR_NOT_CONVERGED = 6
 SFB_ERR_TIMEOUT = 9
 FP64, MIXED, FP32_NOREFINE = 0, 1, 2
-CG, CG_MIXED = 0, 1
+CG, CG_MIXED, GMRES = 0, 1, 2
 FIELDS = {"darcy_p": 0, "darcy_flux": 1, "stokes_u": 2, "stokes_p": 3}
 STATUS = {0: "OK", 1: "ARG", 2: "STATE", 3: "CUDA", 4: "WORKSPACE", 5: "NONFINITE",
           6: "NOT_CONVERGED", 7: "NOT_SPD", 8: "UNSUPPORTED", 9: "TIMEOUT"}
@@ -96,7 +96,8 @@ _SIGS = {
     "sfb_solve_timings": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _i32p]),
     "sfb_cg_phase_cycles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sfb_launch_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
-    "sfb_basis_launch_shape": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p]),
+    "sfb_basis_launch_shape": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p,
+                                              _i32p]),
     "sfb_build_basis_item_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
@@ -124,14 +125,16 @@ def load():
 
 
 def basis_launch_shape(prec, wide, shape):
-    """(threads per CTA, CTAs per SM, G buffers) of a basis-kernel launch
-    shape, or None when the precision has no such shape for that size class."""
+    """(threads per CTA, CTAs per SM, G buffers, tcgen05) of a basis-kernel
+    launch shape (tcgen05 = 1: the tensor-core form), or None when the
+    precision has no such shape for that size class."""
     lib = load()
-    t, c, g = (ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32())
-    rc = lib.sfb_basis_launch_shape(prec, int(bool(wide)), shape, ctypes.byref(t), ctypes.byref(c), ctypes.byref(g))
+    t, c, g, tc = (ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32())
+    rc = lib.sfb_basis_launch_shape(prec, int(bool(wide)), shape, ctypes.byref(t), ctypes.byref(c), ctypes.byref(g),
+                                    ctypes.byref(tc))
     if rc != SFB_OK:
         return None
-    return t.value, c.value, g.value
+    return t.value, c.value, g.value, tc.value
 
 
 class SfbError(RuntimeError):
@@ -382,7 +385,8 @@ class Solver:
     def solve(self, y, w, rtol=1e-10, max_it=1000, lam_out=None, iters_out=None, check=True, krylov=CG):
         """Interface CG for a batch of points (host numpy or device torch
         arrays); outputs go to the given buffers (host or device). ``krylov``
-        is CG (FP64) or CG_MIXED (FP32 products, FP64 residuals)."""
+        is CG (FP64), CG_MIXED (FP32 products, FP64 residuals) or GMRES (restarted
+        GMRES(m) in FP64)."""
         y = np.ascontiguousarray(y, dtype=np.float64) if isinstance(y, np.ndarray) else y
         w = np.ascontiguousarray(w, dtype=np.float64) if isinstance(w, np.ndarray) else w
         n = int(y.shape[0])

@@ -612,14 +612,16 @@ cudaError_t launch_basis(const BasisArgs& a, int max_nx, int max_cols, int refin
 // wide), the candidates that the build's autotuner times. Shape 0 is the one
 // launch_basis picks. FP32 has a second shape per class that trades the G
 // prefetch buffer against resident CTAs the other way: narrow grids 3 CTAs per
-// SM with two G buffers, wide grids 2 CTAs per SM with one. FP64 has one
-// shape per class (its shared memory already limits residency).
-constexpr int kShapes = 2;
+// SM with two G buffers, wide grids 2 CTAs per SM with one. Its third shape,
+// narrow grids only, is the tensor-core kernel of basis_tc.cu. FP64 has one
+// shape per class (its shared memory already limits residency). Entries with
+// zero threads do not exist.
+constexpr int kShapes = 3;
 constexpr BasisShape kShape[2][2][kShapes] = {
     // FP32: narrow, wide
-    {{{256, 4, 1}, {256, 3, 2}}, {{256, 1, 2}, {256, 2, 1}}},
+    {{{256, 4, 1, 0}, {256, 3, 2, 0}, {256, 3, 1, 1}}, {{256, 1, 2, 0}, {256, 2, 1, 0}, {0, 0, 0, 0}}},
     // FP64: narrow, wide
-    {{{256, 2, 1}, {0, 0, 0}}, {{512, 1, 1}, {0, 0, 0}}},
+    {{{256, 2, 1, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}}, {{512, 1, 1, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}}},
 };
 
 template <typename T, int MT, int NT, int MINB, int GB>
@@ -652,6 +654,8 @@ cudaError_t shape_dispatch(const BasisArgs* a, bool wide, int shape, int max_nx,
       const size_t sm = basis_smem<T>(max_nx, max_cols, 1);
       return ctas ? occupancy_of<T, 4, 256, 2, 1>(sm, ctas) : launch_one<T, 4, 256, 2, 1>(*a, sm, refine, st);
     }
+    if (!wide && shape == 2)
+      return ctas ? basis_tc_ctas(max_nx, max_cols, ctas) : launch_basis_tc(*a, max_nx, max_cols, refine, st);
   } else {
     const size_t sm = basis_smem<T>(max_nx, max_cols, 1);
     if (!wide && shape == 0)
@@ -668,13 +672,16 @@ int basis_shape_count(int fp64) { return fp64 ? 1 : kShapes; }
 
 bool basis_shape_desc(int fp64, int wide, int shape, BasisShape* out) {
   if (shape < 0 || shape >= basis_shape_count(fp64)) return false;
-  *out = kShape[fp64 ? 1 : 0][wide ? 1 : 0][shape];
+  const BasisShape& d = kShape[fp64 ? 1 : 0][wide ? 1 : 0][shape];
+  if (d.threads == 0) return false;
+  *out = d;
   return true;
 }
 
 cudaError_t basis_shape_ctas(int fp64, int wide, int shape, int max_nx, int max_cols, int* ctas) {
   *ctas = 0;
-  if (shape < 0 || shape >= basis_shape_count(fp64)) return cudaErrorInvalidValue;
+  BasisShape d;
+  if (!basis_shape_desc(fp64, wide, shape, &d)) return cudaErrorInvalidValue;
   if ((wide != 0) != (max_nx > 64)) return cudaErrorInvalidValue;
   return fp64 ? shape_dispatch<double>(nullptr, wide, shape, max_nx, max_cols, 0, nullptr, ctas)
               : shape_dispatch<float>(nullptr, wide, shape, max_nx, max_cols, 0, nullptr, ctas);
@@ -682,7 +689,8 @@ cudaError_t basis_shape_ctas(int fp64, int wide, int shape, int max_nx, int max_
 
 cudaError_t launch_basis_shape(const BasisArgs& a, int fp64, int wide, int shape, int max_nx, int max_cols,
                                int refine, cudaStream_t st) {
-  if (shape < 0 || shape >= basis_shape_count(fp64)) return cudaErrorInvalidValue;
+  BasisShape d;
+  if (!basis_shape_desc(fp64, wide, shape, &d)) return cudaErrorInvalidValue;
   if ((wide != 0) != (max_nx > 64)) return cudaErrorInvalidValue;
   return fp64 ? shape_dispatch<double>(&a, wide, shape, max_nx, max_cols, 0, st, nullptr)
               : shape_dispatch<float>(&a, wide, shape, max_nx, max_cols, refine, st, nullptr);

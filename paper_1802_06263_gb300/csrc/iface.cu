@@ -696,6 +696,254 @@ __global__ void reliable_kernel(IfaceArgs a, double rtol, int it) {
   reliable_point(a, l, threadIdx.x & 31, stage_all + (threadIdx.x >> 5) * a.n_lambda, rtol, it);
 }
 
+// ---- restarted GMRES ------------------------------------------------------------------
+// GMRES(m) for every point's S^l lambda = g^l (Section 5.4 Step 5 names CG or
+// GMRES for the interface problem), one warp per point, all points in
+// lockstep like the CG. Right preconditioning with the CG's preconditioner M
+// (none, Jacobi, or the interface blocks, whose FP32 inverses are applied here
+// in FP64 arithmetic so that M^{-1} is one fixed linear map): the Arnoldi
+// process runs on S M^{-1}, its residual is that of the unpreconditioned
+// system, and lambda = M^{-1} u. Orthogonalization is classical Gram-Schmidt
+// with one re-orthogonalization pass (each pass: all the cycle's dot products
+// in one sweep over the DOFs, then one update sweep). Givens rotations keep
+// the least-squares residual |gv[j+1]|; at the end of a cycle (that residual
+// at rtol ||g||, m steps, or a breakdown) the warp solves the triangular
+// system, adds M^{-1} V y to lambda and marks the point for the FP64 true
+// residual g - S lambda, which either accepts it or starts the next cycle.
+struct GmArgs {
+  double* V;    // [kGmresMax + 1][n_pts][n_lambda]: Krylov basis
+  double* st;   // [n_pts][kGmresState]: Hessenberg columns, rotations, rotated right-hand side
+  int* j;       // [n_pts]: steps taken in the current cycle
+  int m;        // restart length (<= kGmresMax)
+};
+// a point's state: column k of H (entries 0..k+1) at k * (kGmresMax + 1), then
+// the cosines, the sines and the rotated right-hand side
+__device__ __forceinline__ double* gm_col(const GmArgs& g, int64_t l, int k) {
+  return g.st + l * kGmresState + k * (kGmresMax + 1);
+}
+__device__ __forceinline__ double* gm_cs(const GmArgs& g, int64_t l) {
+  return g.st + l * kGmresState + kGmresMax * (kGmresMax + 1);
+}
+__device__ __forceinline__ double* gm_sn(const GmArgs& g, int64_t l) { return gm_cs(g, l) + kGmresMax; }
+__device__ __forceinline__ double* gm_gv(const GmArgs& g, int64_t l) { return gm_cs(g, l) + 2 * kGmresMax; }
+__device__ __forceinline__ double* gm_v(const GmArgs& g, const IfaceArgs& a, int i, int64_t l) {
+  return g.V + ((int64_t)i * a.n_pts + l) * a.n_lambda;
+}
+
+// (M^{-1} v)_d for point l with v in global memory, in FP64 arithmetic.
+__device__ __forceinline__ double precond64(const IfaceArgs& a, int64_t l, const double* v, int d) {
+  if (a.minv) {
+    const int e = a.dof_if[d];
+    const int n = a.if_n[e], d0 = a.if_off[e], i = d - d0;
+    const float* M = a.minv + l * a.minv_ld + a.if_moff[e] + i * n;
+    double z = 0.0;
+    for (int j = 0; j < n; ++j) z = fma(f32_to_f64_bits(M[j]), v[d0 + j], z);
+    return z;
+  }
+  if (a.dinv) return a.dinv[l * a.n_lambda + d] * v[d];
+  return v[d];
+}
+
+// g_d of point l (the two units' flux data); with want_diag also the diagonal
+// of S^l at d.
+__device__ __forceinline__ double rhs_g(const IfaceArgs& a, int64_t l, int64_t d, double* diag) {
+  double g = 0.0, dg = 0.0;
+  for (int side = 0; side < 2; ++side) {
+    const int u = a.ldof[4 * d + 2 * side], loc = a.ldof[4 * d + 2 * side + 1];
+    const int k = u < a.ns ? a.kmap[l * a.ns + u] : 0;
+    if (k < 0) continue;
+    int R;
+    const double* ph = unit_phi(a, u, k, R);
+    g += ph[R * R + loc];
+    dg += ph[loc * R + loc];
+  }
+  if (diag) *diag = dg;
+  return g;
+}
+
+// New cycle of point l from the residual r (global, n_lambda entries) of norm
+// rn > 0: V_0 = r / rn, gv = (rn, 0, ...), j = 0, p = M^{-1} V_0.
+__device__ __forceinline__ void gm_new_cycle(const IfaceArgs& a, const GmArgs& g, int64_t l, int lane,
+                                             const double* r, double rn) {
+  double* v0 = gm_v(g, a, 0, l);
+  const double inv = 1.0 / rn;
+  for (int64_t d = lane; d < a.n_lambda; d += 32) v0[d] = r[d] * inv;
+  double* gv = gm_gv(g, l);
+  for (int i = lane; i <= kGmresMax; i += 32) gv[i] = i == 0 ? rn : 0.0;
+  __syncwarp();
+  double* pl = a.p + l * a.n_lambda;
+  for (int64_t d = lane; d < a.n_lambda; d += 32) pl[d] = precond64(a, l, v0, (int)d);
+  if (lane == 0) g.j[l] = 0;
+}
+
+// First cycle from lambda = 0: r = g, ||g||, the Jacobi diagonal when used.
+__global__ void gmres_init_kernel(IfaceArgs a, GmArgs g) {
+  const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (l >= a.n_pts) return;
+  double* rl = a.r + l * a.n_lambda;
+  double s2 = 0.0;
+  for (int64_t d = lane; d < a.n_lambda; d += 32) {
+    double dg = 0.0;
+    const double gd = rhs_g(a, l, d, &dg);
+    if (a.dinv) a.dinv[l * a.n_lambda + d] = dg > 0.0 ? 1.0 / dg : 1.0;
+    rl[d] = gd;
+    a.lam[l * a.n_lambda + d] = 0.0;
+    s2 = fma(gd, gd, s2);
+  }
+  s2 = warp_sum(s2);
+  const double gn = sqrt(s2);
+  int st = a.pstat[l] & kBadIdx;
+  if (!st && s2 == 0.0) st = 1;   // zero data: converged with lambda = 0
+  __syncwarp();
+  if (st == 0) gm_new_cycle(a, g, l, lane, rl, gn);
+  if (lane == 0) {
+    a.gn[l] = gn;
+    a.pstat[l] = st;
+  }
+}
+
+// One Arnoldi step of every iterating point, on the products Y = S p of
+// p = M^{-1} V_j: w = S M^{-1} V_j orthogonalized against V_0..V_j (two
+// classical Gram-Schmidt passes), H column j, V_{j+1} = w / ||w||, the
+// rotations, and at the end of the cycle the solution update.
+__global__ void __launch_bounds__(256) gmres_arnoldi_kernel(IfaceArgs a, GmArgs g, int it, double rtol) {
+  const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (l >= a.n_pts) return;
+  if (a.pstat[l] != 0) return;
+  const int j = g.j[l];
+  const int64_t n = a.n_lambda;
+  const double* Yl = a.Y + l * a.NY;
+  double* w = a.r + l * n;   // the new direction, then the update's V y
+  for (int64_t d = lane; d < n; d += 32) w[d] = Yl[a.yoff[2 * d]] + Yl[a.yoff[2 * d + 1]];
+  __syncwarp();
+  double* hcol = gm_col(g, l, j);
+  for (int pass = 0; pass < 2; ++pass) {
+    double acc[kGmresMax + 1];
+#pragma unroll
+    for (int i = 0; i <= kGmresMax; ++i) acc[i] = 0.0;
+    for (int64_t d = lane; d < n; d += 32) {
+      const double wd = w[d];
+#pragma unroll
+      for (int i = 0; i <= kGmresMax; ++i)
+        if (i <= j) acc[i] = fma(gm_v(g, a, i, l)[d], wd, acc[i]);
+    }
+#pragma unroll
+    for (int i = 0; i <= kGmresMax; ++i)
+      if (i <= j) acc[i] = warp_sum(acc[i]);
+    for (int64_t d = lane; d < n; d += 32) {
+      double wd = w[d];
+#pragma unroll
+      for (int i = 0; i <= kGmresMax; ++i)
+        if (i <= j) wd = fma(-acc[i], gm_v(g, a, i, l)[d], wd);
+      w[d] = wd;
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int i = 0; i <= kGmresMax; ++i)
+        if (i <= j) hcol[i] = pass == 0 ? acc[i] : hcol[i] + acc[i];
+    }
+    __syncwarp();
+  }
+  double s2 = 0.0;
+  for (int64_t d = lane; d < n; d += 32) s2 = fma(w[d], w[d], s2);
+  const double hn = sqrt(warp_sum(s2));
+  const bool brk = !(hn > 0.0);   // the Krylov space is invariant: the cycle's solution is exact
+  if (!brk) {
+    double* vn = gm_v(g, a, j + 1, l);
+    const double inv = 1.0 / hn;
+    for (int64_t d = lane; d < n; d += 32) vn[d] = w[d] * inv;
+  }
+  // rotations (lane 0): the earlier ones on column j, then the one that
+  // annihilates H[j+1][j]; the rotated right-hand side's last entry is the
+  // least-squares residual of the cycle
+  int end = 0;
+  if (lane == 0) {
+    double* cs = gm_cs(g, l);
+    double* sn = gm_sn(g, l);
+    double* gv = gm_gv(g, l);
+    for (int i = 0; i < j; ++i) {
+      const double t = cs[i] * hcol[i] + sn[i] * hcol[i + 1];
+      hcol[i + 1] = -sn[i] * hcol[i] + cs[i] * hcol[i + 1];
+      hcol[i] = t;
+    }
+    const double hjj = hcol[j];
+    const double rho = hypot(hjj, hn);
+    const double c = rho > 0.0 ? hjj / rho : 1.0, s = rho > 0.0 ? hn / rho : 0.0;
+    cs[j] = c;
+    sn[j] = s;
+    hcol[j] = rho;
+    hcol[j + 1] = 0.0;
+    gv[j + 1] = -s * gv[j];
+    gv[j] = c * gv[j];
+    end = (fabs(gv[j + 1]) <= rtol * a.gn[l] || j + 1 >= g.m || brk) ? 1 : 0;
+  }
+  end = __shfl_sync(0xffffffffu, end, 0);
+  __syncwarp();
+  if (!end) {
+    const double* vn = gm_v(g, a, j + 1, l);
+    double* pl = a.p + l * n;
+    for (int64_t d = lane; d < n; d += 32) pl[d] = precond64(a, l, vn, (int)d);
+    if (lane == 0) g.j[l] = j + 1;
+    return;
+  }
+  // end of the cycle: H(0:jn, 0:jn) y = gv(0:jn) by back substitution (lane k
+  // holds y_k), then lambda += M^{-1} (V y)
+  const int jn = j + 1;
+  const double* gv = gm_gv(g, l);
+  double yk = 0.0;
+  for (int i = jn - 1; i >= 0; --i) {
+    double part = (lane > i && lane < jn) ? gm_col(g, l, lane)[i] * yk : 0.0;
+    part = warp_sum(part);
+    if (lane == i) yk = (gv[i] - part) / gm_col(g, l, i)[i];
+  }
+  double ys[kGmresMax];
+#pragma unroll
+  for (int i = 0; i < kGmresMax; ++i) ys[i] = __shfl_sync(0xffffffffu, yk, i);
+  for (int64_t d = lane; d < n; d += 32) {
+    double u = 0.0;
+#pragma unroll
+    for (int i = 0; i < kGmresMax; ++i)
+      if (i < jn) u = fma(ys[i], gm_v(g, a, i, l)[d], u);
+    w[d] = u;
+  }
+  __syncwarp();
+  double* ll = a.lam + l * n;
+  for (int64_t d = lane; d < n; d += 32) ll[d] += precond64(a, l, w, (int)d);
+  if (lane == 0) {
+    g.j[l] = 0;
+    a.pstat[l] = kPending | (it + 1);
+  }
+}
+
+// The FP64 true residual r = g - S lambda of every point whose cycle ended,
+// on the products Y = S lambda: accepted when ||r|| <= rtol ||g||, otherwise
+// the next cycle starts from r.
+__global__ void gmres_restart_kernel(IfaceArgs a, GmArgs g, double rtol) {
+  const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (l >= a.n_pts) return;
+  const int s = a.pstat[l];
+  if (!is_pending(s)) return;
+  const double* Yl = a.Y + l * a.NY;
+  double* rl = a.r + l * a.n_lambda;
+  double s2 = 0.0;
+  for (int64_t d = lane; d < a.n_lambda; d += 32) {
+    const double rv = rhs_g(a, l, d, nullptr) - (Yl[a.yoff[2 * d]] + Yl[a.yoff[2 * d + 1]]);
+    rl[d] = rv;
+    s2 = fma(rv, rv, s2);
+  }
+  const double rn = sqrt(warp_sum(s2));
+  __syncwarp();
+  if (rn <= rtol * a.gn[l]) {
+    if (lane == 0) a.pstat[l] = s & kItMask;
+    return;
+  }
+  gm_new_cycle(a, g, l, lane, rl, rn);
+  if (lane == 0) a.pstat[l] = 0;
+}
+
 __global__ void count_active(const int* pstat, int64_t n, int* out) {
   int c = 0;
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x)
@@ -2059,7 +2307,15 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
     ++c->launches;
     CK(cudaGetLastError());
   }
-  init_kernel<<<ublocks, 32 * warps_per_block, stg, st>>>(a);
+  const bool gmres = krylov == SFB_GMRES;
+  GmArgs gma;
+  gma.V = d.gmV; gma.st = d.gmS; gma.j = d.gmJ; gma.m = c->opt_gmres_m;
+  if (gmres) {
+    CK(cudaMemsetAsync(d.rflag, 0, sizeof(int) * n_pts, st));
+    gmres_init_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, gma);
+  } else {
+    init_kernel<<<ublocks, 32 * warps_per_block, stg, st>>>(a);
+  }
   ++c->launches;
   CK(cudaGetLastError());
   int maxR = (int)c->stokes.dofs.size();
@@ -2077,7 +2333,7 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   // its shared memory fits (for the mixed CG: when its FP32 tiles can stay
   // resident); otherwise one launch per step below
   bool persistent = false;
-  if (c->opt_cg_persistent && nu <= kPcgUnits) {
+  if (c->opt_cg_persistent && nu <= kPcgUnits && !gmres) {
     int dev = 0, coop = 0, n_sm = 0, smem_max = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
@@ -2204,7 +2460,27 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
     }
   }
   int it = 0;
-  for (; it < max_it && !persistent;) {
+  // GMRES: chunks of Arnoldi steps, then the true residuals of the points
+  // whose cycle ended (accepted, or the next cycle)
+  for (; gmres && it < max_it;) {
+    for (int q = 0; q < chunk && it < max_it; ++q, ++it) {
+      matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.p, 0, d.active + 2);
+      gmres_arnoldi_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, gma, it, rtol);
+      c->launches += 2;
+    }
+    matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.lam, 1, d.active + 2);
+    gmres_restart_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, gma, rtol);
+    c->launches += 2;
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(d.active, 0, sizeof(int), st));
+    count_active<<<std::min(1024, (int)((n_pts + 255) / 256)), 256, 0, st>>>(d.pstat, n_pts, d.active);
+    ++c->launches;
+    int h_active = 0;
+    CK(cudaMemcpyAsync(&h_active, d.active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h_active == 0) break;
+  }
+  for (; it < max_it && !persistent && !gmres;) {
     for (int q = 0; q < chunk && it < max_it; ++q, ++it) {
       if (mixed) matvec_kernel<float><<<mgrid, 256, smv32, st>>>(a, d.p, 0, d.active + 2);
       else matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.p, 0, d.active + 2);

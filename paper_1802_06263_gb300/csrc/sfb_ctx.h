@@ -59,6 +59,7 @@ struct Dev {
   double* T = nullptr;
   void* G = nullptr;
   void* Z = nullptr;
+  void* gmaps = nullptr;     // per item: tensor map (128 bytes) of its block inverses, tensor-core form
   double* phi = nullptr;
   float* phi32 = nullptr;    // FP32 copy of phi for the FP32 interface products
   double* D = nullptr;
@@ -107,7 +108,10 @@ struct Dev {
   double* rr = nullptr;
   double* gn = nullptr;
   double* rlast = nullptr;
-  double* dinv = nullptr;     // Jacobi preconditioner of the interface CG, per point
+  double* dinv = nullptr;
+  double* gmV = nullptr;      // GMRES Krylov basis [kGmresMax + 1][n_pts][n_lambda]
+  double* gmS = nullptr;      // GMRES per-point state [n_pts][kGmresState]
+  int* gmJ = nullptr;         // GMRES steps of the current cycle per point     // Jacobi preconditioner of the interface CG, per point
   float* minv = nullptr;      // interface block-Jacobi inverses, per point [minv_ld]
   int* if_off = nullptr;      // per interface: first global DOF, DOF count, offset of its block
   int* if_n = nullptr;
@@ -197,6 +201,7 @@ struct sfb_ctx {
   int opt_cg_persistent = 1;    // interface CG in one cooperative launch (0: one launch per step)
   int opt_cg_precond = 2;       // interface CG preconditioner: 0 none, 1 Jacobi, 2 interface blocks
   double opt_cg_replace = 0.1;  // mixed CG: FP64 residual once the recursive one drops by this factor
+  int opt_gmres_m = sfb::kGmresMax;   // GMRES restart length
   int opt_mom_df = 1;           // mixed form: moment contractions in double-float (0: FP64)
   double opt_big_factor = 1.0;   // groups above this many times (R+1) points use coefficient moments
   int opt_basis_graph = 1;      // basis launches of every size class replayed as one CUDA graph
@@ -221,6 +226,10 @@ struct sfb_ctx {
   GraphKey bkey[3];
   int bgraph_kernels[3] = {0, 0, 0};
   bool last_build_graph = false;
+  // tensor maps of the block inverses (tensor-core basis kernel): encoded for
+  // the workspace at gmaps_ws; gmaps_ok false when the driver cannot encode them
+  const char* gmaps_ws = nullptr;
+  bool gmaps_ok = false;
   // device-time phase markers of the last interface solve (CUDA events)
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int cg_iters_run = 0;

@@ -8,6 +8,9 @@
 #include <new>
 #include <numeric>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "sfb_ctx.h"
 
 namespace sfb {
@@ -155,12 +158,15 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
     const int nl = c->n_local.empty() ? 0 : c->n_local[s];
     for (int k = 0; k < nl; ++k) {
       ItemOff o;
-      const int64_t npad_ = (S.nx + kPanel - 1) / kPanel * kPanel, cpad_ = (C + 3) & ~3;
+      // row blocks of Z: [ny][npad][C rounded up to 8] (the tensor-core form's
+      // accumulator columns; the CUDA-core form uses C rounded up to 4)
+      const int64_t npad_ = (S.nx + kPanel - 1) / kPanel * kPanel, cpad_ = (C + 7) & ~7;
       o.x = nX; nX += (int64_t)nc * C;
       o.z = nZ; nZ += (int64_t)S.ny * npad_ * cpad_;   // row blocks in the shared-memory layout
       o.t = nT; nT += (int64_t)S.ny * (S.nx + 1) + (int64_t)(S.ny + 1) * S.nx;
       const int64_t npad = (S.nx + kPanel - 1) / kPanel * kPanel;  // identity-padded block size of the factor
-      o.g = nG; nG += (int64_t)S.ny * npad * npad;
+      // G: [ny][npad][npad]; twice that, for the tensor-core form's TF32 hi and lo parts
+      o.g = nG; nG += 2 * (int64_t)S.ny * npad * npad;
       o.phi = nPhi; nPhi += ((int64_t)R * R + R + 3) & ~int64_t(3);   // 16-byte aligned in FP32 and FP64
       o.diag = nD; o.sc = nD; nD += nc;
       c->offs.push_back(o);
@@ -187,6 +193,7 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   d.T = cv.take<double>(nT);
   d.G = cv.take<char>(nG * gsz);
   d.Z = cv.take<char>(nZ * gsz);
+  d.gmaps = cv.take<char>((size_t)n_items * 128);
   d.phi = cv.take<double>(nPhi);
   d.phi32 = cv.take<float>(nPhi);
   d.D = cv.take<double>(nD);
@@ -256,6 +263,9 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   d.gn = cv.take<double>(P);
   d.rlast = cv.take<double>(P);
   d.dinv = cv.take<double>((size_t)P * c->n_lambda);
+  d.gmV = cv.take<double>((size_t)(kGmresMax + 1) * P * c->n_lambda);
+  d.gmS = cv.take<double>((size_t)P * kGmresState);
+  d.gmJ = cv.take<int>(P);
   c->minv_ld = 0; c->max_if_dof = 0;
   for (const HostIface& f : c->ifaces) { c->minv_ld += (int64_t)f.n_dof * f.n_dof; c->max_if_dof = std::max(c->max_if_dof, f.n_dof); }
   d.minv = cv.take<float>((size_t)P * std::max<int64_t>(c->minv_ld, 1));
@@ -649,6 +659,7 @@ sfb_status sfb_set_workspace(sfb_ctx* c, void* ptr, size_t bytes) {
   c->basis_prec = -1;
   c->n_solved = 0;
   c->mom_shift_set = false;
+  c->gmaps_ws = nullptr;   // the tensor maps point into the workspace: encode them again
   Carver cv;
   cv.base = c->ws;
   layout(c, cv, c->ws_prec, c->ws_pts);
@@ -797,6 +808,8 @@ sfb_status autotune_basis(sfb_ctx* c, int prec, const BasisArgs* cls, const int*
     if (cls[q].n_items == 0 || ns < 2) continue;
     int best = -1;
     for (int v = 0; v < ns && v < 4 && e == cudaSuccess; ++v) {
+      BasisShape sd;
+      if (!basis_shape_desc(fp64, q == 0, v, &sd) || (sd.tcgen05 && !cls[q].gmaps)) continue;
       int ctas = 0;
       e = basis_shape_ctas(fp64, q == 0, v, cls_nx[q], cls_cols[q], &ctas);
       if (e != cudaSuccess || ctas < 1) {
@@ -828,6 +841,57 @@ sfb_status autotune_basis(sfb_ctx* c, int prec, const BasisArgs* cls, const int*
   if (e != cudaSuccess) return cuda_fail(c, e, "basis autotuner");
   c->btuned[prec] = true;
   return SFB_OK;
+}
+
+// Tensor maps of every item's block inverses for the tensor-core basis kernel:
+// the item's hi and lo arrays, [2][ny][np][np] FP32, as one row-major 2-D
+// tensor of np columns and 2 ny np rows, read in boxes of 4 columns by np
+// rows (one K-chunk of the product's A operand, which the copy lays down in
+// the core-matrix layout). Encoded once per workspace with the driver's
+// cuTensorMapEncodeTiled (looked up through the runtime, so the library does
+// not link the driver); false when the driver cannot encode them, and the
+// tensor-core launch shape is then skipped.
+bool encode_gmaps(sfb_ctx* c) {
+  if (c->gmaps_ws == c->ws) return c->gmaps_ok;
+  c->gmaps_ws = c->ws;
+  c->gmaps_ok = false;
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  if (!enc) {
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  std::vector<CUtensorMap> maps((size_t)c->n_items);
+  int64_t id = 0;
+  for (int s = 0; s < (int)c->subs.size(); ++s) {
+    const HostSub& H = c->subs[s];
+    const cuuint64_t np = (cuuint64_t)((H.nx + kPanel - 1) / kPanel * kPanel);
+    for (int k = 0; k < c->n_local[s]; ++k, ++id) {
+      float* base = reinterpret_cast<float*>(c->dev.G) + c->offs[id].g;
+      const cuuint64_t dims[2] = {np, 2 * (cuuint64_t)H.ny * np};
+      const cuuint64_t strides[1] = {np * 4};
+      const cuuint32_t box[2] = {4, (cuuint32_t)np};
+      const cuuint32_t es[2] = {1, 1};
+      const CUresult r = enc(&maps[id], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return false;
+    }
+  }
+  if (cudaMemcpyAsync(c->dev.gmaps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
+                      c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  c->gmaps_ok = true;
+  return true;
 }
 
 bool host_or_device_copy(void* dst, const void* src, size_t bytes, cudaStream_t st) {
@@ -869,6 +933,7 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   a.cycles = d.cycles;
   a.max_refine = c->opt_refine_max;
   a.refine_tol = c->opt_refine_tol;
+  if (prec != SFB_FP64 && encode_gmaps(c)) a.gmaps = d.gmaps;
   // size classes: [0] grids wider than 64 cells (the first n_wide items), [1] the rest
   const int fp64 = prec == SFB_FP64 ? 1 : 0;
   const int refine = prec == SFB_MIXED ? a.max_refine : 0;
@@ -887,7 +952,11 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   SFB_CUDA(cudaMemsetAsync(d.corr1, 0, sizeof(double) * n, st), "memset");
   SFB_CUDA(cudaMemsetAsync(d.errest, 0, sizeof(double) * n, st), "memset");
   SFB_CUDA(cudaMemsetAsync(d.nref, 0, sizeof(int) * n, st), "memset");
-  const int shp[2] = {c->bshape[prec][0], c->bshape[prec][1]};
+  int shp[2] = {c->bshape[prec][0], c->bshape[prec][1]};
+  for (int q = 0; q < 2; ++q) {   // a shape this class lacks, or the tensor-core one without maps: shape 0
+    BasisShape sd;
+    if (!basis_shape_desc(fp64, q == 0, shp[q], &sd) || (sd.tcgen05 && !a.gmaps)) shp[q] = 0;
+  }
   const bool two = cls[0].n_items > 0 && cls[1].n_items > 0;
   if (two) {
     if (!c->side) SFB_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "stream");
@@ -1047,13 +1116,14 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
 }
 
 sfb_status sfb_basis_launch_shape(int32_t prec, int32_t wide, int32_t shape, int32_t* threads,
-                                  int32_t* ctas_per_sm, int32_t* g_buffers) {
+                                  int32_t* ctas_per_sm, int32_t* g_buffers, int32_t* tcgen05) {
   if (prec < 0 || prec > 2 || (wide != 0 && wide != 1)) return SFB_ERR_ARG;
   BasisShape d;
   if (!basis_shape_desc(prec == SFB_FP64, wide, shape, &d)) return SFB_ERR_ARG;
   if (threads) *threads = d.threads;
   if (ctas_per_sm) *ctas_per_sm = d.min_ctas;
   if (g_buffers) *g_buffers = d.g_buffers;
+  if (tcgen05) *tcgen05 = d.tcgen05;
   return SFB_OK;
 }
 
@@ -1089,7 +1159,8 @@ sfb_status sfb_interface_solve_batch(sfb_ctx* c, const double* y, const double* 
                                      double rtol, int32_t max_it, double* lambda_out, int32_t* iters_out) {
   if (!c) return SFB_ERR_ARG;
   if (!c->basis_done) return fail(c, SFB_ERR_STATE, "sfb_build_stochastic_basis must come first");
-  if (n_pts < 0 || (krylov != SFB_CG && krylov != SFB_CG_MIXED) || !(rtol > 0) || max_it < 1)
+  if (n_pts < 0 || (krylov != SFB_CG && krylov != SFB_CG_MIXED && krylov != SFB_GMRES) || !(rtol > 0) ||
+      max_it < 1)
     return fail(c, SFB_ERR_ARG, "bad interface solve arguments");
   if (n_pts == 0) return SFB_OK;  // an empty batch changes nothing
   if (!y || !w) return fail(c, SFB_ERR_ARG, "bad interface solve arguments");
@@ -1200,13 +1271,19 @@ sfb_status sfb_set_option(sfb_ctx* c, const char* name, double value) {
       return fail(c, SFB_ERR_ARG, "no precision has launch shape " + std::to_string(v));
     c->opt_basis_autotune = 0;
     for (int p = 0; p < 3; ++p) {
-      const int cnt = basis_shape_count(p == SFB_FP64);
-      c->bshape[p][0] = c->bshape[p][1] = v < cnt ? v : 0;
+      for (int q = 0; q < 2; ++q) {
+        BasisShape sd;
+        c->bshape[p][q] = basis_shape_desc(p == SFB_FP64, q == 0, v, &sd) ? v : 0;
+      }
       c->btuned[p] = true;
     }
   } else if (n == "basis_graph") {
     if (!(value == 0 || value == 1)) return fail(c, SFB_ERR_ARG, "basis_graph must be 0 or 1");
     c->opt_basis_graph = (int)value;
+  } else if (n == "gmres_restart") {
+    if (!(value >= 1 && value <= kGmresMax && value == (int)value))
+      return fail(c, SFB_ERR_ARG, "gmres_restart must be an integer in 1.." + std::to_string(kGmresMax));
+    c->opt_gmres_m = (int)value;
   } else if (n == "cg_replace_ratio") {
     if (!(value >= 1e-4 && value < 1)) return fail(c, SFB_ERR_ARG, "cg_replace_ratio must lie in [1e-4, 1)");
     c->opt_cg_replace = value;

@@ -92,6 +92,12 @@ constexpr int kPcgMaxGrid = 2048;
 // Point chunks of the Stokes coefficient moments (partials summed in order).
 constexpr int kStokesChunks = 32;
 
+// Restarted GMRES of the interface problem: the largest restart length, and
+// the per-point state (Hessenberg columns, Givens rotations, rotated
+// right-hand side) in doubles.
+constexpr int kGmresMax = 30;
+constexpr int kGmresState = 1024;
+
 // Per-item storage offsets (elements) into the basis store arrays.
 struct ItemOff {
   int64_t x;    // X: [R+1][n_cells] FP64 pressure responses (column-major)
@@ -130,6 +136,7 @@ struct BasisArgs {
   long long* cycles;       // per item: SM cycles in [setup, factor, forward, backward]
   int max_refine;
   double refine_tol;
+  const void* gmaps = nullptr;  // per item id: CUtensorMap of its block inverses (tensor-core form)
 };
 
 // Launchers (basis.cu).
@@ -146,6 +153,7 @@ struct BasisShape {
   int threads;    // threads per CTA
   int min_ctas;   // CTAs per SM the register budget is compiled for
   int g_buffers;  // shared-memory buffers of G_b (2: the next block row is prefetched)
+  int tcgen05;    // 1: block-row products on the tensor cores (basis_tc.cu)
 };
 int basis_shape_count(int fp64);
 bool basis_shape_desc(int fp64, int wide, int shape, BasisShape* out);
@@ -153,5 +161,10 @@ bool basis_shape_desc(int fp64, int wide, int shape, BasisShape* out);
 cudaError_t basis_shape_ctas(int fp64, int wide, int shape, int max_nx, int max_cols, int* ctas);
 cudaError_t launch_basis_shape(const BasisArgs& a, int fp64, int wide, int shape, int max_nx, int max_cols,
                                int refine, cudaStream_t st);
+// Tensor-core form of the mixed basis kernel (basis_tc.cu): grids up to 64
+// cells wide, up to 128 right-hand sides; needs BasisArgs::gmaps.
+bool basis_tc_supported(int max_nx, int max_cols);
+cudaError_t basis_tc_ctas(int max_nx, int max_cols, int* ctas);
+cudaError_t launch_basis_tc(const BasisArgs& a, int max_nx, int max_cols, int refine, cudaStream_t st);
 
 }  // namespace sfb

@@ -200,3 +200,23 @@ def test_empty_batch_is_a_no_op(gpu):
     for f in FIELDS:
         m, v = s.moments(f)
         assert np.array_equal(m, before[f][0]) and np.array_equal(v, before[f][1])
+
+
+def test_gmres_full_batch_against_the_oracle(gpu):
+    """Restarted GMRES(30) in FP64 on the FP64 basis over all 2,049 points,
+    against the oracle's moments and sampled mortar solutions at 1e-10."""
+    import paper_1802_06263_gb300 as sfb
+    g = np.load(GOLDEN)
+    s = gpu["solver"]
+    y, wt = gpu["y"], gpu["w"]
+    s.build_basis(sfb.FP64)
+    s.moments_reset()
+    lam, it, rc = s.solve_host(y, wt, rtol=RTOL_FP64, max_it=2000, krylov=sfb.GMRES)
+    assert rc == 0 and np.all(it > 0)
+    for f in FIELDS:
+        m, v = s.moments(f)
+        assert_close(m, g[f + "_mean"], 1e-10, (f, "mean"))
+        assert_close(v, g[f + "_var"], 1e-10, (f, "variance"))
+    idx = _golden_index(y, g["sample_y"])
+    for j, l in enumerate(idx):
+        assert_close(lam[l], g["sample_lambda"][j], 1e-10, ("lambda", int(l)))

@@ -47,12 +47,13 @@ def test_basis_parity(key, prec):
     print(key, prec, "worst basis rel err", worst, st)
 
 
-@pytest.mark.parametrize("krylov", [0, 1])
+@pytest.mark.parametrize("krylov", [0, 1, 2])
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("key", CASES)
 def test_interface_and_moments_parity(key, prec, krylov):
     """krylov 0: FP64 CG; 1: CG with FP32 products and FP64 residual
-    replacement, which must reach the same FP64 residual tolerance."""
+    replacement, which must reach the same FP64 residual tolerance; 2:
+    restarted GMRES(30) in FP64, accepted on its FP64 true residual."""
     p, y, wt, lams, mom = oracle_case(key)
     s, _ = _solver(key, prec)
     rtol = 1e-14 if krylov == 0 else 1e-13
@@ -211,3 +212,38 @@ def test_persistent_cg_barrier_wait_runs_out_and_the_context_recovers():
     s.moments_reset()
     lam1, it1, rc1 = s.solve_host(y, wt, rtol=1e-12, max_it=5000, krylov=0)
     assert rc1 == 0 and np.array_equal(lam1, lam0) and np.array_equal(it1, it0)
+
+
+@pytest.mark.parametrize("m", [5, 30])
+def test_gmres_restart_lengths_reach_the_same_solution(m):
+    """GMRES(m) with a short restart (several cycles per point, each accepted
+    or restarted on the FP64 true residual) and with the default 30 give the
+    oracle's mortar solution; the short restart needs more Arnoldi steps. With
+    no preconditioner GMRES is plain GMRES on S^l."""
+    import paper_1802_06263_gb300 as sfb
+    p, y, wt, lams, mom = oracle_case("medium")
+    s, _ = _solver("medium", 0)
+    its = {}
+    for precond in (0, 2):
+        s.set_option("cg_precond", precond)
+        s.set_option("gmres_restart", m)
+        s.moments_reset()
+        lam, it, rc = s.solve_host(y, wt, rtol=1e-13, max_it=5000, krylov=sfb.GMRES)
+        assert rc == 0 and np.all(it > 0)
+        for l in range(len(y)):
+            assert_close(lam[l], lams[l], 1e-10, ("lambda", l))
+        m_, v_ = s.moments("darcy_flux")
+        assert_close(m_, mom["darcy_flux"][0], 1e-10, "mean")
+        its[precond] = it.max()
+    assert its[2] < its[0]   # the interface blocks help GMRES as they help CG
+    if m == 5:
+        assert its[0] > 5
+
+
+def test_gmres_not_converged_is_reported():
+    import paper_1802_06263_gb300 as sfb
+    p, y, wt, lams, mom = oracle_case("medium")
+    s, _ = _solver("medium", 0)
+    lam, it, rc = s.solve_host(y, wt, rtol=1e-14, max_it=3, check=False, krylov=sfb.GMRES)
+    assert rc == sfb.SFB_ERR_NOT_CONVERGED
+    assert np.all(it == -3)
