@@ -15,7 +15,10 @@ realizations per second (mixed form: FP32 factor + FP64 refinement), with
 the FP64 form and the mortar flux responses per second beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload NAME]
+                  [--workload NAME] [--methods]
+
+--methods times Methods S3, S2 and S1 side by side on the workload's points
+(FP64, unpreconditioned CG for all three) instead of the default step.
 """
 
 import argparse
@@ -34,6 +37,10 @@ import numpy as np  # noqa: E402
 import sfb_workloads as W  # noqa: E402
 
 METRIC = "collocation realizations/sec (mixed FP32/FP64, <=1e-8 vs FP64)"
+# points per interface solve where the batch is solved in chunks
+CHUNK = {"large": 32768}
+# workloads whose configuration names GMRES as the interface solver
+GMRES_WORKLOADS = ("large",)
 UNIT = "realizations/s"
 WORKLOAD = "precision"
 
@@ -195,20 +202,31 @@ def run_ours(args):
     if wl.get("n_batch"):
         y, wt = y[:wl["n_batch"]], wt[:wl["n_batch"]]
     n_pts = len(y)
-    s.allocate(sfb.FP64, max_pts=n_pts)   # the FP64 layout also holds the mixed form
+    # points per interface solve: the whole batch, or chunks whose moments
+    # accumulate (the Large workload's 341,505 points)
+    chunk = min(n_pts, CHUNK.get(args.workload, n_pts))
+    s.allocate(sfb.FP64, max_pts=chunk)   # the FP64 layout also holds the mixed form
     yd = torch.tensor(y, device="cuda")
     wd = torch.tensor(wt, device="cuda")
-    lam_d = torch.empty((n_pts, s.n_lambda), dtype=torch.float64, device="cuda")
-    it_d = torch.empty(n_pts, dtype=torch.int32, device="cuda")
+    lam_d = torch.empty((chunk, s.n_lambda), dtype=torch.float64, device="cuda")
+    it_d = torch.empty(chunk, dtype=torch.int32, device="cuda")
     # CG tolerance per form: the mixed form's moments reach 1e-8 of the oracle
     # at 1e-10; the FP64 form's need 1e-12 to reach 1e-10 entry by entry
     rtol_of = {sfb.MIXED: 1e-10, sfb.FP64: 1e-12}
-    max_it = 2000
+    max_it = 3000
 
     def krylov(prec):
-        # the mixed form runs the interface CG on FP32 products with FP64
-        # residual replacement; the FP64 form runs plain FP64 CG
+        # the Large workload's interface solver is GMRES (FP64) in both forms;
+        # elsewhere the mixed form runs the interface CG on FP32 products with
+        # FP64 residual replacement and the FP64 form plain FP64 CG
+        if args.workload in GMRES_WORKLOADS:
+            return sfb.GMRES_MIXED if prec == sfb.MIXED else sfb.GMRES
         return sfb.CG_MIXED if prec == sfb.MIXED else sfb.CG
+
+    def solve_all_chunks(prec, yy, ww, lam, it):
+        for a in range(0, n_pts, chunk):
+            b = min(n_pts, a + chunk)
+            s.solve(yy[a:b], ww[a:b], rtol_of[prec], max_it, lam[:b - a], it[:b - a], krylov=krylov(prec))
 
     def step(prec):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -216,7 +234,7 @@ def run_ours(args):
         st = s.build_basis(prec)
         ev[1].record(stream)
         s.moments_reset()
-        s.solve(yd, wd, rtol_of[prec], max_it, lam_d, it_d, krylov=krylov(prec))
+        solve_all_chunks(prec, yd, wd, lam_d, it_d)
         ev[2].record(stream)
         ev[3].record(stream)
         return st, ev
@@ -271,8 +289,8 @@ def run_ours(args):
     # weights, D2H of lambda, iteration counts and the moments
     y_h = torch.tensor(y).pin_memory()
     w_h = torch.tensor(wt).pin_memory()
-    lam_h = torch.empty((n_pts, s.n_lambda), dtype=torch.float64).pin_memory()
-    it_h = torch.empty(n_pts, dtype=torch.int32).pin_memory()
+    lam_h = torch.empty((chunk, s.n_lambda), dtype=torch.float64).pin_memory()
+    it_h = torch.empty(chunk, dtype=torch.int32).pin_memory()
     mom_bytes = 0
     torch.cuda.synchronize()
     if world > 1:
@@ -281,7 +299,7 @@ def run_ours(args):
     for _ in range(args.steps):
         s.build_basis(sfb.MIXED)
         s.moments_reset()
-        s.solve(y_h, w_h, rtol_of[sfb.MIXED], max_it, lam_h, it_h, krylov=sfb.CG_MIXED)
+        solve_all_chunks(sfb.MIXED, y_h, w_h, lam_h, it_h)
         mom_bytes = 0
         for f in sfb.FIELDS:
             m, v = s.moments(f)
@@ -336,6 +354,10 @@ def run_ours(args):
         "data": "synthetic (seeded KL/Smolyak inputs of the %s workload; no paper datasets)" % args.workload,
         "config": {"workload": describe(wl, s, n_pts),
                    "n_points": n_pts, "n_basis_items": n_items, "flux_responses": fr,
+                   "interface_solver": ("GMRES(30), right-preconditioned (mixed: FP32 Arnoldi products, FP64 "
+                                        "restarts; FP64)" if args.workload in GMRES_WORKLOADS
+                                        else "CG (mixed: FP32 products, FP64 residual replacement; FP64)"),
+                   "points_per_solve": chunk,
                    "cg_rtol": {"mixed": rtol_of[sfb.MIXED], "fp64": rtol_of[sfb.FP64]}, "cg_preconditioner": "interface block-Jacobi (diagonal blocks of S^l per mortar interface)",
                    "l2": "working set larger than L2 (basis store %.2f GB)"
                    % (s.workspace_bytes(sfb.MIXED, n_pts) / 1e9),
@@ -360,7 +382,7 @@ def run_ours(args):
         "speedup_mixed_vs_fp64": t_fp64 / t_mixed,
         "e2e": {"value": world * n_pts / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(y.nbytes + wt.nbytes),
-                "d2h_bytes_per_step": int(lam_h.numel() * 8 + it_h.numel() * 4 + mom_bytes)},
+                "d2h_bytes_per_step": int(n_pts * (s.n_lambda * 8 + 4) + mom_bytes)},
         "clocks": clk,
         "roofline": dict({"bound": "alu", "kernel": "basis_kernel<float> (mixed form)", "unit": "TFLOP/s",
                           "traffic": traffic,
@@ -565,6 +587,96 @@ def run_reference(args):
             "wall_s": wall}
 
 
+def run_methods(args):
+    """Methods S3, S2 and S1 (Sections 5.4, 5.3, 5.2) on the same points of one
+    workload, each a whole step (basis or factor build, interface solves,
+    moments) with the same solver: unpreconditioned FP64 CG to rtol 1e-12
+    (S1 and S2/S3 apply the same operator, so their iterations agree). S2
+    builds one basis per global point (local sets per point), S1 the FP64
+    block factors of the local realizations and one subdomain solve per
+    (point, subdomain) and iteration. Reports realizations/s per method, the
+    subdomain solves of each (Section 5.2, 5.3, 5.4 counts) and the agreement
+    of their moments with Method S3's."""
+    import copy
+
+    import torch
+    import paper_1802_06263_gb300 as sfb
+
+    _, _, local = _dist()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    base = W.ALL[args.workload]()
+    res, mom3 = {}, None
+    clocks = ClockSampler(local)
+    clocks.start()
+    for meth in ("s3", "s2", "s1"):
+        wl = copy.deepcopy(base)
+        if meth == "s2":
+            wl["collocation"] = dict(wl["collocation"], local="per_point")
+        s = sfb.Solver(wl, stream=stream)
+        y, wt = s.points()
+        if wl.get("n_batch"):
+            y, wt = y[:wl["n_batch"]], wt[:wl["n_batch"]]
+        n = len(y)
+        s.allocate(sfb.FP64, max_pts=n)
+        s.set_option("cg_precond", 0)
+        build = sfb.FACTOR_FP64 if meth == "s1" else sfb.FP64
+        kr = sfb.CG_DTN if meth == "s1" else sfb.CG
+        yd, wd = torch.tensor(y, device="cuda"), torch.tensor(wt, device="cuda")
+        lam = torch.empty((n, s.n_lambda), dtype=torch.float64, device="cuda")
+        it = torch.empty(n, dtype=torch.int32, device="cuda")
+
+        def step():
+            s.build_basis(build)
+            s.moments_reset()
+            s.solve(yd, wd, 1e-12, 5000, lam, it, krylov=kr)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = s.launch_count()
+        t0.record(stream)
+        for _ in range(args.steps):
+            step()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / args.steps
+        iters = it.cpu().numpy()
+        r = [len(s.subdomain_dofs(j)) for j in range(s.n_darcy)]
+        nloc = [len(s.local_points(j)) for j in range(s.n_darcy)]
+        if meth == "s1":
+            solves = [int(np.abs(iters).sum()) + 2 * n for _ in r]
+        elif meth == "s2":
+            solves = [(rj + 2) * n for rj in r]
+        else:
+            solves = [rj * nj + 2 * n for rj, nj in zip(r, nloc)]
+        mom = {f: s.moments(f) for f in sfb.FIELDS}
+        res[meth] = {"value": n / (ms * 1e-3), "ms_per_step": ms, "cg_iters_min_max": [int(iters.min()), int(iters.max())],
+                     "cg_iters_sum": int(np.abs(iters).sum()), "subdomain_solves": solves,
+                     "gpu_launches_per_step": (s.launch_count() - l0) / args.steps,
+                     "build": "factor only (FP64)" if meth == "s1" else "flux basis (FP64)",
+                     "items": int(sum(nloc))}
+        if meth == "s3":
+            mom3 = mom
+        else:
+            res[meth]["moments_rel_vs_s3"] = max(
+                float(np.linalg.norm(mom[f][j] - mom3[f][j]) / max(np.linalg.norm(mom3[f][j]), 1e-300))
+                for f in sfb.FIELDS for j in (0, 1))
+        del s
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    out = {"metric": "collocation realizations/sec per method (FP64, unpreconditioned CG)",
+           "value": res["s3"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": res["s3"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded KL/Smolyak inputs)",
+           "config": {"workload": args.workload, "n_points": n, "cg_rtol": 1e-12,
+                      "interface_solver": "CG, FP64, no preconditioner (the same for the three methods)"},
+           "methods": res, "s3_over_s2": res["s3"]["value"] / res["s2"]["value"],
+           "s3_over_s1": res["s3"]["value"] / res["s1"]["value"], "clocks": clk}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -572,8 +684,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=["tiny", "medium", WORKLOAD, "batched"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=["tiny", "medium", WORKLOAD, "batched", "large"])
+    ap.add_argument("--methods", action="store_true",
+                    help="time Methods S3, S2 and S1 on the workload (one GPU) instead of the default step")
     args = ap.parse_args()
+    if args.methods:
+        print(json.dumps(run_methods(args)))
+        return
     if args.impl == "reference":
         out = run_reference(args)
         if out is not None:
@@ -582,8 +699,12 @@ def main():
     out, rank = run_ours(args)
     if rank == 0:
         if not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline_sample(workload=args.workload)
-            out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(workload=args.workload)
+            small = args.workload in CHUNK   # the oracle's full-size grid and Stokes basis alone take minutes
+            out["cpu_baseline"] = cpu_baseline_sample(workload=args.workload, n_pts=16 if small else 48)
+            out["cpu_baseline_all_cores"] = (
+                {"skipped": "one oracle process per core would each rebuild the 128x128 Stokes basis and "
+                            "the 341,505-point grid (about 1.5 minutes each)"} if small
+                else cpu_baseline_all_cores(workload=args.workload))
         print(json.dumps(out))
 
 

@@ -65,7 +65,11 @@ typedef enum {
   SFB_FP64 = 0,          /* factor and solve in FP64                                  */
   SFB_MIXED = 1,         /* FP32 factor/solves with diagonal scaling, refined by FP64 */
                          /* residuals of the 5-point operator                          */
-  SFB_FP32_NOREFINE = 2  /* FP32 factor/solve only: diagnostics of the unrefined error */
+  SFB_FP32_NOREFINE = 2, /* FP32 factor/solve only: diagnostics of the unrefined error */
+  SFB_FACTOR_FP64 = 3    /* Method S1's set-up (Section 5.2): the FP64 block factor of  */
+                         /* every item and its particular solution, so g; no flux     */
+                         /* basis (Phi) is formed. Needs an SFB_FP64 workspace; only  */
+                         /* SFB_CG_DTN solves from it.                                */
 } sfb_precision;
 
 /* Interface Krylov solver (Section 5.4 Step 5, reading of Eq. 5.10 as an SPD
@@ -89,8 +93,33 @@ typedef enum {
  *               reaches rtol ||g|| or after m steps, and a point is accepted
  *               only on its FP64 true residual ||g - S lambda|| <= rtol ||g||
  *               (otherwise the next cycle starts from it). The iteration
- *               count is the number of Arnoldi steps. */
-typedef enum { SFB_CG = 0, SFB_CG_MIXED = 1, SFB_GMRES = 2 } sfb_krylov;
+ *               count is the number of Arnoldi steps.
+ * SFB_GMRES_MIXED: the same GMRES with the Arnoldi products S p on the bases
+ *               rounded to FP32 (orthogonalization, Hessenberg, rotations,
+ *               updates and iterates in FP64); a cycle also ends once it has
+ *               reduced its initial residual by 1e-5, and every cycle starts
+ *               from, and every point is accepted on, the FP64 true residual:
+ *               restarted GMRES as the inner solver of FP64 iterative
+ *               refinement. Not in the paper, like SFB_CG_MIXED.
+ * SFB_CG_DTN:   Method S1 (Section 5.2): unpreconditioned CG in FP64 whose
+ *               product S p applies every Darcy subdomain's Dirichlet-to-
+ *               Neumann map by one subdomain solve per iteration (Eqs. 5.5-
+ *               5.6 with the data R_i p, then -<u.n, xi> on its mortar DOFs),
+ *               with the point's own block factor from an SFB_FP64 or
+ *               SFB_FACTOR_FP64 build; the Stokes subdomain, whose operator
+ *               is the same for every point, is applied by its basis. The
+ *               Darcy moments then come from one more subdomain solve per
+ *               point (the recovery of Section 5.2, Eqs. 5.7-5.8). Per Darcy
+ *               subdomain the point's solves number its iterations plus two
+ *               (the right-hand side, folded into the build, and the
+ *               recovery). */
+typedef enum {
+  SFB_CG = 0,
+  SFB_CG_MIXED = 1,
+  SFB_GMRES = 2,
+  SFB_GMRES_MIXED = 3,
+  SFB_CG_DTN = 4
+} sfb_krylov;
 
 typedef enum {
   SFB_FIELD_DARCY_P = 0,     /* cell pressures, subdomain by subdomain, c = iy*nx+ix    */
@@ -139,7 +168,10 @@ typedef struct {
  * (n_rule == 0: the paper's 2^(p+1)-1). local_tensor = 1 builds every
  * region's basis on the full local tensor grid of the largest 1-D rule (of
  * the region's own rules for an anisotropic tensor grid); 0 on the distinct
- * projections of the global grid. m_dim (tensor only, nullable, host): the
+ * projections of the global grid (Method S3, Section 5.4); 2 on the
+ * projection of every global point, repeats kept, so that every point gets
+ * its own basis items (Method S2, Section 5.3: a multiscale flux basis per
+ * global point, no reuse). m_dim (tensor only, nullable, host): the
  * anisotropic tensor rule of Section 4.1, m_dim[kappa] points in global
  * stochastic dimension kappa (sum of n_term entries, regions in order, each
  * in [1, 32]); NULL: m points in every dimension. */
@@ -270,7 +302,11 @@ sfb_status sfb_set_workspace(sfb_ctx* ctx, void* dev_ptr, size_t bytes);
  * factorization, R+1 right-hand sides (R mortar DOFs plus the particular
  * problem Eqs. 5.7-5.8), and the flux basis Phi[l][j] = -<u*(xi_j).n, xi_l>
  * with g[l] = <u_bar.n, xi_l>; also the deterministic Stokes basis (Section
- * 5.4: N_real = 1 for Stokes subdomains). stats_out is nullable. */
+ * 5.4: N_real = 1 for Stokes subdomains). stats_out is nullable.
+ * prec = SFB_FACTOR_FP64 (Method S1, Section 5.2) stops after the FP64 factor
+ * and the particular solution: g is formed, Phi and the mortar responses are
+ * not (no autotuning and no captured graph: one plain launch per size class);
+ * SFB_ERR_WORKSPACE unless the workspace was sized for SFB_FP64. */
 sfb_status sfb_build_stochastic_basis(sfb_ctx* ctx, int32_t prec, sfb_basis_stats* stats_out);
 
 /* Launch shapes of the basis kernel (no counterpart in the paper: how the
@@ -294,7 +330,9 @@ sfb_status sfb_basis_launch_shape(int32_t prec, int32_t wide, int32_t shape, int
 /* Read-back of one stored basis item (host or device buffers): phi [R x R]
  * row-major, g [R], x [(R+1) x n_cells] (pressure responses, column j is the
  * response to xi_j, column R the particular solution; nullable). sub = -1 and
- * k = 0 return the Stokes basis (x must be NULL). */
+ * k = 0 return the Stokes basis (x must be NULL). After an SFB_FACTOR_FP64
+ * build a Darcy item has g and the particular solution (column R of x) only:
+ * phi must be NULL and the response columns of x are left unwritten. */
 sfb_status sfb_get_basis(sfb_ctx* ctx, int32_t sub, int32_t k, double* phi, double* g, double* x);
 
 /* Section 5.4 Steps 3-6 for a batch of global points y [n_pts x n_dim] with
@@ -304,7 +342,10 @@ sfb_status sfb_get_basis(sfb_ctx* ctx, int32_t sub, int32_t k, double* phi, doub
  * (nullable, host or device): lambda_out [n_pts x n_lambda], iters_out
  * [n_pts] (negative: not converged). Returns SFB_ERR_NOT_CONVERGED with all
  * outputs filled if a point did not converge within max_it. An empty batch
- * (n_pts = 0, y and w may be NULL) returns SFB_OK and changes nothing. */
+ * (n_pts = 0, y and w may be NULL) returns SFB_OK and changes nothing.
+ * krylov = SFB_CG_DTN (Method S1) needs the block factors of an SFB_FP64 or
+ * SFB_FACTOR_FP64 build, every other solver the flux basis of an SFB_FP64,
+ * SFB_MIXED or SFB_FP32_NOREFINE build (SFB_ERR_STATE otherwise). */
 sfb_status sfb_interface_solve_batch(sfb_ctx* ctx, const double* y, const double* w, int64_t n_pts,
                                      int32_t krylov, double rtol, int32_t max_it,
                                      double* lambda_out, int32_t* iters_out);

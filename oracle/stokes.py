@@ -254,7 +254,14 @@ class StokesSub:
         if dirichlet_on:
             full[dirv] = val[dirv][:, None]
             rhs = rhs - M[:, dirv] @ full[dirv]
-        full[free] = lu.solve(rhs[free])
+        # the discrete solution of the saddle-point system: the pivoted LU
+        # solve, then one step of iterative refinement with the assembled
+        # matrix (a 128 x 128 Taylor-Hood system leaves the pressure about
+        # 1e-9 off after the LU solve alone, at a residual of 1e-13)
+        x = lu.solve(rhs[free])
+        A_ff = M[free][:, free]
+        x = x + lu.solve(rhs[free] - A_ff @ x)
+        full[free] = x
         return full[:nu_], full[nu_:]
 
     def flux_basis(self):

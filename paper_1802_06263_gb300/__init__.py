@@ -19,8 +19,10 @@ from ._build import LIB as _LIB_PATH, build  # noqa: F401
 SFB_OK = 0
 SFB_ERR_NOT_CONVERGED = 6
 SFB_ERR_TIMEOUT = 9
-FP64, MIXED, FP32_NOREFINE = 0, 1, 2
-CG, CG_MIXED, GMRES = 0, 1, 2
+# basis builds: FACTOR_FP64 is Method S1's set-up (FP64 block factors and g, no flux basis)
+FP64, MIXED, FP32_NOREFINE, FACTOR_FP64 = 0, 1, 2, 3
+# interface solvers: CG_DTN is Method S1 (a subdomain solve per CG iteration)
+CG, CG_MIXED, GMRES, GMRES_MIXED, CG_DTN = 0, 1, 2, 3, 4
 FIELDS = {"darcy_p": 0, "darcy_flux": 1, "stokes_u": 2, "stokes_p": 3}
 STATUS = {0: "OK", 1: "ARG", 2: "STATE", 3: "CUDA", 4: "WORKSPACE", 5: "NONFINITE",
           6: "NOT_CONVERGED", 7: "NOT_SPD", 8: "UNSUPPORTED", 9: "TIMEOUT"}
@@ -245,7 +247,10 @@ class Solver:
         self._keep.append(rule_a)
         C.n_rule = len(rule)
         C.rule = rule_a.ctypes.data_as(_i32p)
-        C.local_tensor = 1 if col.get("local", "projections") == "tensor" else 0
+        # local realizations: "tensor" (the region's full local tensor grid),
+        # "projections" (the distinct projections of the global grid: Method
+        # S3) or "per_point" (one per global point, repeats kept: Method S2)
+        C.local_tensor = {"projections": 0, "tensor": 1, "per_point": 2}[col.get("local", "projections")]
         npts = ctypes.c_int64()
         self._check(self.lib.sfb_collocation_setup(self.h, ctypes.byref(C), ctypes.byref(npts)))
         self.n_pts = npts.value
@@ -326,6 +331,7 @@ class Solver:
     def build_basis(self, prec=FP64, check=True):
         st = BasisStats()
         rc = self.lib.sfb_build_stochastic_basis(self.h, prec, ctypes.byref(st))
+        self.basis_prec = prec
         if check and rc != SFB_OK:
             self._check(rc)
         out = {k: getattr(st, k) for k, _ in BasisStats._fields_}
@@ -344,10 +350,13 @@ class Solver:
             return phi, g, None
         R = len(self.subdomain_dofs(sub))
         nx, ny = self.w["darcy_grid"][sub]
-        phi, g = np.zeros((R, R)), np.zeros(R)
+        # after the factor-only build (Method S1) there is no phi, and x holds
+        # the particular solution (its last column) only
+        phi = None if getattr(self, "basis_prec", None) == FACTOR_FP64 else np.zeros((R, R))
+        g = np.zeros(R)
         x = np.zeros((R + 1, nx * ny)) if with_x else None
-        self._check(self.lib.sfb_get_basis(self.h, sub, k, phi.ctypes.data, g.ctypes.data,
-                                           x.ctypes.data if with_x else None))
+        self._check(self.lib.sfb_get_basis(self.h, sub, k, phi.ctypes.data if phi is not None else None,
+                                           g.ctypes.data, x.ctypes.data if with_x else None))
         return phi, g, (x.T.copy() if with_x else None)
 
     def build_item_noalloc(self, sub, k, prec, phi_out, g_out, x_out, check=True):
@@ -385,8 +394,10 @@ class Solver:
     def solve(self, y, w, rtol=1e-10, max_it=1000, lam_out=None, iters_out=None, check=True, krylov=CG):
         """Interface CG for a batch of points (host numpy or device torch
         arrays); outputs go to the given buffers (host or device). ``krylov``
-        is CG (FP64), CG_MIXED (FP32 products, FP64 residuals) or GMRES (restarted
-        GMRES(m) in FP64)."""
+        is CG (FP64), CG_MIXED (FP32 products, FP64 residuals), GMRES (restarted
+        GMRES(m) in FP64), GMRES_MIXED (FP32 Arnoldi products, FP64 restarts)
+        or CG_DTN (Method S1: the Darcy products by a subdomain solve per
+        iteration, after an FP64 or FACTOR_FP64 build)."""
         y = np.ascontiguousarray(y, dtype=np.float64) if isinstance(y, np.ndarray) else y
         w = np.ascontiguousarray(w, dtype=np.float64) if isinstance(w, np.ndarray) else w
         n = int(y.shape[0])

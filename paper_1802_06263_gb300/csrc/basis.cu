@@ -160,7 +160,11 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
   const int id = (int)S.item0 + kk;
   const ItemOff off = a.off[id];
   Geo g;
-  g.nx = S.nx; g.ny = S.ny; g.R = S.R; g.C = S.R + 1; g.Cp = (g.C + 3) & ~3; g.nc = S.nx * S.ny;
+  // all R + 1 right-hand sides, or (Method S1's set-up) only the particular
+  // one, column R of the right-hand side and of X
+  const int coff = a.particular_only ? S.R : 0;
+  g.nx = S.nx; g.ny = S.ny; g.R = S.R; g.C = a.particular_only ? 1 : S.R + 1; g.Cp = (g.C + 3) & ~3;
+  g.nc = S.nx * S.ny;
   const int nx = g.nx, ny = g.ny, nc = g.nc, C = g.C, Cp = g.Cp;
   constexpr int kP = panel_of<T>();
   const int np = (nx + kPanel - 1) & ~(kPanel - 1);  // identity-padded block size
@@ -170,7 +174,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
   double* Tx = a.T + off.t;
   double* Ty = Tx + (int64_t)ny * (nx + 1);
   g.Tx = Tx; g.Ty = Ty;
-  double* X = a.X + off.x;
+  double* X = a.X + off.x + (int64_t)coff * S.nx * S.ny;
   double* Dg = a.D + off.diag;
   T* Sg = reinterpret_cast<T*>(a.S) + off.sc;
   T* DLg = reinterpret_cast<T*>(a.DL) + off.sc;  // [ny][nx] scaled couplings to the row below
@@ -292,7 +296,9 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
     if constexpr (sizeof(T) == 4) blocked_sweep<T, MT, NT, panel_of<T>()>(areg, np, ntr, VT, W, Ablk, &bad_spd);
     else blocked_sweep_w0<T, MT, NT, panel_of<T>()>(areg, np, ntr, VT, W, Ablk, &bad_spd);
     SFB_MARK(1);
-    T* Gs = Gs0 + (b % GB) * np * np;
+    // G_b in shared memory (bulk-stored below), or straight to global memory
+    // when the shape keeps no G buffer (GB == 0: the 128-wide FP64 blocks)
+    T* Gs = GB == 0 ? Gg + (int64_t)b * np * np : Gs0 + (b % (GB == 0 ? 1 : GB)) * np * np;
     if (threadIdx.x == 0) bulk_wait_read();   // the store that last read Gs / Zs is done
     __syncthreads();
 #pragma unroll
@@ -308,14 +314,14 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
     // first forward solve row: u_b = s_b B_b + dlo_b z_{b-1}
     for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
       const int i = e % nx, c = e / nx;
-      T u = sc[i] * from_f64<T>(rhs_entry(S, g, a.proj, b, i, c));
+      T u = sc[i] * from_f64<T>(rhs_entry(S, g, a.proj, b, i, c + coff));
       if (b > 0) u = fma(dlo[i], Zs[i * Cp + c], u);
       Us[i * Cp + c] = u;
     }
     fence_async_shared();
     __syncthreads();
     SFB_MARK(2);
-    if (threadIdx.x == 0) bulk_store(Gg + (int64_t)b * np * np, Gs, gbytes);
+    if (GB > 0 && threadIdx.x == 0) bulk_store(Gg + (int64_t)b * np * np, Gs, gbytes);
     gemm_g<T>(Gs, Us, Zs, false, np, Cp, C);
     fence_async_shared();
     __syncthreads();
@@ -337,14 +343,14 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
     float rr = 0.f;
     if (it > 0) {
       // forward sweep: r_b = B_b - (A x)_b in FP64; u_b = s_b r_b + dlo_b z_{b-1}
-      if (threadIdx.x == 0) { fence_async_shared(); bulk_load(Gs0, Gg, gbytes, &gbar[0]); }
+      if (GB > 0 && threadIdx.x == 0) { fence_async_shared(); bulk_load(Gs0, Gg, gbytes, &gbar[0]); }
       // row scalings of the next row travel in registers while a row runs
       T nsc = threadIdx.x < nx ? Sg[threadIdx.x] : T(0), ndl = threadIdx.x < nx ? DLg[threadIdx.x] : T(0);
       prefetch_x_row(X, nc, nx, 0, C);
       if (ny > 1) prefetch_x_row(X, nc, nx, 1, C);
       for (int b = 0; b < ny; ++b) {
         const int cur = GB == 2 ? (b & 1) : 0;
-        T* Gs = Gs0 + cur * np * np;
+        T* Gs = GB == 0 ? Gg + (int64_t)b * np * np : Gs0 + cur * np * np;
         if (threadIdx.x < nx) {
           sc[threadIdx.x] = nsc;
           dlo[threadIdx.x] = ndl;
@@ -363,7 +369,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
           const int64_t cell = (int64_t)b * nx + i;
           const double* xc = X + (int64_t)c * nc;
           // r = B - A x as five FP64 FMAs: B - D x, then + T x over the neighbours
-          double r = fma(-Dg[cell], xc[cell], rhs_entry(S, g, a.proj, b, i, c));
+          double r = fma(-Dg[cell], xc[cell], rhs_entry(S, g, a.proj, b, i, c + coff));
           if (i > 0) r = fma(Tx[b * (nx + 1) + i], xc[cell - 1], r);
           if (i < nx - 1) r = fma(Tx[b * (nx + 1) + i + 1], xc[cell + 1], r);
           if (b > 0) r = fma(Ty[b * nx + i], xc[cell - nx], r);
@@ -377,8 +383,11 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
         }
         // G_b present, and the store that reads Zs finished
         if (threadIdx.x == 0) bulk_wait_read();
-        const bool ok = mbar_wait(&gbar[cur], gph[cur]);
-        gph[cur] ^= 1u;
+        bool ok = true;
+        if (GB > 0) {
+          ok = mbar_wait(&gbar[cur], gph[cur]);
+          gph[cur] ^= 1u;
+        }
         if (__syncthreads_or(!ok)) { timeout = true; break; }
         SFB_MARK(5);
         gemm_g<T>(Gs, Us, Zs, false, np, Cp, C);
@@ -404,7 +413,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
       float bb = 0.f;
       for (int e = threadIdx.x; e < nc * C; e += blockDim.x) {
         const int c = e / nc, cell = e - c * nc;
-        const float v = f64_to_f32_bits(rhs_entry(S, g, a.proj, cell / nx, cell % nx, c));
+        const float v = f64_to_f32_bits(rhs_entry(S, g, a.proj, cell / nx, cell % nx, c + coff));
         bb = fmaf(v, v, bb);
       }
       bnorm2 = block_sum((double)bb, red);
@@ -419,7 +428,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
     T bsc = threadIdx.x < nx ? Sg[(ny - 1) * nx + threadIdx.x] : T(0), bdu = T(0);
     for (int b = ny - 1; b >= 0; --b) {
       const int cur = GB == 2 ? ((ny - 2 - b) & 1) : 0;   // buffer of G_b (b <= ny-2)
-      T* Gs = Gs0 + cur * np * np;
+      T* Gs = GB == 0 ? Gg + (int64_t)b * np * np : Gs0 + cur * np * np;
       if (threadIdx.x < nx) {
         sc[threadIdx.x] = bsc;
         dup[threadIdx.x] = bdu;   // D_b = the coupling to row b + 1
@@ -446,7 +455,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
       if (threadIdx.x == 0) bulk_load(Zs, Zg + (int64_t)b * np * Cp, zbytes, &zbar);
       bool ok = mbar_wait(&zbar, zph);
       zph ^= 1u;
-      if (b < ny - 1) {
+      if (GB > 0 && b < ny - 1) {
         ok = mbar_wait(&gbar[cur], gph[cur]) && ok;
         gph[cur] ^= 1u;
       }
@@ -506,7 +515,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
   if (timeout) {
     // give the copies in flight a bounded chance to land before the CTA exits
     if (threadIdx.x == 0) {
-      mbar_wait(&gbar[0], gph[0]);
+      if (GB > 0) mbar_wait(&gbar[0], gph[0]);
       mbar_wait(&gbar[1], gph[1]);
       mbar_wait(&zbar, zph);
       bulk_wait_all();
@@ -548,8 +557,10 @@ __global__ void flux_epilogue_kernel(BasisArgs a) {
   const double* X = a.X + off.x;
   double* phi = a.phi + off.phi;
   const int* info = a.dofinfo + S.dofinfo_off;
-  for (int e2 = threadIdx.x; e2 < R * C; e2 += blockDim.x) {
-    const int l = e2 / C, j = e2 - l * C;
+  // Method S1's set-up keeps only the particular solution (X's column R): g alone
+  const int ncol = a.particular_only ? 1 : C;
+  for (int e2 = threadIdx.x; e2 < R * ncol; e2 += blockDim.x) {
+    const int l = e2 / ncol, j = a.particular_only ? R : e2 - l * ncol;
     const int side = info[3 * l], f0 = info[3 * l + 1], f1 = info[3 * l + 2];
     const double* P = a.proj + S.proj_off[side];
     double acc = 0.0;
@@ -620,8 +631,9 @@ constexpr int kShapes = 3;
 constexpr BasisShape kShape[2][2][kShapes] = {
     // FP32: narrow, wide
     {{{256, 4, 1, 0}, {256, 3, 2, 0}, {256, 3, 1, 1}}, {{256, 1, 2, 0}, {256, 2, 1, 0}, {0, 0, 0, 0}}},
-    // FP64: narrow, wide
-    {{{256, 2, 1, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}}, {{512, 1, 1, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}}},
+    // FP64: narrow, wide (the second wide shape keeps G_b in global memory,
+    // for blocks too large for shared memory beside the right-hand sides)
+    {{{256, 2, 1, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}}, {{512, 1, 1, 0}, {512, 1, 0, 0}, {0, 0, 0, 0}}},
 };
 
 template <typename T, int MT, int NT, int MINB, int GB>
@@ -662,13 +674,17 @@ cudaError_t shape_dispatch(const BasisArgs* a, bool wide, int shape, int max_nx,
       return ctas ? occupancy_of<T, 1, 256, 2, 1>(sm, ctas) : launch_one<T, 1, 256, 2, 1>(*a, sm, refine, st);
     if (wide && shape == 0)
       return ctas ? occupancy_of<T, 2, 512, 1, 1>(sm, ctas) : launch_one<T, 2, 512, 1, 1>(*a, sm, refine, st);
+    if (wide && shape == 1) {
+      const size_t sm0 = basis_smem<T>(max_nx, max_cols, 0);
+      return ctas ? occupancy_of<T, 2, 512, 1, 0>(sm0, ctas) : launch_one<T, 2, 512, 1, 0>(*a, sm0, refine, st);
+    }
   }
   return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-int basis_shape_count(int fp64) { return fp64 ? 1 : kShapes; }
+int basis_shape_count(int fp64) { return fp64 ? 2 : kShapes; }
 
 bool basis_shape_desc(int fp64, int wide, int shape, BasisShape* out) {
   if (shape < 0 || shape >= basis_shape_count(fp64)) return false;

@@ -462,11 +462,11 @@ __device__ __forceinline__ void tile_product(const IfaceArgs& a, int u, int R, i
 
 template <typename T>
 __global__ void __launch_bounds__(256) matvec_kernel(IfaceArgs a, const double* __restrict__ vin, int sel,
-                                                     int* err) {
+                                                     int* err, int u0) {
   extern __shared__ __align__(16) unsigned char smv_raw[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ TileScratch ts;
-  const int u = blockIdx.y;
+  const int u = u0 + blockIdx.y;   // units u0, u0 + 1, ...
   const int t = blockIdx.x;
   if (t >= a.n_tiles[u]) return;
   const int* tl = a.tiles + 3 * ((int64_t)u * a.max_tiles + t);
@@ -715,7 +715,10 @@ struct GmArgs {
   double* st;   // [n_pts][kGmresState]: Hessenberg columns, rotations, rotated right-hand side
   int* j;       // [n_pts]: steps taken in the current cycle
   int m;        // restart length (<= kGmresMax)
+  double cycle_tol;   // > 0: a cycle also ends once it has reduced its initial residual by this factor
 };
+// the state's last slot: the residual norm a cycle started from
+constexpr int kGmBeta = kGmresState - 1;
 // a point's state: column k of H (entries 0..k+1) at k * (kGmresMax + 1), then
 // the cosines, the sines and the rotated right-hand side
 __device__ __forceinline__ double* gm_col(const GmArgs& g, int64_t l, int k) {
@@ -770,6 +773,7 @@ __device__ __forceinline__ void gm_new_cycle(const IfaceArgs& a, const GmArgs& g
   for (int64_t d = lane; d < a.n_lambda; d += 32) v0[d] = r[d] * inv;
   double* gv = gm_gv(g, l);
   for (int i = lane; i <= kGmresMax; i += 32) gv[i] = i == 0 ? rn : 0.0;
+  if (lane == 0) g.st[l * kGmresState + kGmBeta] = rn;
   __syncwarp();
   double* pl = a.p + l * a.n_lambda;
   for (int64_t d = lane; d < a.n_lambda; d += 32) pl[d] = precond64(a, l, v0, (int)d);
@@ -819,36 +823,40 @@ __global__ void __launch_bounds__(256) gmres_arnoldi_kernel(IfaceArgs a, GmArgs 
   for (int64_t d = lane; d < n; d += 32) w[d] = Yl[a.yoff[2 * d]] + Yl[a.yoff[2 * d + 1]];
   __syncwarp();
   double* hcol = gm_col(g, l, j);
-  for (int pass = 0; pass < 2; ++pass) {
-    double acc[kGmresMax + 1];
-#pragma unroll
-    for (int i = 0; i <= kGmresMax; ++i) acc[i] = 0.0;
-    for (int64_t d = lane; d < n; d += 32) {
-      const double wd = w[d];
-#pragma unroll
-      for (int i = 0; i <= kGmresMax; ++i)
-        if (i <= j) acc[i] = fma(gm_v(g, a, i, l)[d], wd, acc[i]);
-    }
-#pragma unroll
-    for (int i = 0; i <= kGmresMax; ++i)
-      if (i <= j) acc[i] = warp_sum(acc[i]);
-    for (int64_t d = lane; d < n; d += 32) {
-      double wd = w[d];
-#pragma unroll
-      for (int i = 0; i <= kGmresMax; ++i)
-        if (i <= j) wd = fma(-acc[i], gm_v(g, a, i, l)[d], wd);
-      w[d] = wd;
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int i = 0; i <= kGmresMax; ++i)
-        if (i <= j) hcol[i] = pass == 0 ? acc[i] : hcol[i] + acc[i];
-    }
-    __syncwarp();
-  }
+  // the warp's Gram-Schmidt coefficients (one basis vector at a time, so that
+  // no thread holds the whole column: occupancy for the memory-bound sweeps)
+  __shared__ double hsh[8][kGmresMax + 1];
+  double* hw = hsh[threadIdx.x >> 5];
+  // classical Gram-Schmidt, repeated only when the first pass cancelled more
+  // than a factor 1/sqrt(2) of w (the criterion of Daniel, Gragg, Kaufman and
+  // Stewart): one pass keeps orthogonality unless w was nearly in the span
   double s2 = 0.0;
   for (int64_t d = lane; d < n; d += 32) s2 = fma(w[d], w[d], s2);
-  const double hn = sqrt(warp_sum(s2));
+  const double w0 = sqrt(warp_sum(s2));
+  double hn = 0.0;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int i = 0; i <= j; ++i) {
+      const double* vi = gm_v(g, a, i, l);
+      double acc = 0.0;
+      for (int64_t d = lane; d < n; d += 32) acc = fma(vi[d], w[d], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        hw[i] = acc;
+        hcol[i] = pass == 0 ? acc : hcol[i] + acc;
+      }
+    }
+    __syncwarp();
+    s2 = 0.0;
+    for (int64_t d = lane; d < n; d += 32) {
+      double wd = w[d];
+      for (int i = 0; i <= j; ++i) wd = fma(-hw[i], gm_v(g, a, i, l)[d], wd);
+      w[d] = wd;
+      s2 = fma(wd, wd, s2);
+    }
+    hn = sqrt(warp_sum(s2));
+    __syncwarp();
+    if (hn >= 0.70710678118654752 * w0) break;   // warp-uniform: every lane holds the sums
+  }
   const bool brk = !(hn > 0.0);   // the Krylov space is invariant: the cycle's solution is exact
   if (!brk) {
     double* vn = gm_v(g, a, j + 1, l);
@@ -877,7 +885,8 @@ __global__ void __launch_bounds__(256) gmres_arnoldi_kernel(IfaceArgs a, GmArgs 
     hcol[j + 1] = 0.0;
     gv[j + 1] = -s * gv[j];
     gv[j] = c * gv[j];
-    end = (fabs(gv[j + 1]) <= rtol * a.gn[l] || j + 1 >= g.m || brk) ? 1 : 0;
+    const double target = fmax(rtol * a.gn[l], g.cycle_tol * g.st[l * kGmresState + kGmBeta]);
+    end = (fabs(gv[j + 1]) <= target || j + 1 >= g.m || brk) ? 1 : 0;
   }
   end = __shfl_sync(0xffffffffu, end, 0);
   __syncwarp();
@@ -898,14 +907,11 @@ __global__ void __launch_bounds__(256) gmres_arnoldi_kernel(IfaceArgs a, GmArgs 
     part = warp_sum(part);
     if (lane == i) yk = (gv[i] - part) / gm_col(g, l, i)[i];
   }
-  double ys[kGmresMax];
-#pragma unroll
-  for (int i = 0; i < kGmresMax; ++i) ys[i] = __shfl_sync(0xffffffffu, yk, i);
+  if (lane < jn) hw[lane] = yk;
+  __syncwarp();
   for (int64_t d = lane; d < n; d += 32) {
     double u = 0.0;
-#pragma unroll
-    for (int i = 0; i < kGmresMax; ++i)
-      if (i < jn) u = fma(ys[i], gm_v(g, a, i, l)[d], u);
+    for (int i = 0; i < jn; ++i) u = fma(hw[i], gm_v(g, a, i, l)[d], u);
     w[d] = u;
   }
   __syncwarp();
@@ -2291,6 +2297,10 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   ++c->launches;
   CK(cudaGetLastError());
   IfaceArgs a = make_args(c, n_pts);
+  // Method S1: unpreconditioned FP64 CG, the Darcy units' products by subdomain solves
+  const bool dtn = krylov == SFB_CG_DTN;
+  if (dtn) { a.dinv = nullptr; a.minv = nullptr; }
+  c->last_dtn = dtn;
   CK(cudaEventRecord(c->ev[1], st));
   const int warps_per_block = 8;
   const int ublocks = (int)((n_pts + warps_per_block - 1) / warps_per_block);
@@ -2307,9 +2317,13 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
     ++c->launches;
     CK(cudaGetLastError());
   }
-  const bool gmres = krylov == SFB_GMRES;
+  const bool gmres = krylov == SFB_GMRES || krylov == SFB_GMRES_MIXED;
+  const bool gmres_mixed = krylov == SFB_GMRES_MIXED;
   GmArgs gma;
   gma.V = d.gmV; gma.st = d.gmS; gma.j = d.gmJ; gma.m = c->opt_gmres_m;
+  // mixed GMRES: the FP32 products limit what one cycle can resolve; a cycle
+  // ends once it has gained this factor, and the FP64 true residual restarts it
+  gma.cycle_tol = gmres_mixed ? 1e-5 : 0.0;
   if (gmres) {
     CK(cudaMemsetAsync(d.rflag, 0, sizeof(int) * n_pts, st));
     gmres_init_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, gma);
@@ -2333,7 +2347,7 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   // its shared memory fits (for the mixed CG: when its FP32 tiles can stay
   // resident); otherwise one launch per step below
   bool persistent = false;
-  if (c->opt_cg_persistent && nu <= kPcgUnits && !gmres) {
+  if (c->opt_cg_persistent && nu <= kPcgUnits && !gmres && !dtn) {
     int dev = 0, coop = 0, n_sm = 0, smem_max = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
@@ -2464,11 +2478,12 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   // whose cycle ended (accepted, or the next cycle)
   for (; gmres && it < max_it;) {
     for (int q = 0; q < chunk && it < max_it; ++q, ++it) {
-      matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.p, 0, d.active + 2);
+      if (gmres_mixed) matvec_kernel<float><<<mgrid, 256, smv32, st>>>(a, d.p, 0, d.active + 2, 0);
+      else matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.p, 0, d.active + 2, 0);
       gmres_arnoldi_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, gma, it, rtol);
       c->launches += 2;
     }
-    matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.lam, 1, d.active + 2);
+    matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.lam, 1, d.active + 2, 0);
     gmres_restart_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, gma, rtol);
     c->launches += 2;
     CK(cudaGetLastError());
@@ -2482,8 +2497,15 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   }
   for (; it < max_it && !persistent && !gmres;) {
     for (int q = 0; q < chunk && it < max_it; ++q, ++it) {
-      if (mixed) matvec_kernel<float><<<mgrid, 256, smv32, st>>>(a, d.p, 0, d.active + 2);
-      else matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.p, 0, d.active + 2);
+      if (dtn) {
+        // Darcy units by one subdomain solve per (point, subdomain); the Stokes unit by its basis
+        CK(launch_dtn(c, d.p, 0, n_pts, 0, nullptr, st));
+        matvec_kernel<double><<<dim3(c->max_tiles, 1), 256, smv, st>>>(a, d.p, 0, d.active + 2, ns);
+      } else if (mixed) {
+        matvec_kernel<float><<<mgrid, 256, smv32, st>>>(a, d.p, 0, d.active + 2, 0);
+      } else {
+        matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.p, 0, d.active + 2, 0);
+      }
       ++c->launches;
       if (regs)
         update_kernel<true><<<ublocks, 32 * warps_per_block, stg, st>>>(a, it, rtol, mixed ? 1 : 0, replace_ratio,
@@ -2495,7 +2517,7 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
     }
     if (mixed) {
       // FP64 residuals of the points that asked for one
-      matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.lam, 1, d.active + 2);
+      matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.lam, 1, d.active + 2, 0);
       ++c->launches;
       reliable_kernel<<<ublocks, 32 * warps_per_block, stg, st>>>(a, rtol, it);
       ++c->launches;
@@ -2585,39 +2607,52 @@ sfb_status moments_accumulate_device(sfb_ctx* c, int64_t n_pts) {
   const int row_tiles = (max_ny + m.rt - 1) / m.rt;
   const int first = c->mom_shift_set ? 0 : 1;
   CK(cudaEventRecord(c->ev[3], st));
-  if (first) {
-    m.mode = 0;
-    darcy_moments_kernel<<<dim3(row_tiles, ns, 1), kMomT, smd, st>>>(m);
-    LAUNCHED("darcy_moments_kernel");
+  if (c->last_dtn) {
+    // Method S1: the Darcy entries of every point from one more subdomain
+    // solve each (the recovery), point chunk by point chunk as rows of the
+    // partial-sum buffer, then their shifted moments
+    const int64_t rows = 2 * ((int64_t)c->mom_chunks + 1);
+    for (int64_t p0 = 0; p0 < n_pts; p0 += rows) {
+      const int64_t cnt = std::min(rows, n_pts - p0);
+      CK(cudaMemsetAsync(d.mom_part, 0, sizeof(double) * cnt * m.len_d, st));
+      CK(launch_dtn(c, d.lam, p0, cnt, 1, d.mom_part, st));
+      CK(launch_s1_moments(c, d.mom_part, p0, cnt, first && p0 == 0 ? 1 : 0, st));
+    }
+  } else {
+    if (first) {
+      m.mode = 0;
+      darcy_moments_kernel<<<dim3(row_tiles, ns, 1), kMomT, smd, st>>>(m);
+      LAUNCHED("darcy_moments_kernel");
+      CK(cudaGetLastError());
+    }
+    m.mode = 1;
+    CK(cudaFuncSetAttribute(darcy_moments_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd));
+    CK(cudaMemsetAsync(d.mom_part, 0, sizeof(double) * 2 * (size_t)m.n_chunks * m.len_d, st));
+    moments_worklist_kernel<<<1, 256, 0, st>>>(m, d.mom_work, d.active + 3, c->mom_work_cap, d.active + 2);
+    LAUNCHED("moments_worklist_kernel");
+    darcy_moments_list_kernel<<<dim3(row_tiles, 1, m.n_chunks), kMomT, smd, st>>>(m, d.mom_work, d.active + 3,
+                                                                                 d.active + 2);
+    LAUNCHED("darcy_moments_list_kernel");
     CK(cudaGetLastError());
+    int max_local = 1;
+    for (int nl : c->n_local) max_local = std::max(max_local, nl);
+    group_moments_kernel<<<dim3(max_local, ns, kGChunks), 256, 0, st>>>(m, d.gmom_part);
+    LAUNCHED("group_moments_kernel");
+    group_moments_reduce<<<dim3(max_local, ns), 256, 0, st>>>(m, d.gmom_part);
+    LAUNCHED("group_moments_reduce");
+    int big_t = kBigT;
+    auto smb_of = [&](int t) { return sizeof(double) * ((size_t)maxC * maxC + 2 * (size_t)maxC + (size_t)maxC * t); };
+    while (big_t > 32 && smb_of(big_t) > 227 * 1024) big_t >>= 1;
+    const size_t smb = smb_of(big_t);
+    CK(cudaFuncSetAttribute(bigroup_moments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+    int max_ent = 0;
+    for (const HostSub& S : c->subs) max_ent = std::max(max_ent, S.ny * S.nx + S.ny * (S.nx + 1) + (S.ny + 1) * S.nx);
+    bigroup_moments_kernel<<<dim3((max_ent + big_t * kBigE - 1) / (big_t * kBigE), ns), big_t, smb, st>>>(m, m.n_chunks);
+    LAUNCHED("bigroup_moments_kernel");
+    CK(cudaGetLastError());
+    reduce_partials<<<256, 256, 0, st>>>(d.mom_part, m.n_chunks + 1, m.len_d, d.mom + m.len_d, d.mom + 2 * m.len_d);
+    LAUNCHED("reduce_partials");
   }
-  m.mode = 1;
-  CK(cudaFuncSetAttribute(darcy_moments_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd));
-  CK(cudaMemsetAsync(d.mom_part, 0, sizeof(double) * 2 * (size_t)m.n_chunks * m.len_d, st));
-  moments_worklist_kernel<<<1, 256, 0, st>>>(m, d.mom_work, d.active + 3, c->mom_work_cap, d.active + 2);
-  LAUNCHED("moments_worklist_kernel");
-  darcy_moments_list_kernel<<<dim3(row_tiles, 1, m.n_chunks), kMomT, smd, st>>>(m, d.mom_work, d.active + 3,
-                                                                               d.active + 2);
-  LAUNCHED("darcy_moments_list_kernel");
-  CK(cudaGetLastError());
-  int max_local = 1;
-  for (int nl : c->n_local) max_local = std::max(max_local, nl);
-  group_moments_kernel<<<dim3(max_local, ns, kGChunks), 256, 0, st>>>(m, d.gmom_part);
-  LAUNCHED("group_moments_kernel");
-  group_moments_reduce<<<dim3(max_local, ns), 256, 0, st>>>(m, d.gmom_part);
-  LAUNCHED("group_moments_reduce");
-  int big_t = kBigT;
-  auto smb_of = [&](int t) { return sizeof(double) * ((size_t)maxC * maxC + 2 * (size_t)maxC + (size_t)maxC * t); };
-  while (big_t > 32 && smb_of(big_t) > 227 * 1024) big_t >>= 1;
-  const size_t smb = smb_of(big_t);
-  CK(cudaFuncSetAttribute(bigroup_moments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
-  int max_ent = 0;
-  for (const HostSub& S : c->subs) max_ent = std::max(max_ent, S.ny * S.nx + S.ny * (S.nx + 1) + (S.ny + 1) * S.nx);
-  bigroup_moments_kernel<<<dim3((max_ent + big_t * kBigE - 1) / (big_t * kBigE), ns), big_t, smb, st>>>(m, m.n_chunks);
-  LAUNCHED("bigroup_moments_kernel");
-  CK(cudaGetLastError());
-  reduce_partials<<<256, 256, 0, st>>>(d.mom_part, m.n_chunks + 1, m.len_d, d.mom + m.len_d, d.mom + 2 * m.len_d);
-  LAUNCHED("reduce_partials");
   CK(cudaEventRecord(c->ev[4], st));
   const int Cs = (int)c->stokes.dofs.size() + 1;
   stokes_cov_kernel<<<kStokesChunks, 256, 0, st>>>(m.ia, d.w, first, d.st_c0, d.st_part);

@@ -41,6 +41,12 @@ struct StokesHost {
   std::vector<double> dir_val;     // full velocity vector of Dirichlet values
   std::vector<double> nb;          // [n_bottom_nodes][R_s]: <xi_l, phi_node . n>
   std::vector<int> nb_node;        // bottom node ids
+  // the free system is ordered node by node along the shorter lattice
+  // direction (u_x, u_y and the vertex pressure of a node together), which
+  // makes it banded: kl sub- and ku super-diagonals; the triplets are sorted
+  // by row, row r's entries at [row_ptr[r], row_ptr[r + 1])
+  int kl = 0, ku = 0;
+  std::vector<int> row_ptr;
 };
 
 struct Dev {
@@ -73,8 +79,12 @@ struct Dev {
   int* nref = nullptr;
   // Stokes
   double* s_mat = nullptr;
+  double* s_pl = nullptr;    // the band LU's panel multipliers in final row order
   int* s_piv = nullptr;
   double* s_rhs = nullptr;
+  double* s_b = nullptr;     // the Stokes right-hand sides, kept for the refinement residual
+  double* s_res = nullptr;   // residual, then correction, of the refinement pass
+  int* s_row_ptr = nullptr;
   double* s_U = nullptr;     // [n_u][Cs]
   double* s_P = nullptr;     // [n_p][Cs]
   double* s_phi = nullptr;   // [Rs][Rs] then g [Rs]
@@ -239,6 +249,7 @@ struct sfb_ctx {
   std::vector<int> pcg_starts;   // host copy of the last resident partition
   int pcg_mode = 0;   // last persistent CG: bit 0 resident tiles, bit 1 two streaming buffers
   double pcg_cycles[6] = {0, 0, 0, 0, 0, 0};   // per CTA, last persistent CG
+  bool last_dtn = false;   // the last batch was solved by Method S1 (its moments recover by subdomain solves)
   ~sfb_ctx() {
     for (cudaEvent_t e : ev)
       if (e) cudaEventDestroy(e);
@@ -250,3 +261,13 @@ struct sfb_ctx {
     if (gcap) cudaStreamDestroy(gcap);
   }
 };
+
+namespace sfb {
+// Method S1 (s1.cu): the subdomain-solve form of the Darcy units' products,
+// the recovery of the Darcy entries, and their moments.
+size_t dtn_smem_bytes(int max_nx, int max_ny, int max_R);
+cudaError_t launch_dtn(sfb_ctx* c, const double* vin, int64_t p0, int64_t cnt, int recovery, double* field,
+                       cudaStream_t st);
+cudaError_t launch_s1_moments(sfb_ctx* c, const double* field, int64_t p0, int64_t cnt, int first,
+                              cudaStream_t st);
+}  // namespace sfb

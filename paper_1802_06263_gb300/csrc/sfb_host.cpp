@@ -208,9 +208,15 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   // Stokes
   const StokesHost& St = c->stokes;
   const int Rs = (int)St.dofs.size(), Cs = Rs + 1;
-  d.s_mat = cv.take<double>((size_t)St.n_free * St.n_free);
+  // the band of the Stokes system's LU factors: row i holds columns
+  // i - kl .. i + kl + ku (partial pivoting widens U to kl + ku)
+  d.s_mat = cv.take<double>((size_t)St.n_free * (2 * St.kl + St.ku + 1) + 8);
+  d.s_pl = cv.take<double>((size_t)(32 + St.kl) * 32);
   d.s_piv = cv.take<int>(St.n_free);
   d.s_rhs = cv.take<double>((size_t)St.n_free * Cs);
+  d.s_b = cv.take<double>((size_t)St.n_free * Cs);
+  d.s_res = cv.take<double>((size_t)St.n_free * Cs);
+  d.s_row_ptr = cv.take<int>((size_t)St.n_free + 1);
   d.s_U = cv.take<double>((size_t)St.n_u * Cs);
   d.s_P = cv.take<double>((size_t)St.n_p * Cs);
   d.s_phi = cv.take<double>((size_t)Rs * Rs + Rs);
@@ -534,6 +540,7 @@ sfb_status sfb_collocation_setup(sfb_ctx* c, const sfb_collocation* spec, int64_
   }
   // points per global dimension of a tensor grid (Section 4.1: isotropic m,
   // or the anisotropic multi-index m_dim)
+  if (spec->local_tensor < 0 || spec->local_tensor > 2) return fail(c, SFB_ERR_ARG, "local_tensor must be 0, 1 or 2");
   std::vector<int> ms;
   if (spec->kind == 0) {
     if (spec->m_dim) ms.assign(spec->m_dim, spec->m_dim + n_dim);
@@ -558,7 +565,14 @@ sfb_status sfb_collocation_setup(sfb_ctx* c, const sfb_collocation* spec, int64_
   const int64_t np_ = c->grid.n_pts();
   for (int s = 0; s < ns; ++s) {
     const int nt = c->subs[s].n_term;
-    if (spec->local_tensor) {
+    if (spec->local_tensor == 2) {
+      // Method S2 (Section 5.3): one local realization per global point, no
+      // reuse: the projections of all global points in order, repeats kept
+      c->loc_y[s].resize((size_t)np_ * nt);
+      for (int64_t l = 0; l < np_; ++l)
+        for (int j = 0; j < nt; ++j) c->loc_y[s][(size_t)l * nt + j] = c->grid.y[l * n_dim + c->dim_off[s] + j];
+      c->n_local[s] = (int)np_;
+    } else if (spec->local_tensor) {
       // the region's own rules on a tensor grid; the largest 1-D rule of the
       // sequence on a Smolyak grid
       std::vector<int> lm;
@@ -794,6 +808,18 @@ sfb_status upload_tables(sfb_ctx* c) {
 // shape with the shorter of its two times is kept for later builds of this
 // precision. The trial launches write the same outputs as the build that
 // follows, which overwrites them and clears the per-item status first.
+// A launch shape exists for the precision and size class, runs at least one
+// CTA per SM at the class's largest grid and column count, and (tensor-core
+// form) has its tensor maps.
+bool shape_fits(int fp64, int wide, int v, int max_nx, int max_cols, bool have_maps) {
+  BasisShape sd;
+  if (!basis_shape_desc(fp64, wide, v, &sd) || (sd.tcgen05 && !have_maps)) return false;
+  int ctas = 0;
+  const cudaError_t e = basis_shape_ctas(fp64, wide, v, max_nx, max_cols, &ctas);
+  if (e != cudaSuccess) cudaGetLastError();
+  return e == cudaSuccess && ctas >= 1;
+}
+
 sfb_status autotune_basis(sfb_ctx* c, int prec, const BasisArgs* cls, const int* cls_nx, const int* cls_cols,
                           int refine) {
   const int fp64 = prec == SFB_FP64 ? 1 : 0;
@@ -805,19 +831,16 @@ sfb_status autotune_basis(sfb_ctx* c, int prec, const BasisArgs* cls, const int*
   for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
     for (int v = 0; v < 4; ++v) c->btune_ms[prec][q][v] = 0.0;
     c->bshape[prec][q] = 0;
-    if (cls[q].n_items == 0 || ns < 2) continue;
+    if (cls[q].n_items == 0) continue;
+    // the shapes of this class that fit at its sizes; one alone is not timed
+    std::vector<int> fit;
+    for (int v = 0; v < ns && v < 4; ++v)
+      if (shape_fits(fp64, q == 0, v, cls_nx[q], cls_cols[q], cls[q].gmaps != nullptr)) fit.push_back(v);
+    if (fit.size() == 1) c->bshape[prec][q] = fit[0];
+    if (fit.size() < 2) continue;
     int best = -1;
-    for (int v = 0; v < ns && v < 4 && e == cudaSuccess; ++v) {
-      BasisShape sd;
-      if (!basis_shape_desc(fp64, q == 0, v, &sd) || (sd.tcgen05 && !cls[q].gmaps)) continue;
-      int ctas = 0;
-      e = basis_shape_ctas(fp64, q == 0, v, cls_nx[q], cls_cols[q], &ctas);
-      if (e != cudaSuccess || ctas < 1) {
-        // a shape that does not fit at these sizes is skipped, not an error
-        cudaGetLastError();
-        e = cudaSuccess;
-        continue;
-      }
+    for (int v : fit) {
+      if (e != cudaSuccess) break;
       float ms_min = 0.f;
       for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
         if (rep > 0) e = cudaEventRecord(t0, st);
@@ -904,13 +927,17 @@ extern "C" {
 
 sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats* stats) {
   if (!c) return SFB_ERR_ARG;
-  if (prec < 0 || prec > 2) return fail(c, SFB_ERR_ARG, "bad precision");
+  if (prec < 0 || prec > SFB_FACTOR_FP64) return fail(c, SFB_ERR_ARG, "bad precision");
   if (!c->ws) return fail(c, SFB_ERR_WORKSPACE, "no workspace set");
   if (c->ws_stale)
     return fail(c, SFB_ERR_STATE, "set-up changed after sfb_set_workspace: call sfb_workspace_size and "
                                   "sfb_set_workspace again");
-  if (prec == SFB_FP64 && c->ws_prec != SFB_FP64)
+  if ((prec == SFB_FP64 || prec == SFB_FACTOR_FP64) && c->ws_prec != SFB_FP64)
     return fail(c, SFB_ERR_WORKSPACE, "workspace was sized for the FP32 factor; FP64 needs more");
+  // Method S1's set-up: the FP64 kernel with the particular right-hand side
+  // only, launched plainly with the FP64 build's launch shapes
+  const bool factor_only = prec == SFB_FACTOR_FP64;
+  if (factor_only) prec = SFB_FP64;
   Dev& d = c->dev;
   cudaStream_t st = c->stream;
   if (c->basis_prec < 0) {
@@ -933,6 +960,7 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   a.cycles = d.cycles;
   a.max_refine = c->opt_refine_max;
   a.refine_tol = c->opt_refine_tol;
+  a.particular_only = factor_only ? 1 : 0;
   if (prec != SFB_FP64 && encode_gmaps(c)) a.gmaps = d.gmaps;
   // size classes: [0] grids wider than 64 cells (the first n_wide items), [1] the rest
   const int fp64 = prec == SFB_FP64 ? 1 : 0;
@@ -943,7 +971,7 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   cls[1].item_k = a.item_k + c->n_wide;
   cls[1].n_items = n - (int)c->n_wide;
   const int cls_nx[2] = {c->wide_nx, c->narrow_nx}, cls_cols[2] = {c->wide_cols, c->narrow_cols};
-  if (c->opt_basis_autotune && !c->btuned[prec]) {
+  if (c->opt_basis_autotune && !c->btuned[prec] && !factor_only) {
     sfb_status s = autotune_basis(c, prec, cls, cls_nx, cls_cols, refine);
     if (s != SFB_OK) return s;
   }
@@ -953,9 +981,13 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   SFB_CUDA(cudaMemsetAsync(d.errest, 0, sizeof(double) * n, st), "memset");
   SFB_CUDA(cudaMemsetAsync(d.nref, 0, sizeof(int) * n, st), "memset");
   int shp[2] = {c->bshape[prec][0], c->bshape[prec][1]};
-  for (int q = 0; q < 2; ++q) {   // a shape this class lacks, or the tensor-core one without maps: shape 0
-    BasisShape sd;
-    if (!basis_shape_desc(fp64, q == 0, shp[q], &sd) || (sd.tcgen05 && !a.gmaps)) shp[q] = 0;
+  // a shape this class lacks or that does not fit (or the tensor-core one
+  // without maps): the first shape that fits
+  for (int q = 0; q < 2; ++q) {
+    if (cls[q].n_items == 0 || shape_fits(fp64, q == 0, shp[q], cls_nx[q], cls_cols[q], a.gmaps != nullptr)) continue;
+    shp[q] = 0;
+    for (int v = 0; v < basis_shape_count(fp64); ++v)
+      if (shape_fits(fp64, q == 0, v, cls_nx[q], cls_cols[q], a.gmaps != nullptr)) { shp[q] = v; break; }
   }
   const bool two = cls[0].n_items > 0 && cls[1].n_items > 0;
   if (two) {
@@ -987,7 +1019,7 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   // that is itself being captured (the caller's graph) gets the plain launches.
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   SFB_CUDA(cudaStreamIsCapturing(st, &cap), "capture status");
-  const bool graph = c->opt_basis_graph && cap == cudaStreamCaptureStatusNone;
+  const bool graph = c->opt_basis_graph && cap == cudaStreamCaptureStatusNone && !factor_only;
   if (graph) {
     sfb_ctx::GraphKey key;
     key.ws = c->ws;
@@ -1066,7 +1098,7 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
     stats->n_items = n;
     int64_t fr = 0;
     for (int s = 0; s < (int)c->subs.size(); ++s) fr += (int64_t)c->subs[s].dofs.size() * c->n_local[s];
-    stats->n_flux_responses = fr;
+    stats->n_flux_responses = factor_only ? 0 : fr;
     stats->max_refine_steps = n ? *std::max_element(nref.begin(), nref.end()) : 0;
     double nref_sum = 0.0;
     for (int i = 0; i < n; ++i) nref_sum += nref[i];
@@ -1086,7 +1118,7 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
     int64_t id = 0;
     for (int s = 0; s < (int)c->subs.size(); ++s) {
       const HostSub& H = c->subs[s];
-      const double nx = H.nx, ny = H.ny, C = (double)H.dofs.size() + 1.0;
+      const double nx = H.nx, ny = H.ny, C = factor_only ? 1.0 : (double)H.dofs.size() + 1.0;
       const double fac = 7.0 / 3.0 * nx * nx * nx * ny, sol = 6.0 * nx * nx * ny * C, pass = 11.0 * nx * ny * C;
       for (int k = 0; k < c->n_local[s]; ++k, ++id) {
         if (prec == SFB_FP64) {
@@ -1107,7 +1139,7 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
     stats->reserved = 0;
   }
   c->basis_done = true;
-  c->basis_prec = prec;
+  c->basis_prec = factor_only ? SFB_FACTOR_FP64 : prec;
   if (any & ST_NONFINITE) return fail(c, SFB_ERR_NONFINITE, "non-finite permeability or solution");
   if (any & ST_NOT_SPD) return fail(c, SFB_ERR_NOT_SPD, "non-positive pivot in a block factorization");
   if (any & ST_TIMEOUT) return fail(c, SFB_ERR_TIMEOUT, "a bulk copy did not complete within the wait limit");
@@ -1147,6 +1179,8 @@ sfb_status sfb_get_basis(sfb_ctx* c, int32_t sub, int32_t k, double* phi, double
   const ItemOff& o = c->offs[id];
   const HostSub& S = c->subs[sub];
   const int R = (int)S.dofs.size();
+  if (phi && c->basis_prec == SFB_FACTOR_FP64)
+    return fail(c, SFB_ERR_STATE, "the factor-only build forms no flux basis: phi must be NULL");
   if (phi) SFB_CUDA(cudaMemcpyAsync(phi, c->dev.phi + o.phi, sizeof(double) * R * R, cudaMemcpyDefault, st), "copy");
   if (g) SFB_CUDA(cudaMemcpyAsync(g, c->dev.phi + o.phi + (int64_t)R * R, sizeof(double) * R, cudaMemcpyDefault, st), "copy");
   if (x) SFB_CUDA(cudaMemcpyAsync(x, c->dev.X + o.x, sizeof(double) * (size_t)S.nx * S.ny * (R + 1),
@@ -1159,9 +1193,22 @@ sfb_status sfb_interface_solve_batch(sfb_ctx* c, const double* y, const double* 
                                      double rtol, int32_t max_it, double* lambda_out, int32_t* iters_out) {
   if (!c) return SFB_ERR_ARG;
   if (!c->basis_done) return fail(c, SFB_ERR_STATE, "sfb_build_stochastic_basis must come first");
-  if (n_pts < 0 || (krylov != SFB_CG && krylov != SFB_CG_MIXED && krylov != SFB_GMRES) || !(rtol > 0) ||
-      max_it < 1)
+  if (n_pts < 0 || krylov < SFB_CG || krylov > SFB_CG_DTN || !(rtol > 0) || max_it < 1)
     return fail(c, SFB_ERR_ARG, "bad interface solve arguments");
+  if (krylov == SFB_CG_DTN && c->basis_prec != SFB_FP64 && c->basis_prec != SFB_FACTOR_FP64)
+    return fail(c, SFB_ERR_STATE, "SFB_CG_DTN needs the FP64 block factors (an SFB_FP64 or SFB_FACTOR_FP64 build)");
+  if (krylov != SFB_CG_DTN && c->basis_prec == SFB_FACTOR_FP64)
+    return fail(c, SFB_ERR_STATE, "the factor-only build forms no flux basis: only SFB_CG_DTN solves from it");
+  if (krylov == SFB_CG_DTN) {
+    int mnx = 1, mny = 1, mR = 1;
+    for (const HostSub& H : c->subs) {
+      mnx = std::max(mnx, H.nx);
+      mny = std::max(mny, H.ny);
+      mR = std::max(mR, (int)H.dofs.size());
+    }
+    if (dtn_smem_bytes(mnx, mny, mR) > 227 * 1024)
+      return fail(c, SFB_ERR_UNSUPPORTED, "SFB_CG_DTN keeps a subdomain's forward sweep in shared memory: grid too large");
+  }
   if (n_pts == 0) return SFB_OK;  // an empty batch changes nothing
   if (!y || !w) return fail(c, SFB_ERR_ARG, "bad interface solve arguments");
   if (n_pts > c->ws_pts) return fail(c, SFB_ERR_WORKSPACE, "batch larger than the workspace was sized for");

@@ -137,6 +137,7 @@ struct BasisArgs {
   int max_refine;
   double refine_tol;
   const void* gmaps = nullptr;  // per item id: CUtensorMap of its block inverses (tensor-core form)
+  int particular_only = 0;      // Method S1's set-up: factor and particular solution only (FP64 kernel)
 };
 
 // Launchers (basis.cu).

@@ -187,6 +187,60 @@ void stokes_assemble_host(sfb_ctx* c) {
     if (fr < 0) continue;
     for (int l = 0; l < Rs; ++l) S.rhs[(size_t)fr * Cs + l] = -S.nb[(size_t)bi * Rs + l];
   }
+  // Band ordering of the free unknowns: by P2-lattice node along the shorter
+  // lattice direction, the two velocity components and (at vertices) the
+  // pressure of a node together. A triangle couples nodes of two neighbouring
+  // lattice lines, so the bandwidth is about six lattice lines' worth of
+  // unknowns instead of the whole system.
+  const bool by_column = S.NY < S.NX;
+  auto key_of = [&](int d) -> int64_t {
+    int i, j, comp;
+    if (d < S.n_u) {
+      comp = d / nn;
+      i = (d % nn) % S.NX;
+      j = (d % nn) / S.NX;
+    } else {
+      const int q = d - S.n_u;
+      comp = 2;
+      i = 2 * (q % (S.sx + 1));
+      j = 2 * (q / (S.sx + 1));
+    }
+    const int64_t line = by_column ? (int64_t)i * S.NY + j : (int64_t)j * S.NX + i;
+    return line * 3 + comp;
+  };
+  std::vector<int> order(S.n_free);
+  for (int f = 0; f < S.n_free; ++f) order[f] = f;
+  std::sort(order.begin(), order.end(),
+            [&](int a, int b) { return key_of(S.free_to_full[a]) < key_of(S.free_to_full[b]); });
+  std::vector<int> pos(S.n_free);
+  for (int b = 0; b < S.n_free; ++b) pos[order[b]] = b;
+  std::vector<int> f2f(S.n_free);
+  for (int b = 0; b < S.n_free; ++b) f2f[b] = S.free_to_full[order[b]];
+  S.free_to_full.swap(f2f);
+  for (int d = 0; d < n_full; ++d)
+    if (S.free_index[d] >= 0) S.free_index[d] = pos[S.free_index[d]];
+  std::vector<double> rhs2(S.rhs.size());
+  for (int f = 0; f < S.n_free; ++f)
+    std::copy(S.rhs.begin() + (size_t)f * Cs, S.rhs.begin() + (size_t)(f + 1) * Cs, rhs2.begin() + (size_t)pos[f] * Cs);
+  S.rhs.swap(rhs2);
+  S.kl = S.ku = 0;
+  std::vector<Trip> bt(S.tr_val.size());
+  for (size_t t = 0; t < S.tr_val.size(); ++t) {
+    const int r = pos[S.tr_row[t]], q = pos[S.tr_col[t]];
+    bt[t] = {(int64_t)r * S.n_free + q, S.tr_val[t]};
+    S.kl = std::max(S.kl, r - q);
+    S.ku = std::max(S.ku, q - r);
+  }
+  // row-major order (the refinement residual runs row by row)
+  std::sort(bt.begin(), bt.end(), [](const Trip& a, const Trip& b) { return a.key < b.key; });
+  S.row_ptr.assign((size_t)S.n_free + 1, 0);
+  for (size_t t = 0; t < bt.size(); ++t) {
+    S.tr_row[t] = (int)(bt[t].key / S.n_free);
+    S.tr_col[t] = (int)(bt[t].key % S.n_free);
+    S.tr_val[t] = bt[t].val;
+    ++S.row_ptr[(size_t)S.tr_row[t] + 1];
+  }
+  for (int r = 0; r < S.n_free; ++r) S.row_ptr[(size_t)r + 1] += S.row_ptr[r];
 }
 
 }  // namespace sfb

@@ -120,6 +120,7 @@ def test_basis_launch_shapes_and_options():
     assert sfb.basis_launch_shape(sfb.MIXED, 1, 2) is None   # no tensor-core form beyond 64 cells
     assert sfb.basis_launch_shape(sfb.FP64, 0, 0) == (256, 2, 1, 0)
     assert sfb.basis_launch_shape(sfb.FP64, 1, 0) == (512, 1, 1, 0)
+    assert sfb.basis_launch_shape(sfb.FP64, 1, 1) == (512, 1, 0, 0)   # G_b from global memory
     assert sfb.basis_launch_shape(sfb.FP64, 0, 1) is None
     assert sfb.basis_launch_shape(sfb.MIXED, 0, 3) is None
     assert sfb.basis_launch_shape(sfb.MIXED, 0, -1) is None

@@ -43,13 +43,15 @@ def test_every_launch_shape_builds_the_same_basis(prec):
     import paper_1802_06263_gb300 as sfb
     s = _solver()
     s.set_option("basis_graph", 0)
-    n_shapes = 3 if prec == sfb.MIXED else 1
+    n_shapes = 3 if prec == sfb.MIXED else 2
     ref = None
     for v in range(n_shapes):
         s.set_option("basis_shape", v)
         st = s.build_basis(prec)
         tc = v == 2   # the tensor-core shape exists for the narrow class only
-        assert st["launch_shape"] == ([0, v] if tc else [v, v]) and st["graph"] == 0
+        # a class without shape v (FP64 narrow grids have one shape) keeps shape 0
+        expect = [v if sfb.basis_launch_shape(prec, wide, v) else 0 for wide in (1, 0)]
+        assert st["launch_shape"] == expect and st["graph"] == 0
         assert st["n_not_converged"] == 0
         items = _items(s)
         if ref is None:
@@ -157,7 +159,9 @@ def test_autotuner_times_every_shape_and_keeps_the_fastest():
     n0 = s.launch_count()
     st2 = s.build_basis(sfb.MIXED)
     assert st2["launch_shape"] == st["launch_shape"] and s.launch_count() - n0 == 3
-    # FP64 has one shape per class: nothing to time
+    # FP64: two shapes for the wide grids (G_b in shared or in global memory),
+    # both timed; one for the narrow grids, not timed
     st64 = s.build_basis(sfb.FP64)
-    assert st64["launch_shape"] == [0, 0]
-    assert all(m == 0 for r in st64["tune_ms"] for m in r)
+    assert all(m > 0 for m in st64["tune_ms"][0][:2]), st64["tune_ms"]
+    assert st64["launch_shape"][0] == int(np.argmin(st64["tune_ms"][0][:2]))
+    assert st64["launch_shape"][1] == 0 and all(m == 0 for m in st64["tune_ms"][1])

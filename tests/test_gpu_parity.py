@@ -47,13 +47,14 @@ def test_basis_parity(key, prec):
     print(key, prec, "worst basis rel err", worst, st)
 
 
-@pytest.mark.parametrize("krylov", [0, 1, 2])
+@pytest.mark.parametrize("krylov", [0, 1, 2, 3])
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("key", CASES)
 def test_interface_and_moments_parity(key, prec, krylov):
     """krylov 0: FP64 CG; 1: CG with FP32 products and FP64 residual
     replacement, which must reach the same FP64 residual tolerance; 2:
-    restarted GMRES(30) in FP64, accepted on its FP64 true residual."""
+    restarted GMRES(30) in FP64, accepted on its FP64 true residual; 3: the
+    same GMRES with FP32 Arnoldi products, restarted from FP64 residuals."""
     p, y, wt, lams, mom = oracle_case(key)
     s, _ = _solver(key, prec)
     rtol = 1e-14 if krylov == 0 else 1e-13
@@ -247,3 +248,125 @@ def test_gmres_not_converged_is_reported():
     lam, it, rc = s.solve_host(y, wt, rtol=1e-14, max_it=3, check=False, krylov=sfb.GMRES)
     assert rc == sfb.SFB_ERR_NOT_CONVERGED
     assert np.all(it == -3)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_method_s2_per_point_bases(prec):
+    """Method S2 (Section 5.3): a multiscale flux basis built for every global
+    point, with no reuse between points. The per-point local sets give each of
+    the medium workload's 289 points its own items in every subdomain (289 x 4
+    builds, the paper's N_S2 counts R + 2 subdomain solves per point and
+    subdomain: R basis columns here, the particular column beside them, the
+    recovery from the stored responses), and the same mortar solutions and
+    moments as the oracle (and hence as Method S3)."""
+    import paper_1802_06263_gb300 as sfb
+    p, y, wt, lams, mom = oracle_case("medium")
+    w = make_workload("medium")
+    w["collocation"] = dict(w["collocation"], local="per_point")
+    s = sfb.Solver(w)
+    assert s.n_pts == len(y) == 289
+    for i in range(s.n_darcy):
+        assert len(s.local_points(i)) == 289
+    s.allocate(prec)
+    st = s.build_basis(prec)
+    assert st["n_items"] == 289 * 4
+    assert st["n_flux_responses"] == 289 * sum(len(s.subdomain_dofs(i)) for i in range(4))
+    lam, it, rc = s.solve_host(y, wt, rtol=1e-13, max_it=5000, krylov=prec)
+    assert rc == 0
+    tol = TOL[prec]
+    for l in range(len(y)):
+        assert_close(lam[l], lams[l], tol, ("lambda", l))
+    for f in ("darcy_p", "darcy_flux", "stokes_u", "stokes_p"):
+        m, v = s.moments(f)
+        assert_close(m, mom[f][0], tol, (f, "mean"))
+        assert_close(v, mom[f][1], tol, (f, "variance"))
+
+
+@pytest.mark.parametrize("case", ["tiny", "ragged", "paper_l2"])
+def test_method_s1_against_the_oracle(case):
+    """Method S1 (Section 5.2): FP64 block factors and the particular solution
+    built once per local realization, then unpreconditioned FP64 CG whose
+    Darcy products are one subdomain solve per (point, subdomain) and
+    iteration. Against the oracle's own Method S1 (sparse LU solves inside
+    CG): the mortar solutions within 1e-10, the CG iterations within one of
+    each other, so the solve counts of Section 5.2 (per Darcy subdomain the
+    iterations plus the right-hand side and recovery solves of every point)
+    within one per point; the moments agree with the oracle's Method S3
+    result, the same discrete solution."""
+    import paper_1802_06263_gb300 as sfb
+    from oracle import coupled
+    p, y, wt, lams3, mom = oracle_case(case)
+    lams1, its1, counts1 = coupled.method_s1(p, y, rtol=1e-12, max_it=5000)
+    s = sfb.Solver(make_workload(case))
+    s.allocate(sfb.FP64)
+    st = s.build_basis(sfb.FACTOR_FP64)
+    assert st["n_not_converged"] == 0 and st["n_flux_responses"] == 0
+    lam, it, rc = s.solve_host(y, wt, rtol=1e-12, max_it=5000, krylov=sfb.CG_DTN)
+    assert rc == 0
+    for l in range(len(y)):
+        assert_close(lam[l], lams1[l], 1e-10, ("lambda", l))
+        assert_close(lam[l], lams3[l], 1e-10, ("lambda vs S3", l))
+    assert np.all(np.abs(it - its1) <= 1), (it, its1)
+    n_gpu = int(np.sum(it)) + 2 * len(y)
+    for sub in range(s.n_darcy):
+        assert abs(n_gpu - int(counts1[sub])) <= len(y)
+    for f in ("darcy_p", "darcy_flux", "stokes_u", "stokes_p"):
+        m, v = s.moments(f)
+        assert_close(m, mom[f][0], 1e-10, (f, "mean"))
+        assert_close(v, mom[f][1], 1e-10, (f, "variance"))
+
+
+@pytest.mark.parametrize("build", ["factor", "fp64"])
+def test_method_s1_medium(build):
+    """Method S1 on the medium workload (289 points, 4 subdomains of 32 x 32
+    cells), from the factor-only build and from the full FP64 build (whose
+    block factors it reuses): the mortar solutions and moments of the oracle
+    within 1e-10, the same CG iterations as Method S3's unpreconditioned
+    FP64 CG on the same points (both apply the same operator), and the
+    particular solutions' g equal to the full build's."""
+    import paper_1802_06263_gb300 as sfb
+    p, y, wt, lams, mom = oracle_case("medium")
+    s = sfb.Solver(make_workload("medium"))
+    s.allocate(sfb.FP64)
+    s.set_option("cg_precond", 0)
+    s.build_basis(sfb.FP64)
+    g_full = [s.get_basis(i, 0)[1] for i in range(s.n_darcy)]
+    _, it3, rc3 = s.solve_host(y, wt, rtol=1e-12, max_it=5000, krylov=sfb.CG)
+    assert rc3 == 0
+    if build == "factor":
+        st = s.build_basis(sfb.FACTOR_FP64)
+        assert st["n_items"] > 0 and st["n_not_converged"] == 0
+        for i in range(s.n_darcy):
+            phi, g, x = s.get_basis(i, 0, with_x=True)
+            assert phi is None
+            assert_close(g, g_full[i], 1e-12, ("g", i))
+    s.moments_reset()
+    lam, it, rc = s.solve_host(y, wt, rtol=1e-12, max_it=5000, krylov=sfb.CG_DTN)
+    assert rc == 0
+    for l in range(len(y)):
+        assert_close(lam[l], lams[l], 1e-10, ("lambda", l))
+    assert np.all(np.abs(it - it3) <= 1)
+    for f in ("darcy_p", "darcy_flux", "stokes_u", "stokes_p"):
+        m, v = s.moments(f)
+        assert_close(m, mom[f][0], 1e-10, (f, "mean"))
+        assert_close(v, mom[f][1], 1e-10, (f, "variance"))
+
+
+def test_method_s1_state_checks():
+    """The factor-only build forms no flux basis: the basis-product solvers
+    refuse it (SFB_ERR_STATE), and so does Method S1 after a mixed build,
+    which stores FP32 factors."""
+    import paper_1802_06263_gb300 as sfb
+    s = sfb.Solver(make_workload("tiny"))
+    y, wt = s.points()
+    s.allocate(sfb.FP64)
+    s.build_basis(sfb.FACTOR_FP64)
+    for kr in (sfb.CG, sfb.CG_MIXED, sfb.GMRES, sfb.GMRES_MIXED):
+        _, _, rc = s.solve_host(y, wt, krylov=kr, check=False)
+        assert rc == 2
+    s.build_basis(sfb.MIXED)
+    _, _, rc = s.solve_host(y, wt, krylov=sfb.CG_DTN, check=False)
+    assert rc == 2
+    s.build_basis(sfb.FP64)
+    lam, it, rc = s.solve_host(y, wt, rtol=1e-12, krylov=sfb.CG_DTN)
+    assert rc == 0 and np.all(it > 0)
