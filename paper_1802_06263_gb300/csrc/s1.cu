@@ -46,51 +46,43 @@ struct DtnArgs {
   int recovery;
 };
 
-// z = G u for the np x np block G (FP64, symmetric, so row r is read as
-// column r and consecutive threads read consecutive entries), u and z in
-// shared memory; the threads split the sum into parts, added up in `part`.
-__device__ __forceinline__ void block_matvec(const double* __restrict__ G, const double* u, double* z, int np,
-                                             double* part) {
-  const int t = threadIdx.x;
-  if (np > kDtnThreads / 2) {   // one thread per row
-    for (int r = t; r < np; r += blockDim.x) {
-      double acc = 0.0;
-      for (int k = 0; k < np; ++k) acc = fma(G[(int64_t)k * np + r], u[k], acc);
-      z[r] = acc;
-    }
-    __syncthreads();
-    return;
-  }
-  const int parts = kDtnThreads / np;   // >= 2
-  const int r = t % np, q = t / np;
-  if (q < parts) {
+// Partial sums of z = G u for the np x np block G (FP64, symmetric, so row r
+// is read as column r and consecutive threads read consecutive entries):
+// part[q][r] = sum over the q-th of `parts` slices of k of G[k][r] u[k].
+__device__ __forceinline__ void block_partials(const double* __restrict__ G, const double* u, int np, int parts,
+                                               double* part) {
+  for (int idx = threadIdx.x; idx < parts * np; idx += blockDim.x) {
+    const int q = idx / np, r = idx - q * np;
     const int k0 = q * np / parts, k1 = (q + 1) * np / parts;
-    double acc = 0.0;
-    for (int k = k0; k < k1; ++k) acc = fma(G[(int64_t)k * np + r], u[k], acc);
-    part[q * np + r] = acc;
+    double a0 = 0.0, a1 = 0.0;
+    int k = k0;
+    for (; k + 1 < k1; k += 2) {
+      a0 = fma(G[(int64_t)k * np + r], u[k], a0);
+      a1 = fma(G[(int64_t)(k + 1) * np + r], u[k + 1], a1);
+    }
+    if (k < k1) a0 = fma(G[(int64_t)k * np + r], u[k], a0);
+    part[idx] = a0 + a1;
   }
-  __syncthreads();
-  for (int rr = t; rr < np; rr += blockDim.x) {
-    double acc = 0.0;
-    for (int qq = 0; qq < parts; ++qq) acc += part[qq * np + rr];
-    z[rr] = acc;
-  }
-  __syncthreads();
 }
 
-// One CTA per (point p0 + blockIdx.x, Darcy subdomain blockIdx.y).
-__global__ void __launch_bounds__(kDtnThreads) dtn_kernel(DtnArgs a) {
+// One CTA per (point p0 + blockIdx.x, Darcy subdomain blockIdx.y). Each block
+// row costs two barriers: one after the partial products, one after the
+// threads r < np have summed row r and formed their entry of the next row's
+// right-hand side.
+__global__ void __launch_bounds__(kDtnThreads, 4) dtn_kernel(DtnArgs a) {
   extern __shared__ __align__(16) double dsm[];
   const int64_t l = a.p0 + blockIdx.x;
   const int sub = blockIdx.y;
   // product mode: the points still iterating; recovery: every point
   if (!a.recovery && a.pstat[l] != 0) return;
-  const SubDev S = a.subs[sub];
+  const SubDev& S = a.subs[sub];
   const int k = a.kmap[l * a.ns + sub];
   if (k < 0) return;
   const ItemOff off = a.off[S.item0 + k];
   const int nx = S.nx, ny = S.ny, R = S.R;
   const int np = (nx + kPanel - 1) & ~(kPanel - 1);
+  const int parts = max(1, kDtnThreads / np);
+  const int nb = 2 * nx + 2 * ny;   // boundary faces: bottom nx, right ny, top nx, left ny
   Geo g;
   g.nx = nx; g.ny = ny; g.R = R; g.C = R + 1; g.Cp = (R + 4) & ~3; g.nc = nx * ny;
   g.Tx = a.T + off.t;
@@ -98,61 +90,87 @@ __global__ void __launch_bounds__(kDtnThreads) dtn_kernel(DtnArgs a) {
   const double* Gi = a.G + off.g;
   const double* Sg = a.S + off.sc;
   const double* DLg = a.DL + off.sc;
-  // shared memory: z rows [ny][np] | c [R] | u [np] | d [np] | v [np] | parts | boundary x
+  // shared memory: z rows [ny][np] | c [R] | u [np] | part | mortar values gf [nb] | boundary x [nb]
   double* Z = dsm;
   double* c = Z + (int64_t)ny * np;
   double* u = c + ((R + 1) & ~1);
-  double* d = u + np;
-  double* v = d + np;
-  double* part = v + np;
-  double* xb = part + kDtnThreads;   // x on the bottom, right, top, left cells: nx, ny, nx, ny
+  double* part = u + np;
+  double* gf = part + max(kDtnThreads, np);
+  double* xb = gf + nb;
   const int64_t* gd = a.gdof + S.gdof_off;
   for (int j = threadIdx.x; j < R; j += blockDim.x) c[j] = a.vin[l * a.n_lambda + gd[j]];
   __syncthreads();
-  // forward sweep: z_b = G_b (s_b r_b + D_{b-1} z_{b-1}), r = B c (+ the particular data)
+  // mortar pressure on every boundary face of an interface side, sum_j c_j <xi_j>_f
+  for (int e = threadIdx.x; e < nb; e += blockDim.x) {
+    const int side = e < nx ? 0 : e < nx + ny ? 1 : e < 2 * nx + ny ? 2 : 3;
+    const int f = side == 0 ? e : side == 1 ? e - nx : side == 2 ? e - nx - ny : e - 2 * nx - ny;
+    double v = 0.0;
+    if (S.side_type[side] == SIDE_IFACE) {
+      const double* P = a.proj + S.proj_off[side] + (int64_t)f * R;
+      for (int j = 0; j < R; ++j) v = fma(P[j], c[j], v);
+    }
+    gf[e] = v;
+  }
+  __syncthreads();
+  // entry r of row b of s (B c + particular data) + D_{b-1} z_{b-1}
+  auto urow = [&](int b, int r, double zprev) -> double {
+    if (r >= nx) return 0.0;
+    double rhs = 0.0;
+    if (b == 0) rhs = fma(g.Ty[r], gf[r], rhs);
+    if (b == ny - 1) rhs = fma(g.Ty[ny * nx + r], gf[nx + ny + r], rhs);
+    if (r == 0) rhs = fma(g.Tx[b * (nx + 1)], gf[2 * nx + ny + b], rhs);
+    if (r == nx - 1) rhs = fma(g.Tx[b * (nx + 1) + nx], gf[nx + b], rhs);
+    if (a.recovery) rhs += rhs_entry(S, g, a.proj, b, r, R);
+    double v = Sg[b * nx + r] * rhs;
+    if (b > 0) v = fma(DLg[b * nx + r], zprev, v);
+    return v;
+  };
+  // forward sweep: z_b = G_b (s_b r_b + D_{b-1} z_{b-1})
+  for (int r = threadIdx.x; r < np; r += blockDim.x) u[r] = urow(0, r, 0.0);
+  __syncthreads();
   for (int b = 0; b < ny; ++b) {
-    for (int i = threadIdx.x; i < np; i += blockDim.x) {
-      double ui = 0.0;
-      if (i < nx) {
-        double rhs = 0.0;
-        if (b == 0 || b == ny - 1 || i == 0 || i == nx - 1)
-          for (int j = 0; j < R; ++j) rhs = fma(c[j], rhs_entry(S, g, a.proj, b, i, j), rhs);
-        if (a.recovery) rhs += rhs_entry(S, g, a.proj, b, i, R);
-        ui = Sg[b * nx + i] * rhs;
-        if (b > 0) ui = fma(DLg[b * nx + i], Z[(int64_t)(b - 1) * np + i], ui);
-      }
-      u[i] = ui;
+    block_partials(Gi + (int64_t)b * np * np, u, np, parts, part);
+    __syncthreads();
+    for (int r = threadIdx.x; r < np; r += blockDim.x) {
+      double z = 0.0;
+      for (int q = 0; q < parts; ++q) z += part[q * np + r];
+      Z[(int64_t)b * np + r] = z;
+      if (b + 1 < ny) u[r] = urow(b + 1, r, z);
     }
     __syncthreads();
-    block_matvec(Gi + (int64_t)b * np * np, u, Z + (int64_t)b * np, np, part);
   }
-  // backward sweep: d_b = z_b + G_b (D_b d_{b+1}), x_b = s_b d_b (d holds d_{b+1})
+  // backward sweep: d_b = z_b + G_b (D_{b+1} d_{b+1}), x_b = s_b d_b; u holds D_{b+1} d_{b+1}
   double* fld = a.recovery ? a.field + (int64_t)blockIdx.x * a.len_d : nullptr;
-  for (int b = ny - 1; b >= 0; --b) {
-    if (b < ny - 1) {
-      for (int i = threadIdx.x; i < np; i += blockDim.x) v[i] = i < nx ? DLg[(b + 1) * nx + i] * d[i] : 0.0;
-      __syncthreads();
-      block_matvec(Gi + (int64_t)b * np * np, v, u, np, part);
-    }
-    for (int i = threadIdx.x; i < np; i += blockDim.x) {
-      const double di = Z[(int64_t)b * np + i] + (b < ny - 1 ? u[i] : 0.0);
-      d[i] = di;
-      if (i < nx) {
-        const double x = Sg[b * nx + i] * di;
-        if (fld) fld[a.cell_off[sub] + (int64_t)b * nx + i] = x;
-        if (b == 0) xb[i] = x;
-        if (i == nx - 1) xb[nx + b] = x;
-        if (b == ny - 1) xb[nx + ny + i] = x;
-        if (i == 0) xb[2 * nx + ny + b] = x;
-      }
+  auto emit = [&](int b, int r, double dv) {
+    const double x = Sg[b * nx + r] * dv;
+    if (fld) fld[a.cell_off[sub] + (int64_t)b * nx + r] = x;
+    if (b == 0) xb[r] = x;
+    if (r == nx - 1) xb[nx + b] = x;
+    if (b == ny - 1) xb[nx + ny + r] = x;
+    if (r == 0) xb[2 * nx + ny + b] = x;
+  };
+  for (int r = threadIdx.x; r < np; r += blockDim.x) {
+    const double dv = Z[(int64_t)(ny - 1) * np + r];
+    if (r < nx) emit(ny - 1, r, dv);
+    u[r] = (ny > 1 && r < nx) ? DLg[(ny - 1) * nx + r] * dv : 0.0;
+  }
+  __syncthreads();
+  for (int b = ny - 2; b >= 0; --b) {
+    block_partials(Gi + (int64_t)b * np * np, u, np, parts, part);
+    __syncthreads();
+    for (int r = threadIdx.x; r < np; r += blockDim.x) {
+      double dv = Z[(int64_t)b * np + r];
+      for (int q = 0; q < parts; ++q) dv += part[q * np + r];
+      if (r < nx) emit(b, r, dv);
+      u[r] = (b > 0 && r < nx) ? DLg[b * nx + r] * dv : 0.0;
     }
     __syncthreads();
   }
   if (a.recovery) {
     // normal velocities of every face (the Darcy flux field's layout: x-faces
-    // [ny][nx+1], then y-faces [ny+1][nx], oriented +x / +y); on a mortar side
-    // the outer value is the mortar pressure sum_j c_j <xi_j>_e, on an outer
-    // Dirichlet side its data, on a no-flow side the flux is zero
+    // [ny][nx+1], then y-faces [ny+1][nx], oriented +x / +y); outside a
+    // boundary face the value is the mortar pressure on an interface side,
+    // the data on an outer Dirichlet side; a no-flow face carries no flux
     const double* P = fld + a.cell_off[sub];   // the pressures just written
     double* F = fld + a.off_f + a.face_off[sub];
     const double ihx = 1.0 / S.hx, ihy = 1.0 / S.hy;
@@ -166,11 +184,8 @@ __global__ void __launch_bounds__(kDtnThreads) dtn_kernel(DtnArgs a) {
           val = t * (P[r * nx + ix - 1] - P[r * nx + ix]);
         } else {
           const int side = ix == 0 ? 3 : 1;
-          double gb = S.side_val[side];
-          if (S.side_type[side] == SIDE_IFACE) {
-            gb = 0.0;
-            for (int j = 0; j < R; ++j) gb = fma(a.proj[S.proj_off[side] + (int64_t)r * R + j], c[j], gb);
-          }
+          const double gb = S.side_type[side] == SIDE_IFACE ? gf[ix == 0 ? 2 * nx + ny + r : nx + r]
+                                                             : S.side_val[side];
           const double fo = t * (P[r * nx + (ix == 0 ? 0 : nx - 1)] - gb);
           val = S.side_type[side] == SIDE_NOFLOW ? 0.0 : (ix == 0 ? -fo : fo);
         }
@@ -181,11 +196,7 @@ __global__ void __launch_bounds__(kDtnThreads) dtn_kernel(DtnArgs a) {
           val = t * (P[(jr - 1) * nx + ix] - P[jr * nx + ix]);
         } else {
           const int side = jr == 0 ? 0 : 2;
-          double gb = S.side_val[side];
-          if (S.side_type[side] == SIDE_IFACE) {
-            gb = 0.0;
-            for (int j = 0; j < R; ++j) gb = fma(a.proj[S.proj_off[side] + (int64_t)ix * R + j], c[j], gb);
-          }
+          const double gb = S.side_type[side] == SIDE_IFACE ? gf[jr == 0 ? ix : nx + ny + ix] : S.side_val[side];
           const double fo = t * (P[(jr == 0 ? 0 : ny - 1) * nx + ix] - gb);
           val = S.side_type[side] == SIDE_NOFLOW ? 0.0 : (jr == 0 ? -fo : fo);
         }
@@ -199,16 +210,12 @@ __global__ void __launch_bounds__(kDtnThreads) dtn_kernel(DtnArgs a) {
   for (int ll = threadIdx.x; ll < R; ll += blockDim.x) {
     const int side = info[3 * ll], f0 = info[3 * ll + 1], f1 = info[3 * ll + 2];
     const double* Pj = a.proj + S.proj_off[side];
+    const int base = side == 0 ? 0 : side == 1 ? nx : side == 2 ? nx + ny : 2 * nx + ny;
     double acc = 0.0;
     for (int f = f0; f < f1; ++f) {
-      double t, xc;
-      if (side == 0) { t = g.Ty[f]; xc = xb[f]; }
-      else if (side == 1) { t = g.Tx[f * (nx + 1) + nx]; xc = xb[nx + f]; }
-      else if (side == 2) { t = g.Ty[ny * nx + f]; xc = xb[nx + ny + f]; }
-      else { t = g.Tx[f * (nx + 1)]; xc = xb[2 * nx + ny + f]; }
-      double pc = 0.0;
-      for (int j = 0; j < R; ++j) pc = fma(Pj[(int64_t)f * R + j], c[j], pc);
-      acc = fma(Pj[(int64_t)f * R + ll] * t, xc - pc, acc);
+      const double t = side == 0 ? g.Ty[f] : side == 1 ? g.Tx[f * (nx + 1) + nx]
+                     : side == 2 ? g.Ty[ny * nx + f] : g.Tx[f * (nx + 1)];
+      acc = fma(Pj[(int64_t)f * R + ll] * t, xb[base + f] - gf[base + f], acc);
     }
     a.Y[l * a.NY + a.ybase[sub] + ll] = -acc;
   }
@@ -236,9 +243,9 @@ __global__ void s1_moments_kernel(const double* __restrict__ field, int64_t cnt,
 }  // namespace
 
 size_t dtn_smem_bytes(int max_nx, int max_ny, int max_R) {
-  const int np = (max_nx + kPanel - 1) / kPanel * kPanel;
-  return sizeof(double) * ((size_t)max_ny * np + ((max_R + 1) & ~1) + 3 * (size_t)np + kDtnThreads +
-                           2 * (size_t)max_nx + 2 * (size_t)max_ny);
+  const size_t np = (max_nx + kPanel - 1) / kPanel * kPanel;
+  return sizeof(double) * ((size_t)max_ny * np + ((max_R + 1) & ~1) + np + std::max<size_t>(kDtnThreads, np) +
+                           4 * ((size_t)max_nx + max_ny));
 }
 
 // Product mode (recovery = 0): Y (Darcy units) of the iterating points among
