@@ -212,7 +212,11 @@ def run_ours(args):
     it_d = torch.empty(chunk, dtype=torch.int32, device="cuda")
     # CG tolerance per form: the mixed form's moments reach 1e-8 of the oracle
     # at 1e-10; the FP64 form's need 1e-12 to reach 1e-10 entry by entry
-    rtol_of = {sfb.MIXED: 1e-10, sfb.FP64: 1e-12}
+    # The Large workload's level-3 grid has weights whose magnitudes sum to
+    # about 11,490 (against a total of 1): per-point errors reach its moments
+    # multiplied by up to that much, and at 1e-10 the mixed form's moments were
+    # 1e-7 from the FP64 form's, so there both forms solve to 1e-12
+    rtol_of = {sfb.MIXED: 1e-12 if args.workload in GMRES_WORKLOADS else 1e-10, sfb.FP64: 1e-12}
     max_it = 3000
 
     def krylov(prec):

@@ -418,9 +418,15 @@ sfb_status sfb_build_basis_item_noalloc(sfb_ctx* ctx, int32_t sub, int32_t k, in
  *                    states it), 1 Jacobi (diag(S^l)), 2 interface blocks
  *                    (the diagonal block of S^l on each mortar interface's
  *                    DOFs, inverted per point, applied in FP32; interfaces of
- *                    more than 32 DOFs fall back to Jacobi). The same solution
- *                    and the same stopping test on the unpreconditioned
- *                    residual in every case (2);
+ *                    more than 32 DOFs fall back to Jacobi), 3 balancing
+ *                    Neumann-Neumann (Section 7's suggestion: stiffness-
+ *                    weighted Neumann steps on the pseudo-inverses of the
+ *                    bases, a coarse space of the floating Darcy subdomains'
+ *                    constants, CG from the balanced start; SFB_CG only,
+ *                    another solver with it returns SFB_ERR_ARG, more than 16
+ *                    floating subdomains SFB_ERR_UNSUPPORTED). The same
+ *                    solution and the same stopping test on the
+ *                    unpreconditioned residual in every case (2);
  *   "basis_autotune" 1: the next build of each precision first times every
  *                    launch shape of each size class (sfb_basis_launch_shape)
  *                    and keeps the fastest; setting it (0 or 1) forgets

@@ -85,7 +85,12 @@ def smolyak_grid(n_dim, lmax, rule):
 
     ``sum_{lmin <= |p| <= lmax} (-1)^(lmax-|p|) C(N-1, lmax-|p|) I^TG_{m(p)}``,
     ``lmin = max(0, lmax - N + 1)``. The abscissae are the union of the tensor
-    grids; equal abscissae are merged and their weights summed. Returns
+    grids; equal abscissae are merged and their weights summed. A merged
+    weight adds up terms of opposite signs whose running sums are far larger
+    than the result (at level 3 over 64 dimensions, the origin collects about
+    2e5 terms against a coefficient of C(63, 3) = 39,711), so each point's
+    terms are summed exactly rounded (``math.fsum``); the weights then sum to
+    one, as the combination formula integrates constants exactly. Returns
     ``(y[n_pts, N], w[n_pts])`` in lexicographic order of the coordinates.
     """
     lmin = max(0, lmax - n_dim + 1)
@@ -106,11 +111,12 @@ def smolyak_grid(n_dim, lmax, rule):
                     w *= r[1][i]
                 key = tuple(sorted((d, _key(v)) for d, v in coords.items()))
                 if key in acc:
-                    acc[key][1] += w
+                    acc[key][1].append(w)
                 else:
-                    acc[key] = [coords, w]
+                    acc[key] = [coords, [w]]
     items = []
-    for coords, w in acc.values():
+    for coords, terms in acc.values():
+        w = math.fsum(terms)
         y = np.zeros(n_dim)
         for d, v in coords.items():
             y[d] = v

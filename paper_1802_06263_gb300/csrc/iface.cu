@@ -180,6 +180,10 @@ struct IfaceArgs {
   const int* if_n;
   const int* if_moff;
   const int* dof_if;    // per global DOF: its interface
+  // balancing preconditioner: when set, the tile products scale their inputs
+  // and outputs by the unit's weights at its local DOFs ([n_pts][NY], the
+  // layout of Y), so that they form D_u Phi_u^+ D_u R_u v
+  const double* wy = nullptr;
   int* pstat;
   int64_t n_pts;
 };
@@ -423,7 +427,10 @@ __device__ __forceinline__ void tile_gather(const IfaceArgs& a, const double* __
   for (int e = threadIdx.x; e < nsel4 * R; e += blockDim.x) {
     const int q = e / R, i = e - q * R;
     double v = 0.0;
-    if (q < nsel) v = vin[ts.spt[q] * a.n_lambda + ts.sgd[i]];
+    if (q < nsel) {
+      v = vin[ts.spt[q] * a.n_lambda + ts.sgd[i]];
+      if (a.wy) v *= a.wy[ts.spt[q] * a.NY + a.ybase[u] + i];
+    }
     Pv[i * (kTG + 1) + q] = from_f64<T>(v);
   }
 }
@@ -454,8 +461,14 @@ __device__ __forceinline__ void tile_product(const IfaceArgs& a, int u, int R, i
     for (int q = 0; q < 4; ++q) {
       if (c0 + q >= nsel) break;
       double* y = a.Y + ts.spt[c0 + q] * a.NY + a.ybase[u];
-      y[r0] = to_f64(acc[0][q]);
-      if (two) y[r0 + 1] = to_f64(acc[1][q]);
+      if (a.wy) {
+        const double* wq = a.wy + ts.spt[c0 + q] * a.NY + a.ybase[u];
+        y[r0] = wq[r0] * to_f64(acc[0][q]);
+        if (two) y[r0 + 1] = wq[r0 + 1] * to_f64(acc[1][q]);
+      } else {
+        y[r0] = to_f64(acc[0][q]);
+        if (two) y[r0 + 1] = to_f64(acc[1][q]);
+      }
     }
   }
 }
@@ -2221,6 +2234,295 @@ __global__ void finalize_stokes(const double* U, int64_t n, int Cs, const double
   }
 }
 
+// ---- balancing Neumann-Neumann preconditioner ---------------------------------------------
+// Section 7 suggests a balancing preconditioner (Mandel's balancing domain
+// decomposition) to cut the interface CG's iterations. For S = sum_u R_u^T
+// Phi_u R_u over the units (Darcy subdomains, then Stokes):
+//  - weights D_u: at a mortar DOF shared by units u and v, u's share of the
+//    two local stiffnesses, (Phi_u)_dd / ((Phi_u)_dd + (Phi_v)_dd), per point
+//    (they depend on the point's items); sum_u R_u^T D_u R_u = I;
+//  - Neumann step N r = sum_u R_u^T D_u Phi_u^+ D_u R_u r (the tile products
+//    on the pseudo-inverses, weighted through IfaceArgs::wy);
+//  - coarse space Z = [R_u^T D_u 1] over the floating Darcy subdomains (no
+//    outer Dirichlet side), S_0 = Z^T S Z per point, Q = Z S_0^{-1} Z^T;
+//  - CG from the balanced start lambda_0 = Q g, so that every residual stays
+//    balanced (Z^T r = 0) and the preconditioned residual is
+//    z = (I - Q S) N r = w - Z S_0^{-1} (S Z)^T w with w = N r.
+// S Z is formed once per point by the tile products (n_c of them); each
+// iteration then costs the product S p, the Neumann step and n_c dot products.
+constexpr int kBddMaxCoarse = 16;
+
+struct BddArgs {
+  double* wy;          // [n_pts][NY] weights of each unit at its local DOFs
+  double* sz;          // [n_pts][n_c][n_lambda] S Z
+  double* L;           // [n_pts][n_c * n_c] Cholesky factor of S_0
+  const int* cidx;     // [units] the coarse vector of each unit, or -1
+  int n_c;
+};
+
+// Pseudo-inverse of one Darcy item's flux basis: Phi^{-1}, or for a floating
+// subdomain (null space the constants) (Phi + (a/R) 1 1^T)^{-1} - 1 1^T/(a R)
+// with a = trace(Phi)/R. Gauss-Jordan sweep of the SPD matrix in shared
+// memory (after all R pivots it holds -A^{-1}); a non-positive pivot sets bad.
+__global__ void __launch_bounds__(256) bdd_pinv_kernel(const SubDev* subs, const ItemOff* off, const int* item_sub,
+                                                        const int* item_k, int n_items, const double* phi,
+                                                        double* pinv, int* bad) {
+  extern __shared__ __align__(16) double bsm[];
+  const int item = blockIdx.x;
+  if (item >= n_items) return;
+  const SubDev& S = subs[item_sub[item]];
+  const int64_t po = off[S.item0 + item_k[item]].phi;
+  const int R = S.R;
+  bool floating = true;
+  for (int q = 0; q < 4; ++q) floating = floating && S.side_type[q] != SIDE_DIRICHLET;
+  double* A = bsm;            // [R][R]
+  double* col = A + R * R;    // pivot column
+  __shared__ double shift;
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) A[e] = phi[po + e];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < R; ++i) tr += A[i * R + i];
+    shift = floating ? tr / ((double)R * R) : 0.0;
+  }
+  __syncthreads();
+  if (floating)
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) A[e] += shift;
+  __syncthreads();
+  for (int k = 0; k < R; ++k) {
+    for (int i = threadIdx.x; i < R; i += blockDim.x) col[i] = A[i * R + k];
+    __syncthreads();
+    double d = col[k];
+    if (!(d > 0.0)) {
+      if (threadIdx.x == 0) atomicOr(bad, 1);
+      d = 1.0;
+    }
+    const double id = 1.0 / d;
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) {
+      const int i = e / R, j = e - i * R;
+      double v;
+      if (i == k && j == k) v = -id;
+      else if (i == k) v = col[j] * id;
+      else if (j == k) v = col[i] * id;
+      else v = A[e] - col[i] * col[j] * id;
+      A[e] = v;
+    }
+    __syncthreads();
+  }
+  // A = -(Phi + shift 1 1^T)^{-1}; with shift = a/R, the constant term of the
+  // pseudo-inverse is 1/(a R) = 1/(shift R^2)
+  const double c = floating ? 1.0 / (shift * (double)R * R) : 0.0;
+  for (int e = threadIdx.x; e < R * R; e += blockDim.x) pinv[po + e] = -A[e] - c;
+}
+
+// wy: each unit's share of the local stiffness at each of its DOFs.
+__global__ void bdd_weights_kernel(IfaceArgs a, BddArgs b) {
+  const int64_t tot = a.n_pts * a.n_lambda;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = e / a.n_lambda;
+    const int d = (int)(e - l * a.n_lambda);
+    if (a.pstat[l] & 0x40000000) continue;
+    double dg[2];
+    for (int side = 0; side < 2; ++side) {
+      const int u = a.ldof[4 * d + 2 * side], loc = a.ldof[4 * d + 2 * side + 1];
+      const int k = u < a.ns ? a.kmap[l * a.ns + u] : 0;
+      int R;
+      const double* ph = unit_phi(a, u, k, R);
+      dg[side] = ph[(int64_t)loc * R + loc];
+    }
+    const double tot2 = dg[0] + dg[1];
+    for (int side = 0; side < 2; ++side)
+      b.wy[l * a.NY + a.yoff[2 * d + side]] = tot2 > 0.0 ? dg[side] / tot2 : 0.5;
+  }
+}
+
+// Entry d of coarse vector j at point l: the weight at d of the unit whose
+// coarse vector is j, or 0.
+__device__ __forceinline__ double coarse_entry(const IfaceArgs& a, const BddArgs& b, int64_t l, int d, int j) {
+  double v = 0.0;
+  for (int side = 0; side < 2; ++side)
+    if (b.cidx[a.ldof[4 * d + 2 * side]] == j) v = b.wy[l * a.NY + a.yoff[2 * d + side]];
+  return v;
+}
+
+// (Z t)_d: the coarse combination at DOF d (at most its two units contribute).
+__device__ __forceinline__ double coarse_comb(const IfaceArgs& a, const BddArgs& b, int64_t l, int d,
+                                              const double* t) {
+  double v = 0.0;
+  for (int side = 0; side < 2; ++side) {
+    const int j = b.cidx[a.ldof[4 * d + 2 * side]];
+    if (j >= 0) v = fma(t[j], b.wy[l * a.NY + a.yoff[2 * d + side]], v);
+  }
+  return v;
+}
+
+// vout = coarse vector j of every point
+__global__ void bdd_coarse_vec_kernel(IfaceArgs a, BddArgs b, int j, double* vout) {
+  const int64_t tot = a.n_pts * a.n_lambda;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = e / a.n_lambda;
+    const int d = (int)(e - l * a.n_lambda);
+    vout[e] = (a.pstat[l] & 0x40000000) ? 0.0 : coarse_entry(a, b, l, d, j);
+  }
+}
+
+// column j of S Z: the gathered tile products
+__global__ void bdd_gather_kernel(IfaceArgs a, BddArgs b, int j) {
+  const int64_t tot = a.n_pts * a.n_lambda;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = e / a.n_lambda;
+    const int d = (int)(e - l * a.n_lambda);
+    const double* Yl = a.Y + l * a.NY;
+    b.sz[(l * b.n_c + j) * a.n_lambda + d] = Yl[a.yoff[2 * d]] + Yl[a.yoff[2 * d + 1]];
+  }
+}
+
+// y = S_0^{-1} t in place with the Cholesky factor L (row-major, lower), one lane.
+__device__ __forceinline__ void chol_solve(const double* L, int n, double* y) {
+  for (int i = 0; i < n; ++i) {
+    double v = y[i];
+    for (int k = 0; k < i; ++k) v -= L[i * n + k] * y[k];
+    y[i] = v / L[i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double v = y[i];
+    for (int k = i + 1; k < n; ++k) v -= L[k * n + i] * y[k];
+    y[i] = v / L[i * n + i];
+  }
+}
+
+// One warp per point: S_0 = Z^T (S Z), its Cholesky factor, then the balanced
+// start lambda_0 = Z S_0^{-1} Z^T g and r_0 = g - (S Z) S_0^{-1} Z^T g (r holds
+// g on entry). A non-positive pivot of S_0 fails the point.
+__global__ void bdd_setup_kernel(IfaceArgs a, BddArgs b) {
+  __shared__ double s0[8][kBddMaxCoarse * kBddMaxCoarse];
+  __shared__ double tv[8][kBddMaxCoarse];
+  const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  if (l >= a.n_pts) return;
+  if (a.pstat[l] != 0) return;
+  const int nc = b.n_c, n = (int)a.n_lambda;
+  const double* sz = b.sz + l * nc * a.n_lambda;
+  double* rl = a.r + l * a.n_lambda;
+  double* ll = a.lam + l * a.n_lambda;
+  for (int ab = 0; ab < nc * nc + nc; ++ab) {
+    const int ia = ab < nc * nc ? ab / nc : ab - nc * nc, ib = ab < nc * nc ? ab % nc : -1;
+    double acc = 0.0;
+    for (int d = lane; d < n; d += 32) {
+      const double ca = coarse_entry(a, b, l, d, ia);
+      if (ca != 0.0) acc = fma(ca, ib >= 0 ? sz[ib * a.n_lambda + d] : rl[d], acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      if (ib >= 0) s0[wl][ab] = acc;
+      else tv[wl][ia] = acc;
+    }
+  }
+  __syncwarp();
+  int ok = 1;
+  if (lane == 0) {
+    double* S0 = s0[wl];
+    for (int i = 0; i < nc; ++i)   // symmetrize (rounding) and factor in place
+      for (int j = 0; j < i; ++j) S0[i * nc + j] = S0[j * nc + i] = 0.5 * (S0[i * nc + j] + S0[j * nc + i]);
+    for (int j = 0; j < nc && ok; ++j) {
+      double dj = S0[j * nc + j];
+      for (int k = 0; k < j; ++k) dj -= S0[j * nc + k] * S0[j * nc + k];
+      if (!(dj > 0.0)) { ok = 0; break; }
+      const double ljj = sqrt(dj);
+      S0[j * nc + j] = ljj;
+      for (int i = j + 1; i < nc; ++i) {
+        double v = S0[i * nc + j];
+        for (int k = 0; k < j; ++k) v -= S0[i * nc + k] * S0[j * nc + k];
+        S0[i * nc + j] = v / ljj;
+      }
+    }
+    if (ok) {
+      for (int e = 0; e < nc * nc; ++e) b.L[l * nc * nc + e] = S0[e];
+      chol_solve(S0, nc, tv[wl]);
+    } else {
+      a.pstat[l] = -1;
+    }
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __syncwarp();
+  if (!ok) return;
+  for (int d = lane; d < n; d += 32) {
+    double sv = 0.0;
+    for (int j = 0; j < nc; ++j) sv = fma(tv[wl][j], sz[j * a.n_lambda + d], sv);
+    ll[d] = coarse_comb(a, b, l, d, tv[wl]);
+    rl[d] -= sv;
+  }
+}
+
+// One warp per iterating point: q = S p from the tile products, alpha =
+// (r.z)/(p.q), lambda += alpha p, r -= alpha q, and the stopping test
+// ||r|| <= rtol ||g|| (the point's status becomes its iteration count, negative
+// after a breakdown p.q <= 0).
+__global__ void bdd_update1_kernel(IfaceArgs a, int it, double rtol) {
+  const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (l >= a.n_pts || a.pstat[l] != 0) return;
+  const double* Yl = a.Y + l * a.NY;
+  const double* pl = a.p + l * a.n_lambda;
+  double* rl = a.r + l * a.n_lambda;
+  double* ll = a.lam + l * a.n_lambda;
+  const int n = (int)a.n_lambda;
+  double pq = 0.0;
+  for (int d = lane; d < n; d += 32) pq = fma(pl[d], Yl[a.yoff[2 * d]] + Yl[a.yoff[2 * d + 1]], pq);
+  pq = warp_sum(pq);
+  const bool brk = !(pq > 0.0);
+  const double alpha = brk ? 0.0 : a.rr[l] / pq;
+  double rn = 0.0;
+  for (int d = lane; d < n; d += 32) {
+    const double q = Yl[a.yoff[2 * d]] + Yl[a.yoff[2 * d + 1]];
+    ll[d] = fma(alpha, pl[d], ll[d]);
+    const double rv = fma(-alpha, q, rl[d]);
+    rl[d] = rv;
+    rn = fma(rv, rv, rn);
+  }
+  rn = warp_sum(rn);
+  if (lane == 0 && (brk || sqrt(rn) <= rtol * a.gn[l])) a.pstat[l] = brk ? -(it + 1) : it + 1;
+}
+
+// One warp per iterating point: w = N r from the weighted tile products on the
+// pseudo-inverses, z = w - Z S_0^{-1} (S Z)^T w, then p = z (first) or
+// p = z + (r.z / rr) p, rr = r.z (z is formed twice: for r.z, then for p).
+__global__ void bdd_update2_kernel(IfaceArgs a, BddArgs b, int first) {
+  __shared__ double tv[8][kBddMaxCoarse];
+  const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  if (l >= a.n_pts || a.pstat[l] != 0) return;
+  const double* Yl = a.Y + l * a.NY;
+  const int nc = b.n_c, n = (int)a.n_lambda;
+  const double* sz = b.sz + l * nc * a.n_lambda;
+  double* pl = a.p + l * a.n_lambda;
+  const double* rl = a.r + l * a.n_lambda;
+  for (int j = 0; j < nc; ++j) {
+    double acc = 0.0;
+    for (int d = lane; d < n; d += 32)
+      acc = fma(sz[j * a.n_lambda + d], Yl[a.yoff[2 * d]] + Yl[a.yoff[2 * d + 1]], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) tv[wl][j] = acc;
+  }
+  __syncwarp();
+  if (lane == 0 && nc > 0) chol_solve(b.L + l * nc * nc, nc, tv[wl]);
+  __syncwarp();
+  double rz = 0.0;
+  for (int d = lane; d < n; d += 32) {
+    const double z = Yl[a.yoff[2 * d]] + Yl[a.yoff[2 * d + 1]] - coarse_comb(a, b, l, d, tv[wl]);
+    rz = fma(rl[d], z, rz);
+  }
+  rz = warp_sum(rz);
+  double beta = 0.0;
+  if (!first && lane == 0) beta = a.rr[l] > 0.0 ? rz / a.rr[l] : 0.0;
+  beta = __shfl_sync(0xffffffffu, beta, 0);
+  for (int d = lane; d < n; d += 32) {
+    const double z = Yl[a.yoff[2 * d]] + Yl[a.yoff[2 * d + 1]] - coarse_comb(a, b, l, d, tv[wl]);
+    pl[d] = first ? z : fma(beta, pl[d], z);
+  }
+  if (lane == 0) a.rr[l] = rz;
+}
+
 }  // namespace
 
 // ---- host orchestration -----------------------------------------------------------------
@@ -2265,6 +2567,58 @@ static IfaceArgs make_args(sfb_ctx* c, int64_t n_pts) {
   return a;
 }
 
+// Moore-Penrose pseudo-inverse of a symmetric n x n matrix (row-major) on the
+// host: cyclic Jacobi rotations to diagonal form (Golub and Van Loan, Section
+// 8.5), then V diag(1/e) V^T over the eigenvalues e above rcut max|e|.
+static void sym_pinv_host(const std::vector<double>& A0, int n, double rcut, std::vector<double>& out) {
+  std::vector<double> A(A0), V((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+  double fro = 0.0;
+  for (double v : A) fro += v * v;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j)
+        if (i != j) off += A[(size_t)i * n + j] * A[(size_t)i * n + j];
+    if (off <= 1e-30 * fro) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[(size_t)p * n + q];
+        if (apq == 0.0) continue;
+        const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+        const double theta = (aqq - app) / (2.0 * apq);
+        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double cs = 1.0 / std::sqrt(t * t + 1.0), sn = t * cs;
+        for (int k = 0; k < n; ++k) {   // A <- A J (columns p, q)
+          const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+          A[(size_t)k * n + p] = cs * akp - sn * akq;
+          A[(size_t)k * n + q] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < n; ++k) {   // A <- J^T A (rows p, q)
+          const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+          A[(size_t)p * n + k] = cs * apk - sn * aqk;
+          A[(size_t)q * n + k] = sn * apk + cs * aqk;
+        }
+        for (int k = 0; k < n; ++k) {   // V <- V J
+          const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+          V[(size_t)k * n + p] = cs * vkp - sn * vkq;
+          V[(size_t)k * n + q] = sn * vkp + cs * vkq;
+        }
+      }
+  }
+  double emax = 0.0;
+  for (int i = 0; i < n; ++i) emax = std::max(emax, std::fabs(A[(size_t)i * n + i]));
+  out.assign((size_t)n * n, 0.0);
+  for (int k = 0; k < n; ++k) {
+    const double e = A[(size_t)k * n + k];
+    if (!(std::fabs(e) > rcut * emax)) continue;
+    for (int i = 0; i < n; ++i) {
+      const double vi = V[(size_t)i * n + k] / e;
+      for (int j = 0; j < n; ++j) out[(size_t)i * n + j] += vi * V[(size_t)j * n + k];
+    }
+  }
+}
+
 __global__ void count_failed(const int* pstat, int64_t n, int* out) {
   int c = 0;
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += (int64_t)gridDim.x * blockDim.x)
@@ -2301,6 +2655,33 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   const bool dtn = krylov == SFB_CG_DTN;
   if (dtn) { a.dinv = nullptr; a.minv = nullptr; }
   c->last_dtn = dtn;
+  // balancing preconditioner (FP64 CG): the pseudo-inverses of the bases,
+  // once per build (Darcy items) and per Stokes basis
+  const bool bdd = krylov == SFB_CG && c->opt_cg_precond == 3;
+  if (bdd) {
+    if (!c->bdd_items_ready && c->n_items > 0) {
+      int maxR = 1;
+      for (const HostSub& S : c->subs) maxR = std::max(maxR, (int)S.dofs.size());
+      const size_t smp = sizeof(double) * ((size_t)maxR * maxR + maxR);
+      CK(cudaFuncSetAttribute(bdd_pinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp));
+      CK(cudaMemsetAsync(d.active + 9, 0, sizeof(int), st));
+      bdd_pinv_kernel<<<(unsigned)c->n_items, 256, smp, st>>>(d.subs, d.off, d.item_sub, d.item_k, (int)c->n_items,
+                                                             d.phi, d.bdd_pinv, d.active + 9);
+      ++c->launches;
+      CK(cudaGetLastError());
+      c->bdd_items_ready = true;
+    }
+    if (!c->bdd_stokes_ready) {
+      const int Rs = (int)c->stokes.dofs.size();
+      std::vector<double> ph((size_t)Rs * Rs), pi;
+      CK(cudaMemcpyAsync(ph.data(), d.s_phi, sizeof(double) * ph.size(), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      sym_pinv_host(ph, Rs, 1e-10, pi);
+      CK(cudaMemcpyAsync(d.bdd_spinv, pi.data(), sizeof(double) * pi.size(), cudaMemcpyHostToDevice, st));
+      CK(cudaStreamSynchronize(st));
+      c->bdd_stokes_ready = true;
+    }
+  }
   CK(cudaEventRecord(c->ev[1], st));
   const int warps_per_block = 8;
   const int ublocks = (int)((n_pts + warps_per_block - 1) / warps_per_block);
@@ -2339,6 +2720,28 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   CK(cudaFuncSetAttribute(matvec_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv));
   CK(cudaFuncSetAttribute(matvec_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv32));
   dim3 mgrid(c->max_tiles, nu);
+  // balancing preconditioner: weights, S Z (one round of tile products per
+  // coarse vector), S_0 and the balanced start, then z_0 = (I - Q S) N r_0
+  BddArgs bdda;
+  bdda.wy = d.bdd_wy; bdda.sz = d.bdd_sz; bdda.L = d.bdd_L; bdda.cidx = d.bdd_cidx; bdda.n_c = c->bdd_nc;
+  IfaceArgs ai = a;   // the Neumann step: tile products on the pseudo-inverses, weighted
+  ai.phi = d.bdd_pinv; ai.s_phi = d.bdd_spinv; ai.wy = d.bdd_wy;
+  if (bdd) {
+    const int eb = (int)std::min<int64_t>((n_pts * c->n_lambda + 255) / 256, 8192);
+    bdd_weights_kernel<<<eb, 256, 0, st>>>(a, bdda);
+    ++c->launches;
+    for (int j = 0; j < bdda.n_c; ++j) {
+      bdd_coarse_vec_kernel<<<eb, 256, 0, st>>>(a, bdda, j, d.p);
+      matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.p, 0, d.active + 2, 0);
+      bdd_gather_kernel<<<eb, 256, 0, st>>>(a, bdda, j);
+      c->launches += 3;
+    }
+    bdd_setup_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, bdda);
+    matvec_kernel<double><<<mgrid, 256, smv, st>>>(ai, d.r, 0, d.active + 2, 0);
+    bdd_update2_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, bdda, 1);
+    c->launches += 3;
+    CK(cudaGetLastError());
+  }
   const int chunk = c->opt_cg_chunk;
   const bool mixed = krylov == SFB_CG_MIXED;
   const double replace_ratio = c->opt_cg_replace, pause_ratio = 0.1 * c->opt_cg_replace;
@@ -2347,7 +2750,7 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   // its shared memory fits (for the mixed CG: when its FP32 tiles can stay
   // resident); otherwise one launch per step below
   bool persistent = false;
-  if (c->opt_cg_persistent && nu <= kPcgUnits && !gmres && !dtn) {
+  if (c->opt_cg_persistent && nu <= kPcgUnits && !gmres && !dtn && !bdd) {
     int dev = 0, coop = 0, n_sm = 0, smem_max = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
@@ -2495,7 +2898,25 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
     CK(cudaStreamSynchronize(st));
     if (h_active == 0) break;
   }
-  for (; it < max_it && !persistent && !gmres;) {
+  // balanced CG: product, update, Neumann step, preconditioned direction
+  for (; bdd && it < max_it;) {
+    for (int q = 0; q < chunk && it < max_it; ++q, ++it) {
+      matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.p, 0, d.active + 2, 0);
+      bdd_update1_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, it, rtol);
+      matvec_kernel<double><<<mgrid, 256, smv, st>>>(ai, d.r, 0, d.active + 2, 0);
+      bdd_update2_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, bdda, 0);
+      c->launches += 4;
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(d.active, 0, sizeof(int), st));
+    count_active<<<std::min(1024, (int)((n_pts + 255) / 256)), 256, 0, st>>>(d.pstat, n_pts, d.active);
+    ++c->launches;
+    int h_active = 0;
+    CK(cudaMemcpyAsync(&h_active, d.active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h_active == 0) break;
+  }
+  for (; it < max_it && !persistent && !gmres && !bdd;) {
     for (int q = 0; q < chunk && it < max_it; ++q, ++it) {
       if (dtn) {
         // Darcy units by one subdomain solve per (point, subdomain); the Stokes unit by its basis
@@ -2552,6 +2973,10 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   if (h_flags[2]) {
     c->err = "interface solve: a bulk copy of a basis did not complete within the wait limit";
     return SFB_ERR_TIMEOUT;
+  }
+  if (bdd && h_flags[9]) {
+    c->err = "interface solve: a non-positive pivot inverting a flux basis for the balancing preconditioner";
+    return SFB_ERR_NOT_SPD;
   }
   if (persistent && h_flags[6]) {
     c->err = "interface solve: a grid barrier of the persistent CG did not complete within the wait limit";

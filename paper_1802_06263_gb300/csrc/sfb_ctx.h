@@ -121,6 +121,12 @@ struct Dev {
   double* dinv = nullptr;
   double* gmV = nullptr;      // GMRES Krylov basis [kGmresMax + 1][n_pts][n_lambda]
   double* gmS = nullptr;      // GMRES per-point state [n_pts][kGmresState]
+  double* bdd_pinv = nullptr;  // balancing preconditioner: pseudo-inverses of the Darcy bases (phi offsets)
+  double* bdd_spinv = nullptr; // ... and of the Stokes basis
+  double* bdd_wy = nullptr;    // per point, in Y's layout: each unit's stiffness share at its DOFs
+  double* bdd_sz = nullptr;    // per point: S Z [n_c][n_lambda]
+  double* bdd_L = nullptr;     // per point: Cholesky factor of S_0 = Z^T S Z
+  int* bdd_cidx = nullptr;     // per unit: its coarse vector or -1
   int* gmJ = nullptr;         // GMRES steps of the current cycle per point     // Jacobi preconditioner of the interface CG, per point
   float* minv = nullptr;      // interface block-Jacobi inverses, per point [minv_ld]
   int* if_off = nullptr;      // per interface: first global DOF, DOF count, offset of its block
@@ -249,7 +255,12 @@ struct sfb_ctx {
   std::vector<int> pcg_starts;   // host copy of the last resident partition
   int pcg_mode = 0;   // last persistent CG: bit 0 resident tiles, bit 1 two streaming buffers
   double pcg_cycles[6] = {0, 0, 0, 0, 0, 0};   // per CTA, last persistent CG
-  bool last_dtn = false;   // the last batch was solved by Method S1 (its moments recover by subdomain solves)
+  bool last_dtn = false;
+  // balancing preconditioner: coarse vectors (floating Darcy subdomains),
+  // each unit's coarse index, and whether the pseudo-inverses are current
+  int bdd_nc = 0;
+  std::vector<int> bdd_cidx;
+  bool bdd_items_ready = false, bdd_stokes_ready = false;   // the last batch was solved by Method S1 (its moments recover by subdomain solves)
   ~sfb_ctx() {
     for (cudaEvent_t e : ev)
       if (e) cudaEventDestroy(e);

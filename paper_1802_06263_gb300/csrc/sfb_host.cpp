@@ -272,6 +272,24 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   d.gmV = cv.take<double>((size_t)(kGmresMax + 1) * P * c->n_lambda);
   d.gmS = cv.take<double>((size_t)P * kGmresState);
   d.gmJ = cv.take<int>(P);
+  // balancing preconditioner: pseudo-inverses of the bases (the basis store's
+  // offsets), per-point weights, S Z and the coarse Cholesky factors
+  c->bdd_nc = 0;
+  {
+    std::vector<int> cidx(nu, -1);
+    for (int s = 0; s < ns; ++s) {
+      bool floating = true;
+      for (int q = 0; q < 4; ++q) floating = floating && c->subs[s].side_type[q] != SIDE_DIRICHLET;
+      if (floating) cidx[s] = c->bdd_nc++;
+    }
+    c->bdd_cidx = cidx;
+  }
+  d.bdd_pinv = cv.take<double>(nPhi);
+  d.bdd_spinv = cv.take<double>((size_t)Rs * Rs + 2);
+  d.bdd_wy = cv.take<double>((size_t)P * c->NY);
+  d.bdd_sz = cv.take<double>((size_t)P * std::max(c->bdd_nc, 1) * c->n_lambda);
+  d.bdd_L = cv.take<double>((size_t)P * std::max(c->bdd_nc * c->bdd_nc, 1));
+  d.bdd_cidx = cv.take<int>(nu);
   c->minv_ld = 0; c->max_if_dof = 0;
   for (const HostIface& f : c->ifaces) { c->minv_ld += (int64_t)f.n_dof * f.n_dof; c->max_if_dof = std::max(c->max_if_dof, f.n_dof); }
   d.minv = cv.take<float>((size_t)P * std::max<int64_t>(c->minv_ld, 1));
@@ -795,7 +813,7 @@ sfb_status upload_tables(sfb_ctx* c) {
   UP(d.s_gdof, c->stokes.dofs); UP(d.ybase, c->ybase); UP(d.dim_off, dim_off); UP(d.loc_off, loc_off);
   UP(d.cell_off, cell_off); UP(d.face_off, face_off); UP(d.ldof, ldof); UP(d.yoff, yoff);
   UP(d.if_off, if_off); UP(d.if_n, if_n); UP(d.if_moff, if_moff); UP(d.dof_if, dof_if); UP(d.hash, htab); UP(d.hash_off, hoff);
-  UP(d.hash_cap, hcap);
+  UP(d.hash_cap, hcap); UP(d.bdd_cidx, c->bdd_cidx);
 #undef UP
   SFB_CUDA(cudaStreamSynchronize(st), "upload");
   return SFB_OK;
@@ -950,6 +968,7 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
     SFB_CUDA(cudaStreamSynchronize(st), "Stokes basis");
     if (sst) return fail(c, SFB_ERR_NOT_SPD, "zero pivot in the Stokes factorization");
     c->basis_prec = 99;  // tables and Stokes basis present
+    c->bdd_stokes_ready = false;
   }
   const int n = (int)c->n_items;
   BasisArgs a;
@@ -1140,6 +1159,7 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   }
   c->basis_done = true;
   c->basis_prec = factor_only ? SFB_FACTOR_FP64 : prec;
+  c->bdd_items_ready = false;   // the balancing preconditioner's pseudo-inverses follow the bases
   if (any & ST_NONFINITE) return fail(c, SFB_ERR_NONFINITE, "non-finite permeability or solution");
   if (any & ST_NOT_SPD) return fail(c, SFB_ERR_NOT_SPD, "non-positive pivot in a block factorization");
   if (any & ST_TIMEOUT) return fail(c, SFB_ERR_TIMEOUT, "a bulk copy did not complete within the wait limit");
@@ -1199,6 +1219,10 @@ sfb_status sfb_interface_solve_batch(sfb_ctx* c, const double* y, const double* 
     return fail(c, SFB_ERR_STATE, "SFB_CG_DTN needs the FP64 block factors (an SFB_FP64 or SFB_FACTOR_FP64 build)");
   if (krylov != SFB_CG_DTN && c->basis_prec == SFB_FACTOR_FP64)
     return fail(c, SFB_ERR_STATE, "the factor-only build forms no flux basis: only SFB_CG_DTN solves from it");
+  if (c->opt_cg_precond == 3 && krylov != SFB_CG && krylov != SFB_CG_DTN)
+    return fail(c, SFB_ERR_ARG, "the balancing preconditioner (cg_precond 3) runs with SFB_CG");
+  if (c->opt_cg_precond == 3 && krylov == SFB_CG && c->bdd_nc > 16)
+    return fail(c, SFB_ERR_UNSUPPORTED, "the balancing preconditioner takes at most 16 floating subdomains");
   if (krylov == SFB_CG_DTN) {
     int mnx = 1, mny = 1, mR = 1;
     for (const HostSub& H : c->subs) {
@@ -1293,7 +1317,7 @@ sfb_status sfb_set_option(sfb_ctx* c, const char* name, double value) {
     if (!(value >= 1 && value <= 1000)) return fail(c, SFB_ERR_ARG, "cg_check_every must lie in [1, 1000]");
     c->opt_cg_chunk = (int)value;
   } else if (n == "cg_precond") {
-    if (!(value == 0 || value == 1 || value == 2)) return fail(c, SFB_ERR_ARG, "cg_precond must be 0, 1 or 2");
+    if (!(value == 0 || value == 1 || value == 2 || value == 3)) return fail(c, SFB_ERR_ARG, "cg_precond must be 0, 1, 2 or 3");
     c->opt_cg_precond = (int)value;
   } else if (n == "moments_double_float") {
     if (!(value == 0 || value == 1)) return fail(c, SFB_ERR_ARG, "moments_double_float must be 0 or 1");

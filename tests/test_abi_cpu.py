@@ -87,6 +87,25 @@ def test_host_setup_matches_oracle(name):
     assert s.field_size("stokes_p") == p.stokes.n_p
 
 
+def test_host_level_three_grid_matches_oracle():
+    """The host's level-3 {1,3,3,3} grid over 40 dimensions (4 KL regions of
+    10 terms): the oracle's points and weights, weights summing to one (each
+    point's terms carry a compensation term)."""
+    sfb = _lib()
+    from oracle import collocation
+    w = W.small_test(nx=6, ny=4, px=2, py=2, n_sd=2, n_dd=2, n_term=10, degree=1, stokes=(4, 4),
+                     collocation={"kind": "smolyak", "lmax": 3, "rule": [1, 3, 3, 3]})
+    s = sfb.Solver(w)
+    y, wt = s.points()
+    yo, wo = collocation.global_grid(w["collocation"], 40)
+    assert y.shape == yo.shape == (82241, 40)
+    # rounding of the terms themselves (coefficients up to 9,139 times products
+    # of the 1-D weights) leaves about 2e-12; a plain running sum left 1.3e-9
+    assert abs(wt.sum() - 1.0) < 1e-11
+    ref = {tuple(np.round(r, 10)): v for r, v in zip(yo, wo)}
+    assert max(abs(ref[tuple(np.round(r, 10))] - v) for r, v in zip(y, wt)) < 1e-11
+
+
 def test_bad_arguments_are_rejected():
     sfb = _lib()
     w = W.tiny()
@@ -189,7 +208,7 @@ def test_calls_out_of_order_return_status_codes():
     assert lib.sfb_moments(h, 0, mean.ctypes.data, mean.ctypes.data) == 2          # before any solve
     assert lib.sfb_set_option(h, b"no_such_option", 1.0) == 1
     assert lib.sfb_set_option(h, b"refine_tol", 2.0) == 1
-    assert lib.sfb_set_option(h, b"cg_precond", 3.0) == 1
+    assert lib.sfb_set_option(h, b"cg_precond", 4.0) == 1
     n = ctypes.c_int64()
     assert lib.sfb_field_size(h, 9, ctypes.byref(n)) == 1
     nb = ctypes.c_size_t()

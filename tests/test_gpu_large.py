@@ -12,7 +12,9 @@ sub-batch at strided entries of every field and the full fields' norms, the
 mortar solutions of 32 of its points, the Stokes basis and the flux bases of
 four items. The GPU solves the same sub-batch after building every basis
 item: FP64 form (FP64 GMRES to rtol 1e-12) within 1e-10, mixed form (GMRES
-with FP32 Arnoldi products and FP64 restarts, to rtol 1e-10) within 1e-8."""
+with FP32 Arnoldi products and FP64 restarts, to rtol 1e-12 as the benchmark
+runs it: the grid's weights amplify per-point errors in the moments) within
+1e-8."""
 
 import functools
 import os
@@ -27,7 +29,7 @@ pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_large.npz")
 FIELDS = ("darcy_p", "darcy_flux", "stokes_u", "stokes_p")
-RTOL = {0: 1e-12, 1: 1e-10}
+RTOL = {0: 1e-12, 1: 1e-12}
 
 
 @functools.lru_cache(maxsize=None)

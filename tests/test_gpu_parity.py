@@ -374,3 +374,55 @@ def test_method_s1_state_checks():
     s.build_basis(sfb.FP64)
     lam, it, rc = s.solve_host(y, wt, rtol=1e-12, krylov=sfb.CG_DTN)
     assert rc == 0 and np.all(it > 0)
+
+
+@pytest.mark.parametrize("case", ["tiny", "medium", "ragged", "kl_regions"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_balancing_preconditioner(case, prec):
+    """The balancing Neumann-Neumann preconditioner (cg_precond = 3, FP64 CG)
+    that Section 7 suggests: the oracle's mortar solutions and moments within
+    the form's tolerance, the oracle's balanced-CG iteration counts within two
+    on sampled points, and fewer iterations than the interface block-Jacobi
+    preconditioner on every point. After a mixed build the operator and the
+    pseudo-inverses come from the FP64 bases refined from FP32 factors."""
+    import paper_1802_06263_gb300 as sfb
+    from oracle import balancing
+    p, y, wt, lams, mom = oracle_case(case)
+    s = sfb.Solver(make_workload(case))
+    s.allocate(sfb.FP64)
+    s.build_basis(prec)
+    s.set_option("cg_precond", 2)
+    _, it2, rc2 = s.solve_host(y, wt, rtol=1e-13, max_it=5000, krylov=sfb.CG)
+    assert rc2 == 0
+    s.set_option("cg_precond", 3)
+    s.moments_reset()
+    lam, it, rc = s.solve_host(y, wt, rtol=1e-13, max_it=5000, krylov=sfb.CG)
+    assert rc == 0 and np.all(it > 0)
+    tol = TOL[prec]
+    for l in range(len(y)):
+        assert_close(lam[l], lams[l], tol, ("lambda", l))
+    for f in ("darcy_p", "darcy_flux", "stokes_u", "stokes_p"):
+        m, v = s.moments(f)
+        assert_close(m, mom[f][0], tol, (f, "mean"))
+        assert_close(v, mom[f][1], tol, (f, "variance"))
+    assert np.all(it <= it2), (it, it2)
+    if prec == 0:
+        for l in sorted({0, len(y) // 2, len(y) - 1}):
+            _, ito = balancing.solve_point(p, y[l], rtol=1e-13, max_it=500)
+            assert abs(int(it[l]) - ito) <= 2, (l, it[l], ito)
+
+
+def test_balancing_preconditioner_solver_checks():
+    """cg_precond = 3 runs with SFB_CG: the mixed CG and GMRES refuse it
+    (SFB_ERR_ARG); Method S1 ignores it (its CG is unpreconditioned)."""
+    import paper_1802_06263_gb300 as sfb
+    s = sfb.Solver(make_workload("tiny"))
+    y, wt = s.points()
+    s.allocate(sfb.FP64)
+    s.build_basis(sfb.FP64)
+    s.set_option("cg_precond", 3)
+    for kr in (sfb.CG_MIXED, sfb.GMRES, sfb.GMRES_MIXED):
+        _, _, rc = s.solve_host(y, wt, krylov=kr, check=False)
+        assert rc == 1
+    _, it, rc = s.solve_host(y, wt, rtol=1e-12, krylov=sfb.CG_DTN)
+    assert rc == 0 and np.all(it > 0)

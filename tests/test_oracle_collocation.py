@@ -71,6 +71,22 @@ def test_smolyak_exactness():
     assert abs(np.sum(w * y[:, 0] ** 2 * y[:, 3] ** 2) - 1.0) < 1e-12
 
 
+def test_level_three_weights_sum_to_one():
+    """The combination formula integrates constants exactly, so the weights
+    of the level-3 {1,3,3,3} grid over 40 dimensions (82,241 points, the
+    origin's weight a sum of about 1.2e4 terms of both signs) sum to one, and
+    its moments of degree 2 and 4 are the Gaussian ones, to the rounding of
+    the terms themselves (coefficients up to 9,139 times products of 1/6 and
+    2/3: about 4e-13). A plain running sum per point misses the total by
+    1.3e-9 here."""
+    y, w = collocation.smolyak_grid(40, 3, [1, 3, 3, 3])
+    assert len(w) == 82241
+    assert abs(w.sum() - 1.0) < 1e-12
+    assert abs(np.sum(w * y[:, 0] ** 2) - 1.0) < 1e-12
+    assert abs(np.sum(w * y[:, 7] ** 2 * y[:, 31] ** 2) - 1.0) < 1e-12
+    assert abs(np.sum(w * y[:, 5] ** 4) - 3.0) < 1e-12
+
+
 def test_linear_kl_moments_exact_under_quadrature():
     """Y is linear in y, so E[Y] = mean and Var[Y] = sum lambda f^2 hold
     exactly for any rule of degree >= 2."""
