@@ -396,7 +396,10 @@ def test_balancing_preconditioner(case, prec):
     assert rc2 == 0
     s.set_option("cg_precond", 3)
     s.moments_reset()
-    lam, it, rc = s.solve_host(y, wt, rtol=1e-13, max_it=5000, krylov=sfb.CG)
+    # after a mixed build the bases are symmetric, and a floating item's null
+    # space the constants, only to the refinement's 1e-11: the balanced CG
+    # then stalls above 1e-13 on some points, and its tolerance is 1e-11
+    lam, it, rc = s.solve_host(y, wt, rtol=1e-13 if prec == 0 else 1e-11, max_it=5000, krylov=sfb.CG)
     assert rc == 0 and np.all(it > 0)
     tol = TOL[prec]
     for l in range(len(y)):
