@@ -419,9 +419,9 @@ def basis_launch(sfb, prec, st):
         v = st["launch_shape"][q]
         if v < 0:
             continue
-        t, c, g, tc = sfb.basis_launch_shape(prec, q == 0, v)
+        t, c, g, tc, sp = sfb.basis_launch_shape(prec, q == 0, v)
         out[cls] = {"shape": v, "threads": t, "ctas_per_sm": c, "g_buffers": g, "tcgen05": bool(tc),
-                    "autotune_ms": [m for m in st["tune_ms"][q] if m > 0]}
+                    "split": bool(sp), "autotune_ms": [m for m in st["tune_ms"][q] if m > 0]}
     return out
 
 

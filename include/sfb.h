@@ -312,20 +312,29 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* ctx, int32_t prec, sfb_basis_stat
 /* Launch shapes of the basis kernel (no counterpart in the paper: how the
  * items of Section 5.4 Steps 1-2 map onto the GPU). The items fall into two
  * size classes, grids more than 64 cells wide (wide = 1) and the rest; each
- * class is one launch, the two run concurrently. prec selects the factor
- * precision (SFB_FP64: one shape per class; SFB_MIXED, SFB_FP32_NOREFINE: two).
- * Writes the shape's threads per CTA, the CTAs per SM its register budget is
- * compiled for, its number of shared-memory G_b buffers (2: the next block
- * row's inverse is prefetched) and whether it runs the block-row products on
- * the tensor cores (tcgen05 = 1: SFB_MIXED / SFB_FP32_NOREFINE shape 2, grids
- * up to 64 cells wide; tcgen05.mma kind::tf32 with every operand split into
- * two TF32 parts and FP32 accumulation, the block inverses fed by TMA tensor
- * copies). Pointers are host memory and nullable. SFB_ERR_ARG for a shape that
- * the precision and class do not have. By default the first build of each
- * precision times every shape of each class on that class's own items and
- * keeps the fastest (option "basis_autotune"). */
+ * class is one launch (a pipeline of launches for a split shape), the two
+ * classes run concurrently. prec selects the factor precision (SFB_FP64: one
+ * narrow and two wide shapes; SFB_MIXED, SFB_FP32_NOREFINE: four narrow and
+ * three wide). Writes the shape's threads per CTA, the CTAs per SM its
+ * register budget is compiled for, its number of shared-memory G_b buffers
+ * (2: the next block row's inverse is prefetched), whether it runs the
+ * block-row products on the tensor cores (tcgen05 = 1: SFB_MIXED /
+ * SFB_FP32_NOREFINE narrow shape 2; tcgen05.mma kind::tf32 with every operand
+ * split into two TF32 parts and FP32 accumulation, the block inverses fed by
+ * TMA tensor copies), and whether it is split (split = 1: narrow shape 3 and
+ * wide shape 2 of the FP32 factor). A split shape factors every item in one
+ * launch of 256-thread CTAs and solves and refines every chunk of at most 24
+ * of an item's right-hand sides in a CTA of its own, in a second launch; the
+ * items go in two groups, and the second group's factor launch runs while
+ * the first group's solves run on another stream.
+ * The other outputs describe the solve launch. Pointers are host memory and
+ * nullable. SFB_ERR_ARG for a shape that the precision and class do not
+ * have. By default the first build of each precision times every shape of
+ * each class on that class's own items and keeps the fastest (option
+ * "basis_autotune"). */
 sfb_status sfb_basis_launch_shape(int32_t prec, int32_t wide, int32_t shape, int32_t* threads,
-                                  int32_t* ctas_per_sm, int32_t* g_buffers, int32_t* tcgen05);
+                                  int32_t* ctas_per_sm, int32_t* g_buffers, int32_t* tcgen05,
+                                  int32_t* split);
 
 /* Read-back of one stored basis item (host or device buffers): phi [R x R]
  * row-major, g [R], x [(R+1) x n_cells] (pressure responses, column j is the

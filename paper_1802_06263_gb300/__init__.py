@@ -99,7 +99,7 @@ _SIGS = {
     "sfb_cg_phase_cycles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "sfb_launch_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "sfb_basis_launch_shape": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p,
-                                              _i32p]),
+                                              _i32p, _i32p]),
     "sfb_build_basis_item_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
@@ -127,16 +127,18 @@ def load():
 
 
 def basis_launch_shape(prec, wide, shape):
-    """(threads per CTA, CTAs per SM, G buffers, tcgen05) of a basis-kernel
-    launch shape (tcgen05 = 1: the tensor-core form), or None when the
-    precision has no such shape for that size class."""
+    """(threads per CTA, CTAs per SM, G buffers, tcgen05, split) of a
+    basis-kernel launch shape (tcgen05 = 1: the tensor-core form; split = 1:
+    factor launches, then launches over column chunks, which the other values
+    describe), or None when the precision has no such shape for that size
+    class."""
     lib = load()
-    t, c, g, tc = (ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32())
+    t, c, g, tc, sp = (ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32())
     rc = lib.sfb_basis_launch_shape(prec, int(bool(wide)), shape, ctypes.byref(t), ctypes.byref(c), ctypes.byref(g),
-                                    ctypes.byref(tc))
+                                    ctypes.byref(tc), ctypes.byref(sp))
     if rc != SFB_OK:
         return None
-    return t.value, c.value, g.value, tc.value
+    return t.value, c.value, g.value, tc.value, sp.value
 
 
 class SfbError(RuntimeError):

@@ -146,24 +146,44 @@ __device__ __forceinline__ void blocked_sweep_w0(T (&areg)[MT][4][4], int np, in
   }
 }
 
-template <typename T, int MT, int NT, int MINB, int GB>
+// MODE 0: one CTA per item does everything; MODE 1: one CTA per item does
+// phases 1-2 only (KL, assembly, factor: G_b, S, D_{b-1}, T and diag(A) to
+// global memory); MODE 2: one CTA per column chunk of an item runs phases 3-4
+// for its columns on the stored factor, the first solve as a forward sweep on
+// x = 0. Splitting an item's solves over several CTAs shortens the longest
+// dependent chain per CTA and gives the scheduler several times more, smaller
+// work units than there are items.
+template <typename T, int MT, int NT, int MINB, int GB, int MODE = 0>
 __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   __shared__ int bad_spd;
   __shared__ __align__(8) uint64_t gbar[2];
   __shared__ __align__(8) uint64_t zbar;
-  const int item = blockIdx.x;
-  if (item >= a.n_items) return;
+  int item, c0 = 0, ccount = 0;
+  if constexpr (MODE == 2) {
+    if ((int)blockIdx.x >= a.n_chunks) return;
+    item = a.chunk_item[blockIdx.x];
+    c0 = a.chunk_c0[blockIdx.x];
+    ccount = a.chunk_cnt[blockIdx.x];
+  } else {
+    item = blockIdx.x;
+    if (item >= a.n_items) return;
+  }
   const int s = a.item_sub[item], kk = a.item_k[item];
   const SubDev S = a.subs[s];
   const int id = (int)S.item0 + kk;
+  // statistics slot: the item, or (MODE 2) the chunk after all items
+  const int wid = MODE == 2 ? a.n_items_all + a.chunk_slot0 + (int)blockIdx.x : id;
   const ItemOff off = a.off[id];
   Geo g;
   // all R + 1 right-hand sides, or (Method S1's set-up) only the particular
-  // one, column R of the right-hand side and of X
-  const int coff = a.particular_only ? S.R : 0;
-  g.nx = S.nx; g.ny = S.ny; g.R = S.R; g.C = a.particular_only ? 1 : S.R + 1; g.Cp = (g.C + 3) & ~3;
+  // one, column R of the right-hand side and of X, or (MODE 2) the chunk's
+  // columns; none in MODE 1
+  const int coff = MODE == 2 ? c0 : (a.particular_only ? S.R : 0);
+  g.nx = S.nx; g.ny = S.ny; g.R = S.R;
+  g.C = MODE == 2 ? ccount : MODE == 1 ? 0 : (a.particular_only ? 1 : S.R + 1);
+  g.Cp = (g.C + 3) & ~3;
   g.nc = S.nx * S.ny;
   const int nx = g.nx, ny = g.ny, nc = g.nc, C = g.C, Cp = g.Cp;
   constexpr int kP = panel_of<T>();
@@ -179,12 +199,14 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
   T* Sg = reinterpret_cast<T*>(a.S) + off.sc;
   T* DLg = reinterpret_cast<T*>(a.DL) + off.sc;  // [ny][nx] scaled couplings to the row below
   T* Gg = reinterpret_cast<T*>(a.G) + off.g;   // [ny][np][np]
-  T* Zg = reinterpret_cast<T*>(a.Z) + off.z;   // [ny][np][Cp], the shared-memory image of a row block
+  // [ny][np][Cp], the shared-memory image of a row block; a chunk's own block
+  // starts after the earlier chunks' (their column counts are multiples of 4)
+  T* Zg = reinterpret_cast<T*>(a.Z) + off.z + (MODE == 2 ? (int64_t)ny * np * c0 : 0);
 
   // smem: Gs[GB][np*np] | U region | Zs[np*Cp] | sc | dlo | dup | txh, the U region
   // holding Us[np*Cp] in the solves and VT[kP*np] | W[kP*np] | Ablk[kP*kP]
   // during the block inversions (never both at once)
-  const int ureg = max(np * Cp, 2 * kP * np + kP * kP);
+  const int ureg = MODE == 2 ? np * Cp : max(np * Cp, 2 * kP * np + kP * kP);
   T* Gs0 = reinterpret_cast<T*>(smem_raw);
   T* Us = Gs0 + GB * np * np;
   T* VT = Us;
@@ -206,7 +228,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
   }
   int st = 0;
   long long t_mark = clock64(), t_fwd = 0, t_bwd = 0;
-  long long* cyc = a.cycles + kCycSlots * (int64_t)id;
+  long long* cyc = a.cycles + kCycSlots * (int64_t)wid;
   // thread 0's clock between barriers: sub-phases of the factor, forward and
   // backward row steps (slots 4-15 of the per-item cycle record)
   long long sub[12] = {}, t_sub = t_mark;
@@ -223,7 +245,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
   __syncthreads();
 
   // ---- 1. permeability, transmissibilities, diagonal and scaling ------------
-  {
+  if constexpr (MODE != 2) {
     const int nt = S.n_term;
     const double* slam = a.kl + S.kl_off;
     const double* fx = slam + nt;
@@ -283,7 +305,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
   // ---- 2. factorization, fused with the first forward solve ------------------
   // G_b and z_b leave through bulk stores from shared memory.
   T areg[MT][4][4];
-  for (int b = 0; b < ny; ++b) {
+  for (int b = 0; b < (MODE == 2 ? 0 : ny); ++b) {
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
       const double si = (double)Sg[b * nx + i];
       sc[i] = T(si);
@@ -312,21 +334,24 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
         for (int q = 0; q < 4; ++q) Gs[(i0 + a2) * np + j0 + q] = -areg[m][a2][q];
     }
     // first forward solve row: u_b = s_b B_b + dlo_b z_{b-1}
-    for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
-      const int i = e % nx, c = e / nx;
-      T u = sc[i] * from_f64<T>(rhs_entry(S, g, a.proj, b, i, c + coff));
-      if (b > 0) u = fma(dlo[i], Zs[i * Cp + c], u);
-      Us[i * Cp + c] = u;
-    }
+    if constexpr (MODE == 0)
+      for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
+        const int i = e % nx, c = e / nx;
+        T u = sc[i] * from_f64<T>(rhs_entry(S, g, a.proj, b, i, c + coff));
+        if (b > 0) u = fma(dlo[i], Zs[i * Cp + c], u);
+        Us[i * Cp + c] = u;
+      }
     fence_async_shared();
     __syncthreads();
     SFB_MARK(2);
     if (GB > 0 && threadIdx.x == 0) bulk_store(Gg + (int64_t)b * np * np, Gs, gbytes);
-    gemm_g<T>(Gs, Us, Zs, false, np, Cp, C);
-    fence_async_shared();
-    __syncthreads();
-    SFB_MARK(3);
-    if (threadIdx.x == 0) bulk_store(Zg + (int64_t)b * np * Cp, Zs, zbytes);
+    if constexpr (MODE == 0) {
+      gemm_g<T>(Gs, Us, Zs, false, np, Cp, C);
+      fence_async_shared();
+      __syncthreads();
+      SFB_MARK(3);
+      if (threadIdx.x == 0) bulk_store(Zg + (int64_t)b * np * Cp, Zs, zbytes);
+    }
   }
   if (threadIdx.x == 0) {
     bulk_wait_all();
@@ -334,6 +359,17 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
   }
   __syncthreads();
   if (threadIdx.x == 0) { const long long t = clock64(); cyc[1] = t - t_mark; t_mark = t; t_sub = t; }
+  if constexpr (MODE == 1) {
+    // the factor alone: its status, and the sub-phase clocks of its rows
+    if (threadIdx.x == 0) {
+      cyc[2] = 0;
+      cyc[3] = 0;
+      for (int q = 0; q < 12; ++q) cyc[4 + q] = sub[q];
+    }
+    if (bad_spd) st |= ST_NOT_SPD;
+    if (st) atomicOr(&a.status[id], st);
+    return;
+  }
 
   // ---- 3./4. backward sweep, then refine with FP64 residuals --------------------------
   double xref2 = 0.0, prev_corr = 0.0, est = 1.0, bnorm2 = 0.0;
@@ -341,13 +377,17 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
   bool timeout = false;
   for (int it = 0; it <= refine && !timeout; ++it) {
     float rr = 0.f;
-    if (it > 0) {
+    // x = 0 before a chunk's first forward sweep (MODE 2): r = B
+    const bool xzero = MODE == 2 && it == 0;
+    if (it > 0 || MODE == 2) {
       // forward sweep: r_b = B_b - (A x)_b in FP64; u_b = s_b r_b + dlo_b z_{b-1}
       if (GB > 0 && threadIdx.x == 0) { fence_async_shared(); bulk_load(Gs0, Gg, gbytes, &gbar[0]); }
       // row scalings of the next row travel in registers while a row runs
       T nsc = threadIdx.x < nx ? Sg[threadIdx.x] : T(0), ndl = threadIdx.x < nx ? DLg[threadIdx.x] : T(0);
-      prefetch_x_row(X, nc, nx, 0, C);
-      if (ny > 1) prefetch_x_row(X, nc, nx, 1, C);
+      if (!xzero) {
+        prefetch_x_row(X, nc, nx, 0, C);
+        if (ny > 1) prefetch_x_row(X, nc, nx, 1, C);
+      }
       for (int b = 0; b < ny; ++b) {
         const int cur = GB == 2 ? (b & 1) : 0;
         T* Gs = GB == 0 ? Gg + (int64_t)b * np * np : Gs0 + cur * np * np;
@@ -356,7 +396,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
           dlo[threadIdx.x] = ndl;
           if (b + 1 < ny) { nsc = Sg[(b + 1) * nx + threadIdx.x]; ndl = DLg[(b + 1) * nx + threadIdx.x]; }
         }
-        if (b + 2 < ny) prefetch_x_row(X, nc, nx, b + 2, C);   // the residual of row b + 1 reads it
+        if (b + 2 < ny && !xzero) prefetch_x_row(X, nc, nx, b + 2, C);   // the residual of row b + 1 reads it
         __syncthreads();
         SFB_MARK(4);
         if (GB == 2 && threadIdx.x == 0 && b + 1 < ny) {
@@ -369,11 +409,14 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
           const int64_t cell = (int64_t)b * nx + i;
           const double* xc = X + (int64_t)c * nc;
           // r = B - A x as five FP64 FMAs: B - D x, then + T x over the neighbours
-          double r = fma(-Dg[cell], xc[cell], rhs_entry(S, g, a.proj, b, i, c + coff));
-          if (i > 0) r = fma(Tx[b * (nx + 1) + i], xc[cell - 1], r);
-          if (i < nx - 1) r = fma(Tx[b * (nx + 1) + i + 1], xc[cell + 1], r);
-          if (b > 0) r = fma(Ty[b * nx + i], xc[cell - nx], r);
-          if (b < ny - 1) r = fma(Ty[(b + 1) * nx + i], xc[cell + nx], r);
+          double r = rhs_entry(S, g, a.proj, b, i, c + coff);
+          if (!xzero) {
+            r = fma(-Dg[cell], xc[cell], r);
+            if (i > 0) r = fma(Tx[b * (nx + 1) + i], xc[cell - 1], r);
+            if (i < nx - 1) r = fma(Tx[b * (nx + 1) + i + 1], xc[cell + 1], r);
+            if (b > 0) r = fma(Ty[b * nx + i], xc[cell - nx], r);
+            if (b < ny - 1) r = fma(Ty[(b + 1) * nx + i], xc[cell + nx], r);
+          }
           const T rt = from_f64<T>(r);
           const float rf = to_f32(rt);
           rr = fmaf(rf, rf, rr);
@@ -406,7 +449,8 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
       __syncthreads();
       if (timeout) break;
       const double rnorm2 = block_sum((double)rr, red);
-      if (threadIdx.x == 0) a.resid[id] = sqrt(rnorm2 / fmax(bnorm2, 1e-300));
+      if (xzero) bnorm2 = rnorm2;   // |B|^2 for the relative residual
+      else if (threadIdx.x == 0) a.resid[wid] = sqrt(rnorm2 / fmax(bnorm2, 1e-300));
       if (threadIdx.x == 0) { const long long t = clock64(); t_fwd += t - t_mark; t_mark = t; t_sub = t; }
     } else {
       // |B|^2 for the relative residual
@@ -501,7 +545,7 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
       const double corr = sqrt(dn2 / fmax(xref2, 1e-300));  // ||d_it|| / ||x||
       const double rho = corr / fmax(prev_corr, 1e-300);
       est = rho < 1.0 ? rho / (1.0 - rho) * corr : 1.0;
-      if (threadIdx.x == 0 && it == 1) a.corr1[id] = corr;
+      if (threadIdx.x == 0 && it == 1) a.corr1[wid] = corr;
       prev_corr = corr;
       n_done = it;
       if (est <= a.refine_tol) break;
@@ -529,8 +573,8 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
     cyc[2] = t_fwd;
     cyc[3] = t_bwd;
     for (int q = 0; q < 12; ++q) cyc[4 + q] = sub[q];
-    a.nref[id] = n_done;
-    a.errest[id] = refine > 0 ? est : 0.0;
+    a.nref[wid] = n_done;
+    a.errest[wid] = refine > 0 ? est : 0.0;
   }
   // non-finite check on the result
   for (int e = threadIdx.x; e < nc * C; e += blockDim.x)
@@ -589,20 +633,37 @@ __global__ void flux_epilogue_kernel(BasisArgs a) {
 // against 18.0 ms, the lost prefetch and 64 registers included). The
 // autotuner times both FP32 shapes of each size class (kShape below).
 template <typename T>
-size_t basis_smem(int max_nx, int max_cols, int gb) {
-  const size_t cp = (max_cols + 3) & ~3;
+size_t basis_smem(int max_nx, int max_cols, int gb, int mode = 0) {
+  // mode 1 (factor alone) holds no right-hand sides; mode 2 (a chunk's
+  // solves) at most kChunkCols of them and no inversion scratch
+  const size_t cp = mode == 1 ? 0 : mode == 2 ? (size_t)((std::min(max_cols, kChunkCols) + 3) & ~3)
+                                               : (size_t)((max_cols + 3) & ~3);
   constexpr size_t kP = panel_of<T>();
   const size_t np = (max_nx + kPanel - 1) & ~size_t(kPanel - 1);
-  return sizeof(T) * (gb * np * np + std::max(np * cp, 2 * kP * np + kP * kP) + np * cp + 4 * np);
+  const size_t ureg = mode == 2 ? np * cp : std::max(np * cp, 2 * kP * np + kP * kP);
+  return sizeof(T) * (gb * np * np + ureg + np * cp + 4 * np);
 }
 
-template <typename T, int MT, int NT, int MINB, int GB>
+template <typename T, int MT, int NT, int MINB, int GB, int MODE = 0>
 cudaError_t launch_one(const BasisArgs& a, size_t smem, int refine, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(basis_kernel<T, MT, NT, MINB, GB>,
+  cudaError_t e = cudaFuncSetAttribute(basis_kernel<T, MT, NT, MINB, GB, MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  basis_kernel<T, MT, NT, MINB, GB><<<a.n_items, NT, smem, st>>>(a, refine);
+  const int grid = MODE == 2 ? a.n_chunks : a.n_items;
+  if (grid == 0) return cudaSuccess;
+  basis_kernel<T, MT, NT, MINB, GB, MODE><<<grid, NT, smem, st>>>(a, refine);
   return cudaGetLastError();
+}
+
+// A split shape: the factor of every item (part 1), then the solves of every
+// chunk (part 2); part 0 runs both on one stream.
+template <typename T, int MT1, int NT1, int MINB1, int GB1, int MT2, int NT2, int MINB2, int GB2>
+cudaError_t launch_split(const BasisArgs& a, int max_nx, int max_cols, int refine, cudaStream_t st, int part) {
+  cudaError_t e = cudaSuccess;
+  if (part != 2)
+    e = launch_one<T, MT1, NT1, MINB1, GB1, 1>(a, basis_smem<T>(max_nx, max_cols, GB1, 1), refine, st);
+  if (e != cudaSuccess || part == 1) return e;
+  return launch_one<T, MT2, NT2, MINB2, GB2, 2>(a, basis_smem<T>(max_nx, max_cols, GB2, 2), refine, st);
 }
 
 // Thread-block shape: the register tiles of the sweep are 4 x 4; np <= 64
@@ -627,28 +688,33 @@ cudaError_t launch_basis(const BasisArgs& a, int max_nx, int max_cols, int refin
 // narrow grids only, is the tensor-core kernel of basis_tc.cu. FP64 has one
 // shape per class (its shared memory already limits residency). Entries with
 // zero threads do not exist.
-constexpr int kShapes = 3;
+// The split shapes (split = 1) run a factor launch (256 threads, MODE 1) and
+// a solve launch over the column chunks (MODE 2); the table gives the solve
+// launch's threads, CTAs per SM and G buffers.
+constexpr int kShapes = 4;
 constexpr BasisShape kShape[2][2][kShapes] = {
     // FP32: narrow, wide
-    {{{256, 4, 1, 0}, {256, 3, 2, 0}, {256, 3, 1, 1}}, {{256, 1, 2, 0}, {256, 2, 1, 0}, {0, 0, 0, 0}}},
+    {{{256, 4, 1, 0, 0}, {256, 3, 2, 0, 0}, {256, 3, 1, 1, 0}, {128, 8, 1, 0, 1}},
+     {{256, 1, 2, 0, 0}, {256, 2, 1, 0, 0}, {128, 2, 1, 0, 1}, {0, 0, 0, 0, 0}}},
     // FP64: narrow, wide (the second wide shape keeps G_b in global memory,
     // for blocks too large for shared memory beside the right-hand sides)
-    {{{256, 2, 1, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}}, {{512, 1, 1, 0}, {512, 1, 0, 0}, {0, 0, 0, 0}}},
+    {{{256, 2, 1, 0, 0}, {0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}},
+     {{512, 1, 1, 0, 0}, {512, 1, 0, 0, 0}, {0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}}},
 };
 
-template <typename T, int MT, int NT, int MINB, int GB>
+template <typename T, int MT, int NT, int MINB, int GB, int MODE = 0>
 cudaError_t occupancy_of(size_t smem, int* ctas) {
-  cudaError_t e = cudaFuncSetAttribute(basis_kernel<T, MT, NT, MINB, GB>,
+  cudaError_t e = cudaFuncSetAttribute(basis_kernel<T, MT, NT, MINB, GB, MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, basis_kernel<T, MT, NT, MINB, GB>, NT, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, basis_kernel<T, MT, NT, MINB, GB, MODE>, NT, smem);
 }
 
 // Launches (ctas == nullptr) or sizes (ctas != nullptr: resident CTAs per SM)
 // one shape. The template arguments match kShape.
 template <typename T>
 cudaError_t shape_dispatch(const BasisArgs* a, bool wide, int shape, int max_nx, int max_cols, int refine,
-                           cudaStream_t st, int* ctas) {
+                           cudaStream_t st, int* ctas, int part = 0) {
   if constexpr (sizeof(T) == 4) {
     if (!wide && shape == 0) {
       const size_t sm = basis_smem<T>(max_nx, max_cols, 1);
@@ -668,6 +734,12 @@ cudaError_t shape_dispatch(const BasisArgs* a, bool wide, int shape, int max_nx,
     }
     if (!wide && shape == 2)
       return ctas ? basis_tc_ctas(max_nx, max_cols, ctas) : launch_basis_tc(*a, max_nx, max_cols, refine, st);
+    if (!wide && shape == 3)
+      return ctas ? occupancy_of<T, 1, 128, 8, 1, 2>(basis_smem<T>(max_nx, max_cols, 1, 2), ctas)
+                  : launch_split<T, 1, 256, 4, 1, 1, 128, 8, 1>(*a, max_nx, max_cols, refine, st, part);
+    if (wide && shape == 2)
+      return ctas ? occupancy_of<T, 1, 128, 2, 1, 2>(basis_smem<T>(max_nx, max_cols, 1, 2), ctas)
+                  : launch_split<T, 4, 256, 2, 1, 1, 128, 2, 1>(*a, max_nx, max_cols, refine, st, part);
   } else {
     const size_t sm = basis_smem<T>(max_nx, max_cols, 1);
     if (!wide && shape == 0)
@@ -685,6 +757,11 @@ cudaError_t shape_dispatch(const BasisArgs* a, bool wide, int shape, int max_nx,
 }  // namespace
 
 int basis_shape_count(int fp64) { return fp64 ? 2 : kShapes; }
+
+bool basis_shape_split(int fp64, int wide, int shape) {
+  BasisShape d;
+  return basis_shape_desc(fp64, wide, shape, &d) && d.split;
+}
 
 bool basis_shape_desc(int fp64, int wide, int shape, BasisShape* out) {
   if (shape < 0 || shape >= basis_shape_count(fp64)) return false;
@@ -710,6 +787,12 @@ cudaError_t launch_basis_shape(const BasisArgs& a, int fp64, int wide, int shape
   if ((wide != 0) != (max_nx > 64)) return cudaErrorInvalidValue;
   return fp64 ? shape_dispatch<double>(&a, wide, shape, max_nx, max_cols, 0, st, nullptr)
               : shape_dispatch<float>(&a, wide, shape, max_nx, max_cols, refine, st, nullptr);
+}
+
+cudaError_t launch_basis_part(const BasisArgs& a, int wide, int shape, int part, int max_nx, int max_cols, int refine,
+                              cudaStream_t st) {
+  if (!basis_shape_split(0, wide, shape) || (wide != 0) != (max_nx > 64)) return cudaErrorInvalidValue;
+  return shape_dispatch<float>(&a, wide, shape, max_nx, max_cols, refine, st, nullptr, part);
 }
 
 cudaError_t launch_basis_fp64(const BasisArgs& a, int max_nx, int max_cols, cudaStream_t st) {

@@ -77,6 +77,9 @@ struct Dev {
   double* resid = nullptr;
   double* corr1 = nullptr;
   int* nref = nullptr;
+  int* chunk_item = nullptr;  // split launch shapes: per column chunk its class-local item,
+  int* chunk_c0 = nullptr;    // first column and column count (wide class first)
+  int* chunk_cnt = nullptr;
   // Stokes
   double* s_mat = nullptr;
   double* s_pl = nullptr;    // the band LU's panel multipliers in final row order
@@ -190,6 +193,10 @@ struct sfb_ctx {
   int64_t ws_pts = 0;
   sfb::Dev dev;
   int64_t n_items = 0;
+  int64_t n_chunks = 0;                 // column chunks of all items (split launch shapes)
+  int64_t chunk_start[2] = {0, 0}, chunk_n[2] = {0, 0};   // per size class (wide, narrow)
+  std::vector<int> h_chunk_item;        // host copy of the chunks' class-local items
+  std::vector<int64_t> item_id;         // item id of each item in build order
   int max_nx = 0, max_cols = 0, max_R = 0;
   // basis items come in decreasing cost; the first n_wide have nx > 64 and run
   // with the wide-grid kernel variant, the rest with the narrow one
@@ -197,6 +204,12 @@ struct sfb_ctx {
   int wide_nx = 0, wide_cols = 0, narrow_nx = 0, narrow_cols = 0;
   cudaStream_t side = nullptr;          // second stream for the narrow items
   cudaEvent_t fork = nullptr, join = nullptr;
+  // split launch shapes: per size class two streams for the solve launches of
+  // alternate item groups, and the events that order each group's solves
+  // after its factor (see sfb_build_stochastic_basis)
+  static constexpr int kPipeGroups = 2;
+  cudaStream_t pipe_stream[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  cudaEvent_t pipe_ev[2][kPipeGroups + 3] = {};
   cudaStream_t gcap = nullptr;          // private stream on which the basis graph is captured
   std::vector<sfb::ItemOff> offs;
   std::vector<int64_t> ybase;              // per unit (Darcy subs, then Stokes) offset into Y
@@ -269,6 +282,12 @@ struct sfb_ctx {
     if (fork) cudaEventDestroy(fork);
     if (join) cudaEventDestroy(join);
     if (side) cudaStreamDestroy(side);
+    for (auto& q : pipe_stream)
+      for (cudaStream_t x : q)
+        if (x) cudaStreamDestroy(x);
+    for (auto& q : pipe_ev)
+      for (cudaEvent_t x : q)
+        if (x) cudaEventDestroy(x);
     if (gcap) cudaStreamDestroy(gcap);
   }
 };

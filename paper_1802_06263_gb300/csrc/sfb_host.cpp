@@ -150,7 +150,7 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   const size_t gsz = prec == SFB_FP64 ? sizeof(double) : sizeof(float);
   int64_t n_items = 0, nX = 0, nZ = 0, nT = 0, nG = 0, nPhi = 0, nD = 0, nproj = 0, ninfo = 0, nkl = 0, nyl = 0,
           ngd = 0;
-  int64_t n_loc_tot = 0;
+  int64_t n_loc_tot = 0, n_chunks = 0;
   c->offs.clear();
   for (int s = 0; s < ns; ++s) {
     const HostSub& S = c->subs[s];
@@ -173,6 +173,7 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
     }
     n_items += nl;
     n_loc_tot += nl;
+    n_chunks += (int64_t)nl * chunk_count(C);
     for (int q = 0; q < 4; ++q) nproj += (int64_t)S.proj[q].size();
     ninfo += 3 * R;
     nkl += S.n_term * (1 + S.nx + S.ny);
@@ -180,6 +181,7 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
     ngd += R;
   }
   c->n_items = n_items;
+  c->n_chunks = n_chunks;
   d.subs = cv.take<SubDev>(ns);
   d.proj = cv.take<double>(nproj);
   d.dofinfo = cv.take<int>(ninfo);
@@ -199,12 +201,16 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   d.D = cv.take<double>(nD);
   d.S = cv.take<char>(nD * gsz);
   d.DL = cv.take<char>(nD * gsz);
+  // per item, then per column chunk of a split launch shape
   d.status = cv.take<int>(n_items);
-  d.resid = cv.take<double>(n_items);
-  d.corr1 = cv.take<double>(n_items);
-  d.errest = cv.take<double>(n_items);
-  d.cycles = cv.take<long long>(kCycSlots * n_items);
-  d.nref = cv.take<int>(n_items);
+  d.resid = cv.take<double>(n_items + n_chunks);
+  d.corr1 = cv.take<double>(n_items + n_chunks);
+  d.errest = cv.take<double>(n_items + n_chunks);
+  d.cycles = cv.take<long long>(kCycSlots * (n_items + n_chunks));
+  d.nref = cv.take<int>(n_items + n_chunks);
+  d.chunk_item = cv.take<int>(std::max<int64_t>(n_chunks, 1));
+  d.chunk_c0 = cv.take<int>(std::max<int64_t>(n_chunks, 1));
+  d.chunk_cnt = cv.take<int>(std::max<int64_t>(n_chunks, 1));
   // Stokes
   const StokesHost& St = c->stokes;
   const int Rs = (int)St.dofs.size(), Cs = Rs + 1;
@@ -770,6 +776,25 @@ sfb_status upload_tables(sfb_ctx* c) {
   }
   for (int64_t i = c->n_wide; i < c->n_items; ++i)
     if (sd[item_sub[i]].nx > 64) return fail(c, SFB_ERR_ARG, "basis items out of size-class order");
+  // column chunks of the split launch shapes, class by class in item order
+  std::vector<int> ch_item, ch_c0, ch_cnt;
+  for (int q = 0; q < 2; ++q) {
+    const int64_t i0 = q == 0 ? 0 : c->n_wide, i1 = q == 0 ? c->n_wide : c->n_items;
+    c->chunk_start[q] = (int64_t)ch_item.size();
+    for (int64_t i = i0; i < i1; ++i) {
+      const int C = sd[item_sub[i]].R + 1, nch = chunk_count(C), base = chunk_base(C);
+      for (int k = 0; k < nch; ++k) {
+        ch_item.push_back((int)(i - i0));
+        ch_c0.push_back(k * base);
+        ch_cnt.push_back(k + 1 < nch ? base : C - base * (nch - 1));
+      }
+    }
+    c->chunk_n[q] = (int64_t)ch_item.size() - c->chunk_start[q];
+  }
+  if ((int64_t)ch_item.size() != c->n_chunks) return fail(c, SFB_ERR_ARG, "column chunk count mismatch");
+  c->h_chunk_item = ch_item;
+  c->item_id.resize(c->n_items);
+  for (int64_t i = 0; i < c->n_items; ++i) c->item_id[i] = sd[item_sub[i]].item0 + item_k[i];
   // interface-solve maps
   std::vector<int> ldof(4 * c->n_lambda, 0);
   std::vector<int> fill(c->n_lambda, 0);
@@ -810,6 +835,7 @@ sfb_status upload_tables(sfb_ctx* c) {
 #define UP(dst, vec) SFB_CUDA(cudaMemcpyAsync(dst, (vec).data(), sizeof((vec)[0]) * (vec).size(), cudaMemcpyHostToDevice, st), "upload")
   UP(d.subs, sd); UP(d.proj, proj); UP(d.dofinfo, info); UP(d.kl, kl); UP(d.yloc, yloc); UP(d.gdof, gdof);
   UP(d.item_sub, item_sub); UP(d.item_k, item_k); UP(d.off, c->offs);
+  if (!ch_item.empty()) { UP(d.chunk_item, ch_item); UP(d.chunk_c0, ch_c0); UP(d.chunk_cnt, ch_cnt); }
   UP(d.s_gdof, c->stokes.dofs); UP(d.ybase, c->ybase); UP(d.dim_off, dim_off); UP(d.loc_off, loc_off);
   UP(d.cell_off, cell_off); UP(d.face_off, face_off); UP(d.ldof, ldof); UP(d.yoff, yoff);
   UP(d.if_off, if_off); UP(d.if_n, if_n); UP(d.if_moff, if_moff); UP(d.dof_if, dof_if); UP(d.hash, htab); UP(d.hash_off, hoff);
@@ -838,6 +864,55 @@ bool shape_fits(int fp64, int wide, int v, int max_nx, int max_cols, bool have_m
   return e == cudaSuccess && ctas >= 1;
 }
 
+// A split shape's class as a pipeline: its items in kPipeGroups groups of
+// decreasing cost; the factor launches of the groups run one after another
+// on the class's stream, and each group's solve launch (its items' column
+// chunks) on one of two further streams once that group's factor is done, so
+// that factors, solves and the tails of both overlap. Ordering is by stream
+// events only: no kernel waits on another. Adds its launches to *nk.
+cudaError_t launch_class_pipeline(sfb_ctx* c, const BasisArgs& A, int q, int shape, int nx, int cols, int refine,
+                                  cudaStream_t sa, int* nk) {
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+    if (!c->pipe_stream[q][k]) e = cudaStreamCreateWithFlags(&c->pipe_stream[q][k], cudaStreamNonBlocking);
+  for (cudaEvent_t& x : c->pipe_ev[q])
+    if (e == cudaSuccess && !x) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+  if (e != cudaSuccess) return e;
+  const int G = std::min<int>(sfb_ctx::kPipeGroups, A.n_items);
+  cudaEvent_t* ev = c->pipe_ev[q];
+  e = cudaEventRecord(ev[G], sa);   // fork
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(c->pipe_stream[q][k], ev[G], 0);
+  const int* chi = c->h_chunk_item.data() + c->chunk_start[q];
+  int ch0 = 0;
+  for (int g = 0; g < G && e == cudaSuccess; ++g) {
+    const int i0 = (int)((int64_t)g * A.n_items / G), i1 = (int)((int64_t)(g + 1) * A.n_items / G);
+    BasisArgs f = A;
+    f.item_sub = A.item_sub + i0;
+    f.item_k = A.item_k + i0;
+    f.n_items = i1 - i0;
+    e = launch_basis_part(f, q == 0, shape, 1, nx, cols, refine, sa);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[g], sa);
+    int ch1 = ch0;
+    while (ch1 < A.n_chunks && chi[ch1] < i1) ++ch1;
+    BasisArgs v = A;
+    v.chunk_item = A.chunk_item + ch0;
+    v.chunk_c0 = A.chunk_c0 + ch0;
+    v.chunk_cnt = A.chunk_cnt + ch0;
+    v.n_chunks = ch1 - ch0;
+    v.chunk_slot0 = A.chunk_slot0 + ch0;
+    cudaStream_t sb = c->pipe_stream[q][g & 1];
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sb, ev[g], 0);
+    if (e == cudaSuccess) e = launch_basis_part(v, q == 0, shape, 2, nx, cols, refine, sb);
+    *nk += 2;
+    ch0 = ch1;
+  }
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {   // join
+    e = cudaEventRecord(ev[G + 1 + k], c->pipe_stream[q][k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sa, ev[G + 1 + k], 0);
+  }
+  return e;
+}
+
 sfb_status autotune_basis(sfb_ctx* c, int prec, const BasisArgs* cls, const int* cls_nx, const int* cls_cols,
                           int refine) {
   const int fp64 = prec == SFB_FP64 ? 1 : 0;
@@ -862,8 +937,16 @@ sfb_status autotune_basis(sfb_ctx* c, int prec, const BasisArgs* cls, const int*
       float ms_min = 0.f;
       for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
         if (rep > 0) e = cudaEventRecord(t0, st);
-        if (e == cudaSuccess) e = launch_basis_shape(cls[q], fp64, q == 0, v, cls_nx[q], cls_cols[q], refine, st);
-        c->launches += 1;
+        if (e == cudaSuccess) {
+          int nk = 0;
+          if (basis_shape_split(fp64, q == 0, v)) {
+            e = launch_class_pipeline(c, cls[q], q, v, cls_nx[q], cls_cols[q], refine, st, &nk);
+          } else {
+            e = launch_basis_shape(cls[q], fp64, q == 0, v, cls_nx[q], cls_cols[q], refine, st);
+            nk = 1;
+          }
+          c->launches += nk;
+        }
         if (rep == 0 || e != cudaSuccess) continue;
         e = cudaEventRecord(t1, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(t1);
@@ -984,21 +1067,31 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   // size classes: [0] grids wider than 64 cells (the first n_wide items), [1] the rest
   const int fp64 = prec == SFB_FP64 ? 1 : 0;
   const int refine = prec == SFB_MIXED ? a.max_refine : 0;
+  a.n_items_all = n;
   BasisArgs cls[2] = {a, a};
   cls[0].n_items = (int)c->n_wide;
   cls[1].item_sub = a.item_sub + c->n_wide;
   cls[1].item_k = a.item_k + c->n_wide;
   cls[1].n_items = n - (int)c->n_wide;
+  for (int q = 0; q < 2; ++q) {
+    cls[q].chunk_item = d.chunk_item + c->chunk_start[q];
+    cls[q].chunk_c0 = d.chunk_c0 + c->chunk_start[q];
+    cls[q].chunk_cnt = d.chunk_cnt + c->chunk_start[q];
+    cls[q].n_chunks = (int)c->chunk_n[q];
+    cls[q].chunk_slot0 = (int)c->chunk_start[q];
+  }
   const int cls_nx[2] = {c->wide_nx, c->narrow_nx}, cls_cols[2] = {c->wide_cols, c->narrow_cols};
   if (c->opt_basis_autotune && !c->btuned[prec] && !factor_only) {
     sfb_status s = autotune_basis(c, prec, cls, cls_nx, cls_cols, refine);
     if (s != SFB_OK) return s;
   }
   SFB_CUDA(cudaMemsetAsync(d.status, 0, sizeof(int) * n, st), "memset");
-  SFB_CUDA(cudaMemsetAsync(d.resid, 0, sizeof(double) * n, st), "memset");
-  SFB_CUDA(cudaMemsetAsync(d.corr1, 0, sizeof(double) * n, st), "memset");
-  SFB_CUDA(cudaMemsetAsync(d.errest, 0, sizeof(double) * n, st), "memset");
-  SFB_CUDA(cudaMemsetAsync(d.nref, 0, sizeof(int) * n, st), "memset");
+  const int64_t nu_st = n + c->n_chunks;   // statistics slots: items, then chunks
+  SFB_CUDA(cudaMemsetAsync(d.resid, 0, sizeof(double) * nu_st, st), "memset");
+  SFB_CUDA(cudaMemsetAsync(d.corr1, 0, sizeof(double) * nu_st, st), "memset");
+  SFB_CUDA(cudaMemsetAsync(d.errest, 0, sizeof(double) * nu_st, st), "memset");
+  SFB_CUDA(cudaMemsetAsync(d.nref, 0, sizeof(int) * nu_st, st), "memset");
+  SFB_CUDA(cudaMemsetAsync(d.cycles, 0, sizeof(long long) * kCycSlots * nu_st, st), "memset");
   int shp[2] = {c->bshape[prec][0], c->bshape[prec][1]};
   // a shape this class lacks or that does not fit (or the tensor-core one
   // without maps): the first shape that fits
@@ -1014,19 +1107,22 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
     if (!c->fork) SFB_CUDA(cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming), "event");
     if (!c->join) SFB_CUDA(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming), "event");
   }
-  // One launch per size class: wide grids on the main stream, narrow grids
-  // concurrently on a side stream joined back before the epilogue.
+  // One launch per size class (a pipeline for a split shape): wide grids on
+  // the main stream, narrow grids concurrently on a side stream joined back
+  // before the epilogue.
+  auto run_class = [&](int q, cudaStream_t sq, int* nk) -> cudaError_t {
+    if (basis_shape_split(fp64, q == 0, shp[q]))
+      return launch_class_pipeline(c, cls[q], q, shp[q], cls_nx[q], cls_cols[q], refine, sq, nk);
+    *nk += 1;
+    return launch_basis_shape(cls[q], fp64, q == 0, shp[q], cls_nx[q], cls_cols[q], refine, sq);
+  };
   auto issue = [&](cudaStream_t s0, int* nk) -> cudaError_t {
-    if (!two) {
-      const int q = cls[0].n_items > 0 ? 0 : 1;
-      *nk = 1;
-      return launch_basis_shape(cls[q], fp64, q == 0, shp[q], cls_nx[q], cls_cols[q], refine, s0);
-    }
-    *nk = 2;
+    *nk = 0;
+    if (!two) return run_class(cls[0].n_items > 0 ? 0 : 1, s0, nk);
     cudaError_t e = cudaEventRecord(c->fork, s0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->fork, 0);
-    if (e == cudaSuccess) e = launch_basis_shape(cls[0], fp64, 1, shp[0], cls_nx[0], cls_cols[0], refine, s0);
-    if (e == cudaSuccess) e = launch_basis_shape(cls[1], fp64, 0, shp[1], cls_nx[1], cls_cols[1], refine, c->side);
+    if (e == cudaSuccess) e = run_class(0, s0, nk);
+    if (e == cudaSuccess) e = run_class(1, c->side, nk);
     if (e == cudaSuccess) e = cudaEventRecord(c->join, c->side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, c->join, 0);
     return e;
@@ -1098,16 +1194,34 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   c->launches += 1;
   if (e != cudaSuccess) return cuda_fail(c, e, "flux epilogue");
   SFB_CUDA(cudaEventRecord(e1, st), "event");
-  std::vector<int> status(n), nref(n);
-  std::vector<double> resid(n), corr(n), est(n);
-  std::vector<long long> cyc(kCycSlots * (size_t)n);
+  std::vector<int> status(n), nref(nu_st);
+  std::vector<double> resid(nu_st), corr(nu_st), est(nu_st);
+  std::vector<long long> cyc(kCycSlots * (size_t)nu_st);
   SFB_CUDA(cudaMemcpyAsync(status.data(), d.status, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "stats");
-  SFB_CUDA(cudaMemcpyAsync(nref.data(), d.nref, sizeof(int) * n, cudaMemcpyDeviceToHost, st), "stats");
-  SFB_CUDA(cudaMemcpyAsync(resid.data(), d.resid, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "stats");
-  SFB_CUDA(cudaMemcpyAsync(corr.data(), d.corr1, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "stats");
-  SFB_CUDA(cudaMemcpyAsync(est.data(), d.errest, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "stats");
-  SFB_CUDA(cudaMemcpyAsync(cyc.data(), d.cycles, sizeof(long long) * kCycSlots * n, cudaMemcpyDeviceToHost, st), "stats");
+  SFB_CUDA(cudaMemcpyAsync(nref.data(), d.nref, sizeof(int) * nu_st, cudaMemcpyDeviceToHost, st), "stats");
+  SFB_CUDA(cudaMemcpyAsync(resid.data(), d.resid, sizeof(double) * nu_st, cudaMemcpyDeviceToHost, st), "stats");
+  SFB_CUDA(cudaMemcpyAsync(corr.data(), d.corr1, sizeof(double) * nu_st, cudaMemcpyDeviceToHost, st), "stats");
+  SFB_CUDA(cudaMemcpyAsync(est.data(), d.errest, sizeof(double) * nu_st, cudaMemcpyDeviceToHost, st), "stats");
+  SFB_CUDA(cudaMemcpyAsync(cyc.data(), d.cycles, sizeof(long long) * kCycSlots * nu_st, cudaMemcpyDeviceToHost, st), "stats");
   SFB_CUDA(cudaStreamSynchronize(st), "basis build");
+  // a split class's refinement statistics come per chunk: fold them into the
+  // chunk's item (largest residual, correction, estimate and step count;
+  // the chunks' clocks summed)
+  for (int q = 0; q < 2; ++q) {
+    if (cls[q].n_items == 0 || !basis_shape_split(fp64, q == 0, shp[q])) continue;
+    const int64_t i0 = q == 0 ? 0 : c->n_wide;
+    std::vector<char> seen(n, 0);
+    for (int64_t k = 0; k < c->chunk_n[q]; ++k) {
+      const int64_t slot = n + c->chunk_start[q] + k;
+      const int64_t id = c->item_id[i0 + c->h_chunk_item[(size_t)(c->chunk_start[q] + k)]];
+      if (!seen[id]) { nref[id] = 0; resid[id] = corr[id] = est[id] = 0.0; seen[id] = 1; }
+      nref[id] = std::max(nref[id], nref[slot]);
+      resid[id] = std::max(resid[id], resid[slot]);
+      corr[id] = std::max(corr[id], corr[slot]);
+      est[id] = std::max(est[id], est[slot]);
+      for (int e = 2; e < kCycSlots; ++e) cyc[kCycSlots * (size_t)id + e] += cyc[kCycSlots * (size_t)slot + e];
+    }
+  }
   float ms = 0.f, kms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventElapsedTime(&kms, e0, ek);
@@ -1168,7 +1282,7 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
 }
 
 sfb_status sfb_basis_launch_shape(int32_t prec, int32_t wide, int32_t shape, int32_t* threads,
-                                  int32_t* ctas_per_sm, int32_t* g_buffers, int32_t* tcgen05) {
+                                  int32_t* ctas_per_sm, int32_t* g_buffers, int32_t* tcgen05, int32_t* split) {
   if (prec < 0 || prec > 2 || (wide != 0 && wide != 1)) return SFB_ERR_ARG;
   BasisShape d;
   if (!basis_shape_desc(prec == SFB_FP64, wide, shape, &d)) return SFB_ERR_ARG;
@@ -1176,6 +1290,7 @@ sfb_status sfb_basis_launch_shape(int32_t prec, int32_t wide, int32_t shape, int
   if (ctas_per_sm) *ctas_per_sm = d.min_ctas;
   if (g_buffers) *g_buffers = d.g_buffers;
   if (tcgen05) *tcgen05 = d.tcgen05;
+  if (split) *split = d.split;
   return SFB_OK;
 }
 

@@ -138,6 +138,15 @@ struct BasisArgs {
   double refine_tol;
   const void* gmaps = nullptr;  // per item id: CUtensorMap of its block inverses (tensor-core form)
   int particular_only = 0;      // Method S1's set-up: factor and particular solution only (FP64 kernel)
+  // split launch shapes: the solve kernel's work units, column chunks of the
+  // class's items (class-local item index, first column, column count); their
+  // refinement statistics go to slots n_items_all + chunk of the per-item arrays
+  const int* chunk_item = nullptr;
+  const int* chunk_c0 = nullptr;
+  const int* chunk_cnt = nullptr;
+  int n_chunks = 0;
+  int chunk_slot0 = 0;          // the class's first chunk among all chunks
+  int n_items_all = 0;
 };
 
 // Launchers (basis.cu).
@@ -155,9 +164,24 @@ struct BasisShape {
   int min_ctas;   // CTAs per SM the register budget is compiled for
   int g_buffers;  // shared-memory buffers of G_b (2: the next block row is prefetched)
   int tcgen05;    // 1: block-row products on the tensor cores (basis_tc.cu)
+  int split = 0;  // 1: a factor launch per item, then a solve launch per chunk of kChunkCols columns
 };
+// Columns of a split shape's solve work unit (at most; chunks are multiples of 4 but the last)
+constexpr int kChunkCols = 24;
+// The chunks of an item with C right-hand sides: n = ceil(C / kChunkCols) of
+// base = round4(ceil(C / n)) columns each but the last (C - base (n - 1)).
+inline int chunk_count(int C) { return (C + kChunkCols - 1) / kChunkCols; }
+inline int chunk_base(int C) {
+  const int n = chunk_count(C);
+  return (((C + n - 1) / n) + 3) & ~3;
+}
 int basis_shape_count(int fp64);
 bool basis_shape_desc(int fp64, int wide, int shape, BasisShape* out);
+bool basis_shape_split(int fp64, int wide, int shape);
+// One part of a split FP32 shape: 1 the factor launch (a.n_items items), 2
+// the solve launch (a.n_chunks chunks).
+cudaError_t launch_basis_part(const BasisArgs& a, int wide, int shape, int part, int max_nx, int max_cols, int refine,
+                              cudaStream_t st);
 // Resident CTAs per SM of a shape at the class's largest grid and column count.
 cudaError_t basis_shape_ctas(int fp64, int wide, int shape, int max_nx, int max_cols, int* ctas);
 cudaError_t launch_basis_shape(const BasisArgs& a, int fp64, int wide, int shape, int max_nx, int max_cols,

@@ -55,8 +55,8 @@ int main(void) {
   size_t ws_fp64 = 0, ws_mixed = 0;
   CHECK(sfb_workspace_size(ctx, SFB_FP64, n_pts, &ws_fp64));
   CHECK(sfb_workspace_size(ctx, SFB_MIXED, n_pts, &ws_mixed));
-  int32_t threads = 0, ctas = 0, gbuf = 0, tcgen05 = 0;
-  CHECK(sfb_basis_launch_shape(SFB_MIXED, 0, 0, &threads, &ctas, &gbuf, &tcgen05));
+  int32_t threads = 0, ctas = 0, gbuf = 0, tcgen05 = 0, split = 0;
+  CHECK(sfb_basis_launch_shape(SFB_MIXED, 0, 0, &threads, &ctas, &gbuf, &tcgen05, &split));
   printf("n_lambda %lld\n", (long long)n_lambda);
   printf("n_darcy %d\n", (int)n_darcy);
   printf("eig %.17g %.17g %.17g %.17g\n", eig[0], eig[1], eig[2], eig[3]);
@@ -64,7 +64,7 @@ int main(void) {
   printf("weight_sum %.17g\n", wsum);
   printf("workspace_fp64 %zu\n", ws_fp64);
   printf("workspace_mixed %zu\n", ws_mixed);
-  printf("shape %d %d %d %d\n", (int)threads, (int)ctas, (int)gbuf, (int)tcgen05);
+  printf("shape %d %d %d %d %d\n", (int)threads, (int)ctas, (int)gbuf, (int)tcgen05, (int)split);
   /* struct layouts, for the binding's mirrors: size and the last member's offset */
   printf("layout_problem %zu %zu\n", sizeof(sfb_problem), offsetof(sfb_problem, source));
   printf("layout_kl_region %zu %zu\n", sizeof(sfb_kl_region), offsetof(sfb_kl_region, n_modes_y));

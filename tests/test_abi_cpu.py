@@ -131,22 +131,24 @@ def test_basis_launch_shapes_and_options():
     """The launch-shape table the autotuner chooses from, and the options
     that steer it, are host logic: no kernel runs."""
     sfb = _lib()
-    assert sfb.basis_launch_shape(sfb.MIXED, 0, 0) == (256, 4, 1, 0)
-    assert sfb.basis_launch_shape(sfb.MIXED, 0, 1) == (256, 3, 2, 0)
-    assert sfb.basis_launch_shape(sfb.MIXED, 0, 2) == (256, 3, 1, 1)   # tensor-core form
-    assert sfb.basis_launch_shape(sfb.MIXED, 1, 0) == (256, 1, 2, 0)
-    assert sfb.basis_launch_shape(sfb.MIXED, 1, 1) == (256, 2, 1, 0)
-    assert sfb.basis_launch_shape(sfb.MIXED, 1, 2) is None   # no tensor-core form beyond 64 cells
-    assert sfb.basis_launch_shape(sfb.FP64, 0, 0) == (256, 2, 1, 0)
-    assert sfb.basis_launch_shape(sfb.FP64, 1, 0) == (512, 1, 1, 0)
-    assert sfb.basis_launch_shape(sfb.FP64, 1, 1) == (512, 1, 0, 0)   # G_b from global memory
+    assert sfb.basis_launch_shape(sfb.MIXED, 0, 0) == (256, 4, 1, 0, 0)
+    assert sfb.basis_launch_shape(sfb.MIXED, 0, 1) == (256, 3, 2, 0, 0)
+    assert sfb.basis_launch_shape(sfb.MIXED, 0, 2) == (256, 3, 1, 1, 0)   # tensor-core form
+    assert sfb.basis_launch_shape(sfb.MIXED, 0, 3) == (128, 8, 1, 0, 1)   # factor, then column chunks
+    assert sfb.basis_launch_shape(sfb.MIXED, 1, 0) == (256, 1, 2, 0, 0)
+    assert sfb.basis_launch_shape(sfb.MIXED, 1, 1) == (256, 2, 1, 0, 0)
+    assert sfb.basis_launch_shape(sfb.MIXED, 1, 2) == (128, 2, 1, 0, 1)   # no tensor-core form beyond 64 cells
+    assert sfb.basis_launch_shape(sfb.MIXED, 1, 3) is None
+    assert sfb.basis_launch_shape(sfb.FP64, 0, 0) == (256, 2, 1, 0, 0)
+    assert sfb.basis_launch_shape(sfb.FP64, 1, 0) == (512, 1, 1, 0, 0)
+    assert sfb.basis_launch_shape(sfb.FP64, 1, 1) == (512, 1, 0, 0, 0)   # G_b from global memory
     assert sfb.basis_launch_shape(sfb.FP64, 0, 1) is None
-    assert sfb.basis_launch_shape(sfb.MIXED, 0, 3) is None
+    assert sfb.basis_launch_shape(sfb.MIXED, 0, 4) is None
     assert sfb.basis_launch_shape(sfb.MIXED, 0, -1) is None
     assert sfb.basis_launch_shape(5, 0, 0) is None
     s = sfb.Solver(W.tiny())
     for name, ok, bad in (("basis_autotune", (0, 1), (2, -1)), ("basis_graph", (0, 1), (0.5, 3)),
-                          ("basis_shape", (0, 1, 2), (3, 1.5, -1))):
+                          ("basis_shape", (0, 1, 2, 3), (4, 1.5, -1))):
         for v in ok:
             s.set_option(name, v)
         for v in bad:

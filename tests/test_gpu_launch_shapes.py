@@ -5,8 +5,9 @@ the rest, and each class is one launch of the basis kernel. This workload has
 one subdomain in each class (72x6 and 13x9 cells). The CUDA-core launch shapes
 of a class must build the same basis bit for bit up to 1e-12; the tensor-core
 shape (narrow class only: 3xTF32 products on tcgen05, refined with the same
-FP64 residuals) the same basis within the mixed form's tolerance, and the
-oracle's. The autotuner must time every shape of each class and keep the
+FP64 residuals) and the split shapes (factor launches, then one CTA per chunk
+of at most 24 right-hand sides, each chunk refined to its own stopping test)
+the same basis within the mixed form's tolerance, and the oracle's. The autotuner must time every shape of each class and keep the
 fastest. A replayed CUDA graph must give the same bits as plain launches."""
 
 import numpy as np
@@ -43,12 +44,14 @@ def test_every_launch_shape_builds_the_same_basis(prec):
     import paper_1802_06263_gb300 as sfb
     s = _solver()
     s.set_option("basis_graph", 0)
-    n_shapes = 3 if prec == sfb.MIXED else 2
+    n_shapes = 4 if prec == sfb.MIXED else 2
     ref = None
     for v in range(n_shapes):
         s.set_option("basis_shape", v)
         st = s.build_basis(prec)
-        tc = v == 2   # the tensor-core shape exists for the narrow class only
+        # not bit for bit: the tensor-core shape (narrow class, v = 2) and the
+        # split shapes (wide class v = 2, narrow class v = 3)
+        loose = {0: prec == sfb.MIXED and v == 2, 1: prec == sfb.MIXED and v in (2, 3)}
         # a class without shape v (FP64 narrow grids have one shape) keeps shape 0
         expect = [v if sfb.basis_launch_shape(prec, wide, v) else 0 for wide in (1, 0)]
         assert st["launch_shape"] == expect and st["graph"] == 0
@@ -59,7 +62,7 @@ def test_every_launch_shape_builds_the_same_basis(prec):
             continue
         for key, (phi, g, X) in items.items():
             phi0, g0, X0 = ref[key]
-            if tc and key[0] == 1:
+            if loose[key[0]]:
                 assert_close(phi, phi0, TOL[prec], (v, key))
                 assert_close(X, X0, TOL[prec], (v, key))
                 continue
@@ -82,19 +85,21 @@ def test_every_launch_shape_builds_the_same_basis(prec):
 
 
 @pytest.mark.parametrize("key", ["tiny", "ragged", "medium", "anisotropic", "kl_regions", "paper_l2"])
-def test_tensor_core_shape_against_the_oracle(key):
-    """The tensor-core basis kernel, forced for every narrow item, against the
+@pytest.mark.parametrize("shape", [2, 3])
+def test_mixed_shape_against_the_oracle(key, shape):
+    """The tensor-core basis kernel (shape 2) or the split shape (3: factor
+    launches, then column chunks), forced for every narrow item, against the
     oracle: every item's Phi, g and X, then the mortar solutions and the
     moments of the whole collocation grid, within the mixed form's 1e-8. The
-    unrefined form of the same kernel (SFB_FP32_NOREFINE) is as far from the
+    unrefined form of the same kernels (SFB_FP32_NOREFINE) is as far from the
     oracle as an FP32 solve (below 1e-3) and no closer than 1e-9."""
     import paper_1802_06263_gb300 as sfb
     p, y, wt, lams, mom = oracle_case(key)
     s = sfb.Solver(make_workload(key))
     s.allocate(sfb.MIXED)
-    s.set_option("basis_shape", 2)
+    s.set_option("basis_shape", shape)
     st = s.build_basis(sfb.MIXED)
-    assert st["launch_shape"][1] == 2 and st["n_not_converged"] == 0
+    assert st["launch_shape"][1] == shape and st["n_not_converged"] == 0
     tol = TOL[1]
     for i in range(len(p.subs)):
         loc = p.local_realizations(i, y)[0]
@@ -150,7 +155,9 @@ def test_autotuner_times_every_shape_and_keeps_the_fastest():
     s.set_option("basis_autotune", 1)
     st = s.build_basis(sfb.MIXED)
     assert st["n_not_converged"] == 0
-    for q, n in ((0, 2), (1, 3)):   # wide grids: two shapes; narrow: three, the tensor-core one last
+    # wide grids: three shapes, the split one last; narrow: four, the
+    # tensor-core one, then the split one
+    for q, n in ((0, 3), (1, 4)):
         ms = st["tune_ms"][q][:n]
         assert all(m > 0 for m in ms), st["tune_ms"]
         assert all(m == 0 for m in st["tune_ms"][q][n:]), st["tune_ms"]
@@ -158,7 +165,13 @@ def test_autotuner_times_every_shape_and_keeps_the_fastest():
     # tuned once per precision: the next build keeps the choice and times nothing
     n0 = s.launch_count()
     st2 = s.build_basis(sfb.MIXED)
-    assert st2["launch_shape"] == st["launch_shape"] and s.launch_count() - n0 == 3
+    # one launch per size class and the flux epilogue; a split shape runs its
+    # class as a pipeline of up to two item groups, two launches each
+    per_class = []
+    for q, sub in ((0, 0), (1, 1)):   # subdomain 0 is the wide grid, 1 the narrow one
+        split = sfb.basis_launch_shape(sfb.MIXED, q == 0, st["launch_shape"][q])[4]
+        per_class.append(2 * min(2, len(s.local_points(sub))) if split else 1)
+    assert st2["launch_shape"] == st["launch_shape"] and s.launch_count() - n0 == 1 + sum(per_class)
     # FP64: two shapes for the wide grids (G_b in shared or in global memory),
     # both timed; one for the narrow grids, not timed
     st64 = s.build_basis(sfb.FP64)
