@@ -322,7 +322,8 @@ def run_ours(args):
     algo = algorithmic_basis_flops(wl, s)
     rl_mixed = pipe_roofline(algo, "fp32", k_mixed * 1e-3)
     rl_fp64 = pipe_roofline(algo, "fp64", k_fp64 * 1e-3)
-    # the committed ncu summary covers the default workload's launch only
+    # the committed ncu summary covers the default workload's basis build only
+    # (DRAM bytes of all its launches)
     traffic = profiled_traffic("basis.cu", "basis_kernel_mixed_precision.md") if args.workload == WORKLOAD else None
     # the other steps of the mixed step, from algorithmic counts:
     # a11 (CG): 2 sum_u R_u^2 FP32 flops per point and iteration for the
@@ -388,7 +389,9 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(y.nbytes + wt.nbytes),
                 "d2h_bytes_per_step": int(n_pts * (s.n_lambda * 8 + 4) + mom_bytes)},
         "clocks": clk,
-        "roofline": dict({"bound": "alu", "kernel": "basis_kernel<float> (mixed form)", "unit": "TFLOP/s",
+        "roofline": dict({"bound": "alu", "kernel": "basis_kernel<float> (mixed form; every launch of the basis "
+                                                 "build, the autotuned shape's: two factor and two solve "
+                                                 "launches for the split shape)", "unit": "TFLOP/s",
                           "traffic": traffic,
                           "traffic_over_algorithmic_bytes": (traffic / x_out_bytes) if traffic else None,
                           "algorithmic_bytes": x_out_bytes, "kernel_ms": k_mixed,
