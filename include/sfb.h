@@ -95,10 +95,13 @@ typedef enum {
  *               (otherwise the next cycle starts from it). The iteration
  *               count is the number of Arnoldi steps.
  * SFB_GMRES_MIXED: the same GMRES with the Arnoldi products S p on the bases
- *               rounded to FP32 (orthogonalization, Hessenberg, rotations,
- *               updates and iterates in FP64); a cycle also ends once it has
- *               reduced its initial residual by 1e-5, and every cycle starts
- *               from, and every point is accepted on, the FP64 true residual:
+ *               rounded to FP32 and the Arnoldi process itself in FP32 (the
+ *               Krylov basis stored in FP32, the Gram-Schmidt sums and
+ *               updates on the FP32 pipe, the preconditioner applied in
+ *               FP32); the Hessenberg matrix, the rotations, the iterate and
+ *               its update stay FP64. A cycle also ends once it has reduced
+ *               its initial residual by 1e-5, and every cycle starts from,
+ *               and every point is accepted on, the FP64 true residual:
  *               restarted GMRES as the inner solver of FP64 iterative
  *               refinement. Not in the paper, like SFB_CG_MIXED.
  * SFB_CG_DTN:   Method S1 (Section 5.2): unpreconditioned CG in FP64 whose

@@ -228,6 +228,10 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
 // r = g = sum_i R_i^T g_i^{k_i(l)}, p = r, lambda = 0; one warp per point.
 constexpr int kBlkMax = 32;   // largest interface block of the block-Jacobi preconditioner
@@ -745,6 +749,20 @@ __device__ __forceinline__ double* gm_gv(const GmArgs& g, int64_t l) { return gm
 __device__ __forceinline__ double* gm_v(const GmArgs& g, const IfaceArgs& a, int i, int64_t l) {
   return g.V + ((int64_t)i * a.n_pts + l) * a.n_lambda;
 }
+// The Krylov basis in the Arnoldi precision VT: FP64 (GMRES) or FP32 (the
+// mixed GMRES, whose cycles are the inner solver of an FP64 refinement: its
+// orthogonalization then runs on the FP32 pipe, at 64 times the FP64 rate,
+// and reads half the bytes). The FP32 basis occupies the front of the same
+// buffer.
+template <typename VT>
+__device__ __forceinline__ VT* gm_vt(const GmArgs& g, const IfaceArgs& a, int i, int64_t l) {
+  return reinterpret_cast<VT*>(g.V) + ((int64_t)i * a.n_pts + l) * a.n_lambda;
+}
+template <typename VT> __device__ __forceinline__ VT to_vt(double v);
+template <> __device__ __forceinline__ double to_vt<double>(double v) { return v; }
+template <> __device__ __forceinline__ float to_vt<float>(double v) { return f64_to_f32_bits(v); }
+__device__ __forceinline__ double vt_f64(double v) { return v; }
+__device__ __forceinline__ double vt_f64(float v) { return f32_to_f64_bits(v); }
 
 // (M^{-1} v)_d for point l with v in global memory, in FP64 arithmetic.
 __device__ __forceinline__ double precond64(const IfaceArgs& a, int64_t l, const double* v, int d) {
@@ -758,6 +776,25 @@ __device__ __forceinline__ double precond64(const IfaceArgs& a, int64_t l, const
   }
   if (a.dinv) return a.dinv[l * a.n_lambda + d] * v[d];
   return v[d];
+}
+
+// (M^{-1} v)_d for the Krylov basis vector v in its own precision: FP64 as
+// precond64, or for FP32 vectors with FP32 arithmetic (the block inverses are
+// stored in FP32; the Jacobi factor rounded to FP32).
+__device__ __forceinline__ double precond_t(const IfaceArgs& a, int64_t l, const double* v, int d) {
+  return precond64(a, l, v, d);
+}
+__device__ __forceinline__ double precond_t(const IfaceArgs& a, int64_t l, const float* v, int d) {
+  if (a.minv) {
+    const int e = a.dof_if[d];
+    const int n = a.if_n[e], d0 = a.if_off[e], i = d - d0;
+    const float* M = a.minv + l * a.minv_ld + a.if_moff[e] + i * n;
+    float z = 0.f;
+    for (int j = 0; j < n; ++j) z = fmaf(M[j], v[d0 + j], z);
+    return f32_to_f64_bits(z);
+  }
+  if (a.dinv) return f32_to_f64_bits(f64_to_f32_bits(a.dinv[l * a.n_lambda + d]) * v[d]);
+  return f32_to_f64_bits(v[d]);
 }
 
 // g_d of point l (the two units' flux data); with want_diag also the diagonal
@@ -779,21 +816,23 @@ __device__ __forceinline__ double rhs_g(const IfaceArgs& a, int64_t l, int64_t d
 
 // New cycle of point l from the residual r (global, n_lambda entries) of norm
 // rn > 0: V_0 = r / rn, gv = (rn, 0, ...), j = 0, p = M^{-1} V_0.
+template <typename VT>
 __device__ __forceinline__ void gm_new_cycle(const IfaceArgs& a, const GmArgs& g, int64_t l, int lane,
                                              const double* r, double rn) {
-  double* v0 = gm_v(g, a, 0, l);
+  VT* v0 = gm_vt<VT>(g, a, 0, l);
   const double inv = 1.0 / rn;
-  for (int64_t d = lane; d < a.n_lambda; d += 32) v0[d] = r[d] * inv;
+  for (int64_t d = lane; d < a.n_lambda; d += 32) v0[d] = to_vt<VT>(r[d] * inv);
   double* gv = gm_gv(g, l);
   for (int i = lane; i <= kGmresMax; i += 32) gv[i] = i == 0 ? rn : 0.0;
   if (lane == 0) g.st[l * kGmresState + kGmBeta] = rn;
   __syncwarp();
   double* pl = a.p + l * a.n_lambda;
-  for (int64_t d = lane; d < a.n_lambda; d += 32) pl[d] = precond64(a, l, v0, (int)d);
+  for (int64_t d = lane; d < a.n_lambda; d += 32) pl[d] = precond_t(a, l, v0, (int)d);
   if (lane == 0) g.j[l] = 0;
 }
 
 // First cycle from lambda = 0: r = g, ||g||, the Jacobi diagonal when used.
+template <typename VT>
 __global__ void gmres_init_kernel(IfaceArgs a, GmArgs g) {
   const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -813,7 +852,7 @@ __global__ void gmres_init_kernel(IfaceArgs a, GmArgs g) {
   int st = a.pstat[l] & kBadIdx;
   if (!st && s2 == 0.0) st = 1;   // zero data: converged with lambda = 0
   __syncwarp();
-  if (st == 0) gm_new_cycle(a, g, l, lane, rl, gn);
+  if (st == 0) gm_new_cycle<VT>(a, g, l, lane, rl, gn);
   if (lane == 0) {
     a.gn[l] = gn;
     a.pstat[l] = st;
@@ -824,6 +863,9 @@ __global__ void gmres_init_kernel(IfaceArgs a, GmArgs g) {
 // p = M^{-1} V_j: w = S M^{-1} V_j orthogonalized against V_0..V_j (two
 // classical Gram-Schmidt passes), H column j, V_{j+1} = w / ||w||, the
 // rotations, and at the end of the cycle the solution update.
+// VT: the precision of the basis and of the Gram-Schmidt sums (FP64, or FP32
+// for the mixed GMRES); the Hessenberg matrix, rotations and updates stay FP64.
+template <typename VT>
 __global__ void __launch_bounds__(256) gmres_arnoldi_kernel(IfaceArgs a, GmArgs g, int it, double rtol) {
   const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -832,48 +874,50 @@ __global__ void __launch_bounds__(256) gmres_arnoldi_kernel(IfaceArgs a, GmArgs 
   const int j = g.j[l];
   const int64_t n = a.n_lambda;
   const double* Yl = a.Y + l * a.NY;
-  double* w = a.r + l * n;   // the new direction, then the update's V y
-  for (int64_t d = lane; d < n; d += 32) w[d] = Yl[a.yoff[2 * d]] + Yl[a.yoff[2 * d + 1]];
+  VT* w = reinterpret_cast<VT*>(a.r + l * n);   // the new direction (in r's storage)
+  for (int64_t d = lane; d < n; d += 32) w[d] = to_vt<VT>(Yl[a.yoff[2 * d]]) + to_vt<VT>(Yl[a.yoff[2 * d + 1]]);
   __syncwarp();
   double* hcol = gm_col(g, l, j);
   // the warp's Gram-Schmidt coefficients (one basis vector at a time, so that
   // no thread holds the whole column: occupancy for the memory-bound sweeps)
   __shared__ double hsh[8][kGmresMax + 1];
+  __shared__ VT hvsh[8][kGmresMax + 1];   // the same, in the basis precision
   double* hw = hsh[threadIdx.x >> 5];
+  VT* hv = hvsh[threadIdx.x >> 5];
   // classical Gram-Schmidt, repeated only when the first pass cancelled more
   // than a factor 1/sqrt(2) of w (the criterion of Daniel, Gragg, Kaufman and
   // Stewart): one pass keeps orthogonality unless w was nearly in the span
-  double s2 = 0.0;
+  VT s2 = VT(0);
   for (int64_t d = lane; d < n; d += 32) s2 = fma(w[d], w[d], s2);
-  const double w0 = sqrt(warp_sum(s2));
+  const double w0 = sqrt(vt_f64(warp_sum(s2)));
   double hn = 0.0;
   for (int pass = 0; pass < 2; ++pass) {
     for (int i = 0; i <= j; ++i) {
-      const double* vi = gm_v(g, a, i, l);
-      double acc = 0.0;
+      const VT* vi = gm_vt<VT>(g, a, i, l);
+      VT acc = VT(0);
       for (int64_t d = lane; d < n; d += 32) acc = fma(vi[d], w[d], acc);
       acc = warp_sum(acc);
       if (lane == 0) {
-        hw[i] = acc;
-        hcol[i] = pass == 0 ? acc : hcol[i] + acc;
+        hv[i] = acc;
+        hcol[i] = pass == 0 ? vt_f64(acc) : hcol[i] + vt_f64(acc);
       }
     }
     __syncwarp();
-    s2 = 0.0;
+    s2 = VT(0);
     for (int64_t d = lane; d < n; d += 32) {
-      double wd = w[d];
-      for (int i = 0; i <= j; ++i) wd = fma(-hw[i], gm_v(g, a, i, l)[d], wd);
+      VT wd = w[d];
+      for (int i = 0; i <= j; ++i) wd = fma(-hv[i], gm_vt<VT>(g, a, i, l)[d], wd);
       w[d] = wd;
       s2 = fma(wd, wd, s2);
     }
-    hn = sqrt(warp_sum(s2));
+    hn = sqrt(vt_f64(warp_sum(s2)));
     __syncwarp();
     if (hn >= 0.70710678118654752 * w0) break;   // warp-uniform: every lane holds the sums
   }
   const bool brk = !(hn > 0.0);   // the Krylov space is invariant: the cycle's solution is exact
   if (!brk) {
-    double* vn = gm_v(g, a, j + 1, l);
-    const double inv = 1.0 / hn;
+    VT* vn = gm_vt<VT>(g, a, j + 1, l);
+    const VT inv = to_vt<VT>(1.0 / hn);
     for (int64_t d = lane; d < n; d += 32) vn[d] = w[d] * inv;
   }
   // rotations (lane 0): the earlier ones on column j, then the one that
@@ -904,9 +948,9 @@ __global__ void __launch_bounds__(256) gmres_arnoldi_kernel(IfaceArgs a, GmArgs 
   end = __shfl_sync(0xffffffffu, end, 0);
   __syncwarp();
   if (!end) {
-    const double* vn = gm_v(g, a, j + 1, l);
+    const VT* vn = gm_vt<VT>(g, a, j + 1, l);
     double* pl = a.p + l * n;
-    for (int64_t d = lane; d < n; d += 32) pl[d] = precond64(a, l, vn, (int)d);
+    for (int64_t d = lane; d < n; d += 32) pl[d] = precond_t(a, l, vn, (int)d);
     if (lane == 0) g.j[l] = j + 1;
     return;
   }
@@ -922,14 +966,15 @@ __global__ void __launch_bounds__(256) gmres_arnoldi_kernel(IfaceArgs a, GmArgs 
   }
   if (lane < jn) hw[lane] = yk;
   __syncwarp();
+  double* u = a.p + l * n;   // V y in FP64, in p's storage (no next direction)
   for (int64_t d = lane; d < n; d += 32) {
-    double u = 0.0;
-    for (int i = 0; i < jn; ++i) u = fma(hw[i], gm_v(g, a, i, l)[d], u);
-    w[d] = u;
+    double ud = 0.0;
+    for (int i = 0; i < jn; ++i) ud = fma(hw[i], vt_f64(gm_vt<VT>(g, a, i, l)[d]), ud);
+    u[d] = ud;
   }
   __syncwarp();
   double* ll = a.lam + l * n;
-  for (int64_t d = lane; d < n; d += 32) ll[d] += precond64(a, l, w, (int)d);
+  for (int64_t d = lane; d < n; d += 32) ll[d] += precond64(a, l, u, (int)d);
   if (lane == 0) {
     g.j[l] = 0;
     a.pstat[l] = kPending | (it + 1);
@@ -939,6 +984,7 @@ __global__ void __launch_bounds__(256) gmres_arnoldi_kernel(IfaceArgs a, GmArgs 
 // The FP64 true residual r = g - S lambda of every point whose cycle ended,
 // on the products Y = S lambda: accepted when ||r|| <= rtol ||g||, otherwise
 // the next cycle starts from r.
+template <typename VT>
 __global__ void gmres_restart_kernel(IfaceArgs a, GmArgs g, double rtol) {
   const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -959,7 +1005,7 @@ __global__ void gmres_restart_kernel(IfaceArgs a, GmArgs g, double rtol) {
     if (lane == 0) a.pstat[l] = s & kItMask;
     return;
   }
-  gm_new_cycle(a, g, l, lane, rl, rn);
+  gm_new_cycle<VT>(a, g, l, lane, rl, rn);
   if (lane == 0) a.pstat[l] = 0;
 }
 
@@ -2707,7 +2753,8 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
   gma.cycle_tol = gmres_mixed ? 1e-5 : 0.0;
   if (gmres) {
     CK(cudaMemsetAsync(d.rflag, 0, sizeof(int) * n_pts, st));
-    gmres_init_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, gma);
+    if (gmres_mixed) gmres_init_kernel<float><<<ublocks, 32 * warps_per_block, 0, st>>>(a, gma);
+    else gmres_init_kernel<double><<<ublocks, 32 * warps_per_block, 0, st>>>(a, gma);
   } else {
     init_kernel<<<ublocks, 32 * warps_per_block, stg, st>>>(a);
   }
@@ -2883,11 +2930,13 @@ sfb_status iface_solve_device(sfb_ctx* c, int64_t n_pts, double rtol, int max_it
     for (int q = 0; q < chunk && it < max_it; ++q, ++it) {
       if (gmres_mixed) matvec_kernel<float><<<mgrid, 256, smv32, st>>>(a, d.p, 0, d.active + 2, 0);
       else matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.p, 0, d.active + 2, 0);
-      gmres_arnoldi_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, gma, it, rtol);
+      if (gmres_mixed) gmres_arnoldi_kernel<float><<<ublocks, 32 * warps_per_block, 0, st>>>(a, gma, it, rtol);
+      else gmres_arnoldi_kernel<double><<<ublocks, 32 * warps_per_block, 0, st>>>(a, gma, it, rtol);
       c->launches += 2;
     }
     matvec_kernel<double><<<mgrid, 256, smv, st>>>(a, d.lam, 1, d.active + 2, 0);
-    gmres_restart_kernel<<<ublocks, 32 * warps_per_block, 0, st>>>(a, gma, rtol);
+    if (gmres_mixed) gmres_restart_kernel<float><<<ublocks, 32 * warps_per_block, 0, st>>>(a, gma, rtol);
+    else gmres_restart_kernel<double><<<ublocks, 32 * warps_per_block, 0, st>>>(a, gma, rtol);
     c->launches += 2;
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(d.active, 0, sizeof(int), st));
