@@ -418,7 +418,8 @@ def run_ours(args):
 def basis_launch(sfb, prec, st):
     """Launch shape of each size class of the basis build (threads, CTAs per
     SM, G buffers), the autotuner's timings and whether a graph replayed it."""
-    out = {"graph_replay": bool(st["graph"])}
+    out = {"graph_replay": bool(st["graph"]),
+           "persistent_launch": bool(st["persistent"])}   # every item of both classes in one launch
     for q, cls in enumerate(("wide_grids", "narrow_grids")):
         v = st["launch_shape"][q]
         if v < 0:

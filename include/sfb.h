@@ -221,7 +221,10 @@ typedef struct {
                               /* (sfb_basis_launch_shape); -1: class is empty     */
   int32_t graph;              /* 1: the launches of all size classes ran as one   */
                               /* replayed CUDA graph                              */
-  int32_t reserved;
+  int32_t persistent;         /* 1: every item of both size classes ran in one    */
+                              /* persistent launch (factor tasks, then chunk      */
+                              /* tasks; launch_shape then gives the per-class     */
+                              /* choices it was timed against)                    */
   double tune_ms[2][4];       /* autotuner, per size class and launch shape: the  */
                               /* shorter of two timed launches of the class's     */
                               /* items (ms); 0: not timed                         */

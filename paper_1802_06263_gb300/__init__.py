@@ -62,7 +62,7 @@ class BasisStats(ctypes.Structure):
                 ("max_error_estimate", ctypes.c_double), ("ms", ctypes.c_double),
                 ("phase_cycles", ctypes.c_double * 16), ("kernel_ms", ctypes.c_double),
                 ("flops_fp32", ctypes.c_double), ("flops_fp64", ctypes.c_double),
-                ("launch_shape", ctypes.c_int32 * 2), ("graph", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("launch_shape", ctypes.c_int32 * 2), ("graph", ctypes.c_int32), ("persistent", ctypes.c_int32),
                 ("tune_ms", (ctypes.c_double * 4) * 2), ("mean_refine_steps", ctypes.c_double)]
 
 
@@ -340,7 +340,6 @@ class Solver:
         out["phase_cycles"] = list(st.phase_cycles)
         out["launch_shape"] = list(st.launch_shape)
         out["tune_ms"] = [list(r) for r in st.tune_ms]
-        del out["reserved"]
         out["status"] = rc
         return out
 

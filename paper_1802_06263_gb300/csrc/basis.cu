@@ -153,28 +153,19 @@ __device__ __forceinline__ void blocked_sweep_w0(T (&areg)[MT][4][4], int np, in
 // x = 0. Splitting an item's solves over several CTAs shortens the longest
 // dependent chain per CTA and gives the scheduler several times more, smaller
 // work units than there are items.
-template <typename T, int MT, int NT, int MINB, int GB, int MODE = 0>
-__global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[32];
-  __shared__ int bad_spd;
-  __shared__ __align__(8) uint64_t gbar[2];
-  __shared__ __align__(8) uint64_t zbar;
-  int item, c0 = 0, ccount = 0;
-  if constexpr (MODE == 2) {
-    if ((int)blockIdx.x >= a.n_chunks) return;
-    item = a.chunk_item[blockIdx.x];
-    c0 = a.chunk_c0[blockIdx.x];
-    ccount = a.chunk_cnt[blockIdx.x];
-  } else {
-    item = blockIdx.x;
-    if (item >= a.n_items) return;
-  }
+// The work of one CTA on item `item` (an index into a.item_sub / a.item_k)
+// and, in MODE 2, on its columns c0 .. c0 + ccount - 1; statistics go to slot
+// wid_in (the item's id when negative). The shared-memory state comes from
+// the calling kernel.
+template <typename T, int MT, int NT, int GB, int MODE>
+__device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int item, int c0, int ccount, int wid_in,
+                                           unsigned char* smem_raw, double* red, int& bad_spd, uint64_t* gbar,
+                                           uint64_t& zbar) {
   const int s = a.item_sub[item], kk = a.item_k[item];
   const SubDev S = a.subs[s];
   const int id = (int)S.item0 + kk;
   // statistics slot: the item, or (MODE 2) the chunk after all items
-  const int wid = MODE == 2 ? a.n_items_all + a.chunk_slot0 + (int)blockIdx.x : id;
+  const int wid = wid_in >= 0 ? wid_in : id;
   const ItemOff off = a.off[id];
   Geo g;
   // all R + 1 right-hand sides, or (Method S1's set-up) only the particular
@@ -585,6 +576,103 @@ __global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine
 #undef SFB_MARK
 }
 
+template <typename T, int MT, int NT, int MINB, int GB, int MODE = 0>
+__global__ void __launch_bounds__(NT, MINB) basis_kernel(BasisArgs a, int refine) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  __shared__ int bad_spd;
+  __shared__ __align__(8) uint64_t gbar[2];
+  __shared__ __align__(8) uint64_t zbar;
+  if constexpr (MODE == 2) {
+    if ((int)blockIdx.x >= a.n_chunks) return;
+    basis_body<T, MT, NT, GB, MODE>(a, refine, a.chunk_item[blockIdx.x], a.chunk_c0[blockIdx.x],
+                                    a.chunk_cnt[blockIdx.x], a.n_items_all + a.chunk_slot0 + (int)blockIdx.x,
+                                    smem_raw, red, bad_spd, gbar, zbar);
+  } else {
+    if ((int)blockIdx.x >= a.n_items) return;
+    basis_body<T, MT, NT, GB, MODE>(a, refine, blockIdx.x, 0, 0, -1, smem_raw, red, bad_spd, gbar, zbar);
+  }
+}
+
+// Persistent form of the split shapes: one launch for every item of every size
+// class. Each CTA takes tasks in order from a counter: first the factor of
+// every item (MODE 1), then every column chunk (MODE 2). A chunk waits for its
+// item's factor flag. Every factor task is taken before any chunk task, and a
+// task is only taken by a running CTA, so the factor a chunk waits for is
+// already running; the wait is bounded all the same (about 4 s), after which
+// the chunk's item is marked ST_TIMEOUT and the chunk skipped.
+struct PersistArgs {
+  int* counter;     // task counter, zero at launch
+  int* flags;       // per item (build order): 1 once its factor is in global memory; zero at launch
+  int n_items, n_chunks;
+  int n_wide;       // the chunks' items are class-local: the wide class first
+  int chunk_n0;     // chunks of the wide class
+};
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <typename T, int MT, int NT, int MINB, int GB>
+__global__ void __launch_bounds__(NT, MINB) basis_persistent_kernel(BasisArgs a, int refine, PersistArgs p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  __shared__ int bad_spd;
+  __shared__ __align__(8) uint64_t gbar[2];
+  __shared__ __align__(8) uint64_t zbar;
+  __shared__ int task, ready;
+  const int n_tasks = p.n_items + p.n_chunks;
+  for (;;) {
+    __syncthreads();   // the last task's reads of `task` and of the barriers are done
+    if (threadIdx.x == 0) task = atomicAdd(p.counter, 1);
+    __syncthreads();
+    const int t = task;
+    if (t >= n_tasks) break;
+    if (t < p.n_items) {
+      basis_body<T, MT, NT, GB, 1>(a, refine, t, 0, 0, -1, smem_raw, red, bad_spd, gbar, zbar);
+      // publish the factor: every thread's global stores, then the flag
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        fence_async_global();
+        __threadfence();
+        atomicExch(&p.flags[t], 1);
+      }
+    } else {
+      const int ch = t - p.n_items;
+      const int item = (ch < p.chunk_n0 ? 0 : p.n_wide) + a.chunk_item[ch];
+      if (threadIdx.x == 0) {
+        int ok = 0;
+        for (int k = 0; k < (1 << 24); ++k) {
+          if (ld_acquire(&p.flags[item]) == 1) { ok = 1; break; }
+          __nanosleep(256);
+        }
+        fence_async_global();   // the bulk loads of the factor come after the acquire
+        ready = ok;
+      }
+      __syncthreads();
+      if (ready) {
+        basis_body<T, MT, NT, GB, 2>(a, refine, item, a.chunk_c0[ch], a.chunk_cnt[ch], a.n_items_all + ch, smem_raw,
+                                     red, bad_spd, gbar, zbar);
+      } else if (threadIdx.x == 0) {
+        const SubDev& S = a.subs[a.item_sub[item]];
+        atomicOr(&a.status[S.item0 + a.item_k[item]], ST_TIMEOUT);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {   // the body initialises them again for the next task
+      mbar_inval(&gbar[0]);
+      mbar_inval(&gbar[1]);
+      mbar_inval(&zbar);
+    }
+  }
+}
+
 // Phi[l][j] = -sum_e P[e][l] T_e (X[c_e][j] - P[e][j]) (j < R) and
 // g[l] = sum_e P[e][l] T_e X[c_e][R], the sum running over the faces e of the
 // side that carries mortar DOF l and lying in the support of xi_l.
@@ -787,6 +875,47 @@ cudaError_t launch_basis_shape(const BasisArgs& a, int fp64, int wide, int shape
   if ((wide != 0) != (max_nx > 64)) return cudaErrorInvalidValue;
   return fp64 ? shape_dispatch<double>(&a, wide, shape, max_nx, max_cols, 0, st, nullptr)
               : shape_dispatch<float>(&a, wide, shape, max_nx, max_cols, refine, st, nullptr);
+}
+
+namespace {
+template <typename T, int MT, int NT, int MINB, int GB>
+cudaError_t persistent_one(const BasisArgs& a, const PersistArgs& p, int max_nx, int max_cols, int refine,
+                           cudaStream_t st, int* ctas) {
+  const size_t smem = std::max(basis_smem<T>(max_nx, max_cols, GB, 1), basis_smem<T>(max_nx, max_cols, GB, 2));
+  auto fn = basis_persistent_kernel<T, MT, NT, MINB, GB>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, NT, smem);
+  if (e != cudaSuccess) return e;
+  if (ctas) { *ctas = per; return cudaSuccess; }
+  if (per < 1) return cudaErrorInvalidConfiguration;
+  int dev = 0, n_sm = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p.counter, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p.flags, 0, sizeof(int) * std::max(p.n_items, 1), st);
+  if (e != cudaSuccess) return e;
+  const int grid = std::min(p.n_items + p.n_chunks, per * n_sm);
+  if (grid == 0) return cudaSuccess;
+  fn<<<grid, NT, smem, st>>>(a, refine, p);
+  return cudaGetLastError();
+}
+}  // namespace
+
+// One instantiation for both size classes: the wide one's register tiles (up
+// to 128-wide grids) when there are wide items, else the narrow one's.
+cudaError_t launch_basis_persistent(const BasisArgs& a, int* counter, int* flags, int n_wide, int chunk_n0,
+                                    int max_nx, int max_cols, int refine, cudaStream_t st, int* ctas) {
+  PersistArgs p;
+  p.counter = counter;
+  p.flags = flags;
+  p.n_items = a.n_items;
+  p.n_chunks = a.n_chunks;
+  p.n_wide = n_wide;
+  p.chunk_n0 = chunk_n0;
+  if (max_nx > 128) return cudaErrorInvalidValue;
+  return max_nx > 64 ? persistent_one<float, 4, 256, 2, 1>(a, p, max_nx, max_cols, refine, st, ctas)
+                     : persistent_one<float, 1, 256, 4, 1>(a, p, max_nx, max_cols, refine, st, ctas);
 }
 
 cudaError_t launch_basis_part(const BasisArgs& a, int wide, int shape, int part, int max_nx, int max_cols, int refine,

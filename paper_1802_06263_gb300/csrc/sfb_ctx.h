@@ -80,6 +80,8 @@ struct Dev {
   int* chunk_item = nullptr;  // split launch shapes: per column chunk its class-local item,
   int* chunk_c0 = nullptr;    // first column and column count (wide class first)
   int* chunk_cnt = nullptr;
+  int* persist_counter = nullptr;   // the persistent basis launch's task counter
+  int* persist_flags = nullptr;     // ... and its per-item "factor done" flags
   // Stokes
   double* s_mat = nullptr;
   double* s_pl = nullptr;    // the band LU's panel multipliers in final row order
@@ -240,15 +242,21 @@ struct sfb_ctx {
   // each candidate (ms, 0 = not timed), and the captured graph per precision
   int bshape[3][2] = {{0, 0}, {0, 0}, {0, 0}};
   bool btuned[3] = {false, false, false};
+  // the persistent basis launch: option (-1 autotuned, 0 off, 1 on), the
+  // autotuner's choice and timings (per-class launches, persistent launch)
+  int opt_basis_persistent = -1;
+  bool bpersist[3] = {false, false, false}, bpersist_tuned[3] = {false, false, false};
+  double bpersist_ms[3][2] = {};
   double btune_ms[3][2][4] = {};
   struct GraphKey {
     const char* ws = nullptr;
     int refine = 0;
     double refine_tol = 0.0;
     int shape[2] = {0, 0};
+    int persist = 0;
     bool operator==(const GraphKey& o) const {
       return ws == o.ws && refine == o.refine && refine_tol == o.refine_tol && shape[0] == o.shape[0] &&
-             shape[1] == o.shape[1];
+             shape[1] == o.shape[1] && persist == o.persist;
     }
   };
   cudaGraphExec_t bgraph[3] = {nullptr, nullptr, nullptr};

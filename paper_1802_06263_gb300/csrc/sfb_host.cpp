@@ -211,6 +211,8 @@ size_t layout(sfb_ctx* c, Carver& cv, int prec, int64_t max_pts) {
   d.chunk_item = cv.take<int>(std::max<int64_t>(n_chunks, 1));
   d.chunk_c0 = cv.take<int>(std::max<int64_t>(n_chunks, 1));
   d.chunk_cnt = cv.take<int>(std::max<int64_t>(n_chunks, 1));
+  d.persist_counter = cv.take<int>(4);
+  d.persist_flags = cv.take<int>(std::max<int64_t>(n_items, 1));
   // Stokes
   const StokesHost& St = c->stokes;
   const int Rs = (int)St.dofs.size(), Cs = Rs + 1;
@@ -1116,7 +1118,31 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
     *nk += 1;
     return launch_basis_shape(cls[q], fp64, q == 0, shp[q], cls_nx[q], cls_cols[q], refine, sq);
   };
-  auto issue = [&](cudaStream_t s0, int* nk) -> cudaError_t {
+  // The persistent form: one launch over every item of both classes (FP32
+  // factor, not Method S1's set-up); the autotuner times it against the
+  // per-class launches above (option "basis_persistent": -1 the autotuner
+  // decides, 0 never, 1 always).
+  BasisArgs pa = a;
+  pa.n_items = n;
+  pa.chunk_item = d.chunk_item;
+  pa.chunk_c0 = d.chunk_c0;
+  pa.chunk_cnt = d.chunk_cnt;
+  pa.n_chunks = (int)c->n_chunks;
+  pa.chunk_slot0 = 0;
+  const int all_nx = std::max(cls_nx[0], cls_nx[1]), all_cols = std::max(cls_cols[0], cls_cols[1]);
+  int pctas = 0;
+  const bool can_persist = !fp64 && !factor_only && n > 0 && all_nx <= 128 &&
+                           launch_basis_persistent(pa, d.persist_counter, d.persist_flags, (int)c->n_wide,
+                                                   (int)c->chunk_n[0], all_nx, all_cols, refine, st, &pctas) ==
+                               cudaSuccess &&
+                           pctas >= 1;
+  cudaGetLastError();
+  auto issue_persistent = [&](cudaStream_t s0, int* nk) -> cudaError_t {
+    *nk = 1;
+    return launch_basis_persistent(pa, d.persist_counter, d.persist_flags, (int)c->n_wide, (int)c->chunk_n[0], all_nx,
+                                   all_cols, refine, s0, nullptr);
+  };
+  auto issue_classes = [&](cudaStream_t s0, int* nk) -> cudaError_t {
     *nk = 0;
     if (!two) return run_class(cls[0].n_items > 0 ? 0 : 1, s0, nk);
     cudaError_t e = cudaEventRecord(c->fork, s0);
@@ -1126,6 +1152,40 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
     if (e == cudaSuccess) e = cudaEventRecord(c->join, c->side);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, c->join, 0);
     return e;
+  };
+  bool persist = can_persist && c->opt_basis_persistent == 1;
+  if (can_persist && c->opt_basis_persistent == -1 && c->opt_basis_autotune) {
+    if (!c->bpersist_tuned[prec]) {
+      // one untimed and two timed builds of each form; the shorter time wins
+      cudaEvent_t t0 = nullptr, t1 = nullptr;
+      cudaError_t e = cudaEventCreate(&t0);
+      if (e == cudaSuccess) e = cudaEventCreate(&t1);
+      float best[2] = {0.f, 0.f};
+      for (int form = 0; form < 2 && e == cudaSuccess; ++form) {
+        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+          int nk = 0;
+          e = cudaEventRecord(t0, st);
+          if (e == cudaSuccess) e = form == 0 ? issue_classes(st, &nk) : issue_persistent(st, &nk);
+          c->launches += nk;
+          if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+          if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+          float ms = 0.f;
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+          if (e == cudaSuccess && rep > 0 && (rep == 1 || ms < best[form])) best[form] = ms;
+        }
+      }
+      if (t0) cudaEventDestroy(t0);
+      if (t1) cudaEventDestroy(t1);
+      if (e != cudaSuccess) return cuda_fail(c, e, "basis autotuner (persistent form)");
+      c->bpersist_ms[prec][0] = best[0];
+      c->bpersist_ms[prec][1] = best[1];
+      c->bpersist[prec] = best[1] < best[0];
+      c->bpersist_tuned[prec] = true;
+    }
+    persist = c->bpersist[prec];
+  }
+  auto issue = [&](cudaStream_t s0, int* nk) -> cudaError_t {
+    return persist ? issue_persistent(s0, nk) : issue_classes(s0, nk);
   };
   // The launches of all size classes as one CUDA graph, captured on a private
   // stream (the context stream may be the legacy default stream, which cannot
@@ -1142,6 +1202,7 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
     key.refine_tol = a.refine_tol;
     key.shape[0] = shp[0];
     key.shape[1] = shp[1];
+    key.persist = persist ? 1 : 0;
     if (c->bgraph[prec] && !(c->bkey[prec] == key)) {
       cudaGraphExecDestroy(c->bgraph[prec]);
       c->bgraph[prec] = nullptr;
@@ -1208,7 +1269,7 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
   // chunk's item (largest residual, correction, estimate and step count;
   // the chunks' clocks summed)
   for (int q = 0; q < 2; ++q) {
-    if (cls[q].n_items == 0 || !basis_shape_split(fp64, q == 0, shp[q])) continue;
+    if (cls[q].n_items == 0 || !(persist || basis_shape_split(fp64, q == 0, shp[q]))) continue;
     const int64_t i0 = q == 0 ? 0 : c->n_wide;
     std::vector<char> seen(n, 0);
     for (int64_t k = 0; k < c->chunk_n[q]; ++k) {
@@ -1269,7 +1330,7 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* c, int32_t prec, sfb_basis_stats*
       for (int v = 0; v < 4; ++v) stats->tune_ms[q][v] = c->btune_ms[prec][q][v];
     }
     stats->graph = graph ? 1 : 0;
-    stats->reserved = 0;
+    stats->persistent = persist ? 1 : 0;
   }
   c->basis_done = true;
   c->basis_prec = factor_only ? SFB_FACTOR_FP64 : prec;
@@ -1448,6 +1509,7 @@ sfb_status sfb_set_option(sfb_ctx* c, const char* name, double value) {
     c->opt_basis_autotune = (int)value;
     for (int p = 0; p < 3; ++p) {
       c->btuned[p] = false;
+      c->bpersist_tuned[p] = false;
       c->bshape[p][0] = c->bshape[p][1] = 0;
     }
   } else if (n == "basis_shape") {
@@ -1463,6 +1525,10 @@ sfb_status sfb_set_option(sfb_ctx* c, const char* name, double value) {
       }
       c->btuned[p] = true;
     }
+  } else if (n == "basis_persistent") {
+    if (!(value == -1 || value == 0 || value == 1)) return fail(c, SFB_ERR_ARG, "basis_persistent must be -1, 0 or 1");
+    c->opt_basis_persistent = (int)value;
+    for (int p = 0; p < 3; ++p) c->bpersist_tuned[p] = false;
   } else if (n == "basis_graph") {
     if (!(value == 0 || value == 1)) return fail(c, SFB_ERR_ARG, "basis_graph must be 0 or 1");
     c->opt_basis_graph = (int)value;

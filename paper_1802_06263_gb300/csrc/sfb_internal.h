@@ -178,6 +178,11 @@ inline int chunk_base(int C) {
 int basis_shape_count(int fp64);
 bool basis_shape_desc(int fp64, int wide, int shape, BasisShape* out);
 bool basis_shape_split(int fp64, int wide, int shape);
+// The persistent FP32 launch over every item of both size classes (a: all
+// items in build order, all chunks; counter and flags: workspace words it
+// clears first). ctas: when non-null, only reports the resident CTAs per SM.
+cudaError_t launch_basis_persistent(const BasisArgs& a, int* counter, int* flags, int n_wide, int chunk_n0,
+                                    int max_nx, int max_cols, int refine, cudaStream_t st, int* ctas);
 // One part of a split FP32 shape: 1 the factor launch (a.n_items items), 2
 // the solve launch (a.n_chunks chunks).
 cudaError_t launch_basis_part(const BasisArgs& a, int wide, int shape, int part, int max_nx, int max_cols, int refine,

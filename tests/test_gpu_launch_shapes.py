@@ -68,6 +68,19 @@ def test_every_launch_shape_builds_the_same_basis(prec):
                 continue
             assert rel(phi, phi0) < 1e-12 and rel(X, X0) < 1e-12, (v, key)
             assert np.abs(g - g0).max() <= 1e-12 * max(1.0, np.abs(g0).max()), (v, key)
+    # the persistent launch (both classes' items as tasks of one launch)
+    if prec == sfb.MIXED:
+        s.set_option("basis_shape", 0)
+        s.set_option("basis_persistent", 1)
+        n0 = s.launch_count()
+        st = s.build_basis(prec)
+        assert st["persistent"] == 1 and st["n_not_converged"] == 0
+        assert s.launch_count() - n0 == 2   # the persistent launch and the flux epilogue
+        for key, (phi, g, X) in _items(s).items():
+            phi0, g0, X0 = ref[key]
+            assert_close(phi, phi0, TOL[prec], ("persistent", key))
+            assert_close(X, X0, TOL[prec], ("persistent", key))
+        s.set_option("basis_persistent", -1)
     # the basis is the method's: one item of each class against the oracle
     from oracle import coupled
     p = coupled.Problem(_workload())
@@ -85,11 +98,12 @@ def test_every_launch_shape_builds_the_same_basis(prec):
 
 
 @pytest.mark.parametrize("key", ["tiny", "ragged", "medium", "anisotropic", "kl_regions", "paper_l2"])
-@pytest.mark.parametrize("shape", [2, 3])
+@pytest.mark.parametrize("shape", [2, 3, "persistent"])
 def test_mixed_shape_against_the_oracle(key, shape):
-    """The tensor-core basis kernel (shape 2) or the split shape (3: factor
-    launches, then column chunks), forced for every narrow item, against the
-    oracle: every item's Phi, g and X, then the mortar solutions and the
+    """The tensor-core basis kernel (shape 2), the split shape (3: factor
+    launches, then column chunks) or the persistent launch (every item's factor
+    and column chunks as tasks of one launch), forced for every item, against
+    the oracle: every item's Phi, g and X, then the mortar solutions and the
     moments of the whole collocation grid, within the mixed form's 1e-8. The
     unrefined form of the same kernels (SFB_FP32_NOREFINE) is as far from the
     oracle as an FP32 solve (below 1e-3) and no closer than 1e-9."""
@@ -97,9 +111,14 @@ def test_mixed_shape_against_the_oracle(key, shape):
     p, y, wt, lams, mom = oracle_case(key)
     s = sfb.Solver(make_workload(key))
     s.allocate(sfb.MIXED)
-    s.set_option("basis_shape", shape)
+    if shape == "persistent":
+        s.set_option("basis_shape", 0)
+        s.set_option("basis_persistent", 1)
+    else:
+        s.set_option("basis_shape", shape)
     st = s.build_basis(sfb.MIXED)
-    assert st["launch_shape"][1] == shape and st["n_not_converged"] == 0
+    assert st["n_not_converged"] == 0
+    assert st["persistent"] == 1 if shape == "persistent" else st["launch_shape"][1] == shape
     tol = TOL[1]
     for i in range(len(p.subs)):
         loc = p.local_realizations(i, y)[0]
@@ -171,7 +190,10 @@ def test_autotuner_times_every_shape_and_keeps_the_fastest():
     for q, sub in ((0, 0), (1, 1)):   # subdomain 0 is the wide grid, 1 the narrow one
         split = sfb.basis_launch_shape(sfb.MIXED, q == 0, st["launch_shape"][q])[4]
         per_class.append(2 * min(2, len(s.local_points(sub))) if split else 1)
-    assert st2["launch_shape"] == st["launch_shape"] and s.launch_count() - n0 == 1 + sum(per_class)
+    # (the autotuner also timed the persistent launch against these; when it won,
+    # the build is one launch)
+    assert st2["launch_shape"] == st["launch_shape"] and st2["persistent"] == st["persistent"]
+    assert s.launch_count() - n0 == (2 if st["persistent"] else 1 + sum(per_class))
     # FP64: two shapes for the wide grids (G_b in shared or in global memory),
     # both timed; one for the narrow grids, not timed
     st64 = s.build_basis(sfb.FP64)
