@@ -205,9 +205,11 @@ typedef struct {
                               /* sub-phases of the row steps up to each barrier:  */
                               /* factor [4] row set-up [5] block inversion [6]    */
                               /* G store and right-hand side [7] product;         */
-                              /* forward [8] set-up [9] residual and G wait [10]  */
-                              /* product; backward [11] set-up [12] scaled input  */
-                              /* [13] z and G waits [14] product [15] X update    */
+                              /* forward [8] set-up [12] residual (thread 0's     */
+                              /* loop) [9] G and store waits [10] product;        */
+                              /* backward [11] set-up and copies issued [13] z    */
+                              /* and G waits [14] product [15] X update with the  */
+                              /* next row's product input                         */
   double kernel_ms;           /* device time of the basis kernel alone            */
   double flops_fp32;          /* algorithmic flops of the build by precision, per */
   double flops_fp64;          /* item: factor (7/3) nx^3 ny (block Cholesky       */

@@ -173,6 +173,7 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
   // columns; none in MODE 1
   const int coff = MODE == 2 ? c0 : (a.particular_only ? S.R : 0);
   g.nx = S.nx; g.ny = S.ny; g.R = S.R;
+  g.src = S.source * S.hx * S.hy;
   g.C = MODE == 2 ? ccount : MODE == 1 ? 0 : (a.particular_only ? 1 : S.R + 1);
   g.Cp = (g.C + 3) & ~3;
   g.nc = S.nx * S.ny;
@@ -218,17 +219,25 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
     fence_barrier_init();
   }
   int st = 0;
-  long long t_mark = clock64(), t_fwd = 0, t_bwd = 0;
   long long* cyc = a.cycles + kCycSlots * (int64_t)wid;
-  // thread 0's clock between barriers: sub-phases of the factor, forward and
-  // backward row steps (slots 4-15 of the per-item cycle record)
-  long long sub[12] = {}, t_sub = t_mark;
+  // thread 0's clocks, kept in shared memory so that they take no registers
+  // of the other threads: [0, 12) the sub-phases of the factor, forward and
+  // backward row steps (slots 4-15 of the per-item cycle record), then the
+  // forward and backward totals, the phase mark and the sub-phase mark
+  __shared__ long long clk[16];
+  constexpr int kFwd = 12, kBwd = 13, kMark = 14, kSub = 15;
+  if (threadIdx.x == 0) {
+    const long long t0 = clock64();
+    for (int q = 0; q < kMark; ++q) clk[q] = 0;
+    clk[kMark] = t0;
+    clk[kSub] = t0;
+  }
 #define SFB_MARK(k)                                          \
   do {                                                       \
     if (threadIdx.x == 0) {                                  \
       const long long t_ = clock64();                        \
-      sub[k] += t_ - t_sub;                                  \
-      t_sub = t_;                                            \
+      clk[k] += t_ - clk[kSub];                              \
+      clk[kSub] = t_;                                        \
     }                                                        \
   } while (0)
   for (int e = threadIdx.x; e < np * Cp; e += blockDim.x) { Us[e] = T(0); Zs[e] = T(0); }
@@ -291,7 +300,7 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) { const long long t = clock64(); cyc[0] = t - t_mark; t_mark = t; }
+  if (threadIdx.x == 0) { const long long t = clock64(); cyc[0] = t - clk[kMark]; clk[kMark] = t; }
 
   // ---- 2. factorization, fused with the first forward solve ------------------
   // G_b and z_b leave through bulk stores from shared memory.
@@ -349,13 +358,13 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
     fence_async_global();
   }
   __syncthreads();
-  if (threadIdx.x == 0) { const long long t = clock64(); cyc[1] = t - t_mark; t_mark = t; t_sub = t; }
+  if (threadIdx.x == 0) { const long long t = clock64(); cyc[1] = t - clk[kMark]; clk[kMark] = t; clk[kSub] = t; }
   if constexpr (MODE == 1) {
     // the factor alone: its status, and the sub-phase clocks of its rows
     if (threadIdx.x == 0) {
       cyc[2] = 0;
       cyc[3] = 0;
-      for (int q = 0; q < 12; ++q) cyc[4 + q] = sub[q];
+      for (int q = 0; q < 12; ++q) cyc[4 + q] = clk[q];
     }
     if (bad_spd) st |= ST_NOT_SPD;
     if (st) atomicOr(&a.status[id], st);
@@ -363,9 +372,21 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
   }
 
   // ---- 3./4. backward sweep, then refine with FP64 residuals --------------------------
+  // Row loops over the nx x C entries of a block row: the lanes of a warp take
+  // 8 consecutive cells of 4 consecutive columns (a lane group reads 64
+  // contiguous bytes of an X column; the [i][Cp] shared-memory entries of a
+  // warp fall in distinct banks when Cp = 4 mod 8) and each warp a contiguous
+  // run of these 32-entry tiles, column tile fastest. A lane's cell then
+  // changes a few times per row, its coefficients are loaded once per change,
+  // and no entry needs an integer division.
+  const int li = threadIdx.x & 7, lc = (threadIdx.x >> 3) & 3;
+  const int nct = (C + 3) >> 2, ntile = ((nx + 7) >> 3) * nct;
+  const int nwarp = (int)(blockDim.x >> 5), wrp = (int)(threadIdx.x >> 5);
+  const int tile0 = (int)((int64_t)wrp * ntile / nwarp), tile1 = (int)((int64_t)(wrp + 1) * ntile / nwarp);
+  const int ti0 = nct ? tile0 / nct : 0, tc0 = tile0 - ti0 * nct;
   double xref2 = 0.0, prev_corr = 0.0, est = 1.0, bnorm2 = 0.0;
   int n_done = 0;
-  bool timeout = false;
+  bool timeout = false, nonfinite = false;
   for (int it = 0; it <= refine && !timeout; ++it) {
     float rr = 0.f;
     // x = 0 before a chunk's first forward sweep (MODE 2): r = B
@@ -394,27 +415,51 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
           fence_async_shared();
           bulk_load(Gs0 + (cur ^ 1) * np * np, Gg + (int64_t)(b + 1) * np * np, gbytes, &gbar[cur ^ 1]);
         }
+        {
+          // the lane's cell: its 5-point coefficients and row scalings
+          double dd = 0.0, tw = 0.0, te = 0.0, ts = 0.0, tn = 0.0;
+          T sci = T(0), dli = T(0);
+          bool inner = false;
+          int tcur = -1, ti = ti0, tc = tc0;
+          const double* Tb = Tx + b * (nx + 1);
 #pragma unroll 2
-        for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
-          const int i = e % nx, c = e / nx;
-          const int64_t cell = (int64_t)b * nx + i;
-          const double* xc = X + (int64_t)c * nc;
-          // r = B - A x as five FP64 FMAs: B - D x, then + T x over the neighbours
-          double r = rhs_entry(S, g, a.proj, b, i, c + coff);
-          if (!xzero) {
-            r = fma(-Dg[cell], xc[cell], r);
-            if (i > 0) r = fma(Tx[b * (nx + 1) + i], xc[cell - 1], r);
-            if (i < nx - 1) r = fma(Tx[b * (nx + 1) + i + 1], xc[cell + 1], r);
-            if (b > 0) r = fma(Ty[b * nx + i], xc[cell - nx], r);
-            if (b < ny - 1) r = fma(Ty[(b + 1) * nx + i], xc[cell + nx], r);
+          for (int t = tile0; t < tile1; ++t) {
+            const int i = ti * 8 + li, c = tc * 4 + lc;
+            if (ti != tcur && i < nx) {
+              tcur = ti;
+              sci = sc[i];
+              dli = dlo[i];
+              inner = b > 0 && b < ny - 1 && i > 0 && i < nx - 1;
+              if (!xzero) {
+                dd = Dg[(int64_t)b * nx + i];
+                tw = i > 0 ? Tb[i] : 0.0;
+                te = i < nx - 1 ? Tb[i + 1] : 0.0;
+                ts = b > 0 ? Ty[b * nx + i] : 0.0;
+                tn = b < ny - 1 ? Ty[(b + 1) * nx + i] : 0.0;
+              }
+            }
+            if (i < nx && c < C) {
+              // r = B - A x as five FP64 FMAs: B - D x, then + T x over the neighbours
+              double r = inner ? (c + coff < g.R ? 0.0 : g.src) : rhs_boundary(S, g, a.proj, b, i, c + coff);
+              if (!xzero) {
+                const double* xp = X + (int64_t)c * nc + (int64_t)b * nx + i;
+                r = fma(-dd, xp[0], r);
+                if (i > 0) r = fma(tw, xp[-1], r);
+                if (i < nx - 1) r = fma(te, xp[1], r);
+                if (b > 0) r = fma(ts, xp[-nx], r);
+                if (b < ny - 1) r = fma(tn, xp[nx], r);
+              }
+              const T rt = from_f64<T>(r);
+              const float rf = to_f32(rt);
+              rr = fmaf(rf, rf, rr);
+              T u = sci * rt;
+              if (b > 0) u = fma(dli, Zs[i * Cp + c], u);
+              Us[i * Cp + c] = u;
+            }
+            if (++tc == nct) { tc = 0; ++ti; }
           }
-          const T rt = from_f64<T>(r);
-          const float rf = to_f32(rt);
-          rr = fmaf(rf, rf, rr);
-          T u = sc[i] * rt;
-          if (b > 0) u = fma(dlo[i], Zs[i * Cp + c], u);
-          Us[i * Cp + c] = u;
         }
+        SFB_MARK(8);
         // G_b present, and the store that reads Zs finished
         if (threadIdx.x == 0) bulk_wait_read();
         bool ok = true;
@@ -442,7 +487,7 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
       const double rnorm2 = block_sum((double)rr, red);
       if (xzero) bnorm2 = rnorm2;   // |B|^2 for the relative residual
       else if (threadIdx.x == 0) a.resid[wid] = sqrt(rnorm2 / fmax(bnorm2, 1e-300));
-      if (threadIdx.x == 0) { const long long t = clock64(); t_fwd += t - t_mark; t_mark = t; t_sub = t; }
+      if (threadIdx.x == 0) { const long long t = clock64(); clk[kFwd] += t - clk[kMark]; clk[kMark] = t; clk[kSub] = t; }
     } else {
       // |B|^2 for the relative residual
       float bb = 0.f;
@@ -453,41 +498,38 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
       }
       bnorm2 = block_sum((double)bb, red);
     }
-    // backward sweep: d_b = z_b + G_b (dup_b .* d_{b+1}); x_b += s_b d_b.
-    // G_{b-1} is prefetched while row b runs (two G buffers).
+    // backward sweep: d_b = z_b + G_b (dup_b .* d_{b+1}); x_b += s_b d_b, with
+    // dup_b .* d_{b+1} formed by the update loop of row b + 1 (dup holding the
+    // coupling of that row to the one below). G_{b-1} is prefetched while row b
+    // runs (two G buffers).
     float dn2f = 0.f;
     if (GB == 2 && threadIdx.x == 0 && ny >= 2) {
       fence_async_shared();
       bulk_load(Gs0, Gg + (int64_t)(ny - 2) * np * np, gbytes, &gbar[0]);
     }
-    T bsc = threadIdx.x < nx ? Sg[(ny - 1) * nx + threadIdx.x] : T(0), bdu = T(0);
+    T bsc = threadIdx.x < nx ? Sg[(ny - 1) * nx + threadIdx.x] : T(0);
+    T bdl = threadIdx.x < nx ? DLg[(ny - 1) * nx + threadIdx.x] : T(0);
     for (int b = ny - 1; b >= 0; --b) {
       const int cur = GB == 2 ? ((ny - 2 - b) & 1) : 0;   // buffer of G_b (b <= ny-2)
       T* Gs = GB == 0 ? Gg + (int64_t)b * np * np : Gs0 + cur * np * np;
+      // the previous row's loop finished with Zs and sc / dup (trailing barrier)
       if (threadIdx.x < nx) {
         sc[threadIdx.x] = bsc;
-        dup[threadIdx.x] = bdu;   // D_b = the coupling to row b + 1
-        if (b > 0) { bsc = Sg[(b - 1) * nx + threadIdx.x]; bdu = DLg[b * nx + threadIdx.x]; }
+        dup[threadIdx.x] = bdl;   // coupling of row b to row b - 1 (zero for row 0)
+        if (b > 0) { bsc = Sg[(b - 1) * nx + threadIdx.x]; bdl = DLg[(b - 1) * nx + threadIdx.x]; }
       }
       if (it > 0) prefetch_x_row(X, nc, nx, b, C);   // updated after the product below
-      __syncthreads();
       SFB_MARK(7);
-      if (threadIdx.x == 0 && b < ny - 1) {
+      if (threadIdx.x == 0) {
         fence_async_shared();
-        if (GB == 2 && b >= 1)   // prefetch G_{b-1}
-          bulk_load(Gs0 + (cur ^ 1) * np * np, Gg + (int64_t)(b - 1) * np * np, gbytes, &gbar[cur ^ 1]);
-        if (GB == 1)             // G_b into the single buffer
-          bulk_load(Gs0, Gg + (int64_t)b * np * np, gbytes, &gbar[0]);
+        if (b < ny - 1) {
+          if (GB == 2 && b >= 1)   // prefetch G_{b-1}
+            bulk_load(Gs0 + (cur ^ 1) * np * np, Gg + (int64_t)(b - 1) * np * np, gbytes, &gbar[cur ^ 1]);
+          if (GB == 1)             // G_b into the single buffer
+            bulk_load(Gs0, Gg + (int64_t)b * np * np, gbytes, &gbar[0]);
+        }
+        bulk_load(Zs, Zg + (int64_t)b * np * Cp, zbytes, &zbar);
       }
-      // Us = dup .* d_{b+1} (d_{b+1} in Zs), then z_b -> Zs
-      for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
-        const int i = e % nx, c = e / nx;
-        Us[i * Cp + c] = dup[i] * Zs[i * Cp + c];
-      }
-      fence_async_shared();
-      __syncthreads();
-      SFB_MARK(8);
-      if (threadIdx.x == 0) bulk_load(Zs, Zg + (int64_t)b * np * Cp, zbytes, &zbar);
       bool ok = mbar_wait(&zbar, zph);
       zph ^= 1u;
       if (GB > 0 && b < ny - 1) {
@@ -499,35 +541,43 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
       if (b < ny - 1) gemm_g<T>(Gs, Us, Zs, true, np, Cp, C);
       __syncthreads();
       SFB_MARK(10);
-      // x_b += s d_b: the X entries of four iterations are loaded before any
-      // of them is stored, so that the loads overlap
-      constexpr int kXU = 4;
-      for (int e0 = threadIdx.x; e0 < nx * C; e0 += kXU * blockDim.x) {
-        double xo[kXU];
+      // x_b += s d_b and Us = dup .* d_b for row b - 1: the X entries of four
+      // tiles are loaded before any of them is stored, so that the loads overlap
+      {
+        int ti = ti0, tc = tc0;
+        for (int t = tile0; t < tile1; t += 4) {
+          double xo[4];
+          int ii[4], cc[4];
 #pragma unroll
-        for (int u = 0; u < kXU; ++u) {
-          const int e = e0 + u * blockDim.x;
-          const int i = e % nx, c = e / nx;
-          xo[u] = (it > 0 && e < nx * C) ? X[(int64_t)c * nc + (int64_t)b * nx + i] : 0.0;
-        }
+          for (int u = 0; u < 4; ++u) {
+            ii[u] = t + u < tile1 ? ti * 8 + li : nx;
+            cc[u] = tc * 4 + lc;
+            xo[u] = (it > 0 && ii[u] < nx && cc[u] < C) ? X[(int64_t)cc[u] * nc + (int64_t)b * nx + ii[u]] : 0.0;
+            if (++tc == nct) { tc = 0; ++ti; }
+          }
 #pragma unroll
-        for (int u = 0; u < kXU; ++u) {
-          const int e = e0 + u * blockDim.x;
-          if (e >= nx * C) break;
-          const int i = e % nx, c = e / nx;
-          const int64_t idx = (int64_t)c * nc + (int64_t)b * nx + i;
-          const T dt = sc[i] * Zs[i * Cp + c];
-          const float df = to_f32(dt);
-          dn2f = fmaf(df, df, dn2f);
-          X[idx] = it == 0 ? to_f64(dt) : xo[u] + to_f64(dt);
+          for (int u = 0; u < 4; ++u) {
+            const int i = ii[u], c = cc[u];
+            if (i >= nx || c >= C) continue;
+            const T z = Zs[i * Cp + c];
+            const T dt = sc[i] * z;
+            const float df = to_f32(dt);
+            dn2f = fmaf(df, df, dn2f);
+            const double xn = it == 0 ? to_f64(dt) : xo[u] + to_f64(dt);
+            nonfinite |= ((__double2hiint(xn) >> 20) & 0x7ff) == 0x7ff;
+            X[(int64_t)c * nc + (int64_t)b * nx + i] = xn;
+            if (b > 0) Us[i * Cp + c] = dup[i] * z;
+          }
         }
       }
+      // the reads of Zs above come before the next row's copy into it
+      fence_async_shared();
       __syncthreads();
       SFB_MARK(11);
     }
     if (timeout) break;
     const double dn2 = block_sum((double)dn2f, red);
-    if (threadIdx.x == 0) { const long long t = clock64(); t_bwd += t - t_mark; t_mark = t; t_sub = t; }
+    if (threadIdx.x == 0) { const long long t = clock64(); clk[kBwd] += t - clk[kMark]; clk[kMark] = t; clk[kSub] = t; }
     if (it == 0) {
       xref2 = dn2;  // ||x_0||^2
       prev_corr = 1.0;
@@ -561,15 +611,15 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
   }
   if (threadIdx.x == 0) {
     bulk_wait_all();
-    cyc[2] = t_fwd;
-    cyc[3] = t_bwd;
-    for (int q = 0; q < 12; ++q) cyc[4 + q] = sub[q];
+    cyc[2] = clk[kFwd];
+    cyc[3] = clk[kBwd];
+    for (int q = 0; q < 12; ++q) cyc[4 + q] = clk[q];
     a.nref[wid] = n_done;
     a.errest[wid] = refine > 0 ? est : 0.0;
   }
-  // non-finite check on the result
-  for (int e = threadIdx.x; e < nc * C; e += blockDim.x)
-    if (!isfinite(X[e])) st |= ST_NONFINITE;
+  // non-finite entries of X (every value X took was checked when stored; a
+  // non-finite entry stays non-finite under later corrections)
+  if (nonfinite) st |= ST_NONFINITE;
   __syncthreads();
   if (bad_spd) st |= ST_NOT_SPD;
   if (st) atomicOr(&a.status[id], st);
@@ -782,7 +832,7 @@ cudaError_t launch_basis(const BasisArgs& a, int max_nx, int max_cols, int refin
 constexpr int kShapes = 4;
 constexpr BasisShape kShape[2][2][kShapes] = {
     // FP32: narrow, wide
-    {{{256, 4, 1, 0, 0}, {256, 3, 2, 0, 0}, {256, 3, 1, 1, 0}, {128, 8, 1, 0, 1}},
+    {{{256, 4, 1, 0, 0}, {256, 3, 2, 0, 0}, {256, 3, 1, 1, 0}, {128, 7, 1, 0, 1}},
      {{256, 1, 2, 0, 0}, {256, 2, 1, 0, 0}, {128, 2, 1, 0, 1}, {0, 0, 0, 0, 0}}},
     // FP64: narrow, wide (the second wide shape keeps G_b in global memory,
     // for blocks too large for shared memory beside the right-hand sides)
@@ -823,8 +873,8 @@ cudaError_t shape_dispatch(const BasisArgs* a, bool wide, int shape, int max_nx,
     if (!wide && shape == 2)
       return ctas ? basis_tc_ctas(max_nx, max_cols, ctas) : launch_basis_tc(*a, max_nx, max_cols, refine, st);
     if (!wide && shape == 3)
-      return ctas ? occupancy_of<T, 1, 128, 8, 1, 2>(basis_smem<T>(max_nx, max_cols, 1, 2), ctas)
-                  : launch_split<T, 1, 256, 4, 1, 1, 128, 8, 1>(*a, max_nx, max_cols, refine, st, part);
+      return ctas ? occupancy_of<T, 1, 128, 7, 1, 2>(basis_smem<T>(max_nx, max_cols, 1, 2), ctas)
+                  : launch_split<T, 1, 256, 4, 1, 1, 128, 7, 1>(*a, max_nx, max_cols, refine, st, part);
     if (wide && shape == 2)
       return ctas ? occupancy_of<T, 1, 128, 2, 1, 2>(basis_smem<T>(max_nx, max_cols, 1, 2), ctas)
                   : launch_split<T, 4, 256, 2, 1, 1, 128, 2, 1>(*a, max_nx, max_cols, refine, st, part);

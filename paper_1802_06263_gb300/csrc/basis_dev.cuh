@@ -16,17 +16,20 @@ struct Geo {
   int nx, ny, R, C, Cp, nc;
   const double* Tx;  // [ny][nx+1]
   const double* Ty;  // [ny+1][nx]
+  double src;        // source * hx * hy, the particular column's entry of an inner cell
 };
 
 // Right-hand side entry B[(b, i)][c] in FP64: interface columns c < R carry
 // T_e * P_side[face][c] on interface faces of boundary cells; column R carries
-// the source and the outer Dirichlet data.
-__device__ __forceinline__ double rhs_entry(const SubDev& S, const Geo& g, const double* proj, int b, int i,
+// the source and the outer Dirichlet data. The terms of the boundary cells
+// sit in a function of their own, called (not inlined) from the cells of the
+// grid's outer ring only: inlined, its FP64 products were issued, predicated
+// off, for every entry, and the FP64 pipe runs at 1/64 of the FP32 rate.
+__device__ __noinline__ double rhs_boundary(const SubDev& S, const Geo& g, const double* proj, int b, int i,
                                             int c) {
   const int nx = g.nx, ny = g.ny;
   double v = 0.0;
   if (c < g.R) {
-    if (b > 0 && b < ny - 1 && i > 0 && i < nx - 1) return 0.0;
     if (b == 0 && S.side_type[0] == SIDE_IFACE) v += g.Ty[i] * proj[S.proj_off[0] + (int64_t)i * g.R + c];
     if (b == ny - 1 && S.side_type[2] == SIDE_IFACE)
       v += g.Ty[ny * nx + i] * proj[S.proj_off[2] + (int64_t)i * g.R + c];
@@ -35,13 +38,18 @@ __device__ __forceinline__ double rhs_entry(const SubDev& S, const Geo& g, const
     if (i == nx - 1 && S.side_type[1] == SIDE_IFACE)
       v += g.Tx[b * (nx + 1) + nx] * proj[S.proj_off[1] + (int64_t)b * g.R + c];
   } else {
-    v = S.source * S.hx * S.hy;
+    v = g.src;
     if (b == 0 && S.side_type[0] == SIDE_DIRICHLET) v += g.Ty[i] * S.side_val[0];
     if (b == ny - 1 && S.side_type[2] == SIDE_DIRICHLET) v += g.Ty[ny * nx + i] * S.side_val[2];
     if (i == 0 && S.side_type[3] == SIDE_DIRICHLET) v += g.Tx[b * (nx + 1)] * S.side_val[3];
     if (i == nx - 1 && S.side_type[1] == SIDE_DIRICHLET) v += g.Tx[b * (nx + 1) + nx] * S.side_val[1];
   }
   return v;
+}
+__device__ __forceinline__ double rhs_entry(const SubDev& S, const Geo& g, const double* proj, int b, int i,
+                                            int c) {
+  if (b > 0 && b < g.ny - 1 && i > 0 && i < g.nx - 1) return c < g.R ? 0.0 : g.src;
+  return rhs_boundary(S, g, proj, b, i, c);
 }
 
 // 4 consecutive values from a 16-byte aligned address (one float4 or two

@@ -160,6 +160,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcMinCtas) basis_tc_kernel(BasisA
   const ItemOff off = a.off[id];
   Geo g;
   g.nx = S.nx; g.ny = S.ny; g.R = S.R; g.C = S.R + 1; g.Cp = (g.C + 7) & ~7; g.nc = S.nx * S.ny;
+  g.src = S.source * S.hx * S.hy;
   const int nx = g.nx, ny = g.ny, nc = g.nc, C = g.C, Cp8 = g.Cp;
   constexpr int kP = 16;
   const int np = (nx + kPanel - 1) & ~(kPanel - 1);

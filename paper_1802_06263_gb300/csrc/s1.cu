@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(kDtnThreads, 4) dtn_kernel(DtnArgs a) {
   const int nb = 2 * nx + 2 * ny;   // boundary faces: bottom nx, right ny, top nx, left ny
   Geo g;
   g.nx = nx; g.ny = ny; g.R = R; g.C = R + 1; g.Cp = (R + 4) & ~3; g.nc = nx * ny;
+  g.src = S.source * S.hx * S.hy;
   g.Tx = a.T + off.t;
   g.Ty = g.Tx + (int64_t)ny * (nx + 1);
   const double* Gi = a.G + off.g;

@@ -134,7 +134,7 @@ def test_basis_launch_shapes_and_options():
     assert sfb.basis_launch_shape(sfb.MIXED, 0, 0) == (256, 4, 1, 0, 0)
     assert sfb.basis_launch_shape(sfb.MIXED, 0, 1) == (256, 3, 2, 0, 0)
     assert sfb.basis_launch_shape(sfb.MIXED, 0, 2) == (256, 3, 1, 1, 0)   # tensor-core form
-    assert sfb.basis_launch_shape(sfb.MIXED, 0, 3) == (128, 8, 1, 0, 1)   # factor, then column chunks
+    assert sfb.basis_launch_shape(sfb.MIXED, 0, 3) == (128, 7, 1, 0, 1)   # factor, then column chunks
     assert sfb.basis_launch_shape(sfb.MIXED, 1, 0) == (256, 1, 2, 0, 0)
     assert sfb.basis_launch_shape(sfb.MIXED, 1, 1) == (256, 2, 1, 0, 0)
     assert sfb.basis_launch_shape(sfb.MIXED, 1, 2) == (128, 2, 1, 0, 1)   # no tensor-core form beyond 64 cells

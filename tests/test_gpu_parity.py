@@ -397,9 +397,10 @@ def test_balancing_preconditioner(case, prec):
     s.set_option("cg_precond", 3)
     s.moments_reset()
     # after a mixed build the bases are symmetric, and a floating item's null
-    # space the constants, only to the refinement's 1e-11: the balanced CG
-    # then stalls above 1e-13 on some points, and its tolerance is 1e-11
-    lam, it, rc = s.solve_host(y, wt, rtol=1e-13 if prec == 0 else 1e-11, max_it=5000, krylov=sfb.CG)
+    # space the constants, only to the refinement's stopping estimate of 1e-11
+    # (an estimate: single items stop a little above it): the balanced CG then
+    # stalls near 1e-11 on some points, and its tolerance is 1e-10
+    lam, it, rc = s.solve_host(y, wt, rtol=1e-13 if prec == 0 else 1e-10, max_it=5000, krylov=sfb.CG)
     assert rc == 0 and np.all(it > 0)
     tol = TOL[prec]
     for l in range(len(y)):
