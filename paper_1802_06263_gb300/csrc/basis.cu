@@ -25,9 +25,11 @@
 // The flux-basis epilogue projects the boundary fluxes of X back onto the
 // mortar space (Section 5.2 step 3): Phi[l][j] = -<u(xi_j).n, xi_l>.
 //
-// Layouts: X and Z are column-major per item ([R+1][n_cells]); in shared
-// memory the right-hand-side block is [nx][Cp] (Cp = R+1 rounded up to 4) so
-// the products G_b U read float4 rows of G_b (symmetric) and of U.
+// Layouts: X is column-major per item ([R+1][n_cells]); a block row of the
+// right-hand sides, in shared memory and in the Z store alike, is column-major
+// [Cp][np] (Cp = R+1 rounded up to 4, np = nx padded to 16), so the row loops
+// give a warp 32 consecutive cells of one column and the products G_b U read
+// 16-byte pieces of G_b (symmetric) rows and of U columns.
 #include <math.h>
 
 #include <algorithm>
@@ -195,9 +197,10 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
   // starts after the earlier chunks' (their column counts are multiples of 4)
   T* Zg = reinterpret_cast<T*>(a.Z) + off.z + (MODE == 2 ? (int64_t)ny * np * c0 : 0);
 
-  // smem: Gs[GB][np*np] | U region | Zs[np*Cp] | sc | dlo | dup | txh, the U region
-  // holding Us[np*Cp] in the solves and VT[kP*np] | W[kP*np] | Ablk[kP*kP]
-  // during the block inversions (never both at once)
+  // smem: Gs[GB][np*np] | U region | Zs[Cp][np] | sc | dlo | dup | txh | rbs,
+  // the U region holding Us[Cp][np] in the solves and VT[kP*np] | W[kP*np] |
+  // Ablk[kP*kP] during the block inversions (never both at once); rbs (FP64,
+  // [2][Cp]) the right-hand sides of a row's two end cells in the solves
   const int ureg = MODE == 2 ? np * Cp : max(np * Cp, 2 * kP * np + kP * kP);
   T* Gs0 = reinterpret_cast<T*>(smem_raw);
   T* Us = Gs0 + GB * np * np;
@@ -209,6 +212,7 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
   T* dlo = sc + np;
   T* dup = dlo + np;
   T* txh = dup + np;
+  double* rbs = reinterpret_cast<double*>(txh + np);
   uint32_t gph[2] = {0u, 0u}, zph = 0u;
 
   if (threadIdx.x == 0) {
@@ -335,18 +339,19 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
     }
     // first forward solve row: u_b = s_b B_b + dlo_b z_{b-1}
     if constexpr (MODE == 0)
-      for (int e = threadIdx.x; e < nx * C; e += blockDim.x) {
-        const int i = e % nx, c = e / nx;
+      for (int e = threadIdx.x; e < np * C; e += blockDim.x) {
+        const int c = e / np, i = e - c * np;
+        if (i >= nx) continue;
         T u = sc[i] * from_f64<T>(rhs_entry(S, g, a.proj, b, i, c + coff));
-        if (b > 0) u = fma(dlo[i], Zs[i * Cp + c], u);
-        Us[i * Cp + c] = u;
+        if (b > 0) u = fma(dlo[i], Zs[c * np + i], u);
+        Us[c * np + i] = u;
       }
     fence_async_shared();
     __syncthreads();
     SFB_MARK(2);
     if (GB > 0 && threadIdx.x == 0) bulk_store(Gg + (int64_t)b * np * np, Gs, gbytes);
     if constexpr (MODE == 0) {
-      gemm_g<T>(Gs, Us, Zs, false, np, Cp, C);
+      gemm_g<T>(Gs, Us, Zs, false, np, C);
       fence_async_shared();
       __syncthreads();
       SFB_MARK(3);
@@ -372,18 +377,31 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
   }
 
   // ---- 3./4. backward sweep, then refine with FP64 residuals --------------------------
-  // Row loops over the nx x C entries of a block row: the lanes of a warp take
-  // 8 consecutive cells of 4 consecutive columns (a lane group reads 64
-  // contiguous bytes of an X column; the [i][Cp] shared-memory entries of a
-  // warp fall in distinct banks when Cp = 4 mod 8) and each warp a contiguous
-  // run of these 32-entry tiles, column tile fastest. A lane's cell then
-  // changes a few times per row, its coefficients are loaded once per change,
-  // and no entry needs an integer division.
-  const int li = threadIdx.x & 7, lc = (threadIdx.x >> 3) & 3;
-  const int nct = (C + 3) >> 2, ntile = ((nx + 7) >> 3) * nct;
-  const int nwarp = (int)(blockDim.x >> 5), wrp = (int)(threadIdx.x >> 5);
-  const int tile0 = (int)((int64_t)wrp * ntile / nwarp), tile1 = (int)((int64_t)(wrp + 1) * ntile / nwarp);
-  const int ti0 = nct ? tile0 / nct : 0, tc0 = tile0 - ti0 * nct;
+  // Row loops over the nx x C entries of a block row: the 32 lanes of a warp
+  // take 32 consecutive cells of one column (a 256-byte run of an X column,
+  // consecutive words of the column-major shared-memory blocks) and the warps
+  // the (cell segment, column) tasks in turn, task k = (k mod nseg, k / nseg).
+  // When the segments divide the warps (nx <= 32, or 64 with an even number
+  // of warps, ...) a lane keeps one cell for the whole row and loads the
+  // cell's coefficients once.
+  const int lane = (int)(threadIdx.x & 31);
+  const int nseg = (nx + 31) >> 5, nwarp = (int)(blockDim.x >> 5), wrp = (int)(threadIdx.x >> 5);
+  const int seg0 = wrp % nseg, col0 = wrp / nseg;       // the warp's first task
+  const int dseg = nwarp % nseg, dcol = nwarp / nseg;   // the step between its tasks
+  // the two end cells of a row (rows 1 .. ny-2): their right-hand sides come
+  // from rbs, prefetched a row ahead as the operands of T_face * value
+  const int rbt = (int)threadIdx.x;
+  const int rb_side = rbt < 2 * C ? rbt / C : 0, rb_col = rbt < 2 * C ? rbt - rb_side * C : 0;
+  auto edge_operands = [&](int bb, double& t, double& v) {
+    const int sd = rb_side ? 1 : 3, cg = rb_col + coff;
+    t = Tx[bb * (nx + 1) + (rb_side ? nx : 0)];
+    v = 0.0;
+    if (cg < S.R) {
+      if (S.side_type[sd] == SIDE_IFACE) v = a.proj[S.proj_off[sd] + (int64_t)bb * S.R + cg];
+    } else if (S.side_type[sd] == SIDE_DIRICHLET) {
+      v = S.side_val[sd];
+    }
+  };
   double xref2 = 0.0, prev_corr = 0.0, est = 1.0, bnorm2 = 0.0;
   int n_done = 0;
   bool timeout = false, nonfinite = false;
@@ -400,6 +418,9 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
         prefetch_x_row(X, nc, nx, 0, C);
         if (ny > 1) prefetch_x_row(X, nc, nx, 1, C);
       }
+      const bool rb_thread = rbt < 2 * C && nx > 1;
+      double rb_t = 0.0, rb_v = 0.0;
+      if (rb_thread && ny > 2) edge_operands(1, rb_t, rb_v);
       for (int b = 0; b < ny; ++b) {
         const int cur = GB == 2 ? (b & 1) : 0;
         T* Gs = GB == 0 ? Gg + (int64_t)b * np * np : Gs0 + cur * np * np;
@@ -409,6 +430,11 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
           if (b + 1 < ny) { nsc = Sg[(b + 1) * nx + threadIdx.x]; ndl = DLg[(b + 1) * nx + threadIdx.x]; }
         }
         if (b + 2 < ny && !xzero) prefetch_x_row(X, nc, nx, b + 2, C);   // the residual of row b + 1 reads it
+        if (rb_thread && b >= 1 && b <= ny - 2) {
+          // an end cell's right-hand side: T_face * value (+ the source in column R)
+          rbs[rb_side * Cp + rb_col] = rb_col + coff < S.R ? rb_t * rb_v : fma(rb_t, rb_v, g.src);
+          if (b + 1 <= ny - 2) edge_operands(b + 1, rb_t, rb_v);
+        }
         __syncthreads();
         SFB_MARK(4);
         if (GB == 2 && threadIdx.x == 0 && b + 1 < ny) {
@@ -416,47 +442,78 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
           bulk_load(Gs0 + (cur ^ 1) * np * np, Gg + (int64_t)(b + 1) * np * np, gbytes, &gbar[cur ^ 1]);
         }
         {
-          // the lane's cell: its 5-point coefficients and row scalings
-          double dd = 0.0, tw = 0.0, te = 0.0, ts = 0.0, tn = 0.0;
-          T sci = T(0), dli = T(0);
-          bool inner = false;
-          int tcur = -1, ti = ti0, tc = tc0;
+          // rows 1 .. ny-2 (and nx > 1): every cell's five stencil FMAs without
+          // a branch, the end cells' right-hand sides from rbs and their
+          // missing neighbour's coefficient zero (its load then reads the end
+          // cell of an adjacent row, in bounds, times zero); rows 0 and ny-1
+          // take the general right-hand side and guarded neighbours
+          const bool edge_row = b == 0 || b == ny - 1 || nx == 1;
           const double* Tb = Tx + b * (nx + 1);
-#pragma unroll 2
-          for (int t = tile0; t < tile1; ++t) {
-            const int i = ti * 8 + li, c = tc * 4 + lc;
-            if (ti != tcur && i < nx) {
-              tcur = ti;
-              sci = sc[i];
-              dli = dlo[i];
-              inner = b > 0 && b < ny - 1 && i > 0 && i < nx - 1;
+          const double* xb = X + (int64_t)b * nx;
+          auto coeffs = [&](int i, double& dd, double& tw, double& te, double& ts, double& tn) {
+            dd = Dg[(int64_t)b * nx + i];
+            tw = i > 0 ? Tb[i] : 0.0;
+            te = i < nx - 1 ? Tb[i + 1] : 0.0;
+            ts = b > 0 ? Ty[b * nx + i] : 0.0;
+            tn = b < ny - 1 ? Ty[(b + 1) * nx + i] : 0.0;
+          };
+          auto entry = [&](int i, int c, double dd, double tw, double te, double ts, double tn, T sci, T dli) {
+            const double* xp = xb + (int64_t)c * nc + i;
+            double r;
+            // r = B - A x as five FP64 FMAs: B - D x, then + T x over the neighbours
+            if (!edge_row) {
+              r = (i == 0 || i == nx - 1) ? rbs[(i == 0 ? 0 : Cp) + c] : (c + coff < g.R ? 0.0 : g.src);
               if (!xzero) {
-                dd = Dg[(int64_t)b * nx + i];
-                tw = i > 0 ? Tb[i] : 0.0;
-                te = i < nx - 1 ? Tb[i + 1] : 0.0;
-                ts = b > 0 ? Ty[b * nx + i] : 0.0;
-                tn = b < ny - 1 ? Ty[(b + 1) * nx + i] : 0.0;
+                r = fma(-dd, xp[0], r);
+                r = fma(tw, xp[-1], r);
+                r = fma(te, xp[1], r);
+                r = fma(ts, xp[-nx], r);
+                r = fma(tn, xp[nx], r);
               }
-            }
-            if (i < nx && c < C) {
-              // r = B - A x as five FP64 FMAs: B - D x, then + T x over the neighbours
-              double r = inner ? (c + coff < g.R ? 0.0 : g.src) : rhs_boundary(S, g, a.proj, b, i, c + coff);
+            } else {
+              r = rhs_boundary(S, g, a.proj, b, i, c + coff);
               if (!xzero) {
-                const double* xp = X + (int64_t)c * nc + (int64_t)b * nx + i;
                 r = fma(-dd, xp[0], r);
                 if (i > 0) r = fma(tw, xp[-1], r);
                 if (i < nx - 1) r = fma(te, xp[1], r);
                 if (b > 0) r = fma(ts, xp[-nx], r);
                 if (b < ny - 1) r = fma(tn, xp[nx], r);
               }
-              const T rt = from_f64<T>(r);
-              const float rf = to_f32(rt);
-              rr = fmaf(rf, rf, rr);
-              T u = sci * rt;
-              if (b > 0) u = fma(dli, Zs[i * Cp + c], u);
-              Us[i * Cp + c] = u;
             }
-            if (++tc == nct) { tc = 0; ++ti; }
+            const T rt = from_f64<T>(r);
+            const float rf = to_f32(rt);
+            rr = fmaf(rf, rf, rr);
+            T u = sci * rt;
+            if (b > 0) u = fma(dli, Zs[c * np + i], u);
+            Us[c * np + i] = u;
+          };
+          double dd = 0.0, tw = 0.0, te = 0.0, ts = 0.0, tn = 0.0;
+          if (dseg == 0) {
+            const int i = seg0 * 32 + lane;
+            if (i < nx) {
+              if (!xzero) coeffs(i, dd, tw, te, ts, tn);
+              const T sci = sc[i], dli = dlo[i];
+#pragma unroll 2
+              for (int c = col0; c < C; c += dcol) entry(i, c, dd, tw, te, ts, tn, sci, dli);
+            }
+          } else {
+            int sg = seg0, c = col0, scur = -1, i = 0;
+            T sci = T(0), dli = T(0);
+            while (c < C) {
+              if (sg != scur) {
+                scur = sg;
+                i = sg * 32 + lane;
+                if (i < nx) {
+                  if (!xzero) coeffs(i, dd, tw, te, ts, tn);
+                  sci = sc[i];
+                  dli = dlo[i];
+                }
+              }
+              if (i < nx) entry(i, c, dd, tw, te, ts, tn, sci, dli);
+              sg += dseg;
+              c += dcol;
+              if (sg >= nseg) { sg -= nseg; ++c; }
+            }
           }
         }
         SFB_MARK(8);
@@ -469,7 +526,7 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
         }
         if (__syncthreads_or(!ok)) { timeout = true; break; }
         SFB_MARK(5);
-        gemm_g<T>(Gs, Us, Zs, false, np, Cp, C);
+        gemm_g<T>(Gs, Us, Zs, false, np, C);
         fence_async_shared();
         __syncthreads();
         SFB_MARK(6);
@@ -538,35 +595,50 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
       }
       if (__syncthreads_or(!ok)) { timeout = true; break; }
       SFB_MARK(9);
-      if (b < ny - 1) gemm_g<T>(Gs, Us, Zs, true, np, Cp, C);
+      if (b < ny - 1) gemm_g<T>(Gs, Us, Zs, true, np, C);
       __syncthreads();
       SFB_MARK(10);
-      // x_b += s d_b and Us = dup .* d_b for row b - 1: the X entries of four
-      // tiles are loaded before any of them is stored, so that the loads overlap
+      // x_b += s d_b and Us = dup .* d_b for row b - 1; with a fixed cell per
+      // lane the X entries of four columns are loaded before any of them is
+      // stored, so that the loads overlap
       {
-        int ti = ti0, tc = tc0;
-        for (int t = tile0; t < tile1; t += 4) {
-          double xo[4];
-          int ii[4], cc[4];
+        double* xb = X + (int64_t)b * nx;
+        auto upd = [&](int i, int c, T sci, T dpi, double xo) {
+          const T z = Zs[c * np + i];
+          const T dt = sci * z;
+          const float df = to_f32(dt);
+          dn2f = fmaf(df, df, dn2f);
+          const double xn = it == 0 ? to_f64(dt) : xo + to_f64(dt);
+          nonfinite |= ((__double2hiint(xn) >> 20) & 0x7ff) == 0x7ff;
+          xb[(int64_t)c * nc + i] = xn;
+          if (b > 0) Us[c * np + i] = dpi * z;
+        };
+        if (dseg == 0) {
+          const int i = seg0 * 32 + lane;
+          if (i < nx) {
+            const T sci = sc[i], dpi = dup[i];
+            for (int c = col0; c < C; c += 4 * dcol) {
+              double xo[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            ii[u] = t + u < tile1 ? ti * 8 + li : nx;
-            cc[u] = tc * 4 + lc;
-            xo[u] = (it > 0 && ii[u] < nx && cc[u] < C) ? X[(int64_t)cc[u] * nc + (int64_t)b * nx + ii[u]] : 0.0;
-            if (++tc == nct) { tc = 0; ++ti; }
+              for (int u = 0; u < 4; ++u) {
+                const int cu = c + u * dcol;
+                xo[u] = (it > 0 && cu < C) ? xb[(int64_t)cu * nc + i] : 0.0;
+              }
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int cu = c + u * dcol;
+                if (cu < C) upd(i, cu, sci, dpi, xo[u]);
+              }
+            }
           }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int i = ii[u], c = cc[u];
-            if (i >= nx || c >= C) continue;
-            const T z = Zs[i * Cp + c];
-            const T dt = sc[i] * z;
-            const float df = to_f32(dt);
-            dn2f = fmaf(df, df, dn2f);
-            const double xn = it == 0 ? to_f64(dt) : xo[u] + to_f64(dt);
-            nonfinite |= ((__double2hiint(xn) >> 20) & 0x7ff) == 0x7ff;
-            X[(int64_t)c * nc + (int64_t)b * nx + i] = xn;
-            if (b > 0) Us[i * Cp + c] = dup[i] * z;
+        } else {
+          int sg = seg0, c = col0;
+          while (c < C) {
+            const int i = sg * 32 + lane;
+            if (i < nx) upd(i, c, sc[i], dup[i], it > 0 ? xb[(int64_t)c * nc + i] : 0.0);
+            sg += dseg;
+            c += dcol;
+            if (sg >= nseg) { sg -= nseg; ++c; }
           }
         }
       }
@@ -779,7 +851,8 @@ size_t basis_smem(int max_nx, int max_cols, int gb, int mode = 0) {
   constexpr size_t kP = panel_of<T>();
   const size_t np = (max_nx + kPanel - 1) & ~size_t(kPanel - 1);
   const size_t ureg = mode == 2 ? np * cp : std::max(np * cp, 2 * kP * np + kP * kP);
-  return sizeof(T) * (gb * np * np + ureg + np * cp + 4 * np);
+  // + the two end cells' right-hand sides of a row in the solves (FP64)
+  return sizeof(T) * (gb * np * np + ureg + np * cp + 4 * np) + (mode == 1 ? 0 : 2 * cp * sizeof(double));
 }
 
 template <typename T, int MT, int NT, int MINB, int GB, int MODE = 0>

@@ -64,71 +64,80 @@ __device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
   v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
 }
 
-// out[i][c] (+)= sum_k G[i][k] U[k][c] for i < np, c < C, with G symmetric
-// (row k of G read as column k). G has pitch np, U and out pitch Cp; np and
-// Cp are multiples of 4 and both arrays start 16-byte aligned, so the 4-wide
-// loads are aligned. Columns [0, C & ~3) use 4 x 4 register tiles, the
-// remaining 1-3 columns 4 x 1 tiles, so R + 1 = 4q + 1 columns cost only a
-// sliver more than 4q.
+// 4 consecutive values to a 16-byte aligned address.
+__device__ __forceinline__ void store4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(double* p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// out[c][i] (+)= sum_k G[i][k] U[c][k] for i < np, c < C. The right-hand-side
+// blocks U and out are column-major with pitch np (entry (i, c) at c * np + i);
+// G is symmetric with pitch np, so row k of G is read as its column k. np is a
+// multiple of 16 and all three arrays start 16-byte aligned, so every 4-wide
+// access is aligned. A thread owns a tile of 4 cells by 4 columns (cells
+// fastest across threads: a warp's G reads are contiguous and its U reads
+// broadcasts); the last C mod 4 columns form tiles of 4 cells by 1-3 columns.
+// Per KS = 16 / sizeof(T) steps of k a thread reads KS rows of G and 4
+// column pieces of U, 16 bytes each, for 16 KS FMAs.
+// KS consecutive values (one 16-byte load) from a 16-byte aligned address.
+__device__ __forceinline__ void load_ks(const float* p, float (&v)[4]) { load4(p, v); }
+__device__ __forceinline__ void load_ks(const double* p, double (&v)[2]) {
+  const double2 q = *reinterpret_cast<const double2*>(p);
+  v[0] = q.x; v[1] = q.y;
+}
+
 template <typename T>
 __device__ __forceinline__ void gemm_g(const T* __restrict__ G, const T* __restrict__ U, T* out, bool add_base,
-                                       int np, int Cp, int C) {
+                                       int np, int C) {
+  constexpr int KS = 16 / (int)sizeof(T);   // steps of k per 16-byte piece of a U column
   const int nrt = np >> 2;
   const int Cm = C & ~3;
-  const int nct = Cm >> 2;
-  const int nmain = nrt * nct;
+  const int nmain = nrt * (Cm >> 2);
   const int rc = C - Cm;
   const int ntot = nmain + (rc ? nrt : 0);
   for (int t = threadIdx.x; t < ntot; t += blockDim.x) {
-    if (t < nmain) {
-      const int i0 = (t / nct) * 4, c0 = (t % nct) * 4;
-      T acc[4][4];
+    const bool main_tile = t < nmain;
+    const int tt = main_tile ? t : t - nmain;
+    const int c0 = main_tile ? (tt / nrt) * 4 : Cm, i0 = (tt - (tt / nrt) * nrt) * 4;
+    const int nq = main_tile ? 4 : rc;
+    T acc[4][4];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+    for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[a][q] = T(0);
-#pragma unroll 2
-      for (int k = 0; k < np; ++k) {
-        T gv[4], uv[4];
-        load4(G + k * np + i0, gv);
-        load4(U + k * Cp + c0, uv);
+      for (int a = 0; a < 4; ++a) acc[q][a] = T(0);
+    const T* gp = G + i0;
+    const T* up = U + c0 * np;
+    for (int k = 0; k < np; k += KS) {
+      T gv[KS][4];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+      for (int kk = 0; kk < KS; ++kk) load4(gp + (k + kk) * np, gv[kk]);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) acc[a][q] = fma(gv[a], uv[q], acc[a][q]);
-      }
+      for (int q = 0; q < 4; ++q) {
+        if (q < nq) {
+          T uv[KS];
+          load_ks(up + q * np + k, uv);
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        T* o = out + (i0 + a) * Cp + c0;
+          for (int kk = 0; kk < KS; ++kk)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) o[q] = (add_base ? o[q] : T(0)) + acc[a][q];
-      }
-    } else {
-      const int i0 = (t - nmain) * 4;
-      T acc[4][3];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) acc[a][q] = T(0);
-      for (int k = 0; k < np; ++k) {
-        T gv[4];
-        load4(G + k * np + i0, gv);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          if (q >= rc) break;
-          const T u = U[k * Cp + Cm + q];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) acc[a][q] = fma(gv[a], u, acc[a][q]);
+            for (int a = 0; a < 4; ++a) acc[q][a] = fma(gv[kk][a], uv[kk], acc[q][a]);
         }
       }
+    }
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+    for (int q = 0; q < 4; ++q) {
+      if (q < nq) {
+        T* o = out + (c0 + q) * np + i0;
+        if (add_base) {
+          T base[4];
+          load4(o, base);
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          if (q >= rc) break;
-          T* o = out + (i0 + a) * Cp + Cm + q;
-          *o = (add_base ? *o : T(0)) + acc[a][q];
+          for (int a = 0; a < 4; ++a) acc[q][a] += base[a];
         }
+        store4(o, acc[q]);
+      }
     }
   }
 }
