@@ -493,8 +493,45 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
             if (i < nx) {
               if (!xzero) coeffs(i, dd, tw, te, ts, tn);
               const T sci = sc[i], dli = dlo[i];
+              if (edge_row) {
+                for (int c = col0; c < C; c += dcol) entry(i, c, dd, tw, te, ts, tn, sci, dli);
+              } else {
+                // the uniform conditions hoisted: an end cell reads its right-hand
+                // side from rbs, the others the column's constant (every lane
+                // loads from rbs, in bounds, and selects)
+                const bool end_cell = i == 0 || i == nx - 1;
+                const double* rbp = rbs + (i == nx - 1 ? Cp : 0);
+                const double* xp = xb + (int64_t)col0 * nc + i;
+                const int64_t xs = (int64_t)dcol * nc;
+                int zo = col0 * np + i;
+                const int zs = dcol * np;
+                if (xzero) {
+                  for (int c = col0; c < C; c += dcol, zo += zs) {
+                    const double rbv = rbp[c];
+                    const double r = end_cell ? rbv : (c + coff < g.R ? 0.0 : g.src);
+                    const T rt = from_f64<T>(r);
+                    const float rf = to_f32(rt);
+                    rr = fmaf(rf, rf, rr);
+                    Us[zo] = fma(dli, Zs[zo], sci * rt);
+                  }
+                } else {
 #pragma unroll 2
-              for (int c = col0; c < C; c += dcol) entry(i, c, dd, tw, te, ts, tn, sci, dli);
+                  for (int c = col0; c < C; c += dcol, xp += xs, zo += zs) {
+                    const double rbv = rbp[c];
+                    double r = end_cell ? rbv : (c + coff < g.R ? 0.0 : g.src);
+                    // r = B - A x as five FP64 FMAs: B - D x, then + T x over the neighbours
+                    r = fma(-dd, xp[0], r);
+                    r = fma(tw, xp[-1], r);
+                    r = fma(te, xp[1], r);
+                    r = fma(ts, xp[-nx], r);
+                    r = fma(tn, xp[nx], r);
+                    const T rt = from_f64<T>(r);
+                    const float rf = to_f32(rt);
+                    rr = fmaf(rf, rf, rr);
+                    Us[zo] = fma(dli, Zs[zo], sci * rt);
+                  }
+                }
+              }
             }
           } else {
             int sg = seg0, c = col0, scur = -1, i = 0;
@@ -616,18 +653,27 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
         if (dseg == 0) {
           const int i = seg0 * 32 + lane;
           if (i < nx) {
+            // dup is zero on row 0, so its product input is written there too
             const T sci = sc[i], dpi = dup[i];
-            for (int c = col0; c < C; c += 4 * dcol) {
+            double* xp = xb + (int64_t)col0 * nc + i;
+            const int64_t xs = (int64_t)dcol * nc;
+            int zo = col0 * np + i;
+            const int zs = dcol * np;
+            for (int c = col0; c < C; c += 4 * dcol, xp += 4 * xs, zo += 4 * zs) {
               double xo[4];
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const int cu = c + u * dcol;
-                xo[u] = (it > 0 && cu < C) ? xb[(int64_t)cu * nc + i] : 0.0;
-              }
+              for (int u = 0; u < 4; ++u) xo[u] = (it > 0 && c + u * dcol < C) ? xp[u * xs] : 0.0;
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
-                const int cu = c + u * dcol;
-                if (cu < C) upd(i, cu, sci, dpi, xo[u]);
+                if (c + u * dcol >= C) break;
+                const T z = Zs[zo + u * zs];
+                const T dt = sci * z;
+                const float df = to_f32(dt);
+                dn2f = fmaf(df, df, dn2f);
+                const double xn = it == 0 ? to_f64(dt) : xo[u] + to_f64(dt);
+                nonfinite |= ((__double2hiint(xn) >> 20) & 0x7ff) == 0x7ff;
+                xp[u * xs] = xn;
+                Us[zo + u * zs] = dpi * z;
               }
             }
           }

@@ -89,57 +89,78 @@ __device__ __forceinline__ void load_ks(const double* p, double (&v)[2]) {
   v[0] = q.x; v[1] = q.y;
 }
 
-template <typename T>
-__device__ __forceinline__ void gemm_g(const T* __restrict__ G, const T* __restrict__ U, T* out, bool add_base,
-                                       int np, int C) {
+// One thread's tile of the product: cells i0..i0+3 of columns c0..c0+NQ-1.
+// NP > 0 fixes np at compile time, so every shared-memory offset inside the
+// k loop is an immediate.
+template <typename T, int NQ, int NP>
+__device__ __forceinline__ void gemm_tile(const T* __restrict__ G, const T* __restrict__ U, T* out, bool add_base,
+                                          int np_rt, int i0, int c0) {
   constexpr int KS = 16 / (int)sizeof(T);   // steps of k per 16-byte piece of a U column
-  const int nrt = np >> 2;
+  const int np = NP > 0 ? NP : np_rt;
+  T acc[NQ][4];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) acc[q][a] = T(0);
+  const T* gp = G + i0;
+  const T* up = U + c0 * np;
+#pragma unroll 2
+  for (int k = 0; k < np; k += KS) {
+    T gv[KS][4];
+#pragma unroll
+    for (int kk = 0; kk < KS; ++kk) load4(gp + kk * np, gv[kk]);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      T uv[KS];
+      load_ks(up + q * np, uv);
+#pragma unroll
+      for (int kk = 0; kk < KS; ++kk)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[q][a] = fma(gv[kk][a], uv[kk], acc[q][a]);
+    }
+    gp += KS * np;
+    up += KS;
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    T* o = out + (c0 + q) * np + i0;
+    if (add_base) {
+      T base[4];
+      load4(o, base);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) acc[q][a] += base[a];
+    }
+    store4(o, acc[q]);
+  }
+}
+
+template <typename T, int NP>
+__device__ __forceinline__ void gemm_g_np(const T* __restrict__ G, const T* __restrict__ U, T* out, bool add_base,
+                                          int np, int C) {
+  const int nrt = (NP > 0 ? NP : np) >> 2;
   const int Cm = C & ~3;
   const int nmain = nrt * (Cm >> 2);
   const int rc = C - Cm;
   const int ntot = nmain + (rc ? nrt : 0);
   for (int t = threadIdx.x; t < ntot; t += blockDim.x) {
-    const bool main_tile = t < nmain;
-    const int tt = main_tile ? t : t - nmain;
-    const int c0 = main_tile ? (tt / nrt) * 4 : Cm, i0 = (tt - (tt / nrt) * nrt) * 4;
-    const int nq = main_tile ? 4 : rc;
-    T acc[4][4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int a = 0; a < 4; ++a) acc[q][a] = T(0);
-    const T* gp = G + i0;
-    const T* up = U + c0 * np;
-    for (int k = 0; k < np; k += KS) {
-      T gv[KS][4];
-#pragma unroll
-      for (int kk = 0; kk < KS; ++kk) load4(gp + (k + kk) * np, gv[kk]);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (q < nq) {
-          T uv[KS];
-          load_ks(up + q * np + k, uv);
-#pragma unroll
-          for (int kk = 0; kk < KS; ++kk)
-#pragma unroll
-            for (int a = 0; a < 4; ++a) acc[q][a] = fma(gv[kk][a], uv[kk], acc[q][a]);
-        }
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (q < nq) {
-        T* o = out + (c0 + q) * np + i0;
-        if (add_base) {
-          T base[4];
-          load4(o, base);
-#pragma unroll
-          for (int a = 0; a < 4; ++a) acc[q][a] += base[a];
-        }
-        store4(o, acc[q]);
-      }
+    if (t < nmain) {
+      const int ct = t / nrt;
+      gemm_tile<T, 4, NP>(G, U, out, add_base, np, (t - ct * nrt) * 4, ct * 4);
+    } else {
+      const int i0 = (t - nmain) * 4;
+      if (rc == 1) gemm_tile<T, 1, NP>(G, U, out, add_base, np, i0, Cm);
+      else if (rc == 2) gemm_tile<T, 2, NP>(G, U, out, add_base, np, i0, Cm);
+      else gemm_tile<T, 3, NP>(G, U, out, add_base, np, i0, Cm);
     }
   }
+}
+
+template <typename T>
+__device__ __forceinline__ void gemm_g(const T* __restrict__ G, const T* __restrict__ U, T* out, bool add_base,
+                                       int np, int C) {
+  if (np == 64) gemm_g_np<T, 64>(G, U, out, add_base, np, C);
+  else if (np == 128) gemm_g_np<T, 128>(G, U, out, add_base, np, C);
+  else gemm_g_np<T, 0>(G, U, out, add_base, np, C);
 }
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
