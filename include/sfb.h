@@ -455,6 +455,16 @@ sfb_status sfb_build_basis_item_noalloc(sfb_ctx* ctx, int32_t sub, int32_t k, in
  *                    workspace, refinement options and shapes stay the same;
  *                    plain launches when the context stream is itself being
  *                    captured. 0: plain launches (1);
+ *   "basis_persistent"  FP32 builds whose size classes both run a split
+ *                    shape: 1 runs every item of both classes in one
+ *                    persistent launch (factor tasks, then column-chunk tasks
+ *                    that wait, bounded, on their item's factor); 0 one
+ *                    launch sequence per class; -1 the autotuner times both
+ *                    and keeps the faster (-1);
+ *   "basis_pipe_groups"  a split shape's class runs its items in this many
+ *                    groups, 1..4: the factor launches of the groups in
+ *                    sequence and each group's chunk launch after its factor,
+ *                    on a second stream (1);
  *   "cg_test_barrier_timeout"  test hook: 1 makes CTA 0 of the next one-launch
  *                    CG skip its first grid barrier, so that the other CTAs'
  *                    waits run out (1 s). The solve returns SFB_ERR_TIMEOUT and

@@ -993,7 +993,7 @@ cudaError_t shape_dispatch(const BasisArgs* a, bool wide, int shape, int max_nx,
       return ctas ? basis_tc_ctas(max_nx, max_cols, ctas) : launch_basis_tc(*a, max_nx, max_cols, refine, st);
     if (!wide && shape == 3)
       return ctas ? occupancy_of<T, 1, 128, 7, 1, 2>(basis_smem<T>(max_nx, max_cols, 1, 2), ctas)
-                  : launch_split<T, 1, 256, 4, 1, 1, 128, 7, 1>(*a, max_nx, max_cols, refine, st, part);
+                  : launch_split<T, 2, 128, 5, 1, 1, 128, 7, 1>(*a, max_nx, max_cols, refine, st, part);
     if (wide && shape == 2)
       return ctas ? occupancy_of<T, 1, 128, 2, 1, 2>(basis_smem<T>(max_nx, max_cols, 1, 2), ctas)
                   : launch_split<T, 4, 256, 2, 1, 1, 128, 2, 1>(*a, max_nx, max_cols, refine, st, part);

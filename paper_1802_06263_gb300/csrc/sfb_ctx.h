@@ -209,7 +209,7 @@ struct sfb_ctx {
   // split launch shapes: per size class two streams for the solve launches of
   // alternate item groups, and the events that order each group's solves
   // after its factor (see sfb_build_stochastic_basis)
-  static constexpr int kPipeGroups = 2;
+  static constexpr int kPipeGroups = 4;   // at most (option "basis_pipe_groups")
   cudaStream_t pipe_stream[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   cudaEvent_t pipe_ev[2][kPipeGroups + 3] = {};
   cudaStream_t gcap = nullptr;          // private stream on which the basis graph is captured
@@ -245,6 +245,7 @@ struct sfb_ctx {
   // the persistent basis launch: option (-1 autotuned, 0 off, 1 on), the
   // autotuner's choice and timings (per-class launches, persistent launch)
   int opt_basis_persistent = -1;
+  int opt_pipe_groups = 1;
   bool bpersist[3] = {false, false, false}, bpersist_tuned[3] = {false, false, false};
   double bpersist_ms[3][2] = {};
   double btune_ms[3][2][4] = {};
@@ -254,9 +255,10 @@ struct sfb_ctx {
     double refine_tol = 0.0;
     int shape[2] = {0, 0};
     int persist = 0;
+    int groups = 0;
     bool operator==(const GraphKey& o) const {
       return ws == o.ws && refine == o.refine && refine_tol == o.refine_tol && shape[0] == o.shape[0] &&
-             shape[1] == o.shape[1] && persist == o.persist;
+             shape[1] == o.shape[1] && persist == o.persist && groups == o.groups;
     }
   };
   cudaGraphExec_t bgraph[3] = {nullptr, nullptr, nullptr};

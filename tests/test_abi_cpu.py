@@ -148,7 +148,8 @@ def test_basis_launch_shapes_and_options():
     assert sfb.basis_launch_shape(5, 0, 0) is None
     s = sfb.Solver(W.tiny())
     for name, ok, bad in (("basis_autotune", (0, 1), (2, -1)), ("basis_graph", (0, 1), (0.5, 3)),
-                          ("basis_shape", (0, 1, 2, 3), (4, 1.5, -1)), ("basis_persistent", (-1, 0, 1), (2, 0.5))):
+                          ("basis_shape", (0, 1, 2, 3), (4, 1.5, -1)), ("basis_persistent", (-1, 0, 1), (2, 0.5)),
+                          ("basis_pipe_groups", (1, 2, 3, 4), (0, 5, 1.5))):
         for v in ok:
             s.set_option(name, v)
         for v in bad:

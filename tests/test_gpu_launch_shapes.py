@@ -68,6 +68,24 @@ def test_every_launch_shape_builds_the_same_basis(prec):
                 continue
             assert rel(phi, phi0) < 1e-12 and rel(X, X0) < 1e-12, (v, key)
             assert np.abs(g - g0).max() <= 1e-12 * max(1.0, np.abs(g0).max()), (v, key)
+    # a split shape's pipeline groups run the same chunks: the same bits, and
+    # two launches (factor, chunks) per group
+    if prec == sfb.MIXED:
+        s.set_option("basis_shape", 3)
+        s.build_basis(prec)
+        base = _items(s)
+        n1 = s.launch_count()
+        s.build_basis(prec)
+        per_build = s.launch_count() - n1
+        for groups in (2, 4):
+            s.set_option("basis_pipe_groups", groups)
+            n0 = s.launch_count()
+            st = s.build_basis(prec)
+            assert st["n_not_converged"] == 0 and st["launch_shape"] == [0, 3]
+            assert s.launch_count() - n0 == per_build + 2 * (groups - 1)
+            for key, (phi, g, X) in _items(s).items():
+                assert np.array_equal(X, base[key][2]) and np.array_equal(phi, base[key][0]), (groups, key)
+        s.set_option("basis_pipe_groups", 1)
     # the persistent launch (both classes' items as tasks of one launch)
     if prec == sfb.MIXED:
         s.set_option("basis_shape", 0)
