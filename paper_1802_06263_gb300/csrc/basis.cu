@@ -74,7 +74,7 @@ __device__ __forceinline__ void blocked_sweep_w0(T (&areg)[MT][4][4], int np, in
           if (lane == 0) *bad = 1;
           piv = T(1);
         }
-        const T inv = T(1) / piv;
+        const T inv = rcp_rn(piv);
         T nv[(kP * kP + 31) / 32];
 #pragma unroll
         for (int r = 0; r < (kP * kP + 31) / 32; ++r) {
@@ -402,6 +402,11 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
       v = S.side_val[sd];
     }
   };
+  // the bulk copies of the solves are issued (and their groups waited on) by
+  // lane 0 of the last warp, which holds no product tile and no row set-up
+  // work in the chunk shapes, so that the copies start while the other
+  // threads set up the next row
+  const unsigned tma = blockDim.x - 32;
   double xref2 = 0.0, prev_corr = 0.0, est = 1.0, bnorm2 = 0.0;
   int n_done = 0;
   bool timeout = false, nonfinite = false;
@@ -411,7 +416,7 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
     const bool xzero = MODE == 2 && it == 0;
     if (it > 0 || MODE == 2) {
       // forward sweep: r_b = B_b - (A x)_b in FP64; u_b = s_b r_b + dlo_b z_{b-1}
-      if (GB > 0 && threadIdx.x == 0) { fence_async_shared(); bulk_load(Gs0, Gg, gbytes, &gbar[0]); }
+      if (GB > 0 && threadIdx.x == tma) { fence_async_shared(); bulk_load(Gs0, Gg, gbytes, &gbar[0]); }
       // row scalings of the next row travel in registers while a row runs
       T nsc = threadIdx.x < nx ? Sg[threadIdx.x] : T(0), ndl = threadIdx.x < nx ? DLg[threadIdx.x] : T(0);
       if (!xzero) {
@@ -437,7 +442,7 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
         }
         __syncthreads();
         SFB_MARK(4);
-        if (GB == 2 && threadIdx.x == 0 && b + 1 < ny) {
+        if (GB == 2 && threadIdx.x == tma && b + 1 < ny) {
           fence_async_shared();
           bulk_load(Gs0 + (cur ^ 1) * np * np, Gg + (int64_t)(b + 1) * np * np, gbytes, &gbar[cur ^ 1]);
         }
@@ -555,7 +560,7 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
         }
         SFB_MARK(8);
         // G_b present, and the store that reads Zs finished
-        if (threadIdx.x == 0) bulk_wait_read();
+        if (threadIdx.x == tma) bulk_wait_read();
         bool ok = true;
         if (GB > 0) {
           ok = mbar_wait(&gbar[cur], gph[cur]);
@@ -567,12 +572,12 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
         fence_async_shared();
         __syncthreads();
         SFB_MARK(6);
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == tma) {
           bulk_store(Zg + (int64_t)b * np * Cp, Zs, zbytes);
           if (GB == 1 && b + 1 < ny) { fence_async_shared(); bulk_load(Gs0, Gg + (int64_t)(b + 1) * np * np, gbytes, &gbar[0]); }
         }
       }
-      if (threadIdx.x == 0) {
+      if (threadIdx.x == tma) {
         bulk_wait_all();
         fence_async_global();
       }
@@ -597,7 +602,7 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
     // coupling of that row to the one below). G_{b-1} is prefetched while row b
     // runs (two G buffers).
     float dn2f = 0.f;
-    if (GB == 2 && threadIdx.x == 0 && ny >= 2) {
+    if (GB == 2 && threadIdx.x == tma && ny >= 2) {
       fence_async_shared();
       bulk_load(Gs0, Gg + (int64_t)(ny - 2) * np * np, gbytes, &gbar[0]);
     }
@@ -614,7 +619,7 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
       }
       if (it > 0) prefetch_x_row(X, nc, nx, b, C);   // updated after the product below
       SFB_MARK(7);
-      if (threadIdx.x == 0) {
+      if (threadIdx.x == tma) {
         fence_async_shared();
         if (b < ny - 1) {
           if (GB == 2 && b >= 1)   // prefetch G_{b-1}
@@ -717,7 +722,7 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
   }
   if (timeout) {
     // give the copies in flight a bounded chance to land before the CTA exits
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == tma) {
       if (GB > 0) mbar_wait(&gbar[0], gph[0]);
       mbar_wait(&gbar[1], gph[1]);
       mbar_wait(&zbar, zph);

@@ -82,6 +82,11 @@ __device__ __forceinline__ void store4(double* p, const double (&v)[4]) {
 // broadcasts); the last C mod 4 columns form tiles of 4 cells by 1-3 columns.
 // Per KS = 16 / sizeof(T) steps of k a thread reads KS rows of G and 4
 // column pieces of U, 16 bytes each, for 16 KS FMAs.
+// 1 / x correctly rounded (the value of the IEEE division 1 / x), by the
+// reciprocal intrinsics rather than the division sequence.
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+
 // KS consecutive values (one 16-byte load) from a 16-byte aligned address.
 __device__ __forceinline__ void load_ks(const float* p, float (&v)[4]) { load4(p, v); }
 __device__ __forceinline__ void load_ks(const double* p, double (&v)[2]) {
@@ -316,7 +321,7 @@ __device__ __forceinline__ void blocked_sweep(T (&areg)[MT][4][4], int np, int n
         if (lane == 0 && warp == 0) *bad = 1;
         piv = T(1);
       }
-      const T inv = T(1) / piv;
+      const T inv = rcp_rn(piv);
       const T colk = row[kk];
 #pragma unroll
       for (int q = 0; q < kP; ++q) {
