@@ -285,11 +285,14 @@ __global__ void bjacobi_setup_kernel(IfaceArgs a) {
       col[i] = v;
     }
   }
+  // stored column-major: entry (i, j) of the inverse at j * n + i, so that
+  // the lanes of an apply, which take consecutive rows i, read consecutive
+  // words for each j
   if (lane < n) {
     float* M = a.minv + l * a.minv_ld + a.if_moff[e];
 #pragma unroll
     for (int i = 0; i < kBlkMax; ++i)
-      if (i < n) M[i * n + lane] = -col[i];
+      if (i < n) M[lane * n + i] = -col[i];
   }
 }
 
@@ -298,10 +301,10 @@ __global__ void bjacobi_setup_kernel(IfaceArgs a) {
 __device__ __forceinline__ double bjacobi_apply(const IfaceArgs& a, int64_t l, const float* stage, int d) {
   const int e = a.dof_if[d];
   const int n = a.if_n[e], d0 = a.if_off[e], i = d - d0;
-  const float* M = a.minv + l * a.minv_ld + a.if_moff[e] + i * n;
+  const float* M = a.minv + l * a.minv_ld + a.if_moff[e] + i;   // column-major
   float z = 0.f;
-  for (int j = 0; j < n; ++j) z = fmaf(M[j], stage[d0 + j], z);
-  return (double)z;
+  for (int j = 0; j < n; ++j) z = fmaf(M[j * n], stage[d0 + j], z);
+  return f32_to_f64_bits(z);
 }
 
 // With the Jacobi preconditioner dinv = 1 / diag(S^l), z = dinv r, p = z and
@@ -769,9 +772,9 @@ __device__ __forceinline__ double precond64(const IfaceArgs& a, int64_t l, const
   if (a.minv) {
     const int e = a.dof_if[d];
     const int n = a.if_n[e], d0 = a.if_off[e], i = d - d0;
-    const float* M = a.minv + l * a.minv_ld + a.if_moff[e] + i * n;
+    const float* M = a.minv + l * a.minv_ld + a.if_moff[e] + i;   // column-major
     double z = 0.0;
-    for (int j = 0; j < n; ++j) z = fma(f32_to_f64_bits(M[j]), v[d0 + j], z);
+    for (int j = 0; j < n; ++j) z = fma(f32_to_f64_bits(M[j * n]), v[d0 + j], z);
     return z;
   }
   if (a.dinv) return a.dinv[l * a.n_lambda + d] * v[d];
@@ -788,9 +791,9 @@ __device__ __forceinline__ double precond_t(const IfaceArgs& a, int64_t l, const
   if (a.minv) {
     const int e = a.dof_if[d];
     const int n = a.if_n[e], d0 = a.if_off[e], i = d - d0;
-    const float* M = a.minv + l * a.minv_ld + a.if_moff[e] + i * n;
+    const float* M = a.minv + l * a.minv_ld + a.if_moff[e] + i;   // column-major
     float z = 0.f;
-    for (int j = 0; j < n; ++j) z = fmaf(M[j], v[d0 + j], z);
+    for (int j = 0; j < n; ++j) z = fmaf(M[j * n], v[d0 + j], z);
     return f32_to_f64_bits(z);
   }
   if (a.dinv) return f32_to_f64_bits(f64_to_f32_bits(a.dinv[l * a.n_lambda + d]) * v[d]);
@@ -1088,15 +1091,21 @@ __device__ bool grid_sync(const PcgCtl& c, unsigned& gen) {
       atomicExch(&c.bar[0], 0u);
       st_release(&c.bar[1], target);
     } else {
+      // a tight spin on the release flag first; the abort flag and the clock
+      // are read every 32 polls, and the spin backs off to short sleeps only
+      // after a few hundred polls
       const unsigned long long t0 = global_ns();
+      unsigned polls = 0;
       while (ld_acquire(&c.bar[1]) != target) {
-        if (*((volatile int*)c.abort)) { ok = 0; break; }
-        if (global_ns() - t0 > kBarrierNs) {
-          atomicExch(c.abort, 1);
-          ok = 0;
-          break;
+        if ((++polls & 31u) == 0) {
+          if (*((volatile int*)c.abort)) { ok = 0; break; }
+          if (global_ns() - t0 > kBarrierNs) {
+            atomicExch(c.abort, 1);
+            ok = 0;
+            break;
+          }
         }
-        __nanosleep(20);
+        if (polls > 512) __nanosleep(32);
       }
     }
     if (*((volatile int*)c.abort)) ok = 0;
