@@ -391,8 +391,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(n_pts * (s.n_lambda * 8 + 4) + mom_bytes)},
         "clocks": clk,
         "roofline": dict({"bound": "alu", "kernel": "basis_kernel<float> (mixed form; every launch of the basis "
-                                                 "build, the autotuned shape's: two factor and two solve "
-                                                 "launches for the split shape)", "unit": "TFLOP/s",
+                                                 "build, the autotuned shape's: a factor launch and a "
+                                                 "column-chunk solve launch for the split shape)", "unit": "TFLOP/s",
                           "traffic": traffic,
                           "traffic_over_algorithmic_bytes": (traffic / x_out_bytes) if traffic else None,
                           "algorithmic_bytes": x_out_bytes, "kernel_ms": k_mixed,
