@@ -331,10 +331,11 @@ sfb_status sfb_build_stochastic_basis(sfb_ctx* ctx, int32_t prec, sfb_basis_stat
  * split into two TF32 parts and FP32 accumulation, the block inverses fed by
  * TMA tensor copies), and whether it is split (split = 1: narrow shape 3 and
  * wide shape 2 of the FP32 factor). A split shape factors every item in one
- * launch of 256-thread CTAs and solves and refines every chunk of at most 24
- * of an item's right-hand sides in a CTA of its own, in a second launch; the
- * items go in two groups, and the second group's factor launch runs while
- * the first group's solves run on another stream.
+ * launch (narrow class: 128-thread CTAs, wide class: 256) and solves and
+ * refines every chunk of at most 24 of an item's right-hand sides in a CTA
+ * of its own, in a second launch; option "basis_pipe_groups" splits the
+ * items into groups whose chunk launches follow their own factor launch on a
+ * second stream.
  * The other outputs describe the solve launch. Pointers are host memory and
  * nullable. SFB_ERR_ARG for a shape that the precision and class do not
  * have. By default the first build of each precision times every shape of
