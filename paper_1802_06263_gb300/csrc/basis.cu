@@ -290,17 +290,25 @@ __device__ __forceinline__ void basis_body(const BasisArgs& a, int refine, int i
       Ty[f] = t;
     }
     __syncthreads();
+    // the diagonal scaling s = D^{-1/2}: any positive scaling serves (the
+    // factor, the solves and x += s d all read the same s), so the FP32 factor
+    // takes it from the FP32 reciprocal square root and keeps its FP64 pipe for
+    // the transmissibilities; the FP64 factor keeps it in FP64
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
       const int b = c / nx, i = c - b * nx;
       const double d = Tx[b * (nx + 1) + i] + Tx[b * (nx + 1) + i + 1] + Ty[b * nx + i] + Ty[(b + 1) * nx + i];
       Dg[c] = d;
-      Sg[c] = T(1.0 / sqrt(d));
+      if constexpr (sizeof(T) == 4) Sg[c] = rsqrtf(f64_to_f32_bits(d));
+      else Sg[c] = T(1.0 / sqrt(d));
     }
     __syncthreads();
     // D_{b-1} of the scaled matrix: s_{b-1,i} Ty[b][i] s_{b,i} (zero for row 0)
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
       const int b = c / nx, i = c - b * nx;
-      DLg[c] = b > 0 ? T(Ty[b * nx + i] / sqrt(Dg[c] * Dg[c - nx])) : T(0);
+      if constexpr (sizeof(T) == 4)
+        DLg[c] = b > 0 ? f64_to_f32_bits(Ty[b * nx + i]) * Sg[c] * Sg[c - nx] : T(0);
+      else
+        DLg[c] = b > 0 ? T(Ty[b * nx + i] / sqrt(Dg[c] * Dg[c - nx])) : T(0);
     }
     __syncthreads();
   }
