@@ -165,6 +165,8 @@ __device__ __forceinline__ void gemm_g(const T* __restrict__ G, const T* __restr
                                        int np, int C) {
   if (np == 64) gemm_g_np<T, 64>(G, U, out, add_base, np, C);
   else if (np == 128) gemm_g_np<T, 128>(G, U, out, add_base, np, C);
+  else if (np == 32) gemm_g_np<T, 32>(G, U, out, add_base, np, C);
+  else if (np == 96) gemm_g_np<T, 96>(G, U, out, add_base, np, C);
   else gemm_g_np<T, 0>(G, U, out, add_base, np, C);
 }
 
